@@ -1,0 +1,187 @@
+"""FP64 Ewald sums for Gaussian electrode charges and point electrolyte charges.
+
+Test infrastructure: this oracle is a plain, slow, CPU-only statement of the electrostatics of
+Sec. II.A (Eqs. 1-3). It is imported only by tests/, by __graft_entry__.smoke() and by bench.py's
+cpu_baseline leg; the GPU library never links, imports or calls it, and it shares no code with it.
+
+Model (Eqs. 1-2): electrolyte charges Q_j are points; electrode charges q_i are Gaussians
+rho_i(r) = q_i eta^3 pi^-3/2 exp(-eta^2 |r - r_i|^2).  The interaction energy of two such
+distributions at distance r follows from convolving the densities:
+
+    point-point        1/r
+    Gaussian-point     erf(eta r)/r
+    Gaussian-Gaussian  erf(eta r / sqrt 2)/r          (two width-eta Gaussians)
+    Gaussian self      q^2 eta / sqrt(2 pi)            (half the r -> 0 limit of the line above)
+
+The cell is orthorhombic and 3-D periodic with tin-foil boundary conditions (Sec. II.B).  Each
+1/r is split Ewald-wise as erfc(alpha r)/r + erf(alpha r)/r: the smooth erf(alpha r)/r part of
+every pair (Gaussians included, treated as points) goes to a direct reciprocal-space sum, the
+rest is summed in real space over every periodic image within r_c (no minimum-image
+shortcut, so cells shorter than 2 r_c are handled).  Real-space kernels:
+
+    point-point        erfc(alpha r)/r
+    Gaussian-point     (erfc(alpha r) - erfc(eta r))/r
+    Gaussian-Gaussian  (erfc(alpha r) - erfc(eta r / sqrt 2))/r
+
+and the reciprocal sum, for the potential at r from charges c_a at r_a,
+
+    phi_k(r) = (4 pi / V) sum_{k != 0} exp(-k^2 / 4 alpha^2) / k^2  Re[S(k) exp(-i k.r)],
+    S(k) = sum_a c_a exp(i k.r_a),
+
+with the point self-energy correction -(alpha/sqrt pi) c_a^2.  Energies carry the Coulomb
+constant KE so that potentials are in V, charges in e, lengths in A and energies in eV.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy.special import erfc
+
+KE = 14.3996454784          # e^2 / (4 pi eps0) in eV A (CODATA 2018)
+SQRT_PI = math.sqrt(math.pi)
+SQRT2 = math.sqrt(2.0)
+KMAX_EXPONENT = 27.6        # reciprocal terms below exp(-27.6) ~ 1e-12 of the leading one are dropped
+
+
+def default_kmax(alpha: float) -> float:
+    """Reciprocal cutoff |k| <= 2 alpha sqrt(27.6): exp(-k^2/4 alpha^2) <= 1e-12."""
+    return 2.0 * alpha * math.sqrt(KMAX_EXPONENT)
+
+
+def screened(r, alpha, beta):
+    """(erfc(alpha r) - erfc(beta r)) / r; beta=None means a point charge (erfc(beta r) = 0)."""
+    f = erfc(alpha * r)
+    if beta is not None:
+        f = f - erfc(beta * r)
+    return f / r
+
+
+def screened_dr(r, alpha, beta):
+    """d/dr of screened(r, alpha, beta)."""
+    g = -erfc(alpha * r) / (r * r) - (2.0 * alpha / SQRT_PI) * np.exp(-(alpha * r) ** 2) / r
+    if beta is not None:
+        g = g + erfc(beta * r) / (r * r) + (2.0 * beta / SQRT_PI) * np.exp(-(beta * r) ** 2) / r
+    return g
+
+
+def image_shifts(box, rcut) -> np.ndarray:
+    """Lattice vectors n*L that can bring a minimum-image difference within rcut.
+
+    A wrapped difference has |d| <= L/2 per axis, so image n matters only if |n| L - L/2 < r_c.
+    """
+    nmax = [int(math.floor(rcut / L + 0.5)) for L in box]
+    rng = [np.arange(-n, n + 1) for n in nmax]
+    n = np.stack(np.meshgrid(*rng, indexing="ij"), axis=-1).reshape(-1, 3)
+    # put the zero shift first so the self-exclusion below is easy to read
+    order = np.argsort((n * n).sum(1), kind="stable")
+    return n[order] * np.asarray(box)[None, :]
+
+
+def real_space(targets, sources, charges, box, rcut, alpha, beta, same=False, want_grad=False,
+               chunk=256):
+    """Real-space Ewald potential (and its gradient) at `targets` from all images of `sources`.
+
+    beta selects the kernel (see module docstring).  same=True means targets and sources are the
+    same set and the i == j, zero-shift term is excluded.
+    Returns phi [nt] (without KE) and, if want_grad, grad [nt, 3] = d phi / d r_target.
+    """
+    targets = np.asarray(targets, np.float64)
+    sources = np.asarray(sources, np.float64)
+    charges = np.asarray(charges, np.float64)
+    box = np.asarray(box, np.float64)
+    nt = targets.shape[0]
+    phi = np.zeros(nt)
+    grad = np.zeros((nt, 3)) if want_grad else None
+    if nt == 0 or sources.shape[0] == 0:
+        return (phi, grad) if want_grad else phi
+    shifts = image_shifts(box, rcut)
+    rc2 = rcut * rcut
+    for a in range(0, nt, chunk):
+        b = min(nt, a + chunk)
+        d0 = targets[a:b, None, :] - sources[None, :, :]
+        d0 -= box * np.round(d0 / box)
+        for si, s in enumerate(shifts):
+            d = d0 + s
+            r2 = np.einsum("ijk,ijk->ij", d, d)
+            m = r2 < rc2
+            if same and not np.any(s):
+                ii = np.arange(b - a)
+                m[ii, a + ii] = False
+            ti, sj = np.nonzero(m)
+            if ti.size == 0:
+                continue
+            r = np.sqrt(r2[ti, sj])
+            f = screened(r, alpha, beta) * charges[sj]
+            phi[a:b] += np.bincount(ti, weights=f, minlength=b - a)
+            if want_grad:
+                g = screened_dr(r, alpha, beta) * charges[sj] / r
+                for c in range(3):
+                    grad[a:b, c] += np.bincount(ti, weights=g * d[ti, sj, c], minlength=b - a)
+    return (phi, grad) if want_grad else phi
+
+
+def kvectors(box, kmax) -> np.ndarray:
+    """Half-space set of nonzero reciprocal vectors k = 2 pi m / L with |k| <= kmax."""
+    box = np.asarray(box, np.float64)
+    mmax = [int(math.floor(kmax * L / (2 * math.pi))) for L in box]
+    rng = [np.arange(-n, n + 1) for n in mmax]
+    m = np.stack(np.meshgrid(*rng, indexing="ij"), axis=-1).reshape(-1, 3)
+    half = (m[:, 0] > 0) | ((m[:, 0] == 0) & (m[:, 1] > 0)) | ((m[:, 0] == 0) & (m[:, 1] == 0) & (m[:, 2] > 0))
+    k = 2 * math.pi * m[half] / box[None, :]
+    k2 = (k * k).sum(1)
+    return k[k2 <= kmax * kmax]
+
+
+def recip_weights(k, box, alpha):
+    """Per half-space vector: 2 * (4 pi / V) exp(-k^2/4 alpha^2) / k^2 (factor 2 for -k)."""
+    V = float(np.prod(box))
+    k2 = (k * k).sum(1)
+    return 2.0 * (4.0 * math.pi / V) * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
+
+
+def recip_space(targets, sources, charges, box, alpha, kmax=None, want_grad=False, kchunk=2048):
+    """Reciprocal-space potential (and gradient) at `targets` from point charges at `sources`.
+
+    phi(r) = sum_{k half} w_k [Re S(k) cos(k.r) + Im S(k) sin(k.r)],
+    grad   = sum_{k half} w_k k [Im S(k) cos(k.r) - Re S(k) sin(k.r)],  w_k from recip_weights.
+    """
+    targets = np.asarray(targets, np.float64)
+    sources = np.asarray(sources, np.float64)
+    charges = np.asarray(charges, np.float64)
+    kmax = default_kmax(alpha) if kmax is None else kmax
+    k_all = kvectors(box, kmax)
+    w_all = recip_weights(k_all, box, alpha)
+    phi = np.zeros(targets.shape[0])
+    grad = np.zeros((targets.shape[0], 3)) if want_grad else None
+    for a in range(0, k_all.shape[0], kchunk):
+        k = k_all[a:a + kchunk]
+        w = w_all[a:a + kchunk]
+        ps = sources @ k.T
+        s_re = np.cos(ps).T @ charges
+        s_im = np.sin(ps).T @ charges
+        pt = targets @ k.T
+        ct, st = np.cos(pt), np.sin(pt)
+        phi += ct @ (w * s_re) + st @ (w * s_im)
+        if want_grad:
+            grad += (ct * (w * s_im) - st * (w * s_re)) @ k
+    return (phi, grad) if want_grad else phi
+
+
+def recip_matrix(positions, box, alpha, kmax=None, kchunk=2048):
+    """Reciprocal-space interaction matrix M_ab = sum_{k half} w_k cos(k.(r_a - r_b))
+    = C diag(w) C^T + S diag(w) S^T with C = cos(r k^T), S = sin(r k^T)."""
+    positions = np.asarray(positions, np.float64)
+    kmax = default_kmax(alpha) if kmax is None else kmax
+    k_all = kvectors(box, kmax)
+    w_all = recip_weights(k_all, box, alpha)
+    n = positions.shape[0]
+    M = np.zeros((n, n))
+    for a in range(0, k_all.shape[0], kchunk):
+        k = k_all[a:a + kchunk]
+        sw = np.sqrt(w_all[a:a + kchunk])
+        p = positions @ k.T
+        c = np.cos(p) * sw
+        s = np.sin(p) * sw
+        M += c @ c.T + s @ s.T
+    return M
