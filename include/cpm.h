@@ -1,0 +1,188 @@
+/*
+ * cpm.h - C ABI of the GB300 constant-potential-method (CPM) electrostatics library.
+ *
+ * The library computes, for fixed electrode sites carrying Gaussian charges and a mobile
+ * electrolyte of point charges in a 3-D periodic orthorhombic cell, the per-timestep CPM
+ * electrostatics of Tee & Searles (arXiv 2201.12963):
+ *
+ *   b      electrolyte-electrode vector of Eq. 3 (b = -(electrolyte potential at each electrode
+ *          site); Eq. 4 reads Psi = A q - b).  The "b" of q = S(psi - b) in other texts is -b.
+ *   q      electrode charges, q = S (b + dpsi v) with S the constraint-projected inverse
+ *          elastance (O A^-1, Eqs. 8-9, or O_1 O A^-1, Eqs. 13-15) and v the geometry vector.
+ *   F      forces on all sites, E the electrostatic energy.
+ *
+ * Geometry (Sec. II.B):
+ *   CPM_FF       finite field (Eqs. 10-11): v = d - z/L_z, one neutrality constraint;
+ *   CPM_DOUBLED  doubled cell (Eqs. 12-15): v = d, constraints on the whole cell and sub-cell 1;
+ *   CPM_SLAB     slab with z padded by slab_factor and the Yeh-Berkowitz dipole term, v = d.
+ * d = +1/2 on sites with side +1 and -1/2 on side -1 (Eq. 5).
+ *
+ * Units: lengths in Angstrom, charges in e, potentials in V, energies in eV, forces in eV/A.
+ * Coulomb constant 14.3996454784 eV A / e^2.
+ *
+ * Conventions for every entry point below:
+ *   - Return CPM_OK (0) or a negative cpm_status; no call aborts or throws across the ABI.
+ *   - "_dev" pointers are device memory owned by the caller; they must stay valid until the
+ *     work queued on `stream` completes.  "_host" pointers are host memory, read during the call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  All device work
+ *     is queued on it; the per-step calls never synchronise the host, never allocate memory and
+ *     can be captured into a CUDA graph.
+ *   - One context serves one stream at a time; it is not thread-safe.
+ *   - Errors a kernel detects (non-finite coordinates, a site outside the cell in z) are latched
+ *     in a device status word and returned by cpm_status().
+ *   - Electrolyte input is replica-major: replica r owns sites offsets[r] .. offsets[r+1]-1 of
+ *     xyzq (x, y, z, Q per site, float64).  x, y may be unwrapped; z must lie in [0, L_z).  Each
+ *     replica's electrolyte must be electrically neutral.
+ */
+#ifndef CPM_GB300_H
+#define CPM_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cpm_ctx cpm_ctx;
+
+enum cpm_geometry { CPM_FF = 0, CPM_DOUBLED = 1, CPM_SLAB = 2 };
+
+/* CPM_FP64: every kernel computes in float64.
+ * CPM_MIXED: pair, B-spline and mesh work and the stored S in float32 with compensated or float64
+ * accumulation; A, its Cholesky factorisation, the neutrality projection and all energy sums stay
+ * float64. */
+enum cpm_precision { CPM_FP64 = 0, CPM_MIXED = 1 };
+
+enum cpm_status {
+  CPM_OK = 0,
+  CPM_ERR_ARG = -1,        /* invalid argument (null pointer, size, parameter out of range) */
+  CPM_ERR_CUDA = -2,       /* a CUDA runtime call failed; see cpm_last_error() */
+  CPM_ERR_NOT_SPD = -3,    /* Cholesky factorisation of A failed (A not positive definite) */
+  CPM_ERR_NONFINITE = -4,  /* non-finite coordinate or charge seen by a kernel */
+  CPM_ERR_CAPACITY = -5,   /* n_rep or a replica's site count above the build-time capacity */
+  CPM_ERR_DOMAIN = -6,     /* an electrolyte site outside [0, L_z) in z */
+  CPM_ERR_TIMEOUT = -7,    /* a bounded device-side wait gave up */
+  CPM_ERR_LIBRARY = -8,    /* cuFFT / cuBLAS / cuSOLVER reported an error */
+  CPM_ERR_NOMEM = -9       /* device allocation failed during build */
+};
+
+typedef struct {
+  double box[3];        /* physical cell Lx, Ly, Lz (A); for CPM_DOUBLED Lz is the doubled length */
+  double eta;           /* Gaussian width of Eq. 2 (1/A), > 0 */
+  double alpha;         /* Ewald splitting parameter (1/A), 0 < alpha < eta/sqrt(2) */
+  double rcut;          /* real-space cutoff (A): every periodic image within rcut is summed */
+  double slab_factor;   /* CPM_SLAB: the Ewald box is (Lx, Ly, slab_factor*Lz); ignored otherwise */
+  double kmax_build;    /* reciprocal cutoff for building A (1/A); <= 0 selects 2 alpha sqrt(27.6) */
+  int32_t grid[3];      /* SPME mesh K1, K2, K3 (each >= 2*spme_order, K3 even) */
+  int32_t spme_order;   /* cardinal B-spline order p, 3 <= p <= 8 */
+  int32_t geometry;     /* enum cpm_geometry */
+  int32_t precision;    /* enum cpm_precision */
+  int32_t max_replicas; /* capacity: largest n_rep accepted by the per-step calls, >= 1 */
+  int32_t max_elyt;     /* capacity: largest electrolyte site count of one replica, >= 1 */
+} cpm_params;
+
+/*
+ * cpm_build_matrix - build the elastance A (Eq. 3) of a fixed electrode, factorise it and keep
+ * the projected inverse S (Eqs. 8-9 / 13-15; precomputed once because the electrodes are fixed,
+ * Sec. II.A), A^-1 C, (C^T A^-1 C)^-1 and S v, plus every workspace the per-step calls need.
+ *
+ *   p               parameters (copied).
+ *   n_elec          number of electrode sites N_e >= 2.
+ *   elec_xyz_host   [N_e*3] float64 positions (A), row-major (x, y, z).
+ *   elec_side_host  [N_e] int32, +1 or -1: the electrode each site belongs to (d = +-1/2).
+ *   elec_cell_host  [N_e] int32 sub-cell label 0/1 (CPM_DOUBLED only; NULL otherwise).
+ *   stream          stream for the build work; the call synchronises it before returning.
+ *   out             receives the new context (set to NULL on failure).
+ * A is built in float64 on the GPU: real-space Gaussian-Gaussian pairs over all images within
+ * rcut, reciprocal part as a direct Ewald sum up to kmax_build, self terms, and for CPM_SLAB the
+ * dipole term.  Returns CPM_ERR_NOT_SPD if the Cholesky factorisation fails, CPM_ERR_NOMEM if
+ * device memory runs out.
+ */
+int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
+                     const int32_t* elec_side_host, const int32_t* elec_cell_host, void* stream,
+                     cpm_ctx** out);
+
+/*
+ * cpm_step_charges - one CPM charge update for n_rep replicas sharing the electrode (Sec. II.A,
+ * "the main computational burden ... is to obtain b"): cell list, real-space b, SPME spread,
+ * FFT, influence function, inverse FFT, gather at the electrode sites, S-apply and the
+ * neutrality projection.
+ *
+ *   n_rep             1 <= n_rep <= max_replicas.
+ *   elyt_offsets_dev  [n_rep+1] int32 site offsets (offsets[0] = 0).
+ *   elyt_xyzq_dev     [offsets[n_rep]*4] float64 (x, y, z, Q) per electrolyte site.
+ *   dpsi_dev          [n_rep] float64 potential differences (V).
+ *   q_dev             [n_rep*N_e] float64 output charges (e), replica-major.
+ *   b_dev             [n_rep*N_e] float64 output b (V) or NULL.
+ *   psibar_dev        [n_rep*ncons] float64 output offset potentials (V) or NULL; ncons = 1, or 2
+ *                     for CPM_DOUBLED (psibar, psibar_1 of Eq. 12).
+ */
+int cpm_step_charges(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
+                     const double* elyt_xyzq_dev, const double* dpsi_dev, double* q_dev,
+                     double* b_dev, double* psibar_dev, void* stream);
+
+/*
+ * cpm_forces - forces (and optionally energies) for given electrode charges q_dev
+ * [n_rep*N_e]: SPME of all charges plus real-space pair forces, with the finite-field force
+ * -Q dpsi/L_z (Sec. II.B.1) or the slab dipole force.
+ *
+ *   f_elyt_dev   [offsets[n_rep]*3] float64 forces on the electrolyte sites (eV/A) or NULL.
+ *   f_elec_dev   [n_rep*N_e*3] float64 forces on the electrode sites or NULL.
+ *   energy_dev   [n_rep*2] float64 or NULL: per replica (U, H).  U is the Coulomb energy of
+ *                Eq. 3 (plus the slab dipole term); H = U - dpsi q^T v (+ dpsi/L_z sum Q_j Z_j for
+ *                CPM_FF) is the constant-potential energy whose gradient is minus the force.
+ */
+int cpm_forces(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
+               const double* elyt_xyzq_dev, const double* dpsi_dev, const double* q_dev,
+               double* f_elyt_dev, double* f_elec_dev, double* energy_dev, void* stream);
+
+/* cpm_energy - energies only: cpm_forces with both force outputs NULL (energy_dev required). */
+int cpm_energy(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
+               const double* elyt_xyzq_dev, const double* dpsi_dev, const double* q_dev,
+               double* energy_dev, void* stream);
+
+/*
+ * cpm_step - one whole electrostatic step: cpm_step_charges followed by cpm_forces on the new
+ * charges, sharing the cell list.  Outputs as above; q_dev is required, the rest may be NULL.
+ */
+int cpm_step(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
+             const double* elyt_xyzq_dev, const double* dpsi_dev, double* q_dev, double* psibar_dev,
+             double* f_elyt_dev, double* f_elec_dev, double* energy_dev, void* stream);
+
+/*
+ * cpm_capacitance - dQ/d(dpsi) = e_+^T S v (e/V): the charge response of all side +1 sites to the
+ * potential difference (q is linear in dpsi, Eqs. 8, 11, 14).  For CPM_DOUBLED it covers the
+ * positive electrodes of both sub-cells.  Host output, no device work.
+ */
+int cpm_capacitance(const cpm_ctx* ctx, double* dq_ddpsi_host);
+
+/*
+ * cpm_copy_matrix - copy a build-time matrix to host memory (diagnostics and tests).
+ *   which = 0: S (float64, N_e x N_e row-major); 1: S v (N_e); 2: A^-1 C (N_e x ncons row-major).
+ */
+int cpm_copy_matrix(const cpm_ctx* ctx, int32_t which, double* host_out);
+
+/* cpm_info - sizes: n_elec, ncons, the mesh point count and the real-space cell count. */
+int cpm_info(const cpm_ctx* ctx, int32_t* n_elec, int32_t* ncons, int64_t* mesh_points,
+             int32_t* n_cells);
+
+/*
+ * cpm_status - synchronise `stream`, then return and clear the device status word: CPM_OK, or the
+ * first error a kernel latched (CPM_ERR_NONFINITE, CPM_ERR_DOMAIN, CPM_ERR_TIMEOUT).
+ */
+int cpm_status(cpm_ctx* ctx, void* stream);
+
+/* cpm_destroy - free the context and everything it owns (NULL is accepted). */
+void cpm_destroy(cpm_ctx* ctx);
+
+/* cpm_strerror - static description of a cpm_status code. */
+const char* cpm_strerror(int status);
+
+/* cpm_last_error - detail of the last failure in the calling thread ("" if none). */
+const char* cpm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_GB300_H */

@@ -1,0 +1,230 @@
+"""GB300 constant-potential-method (CPM) electrostatics: thin Python binding of the C ABI.
+
+Every function here marshals arguments (torch device tensors -> raw pointers, numpy host arrays
+-> host pointers) and calls the entry point of the same name in libcpm_gb300.so; all arithmetic
+runs in the library's CUDA kernels.  Importing the package loads the library and raises if it is
+missing: there is no CPU fallback.  The C declarations and their contracts are in include/cpm.h.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+CPM_FF, CPM_DOUBLED, CPM_SLAB = 0, 1, 2
+CPM_FP64, CPM_MIXED = 0, 1
+GEOMETRY = {"ff": CPM_FF, "dc": CPM_DOUBLED, "slab": CPM_SLAB}
+PRECISION = {"fp64": CPM_FP64, "mixed": CPM_MIXED}
+
+EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
+            "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_destroy", "cpm_strerror", "cpm_last_error")
+
+
+class CpmParams(ctypes.Structure):
+    """Mirror of cpm_params in include/cpm.h."""
+    _fields_ = [("box", ctypes.c_double * 3), ("eta", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("rcut", ctypes.c_double), ("slab_factor", ctypes.c_double), ("kmax_build", ctypes.c_double),
+                ("grid", ctypes.c_int32 * 3), ("spme_order", ctypes.c_int32), ("geometry", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("max_replicas", ctypes.c_int32), ("max_elyt", ctypes.c_int32)]
+
+
+class CPMError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {_lib.cpm_strerror(status).decode()} ({status})"
+        detail = _lib.cpm_last_error().decode()
+        if detail:
+            msg += f": {detail}"
+        super().__init__(msg)
+
+
+def _load():
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise ImportError(f"CPM CUDA library not built ({path}); run __graft_entry__.build() "
+                          "or python -m paper_2201_12963_gb300.build")
+    lib = ctypes.CDLL(path)
+    vp, i32, pd, pi32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p
+    lib.cpm_build_matrix.argtypes = [ctypes.POINTER(CpmParams), i32, pd, pi32, pi32, vp, ctypes.POINTER(vp)]
+    lib.cpm_step_charges.argtypes = [vp, i32, pi32, pd, pd, pd, pd, pd, vp]
+    lib.cpm_forces.argtypes = [vp, i32, pi32, pd, pd, pd, pd, pd, pd, vp]
+    lib.cpm_energy.argtypes = [vp, i32, pi32, pd, pd, pd, pd, vp]
+    lib.cpm_step.argtypes = [vp, i32, pi32, pd, pd, pd, pd, pd, pd, pd, vp]
+    lib.cpm_capacitance.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    lib.cpm_copy_matrix.argtypes = [vp, i32, pd]
+    lib.cpm_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64),
+                             ctypes.POINTER(i32)]
+    lib.cpm_status.argtypes = [vp, vp]
+    lib.cpm_destroy.argtypes = [vp]
+    lib.cpm_destroy.restype = None
+    lib.cpm_strerror.argtypes = [ctypes.c_int]
+    lib.cpm_strerror.restype = ctypes.c_char_p
+    lib.cpm_last_error.argtypes = []
+    lib.cpm_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name not in ("cpm_destroy", "cpm_strerror", "cpm_last_error"):
+            getattr(lib, name).restype = ctypes.c_int
+    return lib
+
+
+_lib = _load()
+
+
+def library():
+    """The loaded ctypes.CDLL (for symbol checks)."""
+    return _lib
+
+
+def _check(status: int, where: str):
+    if status != 0:
+        raise CPMError(status, where)
+
+
+def make_params(box, eta, alpha, rcut, grid, order=5, geometry="ff", precision="fp64", max_replicas=1,
+                max_elyt=1, slab_factor=3.0, kmax_build=0.0) -> CpmParams:
+    p = CpmParams()
+    for d in range(3):
+        p.box[d] = float(box[d])
+        p.grid[d] = int(grid[d])
+    p.eta, p.alpha, p.rcut = float(eta), float(alpha), float(rcut)
+    p.slab_factor, p.kmax_build = float(slab_factor), float(kmax_build)
+    p.spme_order = int(order)
+    p.geometry = GEOMETRY[geometry] if isinstance(geometry, str) else int(geometry)
+    p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    p.max_replicas, p.max_elyt = int(max_replicas), int(max_elyt)
+    return p
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def _dev(t, dtype, name, numel=None, optional=False):
+    """Raw pointer of a contiguous CUDA tensor of the given torch dtype (or None if optional)."""
+    if t is None:
+        if optional:
+            return None
+        raise ValueError(f"{name} is required")
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA torch.Tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"{name} has {t.numel()} elements, needs {numel}")
+    return t.data_ptr()
+
+
+class Context:
+    """Owning handle of a cpm_ctx (destroyed with the object)."""
+
+    def __init__(self, handle, params: CpmParams):
+        self.handle = handle
+        self.params = params
+        n, c, m, nc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int32()
+        _check(_lib.cpm_info(handle, ctypes.byref(n), ctypes.byref(c), ctypes.byref(m), ctypes.byref(nc)), "cpm_info")
+        self.n_elec, self.ncons, self.mesh_points, self.n_cells = n.value, c.value, m.value, nc.value
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.cpm_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def cpm_build_matrix(params: CpmParams, elec_xyz, elec_side, elec_cell=None, stream=None) -> Context:
+    xyz = np.ascontiguousarray(elec_xyz, dtype=np.float64)
+    side = np.ascontiguousarray(elec_side, dtype=np.int32)
+    cell = None if elec_cell is None else np.ascontiguousarray(elec_cell, dtype=np.int32)
+    n = xyz.shape[0]
+    if xyz.shape != (n, 3) or side.shape != (n,) or (cell is not None and cell.shape != (n,)):
+        raise ValueError("electrode arrays have inconsistent shapes")
+    out = ctypes.c_void_p()
+    st = _stream_ptr(stream)
+    s = _lib.cpm_build_matrix(ctypes.byref(params), n, xyz.ctypes.data, side.ctypes.data,
+                              None if cell is None else cell.ctypes.data, st, ctypes.byref(out))
+    _check(s, "cpm_build_matrix")
+    return Context(out.value, params)
+
+
+def _common(ctx, n_rep, offsets, xyzq, dpsi):
+    import torch
+    p_off = _dev(offsets, torch.int32, "offsets", n_rep + 1)
+    p_x = _dev(xyzq, torch.float64, "xyzq")
+    p_d = _dev(dpsi, torch.float64, "dpsi", n_rep)
+    return p_off, p_x, p_d
+
+
+def cpm_step_charges(ctx: Context, n_rep, offsets, xyzq, dpsi, q, b=None, psibar=None, stream=None):
+    import torch
+    p_off, p_x, p_d = _common(ctx, n_rep, offsets, xyzq, dpsi)
+    ne = ctx.n_elec
+    s = _lib.cpm_step_charges(ctx.handle, n_rep, p_off, p_x, p_d, _dev(q, torch.float64, "q", n_rep * ne),
+                              _dev(b, torch.float64, "b", n_rep * ne, True),
+                              _dev(psibar, torch.float64, "psibar", n_rep * ctx.ncons, True), _stream_ptr(stream))
+    _check(s, "cpm_step_charges")
+
+
+def cpm_forces(ctx: Context, n_rep, offsets, xyzq, dpsi, q, f_elyt=None, f_elec=None, energy=None, stream=None):
+    import torch
+    p_off, p_x, p_d = _common(ctx, n_rep, offsets, xyzq, dpsi)
+    ne = ctx.n_elec
+    s = _lib.cpm_forces(ctx.handle, n_rep, p_off, p_x, p_d, _dev(q, torch.float64, "q", n_rep * ne),
+                        _dev(f_elyt, torch.float64, "f_elyt", None, True),
+                        _dev(f_elec, torch.float64, "f_elec", n_rep * ne * 3, True),
+                        _dev(energy, torch.float64, "energy", 2 * n_rep, True), _stream_ptr(stream))
+    _check(s, "cpm_forces")
+
+
+def cpm_energy(ctx: Context, n_rep, offsets, xyzq, dpsi, q, energy, stream=None):
+    import torch
+    p_off, p_x, p_d = _common(ctx, n_rep, offsets, xyzq, dpsi)
+    s = _lib.cpm_energy(ctx.handle, n_rep, p_off, p_x, p_d, _dev(q, torch.float64, "q", n_rep * ctx.n_elec),
+                        _dev(energy, torch.float64, "energy", 2 * n_rep), _stream_ptr(stream))
+    _check(s, "cpm_energy")
+
+
+def cpm_step(ctx: Context, n_rep, offsets, xyzq, dpsi, q, psibar=None, f_elyt=None, f_elec=None, energy=None,
+             stream=None):
+    import torch
+    p_off, p_x, p_d = _common(ctx, n_rep, offsets, xyzq, dpsi)
+    ne = ctx.n_elec
+    s = _lib.cpm_step(ctx.handle, n_rep, p_off, p_x, p_d, _dev(q, torch.float64, "q", n_rep * ne),
+                      _dev(psibar, torch.float64, "psibar", n_rep * ctx.ncons, True),
+                      _dev(f_elyt, torch.float64, "f_elyt", None, True),
+                      _dev(f_elec, torch.float64, "f_elec", n_rep * ne * 3, True),
+                      _dev(energy, torch.float64, "energy", 2 * n_rep, True), _stream_ptr(stream))
+    _check(s, "cpm_step")
+
+
+def cpm_capacitance(ctx: Context) -> float:
+    v = ctypes.c_double()
+    _check(_lib.cpm_capacitance(ctx.handle, ctypes.byref(v)), "cpm_capacitance")
+    return v.value
+
+
+def cpm_copy_matrix(ctx: Context, which: int) -> np.ndarray:
+    n = ctx.n_elec
+    shape = {0: (n, n), 1: (n,), 2: (n, ctx.ncons)}[which]
+    out = np.zeros(shape, dtype=np.float64)
+    _check(_lib.cpm_copy_matrix(ctx.handle, which, out.ctypes.data), "cpm_copy_matrix")
+    return out
+
+
+def cpm_status(ctx: Context, stream=None) -> int:
+    return int(_lib.cpm_status(ctx.handle, _stream_ptr(stream)))
+
+
+def cpm_strerror(status: int) -> str:
+    return _lib.cpm_strerror(status).decode()

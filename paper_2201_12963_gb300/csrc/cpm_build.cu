@@ -1,0 +1,653 @@
+// Build of the constant-potential context: elastance A (Eq. 3) in float64 on the GPU, its
+// Cholesky factorisation and inverse, the projected inverse S = O A^-1 (Eqs. 8-9) or
+// O_1 O A^-1 (Eqs. 13-15), S v, the fixed electrode B-spline stencils, the SPME influence
+// function and every workspace the per-step calls use.  Also: status, info and teardown.
+#include "cpm_internal.cuh"
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstring>
+#include <vector>
+
+namespace cpm {
+
+static thread_local std::string g_last_error;
+
+void set_error(const char* fmt, ...) {
+  char buf[1024];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+}
+
+// ------------------------------------------------------------------------------------------
+// A: real-space Gaussian-Gaussian part over every periodic image within rcut (float64).
+//   A_ij = KE sum_n (erfc(alpha r) - erfc(eta r / sqrt 2)) / r,  r = |r_i - r_j + n L| < rcut,
+//   excluding i == j at n = 0; plus the self term KE (sqrt2 eta - 2 alpha)/sqrt(pi) on the diagonal.
+// ------------------------------------------------------------------------------------------
+__global__ void k_build_areal(const double4_32a* __restrict__ pos, int ne, int lda, double bx, double by,
+                              double bz, const double3* __restrict__ shifts, int nshift,
+                              double alpha, double beta, double rc2, double self_term,
+                              double* __restrict__ A) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= ne || j >= ne) return;
+  const double4_32a a = pos[i], b = pos[j];
+  double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
+  dx -= bx * rint(dx / bx);
+  dy -= by * rint(dy / by);
+  dz -= bz * rint(dz / bz);
+  double s = 0.0;
+  for (int k = 0; k < nshift; ++k) {
+    const double3 sh = shifts[k];
+    const double x = dx + sh.x, y = dy + sh.y, z = dz + sh.z;
+    const double r2 = x * x + y * y + z * z;
+    if (r2 < rc2 && !(i == j && sh.x == 0.0 && sh.y == 0.0 && sh.z == 0.0)) {
+      const double r = sqrt(r2);
+      s += (erfc(alpha * r) - erfc(beta * r)) / r;
+    }
+  }
+  if (i == j) s += self_term;
+  A[(size_t)j * lda + i] = KE * s;   // symmetric: column-major and row-major coincide
+}
+
+// Reciprocal-space factor table for one chunk of half-space k-vectors, column-major [ne x 2kc]:
+// column 2c = sqrt(w_k) cos(k.r_i), column 2c+1 = sqrt(w_k) sin(k.r_i), so that
+// T T^T = sum_k w_k cos(k.(r_i - r_j)) (the direct Ewald reciprocal sum).
+__global__ void k_build_trig(const double4_32a* __restrict__ pos, int ne, const double4_32a* __restrict__ kv,
+                             int kc, double* __restrict__ T) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int c = blockIdx.y;
+  if (i >= ne || c >= kc) return;
+  const double4_32a k = kv[c];   // (kx, ky, kz, sqrt(w))
+  const double4_32a r = pos[i];
+  double sn, cs;
+  sincos(k.x * r.x + k.y * r.y + k.z * r.z, &sn, &cs);
+  T[(size_t)(2 * c) * ne + i] = k.w * cs;
+  T[(size_t)(2 * c + 1) * ne + i] = k.w * sn;
+}
+
+// Slab (Yeh-Berkowitz) term on the lower triangle: A_ij += KE (4 pi / V) z_i z_j.
+__global__ void k_build_slab(const double* __restrict__ z, int ne, int lda, double coef, double* A) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= ne || j >= ne || i < j) return;
+  A[(size_t)j * lda + i] += coef * z[i] * z[j];
+}
+
+// Copy the lower triangle (column-major) onto the upper one: X_ji = X_ij for i > j.
+__global__ void k_symmetrize_lower(double* X, int n, int lda) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n || i <= j) return;
+  X[(size_t)i * lda + j] = X[(size_t)j * lda + i];
+}
+
+// W[:,0] = A^-1 e, W[:,1] = A^-1 e_1 (row sums over all / sub-cell-1 columns), one warp per row.
+__global__ void k_build_w(const double* __restrict__ Ainv, int n, int lda, const double* __restrict__ c1,
+                          double* __restrict__ W) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = Ainv + (size_t)warp * lda;
+  double s0 = 0.0, s1 = 0.0;
+  for (int j = lane; j < n; j += 32) {
+    const double a = row[j];
+    s0 += a;
+    s1 += a * c1[j];
+  }
+  s0 = warp_sum(s0);
+  s1 = warp_sum(s1);
+  if (lane == 0) {
+    W[2 * warp] = s0;
+    W[2 * warp + 1] = s1;
+  }
+}
+
+// S_ij = (A^-1)_ij - sum_ab W_ia M_ab W_jb  (in place).
+__global__ void k_build_s(double* S, int n, int lda, const double* __restrict__ W, int ncons,
+                          double m00, double m01, double m10, double m11) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const double wi0 = W[2 * i], wj0 = W[2 * j];
+  double corr = wi0 * m00 * wj0;
+  if (ncons == 2) {
+    const double wi1 = W[2 * i + 1], wj1 = W[2 * j + 1];
+    corr += wi0 * m01 * wj1 + wi1 * m10 * wj0 + wi1 * m11 * wj1;
+  }
+  S[(size_t)i * lda + j] -= corr;
+}
+
+// y = S x, one warp per row (float64).
+__global__ void k_matvec64(const double* __restrict__ S, int n, int lda, const double* __restrict__ x,
+                           double* __restrict__ y) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= n) return;
+  const double* row = S + (size_t)warp * lda;
+  double s = 0.0;
+  for (int j = lane; j < n; j += 32) s += row[j] * x[j];
+  s = warp_sum(s);
+  if (lane == 0) y[warp] = s;
+}
+
+__global__ void k_to_float(const double* __restrict__ S, int n, int lda, float* __restrict__ D, int ldd) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y;
+  if (j >= ldd) return;
+  D[(size_t)i * ldd + j] = (j < n) ? (float)S[(size_t)i * lda + j] : 0.0f;
+}
+
+// ------------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------------
+// Cardinal B-spline weights (same recursion as the device helper, float64 on the host).
+static void bspline_host(double f, int p, double* w, double* dw) {
+  for (int t = 0; t < PMAX; ++t) w[t] = dw[t] = 0.0;
+  w[0] = 1.0;
+  for (int n = 2; n <= p; ++n) {
+    if (n == p)
+      for (int t = 0; t < n; ++t) dw[t] = w[t] - (t > 0 ? w[t - 1] : 0.0);
+    for (int t = n - 1; t >= 0; --t) {
+      const double a = (t < n - 1) ? w[t] : 0.0;
+      const double b = (t > 0) ? w[t - 1] : 0.0;
+      w[t] = ((f + t) * a + (n - f - t) * b) / (n - 1);
+    }
+  }
+}
+
+static double wrap_coord(double x, double L) {
+  double y = x - L * std::floor(x / L);
+  if (y >= L) y -= L;
+  if (y < 0) y = 0;
+  return y;
+}
+
+template <typename T> static int dev_alloc(T** p, size_t count) {
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc(%zu bytes): %s", count * sizeof(T), cudaGetErrorString(e));
+    *p = nullptr;
+    return e == cudaErrorMemoryAllocation ? CPM_ERR_NOMEM : CPM_ERR_CUDA;
+  }
+  return CPM_OK;
+}
+
+template <typename T> static int upload(T** d, const std::vector<T>& h, cudaStream_t st) {
+  CPM_TRY(dev_alloc(d, h.size()));
+  CPM_CUDA(cudaMemcpyAsync(*d, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, st));
+  return CPM_OK;
+}
+
+static int validate(const cpm_params* p, int32_t ne, const double* xyz, const int32_t* side,
+                    const int32_t* cell) {
+  if (!p || !xyz || !side || ne < 2) return CPM_ERR_ARG;
+  for (int d = 0; d < 3; ++d)
+    if (!(p->box[d] > 0) || !std::isfinite(p->box[d]) || p->grid[d] < 2 * p->spme_order) return CPM_ERR_ARG;
+  if (p->grid[2] % 2) return CPM_ERR_ARG;
+  if (!(p->eta > 0) || !(p->alpha > 0) || !(p->alpha < p->eta / std::sqrt(2.0))) return CPM_ERR_ARG;
+  if (!(p->rcut > 0)) return CPM_ERR_ARG;
+  if (p->spme_order < 3 || p->spme_order > PMAX) return CPM_ERR_ARG;
+  if (p->geometry < CPM_FF || p->geometry > CPM_SLAB) return CPM_ERR_ARG;
+  if (p->precision != CPM_FP64 && p->precision != CPM_MIXED) return CPM_ERR_ARG;
+  if (p->max_replicas < 1 || p->max_elyt < 1) return CPM_ERR_ARG;
+  if (p->geometry == CPM_SLAB && !(p->slab_factor >= 1.0)) return CPM_ERR_ARG;
+  if (p->geometry == CPM_DOUBLED && !cell) return CPM_ERR_ARG;
+  for (int i = 0; i < ne; ++i) {
+    if (side[i] != 1 && side[i] != -1) return CPM_ERR_ARG;
+    if (p->geometry == CPM_DOUBLED && cell[i] != 0 && cell[i] != 1) return CPM_ERR_ARG;
+    for (int d = 0; d < 3; ++d)
+      if (!std::isfinite(xyz[3 * i + d])) return CPM_ERR_NONFINITE;
+  }
+  return CPM_OK;
+}
+
+// Influence function on the half spectrum [K1][K2][K3/2+1], incl. KE:
+//   G(m) = KE (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2 * prod_d 1 / |sum_{t=0}^{p-2} M_p(t+1) e^{2 pi i m_d t / K_d}|^2
+// (Essmann et al. 1995); G(0) = 0, and G = 0 where an odd order's denominator vanishes (Nyquist).
+static void influence_host(const cpm_ctx* c, std::vector<double>& G) {
+  const int K1 = c->K[0], K2 = c->K[1], K3 = c->K[2], p = c->P;
+  double w[PMAX], dw[PMAX];
+  bspline_host(0.0, p, w, dw);   // w[t] = M_p(t)
+  std::vector<double> den[3];
+  for (int d = 0; d < 3; ++d) {
+    const int K = c->K[d];
+    den[d].resize(K);
+    for (int n = 0; n < K; ++n) {
+      double re = 0, im = 0;
+      for (int t = 0; t <= p - 2; ++t) {
+        const double ph = 2.0 * PI * n * t / K;
+        re += w[t + 1] * std::cos(ph);
+        im += w[t + 1] * std::sin(ph);
+      }
+      den[d][n] = re * re + im * im;
+    }
+  }
+  const int K3h = K3 / 2 + 1;
+  G.assign((size_t)K1 * K2 * K3h, 0.0);
+  const double a2 = c->p.alpha * c->p.alpha;
+  for (int n1 = 0; n1 < K1; ++n1) {
+    const int m1 = n1 <= K1 / 2 ? n1 : n1 - K1;
+    for (int n2 = 0; n2 < K2; ++n2) {
+      const int m2 = n2 <= K2 / 2 ? n2 : n2 - K2;
+      for (int n3 = 0; n3 < K3h; ++n3) {
+        const int m3 = n3;
+        if (m1 == 0 && m2 == 0 && m3 == 0) continue;
+        const double d = den[0][n1] * den[1][n2] * den[2][n3];
+        if (den[0][n1] < 1e-10 || den[1][n2] < 1e-10 || den[2][n3] < 1e-10) continue;
+        const double kx = 2.0 * PI * m1 / c->ebox[0], ky = 2.0 * PI * m2 / c->ebox[1],
+                     kz = 2.0 * PI * m3 / c->ebox[2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        G[((size_t)n1 * K2 + n2) * K3h + n3] = KE * 4.0 * PI / c->V * std::exp(-k2 / (4.0 * a2)) / k2 / d;
+      }
+    }
+  }
+}
+
+static int make_plans(cpm_ctx* c) {
+  int n[3] = {c->K[0], c->K[1], c->K[2]};
+  const int batches[2] = {1, c->p.max_replicas};
+  for (int b = 0; b < 2; ++b) {
+    if (b == 1 && batches[1] == 1) break;
+    const cufftType tf = c->mixed ? CUFFT_R2C : CUFFT_D2Z;
+    const cufftType tb = c->mixed ? CUFFT_C2R : CUFFT_Z2D;
+    int nr[3] = {n[0], n[1], n[2]};
+    int nh[3] = {n[0], n[1], n[2] / 2 + 1};
+    CPM_LIB(cufftPlanMany(&c->plan_r2c[b], 3, n, nr, 1, (int)c->Mr_s, nh, 1, (int)c->Mc_s, tf,
+                          batches[b]) == CUFFT_SUCCESS, "cufftPlanMany(r2c)");
+    CPM_LIB(cufftPlanMany(&c->plan_c2r[b], 3, n, nh, 1, (int)c->Mc_s, nr, 1, (int)c->Mr_s, tb,
+                          batches[b]) == CUFFT_SUCCESS, "cufftPlanMany(c2r)");
+    c->have_plan[b] = true;
+  }
+  return CPM_OK;
+}
+
+static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side, const int32_t* cell,
+                 cudaStream_t st) {
+  const cpm_params& p = c->p;
+  c->ne = ne;
+  c->ncons = (p.geometry == CPM_DOUBLED) ? 2 : 1;
+  c->mixed = (p.precision == CPM_MIXED);
+  for (int d = 0; d < 3; ++d) c->ebox[d] = p.box[d];
+  if (p.geometry == CPM_SLAB) c->ebox[2] *= p.slab_factor;
+  c->V = c->ebox[0] * c->ebox[1] * c->ebox[2];
+  c->Lz = p.box[2];
+  c->P = p.spme_order;
+  for (int d = 0; d < 3; ++d) c->K[d] = p.grid[d];
+  c->Mr = (long long)c->K[0] * c->K[1] * c->K[2];
+  c->Mc = (long long)c->K[0] * c->K[1] * (c->K[2] / 2 + 1);
+  c->Mr_s = (c->Mr + 63) & ~63LL;
+  c->Mc_s = (c->Mc + 31) & ~31LL;
+  CPM_CUDA(cudaGetDevice(&c->dev));
+
+  // real-space cell grid: edge >= rcut/2, stencil half-width ceil(rcut/edge)
+  c->ncell = 1;
+  for (int d = 0; d < 3; ++d) {
+    c->nc[d] = std::max(1, (int)std::floor(c->ebox[d] / (0.5 * p.rcut)));
+    c->edge[d] = c->ebox[d] / c->nc[d];
+    c->sten[d] = (int)std::ceil(p.rcut / c->edge[d] - 1e-12);
+    c->ncell *= c->nc[d];
+  }
+
+  // ---------------- electrode host data ----------------
+  std::vector<double4_32a> pos(ne);
+  std::vector<double> zraw(ne), v(ne), c1(ne, 0.0);
+  for (int i = 0; i < ne; ++i) {
+    pos[i] = make_double4_32a(wrap_coord(xyz[3 * i], c->ebox[0]), wrap_coord(xyz[3 * i + 1], c->ebox[1]),
+                          wrap_coord(xyz[3 * i + 2], c->ebox[2]), 0.0);
+    zraw[i] = xyz[3 * i + 2];
+    const double d = 0.5 * side[i];
+    v[i] = (p.geometry == CPM_FF) ? d - zraw[i] / c->Lz : d;
+    if (p.geometry == CPM_DOUBLED) c1[i] = cell[i] == 1 ? 1.0 : 0.0;
+  }
+  // cell sort (stable by index)
+  std::vector<int> flat(ne), count(c->ncell + 1, 0);
+  std::vector<int4> cc(ne);
+  for (int i = 0; i < ne; ++i) {
+    int ci[3];
+    const double r[3] = {pos[i].x, pos[i].y, pos[i].z};
+    for (int d = 0; d < 3; ++d) ci[d] = std::min(c->nc[d] - 1, std::max(0, (int)std::floor(r[d] / c->edge[d])));
+    flat[i] = (ci[0] * c->nc[1] + ci[1]) * c->nc[2] + ci[2];
+    cc[i] = make_int4(ci[0], ci[1], ci[2], flat[i]);
+    count[flat[i] + 1]++;
+  }
+  for (int k = 0; k < c->ncell; ++k) count[k + 1] += count[k];
+  std::vector<int> start(count.begin(), count.end()), cursor(count.begin(), count.end() - 1);
+  std::vector<int> sorted(ne);
+  std::vector<double4_32a> loc64(ne);
+  std::vector<float4> loc32(ne);
+  std::vector<int4> cellc(ne);
+  for (int i = 0; i < ne; ++i) {
+    const int s = cursor[flat[i]]++;
+    sorted[s] = i;
+    const double lx = pos[i].x - cc[i].x * c->edge[0], ly = pos[i].y - cc[i].y * c->edge[1],
+                 lz = pos[i].z - cc[i].z * c->edge[2];
+    loc64[s] = make_double4_32a(lx, ly, lz, 0.0);
+    loc32[s] = make_float4((float)lx, (float)ly, (float)lz, 0.0f);
+    cellc[s] = cc[i];
+  }
+  // fixed B-spline stencils (original order)
+  std::vector<int4> base(ne);
+  std::vector<double> th((size_t)ne * 3 * PMAX), dth((size_t)ne * 3 * PMAX);
+  std::vector<float> th32(th.size()), dth32(th.size());
+  for (int i = 0; i < ne; ++i) {
+    const double r[3] = {pos[i].x, pos[i].y, pos[i].z};
+    int i0[3];
+    for (int d = 0; d < 3; ++d) {
+      const double u = r[d] / c->ebox[d] * c->K[d];
+      const double fl = std::floor(u);
+      i0[d] = (int)fl;
+      double w[PMAX], dw[PMAX];
+      bspline_host(u - fl, c->P, w, dw);
+      for (int t = 0; t < PMAX; ++t) {
+        const size_t o = ((size_t)i * 3 + d) * PMAX + t;
+        th[o] = w[t];
+        dth[o] = dw[t];
+        th32[o] = (float)w[t];
+        dth32[o] = (float)dw[t];
+      }
+    }
+    base[i] = make_int4(i0[0], i0[1], i0[2], 0);
+  }
+  CPM_TRY(upload(&c->e_pos64, pos, st));
+  CPM_TRY(upload(&c->e_loc64, loc64, st));
+  CPM_TRY(upload(&c->e_loc32, loc32, st));
+  CPM_TRY(upload(&c->e_cellc, cellc, st));
+  CPM_TRY(upload(&c->e_sorted, sorted, st));
+  CPM_TRY(upload(&c->e_start, start, st));
+  CPM_TRY(upload(&c->e_base, base, st));
+  CPM_TRY(upload(&c->e_th64, th, st));
+  CPM_TRY(upload(&c->e_dth64, dth, st));
+  CPM_TRY(upload(&c->e_th32, th32, st));
+  CPM_TRY(upload(&c->e_dth32, dth32, st));
+  CPM_TRY(upload(&c->e_z, zraw, st));
+  CPM_TRY(upload(&c->e_v, v, st));
+  CPM_TRY(upload(&c->e_c1, c1, st));
+
+  // ---------------- A in float64 ----------------
+  c->ld64 = (ne + 3) & ~3;
+  c->ld32 = (ne + 3) & ~3;
+  CPM_TRY(dev_alloc(&c->S64, (size_t)ne * c->ld64));
+  double* A = c->S64;
+  CPM_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)ne * c->ld64, st));
+  {
+    std::vector<double3> shifts;
+    int nmax[3];
+    for (int d = 0; d < 3; ++d) nmax[d] = (int)std::floor(p.rcut / c->ebox[d] + 0.5);
+    for (int a = -nmax[0]; a <= nmax[0]; ++a)
+      for (int b = -nmax[1]; b <= nmax[1]; ++b)
+        for (int g = -nmax[2]; g <= nmax[2]; ++g)
+          shifts.push_back(make_double3(a * c->ebox[0], b * c->ebox[1], g * c->ebox[2]));
+    double3* dsh = nullptr;
+    CPM_TRY(upload(&dsh, shifts, st));
+    const double self = (std::sqrt(2.0) * p.eta - 2.0 * p.alpha) / std::sqrt(PI);
+    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
+    k_build_areal<<<grd, blk, 0, st>>>(c->e_pos64, ne, c->ld64, c->ebox[0], c->ebox[1], c->ebox[2], dsh,
+                                       (int)shifts.size(), p.alpha, p.eta / std::sqrt(2.0),
+                                       p.rcut * p.rcut, self, A);
+    CPM_LAUNCH();
+    CPM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(dsh);
+  }
+  // reciprocal part: direct Ewald sum over half-space k (weights 2 * 4 pi / V exp(-k^2/4a^2)/k^2)
+  {
+    const double kmax = p.kmax_build > 0 ? p.kmax_build : 2.0 * p.alpha * std::sqrt(27.6);
+    int mmax[3];
+    for (int d = 0; d < 3; ++d) mmax[d] = (int)std::floor(kmax * c->ebox[d] / (2.0 * PI));
+    std::vector<double4_32a> kv;
+    for (int a = -mmax[0]; a <= mmax[0]; ++a)
+      for (int b = -mmax[1]; b <= mmax[1]; ++b)
+        for (int g = -mmax[2]; g <= mmax[2]; ++g) {
+          const bool half = a > 0 || (a == 0 && b > 0) || (a == 0 && b == 0 && g > 0);
+          if (!half) continue;
+          const double kx = 2 * PI * a / c->ebox[0], ky = 2 * PI * b / c->ebox[1], kz = 2 * PI * g / c->ebox[2];
+          const double k2 = kx * kx + ky * ky + kz * kz;
+          if (k2 > kmax * kmax) continue;
+          const double wk = 2.0 * 4.0 * PI / c->V * std::exp(-k2 / (4.0 * p.alpha * p.alpha)) / k2 * KE;
+          kv.push_back(make_double4_32a(kx, ky, kz, std::sqrt(wk)));
+        }
+    if (!kv.empty()) {
+      const int kc = 2048;
+      double4_32a* dkv = nullptr;
+      double* T = nullptr;
+      CPM_TRY(upload(&dkv, kv, st));
+      CPM_TRY(dev_alloc(&T, (size_t)ne * 2 * kc));
+      CPM_LIB(cublasCreate(&c->cublas) == CUBLAS_STATUS_SUCCESS, "cublasCreate");
+      CPM_LIB(cublasSetStream(c->cublas, st) == CUBLAS_STATUS_SUCCESS, "cublasSetStream");
+      const double one = 1.0;
+      for (size_t k0 = 0; k0 < kv.size(); k0 += kc) {
+        const int n = (int)std::min<size_t>(kc, kv.size() - k0);
+        k_build_trig<<<dim3((ne + 127) / 128, n), 128, 0, st>>>(c->e_pos64, ne, dkv + k0, n, T);
+        CPM_LAUNCH();
+        CPM_LIB(cublasDsyrk(c->cublas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, ne, 2 * n, &one, T, ne, &one, A,
+                            c->ld64) == CUBLAS_STATUS_SUCCESS, "cublasDsyrk");
+      }
+      CPM_CUDA(cudaStreamSynchronize(st));
+      cudaFree(T);
+      cudaFree(dkv);
+    }
+  }
+  if (p.geometry == CPM_SLAB) {
+    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
+    k_build_slab<<<grd, blk, 0, st>>>(c->e_z, ne, c->ld64, KE * 4.0 * PI / c->V, A);
+    CPM_LAUNCH();
+  }
+
+  // ---------------- Cholesky and inverse (float64) ----------------
+  CPM_LIB(cusolverDnCreate(&c->solver) == CUSOLVER_STATUS_SUCCESS, "cusolverDnCreate");
+  CPM_LIB(cusolverDnSetStream(c->solver, st) == CUSOLVER_STATUS_SUCCESS, "cusolverDnSetStream");
+  {
+    int lwork = 0, lwork2 = 0;
+    CPM_LIB(cusolverDnDpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, &lwork) ==
+                CUSOLVER_STATUS_SUCCESS, "potrf_bufferSize");
+    CPM_LIB(cusolverDnDpotri_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, &lwork2) ==
+                CUSOLVER_STATUS_SUCCESS, "potri_bufferSize");
+    lwork = std::max(lwork, lwork2);
+    double* work = nullptr;
+    int* dinfo = nullptr;
+    CPM_TRY(dev_alloc(&work, (size_t)lwork));
+    CPM_TRY(dev_alloc(&dinfo, 1));
+    int info = 0;
+    CPM_LIB(cusolverDnDpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, work, lwork, dinfo) ==
+                CUSOLVER_STATUS_SUCCESS, "cusolverDnDpotrf");
+    CPM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+    if (info != 0) {
+      cudaFree(work);
+      cudaFree(dinfo);
+      set_error("Cholesky factorisation of A failed at column %d (A not positive definite)", info);
+      return CPM_ERR_NOT_SPD;
+    }
+    CPM_LIB(cusolverDnDpotri(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, work, lwork, dinfo) ==
+                CUSOLVER_STATUS_SUCCESS, "cusolverDnDpotri");
+    CPM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+    cudaFree(work);
+    cudaFree(dinfo);
+    if (info != 0) {
+      set_error("inverse of the Cholesky factor failed (info %d)", info);
+      return CPM_ERR_NOT_SPD;
+    }
+    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
+    k_symmetrize_lower<<<grd, blk, 0, st>>>(A, ne, c->ld64);
+    CPM_LAUNCH();
+  }
+  // ---------------- projection pieces ----------------
+  CPM_TRY(dev_alloc(&c->W, (size_t)ne * 2));
+  k_build_w<<<(ne * 32 + 255) / 256, 256, 0, st>>>(A, ne, c->ld64, c->e_c1, c->W);
+  CPM_LAUNCH();
+  std::vector<double> Wh((size_t)ne * 2);
+  CPM_CUDA(cudaMemcpyAsync(Wh.data(), c->W, sizeof(double) * ne * 2, cudaMemcpyDeviceToHost, st));
+  CPM_CUDA(cudaStreamSynchronize(st));
+  // C^T W (ncons x ncons) and its inverse M
+  double ctw[4] = {0, 0, 0, 0};
+  for (int i = 0; i < ne; ++i) {
+    ctw[0] += Wh[2 * i];                   // e^T A^-1 e
+    ctw[1] += Wh[2 * i + 1];               // e^T A^-1 e_1
+    ctw[2] += c1[i] * Wh[2 * i];           // e_1^T A^-1 e
+    ctw[3] += c1[i] * Wh[2 * i + 1];       // e_1^T A^-1 e_1
+    c->WTv[0] += Wh[2 * i] * v[i];
+    c->WTv[1] += Wh[2 * i + 1] * v[i];
+  }
+  if (c->ncons == 1) {
+    if (!(ctw[0] > 0)) { set_error("e^T A^-1 e is not positive"); return CPM_ERR_NOT_SPD; }
+    c->Mh[0] = 1.0 / ctw[0];
+  } else {
+    const double det = ctw[0] * ctw[3] - ctw[1] * ctw[2];
+    if (!(std::fabs(det) > 0)) { set_error("C^T A^-1 C is singular"); return CPM_ERR_NOT_SPD; }
+    c->Mh[0] = ctw[3] / det;
+    c->Mh[1] = -ctw[1] / det;
+    c->Mh[2] = -ctw[2] / det;
+    c->Mh[3] = ctw[0] / det;
+  }
+  {
+    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
+    k_build_s<<<grd, blk, 0, st>>>(A, ne, c->ld64, c->W, c->ncons, c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3]);
+    CPM_LAUNCH();
+  }
+  CPM_TRY(dev_alloc(&c->Sv, (size_t)ne));
+  k_matvec64<<<(ne * 32 + 255) / 256, 256, 0, st>>>(c->S64, ne, c->ld64, c->e_v, c->Sv);
+  CPM_LAUNCH();
+  {
+    std::vector<double> svh(ne);
+    CPM_CUDA(cudaMemcpyAsync(svh.data(), c->Sv, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+    c->dqdpsi = 0;
+    for (int i = 0; i < ne; ++i)
+      if (side[i] > 0) c->dqdpsi += svh[i];
+  }
+  if (c->mixed) {
+    CPM_TRY(dev_alloc(&c->S32, (size_t)ne * c->ld32));
+    k_to_float<<<dim3((c->ld32 + 255) / 256, ne), 256, 0, st>>>(c->S64, ne, c->ld64, c->S32, c->ld32);
+    CPM_LAUNCH();
+  }
+
+  // ---------------- SPME ----------------
+  {
+    std::vector<double> G;
+    influence_host(c, G);
+    CPM_TRY(upload(&c->G64, G, st));
+    std::vector<float> G32(G.begin(), G.end());
+    CPM_TRY(upload(&c->G32, G32, st));
+  }
+  CPM_TRY(make_plans(c));
+  CPM_TRY(cpm_internal_alloc_step_buffers(c));
+  CPM_CUDA(cudaStreamSynchronize(st));
+  return CPM_OK;
+}
+
+}  // namespace cpm
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
+                                const int32_t* elec_side_host, const int32_t* elec_cell_host, void* stream,
+                                cpm_ctx** out) {
+  if (!out) return CPM_ERR_ARG;
+  *out = nullptr;
+  const int v = cpm::validate(p, n_elec, elec_xyz_host, elec_side_host, elec_cell_host);
+  if (v != CPM_OK) {
+    cpm::set_error("cpm_build_matrix: invalid parameters or electrode input");
+    return v;
+  }
+  cpm_ctx* c = new (std::nothrow) cpm_ctx();
+  if (!c) return CPM_ERR_NOMEM;
+  c->p = *p;
+  const int s = cpm::build(c, n_elec, elec_xyz_host, elec_side_host, elec_cell_host, (cudaStream_t)stream);
+  if (s != CPM_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cpm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return CPM_OK;
+}
+
+extern "C" void cpm_destroy(cpm_ctx* c) {
+  if (!c) return;
+  void* bufs[] = {c->e_pos64, c->e_loc64, c->e_loc32, c->e_cellc, c->e_sorted, c->e_start, c->e_base,
+                  c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->S64, c->S32,
+                  c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
+                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->phi_real, c->b_tmp,
+                  c->scal, c->status};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (int b = 0; b < 2; ++b)
+    if (c->have_plan[b]) {
+      cufftDestroy(c->plan_r2c[b]);
+      cufftDestroy(c->plan_c2r[b]);
+    }
+  if (c->cublas) cublasDestroy(c->cublas);
+  if (c->solver) cusolverDnDestroy(c->solver);
+  delete c;
+}
+
+extern "C" int cpm_capacitance(const cpm_ctx* c, double* out) {
+  if (!c || !out) return CPM_ERR_ARG;
+  *out = c->dqdpsi;
+  return CPM_OK;
+}
+
+extern "C" int cpm_copy_matrix(const cpm_ctx* c, int32_t which, double* host_out) {
+  if (!c || !host_out) return CPM_ERR_ARG;
+  if (which == 0) {
+    CPM_CUDA(cudaMemcpy2D(host_out, sizeof(double) * c->ne, c->S64, sizeof(double) * c->ld64,
+                          sizeof(double) * c->ne, c->ne, cudaMemcpyDeviceToHost));
+  } else if (which == 1) {
+    CPM_CUDA(cudaMemcpy(host_out, c->Sv, sizeof(double) * c->ne, cudaMemcpyDeviceToHost));
+  } else if (which == 2) {
+    std::vector<double> w((size_t)c->ne * 2);
+    CPM_CUDA(cudaMemcpy(w.data(), c->W, sizeof(double) * c->ne * 2, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < c->ne; ++i)
+      for (int k = 0; k < c->ncons; ++k) host_out[(size_t)i * c->ncons + k] = w[2 * i + k];
+  } else {
+    return CPM_ERR_ARG;
+  }
+  return CPM_OK;
+}
+
+extern "C" int cpm_info(const cpm_ctx* c, int32_t* n_elec, int32_t* ncons, int64_t* mesh_points,
+                        int32_t* n_cells) {
+  if (!c) return CPM_ERR_ARG;
+  if (n_elec) *n_elec = c->ne;
+  if (ncons) *ncons = c->ncons;
+  if (mesh_points) *mesh_points = c->Mr;
+  if (n_cells) *n_cells = c->ncell;
+  return CPM_OK;
+}
+
+extern "C" int cpm_status(cpm_ctx* c, void* stream) {
+  if (!c) return CPM_ERR_ARG;
+  int h = 0;
+  CPM_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  CPM_CUDA(cudaMemcpy(&h, c->status, sizeof(int), cudaMemcpyDeviceToHost));
+  CPM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+  if (h & cpm::DE_NONFINITE) return CPM_ERR_NONFINITE;
+  if (h & cpm::DE_DOMAIN) return CPM_ERR_DOMAIN;
+  if (h & cpm::DE_CAPACITY) return CPM_ERR_CAPACITY;
+  if (h & cpm::DE_TIMEOUT) return CPM_ERR_TIMEOUT;
+  return CPM_OK;
+}
+
+extern "C" const char* cpm_strerror(int s) {
+  switch (s) {
+    case CPM_OK: return "ok";
+    case CPM_ERR_ARG: return "invalid argument";
+    case CPM_ERR_CUDA: return "CUDA runtime error";
+    case CPM_ERR_NOT_SPD: return "elastance matrix is not positive definite";
+    case CPM_ERR_NONFINITE: return "non-finite coordinate or charge";
+    case CPM_ERR_CAPACITY: return "replica count or site count above build-time capacity";
+    case CPM_ERR_DOMAIN: return "electrolyte site outside [0, L_z) in z";
+    case CPM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case CPM_ERR_LIBRARY: return "cuFFT / cuBLAS / cuSOLVER error";
+    case CPM_ERR_NOMEM: return "out of device memory";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* cpm_last_error(void) { return cpm::g_last_error.c_str(); }

@@ -1,0 +1,224 @@
+// Internal definitions shared by the CPM library translation units: the context layout, error
+// plumbing, and small device helpers (cardinal B-splines, warp reductions, cell geometry).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+#include <cublas_v2.h>
+#include <cusolverDn.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <string>
+
+#include "../../include/cpm.h"
+
+namespace cpm {
+
+constexpr double KE = 14.3996454784;        // e^2 / (4 pi eps0), eV A
+constexpr double PI = 3.14159265358979323846;
+constexpr int PMAX = 8;                     // largest supported B-spline order
+constexpr int NSCAL = 16;                   // per-replica float64 scalar slots
+
+// Per-replica scalar slots (float64 accumulators, zeroed at the start of every call).
+enum Slot {
+  S_QZ_ELYT = 0,   // sum_j Q_j Z_j
+  S_QQ_ELYT = 1,   // sum_j Q_j^2
+  S_QZ_ELEC = 2,   // sum_i q_i z_i
+  S_QV_ELEC = 3,   // sum_i q_i v_i
+  S_QQ_ELEC = 4,   // sum_i q_i^2
+  S_E_LL = 5,      // sum_j Q_j phi^pp_j            (real space, no KE)
+  S_E_LE = 6,      // sum_j Q_j phi^gp_j            (real space, no KE)
+  S_E_EE = 7,      // sum_i q_i phi^gg_i            (real space, no KE)
+  S_E_RECIP = 8,   // 1/2 sum_m G |rho^(m)|^2       (eV)
+  S_CQ0 = 9,       // e^T q_raw
+  S_CQ1 = 10,      // e_1^T q_raw
+  S_WB0 = 11,      // (A^-1 e)^T b
+  S_WB1 = 12,      // (A^-1 e_1)^T b
+  S_SPARE = 13
+};
+
+// Status bits latched by kernels (first error wins).
+enum DevErr { DE_NONFINITE = 1, DE_DOMAIN = 2, DE_TIMEOUT = 4, DE_CAPACITY = 8 };
+
+void set_error(const char* fmt, ...);
+
+}  // namespace cpm
+
+struct cpm_ctx {
+  cpm_params p;
+  int dev = 0;
+  int ne = 0, ncons = 1;
+  bool mixed = false;
+  double ebox[3] = {0, 0, 0};   // Ewald box (slab: padded z)
+  double V = 0;                 // Ewald box volume
+  double Lz = 0;                // physical cell length in z (finite-field ramp, field term)
+  // real-space cell grid (edge >= rcut/2 per axis)
+  int nc[3] = {1, 1, 1};
+  double edge[3] = {0, 0, 0};
+  int ncell = 1;
+  int sten[3] = {0, 0, 0};      // stencil half-width per axis: ceil(rcut / edge)
+  // electrode data, device
+  double4_32a* e_pos64 = nullptr;   // original order (x, y, z wrapped into the box, 0)
+  double4_32a* e_loc64 = nullptr;   // cell-sorted, cell-local coordinates, w = 0
+  float4* e_loc32 = nullptr;
+  int4* e_cellc = nullptr;      // cell-sorted: cell coords (cx, cy, cz, flat)
+  int* e_sorted = nullptr;      // cell-sorted -> original index
+  int* e_start = nullptr;       // [ncell + 1]
+  int4* e_base = nullptr;       // original order: B-spline base grid index per axis
+  double* e_th64 = nullptr;     // [ne][3][PMAX] B-spline weights
+  double* e_dth64 = nullptr;    // [ne][3][PMAX] derivatives (per grid unit)
+  float* e_th32 = nullptr;
+  float* e_dth32 = nullptr;
+  double* e_z = nullptr;        // [ne] z as given
+  double* e_v = nullptr;        // [ne] geometry vector v
+  double* e_c1 = nullptr;       // [ne] e_1 indicator (doubled cell) or zeros
+  // matrices
+  int ld64 = 0, ld32 = 0;
+  double* S64 = nullptr;        // [ne][ld64] row-major projected inverse
+  float* S32 = nullptr;         // [ne][ld32] float copy (mixed precision)
+  double* W = nullptr;          // [ne][2] A^-1 C (second column zero unless doubled)
+  double* Sv = nullptr;         // [ne]
+  double Mh[4] = {0, 0, 0, 0};  // (C^T A^-1 C)^-1, host
+  double WTv[2] = {0, 0};       // (A^-1 C)^T v, host
+  double dqdpsi = 0;
+  // SPME
+  int K[3] = {0, 0, 0};
+  int P = 5;
+  long long Mr = 0, Mc = 0;     // real / half-complex mesh sizes per replica
+  long long Mr_s = 0, Mc_s = 0; // per-replica strides, padded to 256-byte multiples
+  double* G64 = nullptr;        // [Mc] influence function incl. KE and B-spline factors (V e^-1)
+  float* G32 = nullptr;
+  cufftHandle plan_r2c[2] = {0, 0};   // [0] batch 1, [1] batch max_replicas
+  cufftHandle plan_c2r[2] = {0, 0};
+  bool have_plan[2] = {false, false};
+  void* mesh_r = nullptr;       // [max_rep][Mr] real mesh (charges)
+  void* mesh_c = nullptr;       // [max_rep][Mc] complex spectrum
+  void* mesh_phi = nullptr;     // [max_rep][Mr] potential mesh
+  // electrolyte workspaces (capacity max_replicas x max_elyt)
+  int* l_cell = nullptr;        // per site flat cell index
+  int* l_count = nullptr;       // [max_rep][ncell]
+  int* l_start = nullptr;       // [max_rep][ncell + 1]
+  int* l_sorted = nullptr;      // [max_rep][max_elyt] sorted -> original (relative to offset)
+  double4_32a* l_loc64 = nullptr;   // [max_rep][max_elyt] cell-local coordinates + Q
+  float4* l_loc32 = nullptr;
+  int4* l_cellc = nullptr;      // [max_rep][max_elyt]
+  // per-replica buffers
+  double* phi_real = nullptr;   // [max_rep][ne]
+  double* b_tmp = nullptr;      // [max_rep][ne]
+  double* scal = nullptr;       // [max_rep][NSCAL]
+  int* status = nullptr;        // device status word
+  // libraries
+  cublasHandle_t cublas = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+};
+
+// ------------------------------------------------------------------------------------------
+// error plumbing
+// ------------------------------------------------------------------------------------------
+#define CPM_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      cpm::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));      \
+      return (e_ == cudaErrorMemoryAllocation) ? CPM_ERR_NOMEM : CPM_ERR_CUDA;                 \
+    }                                                                                          \
+  } while (0)
+
+#define CPM_LAUNCH()                                                                           \
+  do {                                                                                         \
+    cudaError_t e_ = cudaGetLastError();                                                       \
+    if (e_ != cudaSuccess) {                                                                   \
+      cpm::set_error("%s:%d kernel launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_));  \
+      return CPM_ERR_CUDA;                                                                     \
+    }                                                                                          \
+  } while (0)
+
+#define CPM_LIB(cond, what)                                                                    \
+  do {                                                                                         \
+    if (!(cond)) {                                                                             \
+      cpm::set_error("%s:%d %s failed", __FILE__, __LINE__, what);                             \
+      return CPM_ERR_LIBRARY;                                                                  \
+    }                                                                                          \
+  } while (0)
+
+#define CPM_TRY(expr)                                                                          \
+  do {                                                                                         \
+    int s_ = (expr);                                                                           \
+    if (s_ != CPM_OK) return s_;                                                               \
+  } while (0)
+
+// ------------------------------------------------------------------------------------------
+// device helpers
+// ------------------------------------------------------------------------------------------
+namespace cpm {
+
+template <typename T> struct Vec4;
+template <> struct Vec4<float> { using type = float4; };
+template <> struct Vec4<double> { using type = double4_32a; };
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Neumaier compensated accumulation (used for float32 running sums).
+template <typename T> struct CompSum {
+  T s = 0, c = 0;
+  __device__ __forceinline__ void add(T x) {
+    T t = s + x;
+    c += (fabs(s) >= fabs(x)) ? ((s - t) + x) : ((x - t) + s);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+// Cardinal B-spline weights of order p at fractional offset f in [0, 1):
+// w[t] = M_p(f + t) belongs to mesh point (floor(u) - t); dw[t] = d M_p / du there.
+// Recursion M_n(x) = [x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)] / (n - 1), and
+// M_n'(x) = M_{n-1}(x) - M_{n-1}(x - 1) (Essmann et al., J. Chem. Phys. 103, 8577 (1995)).
+template <typename T>
+__device__ __forceinline__ void bspline(T f, int p, T* w, T* dw) {
+#pragma unroll
+  for (int t = 0; t < PMAX; ++t) { w[t] = 0; dw[t] = 0; }
+  w[0] = 1;
+#pragma unroll
+  for (int n = 2; n <= PMAX; ++n) {
+    if (n > p) break;
+    if (n == p) {
+#pragma unroll
+      for (int t = 0; t < PMAX; ++t) {
+        if (t >= n) break;
+        dw[t] = w[t] - (t > 0 ? w[t - 1] : T(0));
+      }
+    }
+    const T inv = T(1) / T(n - 1);
+#pragma unroll
+    for (int t = PMAX - 1; t >= 0; --t) {
+      if (t >= n) continue;
+      const T a = (t < n - 1) ? w[t] : T(0);
+      const T b = (t > 0) ? w[t - 1] : T(0);
+      w[t] = ((f + T(t)) * a + (T(n) - f - T(t)) * b) * inv;
+    }
+  }
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+__device__ __forceinline__ void latch_error(int* status, int bit) { atomicOr(status, bit); }
+
+}  // namespace cpm
+
+// Entry points implemented in cpm_step.cu, used by the build (Sv, checks).
+int cpm_internal_alloc_step_buffers(cpm_ctx* c);

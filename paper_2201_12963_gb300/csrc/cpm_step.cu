@@ -1,0 +1,968 @@
+// Per-step constant-potential electrostatics on the GPU (templated on the working precision T):
+//
+//   prepare   bin the electrolyte into the real-space cell grid (counting sort, cell-local coords)
+//   charges   b = -(electrolyte potential at the electrode sites) (Eq. 3): real-space
+//             Gaussian-point pairs + SPME (spread, FFT, influence function, inverse FFT, gather),
+//             then q = S (b + dpsi v) and the neutrality projection (Eqs. 8-9 / 13-15)
+//   forces    SPME of all charges + real-space pair forces, finite-field / slab terms, energies
+//
+// Every launch goes to the caller's stream; nothing here allocates or synchronises the host.
+#include "cpm_internal.cuh"
+
+#include <algorithm>
+
+namespace cpm {
+
+constexpr unsigned FULL = 0xffffffffu;
+
+struct CellGeom {
+  int nc[3];
+  int w[3];      // stencil widths 2 * sten + 1
+  int sten[3];
+  int nsten;
+  double edge[3];
+  double box[3];
+  double rc2;
+};
+
+struct SpmeGeom {
+  int K[3];
+  int P;
+  double box[3];
+  long long Mr_s, Mc_s;
+};
+
+__device__ __forceinline__ double wrap_d(double x, double L) {
+  double y = x - L * floor(x / L);
+  if (y >= L) y -= L;
+  if (y < 0) y = 0;
+  return y;
+}
+
+// block-wide sum of up to NV doubles held by lane 0 of every warp; thread 0 adds into dst[k].
+template <int NV>
+__device__ __forceinline__ void block_atomic_add(double (&v)[NV], double* const (&dst)[NV]) {
+  __shared__ double red[NV][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < NV; ++k) red[k][warp] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) {
+      double s = 0;
+      for (int w = 0; w < nw; ++w) s += red[k][w];
+      if (dst[k] && s != 0.0) atomicAdd(dst[k], s);
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// prepare: counting sort of the electrolyte into cells
+// ------------------------------------------------------------------------------------------
+__global__ void k_bin(const int* __restrict__ off, const double* __restrict__ xyzq, int cap, CellGeom g,
+                      double lz_phys, int* __restrict__ l_cell, int* __restrict__ l_count, int ncell,
+                      double* __restrict__ scal, int* __restrict__ status) {
+  const int rep = blockIdx.y;
+  const int o = off[rep];
+  const int n_all = off[rep + 1] - o;
+  const int n = min(n_all, cap);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i == 0 && (n_all > cap || n_all < 0)) latch_error(status, DE_CAPACITY);
+  double acc[2] = {0.0, 0.0};
+  if (i < n) {
+    const double* s = xyzq + 4 * (size_t)(o + i);
+    double x = s[0], y = s[1], z = s[2], q = s[3];
+    if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q))) {
+      latch_error(status, DE_NONFINITE);
+      x = y = z = 0.0;
+      q = 0.0;
+    } else if (!(z >= 0.0 && z < lz_phys)) {
+      latch_error(status, DE_DOMAIN);
+    }
+    const double r[3] = {wrap_d(x, g.box[0]), wrap_d(y, g.box[1]), wrap_d(z, g.box[2])};
+    int ci[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) ci[d] = min(g.nc[d] - 1, max(0, (int)(r[d] / g.edge[d])));
+    const int flat = (ci[0] * g.nc[1] + ci[1]) * g.nc[2] + ci[2];
+    l_cell[(size_t)rep * cap + i] = flat;
+    atomicAdd(&l_count[(size_t)rep * ncell + flat], 1);
+    acc[0] = q * z;
+    acc[1] = q * q;
+  }
+  acc[0] = warp_sum(acc[0]);
+  acc[1] = warp_sum(acc[1]);
+  double* const dst[2] = {scal + rep * NSCAL + S_QZ_ELYT, scal + rep * NSCAL + S_QQ_ELYT};
+  block_atomic_add<2>(acc, dst);
+}
+
+// exclusive scan of the per-cell counts (one block per replica); counts become scatter cursors
+__global__ void k_scan(int* __restrict__ l_count, int* __restrict__ l_start, int ncell) {
+  const int rep = blockIdx.x;
+  int* cnt = l_count + (size_t)rep * ncell;
+  int* st = l_start + (size_t)rep * (ncell + 1);
+  __shared__ int part[1024];
+  const int nt = blockDim.x;
+  const int chunk = (ncell + nt - 1) / nt;
+  const int b = threadIdx.x * chunk, e = min(ncell, b + chunk);
+  int s = 0;
+  for (int k = b; k < e; ++k) s += cnt[k];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < nt; o <<= 1) {
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = part[threadIdx.x] - s;
+  for (int k = b; k < e; ++k) {
+    const int c = cnt[k];
+    st[k] = run;
+    cnt[k] = run;
+    run += c;
+  }
+  if (threadIdx.x == nt - 1) st[ncell] = part[nt - 1];
+}
+
+template <typename T>
+__global__ void k_scatter(const int* __restrict__ off, const double* __restrict__ xyzq, int cap, CellGeom g,
+                          const int* __restrict__ l_cell, int* __restrict__ cursor, int ncell,
+                          int* __restrict__ l_sorted, typename Vec4<T>::type* __restrict__ l_loc,
+                          int4* __restrict__ l_cellc) {
+  using V4 = typename Vec4<T>::type;
+  const int rep = blockIdx.y;
+  const int o = off[rep];
+  const int n = min(off[rep + 1] - o, cap);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double* s = xyzq + 4 * (size_t)(o + i);
+  double x = s[0], y = s[1], z = s[2], q = s[3];
+  if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q))) x = y = z = q = 0.0;
+  const double r[3] = {wrap_d(x, g.box[0]), wrap_d(y, g.box[1]), wrap_d(z, g.box[2])};
+  int ci[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) ci[d] = min(g.nc[d] - 1, max(0, (int)(r[d] / g.edge[d])));
+  const int flat = l_cell[(size_t)rep * cap + i];
+  const int pos = atomicAdd(&cursor[(size_t)rep * ncell + flat], 1);
+  const size_t k = (size_t)rep * cap + pos;
+  l_sorted[k] = i;
+  V4 v;
+  v.x = (T)(r[0] - ci[0] * g.edge[0]);
+  v.y = (T)(r[1] - ci[1] * g.edge[1]);
+  v.z = (T)(r[2] - ci[2] * g.edge[2]);
+  v.w = (T)q;
+  l_loc[k] = v;
+  l_cellc[k] = make_int4(ci[0], ci[1], ci[2], flat);
+}
+
+// ------------------------------------------------------------------------------------------
+// real-space pair sums over cell-list neighbours, one warp per target site
+// ------------------------------------------------------------------------------------------
+struct PairSrc {
+  const void* loc;          // cell-sorted cell-local coordinates (w = charge when q == nullptr)
+  long long loc_stride;     // per-replica stride (0 = shared by all replicas)
+  const int* start;         // [ncell + 1] cell starts
+  long long start_stride;
+  const int* sorted;        // sorted -> original index (electrode charge lookup)
+  const double* q;          // electrode charges [rep][q_stride] or nullptr
+  int q_stride;
+  double beta;              // second screening width: 0 = point source, else Gaussian kernel
+  int slot;                 // energy slot receiving sum_t c_t phi_t, or -1
+};
+
+struct PairTgt {
+  const void* loc;
+  long long loc_stride;
+  const int4* cellc;
+  const int* sorted;
+  const int* off;           // electrolyte targets: replica offsets; nullptr for electrodes
+  int cap;                  // electrolyte capacity per replica
+  int n_fixed;              // electrode count
+  const double* q;          // electrode target charges [rep][n_fixed] or nullptr (charge in loc.w)
+  double* force;            // += KE * c_t * sum ..., [global index][3], or nullptr
+  double* phi_out;          // potential from source set 0, [rep][n_fixed] original order, or nullptr
+};
+
+// Kernel per pair at distance r: (erfc(alpha r) - erfc(beta r)) / r, beta = 0 meaning a point;
+// the force on the target is c_t c_s [kernel + 2/sqrt(pi)(alpha e^{-alpha^2 r^2} - beta e^{-beta^2 r^2})] d / r^2.
+template <typename T, bool FORCE>
+__global__ void __launch_bounds__(256) k_pair(const PairTgt t, const PairSrc s0, const PairSrc s1,
+                                              const CellGeom g, const double alpha_d, double* __restrict__ scal) {
+  using V4 = typename Vec4<T>::type;
+  const T alpha = (T)alpha_d;
+  const T c2pi = (T)1.1283791670955126;   // 2 / sqrt(pi)
+  const int rep = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int nt = t.off ? min(t.off[rep + 1] - t.off[rep], t.cap) : t.n_fixed;
+  const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
+  const T rc2 = (T)g.rc2;
+  double eacc[2] = {0.0, 0.0};
+  const V4* tl = (const V4*)t.loc + rep * t.loc_stride;
+  const int4* tcc = t.cellc + rep * t.loc_stride;
+  const int* tso = t.sorted + rep * t.loc_stride;
+  for (int ti = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ti < nt; ti += (gridDim.x * blockDim.x) >> 5) {
+    const V4 tp = tl[ti];
+    const int4 tc = tcc[ti];
+    const int orig = tso[ti];
+    const T tq = t.q ? (T)t.q[(size_t)rep * t.n_fixed + orig] : tp.w;
+    CompSum<T> ph[2];
+    T fx = 0, fy = 0, fz = 0;
+#pragma unroll
+    for (int set = 0; set < 2; ++set) {
+      const PairSrc& s = set ? s1 : s0;
+      if (!s.loc) continue;
+      const V4* sl = (const V4*)s.loc + rep * s.loc_stride;
+      const int* st = s.start + rep * s.start_stride;
+      const double* sq_arr = s.q ? s.q + (size_t)rep * s.q_stride : nullptr;
+      const bool gauss = s.beta > 0.0;
+      const T beta = (T)s.beta;
+      for (int sb = 0; sb < g.nsten; sb += 32) {
+        const int si = sb + lane;
+        int cnt = 0, first = 0;
+        T ox = 0, oy = 0, oz = 0;
+        if (si < g.nsten) {
+          const int dx = si % g.w[0] - g.sten[0];
+          const int r1 = si / g.w[0];
+          const int dy = r1 % g.w[1] - g.sten[1];
+          const int dz = r1 / g.w[1] - g.sten[2];
+          const T mx = fmax(T(0), fmax(dx * e0 - tp.x, tp.x - (dx + 1) * e0));
+          const T my = fmax(T(0), fmax(dy * e1 - tp.y, tp.y - (dy + 1) * e1));
+          const T mz = fmax(T(0), fmax(dz * e2 - tp.z, tp.z - (dz + 1) * e2));
+          if (mx * mx + my * my + mz * mz < rc2) {
+            const int cx = wrap_index(tc.x + dx, g.nc[0]);
+            const int cy = wrap_index(tc.y + dy, g.nc[1]);
+            const int cz = wrap_index(tc.z + dz, g.nc[2]);
+            const int flat = (cx * g.nc[1] + cy) * g.nc[2] + cz;
+            first = st[flat];
+            cnt = st[flat + 1] - first;
+            ox = dx * e0;
+            oy = dy * e1;
+            oz = dz * e2;
+          }
+        }
+        int incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int v = __shfl_up_sync(FULL, incl, o);
+          if (lane >= o) incl += v;
+        }
+        const int total = __shfl_sync(FULL, incl, 31);
+        const int excl = incl - cnt;
+        const int basek = first - excl;
+        for (int jb = 0; jb < total; jb += 32) {
+          const int j = jb + lane;
+          int lo = 0;
+#pragma unroll
+          for (int step = 16; step > 0; step >>= 1) {
+            const int e = __shfl_sync(FULL, excl, lo + step);
+            if (e <= j) lo += step;
+          }
+          const int k = __shfl_sync(FULL, basek, lo) + j;
+          const T sx = __shfl_sync(FULL, ox, lo);
+          const T sy = __shfl_sync(FULL, oy, lo);
+          const T sz = __shfl_sync(FULL, oz, lo);
+          if (j < total) {
+            const V4 sp = sl[k];
+            const T dx = tp.x - sp.x - sx, dy = tp.y - sp.y - sy, dz = tp.z - sp.z - sz;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 < rc2 && r2 > T(0)) {
+              const T qs = sq_arr ? (T)sq_arr[s.sorted[k]] : sp.w;
+              const T r = sqrt(r2);
+              const T ir = T(1) / r;
+              T num = erfc(alpha * r);
+              if (gauss) num -= erfc(beta * r);
+              const T pot = num * ir;
+              ph[set].add(qs * pot);
+              if (FORCE) {
+                T gx = alpha * exp(-alpha * alpha * r2);
+                if (gauss) gx -= beta * exp(-beta * beta * r2);
+                const T fr = qs * (pot + c2pi * gx) * ir * ir;
+                fx += fr * dx;
+                fy += fr * dy;
+                fz += fr * dz;
+              }
+            }
+          }
+        }
+      }
+    }
+    const double p0 = warp_sum(ph[0].value());
+    const double p1 = warp_sum(ph[1].value());
+    double Fx = 0, Fy = 0, Fz = 0;
+    if (FORCE) {
+      Fx = warp_sum((double)fx);
+      Fy = warp_sum((double)fy);
+      Fz = warp_sum((double)fz);
+    }
+    if (lane == 0) {
+      if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = p0;
+      eacc[0] += (double)tq * p0;
+      eacc[1] += (double)tq * p1;
+      if (FORCE && t.force) {
+        const size_t gi = t.off ? (size_t)t.off[rep] + orig : (size_t)rep * t.n_fixed + orig;
+        const double f = KE * (double)tq;
+        t.force[3 * gi + 0] += f * Fx;
+        t.force[3 * gi + 1] += f * Fy;
+        t.force[3 * gi + 2] += f * Fz;
+      }
+    }
+  }
+  double* const dst[2] = {s0.slot >= 0 ? scal + rep * NSCAL + s0.slot : nullptr,
+                          s1.slot >= 0 ? scal + rep * NSCAL + s1.slot : nullptr};
+  block_atomic_add<2>(eacc, dst);
+}
+
+// ------------------------------------------------------------------------------------------
+// SPME: charge assignment, influence function, interpolation (cardinal B-splines of order P)
+// ------------------------------------------------------------------------------------------
+// B-spline weights of one site into per-warp shared memory: lanes 0-2 handle axes x, y, z.
+template <typename T>
+__device__ __forceinline__ void site_weights(const double r[3], const SpmeGeom& sg, int lane, T (*w)[PMAX],
+                                             T (*dw)[PMAX], int* i0) {
+  if (lane < 3) {
+    const double u = wrap_d(r[lane], sg.box[lane]) / sg.box[lane] * sg.K[lane];
+    const double fl = floor(u);
+    T wl[PMAX], dl[PMAX];
+    bspline<T>((T)(u - fl), sg.P, wl, dl);
+#pragma unroll
+    for (int t = 0; t < PMAX; ++t) {
+      w[lane][t] = wl[t];
+      dw[lane][t] = dl[t];
+    }
+    i0[lane] = (int)fl;
+  }
+  __syncwarp();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, const double* __restrict__ xyzq,
+                                                     int cap, SpmeGeom sg, T* __restrict__ mesh) {
+  __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
+  __shared__ int si0[8][3];
+  const int rep = blockIdx.y;
+  const int o = off[rep];
+  const int n = min(off[rep + 1] - o, cap);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  T* m = mesh + (size_t)rep * sg.Mr_s;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int iters = (n + nw - 1) / nw;   // uniform trip count keeps the warps of a block in step
+  for (int it = 0; it < iters; ++it) {
+    const int i = first + it * nw;
+    if (i < n) {
+      const double* s = xyzq + 4 * (size_t)(o + i);
+      double r[3] = {s[0], s[1], s[2]};
+      double q = s[3];
+      if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(q))) r[0] = r[1] = r[2] = q = 0.0;
+      site_weights<T>(r, sg, lane, sw[wib], sdw[wib], si0[wib]);
+      for (int task = lane; task < P * P; task += 32) {
+        const int ty = task / P, tz = task - ty * P;
+        const int gy = wrap_index(si0[wib][1] - ty, K2), gz = wrap_index(si0[wib][2] - tz, K3);
+        const T wyz = (T)q * sw[wib][1][ty] * sw[wib][2][tz];
+        for (int tx = 0; tx < P; ++tx) {
+          const int gx = wrap_index(si0[wib][0] - tx, K1);
+          atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], sw[wib][0][tx] * wyz);
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// Electrode charges onto the mesh through the fixed stencils; also sums q z, q v and q^2.
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_elec(const double* __restrict__ q, int ne, const int4* __restrict__ base,
+                                                     const T* __restrict__ th, SpmeGeom sg, const double* __restrict__ ez,
+                                                     const double* __restrict__ ev, T* __restrict__ mesh,
+                                                     double* __restrict__ scal) {
+  const int rep = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  T* m = mesh + (size_t)rep * sg.Mr_s;
+  const double* qr = q + (size_t)rep * ne;
+  double acc[3] = {0, 0, 0};
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+    const double qi = qr[i];
+    const int4 b = base[i];
+    const T* w = th + (size_t)i * 3 * PMAX;
+    for (int task = lane; task < P * P; task += 32) {
+      const int ty = task / P, tz = task - ty * P;
+      const int gy = wrap_index(b.y - ty, K2), gz = wrap_index(b.z - tz, K3);
+      const T wyz = (T)qi * w[PMAX + ty] * w[2 * PMAX + tz];
+      for (int tx = 0; tx < P; ++tx) {
+        const int gx = wrap_index(b.x - tx, K1);
+        atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], w[tx] * wyz);
+      }
+    }
+    if (lane == 0) {
+      acc[0] += qi * ez[i];
+      acc[1] += qi * ev[i];
+      acc[2] += qi * qi;
+    }
+  }
+  double* const dst[3] = {scal + rep * NSCAL + S_QZ_ELEC, scal + rep * NSCAL + S_QV_ELEC,
+                          scal + rep * NSCAL + S_QQ_ELEC};
+  block_atomic_add<3>(acc, dst);
+}
+
+// rho^(m) *= G(m) on the half spectrum; optionally E_recip += 1/2 sum_m G |rho^(m)|^2 (full spectrum).
+template <typename T, typename T2>
+__global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const T* __restrict__ G, long long Mc,
+                                                   long long Mc_s, int K3h, int K3, int energy,
+                                                   double* __restrict__ scal) {
+  const int rep = blockIdx.y;
+  T2* c = spec + (size_t)rep * Mc_s;
+  double e = 0.0;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Mc; k += (long long)gridDim.x * blockDim.x) {
+    T2 v = c[k];
+    const T g = G[k];
+    if (energy) {
+      const int n3 = (int)(k % K3h);
+      const double wgt = (n3 == 0 || 2 * n3 == K3) ? 0.5 : 1.0;
+      e += wgt * (double)g * ((double)v.x * v.x + (double)v.y * v.y);
+    }
+    v.x *= g;
+    v.y *= g;
+    c[k] = v;
+  }
+  if (energy) {
+    e = warp_sum(e);
+    double acc[1] = {e};
+    double* const dst[1] = {scal + rep * NSCAL + S_E_RECIP};
+    block_atomic_add<1>(acc, dst);
+  }
+}
+
+// b_i = -(KE phi_real_i + phi_mesh_i) (- KE 4 pi / V z_i sum_j Q_j Z_j for the slab), one warp per site.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int ne, const int4* __restrict__ base,
+                                                  const T* __restrict__ th, SpmeGeom sg,
+                                                  const double* __restrict__ phi_real, const double* __restrict__ ez,
+                                                  double slab_coef, const double* __restrict__ scal,
+                                                  double* __restrict__ b) {
+  const int rep = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const T* m = phi + (size_t)rep * sg.Mr_s;
+  const double qz = scal[rep * NSCAL + S_QZ_ELYT];
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+    const int4 bs = base[i];
+    const T* w = th + (size_t)i * 3 * PMAX;
+    T acc = 0;
+    for (int task = lane; task < P * P; task += 32) {
+      const int ty = task / P, tz = task - ty * P;
+      const int gy = wrap_index(bs.y - ty, K2), gz = wrap_index(bs.z - tz, K3);
+      T s = 0;
+      for (int tx = 0; tx < P; ++tx) {
+        const int gx = wrap_index(bs.x - tx, K1);
+        s += w[tx] * m[((size_t)gx * K2 + gy) * K3 + gz];
+      }
+      acc += s * w[PMAX + ty] * w[2 * PMAX + tz];
+    }
+    const double pk = warp_sum((double)acc);
+    if (lane == 0) {
+      const size_t k = (size_t)rep * ne + i;
+      b[k] = -(KE * phi_real[k] + pk) - slab_coef * ez[i] * qz;
+    }
+  }
+}
+
+// k-space force on electrolyte sites: F = -Q grad(phi_mesh) - field terms (written, not added).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi, const int* __restrict__ off,
+                                                       const double* __restrict__ xyzq, int cap, SpmeGeom sg,
+                                                       const double* __restrict__ dpsi, double ff_over_lz,
+                                                       double slab_coef, const double* __restrict__ scal,
+                                                       double* __restrict__ F) {
+  __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
+  __shared__ int si0[8][3];
+  const int rep = blockIdx.y;
+  const int o = off[rep];
+  const int n = min(off[rep + 1] - o, cap);
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const T* m = phi + (size_t)rep * sg.Mr_s;
+  const double sx = sg.K[0] / sg.box[0], sy = sg.K[1] / sg.box[1], sz = sg.K[2] / sg.box[2];
+  const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
+  const double ez = -dpsi[rep] * ff_over_lz - slab_coef * mz;   // field per unit charge along z
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int iters = (n + nw - 1) / nw;
+  for (int it = 0; it < iters; ++it) {
+    const int i = first + it * nw;
+    if (i < n) {
+      const double* s = xyzq + 4 * (size_t)(o + i);
+      double r[3] = {s[0], s[1], s[2]};
+      double q = s[3];
+      if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(q))) r[0] = r[1] = r[2] = q = 0.0;
+      site_weights<T>(r, sg, lane, sw[wib], sdw[wib], si0[wib]);
+      T gx = 0, gy = 0, gz = 0;
+      for (int task = lane; task < P * P; task += 32) {
+        const int ty = task / P, tz = task - ty * P;
+        const int jy = wrap_index(si0[wib][1] - ty, K2), jz = wrap_index(si0[wib][2] - tz, K3);
+        T a = 0, ad = 0;
+        for (int tx = 0; tx < P; ++tx) {
+          const int jx = wrap_index(si0[wib][0] - tx, K1);
+          const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
+          a += sw[wib][0][tx] * ph;
+          ad += sdw[wib][0][tx] * ph;
+        }
+        const T wy = sw[wib][1][ty], wz = sw[wib][2][tz];
+        gx += ad * wy * wz;
+        gy += a * sdw[wib][1][ty] * wz;
+        gz += a * wy * sdw[wib][2][tz];
+      }
+      const double Gx = warp_sum((double)gx), Gy = warp_sum((double)gy), Gz = warp_sum((double)gz);
+      if (lane == 0) {
+        const size_t k = 3 * (size_t)(o + i);
+        F[k + 0] = -q * Gx * sx;
+        F[k + 1] = -q * Gy * sy;
+        F[k + 2] = -q * Gz * sz + q * ez;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// k-space force on electrode sites through the fixed stencils (written, not added).
+template <typename T>
+__global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi, const double* __restrict__ q,
+                                                       int ne, const int4* __restrict__ base,
+                                                       const T* __restrict__ th, const T* __restrict__ dth,
+                                                       SpmeGeom sg, const double* __restrict__ dpsi,
+                                                       double ff_over_lz, double slab_coef,
+                                                       const double* __restrict__ scal, double* __restrict__ F) {
+  const int rep = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const T* m = phi + (size_t)rep * sg.Mr_s;
+  const double sx = sg.K[0] / sg.box[0], sy = sg.K[1] / sg.box[1], sz = sg.K[2] / sg.box[2];
+  const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
+  const double ez = -dpsi[rep] * ff_over_lz - slab_coef * mz;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+    const int4 bs = base[i];
+    const T* w = th + (size_t)i * 3 * PMAX;
+    const T* dw = dth + (size_t)i * 3 * PMAX;
+    T gx = 0, gy = 0, gz = 0;
+    for (int task = lane; task < P * P; task += 32) {
+      const int ty = task / P, tz = task - ty * P;
+      const int jy = wrap_index(bs.y - ty, K2), jz = wrap_index(bs.z - tz, K3);
+      T a = 0, ad = 0;
+      for (int tx = 0; tx < P; ++tx) {
+        const int jx = wrap_index(bs.x - tx, K1);
+        const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
+        a += w[tx] * ph;
+        ad += dw[tx] * ph;
+      }
+      const T wy = w[PMAX + ty], wz = w[2 * PMAX + tz];
+      gx += ad * wy * wz;
+      gy += a * dw[PMAX + ty] * wz;
+      gz += a * wy * dw[2 * PMAX + tz];
+    }
+    const double Gx = warp_sum((double)gx), Gy = warp_sum((double)gy), Gz = warp_sum((double)gz);
+    if (lane == 0) {
+      const double qi = q[(size_t)rep * ne + i];
+      const size_t k = 3 * ((size_t)rep * ne + i);
+      F[k + 0] = -qi * Gx * sx;
+      F[k + 1] = -qi * Gy * sy;
+      F[k + 2] = -qi * Gz * sz + qi * ez;
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// S-apply: q_raw = S b + dpsi S v for R replicas per pass, one warp per row (rows grid-strided).
+// S is stored row-major in TS (float64, or float32 with compensated float32 lane sums and the
+// right-hand side split into float32 high and low parts).  The epilogue accumulates C^T q_raw
+// and (A^-1 C)^T b for the projection.
+// ------------------------------------------------------------------------------------------
+template <typename TS, int R>
+__global__ void __launch_bounds__(256) k_sapply(const TS* __restrict__ S, int ld, int ne, const double* __restrict__ b,
+                                                int rep0, int nrep, const double* __restrict__ dpsi,
+                                                const double* __restrict__ Sv, const double* __restrict__ W,
+                                                const double* __restrict__ c1, double* __restrict__ qout,
+                                                double* __restrict__ scal) {
+  const int lane = threadIdx.x & 31;
+  double red[4 * R];
+#pragma unroll
+  for (int k = 0; k < 4 * R; ++k) red[k] = 0.0;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+    const TS* row = S + (size_t)i * ld;
+    double tot[R];
+    if constexpr (sizeof(TS) == 4) {
+      CompSum<float> acc[R];
+      float acc_lo[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc_lo[r] = 0.f;
+      for (int j = 4 * lane; j < ne; j += 128) {
+        const float4 s4 = *reinterpret_cast<const float4*>(row + j);
+        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (rep0 + r >= nrep) break;
+          const double* br = b + (size_t)(rep0 + r) * ne;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            if (j + u < ne) {
+              const double y = br[j + u];
+              const float hi = (float)y;
+              const float lo = (float)(y - (double)hi);
+              acc[r].add(sv[u] * hi);
+              acc_lo[r] += sv[u] * lo;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r].value() + (double)acc_lo[r]);
+    } else {
+      double acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = 0.0;
+      for (int j = 2 * lane; j < ne; j += 64) {
+        const double2 s2 = *reinterpret_cast<const double2*>(row + j);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          if (rep0 + r >= nrep) break;
+          const double* br = b + (size_t)(rep0 + r) * ne;
+          acc[r] = fma(s2.x, br[j], acc[r]);
+          if (j + 1 < ne) acc[r] = fma(s2.y, br[j + 1], acc[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r]);
+    }
+    if (lane == 0) {
+      const double w0 = W[2 * i], w1 = W[2 * i + 1], cc = c1[i], svi = Sv[i];
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int rr = rep0 + r;
+        if (rr >= nrep) break;
+        const double qr = tot[r] + dpsi[rr] * svi;
+        qout[(size_t)rr * ne + i] = qr;
+        const double bi = b[(size_t)rr * ne + i];
+        red[4 * r + 0] += qr;
+        red[4 * r + 1] += qr * cc;
+        red[4 * r + 2] += w0 * bi;
+        red[4 * r + 3] += w1 * bi;
+      }
+    }
+  }
+  __shared__ double sred[4 * R][8];
+  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < 4 * R; ++k) sred[k][warp] = red[k];
+  __syncthreads();
+  if (threadIdx.x < 4 * R) {
+    const int k = threadIdx.x, r = k / 4, which = k % 4;
+    if (rep0 + r < nrep) {
+      double s = 0;
+      for (int w = 0; w < nw; ++w) s += sred[k][w];
+      atomicAdd(&scal[(rep0 + r) * NSCAL + S_CQ0 + which], s);
+    }
+  }
+}
+
+// q = q_raw - A^-1 C M C^T q_raw (restores C^T q = 0 to float64 rounding); psibar = -M (A^-1 C)^T (b + dpsi v).
+__global__ void k_project(double* __restrict__ q, int ne, int nrep, int ncons, const double* __restrict__ W,
+                          const double* __restrict__ scal, const double* __restrict__ dpsi, double m00, double m01,
+                          double m10, double m11, double wtv0, double wtv1, double* __restrict__ psibar) {
+  const int rep = blockIdx.y;
+  const double* s = scal + rep * NSCAL;
+  const double c0 = s[S_CQ0], cq1 = (ncons == 2) ? s[S_CQ1] : 0.0;
+  const double a0 = m00 * c0 + m01 * cq1, a1 = m10 * c0 + m11 * cq1;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ne) {
+    double corr = W[2 * i] * a0;
+    if (ncons == 2) corr += W[2 * i + 1] * a1;
+    q[(size_t)rep * ne + i] -= corr;
+  }
+  if (i == 0 && psibar) {
+    const double y0 = s[S_WB0] + dpsi[rep] * wtv0, y1 = (ncons == 2) ? s[S_WB1] + dpsi[rep] * wtv1 : 0.0;
+    psibar[rep * ncons + 0] = -(m00 * y0 + m01 * y1);
+    if (ncons == 2) psibar[rep * ncons + 1] = -(m10 * y0 + m11 * y1);
+  }
+}
+
+__global__ void k_energy_final(int nrep, const double* __restrict__ scal, const double* __restrict__ dpsi,
+                               double alpha, double eta, double slab_e_coef, double ff_over_lz,
+                               double* __restrict__ energy) {
+  const int rep = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rep >= nrep) return;
+  const double* s = scal + rep * NSCAL;
+  double U = KE * (0.5 * s[S_E_LL] + s[S_E_LE] + 0.5 * s[S_E_EE]) + s[S_E_RECIP] +
+             KE * (-(alpha / sqrt(PI)) * (s[S_QQ_ELYT] + s[S_QQ_ELEC]) + eta / sqrt(2.0 * PI) * s[S_QQ_ELEC]);
+  const double mz = s[S_QZ_ELYT] + s[S_QZ_ELEC];
+  U += slab_e_coef * mz * mz;
+  const double H = U - dpsi[rep] * s[S_QV_ELEC] + dpsi[rep] * ff_over_lz * s[S_QZ_ELYT];
+  energy[2 * rep] = U;
+  energy[2 * rep + 1] = H;
+}
+
+// ------------------------------------------------------------------------------------------
+// host orchestration
+// ------------------------------------------------------------------------------------------
+static CellGeom cell_geom(const cpm_ctx* c) {
+  CellGeom g;
+  g.nsten = 1;
+  for (int d = 0; d < 3; ++d) {
+    g.nc[d] = c->nc[d];
+    g.sten[d] = c->sten[d];
+    g.w[d] = 2 * c->sten[d] + 1;
+    g.nsten *= g.w[d];
+    g.edge[d] = c->edge[d];
+    g.box[d] = c->ebox[d];
+  }
+  g.rc2 = c->p.rcut * c->p.rcut;
+  return g;
+}
+
+static SpmeGeom spme_geom(const cpm_ctx* c) {
+  SpmeGeom s;
+  for (int d = 0; d < 3; ++d) {
+    s.K[d] = c->K[d];
+    s.box[d] = c->ebox[d];
+  }
+  s.P = c->P;
+  s.Mr_s = c->Mr_s;
+  s.Mc_s = c->Mc_s;
+  return s;
+}
+
+static int grid_for(long long warps_needed, int per_block_warps = 8, int max_blocks = 152 * 16) {
+  long long b = (warps_needed + per_block_warps - 1) / per_block_warps;
+  return (int)std::max(1LL, std::min<long long>(b, max_blocks));
+}
+
+template <typename T> struct FftOps;
+template <> struct FftOps<float> {
+  static cufftResult fwd(cufftHandle h, void* in, void* out) { return cufftExecR2C(h, (cufftReal*)in, (cufftComplex*)out); }
+  static cufftResult inv(cufftHandle h, void* in, void* out) { return cufftExecC2R(h, (cufftComplex*)in, (cufftReal*)out); }
+  using C2 = float2;
+};
+template <> struct FftOps<double> {
+  static cufftResult fwd(cufftHandle h, void* in, void* out) {
+    return cufftExecD2Z(h, (cufftDoubleReal*)in, (cufftDoubleComplex*)out);
+  }
+  static cufftResult inv(cufftHandle h, void* in, void* out) {
+    return cufftExecZ2D(h, (cufftDoubleComplex*)in, (cufftDoubleReal*)out);
+  }
+  using C2 = double2;
+};
+
+// mesh -> spectrum, influence (+ energy), spectrum -> potential mesh
+template <typename T>
+static int convolve(cpm_ctx* c, int nrep, bool energy, cudaStream_t st) {
+  using C2 = typename FftOps<T>::C2;
+  const int b = (nrep == c->p.max_replicas && c->have_plan[1]) ? 1 : 0;
+  CPM_LIB(cufftSetStream(c->plan_r2c[b], st) == CUFFT_SUCCESS, "cufftSetStream");
+  CPM_LIB(cufftSetStream(c->plan_c2r[b], st) == CUFFT_SUCCESS, "cufftSetStream");
+  T* mr = (T*)c->mesh_r;
+  C2* mc = (C2*)c->mesh_c;
+  T* mp = (T*)c->mesh_phi;
+  const int nexec = b ? 1 : nrep;
+  for (int r = 0; r < nexec; ++r)
+    CPM_LIB(FftOps<T>::fwd(c->plan_r2c[b], mr + r * c->Mr_s, mc + r * c->Mc_s) == CUFFT_SUCCESS, "cufftExec(r2c)");
+  const T* G = c->mixed ? (const T*)c->G32 : (const T*)c->G64;
+  const int blocks = (int)std::min<long long>((c->Mc + 255) / 256, 152 * 8);
+  k_influence<T, C2><<<dim3(blocks, nrep), 256, 0, st>>>(mc, G, c->Mc, c->Mc_s, c->K[2] / 2 + 1, c->K[2],
+                                                         energy ? 1 : 0, c->scal);
+  CPM_LAUNCH();
+  for (int r = 0; r < nexec; ++r)
+    CPM_LIB(FftOps<T>::inv(c->plan_c2r[b], mc + r * c->Mc_s, mp + r * c->Mr_s) == CUFFT_SUCCESS, "cufftExec(c2r)");
+  return CPM_OK;
+}
+
+template <typename T>
+static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const double* dpsi, bool charges,
+               double* q, double* b_out, double* psibar, double* f_elyt, double* f_elec, double* energy,
+               cudaStream_t st) {
+  using V4 = typename Vec4<T>::type;
+  const int ne = c->ne, cap = c->p.max_elyt;
+  const CellGeom g = cell_geom(c);
+  const SpmeGeom sg = spme_geom(c);
+  const double slab_coef = (c->p.geometry == CPM_SLAB) ? KE * 4.0 * PI / c->V : 0.0;
+  const double ff_over_lz = (c->p.geometry == CPM_FF) ? 1.0 / c->Lz : 0.0;
+  const V4* e_loc = c->mixed ? (const V4*)c->e_loc32 : (const V4*)c->e_loc64;
+  V4* l_loc = c->mixed ? (V4*)c->l_loc32 : (V4*)c->l_loc64;
+  const T* e_th = c->mixed ? (const T*)c->e_th32 : (const T*)c->e_th64;
+  const T* e_dth = c->mixed ? (const T*)c->e_dth32 : (const T*)c->e_dth64;
+
+  // ---- prepare: cell list ----
+  CPM_CUDA(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL * nrep, st));
+  CPM_CUDA(cudaMemsetAsync(c->l_count, 0, sizeof(int) * (size_t)c->ncell * nrep, st));
+  const dim3 gsite((cap + 255) / 256, nrep);
+  k_bin<<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, c->ncell, c->scal, c->status);
+  CPM_LAUNCH();
+  k_scan<<<nrep, 1024, 0, st>>>(c->l_count, c->l_start, c->ncell);
+  CPM_LAUNCH();
+  k_scatter<T><<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->l_cell, c->l_count, c->ncell, c->l_sorted, l_loc,
+                                      c->l_cellc);
+  CPM_LAUNCH();
+
+  PairSrc src_elyt{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, nullptr, 0, 0.0, -1};
+  PairSrc src_elec{e_loc, 0, c->e_start, 0, c->e_sorted, nullptr, ne, 0.0, -1};
+  PairSrc none{nullptr, 0, nullptr, 0, nullptr, nullptr, 0, 0.0, -1};
+  const size_t mesh_bytes = sizeof(T) * (size_t)c->Mr_s * nrep;
+
+  if (charges) {
+    double* b = b_out ? b_out : c->b_tmp;
+    // real-space Gaussian-point part of b at the electrode sites
+    PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, nullptr, nullptr, c->phi_real};
+    PairSrc s = src_elyt;
+    s.beta = c->p.eta;
+    k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, s, none, g, c->p.alpha, c->scal);
+    CPM_LAUNCH();
+    // SPME part
+    CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+    k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
+    CPM_LAUNCH();
+    CPM_TRY(convolve<T>(c, nrep, false, st));
+    k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
+                                                            c->phi_real, c->e_z, slab_coef, c->scal, b);
+    CPM_LAUNCH();
+    // q = S b + dpsi S v, then the projection
+    const int sblocks = std::min(grid_for(ne), 152 * 4);
+    for (int r0 = 0; r0 < nrep; r0 += 4) {
+      if (c->mixed)
+        k_sapply<float, 4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, b, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
+                                                    q, c->scal);
+      else
+        k_sapply<double, 4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
+                                                     q, c->scal);
+      CPM_LAUNCH();
+    }
+    k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, c->scal, dpsi, c->Mh[0],
+                                                            c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0], c->WTv[1],
+                                                            psibar);
+    CPM_LAUNCH();
+  }
+
+  if (f_elyt || f_elec || energy) {
+    // SPME of all charges
+    CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+    k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
+    CPM_LAUNCH();
+    k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(q, ne, c->e_base, e_th, sg, c->e_z, c->e_v,
+                                                               (T*)c->mesh_r, c->scal);
+    CPM_LAUNCH();
+    CPM_TRY(convolve<T>(c, nrep, energy != nullptr, st));
+    if (f_elyt) {
+      k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, xyzq, cap, sg, dpsi,
+                                                                    ff_over_lz, slab_coef, c->scal, f_elyt);
+      CPM_LAUNCH();
+    }
+    if (f_elec) {
+      k_gather_f_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, q, ne, c->e_base, e_th,
+                                                                   e_dth, sg, dpsi, ff_over_lz, slab_coef, c->scal,
+                                                                   f_elec);
+      CPM_LAUNCH();
+    }
+    // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes)
+    {
+      PairTgt tg{l_loc, (long long)cap, c->l_cellc, c->l_sorted, off, cap, ne, nullptr, f_elyt, nullptr};
+      PairSrc a = src_elyt;
+      a.slot = S_E_LL;
+      PairSrc e = src_elec;
+      e.q = q;
+      e.beta = c->p.eta;
+      e.slot = S_E_LE;
+      if (f_elyt)
+        k_pair<T, true><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+      else
+        k_pair<T, false><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+      CPM_LAUNCH();
+    }
+    // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian
+    if (f_elec || energy) {
+      PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, q, f_elec, nullptr};
+      PairSrc a = f_elec ? src_elyt : none;
+      a.beta = c->p.eta;
+      PairSrc e = src_elec;
+      e.q = q;
+      e.beta = c->p.eta / std::sqrt(2.0);
+      e.slot = S_E_EE;
+      if (f_elec)
+        k_pair<T, true><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+      else
+        k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+      CPM_LAUNCH();
+    }
+    if (energy) {
+      const double slab_e = (c->p.geometry == CPM_SLAB) ? KE * 2.0 * PI / c->V : 0.0;
+      k_energy_final<<<(nrep + 127) / 128, 128, 0, st>>>(nrep, c->scal, dpsi, c->p.alpha, c->p.eta, slab_e,
+                                                         ff_over_lz, energy);
+      CPM_LAUNCH();
+    }
+  }
+  return CPM_OK;
+}
+
+static int dispatch(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const double* dpsi, bool charges,
+                    double* q, double* b, double* psibar, double* f_elyt, double* f_elec, double* energy,
+                    void* stream) {
+  if (!c || !off || !xyzq || !dpsi || !q) {
+    set_error("null context or required pointer");
+    return CPM_ERR_ARG;
+  }
+  if (nrep < 1 || nrep > c->p.max_replicas) {
+    set_error("n_rep %d outside [1, %d]", nrep, c->p.max_replicas);
+    return CPM_ERR_CAPACITY;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  return c->mixed ? run<float>(c, nrep, off, xyzq, dpsi, charges, q, b, psibar, f_elyt, f_elec, energy, st)
+                  : run<double>(c, nrep, off, xyzq, dpsi, charges, q, b, psibar, f_elyt, f_elec, energy, st);
+}
+
+}  // namespace cpm
+
+int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
+  const size_t R = c->p.max_replicas, cap = c->p.max_elyt, ne = c->ne;
+  const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
+  CPM_CUDA(cudaMalloc(&c->mesh_r, tsz * c->Mr_s * R));
+  CPM_CUDA(cudaMalloc(&c->mesh_phi, tsz * c->Mr_s * R));
+  CPM_CUDA(cudaMalloc(&c->mesh_c, 2 * tsz * c->Mc_s * R));
+  CPM_CUDA(cudaMalloc(&c->l_cell, sizeof(int) * R * cap));
+  CPM_CUDA(cudaMalloc(&c->l_count, sizeof(int) * R * c->ncell));
+  CPM_CUDA(cudaMalloc(&c->l_start, sizeof(int) * R * (c->ncell + 1)));
+  CPM_CUDA(cudaMalloc(&c->l_sorted, sizeof(int) * R * cap));
+  if (c->mixed)
+    CPM_CUDA(cudaMalloc(&c->l_loc32, sizeof(float4) * R * cap));
+  else
+    CPM_CUDA(cudaMalloc(&c->l_loc64, sizeof(double4_32a) * R * cap));
+  CPM_CUDA(cudaMalloc(&c->l_cellc, sizeof(int4) * R * cap));
+  CPM_CUDA(cudaMalloc(&c->phi_real, sizeof(double) * R * ne));
+  CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * ne));
+  CPM_CUDA(cudaMalloc(&c->scal, sizeof(double) * R * cpm::NSCAL));
+  CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
+  CPM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+  return CPM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" int cpm_step_charges(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const double* xyzq,
+                                const double* dpsi, double* q, double* b, double* psibar, void* stream) {
+  return cpm::dispatch(ctx, n_rep, off, xyzq, dpsi, true, q, b, psibar, nullptr, nullptr, nullptr, stream);
+}
+
+extern "C" int cpm_forces(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const double* xyzq,
+                          const double* dpsi, const double* q, double* f_elyt, double* f_elec, double* energy,
+                          void* stream) {
+  return cpm::dispatch(ctx, n_rep, off, xyzq, dpsi, false, const_cast<double*>(q), nullptr, nullptr, f_elyt,
+                       f_elec, energy, stream);
+}
+
+extern "C" int cpm_energy(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const double* xyzq,
+                          const double* dpsi, const double* q, double* energy, void* stream) {
+  if (!energy) return CPM_ERR_ARG;
+  return cpm::dispatch(ctx, n_rep, off, xyzq, dpsi, false, const_cast<double*>(q), nullptr, nullptr, nullptr,
+                       nullptr, energy, stream);
+}
+
+extern "C" int cpm_step(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const double* xyzq, const double* dpsi,
+                        double* q, double* psibar, double* f_elyt, double* f_elec, double* energy, void* stream) {
+  return cpm::dispatch(ctx, n_rep, off, xyzq, dpsi, true, q, nullptr, psibar, f_elyt, f_elec, energy, stream);
+}

@@ -1,0 +1,68 @@
+"""The C-ABI library loads and exports every entry point that include/cpm.h declares (CPU only:
+no call here touches a GPU)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "cpm.h")).read()
+    return sorted(set(re.findall(r"^(?:int|void|const char\*)\s+(cpm_\w+)\s*\(", txt, flags=re.M)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2201_12963_gb300 import build
+    build.build_library()
+    import paper_2201_12963_gb300 as g
+    return g
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(pkg):
+    lib = ctypes.CDLL(pkg.build.lib_path())
+    for name in _declared():
+        assert hasattr(lib, name), name
+    assert set(pkg.EXPORTED) == set(_declared())
+
+
+def test_strerror_covers_every_status(pkg):
+    for s in range(0, -10, -1):
+        assert pkg.cpm_strerror(s) != "unknown status"
+    assert pkg.cpm_strerror(-99) == "unknown status"
+
+
+def test_invalid_parameters_rejected_before_any_device_work(pkg):
+    xyz = np.array([[0, 0, 1.0], [1, 0, 1.0], [0, 0, 9.0], [1, 0, 9.0]])
+    side = np.array([-1, -1, 1, 1])
+    bad = [dict(order=9), dict(order=2), dict(alpha=2.0), dict(grid=(8, 8, 9)), dict(max_replicas=0)]
+    for kw in bad:
+        args = dict(box=(10, 10, 10), eta=1.979, alpha=0.25, rcut=5.0, grid=(16, 16, 16), order=5)
+        args.update(kw)
+        p = pkg.make_params(**args)
+        with pytest.raises(pkg.CPMError) as ei:
+            pkg.cpm_build_matrix(p, xyz, side, stream=0)
+        assert ei.value.status == -1
+    p = pkg.make_params((10, 10, 10), 1.979, 0.25, 5.0, (16, 16, 16))
+    with pytest.raises(pkg.CPMError) as ei:
+        pkg.cpm_build_matrix(p, xyz, np.array([-1, 2, 1, 1]), stream=0)
+    assert ei.value.status == -1
+    bad_xyz = xyz.copy()
+    bad_xyz[0, 0] = np.nan
+    with pytest.raises(pkg.CPMError) as ei:
+        pkg.cpm_build_matrix(p, bad_xyz, side, stream=0)
+    assert ei.value.status == -4
+    pdc = pkg.make_params((10, 10, 10), 1.979, 0.25, 5.0, (16, 16, 16), geometry="dc")
+    with pytest.raises(pkg.CPMError) as ei:
+        pkg.cpm_build_matrix(pdc, xyz, side, None, stream=0)   # doubled cell needs sub-cell labels
+    assert ei.value.status == -1
