@@ -172,6 +172,44 @@ int cpm_info(const cpm_ctx* ctx, int32_t* n_elec, int32_t* ncons, int64_t* mesh_
  */
 int cpm_status(cpm_ctx* ctx, void* stream);
 
+/* Phases timed by the per-call profiler (cpm_profile_enable / cpm_profile_read). */
+enum cpm_phase {
+  CPM_PH_CELL_LIST = 0,   /* electrolyte binning and counting sort */
+  CPM_PH_B_REAL = 1,      /* real-space Gaussian-point part of b */
+  CPM_PH_B_SPREAD = 2,    /* SPME charge assignment of the electrolyte */
+  CPM_PH_B_FFT = 3,       /* forward FFT, influence function, inverse FFT (charge update) */
+  CPM_PH_B_GATHER = 4,    /* mesh potential at the electrode sites, b assembly */
+  CPM_PH_S_APPLY = 5,     /* q = S b + dpsi S v */
+  CPM_PH_PROJECT = 6,     /* neutrality projection and offsets */
+  CPM_PH_F_SPREAD = 7,    /* SPME charge assignment of all charges */
+  CPM_PH_F_FFT = 8,       /* forward FFT, influence function (+ energy), inverse FFT (forces) */
+  CPM_PH_F_GATHER = 9,    /* mesh forces on all sites */
+  CPM_PH_F_PAIR_ELYT = 10,/* real-space forces / energy, electrolyte targets */
+  CPM_PH_F_PAIR_ELEC = 11,/* real-space forces / energy, electrode targets */
+  CPM_PH_ENERGY = 12,     /* energy assembly */
+  CPM_NPHASES = 13
+};
+
+/*
+ * cpm_profile_enable - per-phase CUDA-event timing of subsequent per-step calls.  capacity > 0
+ * allocates room for that many timed (phase, call) intervals and starts recording (events are
+ * recorded on each call's stream around each phase); capacity = 0 stops recording and frees the
+ * events.  Intervals beyond the capacity are not recorded.  Not for use during graph capture.
+ */
+int cpm_profile_enable(cpm_ctx* ctx, int32_t capacity);
+
+/*
+ * cpm_profile_read - synchronise the device, then write the accumulated milliseconds
+ * (ms_host[CPM_NPHASES]) and interval counts (count_host[CPM_NPHASES]) of everything recorded
+ * since the last read, and reset the accumulators.
+ */
+int cpm_profile_read(cpm_ctx* ctx, double* ms_host, int64_t* count_host);
+
+/* cpm_counters - number of this library's kernels launched by the per-step calls of ctx so far
+ * (host-side count; a CUDA graph replay of a captured call launches the same kernels again
+ * without adding to it). */
+int cpm_counters(const cpm_ctx* ctx, int64_t* kernel_launches);
+
 /* cpm_destroy - free the context and everything it owns (NULL is accepted). */
 void cpm_destroy(cpm_ctx* ctx);
 

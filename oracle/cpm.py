@@ -293,3 +293,33 @@ class Reference:
         if want_forces:
             out["F_elyt"], out["F_elec"] = forces(w, R, Q, q, dpsi, self.kmax)
         return out
+
+    def sampled_step(self, r=0, frac=0.1, seed=0):
+        """A bounded timing sample of step(r): every real-space sum restricted to a random fraction
+        `frac` of its target sites and every reciprocal sum to a random fraction `frac` of the
+        k-vectors, with the KKT solve in full.  Its cost is close to `frac` times that of a full
+        step; the values it produces are partial sums and are not returned."""
+        w = self.w
+        rng = np.random.default_rng(seed)
+        R, Q, dpsi = w.elyt_xyz[r], w.elyt_q[r], float(w.dpsi[r])
+        box = ewald_box(w)
+        E = np.asarray(w.elec_xyz, np.float64)
+        a, eta, rc = w.alpha, w.eta, w.rcut
+        te = np.flatnonzero(rng.random(E.shape[0]) < frac)
+        tl = np.flatnonzero(rng.random(R.shape[0]) < frac)
+
+        def ksub(n):
+            return rng.random(n) < frac
+
+        b = np.zeros(E.shape[0])
+        b[te] = -KE * real_space(E[te], R, Q, box, rc, a, eta)
+        b -= KE * recip_space(E, R, Q, box, a, self.kmax, ksub=ksub)
+        q, _ = solve_charges(self.cho, b, self.v, dpsi, self.C)
+        P = np.vstack([E, R])
+        c = np.concatenate([q, Q])
+        for grad in (False, True):       # step() evaluates energies, then forces
+            real_space(E[te], E, q, box, rc, a, eta / SQRT2, same=True, want_grad=grad, target_index=te)
+            real_space(E[te], R, Q, box, rc, a, eta, want_grad=grad)
+            real_space(R[tl], E, q, box, rc, a, eta, want_grad=grad)
+            real_space(R[tl], R, Q, box, rc, a, None, same=True, want_grad=grad, target_index=tl)
+            recip_space(P, P, c, box, a, self.kmax, want_grad=grad, ksub=ksub)

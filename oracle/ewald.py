@@ -79,11 +79,12 @@ def image_shifts(box, rcut) -> np.ndarray:
 
 
 def real_space(targets, sources, charges, box, rcut, alpha, beta, same=False, want_grad=False,
-               chunk=256):
+               chunk=256, target_index=None):
     """Real-space Ewald potential (and its gradient) at `targets` from all images of `sources`.
 
-    beta selects the kernel (see module docstring).  same=True means targets and sources are the
-    same set and the i == j, zero-shift term is excluded.
+    beta selects the kernel (see module docstring).  same=True means the targets are members of the
+    source set (target i is source target_index[i], default i) and each target's own zero-shift
+    term is excluded.
     Returns phi [nt] (without KE) and, if want_grad, grad [nt, 3] = d phi / d r_target.
     """
     targets = np.asarray(targets, np.float64)
@@ -107,7 +108,8 @@ def real_space(targets, sources, charges, box, rcut, alpha, beta, same=False, wa
             m = r2 < rc2
             if same and not np.any(s):
                 ii = np.arange(b - a)
-                m[ii, a + ii] = False
+                own = a + ii if target_index is None else np.asarray(target_index)[a:b]
+                m[ii, own] = False
             ti, sj = np.nonzero(m)
             if ti.size == 0:
                 continue
@@ -140,17 +142,20 @@ def recip_weights(k, box, alpha):
     return 2.0 * (4.0 * math.pi / V) * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
 
 
-def recip_space(targets, sources, charges, box, alpha, kmax=None, want_grad=False, kchunk=2048):
+def recip_space(targets, sources, charges, box, alpha, kmax=None, want_grad=False, kchunk=2048, ksub=None):
     """Reciprocal-space potential (and gradient) at `targets` from point charges at `sources`.
 
     phi(r) = sum_{k half} w_k [Re S(k) cos(k.r) + Im S(k) sin(k.r)],
     grad   = sum_{k half} w_k k [Im S(k) cos(k.r) - Re S(k) sin(k.r)],  w_k from recip_weights.
+    ksub (timing samples only) maps the number of k-vectors to a selection of them.
     """
     targets = np.asarray(targets, np.float64)
     sources = np.asarray(sources, np.float64)
     charges = np.asarray(charges, np.float64)
     kmax = default_kmax(alpha) if kmax is None else kmax
     k_all = kvectors(box, kmax)
+    if ksub is not None:
+        k_all = k_all[ksub(k_all.shape[0])]
     w_all = recip_weights(k_all, box, alpha)
     phi = np.zeros(targets.shape[0])
     grad = np.zeros((targets.shape[0], 3)) if want_grad else None

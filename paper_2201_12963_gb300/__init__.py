@@ -20,7 +20,11 @@ GEOMETRY = {"ff": CPM_FF, "dc": CPM_DOUBLED, "slab": CPM_SLAB}
 PRECISION = {"fp64": CPM_FP64, "mixed": CPM_MIXED}
 
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
-            "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_destroy", "cpm_strerror", "cpm_last_error")
+            "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
+            "cpm_destroy",
+            "cpm_strerror", "cpm_last_error")
+PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
+          "f_gather", "f_pair_elyt", "f_pair_elec", "energy")
 
 
 class CpmParams(ctypes.Structure):
@@ -58,6 +62,9 @@ def _load():
     lib.cpm_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64),
                              ctypes.POINTER(i32)]
     lib.cpm_status.argtypes = [vp, vp]
+    lib.cpm_profile_enable.argtypes = [vp, i32]
+    lib.cpm_profile_read.argtypes = [vp, pd, pd]
+    lib.cpm_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
     lib.cpm_strerror.argtypes = [ctypes.c_int]
@@ -224,6 +231,25 @@ def cpm_copy_matrix(ctx: Context, which: int) -> np.ndarray:
 
 def cpm_status(ctx: Context, stream=None) -> int:
     return int(_lib.cpm_status(ctx.handle, _stream_ptr(stream)))
+
+
+def cpm_profile_enable(ctx: Context, capacity: int):
+    _check(_lib.cpm_profile_enable(ctx.handle, int(capacity)), "cpm_profile_enable")
+
+
+def cpm_profile_read(ctx: Context) -> dict:
+    """{phase name: (milliseconds, intervals)} accumulated since the last read."""
+    ms = np.zeros(len(PHASES), dtype=np.float64)
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
+    _check(_lib.cpm_profile_read(ctx.handle, ms.ctypes.data, cnt.ctypes.data), "cpm_profile_read")
+    return {name: (float(ms[k]), int(cnt[k])) for k, name in enumerate(PHASES)}
+
+
+def cpm_counters(ctx: Context) -> int:
+    """Kernel launches issued by the per-step calls of ctx so far."""
+    v = ctypes.c_int64()
+    _check(_lib.cpm_counters(ctx.handle, ctypes.byref(v)), "cpm_counters")
+    return v.value
 
 
 def cpm_strerror(status: int) -> str:

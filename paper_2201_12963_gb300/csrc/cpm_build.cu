@@ -570,6 +570,7 @@ extern "C" int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const doubl
 
 extern "C" void cpm_destroy(cpm_ctx* c) {
   if (!c) return;
+  cpm_profile_enable(c, 0);
   void* bufs[] = {c->e_pos64, c->e_loc64, c->e_loc32, c->e_cellc, c->e_sorted, c->e_start, c->e_base,
                   c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->S64, c->S32,
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,

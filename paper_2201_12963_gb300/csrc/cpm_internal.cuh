@@ -109,6 +109,11 @@ struct cpm_ctx {
   double* b_tmp = nullptr;      // [max_rep][ne]
   double* scal = nullptr;       // [max_rep][NSCAL]
   int* status = nullptr;        // device status word
+  // per-phase event profiler
+  cudaEvent_t* prof_ev = nullptr;   // [2 * prof_cap]
+  int* prof_phase = nullptr;        // [prof_cap]
+  int prof_cap = 0, prof_used = 0;
+  long long launches = 0;           // kernels of this library launched by per-step calls
   // libraries
   cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t solver = nullptr;

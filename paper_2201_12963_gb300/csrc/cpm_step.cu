@@ -730,6 +730,32 @@ static SpmeGeom spme_geom(const cpm_ctx* c) {
   return s;
 }
 
+// Every kernel launch of a per-step call is counted (cpm_counters) and checked.
+#define STEP_LAUNCH()  \
+  do {                 \
+    ++c->launches;     \
+    CPM_LAUNCH();      \
+  } while (0)
+
+// Records a (start, stop) event pair around one phase when the profiler is on.
+struct PhaseTimer {
+  cpm_ctx* c;
+  cudaStream_t st;
+  int slot = -1;
+  PhaseTimer(cpm_ctx* c_, cudaStream_t st_, int phase) : c(c_), st(st_) {
+    if (c->prof_cap > 0 && c->prof_used < c->prof_cap) {
+      slot = c->prof_used++;
+      c->prof_phase[slot] = phase;
+      cudaEventRecord(c->prof_ev[2 * slot], st);
+    }
+  }
+  void stop() {
+    if (slot >= 0) cudaEventRecord(c->prof_ev[2 * slot + 1], st);
+    slot = -1;
+  }
+  ~PhaseTimer() { stop(); }
+};
+
 static int grid_for(long long warps_needed, int per_block_warps = 8, int max_blocks = 152 * 16) {
   long long b = (warps_needed + per_block_warps - 1) / per_block_warps;
   return (int)std::max(1LL, std::min<long long>(b, max_blocks));
@@ -768,7 +794,7 @@ static int convolve(cpm_ctx* c, int nrep, bool energy, cudaStream_t st) {
   const int blocks = (int)std::min<long long>((c->Mc + 255) / 256, 152 * 8);
   k_influence<T, C2><<<dim3(blocks, nrep), 256, 0, st>>>(mc, G, c->Mc, c->Mc_s, c->K[2] / 2 + 1, c->K[2],
                                                          energy ? 1 : 0, c->scal);
-  CPM_LAUNCH();
+  STEP_LAUNCH();
   for (int r = 0; r < nexec; ++r)
     CPM_LIB(FftOps<T>::inv(c->plan_c2r[b], mc + r * c->Mc_s, mp + r * c->Mr_s) == CUFFT_SUCCESS, "cufftExec(c2r)");
   return CPM_OK;
@@ -790,16 +816,19 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   const T* e_dth = c->mixed ? (const T*)c->e_dth32 : (const T*)c->e_dth64;
 
   // ---- prepare: cell list ----
+  {
+  PhaseTimer pt(c, st, CPM_PH_CELL_LIST);
   CPM_CUDA(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL * nrep, st));
   CPM_CUDA(cudaMemsetAsync(c->l_count, 0, sizeof(int) * (size_t)c->ncell * nrep, st));
   const dim3 gsite((cap + 255) / 256, nrep);
   k_bin<<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, c->ncell, c->scal, c->status);
-  CPM_LAUNCH();
+  STEP_LAUNCH();
   k_scan<<<nrep, 1024, 0, st>>>(c->l_count, c->l_start, c->ncell);
-  CPM_LAUNCH();
+  STEP_LAUNCH();
   k_scatter<T><<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->l_cell, c->l_count, c->ncell, c->l_sorted, l_loc,
                                       c->l_cellc);
-  CPM_LAUNCH();
+  STEP_LAUNCH();
+  }
 
   PairSrc src_elyt{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, nullptr, 0, 0.0, -1};
   PairSrc src_elec{e_loc, 0, c->e_start, 0, c->e_sorted, nullptr, ne, 0.0, -1};
@@ -812,18 +841,32 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, nullptr, nullptr, c->phi_real};
     PairSrc s = src_elyt;
     s.beta = c->p.eta;
-    k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, s, none, g, c->p.alpha, c->scal);
-    CPM_LAUNCH();
+    {
+      PhaseTimer pt(c, st, CPM_PH_B_REAL);
+      k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, s, none, g, c->p.alpha, c->scal);
+      STEP_LAUNCH();
+    }
     // SPME part
-    CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-    k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
-    CPM_LAUNCH();
-    CPM_TRY(convolve<T>(c, nrep, false, st));
-    k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
-                                                            c->phi_real, c->e_z, slab_coef, c->scal, b);
-    CPM_LAUNCH();
+    {
+      PhaseTimer pt(c, st, CPM_PH_B_SPREAD);
+      CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
+      STEP_LAUNCH();
+    }
+    {
+      PhaseTimer pt(c, st, CPM_PH_B_FFT);
+      CPM_TRY(convolve<T>(c, nrep, false, st));
+    }
+    {
+      PhaseTimer pt(c, st, CPM_PH_B_GATHER);
+      k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
+                                                              c->phi_real, c->e_z, slab_coef, c->scal, b);
+      STEP_LAUNCH();
+    }
     // q = S b + dpsi S v, then the projection
     const int sblocks = std::min(grid_for(ne), 152 * 4);
+    {
+    PhaseTimer pt(c, st, CPM_PH_S_APPLY);
     for (int r0 = 0; r0 < nrep; r0 += 4) {
       if (c->mixed)
         k_sapply<float, 4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, b, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
@@ -831,36 +874,47 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       else
         k_sapply<double, 4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
                                                      q, c->scal);
-      CPM_LAUNCH();
+      STEP_LAUNCH();
     }
+    }
+    PhaseTimer ptp(c, st, CPM_PH_PROJECT);
     k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, c->scal, dpsi, c->Mh[0],
                                                             c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0], c->WTv[1],
                                                             psibar);
-    CPM_LAUNCH();
+    STEP_LAUNCH();
   }
 
   if (f_elyt || f_elec || energy) {
     // SPME of all charges
-    CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-    k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
-    CPM_LAUNCH();
-    k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(q, ne, c->e_base, e_th, sg, c->e_z, c->e_v,
-                                                               (T*)c->mesh_r, c->scal);
-    CPM_LAUNCH();
-    CPM_TRY(convolve<T>(c, nrep, energy != nullptr, st));
+    {
+      PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
+      CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
+      STEP_LAUNCH();
+      k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(q, ne, c->e_base, e_th, sg, c->e_z, c->e_v,
+                                                                 (T*)c->mesh_r, c->scal);
+      STEP_LAUNCH();
+    }
+    {
+      PhaseTimer pt(c, st, CPM_PH_F_FFT);
+      CPM_TRY(convolve<T>(c, nrep, energy != nullptr, st));
+    }
+    PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
     if (f_elyt) {
       k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, xyzq, cap, sg, dpsi,
                                                                     ff_over_lz, slab_coef, c->scal, f_elyt);
-      CPM_LAUNCH();
+      STEP_LAUNCH();
     }
     if (f_elec) {
       k_gather_f_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, q, ne, c->e_base, e_th,
                                                                    e_dth, sg, dpsi, ff_over_lz, slab_coef, c->scal,
                                                                    f_elec);
-      CPM_LAUNCH();
+      STEP_LAUNCH();
     }
+    ptg.stop();
     // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes)
     {
+      PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELYT);
       PairTgt tg{l_loc, (long long)cap, c->l_cellc, c->l_sorted, off, cap, ne, nullptr, f_elyt, nullptr};
       PairSrc a = src_elyt;
       a.slot = S_E_LL;
@@ -872,10 +926,11 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         k_pair<T, true><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
       else
         k_pair<T, false><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
-      CPM_LAUNCH();
+      STEP_LAUNCH();
     }
     // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian
     if (f_elec || energy) {
+      PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
       PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, q, f_elec, nullptr};
       PairSrc a = f_elec ? src_elyt : none;
       a.beta = c->p.eta;
@@ -887,13 +942,14 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         k_pair<T, true><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
       else
         k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
-      CPM_LAUNCH();
+      STEP_LAUNCH();
     }
     if (energy) {
+      PhaseTimer pt(c, st, CPM_PH_ENERGY);
       const double slab_e = (c->p.geometry == CPM_SLAB) ? KE * 2.0 * PI / c->V : 0.0;
       k_energy_final<<<(nrep + 127) / 128, 128, 0, st>>>(nrep, c->scal, dpsi, c->p.alpha, c->p.eta, slab_e,
                                                          ff_over_lz, energy);
-      CPM_LAUNCH();
+      STEP_LAUNCH();
     }
   }
   return CPM_OK;
@@ -965,4 +1021,46 @@ extern "C" int cpm_energy(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const
 extern "C" int cpm_step(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const double* xyzq, const double* dpsi,
                         double* q, double* psibar, double* f_elyt, double* f_elec, double* energy, void* stream) {
   return cpm::dispatch(ctx, n_rep, off, xyzq, dpsi, true, q, nullptr, psibar, f_elyt, f_elec, energy, stream);
+}
+
+extern "C" int cpm_profile_enable(cpm_ctx* c, int32_t capacity) {
+  if (!c || capacity < 0) return CPM_ERR_ARG;
+  if (c->prof_ev) {
+    for (int k = 0; k < 2 * c->prof_cap; ++k) cudaEventDestroy(c->prof_ev[k]);
+    delete[] c->prof_ev;
+    delete[] c->prof_phase;
+    c->prof_ev = nullptr;
+    c->prof_phase = nullptr;
+  }
+  c->prof_cap = 0;
+  c->prof_used = 0;
+  if (capacity == 0) return CPM_OK;
+  c->prof_ev = new cudaEvent_t[2 * (size_t)capacity];
+  c->prof_phase = new int[capacity];
+  for (int k = 0; k < 2 * capacity; ++k) CPM_CUDA(cudaEventCreate(&c->prof_ev[k]));
+  c->prof_cap = capacity;
+  return CPM_OK;
+}
+
+extern "C" int cpm_profile_read(cpm_ctx* c, double* ms, int64_t* count) {
+  if (!c || !ms || !count) return CPM_ERR_ARG;
+  for (int p = 0; p < CPM_NPHASES; ++p) {
+    ms[p] = 0.0;
+    count[p] = 0;
+  }
+  CPM_CUDA(cudaDeviceSynchronize());
+  for (int k = 0; k < c->prof_used; ++k) {
+    float t = 0.f;
+    CPM_CUDA(cudaEventElapsedTime(&t, c->prof_ev[2 * k], c->prof_ev[2 * k + 1]));
+    ms[c->prof_phase[k]] += t;
+    count[c->prof_phase[k]] += 1;
+  }
+  c->prof_used = 0;
+  return CPM_OK;
+}
+
+extern "C" int cpm_counters(const cpm_ctx* c, int64_t* kernel_launches) {
+  if (!c || !kernel_launches) return CPM_ERR_ARG;
+  *kernel_launches = c->launches;
+  return CPM_OK;
 }

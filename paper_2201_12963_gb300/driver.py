@@ -26,7 +26,7 @@ def pack(w):
     counts = [len(q) for q in w.elyt_q]
     offsets = np.zeros(len(counts) + 1, dtype=np.int32)
     offsets[1:] = np.cumsum(counts)
-    xyzq = np.zeros((int(offsets[-1]), 4), dtype=np.float64)
+    xyzq = np.zeros((max(1, int(offsets[-1])), 4), dtype=np.float64)   # >= 1 row: never a null pointer
     for r in range(len(counts)):
         xyzq[offsets[r]:offsets[r + 1], :3] = w.elyt_xyz[r]
         xyzq[offsets[r]:offsets[r + 1], 3] = w.elyt_q[r]

@@ -17,8 +17,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def pkg():
-    from paper_2201_12963_gb300 import build
-    build.build_library()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_2201_12963_gb300 as g
     return g
 
