@@ -214,7 +214,7 @@ def run_gb300(args):
     h_xyzq = torch.from_numpy(xyzq).pin_memory()
     nl = int(off[-1])
     h_f = torch.empty(3 * nl, dtype=torch.float64).pin_memory()
-    h_e = torch.empty(2, dtype=torch.float64).pin_memory()
+    h_e = torch.empty(4, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -224,7 +224,7 @@ def run_gb300(args):
         s.xyzq.copy_(h_xyzq, non_blocking=True)
         graph.replay()
         h_f.copy_(s.f_elyt[: 3 * nl], non_blocking=True)
-        h_e.copy_(s.energy[:2], non_blocking=True)
+        h_e.copy_(s.energy[:4], non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
     e1.record()
     torch.cuda.synchronize(dev)
@@ -274,7 +274,7 @@ def run_gb300(args):
                       "replica_steps_per_s": round(steps_per_s, 1), "wall_s": round(wall, 3)},
            "clocks": clk,
            "e2e": {"value": round(e2e_value, 2), "unit": "ns/day",
-                   "h2d_bytes_per_step": int(xyzq.nbytes), "d2h_bytes_per_step": int(8 * 3 * nl + 16),
+                   "h2d_bytes_per_step": int(xyzq.nbytes), "d2h_bytes_per_step": int(8 * 3 * nl + 32),
                    "steps": Ke},
            "gpu_launches": int(launches_per_step * K),
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},

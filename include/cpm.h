@@ -128,15 +128,18 @@ int cpm_step_charges(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_de
  *
  *   f_elyt_dev   [offsets[n_rep]*3] float64 forces on the electrolyte sites (eV/A) or NULL.
  *   f_elec_dev   [n_rep*N_e*3] float64 forces on the electrode sites or NULL.
- *   energy_dev   [n_rep*2] float64 or NULL: per replica (U, H).  U is the Coulomb energy of
- *                Eq. 3 (plus the slab dipole term); H = U - dpsi q^T v (+ dpsi/L_z sum Q_j Z_j for
- *                CPM_FF) is the constant-potential energy whose gradient is minus the force.
+ *   energy_dev   [n_rep*4] float64 or NULL: per replica (U, H, dH/d(dpsi), Q_+).  U is the
+ *                Coulomb energy of Eq. 3 (plus the slab dipole term) evaluated as the full Ewald
+ *                sum of the given charges; H = U - dpsi q^T v (+ dpsi/L_z sum Q_j Z_j for CPM_FF) is
+ *                the constant-potential energy whose gradient is minus the force at the
+ *                constrained optimum; dH/d(dpsi) = -q^T v (+ sum Q_j Z_j / L_z for CPM_FF) is its
+ *                explicit derivative; Q_+ is the total charge of the side +1 sites.
  */
 int cpm_forces(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
                const double* elyt_xyzq_dev, const double* dpsi_dev, const double* q_dev,
                double* f_elyt_dev, double* f_elec_dev, double* energy_dev, void* stream);
 
-/* cpm_energy - energies only: cpm_forces with both force outputs NULL (energy_dev required). */
+/* cpm_energy - energies only: cpm_forces with both force outputs NULL (energy_dev [n_rep*4] required). */
 int cpm_energy(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
                const double* elyt_xyzq_dev, const double* dpsi_dev, const double* q_dev,
                double* energy_dev, void* stream);
@@ -144,6 +147,9 @@ int cpm_energy(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
 /*
  * cpm_step - one whole electrostatic step: cpm_step_charges followed by cpm_forces on the new
  * charges, sharing the cell list.  Outputs as above; q_dev is required, the rest may be NULL.
+ * Because q is the constrained optimum here, U is assembled in closed form,
+ * U = U_elyt - q^T b / 2 + dpsi q^T v / 2 (A q = b + dpsi v + C psibar, C^T q = 0), which needs no
+ * electrode-electrode pair sum; it agrees with the full sum of cpm_energy to the mesh error.
  */
 int cpm_step(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev,
              const double* elyt_xyzq_dev, const double* dpsi_dev, double* q_dev, double* psibar_dev,

@@ -202,7 +202,8 @@ def energies(w, R, Q, q, dpsi, kmax=None) -> dict:
 
     U = KE [ 1/2 sum_a c_a phi_real,a + 1/2 sum_a c_a phi_k,a - alpha/sqrt pi sum c^2
              + eta/sqrt(2 pi) sum q^2 ] (+ KE 2 pi/V M_z^2 for the slab),
-    H = U - dpsi q^T v (+ dpsi/L_z sum_j Q_j Z_j for the finite field).
+    H = U - dpsi q^T v (+ dpsi/L_z sum_j Q_j Z_j for the finite field); also the explicit
+    derivative dH/d(dpsi) at fixed charges and the total charge Q_+ of the side +1 electrode.
     """
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)
@@ -217,10 +218,11 @@ def energies(w, R, Q, q, dpsi, kmax=None) -> dict:
         mz = float(q @ E[:, 2] + Q @ R[:, 2])
         U += KE * (2.0 * math.pi / V) * mz * mz
     v = geometry_vector(w)
-    H = U - dpsi * float(q @ v)
+    dH = -float(q @ v)
     if w.geometry == "ff":
-        H += dpsi / float(w.box[2]) * float(Q @ R[:, 2])
-    return {"U": U, "H": H}
+        dH += float(Q @ R[:, 2]) / float(w.box[2])
+    H = U + dpsi * dH
+    return {"U": U, "H": H, "dH_ddpsi": dH, "Q_plus": float(q[np.asarray(w.elec_side) > 0].sum())}
 
 
 def electrolyte_energy(w, R, Q, kmax=None) -> float:

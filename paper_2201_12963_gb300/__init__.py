@@ -190,7 +190,7 @@ def cpm_forces(ctx: Context, n_rep, offsets, xyzq, dpsi, q, f_elyt=None, f_elec=
     s = _lib.cpm_forces(ctx.handle, n_rep, p_off, p_x, p_d, _dev(q, torch.float64, "q", n_rep * ne),
                         _dev(f_elyt, torch.float64, "f_elyt", None, True),
                         _dev(f_elec, torch.float64, "f_elec", n_rep * ne * 3, True),
-                        _dev(energy, torch.float64, "energy", 2 * n_rep, True), _stream_ptr(stream))
+                        _dev(energy, torch.float64, "energy", 4 * n_rep, True), _stream_ptr(stream))
     _check(s, "cpm_forces")
 
 
@@ -198,7 +198,7 @@ def cpm_energy(ctx: Context, n_rep, offsets, xyzq, dpsi, q, energy, stream=None)
     import torch
     p_off, p_x, p_d = _common(ctx, n_rep, offsets, xyzq, dpsi)
     s = _lib.cpm_energy(ctx.handle, n_rep, p_off, p_x, p_d, _dev(q, torch.float64, "q", n_rep * ctx.n_elec),
-                        _dev(energy, torch.float64, "energy", 2 * n_rep), _stream_ptr(stream))
+                        _dev(energy, torch.float64, "energy", 4 * n_rep), _stream_ptr(stream))
     _check(s, "cpm_energy")
 
 
@@ -211,7 +211,7 @@ def cpm_step(ctx: Context, n_rep, offsets, xyzq, dpsi, q, psibar=None, f_elyt=No
                       _dev(psibar, torch.float64, "psibar", n_rep * ctx.ncons, True),
                       _dev(f_elyt, torch.float64, "f_elyt", None, True),
                       _dev(f_elec, torch.float64, "f_elec", n_rep * ne * 3, True),
-                      _dev(energy, torch.float64, "energy", 2 * n_rep, True), _stream_ptr(stream))
+                      _dev(energy, torch.float64, "energy", 4 * n_rep, True), _stream_ptr(stream))
     _check(s, "cpm_step")
 
 

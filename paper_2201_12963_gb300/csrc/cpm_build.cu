@@ -295,7 +295,7 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
 
   // ---------------- electrode host data ----------------
   std::vector<double4_32a> pos(ne);
-  std::vector<double> zraw(ne), v(ne), c1(ne, 0.0);
+  std::vector<double> zraw(ne), v(ne), c1(ne, 0.0), eplus(ne, 0.0);
   for (int i = 0; i < ne; ++i) {
     pos[i] = make_double4_32a(wrap_coord(xyz[3 * i], c->ebox[0]), wrap_coord(xyz[3 * i + 1], c->ebox[1]),
                           wrap_coord(xyz[3 * i + 2], c->ebox[2]), 0.0);
@@ -303,6 +303,7 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
     const double d = 0.5 * side[i];
     v[i] = (p.geometry == CPM_FF) ? d - zraw[i] / c->Lz : d;
     if (p.geometry == CPM_DOUBLED) c1[i] = cell[i] == 1 ? 1.0 : 0.0;
+    eplus[i] = side[i] > 0 ? 1.0 : 0.0;
   }
   // cell sort (stable by index)
   std::vector<int> flat(ne), count(c->ncell + 1, 0);
@@ -367,6 +368,7 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
   CPM_TRY(upload(&c->e_z, zraw, st));
   CPM_TRY(upload(&c->e_v, v, st));
   CPM_TRY(upload(&c->e_c1, c1, st));
+  CPM_TRY(upload(&c->e_plus, eplus, st));
 
   // ---------------- A in float64 ----------------
   c->ld64 = (ne + 3) & ~3;
@@ -572,9 +574,9 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
   if (!c) return;
   cpm_profile_enable(c, 0);
   void* bufs[] = {c->e_pos64, c->e_loc64, c->e_loc32, c->e_cellc, c->e_sorted, c->e_start, c->e_base,
-                  c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->S64, c->S32,
+                  c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->e_plus, c->S64, c->S32,
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
-                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->phi_real, c->b_tmp,
+                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->phi_real, c->b_tmp, c->b32,
                   c->scal, c->status};
   for (void* b : bufs)
     if (b) cudaFree(b);

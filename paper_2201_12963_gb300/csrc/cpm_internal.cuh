@@ -36,8 +36,11 @@ enum Slot {
   S_CQ1 = 10,      // e_1^T q_raw
   S_WB0 = 11,      // (A^-1 e)^T b
   S_WB1 = 12,      // (A^-1 e_1)^T b
-  S_SPARE = 13
+  S_E_RECIP_L = 13,// 1/2 sum_m G |rho_elyt^(m)|^2 (eV), electrolyte charges alone
+  S_QB = 14,       // q^T b (after the projection)
+  S_QPLUS = 15     // sum of q over side +1 sites
 };
+constexpr int NENERGY = 4;                  // per-replica energy outputs: U, H, dH/d(dpsi), Q_+
 
 // Status bits latched by kernels (first error wins).
 enum DevErr { DE_NONFINITE = 1, DE_DOMAIN = 2, DE_TIMEOUT = 4, DE_CAPACITY = 8 };
@@ -74,6 +77,7 @@ struct cpm_ctx {
   double* e_z = nullptr;        // [ne] z as given
   double* e_v = nullptr;        // [ne] geometry vector v
   double* e_c1 = nullptr;       // [ne] e_1 indicator (doubled cell) or zeros
+  double* e_plus = nullptr;     // [ne] 1 on side +1 sites, else 0
   // matrices
   int ld64 = 0, ld32 = 0;
   double* S64 = nullptr;        // [ne][ld64] row-major projected inverse
@@ -107,6 +111,7 @@ struct cpm_ctx {
   // per-replica buffers
   double* phi_real = nullptr;   // [max_rep][ne]
   double* b_tmp = nullptr;      // [max_rep][ne]
+  float* b32 = nullptr;         // [max_rep][2][ld32] float32 high / low split of b (mixed S-apply)
   double* scal = nullptr;       // [max_rep][NSCAL]
   int* status = nullptr;        // device status word
   // per-phase event profiler

@@ -374,14 +374,14 @@ __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_elec(const double* __restrict__ q, int ne, const int4* __restrict__ base,
                                                      const T* __restrict__ th, SpmeGeom sg, const double* __restrict__ ez,
-                                                     const double* __restrict__ ev, T* __restrict__ mesh,
-                                                     double* __restrict__ scal) {
+                                                     const double* __restrict__ ev, const double* __restrict__ eplus,
+                                                     T* __restrict__ mesh, double* __restrict__ scal) {
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const double* qr = q + (size_t)rep * ne;
-  double acc[3] = {0, 0, 0};
+  double acc[4] = {0, 0, 0, 0};
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const double qi = qr[i];
     const int4 b = base[i];
@@ -399,18 +399,20 @@ __global__ void __launch_bounds__(256) k_spread_elec(const double* __restrict__ 
       acc[0] += qi * ez[i];
       acc[1] += qi * ev[i];
       acc[2] += qi * qi;
+      acc[3] += qi * eplus[i];
     }
   }
-  double* const dst[3] = {scal + rep * NSCAL + S_QZ_ELEC, scal + rep * NSCAL + S_QV_ELEC,
-                          scal + rep * NSCAL + S_QQ_ELEC};
-  block_atomic_add<3>(acc, dst);
+  double* const dst[4] = {scal + rep * NSCAL + S_QZ_ELEC, scal + rep * NSCAL + S_QV_ELEC,
+                          scal + rep * NSCAL + S_QQ_ELEC, scal + rep * NSCAL + S_QPLUS};
+  block_atomic_add<4>(acc, dst);
 }
 
 // rho^(m) *= G(m) on the half spectrum; optionally E_recip += 1/2 sum_m G |rho^(m)|^2 (full spectrum).
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const T* __restrict__ G, long long Mc,
-                                                   long long Mc_s, int K3h, int K3, int energy,
+                                                   long long Mc_s, int K3h, int K3, int energy_slot,
                                                    double* __restrict__ scal) {
+  const bool energy = energy_slot >= 0;
   const int rep = blockIdx.y;
   T2* c = spec + (size_t)rep * Mc_s;
   double e = 0.0;
@@ -429,18 +431,21 @@ __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const 
   if (energy) {
     e = warp_sum(e);
     double acc[1] = {e};
-    double* const dst[1] = {scal + rep * NSCAL + S_E_RECIP};
+    double* const dst[1] = {scal + rep * NSCAL + energy_slot};
     block_atomic_add<1>(acc, dst);
   }
 }
 
 // b_i = -(KE phi_real_i + phi_mesh_i) (- KE 4 pi / V z_i sum_j Q_j Z_j for the slab), one warp per site.
+// With b32 != nullptr also the float32 split b = hi + lo (hi = fl(b), lo = fl(b - hi)) for the
+// mixed-precision S-apply, rows of stride ld32.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int ne, const int4* __restrict__ base,
                                                   const T* __restrict__ th, SpmeGeom sg,
                                                   const double* __restrict__ phi_real, const double* __restrict__ ez,
                                                   double slab_coef, const double* __restrict__ scal,
-                                                  double* __restrict__ b) {
+                                                  double* __restrict__ b, float* __restrict__ b32, int ld32,
+                                                  int ldb) {
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
@@ -463,7 +468,13 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
     const double pk = warp_sum((double)acc);
     if (lane == 0) {
       const size_t k = (size_t)rep * ne + i;
-      b[k] = -(KE * phi_real[k] + pk) - slab_coef * ez[i] * qz;
+      const double bi = -(KE * phi_real[k] + pk) - slab_coef * ez[i] * qz;
+      b[(size_t)rep * ldb + i] = bi;
+      if (b32) {
+        const float hi = (float)bi;
+        b32[(size_t)rep * 2 * ld32 + i] = hi;
+        b32[(size_t)rep * 2 * ld32 + ld32 + i] = (float)(bi - (double)hi);
+      }
     }
   }
 }
@@ -572,85 +583,39 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
 }
 
 // ------------------------------------------------------------------------------------------
-// S-apply: q_raw = S b + dpsi S v for R replicas per pass, one warp per row (rows grid-strided).
-// S is stored row-major in TS (float64, or float32 with compensated float32 lane sums and the
-// right-hand side split into float32 high and low parts).  The epilogue accumulates C^T q_raw
-// and (A^-1 C)^T b for the projection.
+// S-apply: q_raw = S b + dpsi S v for R replicas per pass, one warp per row (rows grid-strided),
+// S streamed once with 16-byte loads and four loads in flight per lane.
+//   float32 S (mixed): b enters as the float32 split hi + lo, each 4-element group is summed in
+//   float32 and the groups are added with Neumaier compensation; lanes combine in float64.
+//   float64 S: float64 FMAs.
+// The epilogue accumulates C^T q_raw and (A^-1 C)^T b for the projection.
 // ------------------------------------------------------------------------------------------
-template <typename TS, int R>
-__global__ void __launch_bounds__(256) k_sapply(const TS* __restrict__ S, int ld, int ne, const double* __restrict__ b,
-                                                int rep0, int nrep, const double* __restrict__ dpsi,
+template <int R>
+__device__ __forceinline__ void sapply_epilogue(int i, int lane, int rep0, int nrep, int ne, const double (&tot)[R],
+                                                const double* __restrict__ b, int ldb, const double* __restrict__ dpsi,
                                                 const double* __restrict__ Sv, const double* __restrict__ W,
                                                 const double* __restrict__ c1, double* __restrict__ qout,
-                                                double* __restrict__ scal) {
-  const int lane = threadIdx.x & 31;
-  double red[4 * R];
+                                                double (&red)[4 * R]) {
+  if (lane != 0) return;
+  const double w0 = W[2 * i], w1 = W[2 * i + 1], cc = c1[i], svi = Sv[i];
 #pragma unroll
-  for (int k = 0; k < 4 * R; ++k) red[k] = 0.0;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
-    const TS* row = S + (size_t)i * ld;
-    double tot[R];
-    if constexpr (sizeof(TS) == 4) {
-      CompSum<float> acc[R];
-      float acc_lo[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc_lo[r] = 0.f;
-      for (int j = 4 * lane; j < ne; j += 128) {
-        const float4 s4 = *reinterpret_cast<const float4*>(row + j);
-        const float sv[4] = {s4.x, s4.y, s4.z, s4.w};
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (rep0 + r >= nrep) break;
-          const double* br = b + (size_t)(rep0 + r) * ne;
-#pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            if (j + u < ne) {
-              const double y = br[j + u];
-              const float hi = (float)y;
-              const float lo = (float)(y - (double)hi);
-              acc[r].add(sv[u] * hi);
-              acc_lo[r] += sv[u] * lo;
-            }
-          }
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r].value() + (double)acc_lo[r]);
-    } else {
-      double acc[R];
-#pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = 0.0;
-      for (int j = 2 * lane; j < ne; j += 64) {
-        const double2 s2 = *reinterpret_cast<const double2*>(row + j);
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          if (rep0 + r >= nrep) break;
-          const double* br = b + (size_t)(rep0 + r) * ne;
-          acc[r] = fma(s2.x, br[j], acc[r]);
-          if (j + 1 < ne) acc[r] = fma(s2.y, br[j + 1], acc[r]);
-        }
-      }
-#pragma unroll
-      for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r]);
-    }
-    if (lane == 0) {
-      const double w0 = W[2 * i], w1 = W[2 * i + 1], cc = c1[i], svi = Sv[i];
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int rr = rep0 + r;
-        if (rr >= nrep) break;
-        const double qr = tot[r] + dpsi[rr] * svi;
-        qout[(size_t)rr * ne + i] = qr;
-        const double bi = b[(size_t)rr * ne + i];
-        red[4 * r + 0] += qr;
-        red[4 * r + 1] += qr * cc;
-        red[4 * r + 2] += w0 * bi;
-        red[4 * r + 3] += w1 * bi;
-      }
-    }
+  for (int r = 0; r < R; ++r) {
+    const int rr = rep0 + r;
+    if (rr >= nrep) break;
+    const double qr = tot[r] + dpsi[rr] * svi;
+    qout[(size_t)rr * ne + i] = qr;
+    const double bi = b[(size_t)rr * ldb + i];
+    red[4 * r + 0] += qr;
+    red[4 * r + 1] += qr * cc;
+    red[4 * r + 2] += w0 * bi;
+    red[4 * r + 3] += w1 * bi;
   }
+}
+
+template <int R>
+__device__ __forceinline__ void sapply_reduce(const double (&red)[4 * R], int rep0, int nrep, double* scal) {
   __shared__ double sred[4 * R][8];
-  const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if (lane == 0)
     for (int k = 0; k < 4 * R; ++k) sred[k][warp] = red[k];
   __syncthreads();
@@ -664,40 +629,141 @@ __global__ void __launch_bounds__(256) k_sapply(const TS* __restrict__ S, int ld
   }
 }
 
+template <int R>
+__global__ void __launch_bounds__(256) k_sapply32(const float* __restrict__ S, int ld, int ne,
+                                                  const float* __restrict__ b32, const double* __restrict__ b,
+                                                  int ldb, int rep0, int nrep, const double* __restrict__ dpsi,
+                                                  const double* __restrict__ Sv, const double* __restrict__ W,
+                                                  const double* __restrict__ c1, double* __restrict__ qout,
+                                                  double* __restrict__ scal) {
+  const int lane = threadIdx.x & 31;
+  const int n4 = ld >> 2;
+  double red[4 * R];
+#pragma unroll
+  for (int k = 0; k < 4 * R; ++k) red[k] = 0.0;
+  const float4* yh[R];
+  const float4* yl[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int rr = min(rep0 + r, nrep - 1);
+    yh[r] = reinterpret_cast<const float4*>(b32 + (size_t)rr * 2 * ld);
+    yl[r] = reinterpret_cast<const float4*>(b32 + (size_t)rr * 2 * ld + ld);
+  }
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+    const float4* row = reinterpret_cast<const float4*>(S + (size_t)i * ld);
+    CompSum<float> acc[R];
+    float lo[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) lo[r] = 0.f;
+#pragma unroll 4
+    for (int j = lane; j < n4; j += 32) {
+      const float4 sv = __ldcs(row + j);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const float4 h = yh[r][j], l = yl[r][j];
+        acc[r].add(sv.x * h.x + sv.y * h.y + sv.z * h.z + sv.w * h.w);
+        lo[r] += sv.x * l.x + sv.y * l.y + sv.z * l.z + sv.w * l.w;
+      }
+    }
+    double tot[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r].value() + (double)lo[r]);
+    sapply_epilogue<R>(i, lane, rep0, nrep, ne, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
+  }
+  sapply_reduce<R>(red, rep0, nrep, scal);
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_sapply64(const double* __restrict__ S, int ld, int ne,
+                                                  const double* __restrict__ b, int ldb, int rep0, int nrep,
+                                                  const double* __restrict__ dpsi, const double* __restrict__ Sv,
+                                                  const double* __restrict__ W, const double* __restrict__ c1,
+                                                  double* __restrict__ qout, double* __restrict__ scal) {
+  const int lane = threadIdx.x & 31;
+  double red[4 * R];
+#pragma unroll
+  for (int k = 0; k < 4 * R; ++k) red[k] = 0.0;
+  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+    // rows and b are padded to ld (a multiple of 4) with zeros, so whole double2 pairs are read
+    const double2* row = reinterpret_cast<const double2*>(S + (size_t)i * ld);
+    double acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = 0.0;
+    const int n2 = ld >> 1;
+#pragma unroll 4
+    for (int j = lane; j < n2; j += 32) {
+      const double2 sv = __ldcs(row + j);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int rr = min(rep0 + r, nrep - 1);
+        const double2 y = reinterpret_cast<const double2*>(b + (size_t)rr * ldb)[j];
+        acc[r] = fma(sv.x, y.x, fma(sv.y, y.y, acc[r]));
+      }
+    }
+    double tot[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r]);
+    sapply_epilogue<R>(i, lane, rep0, nrep, ne, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
+  }
+  sapply_reduce<R>(red, rep0, nrep, scal);
+}
+
 // q = q_raw - A^-1 C M C^T q_raw (restores C^T q = 0 to float64 rounding); psibar = -M (A^-1 C)^T (b + dpsi v).
-__global__ void k_project(double* __restrict__ q, int ne, int nrep, int ncons, const double* __restrict__ W,
-                          const double* __restrict__ scal, const double* __restrict__ dpsi, double m00, double m01,
-                          double m10, double m11, double wtv0, double wtv1, double* __restrict__ psibar) {
+// Also accumulates q^T b for the closed-form energy.
+__global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne, int nrep, int ncons,
+                                                 const double* __restrict__ W, const double* __restrict__ b, int ldb,
+                                                 double* __restrict__ scal, const double* __restrict__ dpsi,
+                                                 double m00, double m01, double m10, double m11, double wtv0,
+                                                 double wtv1, double* __restrict__ psibar) {
   const int rep = blockIdx.y;
-  const double* s = scal + rep * NSCAL;
+  double* s = scal + rep * NSCAL;
   const double c0 = s[S_CQ0], cq1 = (ncons == 2) ? s[S_CQ1] : 0.0;
   const double a0 = m00 * c0 + m01 * cq1, a1 = m10 * c0 + m11 * cq1;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double qb[1] = {0.0};
   if (i < ne) {
     double corr = W[2 * i] * a0;
     if (ncons == 2) corr += W[2 * i + 1] * a1;
-    q[(size_t)rep * ne + i] -= corr;
+    const size_t k = (size_t)rep * ne + i;
+    const double qi = q[k] - corr;
+    q[k] = qi;
+    qb[0] = qi * b[(size_t)rep * ldb + i];
   }
   if (i == 0 && psibar) {
     const double y0 = s[S_WB0] + dpsi[rep] * wtv0, y1 = (ncons == 2) ? s[S_WB1] + dpsi[rep] * wtv1 : 0.0;
     psibar[rep * ncons + 0] = -(m00 * y0 + m01 * y1);
     if (ncons == 2) psibar[rep * ncons + 1] = -(m10 * y0 + m11 * y1);
   }
+  qb[0] = warp_sum(qb[0]);
+  double* const dst[1] = {s + S_QB};
+  block_atomic_add<1>(qb, dst);
 }
 
+// Per replica (U, H, dH/d(dpsi), Q_+).  closed_form: at the constrained optimum Eq. 3 reduces to
+// U = U_elyt - 1/2 q^T b + 1/2 dpsi q^T v (A q = b + dpsi v + C lam and C^T q = 0); otherwise U is the
+// full Ewald sum of all charges (real space + mesh + self terms).
 __global__ void k_energy_final(int nrep, const double* __restrict__ scal, const double* __restrict__ dpsi,
-                               double alpha, double eta, double slab_e_coef, double ff_over_lz,
+                               double alpha, double eta, double slab_e_coef, double ff_over_lz, int closed_form,
                                double* __restrict__ energy) {
   const int rep = blockIdx.x * blockDim.x + threadIdx.x;
   if (rep >= nrep) return;
   const double* s = scal + rep * NSCAL;
-  double U = KE * (0.5 * s[S_E_LL] + s[S_E_LE] + 0.5 * s[S_E_EE]) + s[S_E_RECIP] +
-             KE * (-(alpha / sqrt(PI)) * (s[S_QQ_ELYT] + s[S_QQ_ELEC]) + eta / sqrt(2.0 * PI) * s[S_QQ_ELEC]);
-  const double mz = s[S_QZ_ELYT] + s[S_QZ_ELEC];
-  U += slab_e_coef * mz * mz;
-  const double H = U - dpsi[rep] * s[S_QV_ELEC] + dpsi[rep] * ff_over_lz * s[S_QZ_ELYT];
-  energy[2 * rep] = U;
-  energy[2 * rep + 1] = H;
+  const double self_pt = alpha / sqrt(PI);
+  double U;
+  if (closed_form) {
+    U = KE * (0.5 * s[S_E_LL] - self_pt * s[S_QQ_ELYT]) + s[S_E_RECIP_L] +
+        slab_e_coef * s[S_QZ_ELYT] * s[S_QZ_ELYT] - 0.5 * s[S_QB] + 0.5 * dpsi[rep] * s[S_QV_ELEC];
+  } else {
+    U = KE * (0.5 * s[S_E_LL] + s[S_E_LE] + 0.5 * s[S_E_EE]) + s[S_E_RECIP] +
+        KE * (-self_pt * (s[S_QQ_ELYT] + s[S_QQ_ELEC]) + eta / sqrt(2.0 * PI) * s[S_QQ_ELEC]);
+    const double mz = s[S_QZ_ELYT] + s[S_QZ_ELEC];
+    U += slab_e_coef * mz * mz;
+  }
+  const double dHdpsi = -s[S_QV_ELEC] + ff_over_lz * s[S_QZ_ELYT];
+  energy[NENERGY * rep + 0] = U;
+  energy[NENERGY * rep + 1] = U + dpsi[rep] * dHdpsi;
+  energy[NENERGY * rep + 2] = dHdpsi;
+  energy[NENERGY * rep + 3] = s[S_QPLUS];
 }
 
 // ------------------------------------------------------------------------------------------
@@ -779,7 +845,7 @@ template <> struct FftOps<double> {
 
 // mesh -> spectrum, influence (+ energy), spectrum -> potential mesh
 template <typename T>
-static int convolve(cpm_ctx* c, int nrep, bool energy, cudaStream_t st) {
+static int convolve(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st) {
   using C2 = typename FftOps<T>::C2;
   const int b = (nrep == c->p.max_replicas && c->have_plan[1]) ? 1 : 0;
   CPM_LIB(cufftSetStream(c->plan_r2c[b], st) == CUFFT_SUCCESS, "cufftSetStream");
@@ -793,7 +859,7 @@ static int convolve(cpm_ctx* c, int nrep, bool energy, cudaStream_t st) {
   const T* G = c->mixed ? (const T*)c->G32 : (const T*)c->G64;
   const int blocks = (int)std::min<long long>((c->Mc + 255) / 256, 152 * 8);
   k_influence<T, C2><<<dim3(blocks, nrep), 256, 0, st>>>(mc, G, c->Mc, c->Mc_s, c->K[2] / 2 + 1, c->K[2],
-                                                         energy ? 1 : 0, c->scal);
+                                                         energy_slot, c->scal);
   STEP_LAUNCH();
   for (int r = 0; r < nexec; ++r)
     CPM_LIB(FftOps<T>::inv(c->plan_c2r[b], mc + r * c->Mc_s, mp + r * c->Mr_s) == CUFFT_SUCCESS, "cufftExec(c2r)");
@@ -835,8 +901,12 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   PairSrc none{nullptr, 0, nullptr, 0, nullptr, nullptr, 0, 0.0, -1};
   const size_t mesh_bytes = sizeof(T) * (size_t)c->Mr_s * nrep;
 
+  // closed-form energy when the charges are solved in this call (cpm_step): U_elyt - q^T b / 2 + dpsi q^T v / 2
+  const bool closed_form = charges && energy != nullptr;
+
   if (charges) {
-    double* b = b_out ? b_out : c->b_tmp;
+    double* b = c->b_tmp;                 // aligned internal copy, row stride ld64
+    const int ldb = c->ld64;
     // real-space Gaussian-point part of b at the electrode sites
     PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, nullptr, nullptr, c->phi_real};
     PairSrc s = src_elyt;
@@ -855,32 +925,53 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     }
     {
       PhaseTimer pt(c, st, CPM_PH_B_FFT);
-      CPM_TRY(convolve<T>(c, nrep, false, st));
+      CPM_TRY(convolve<T>(c, nrep, closed_form ? S_E_RECIP_L : -1, st));
     }
     {
       PhaseTimer pt(c, st, CPM_PH_B_GATHER);
       k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
-                                                              c->phi_real, c->e_z, slab_coef, c->scal, b);
+                                                              c->phi_real, c->e_z, slab_coef, c->scal, b,
+                                                              c->mixed ? c->b32 : nullptr, c->ld32, ldb);
       STEP_LAUNCH();
+      if (b_out) {
+        CPM_CUDA(cudaMemcpy2DAsync(b_out, sizeof(double) * ne, b, sizeof(double) * ldb, sizeof(double) * ne, nrep,
+                                   cudaMemcpyDeviceToDevice, st));
+      }
     }
     // q = S b + dpsi S v, then the projection
     const int sblocks = std::min(grid_for(ne), 152 * 4);
     {
-    PhaseTimer pt(c, st, CPM_PH_S_APPLY);
-    for (int r0 = 0; r0 < nrep; r0 += 4) {
-      if (c->mixed)
-        k_sapply<float, 4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, b, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
-                                                    q, c->scal);
-      else
-        k_sapply<double, 4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
-                                                     q, c->scal);
-      STEP_LAUNCH();
-    }
+      PhaseTimer pt(c, st, CPM_PH_S_APPLY);
+      for (int r0 = 0; r0 < nrep; r0 += 4) {
+        const int left = nrep - r0;
+        if (c->mixed) {
+          if (left == 1)
+            k_sapply32<1><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
+                                                   c->e_c1, q, c->scal);
+          else if (left == 2)
+            k_sapply32<2><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
+                                                   c->e_c1, q, c->scal);
+          else
+            k_sapply32<4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
+                                                   c->e_c1, q, c->scal);
+        } else {
+          if (left == 1)
+            k_sapply64<1><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
+                                                   q, c->scal);
+          else if (left == 2)
+            k_sapply64<2><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
+                                                   q, c->scal);
+          else
+            k_sapply64<4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
+                                                   q, c->scal);
+        }
+        STEP_LAUNCH();
+      }
     }
     PhaseTimer ptp(c, st, CPM_PH_PROJECT);
-    k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, c->scal, dpsi, c->Mh[0],
-                                                            c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0], c->WTv[1],
-                                                            psibar);
+    k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
+                                                            c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
+                                                            c->WTv[1], psibar);
     STEP_LAUNCH();
   }
 
@@ -892,12 +983,12 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
       STEP_LAUNCH();
       k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(q, ne, c->e_base, e_th, sg, c->e_z, c->e_v,
-                                                                 (T*)c->mesh_r, c->scal);
+                                                                 c->e_plus, (T*)c->mesh_r, c->scal);
       STEP_LAUNCH();
     }
     {
       PhaseTimer pt(c, st, CPM_PH_F_FFT);
-      CPM_TRY(convolve<T>(c, nrep, energy != nullptr, st));
+      CPM_TRY(convolve<T>(c, nrep, (energy && !closed_form) ? S_E_RECIP : -1, st));
     }
     PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
     if (f_elyt) {
@@ -928,13 +1019,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         k_pair<T, false><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
       STEP_LAUNCH();
     }
-    // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian
-    if (f_elec || energy) {
+    // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian (energy)
+    if (f_elec || (energy && !closed_form)) {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
       PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, q, f_elec, nullptr};
       PairSrc a = f_elec ? src_elyt : none;
       a.beta = c->p.eta;
-      PairSrc e = src_elec;
+      PairSrc e = (energy && !closed_form) ? src_elec : none;
       e.q = q;
       e.beta = c->p.eta / std::sqrt(2.0);
       e.slot = S_E_EE;
@@ -948,7 +1039,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PhaseTimer pt(c, st, CPM_PH_ENERGY);
       const double slab_e = (c->p.geometry == CPM_SLAB) ? KE * 2.0 * PI / c->V : 0.0;
       k_energy_final<<<(nrep + 127) / 128, 128, 0, st>>>(nrep, c->scal, dpsi, c->p.alpha, c->p.eta, slab_e,
-                                                         ff_over_lz, energy);
+                                                         ff_over_lz, closed_form ? 1 : 0, energy);
       STEP_LAUNCH();
     }
   }
@@ -989,7 +1080,10 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
     CPM_CUDA(cudaMalloc(&c->l_loc64, sizeof(double4_32a) * R * cap));
   CPM_CUDA(cudaMalloc(&c->l_cellc, sizeof(int4) * R * cap));
   CPM_CUDA(cudaMalloc(&c->phi_real, sizeof(double) * R * ne));
-  CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * ne));
+  CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * c->ld64));
+  CPM_CUDA(cudaMemset(c->b_tmp, 0, sizeof(double) * R * c->ld64));
+  CPM_CUDA(cudaMalloc(&c->b32, sizeof(float) * R * 2 * c->ld32));
+  CPM_CUDA(cudaMemset(c->b32, 0, sizeof(float) * R * 2 * c->ld32));
   CPM_CUDA(cudaMalloc(&c->scal, sizeof(double) * R * cpm::NSCAL));
   CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
   CPM_CUDA(cudaMemset(c->status, 0, sizeof(int)));

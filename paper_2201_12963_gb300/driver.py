@@ -59,7 +59,7 @@ class System:
         self.psibar = torch.zeros(self.n_rep * self.ctx.ncons, **f64)
         self.f_elyt = torch.zeros(max(1, n) * 3, **f64)
         self.f_elec = torch.zeros(self.n_rep * self.ne * 3, **f64)
-        self.energy = torch.zeros(2 * self.n_rep, **f64)
+        self.energy = torch.zeros(4 * self.n_rep, **f64)       # U, H, dH/d(dpsi), Q_+ per replica
 
     def charges(self):
         cpm_step_charges(self.ctx, self.n_rep, self.offsets, self.xyzq, self.dpsi, self.q, self.b, self.psibar)
@@ -84,4 +84,4 @@ class System:
                 "psibar": self.psibar.cpu().numpy().reshape(R, -1),
                 "F_elyt": [fl[off[r]:off[r + 1]] for r in range(R)],
                 "F_elec": self.f_elec.cpu().numpy().reshape(R, ne, 3),
-                "energy": self.energy.cpu().numpy().reshape(R, 2)}
+                "energy": self.energy.cpu().numpy().reshape(R, 4)}

@@ -45,9 +45,11 @@ def _check(res, ref, prec, r=0, tol=None):
     assert np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum()) <= t["f"]
     Fe, Feo = res["F_elec"][r], ref["F_elec"]
     assert np.sqrt(((Fe - Feo) ** 2).sum() / (Feo ** 2).sum()) <= 3 * t["f"]
-    U, H = res["energy"][r]
+    U, H, dH, Qp = res["energy"][r]
     assert abs(U - ref["U"]) <= t["e"] * abs(ref["U"])
     assert abs(H - ref["H"]) <= t["e"] * abs(ref["H"])
+    assert abs(Qp - ref["Q_plus"]) <= t["q"] * len(qo)
+    assert abs(dH - ref["dH_ddpsi"]) <= t["b"] * max(1.0, abs(ref["dH_ddpsi"]))
 
 
 def _run(w, prec, **kw):
@@ -119,21 +121,28 @@ def test_batched_ragged_replicas_match_per_replica_oracle():
 
 
 def test_fused_step_equals_separate_calls(plain_ff):
+    """cpm_step equals cpm_step_charges + cpm_forces; its closed-form energy (exact A) agrees with
+    the full Ewald sum of cpm_forces / cpm_energy (mesh for the electrode-electrode part) to the
+    mesh error, and both agree with the oracle."""
     g, System = _lib()
-    w, _, _ = plain_ff
-    a = System(w, "fp64")
+    w, _, out = plain_ff
+    a = System(w, "fp64", order=8)
     a.charges()
     a.forces(elec=False, energy=True)
     ra = a.results()
-    b = System(w, "fp64")
+    b = System(w, "fp64", order=8)
     b.step(elec=False, energy=True)
     rb = b.results()
     assert np.max(np.abs(ra["q"] - rb["q"])) <= 1e-14
-    assert np.max(np.abs(ra["energy"] - rb["energy"])) <= 1e-10
-    c = System(w, "fp64")
+    assert np.max(np.abs(ra["F_elyt"][0] - rb["F_elyt"][0])) <= 1e-12
+    for k in (0, 1):
+        assert abs(ra["energy"][0, k] - rb["energy"][0, k]) <= 1e-7 * abs(rb["energy"][0, k])
+        assert abs(rb["energy"][0, k] - (out["U"], out["H"])[k]) <= 1e-7 * abs(out["U"])
+    assert np.max(np.abs(ra["energy"][0, 2:] - rb["energy"][0, 2:])) <= 1e-12
+    c = System(w, "fp64", order=8)
     c.q.copy_(b.q)
     c.energies()
-    assert np.max(np.abs(c.results()["energy"] - rb["energy"])) <= 1e-10
+    assert np.max(np.abs(c.results()["energy"] - ra["energy"])) <= 1e-10 * abs(out["U"])
 
 
 def test_empty_electrolyte_gives_capacitor_charges():
@@ -162,8 +171,11 @@ def test_device_errors_are_latched():
     s.load(w)
     s.charges()
     assert g.cpm_status(s.ctx) == 0
+    off2 = torch.tensor([0, 2, 4], dtype=torch.int32, device=s.xyzq.device)
+    dp2 = torch.zeros(2, dtype=torch.float64, device=s.xyzq.device)
+    q2 = torch.zeros(2 * s.ne, dtype=torch.float64, device=s.xyzq.device)
     with pytest.raises(g.CPMError) as ei:
-        g.cpm_step_charges(s.ctx, 2, s.offsets, s.xyzq, s.dpsi, s.q)   # n_rep above capacity 1
+        g.cpm_step_charges(s.ctx, 2, off2, s.xyzq, dp2, q2)   # n_rep above capacity 1
     assert ei.value.status == -5
 
 
