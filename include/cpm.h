@@ -216,6 +216,33 @@ int cpm_profile_read(cpm_ctx* ctx, double* ms_host, int64_t* count_host);
  * without adding to it). */
 int cpm_counters(const cpm_ctx* ctx, int64_t* kernel_launches);
 
+/*
+ * cpm_step_charges_static - the charge update of cpm_step_charges for a single replica, for
+ * callers that must not allocate device memory while they run: code executing where cudaMalloc
+ * is unavailable or forbidden (inside another library's allocator-free region, real-time loops
+ * with a no-allocation policy, hosts whose memory pools are owned by someone else).  The paper
+ * has no counterpart; it is a deployment convenience.
+ *
+ * All per-call scratch (cell list, SPME meshes, b and its float32 split, reduction slots) lives
+ * in one file-scope __device__ array of CPM_STATIC_SCRATCH_BYTES bytes that every GPU loading the
+ * library holds until the process exits; this call never calls cudaMalloc, cudaFree or an
+ * allocating library routine.  The context (built earlier by cpm_build_matrix) supplies S, the
+ * stencils and the FFT plans.  Arguments are those of cpm_step_charges with n_rep = 1:
+ * elyt_offsets_dev [2], q_dev / b_dev [N_e], psibar_dev [ncons].
+ *
+ * - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
+ *   that device current); make that first call before any stream capture.
+ * - Returns CPM_ERR_CAPACITY (see cpm_last_error) when the context's mesh, electrolyte capacity
+ *   and electrode count need more scratch than CPM_STATIC_SCRATCH_BYTES.
+ * - Every call shares the one array and it keeps the previous call's contents (each call clears
+ *   what must start at zero): calls that overlap on the GPU — on different streams, or on
+ *   different contexts of the same device — race and corrupt each other.  Serialise them.
+ */
+#define CPM_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const double* elyt_xyzq_dev,
+                            const double* dpsi_dev, double* q_dev, double* b_dev, double* psibar_dev,
+                            void* stream);
+
 /* cpm_destroy - free the context and everything it owns (NULL is accepted). */
 void cpm_destroy(cpm_ctx* ctx);
 

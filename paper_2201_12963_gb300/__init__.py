@@ -21,7 +21,7 @@ PRECISION = {"fp64": CPM_FP64, "mixed": CPM_MIXED}
 
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
-            "cpm_destroy",
+            "cpm_step_charges_static", "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
 PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
           "f_gather", "f_pair_elyt", "f_pair_elec", "energy")
@@ -65,6 +65,7 @@ def _load():
     lib.cpm_profile_enable.argtypes = [vp, i32]
     lib.cpm_profile_read.argtypes = [vp, pd, pd]
     lib.cpm_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.cpm_step_charges_static.argtypes = [vp, pi32, pd, pd, pd, pd, pd, vp]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
     lib.cpm_strerror.argtypes = [ctypes.c_int]
@@ -213,6 +214,18 @@ def cpm_step(ctx: Context, n_rep, offsets, xyzq, dpsi, q, psibar=None, f_elyt=No
                       _dev(f_elec, torch.float64, "f_elec", n_rep * ne * 3, True),
                       _dev(energy, torch.float64, "energy", 4 * n_rep, True), _stream_ptr(stream))
     _check(s, "cpm_step")
+
+
+def cpm_step_charges_static(ctx: Context, offsets, xyzq, dpsi, q, b=None, psibar=None, stream=None):
+    """Single-replica charge update that allocates nothing (scratch in the library's static
+    device array); see cpm_step_charges_static in include/cpm.h."""
+    import torch
+    p_off, p_x, p_d = _common(ctx, 1, offsets, xyzq, dpsi)
+    ne = ctx.n_elec
+    s = _lib.cpm_step_charges_static(ctx.handle, p_off, p_x, p_d, _dev(q, torch.float64, "q", ne),
+                                     _dev(b, torch.float64, "b", ne, True),
+                                     _dev(psibar, torch.float64, "psibar", ctx.ncons, True), _stream_ptr(stream))
+    _check(s, "cpm_step_charges_static")
 
 
 def cpm_capacitance(ctx: Context) -> float:

@@ -10,6 +10,7 @@
 #include "cpm_internal.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace cpm {
 
@@ -1157,4 +1158,101 @@ extern "C" int cpm_counters(const cpm_ctx* c, int64_t* kernel_launches) {
   if (!c || !kernel_launches) return CPM_ERR_ARG;
   *kernel_launches = c->launches;
   return CPM_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// allocation-free single-replica charge update (cpm_step_charges_static)
+// ------------------------------------------------------------------------------------------
+// Scratch for cpm_step_charges_static, held by every device that loads the library.
+static __device__ __align__(256) unsigned char g_cpm_static_scratch[CPM_STATIC_SCRATCH_BYTES];
+
+namespace {
+std::mutex g_static_mu;
+constexpr int kMaxDevices = 64;
+void* g_static_addr[kMaxDevices] = {};   // device address of the array, per device ordinal
+}  // namespace
+
+// Host code cannot use the array's name as a device address; look it up once per device.
+static int static_scratch(void** out) {
+  int dev = 0;
+  CPM_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) {
+    cpm::set_error("device ordinal %d outside the supported range", dev);
+    return CPM_ERR_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_cpm_static_scratch);
+    if (e != cudaSuccess || !p) {
+      cpm::set_error("cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
+      return CPM_ERR_CUDA;
+    }
+    g_static_addr[dev] = p;
+  }
+  *out = g_static_addr[dev];
+  return CPM_OK;
+}
+
+extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const double* xyzq, const double* dpsi,
+                                       double* q, double* b, double* psibar, void* stream) {
+  if (!ctx || !off || !xyzq || !dpsi || !q) {
+    cpm::set_error("cpm_step_charges_static: null context or required pointer");
+    return CPM_ERR_ARG;
+  }
+  void* base_v = nullptr;
+  CPM_TRY(static_scratch(&base_v));
+  unsigned char* base = static_cast<unsigned char*>(base_v);
+  const size_t tsz = ctx->mixed ? sizeof(float) : sizeof(double);
+  const size_t v4 = ctx->mixed ? sizeof(float4) : sizeof(double4_32a);
+  const size_t cap = ctx->p.max_elyt, ncell = ctx->ncell;
+  const size_t sizes[] = {tsz * ctx->Mr_s,       tsz * ctx->Mr_s,          2 * tsz * ctx->Mc_s,
+                          sizeof(int) * cap,     sizeof(int) * ncell,      sizeof(int) * (ncell + 1),
+                          sizeof(int) * cap,     v4 * cap,                 sizeof(int4) * cap,
+                          sizeof(double) * ctx->ne, sizeof(double) * ctx->ld64, sizeof(float) * 2 * ctx->ld32,
+                          sizeof(double) * cpm::NSCAL};
+  constexpr int NREG = sizeof(sizes) / sizeof(sizes[0]);
+  size_t offs[NREG], total = 0;
+  for (int k = 0; k < NREG; ++k) {
+    offs[k] = total;
+    total += (sizes[k] + 255) & ~size_t(255);
+  }
+  if (total > CPM_STATIC_SCRATCH_BYTES) {
+    cpm::set_error("cpm_step_charges_static: this context needs %zu bytes of scratch, the static array holds %u",
+                   total, CPM_STATIC_SCRATCH_BYTES);
+    return CPM_ERR_CAPACITY;
+  }
+  // Shallow copy: S, stencils, plans and the status word are shared read-only; every per-call
+  // workspace points into the static array.  One replica, single-batch FFT plan, no profiling.
+  cpm_ctx t = *ctx;
+  t.p.max_replicas = 1;
+  t.have_plan[1] = false;
+  t.prof_cap = t.prof_used = 0;
+  t.prof_ev = nullptr;
+  t.prof_phase = nullptr;
+  t.mesh_r = base + offs[0];
+  t.mesh_phi = base + offs[1];
+  t.mesh_c = base + offs[2];
+  t.l_cell = reinterpret_cast<int*>(base + offs[3]);
+  t.l_count = reinterpret_cast<int*>(base + offs[4]);
+  t.l_start = reinterpret_cast<int*>(base + offs[5]);
+  t.l_sorted = reinterpret_cast<int*>(base + offs[6]);
+  t.l_loc32 = ctx->mixed ? reinterpret_cast<float4*>(base + offs[7]) : nullptr;
+  t.l_loc64 = ctx->mixed ? nullptr : reinterpret_cast<double4_32a*>(base + offs[7]);
+  t.l_cellc = reinterpret_cast<int4*>(base + offs[8]);
+  t.phi_real = reinterpret_cast<double*>(base + offs[9]);
+  t.b_tmp = reinterpret_cast<double*>(base + offs[10]);
+  t.b32 = reinterpret_cast<float*>(base + offs[11]);
+  t.scal = reinterpret_cast<double*>(base + offs[12]);
+  cudaStream_t st = (cudaStream_t)stream;
+  // The array keeps the previous call's contents: the S-apply reads the padding of b up to the
+  // row stride, so that must be zero.  (The counts, mesh and reduction slots are cleared by the
+  // step itself.)
+  CPM_CUDA(cudaMemsetAsync(t.b_tmp, 0, sizes[10], st));
+  CPM_CUDA(cudaMemsetAsync(t.b32, 0, sizes[11], st));
+  const int s = ctx->mixed
+                    ? cpm::run<float>(&t, 1, off, xyzq, dpsi, true, q, b, psibar, nullptr, nullptr, nullptr, st)
+                    : cpm::run<double>(&t, 1, off, xyzq, dpsi, true, q, b, psibar, nullptr, nullptr, nullptr, st);
+  ctx->launches = t.launches;
+  return s;
 }
