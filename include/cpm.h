@@ -31,8 +31,8 @@
  *   - Errors a kernel detects (non-finite coordinates, a site outside the cell in z) are latched
  *     in a device status word and returned by cpm_status().
  *   - Electrolyte input is replica-major: replica r owns sites offsets[r] .. offsets[r+1]-1 of
- *     xyzq (x, y, z, Q per site, float64).  x, y may be unwrapped; z must lie in [0, L_z).  Each
- *     replica's electrolyte must be electrically neutral.
+ *     xyzq (x, y, z, Q per site, float64, base address 32-byte aligned).  x, y may be unwrapped;
+ *     z must lie in [0, L_z).  Each replica's electrolyte must be electrically neutral.
  */
 #ifndef CPM_GB300_H
 #define CPM_GB300_H

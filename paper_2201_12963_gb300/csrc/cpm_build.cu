@@ -292,6 +292,10 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
     c->sten[d] = (int)std::ceil(p.rcut / c->edge[d] - 1e-12);
     c->ncell *= c->nc[d];
   }
+  if ((2 * c->sten[0] + 1) * (2 * c->sten[1] + 1) * (2 * c->sten[2] + 1) > kMaxStencil) {
+    set_error("the cell is too small for rcut: the neighbour stencil exceeds %d cells", kMaxStencil);
+    return CPM_ERR_ARG;
+  }
 
   // ---------------- electrode host data ----------------
   std::vector<double4_32a> pos(ne);
@@ -530,6 +534,24 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
 
   // ---------------- SPME ----------------
   {
+    // mesh coordinate of every cell origin, split into an integer and a fraction per axis, so the
+    // per-step kernels only add the (small) cell-local offset in the working precision
+    std::vector<int> sI;
+    std::vector<double> sF;
+    std::vector<float> sF32;
+    for (int d = 0; d < 3; ++d)
+      for (int cidx = 0; cidx < c->nc[d]; ++cidx) {
+        const double u0 = (double)cidx * c->K[d] / c->nc[d];
+        const double fl = std::floor(u0);
+        sI.push_back((int)fl);
+        sF.push_back(u0 - fl);
+        sF32.push_back((float)(u0 - fl));
+      }
+    CPM_TRY(upload(&c->spl_I, sI, st));
+    CPM_TRY(upload(&c->spl_F64, sF, st));
+    CPM_TRY(upload(&c->spl_F32, sF32, st));
+  }
+  {
     std::vector<double> G;
     influence_host(c, G);
     CPM_TRY(upload(&c->G64, G, st));
@@ -576,7 +598,8 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
   void* bufs[] = {c->e_pos64, c->e_loc64, c->e_loc32, c->e_cellc, c->e_sorted, c->e_start, c->e_base,
                   c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->e_plus, c->S64, c->S32,
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
-                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->phi_real, c->b_tmp, c->b32,
+                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->l_tmp, c->qT, c->spl_I,
+                  c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32,
                   c->scal, c->status};
   for (void* b : bufs)
     if (b) cudaFree(b);

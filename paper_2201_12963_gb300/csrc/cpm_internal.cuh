@@ -20,6 +20,7 @@ constexpr double KE = 14.3996454784;        // e^2 / (4 pi eps0), eV A
 constexpr double PI = 3.14159265358979323846;
 constexpr int PMAX = 8;                     // largest supported B-spline order
 constexpr int NSCAL = 16;                   // per-replica float64 scalar slots
+constexpr int kMaxStencil = 512;            // neighbour-cell stencil entries of the pair kernel
 
 // Per-replica scalar slots (float64 accumulators, zeroed at the start of every call).
 enum Slot {
@@ -108,6 +109,12 @@ struct cpm_ctx {
   double4_32a* l_loc64 = nullptr;   // [max_rep][max_elyt] cell-local coordinates + Q
   float4* l_loc32 = nullptr;
   int4* l_cellc = nullptr;      // [max_rep][max_elyt]
+  void* l_tmp = nullptr;        // [max_rep][max_elyt] unsorted cell-local coordinates + Q (working precision)
+  void* qT = nullptr;           // [max_rep][ne] electrode charges in the working precision
+  // B-spline coordinate of each cell origin along each axis: c K_d / nc_d = spl_I + spl_F
+  int* spl_I = nullptr;         // [nc0 + nc1 + nc2]
+  double* spl_F64 = nullptr;
+  float* spl_F32 = nullptr;
   // per-replica buffers
   double* phi_real = nullptr;   // [max_rep][ne]
   double* b_tmp = nullptr;      // [max_rep][ne]

@@ -6,6 +6,12 @@
 //             then q = S (b + dpsi v) and the neutrality projection (Eqs. 8-9 / 13-15)
 //   forces    SPME of all charges + real-space pair forces, finite-field / slab terms, energies
 //
+// Precision.  T = float is the mixed path.  GB300 issues float64 arithmetic at a small fraction of
+// the float32 rate, so in the float kernels every per-lane sum is a compensated float32 sum
+// (Knuth TwoSum), warp reductions combine (sum, error) pairs in float32, and float64 appears only
+// in once-per-warp or once-per-site epilogues, in the input conversion and in the float64
+// projection.  T = double is the plain float64 path: the same kernels with float64 throughout.
+//
 // Every launch goes to the caller's stream; nothing here allocates or synchronises the host.
 #include "cpm_internal.cuh"
 
@@ -22,7 +28,9 @@ struct CellGeom {
   int sten[3];
   int nsten;
   double edge[3];
+  double inv_edge[3];
   double box[3];
+  double inv_box[3];
   double rc2;
 };
 
@@ -30,15 +38,51 @@ struct SpmeGeom {
   int K[3];
   int P;
   double box[3];
+  double kl[3];          // K_d / L_d
   long long Mr_s, Mc_s;
+  int spl_off[3];        // axis offsets into the cell-origin tables
 };
 
-__device__ __forceinline__ double wrap_d(double x, double L) {
-  double y = x - L * floor(x / L);
+__device__ __forceinline__ double wrap_d(double x, double L, double invL) {
+  double y = fma(-L, floor(x * invL), x);
   if (y >= L) y -= L;
   if (y < 0) y = 0;
   return y;
 }
+
+// ------------------------------------------------------------------------------------------
+// accumulators: compensated float32 (TwoSum) for T = float, plain float64 for T = double
+// ------------------------------------------------------------------------------------------
+template <typename T> struct Acc;
+
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void warp_reduce() { s = warp_sum(s); }
+  __device__ __forceinline__ double value() const { return s; }
+};
+
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      add(s2);
+      c += c2;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) { return warp_sum(v); }
 
 // block-wide sum of up to NV doubles held by lane 0 of every warp; thread 0 adds into dst[k].
 template <int NV>
@@ -60,9 +104,14 @@ __device__ __forceinline__ void block_atomic_add(double (&v)[NV], double* const 
 // ------------------------------------------------------------------------------------------
 // prepare: counting sort of the electrolyte into cells
 // ------------------------------------------------------------------------------------------
-__global__ void k_bin(const int* __restrict__ off, const double* __restrict__ xyzq, int cap, CellGeom g,
-                      double lz_phys, int* __restrict__ l_cell, int* __restrict__ l_count, int ncell,
-                      double* __restrict__ scal, int* __restrict__ status) {
+// Per site: wrap into the box, cell index, cell-local coordinates (float64 arithmetic, stored in
+// the working precision) and the electrolyte dipole / charge-square sums.
+template <typename T>
+__global__ void __launch_bounds__(256) k_bin(const int* __restrict__ off, const double* __restrict__ xyzq, int cap,
+                                             CellGeom g, double lz_phys, int* __restrict__ l_cell,
+                                             int* __restrict__ l_count, typename Vec4<T>::type* __restrict__ l_tmp,
+                                             int ncell, double* __restrict__ scal, int* __restrict__ status) {
+  using V4 = typename Vec4<T>::type;
   const int rep = blockIdx.y;
   const int o = off[rep];
   const int n_all = off[rep + 1] - o;
@@ -71,22 +120,28 @@ __global__ void k_bin(const int* __restrict__ off, const double* __restrict__ xy
   if (i == 0 && (n_all > cap || n_all < 0)) latch_error(status, DE_CAPACITY);
   double acc[2] = {0.0, 0.0};
   if (i < n) {
-    const double* s = xyzq + 4 * (size_t)(o + i);
-    double x = s[0], y = s[1], z = s[2], q = s[3];
+    const double4_32a s = reinterpret_cast<const double4_32a*>(xyzq)[o + i];
+    double x = s.x, y = s.y, z = s.z, q = s.w;
     if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q))) {
       latch_error(status, DE_NONFINITE);
-      x = y = z = 0.0;
-      q = 0.0;
+      x = y = z = q = 0.0;
     } else if (!(z >= 0.0 && z < lz_phys)) {
       latch_error(status, DE_DOMAIN);
     }
-    const double r[3] = {wrap_d(x, g.box[0]), wrap_d(y, g.box[1]), wrap_d(z, g.box[2])};
+    const double r[3] = {wrap_d(x, g.box[0], g.inv_box[0]), wrap_d(y, g.box[1], g.inv_box[1]),
+                         wrap_d(z, g.box[2], g.inv_box[2])};
     int ci[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) ci[d] = min(g.nc[d] - 1, max(0, (int)(r[d] / g.edge[d])));
+    for (int d = 0; d < 3; ++d) ci[d] = min(g.nc[d] - 1, max(0, (int)(r[d] * g.inv_edge[d])));
     const int flat = (ci[0] * g.nc[1] + ci[1]) * g.nc[2] + ci[2];
     l_cell[(size_t)rep * cap + i] = flat;
     atomicAdd(&l_count[(size_t)rep * ncell + flat], 1);
+    V4 v;
+    v.x = (T)fma(-(double)ci[0], g.edge[0], r[0]);
+    v.y = (T)fma(-(double)ci[1], g.edge[1], r[1]);
+    v.z = (T)fma(-(double)ci[2], g.edge[2], r[2]);
+    v.w = (T)q;
+    l_tmp[(size_t)rep * cap + i] = v;
     acc[0] = q * z;
     acc[1] = q * q;
   }
@@ -126,286 +181,359 @@ __global__ void k_scan(int* __restrict__ l_count, int* __restrict__ l_start, int
 }
 
 template <typename T>
-__global__ void k_scatter(const int* __restrict__ off, const double* __restrict__ xyzq, int cap, CellGeom g,
-                          const int* __restrict__ l_cell, int* __restrict__ cursor, int ncell,
-                          int* __restrict__ l_sorted, typename Vec4<T>::type* __restrict__ l_loc,
-                          int4* __restrict__ l_cellc) {
-  using V4 = typename Vec4<T>::type;
+__global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ off, int cap, CellGeom g,
+                                                 const int* __restrict__ l_cell,
+                                                 const typename Vec4<T>::type* __restrict__ l_tmp,
+                                                 int* __restrict__ cursor, int ncell, int* __restrict__ l_sorted,
+                                                 typename Vec4<T>::type* __restrict__ l_loc,
+                                                 int4* __restrict__ l_cellc) {
   const int rep = blockIdx.y;
-  const int o = off[rep];
-  const int n = min(off[rep + 1] - o, cap);
+  const int n = min(off[rep + 1] - off[rep], cap);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double* s = xyzq + 4 * (size_t)(o + i);
-  double x = s[0], y = s[1], z = s[2], q = s[3];
-  if (!(isfinite(x) && isfinite(y) && isfinite(z) && isfinite(q))) x = y = z = q = 0.0;
-  const double r[3] = {wrap_d(x, g.box[0]), wrap_d(y, g.box[1]), wrap_d(z, g.box[2])};
-  int ci[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) ci[d] = min(g.nc[d] - 1, max(0, (int)(r[d] / g.edge[d])));
-  const int flat = l_cell[(size_t)rep * cap + i];
+  const size_t src = (size_t)rep * cap + i;
+  const int flat = l_cell[src];
   const int pos = atomicAdd(&cursor[(size_t)rep * ncell + flat], 1);
   const size_t k = (size_t)rep * cap + pos;
   l_sorted[k] = i;
-  V4 v;
-  v.x = (T)(r[0] - ci[0] * g.edge[0]);
-  v.y = (T)(r[1] - ci[1] * g.edge[1]);
-  v.z = (T)(r[2] - ci[2] * g.edge[2]);
-  v.w = (T)q;
-  l_loc[k] = v;
-  l_cellc[k] = make_int4(ci[0], ci[1], ci[2], flat);
+  l_loc[k] = l_tmp[src];
+  const int cz = flat % g.nc[2], cy = (flat / g.nc[2]) % g.nc[1], cx = flat / (g.nc[2] * g.nc[1]);
+  l_cellc[k] = make_int4(cx, cy, cz, flat);
+}
+
+// Electrode charges in the working precision plus their float64 sums q z, q v, q^2, q_+.
+template <typename T>
+__global__ void __launch_bounds__(256) k_charge_prep(const double* __restrict__ q, int ne,
+                                                     const double* __restrict__ ez, const double* __restrict__ ev,
+                                                     const double* __restrict__ eplus, T* __restrict__ qT,
+                                                     double* __restrict__ scal) {
+  const int rep = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[4] = {0, 0, 0, 0};
+  if (i < ne) {
+    const double qi = q[(size_t)rep * ne + i];
+    qT[(size_t)rep * ne + i] = (T)qi;
+    acc[0] = qi * ez[i];
+    acc[1] = qi * ev[i];
+    acc[2] = qi * qi;
+    acc[3] = qi * eplus[i];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) acc[k] = warp_sum(acc[k]);
+  double* const dst[4] = {scal + rep * NSCAL + S_QZ_ELEC, scal + rep * NSCAL + S_QV_ELEC,
+                          scal + rep * NSCAL + S_QQ_ELEC, scal + rep * NSCAL + S_QPLUS};
+  block_atomic_add<4>(acc, dst);
 }
 
 // ------------------------------------------------------------------------------------------
-// real-space pair sums over cell-list neighbours, one warp per target site
+// real-space pair sums: one block per target cell.  The block gathers the sources of every
+// neighbour cell that can hold a point within r_c of the target cell into shared memory (image
+// shift folded into the staged coordinates, charges attached), then each warp sweeps a share of
+// the staged sources for one target.  Kernel per pair at distance r:
+//   (erfc(alpha r) - erfc(beta r)) / r,  beta = 0 meaning a point source,
+// and the force on the target  c_t c_s [kernel + 2/sqrt(pi)(alpha e^{-alpha^2 r^2} - beta e^{-beta^2 r^2})] d / r^2.
 // ------------------------------------------------------------------------------------------
 struct PairSrc {
-  const void* loc;          // cell-sorted cell-local coordinates (w = charge when q == nullptr)
+  const void* loc;          // cell-sorted cell-local coordinates (w = charge unless qT != nullptr)
   long long loc_stride;     // per-replica stride (0 = shared by all replicas)
   const int* start;         // [ncell + 1] cell starts
   long long start_stride;
   const int* sorted;        // sorted -> original index (electrode charge lookup)
-  const double* q;          // electrode charges [rep][q_stride] or nullptr
+  const void* qT;           // electrode charges [rep][q_stride] in the working precision, or nullptr
   int q_stride;
   double beta;              // second screening width: 0 = point source, else Gaussian kernel
   int slot;                 // energy slot receiving sum_t c_t phi_t, or -1
 };
 
-struct PairTgt {
-  const void* loc;
-  long long loc_stride;
-  const int4* cellc;
-  const int* sorted;
-  const int* off;           // electrolyte targets: replica offsets; nullptr for electrodes
-  int cap;                  // electrolyte capacity per replica
-  int n_fixed;              // electrode count
-  const double* q;          // electrode target charges [rep][n_fixed] or nullptr (charge in loc.w)
-  double* force;            // += KE * c_t * sum ..., [global index][3], or nullptr
-  double* phi_out;          // potential from source set 0, [rep][n_fixed] original order, or nullptr
+struct CellPairTgt {
+  const void* loc;          // cell-sorted cell-local coordinates (w = charge unless qT != nullptr)
+  long long loc_stride;     // per replica (0: shared)
+  const int* start;         // [ncell + 1] target cell starts
+  long long start_stride;
+  const int* sorted;        // sorted -> original index
+  const int* off;           // electrolyte: replica offsets (global force index); nullptr for electrodes
+  int n_fixed;              // electrode count (force / phi index stride)
+  const void* qT;           // electrode target charges [rep][n_fixed] in the working precision, or nullptr
+  double* force;            // += KE c_t sum_s c_s g(r) d, [global index][3] or nullptr
+  double* phi_out;          // sum over set 0 of c_s kernel(r), [rep][n_fixed] original order, or nullptr
 };
 
-// Kernel per pair at distance r: (erfc(alpha r) - erfc(beta r)) / r, beta = 0 meaning a point;
-// the force on the target is c_t c_s [kernel + 2/sqrt(pi)(alpha e^{-alpha^2 r^2} - beta e^{-beta^2 r^2})] d / r^2.
+constexpr int PC_MAXT = 64;        // targets per pass of a block
+constexpr int kPairSrcCap = 2048;  // sources staged per pass (dynamic shared memory)
+constexpr int PC_MAXSTEN = kMaxStencil;
+constexpr int PC_THREADS = 256;
+
 template <typename T, bool FORCE>
-__global__ void __launch_bounds__(256) k_pair(const PairTgt t, const PairSrc s0, const PairSrc s1,
-                                              const CellGeom g, const double alpha_d, double* __restrict__ scal) {
+__global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
+                                                          const CellGeom g, const double alpha_d, int src_cap,
+                                                          double* __restrict__ scal) {
   using V4 = typename Vec4<T>::type;
-  const T alpha = (T)alpha_d;
-  const T c2pi = (T)1.1283791670955126;   // 2 / sqrt(pi)
+  extern __shared__ __align__(32) unsigned char pc_dyn[];
+  V4* src = reinterpret_cast<V4*>(pc_dyn);
+  __shared__ V4 tpos[PC_MAXT];
+  __shared__ double tphi[2][PC_MAXT];
+  __shared__ double tf[3][PC_MAXT];
+  __shared__ int st_first[PC_MAXSTEN];
+  __shared__ int st_pre[PC_MAXSTEN + 1];
+  __shared__ short st_d[3][PC_MAXSTEN];
+
   const int rep = blockIdx.y;
-  const int lane = threadIdx.x & 31;
-  const int nt = t.off ? min(t.off[rep + 1] - t.off[rep], t.cap) : t.n_fixed;
-  const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
+  const int cell = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int* tst = t.start + rep * t.start_stride;
+  const int t0 = tst[cell], t1 = tst[cell + 1];
+  if (t1 <= t0) return;                                    // whole block: empty cell
+  const T alpha = (T)alpha_d;
+  const T c2pi = (T)1.1283791670955126;
   const T rc2 = (T)g.rc2;
-  double eacc[2] = {0.0, 0.0};
+  const int cz = cell % g.nc[2], cy = (cell / g.nc[2]) % g.nc[1], cx = cell / (g.nc[2] * g.nc[1]);
+  const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
   const V4* tl = (const V4*)t.loc + rep * t.loc_stride;
-  const int4* tcc = t.cellc + rep * t.loc_stride;
   const int* tso = t.sorted + rep * t.loc_stride;
-  for (int ti = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ti < nt; ti += (gridDim.x * blockDim.x) >> 5) {
-    const V4 tp = tl[ti];
-    const int4 tc = tcc[ti];
-    const int orig = tso[ti];
-    const T tq = t.q ? (T)t.q[(size_t)rep * t.n_fixed + orig] : tp.w;
-    CompSum<T> ph[2];
-    T fx = 0, fy = 0, fz = 0;
-#pragma unroll
+  const T* tq = t.qT ? (const T*)t.qT + (size_t)rep * t.n_fixed : nullptr;
+  double eacc[2] = {0.0, 0.0};
+
+  for (int tb = t0; tb < t1; tb += PC_MAXT) {
+    const int nt = min(PC_MAXT, t1 - tb);
+    for (int k = tid; k < nt; k += PC_THREADS) {
+      V4 p = tl[tb + k];
+      if (tq) p.w = tq[tso[tb + k]];
+      tpos[k] = p;
+      tphi[0][k] = tphi[1][k] = 0.0;
+      tf[0][k] = tf[1][k] = tf[2][k] = 0.0;
+    }
     for (int set = 0; set < 2; ++set) {
       const PairSrc& s = set ? s1 : s0;
       if (!s.loc) continue;
       const V4* sl = (const V4*)s.loc + rep * s.loc_stride;
-      const int* st = s.start + rep * s.start_stride;
-      const double* sq_arr = s.q ? s.q + (size_t)rep * s.q_stride : nullptr;
+      const int* sst = s.start + rep * s.start_stride;
+      const T* sq = s.qT ? (const T*)s.qT + (size_t)rep * s.q_stride : nullptr;
       const bool gauss = s.beta > 0.0;
       const T beta = (T)s.beta;
-      for (int sb = 0; sb < g.nsten; sb += 32) {
-        const int si = sb + lane;
-        int cnt = 0, first = 0;
-        T ox = 0, oy = 0, oz = 0;
-        if (si < g.nsten) {
-          const int dx = si % g.w[0] - g.sten[0];
-          const int r1 = si / g.w[0];
-          const int dy = r1 % g.w[1] - g.sten[1];
-          const int dz = r1 / g.w[1] - g.sten[2];
-          const T mx = fmax(T(0), fmax(dx * e0 - tp.x, tp.x - (dx + 1) * e0));
-          const T my = fmax(T(0), fmax(dy * e1 - tp.y, tp.y - (dy + 1) * e1));
-          const T mz = fmax(T(0), fmax(dz * e2 - tp.z, tp.z - (dz + 1) * e2));
-          if (mx * mx + my * my + mz * mz < rc2) {
-            const int cx = wrap_index(tc.x + dx, g.nc[0]);
-            const int cy = wrap_index(tc.y + dy, g.nc[1]);
-            const int cz = wrap_index(tc.z + dz, g.nc[2]);
-            const int flat = (cx * g.nc[1] + cy) * g.nc[2] + cz;
-            first = st[flat];
-            cnt = st[flat + 1] - first;
-            ox = dx * e0;
-            oy = dy * e1;
-            oz = dz * e2;
-          }
+      __syncthreads();
+      // ---- stencil cells whose box can hold a source within r_c of some point of this cell
+      for (int si = tid; si < g.nsten; si += PC_THREADS) {
+        const int dx = si % g.w[0] - g.sten[0];
+        const int r1 = si / g.w[0];
+        const int dy = r1 % g.w[1] - g.sten[1];
+        const int dz = r1 / g.w[1] - g.sten[2];
+        const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)max(0, abs(dz) - 1) * e2;
+        int c = 0, f = 0;
+        if (gx * gx + gy * gy + gz * gz < rc2) {
+          const int flat = (wrap_index(cx + dx, g.nc[0]) * g.nc[1] + wrap_index(cy + dy, g.nc[1])) * g.nc[2] +
+                           wrap_index(cz + dz, g.nc[2]);
+          f = sst[flat];
+          c = sst[flat + 1] - f;
         }
-        int incl = cnt;
+        st_first[si] = f;
+        st_pre[si + 1] = c;                 // counts, scanned below
+        st_d[0][si] = (short)dx;
+        st_d[1][si] = (short)dy;
+        st_d[2][si] = (short)dz;
+      }
+      __syncthreads();
+      // ---- inclusive scan of the counts (one warp, nsten <= PC_MAXSTEN)
+      if (warp == 0) {
+        int run = 0;
+        for (int b = 0; b < g.nsten; b += 32) {
+          const int k = b + lane;
+          int v = k < g.nsten ? st_pre[k + 1] : 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int v = __shfl_up_sync(FULL, incl, o);
-          if (lane >= o) incl += v;
-        }
-        const int total = __shfl_sync(FULL, incl, 31);
-        const int excl = incl - cnt;
-        const int basek = first - excl;
-        for (int jb = 0; jb < total; jb += 32) {
-          const int j = jb + lane;
-          int lo = 0;
-#pragma unroll
-          for (int step = 16; step > 0; step >>= 1) {
-            const int e = __shfl_sync(FULL, excl, lo + step);
-            if (e <= j) lo += step;
+          for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(FULL, v, o);
+            if (lane >= o) v += u;
           }
-          const int k = __shfl_sync(FULL, basek, lo) + j;
-          const T sx = __shfl_sync(FULL, ox, lo);
-          const T sy = __shfl_sync(FULL, oy, lo);
-          const T sz = __shfl_sync(FULL, oz, lo);
-          if (j < total) {
-            const V4 sp = sl[k];
-            const T dx = tp.x - sp.x - sx, dy = tp.y - sp.y - sy, dz = tp.z - sp.z - sz;
+          if (k < g.nsten) st_pre[k + 1] = run + v;
+          run += __shfl_sync(FULL, v, 31);
+        }
+        if (lane == 0) st_pre[0] = 0;
+      }
+      __syncthreads();
+      const int total = st_pre[g.nsten];
+      for (int c0 = 0; c0 < total; c0 += src_cap) {
+        const int ns = min(src_cap, total - c0);
+        // ---- stage: k -> stencil entry by binary search over the prefix sums
+        for (int k = tid; k < ns; k += PC_THREADS) {
+          const int j = c0 + k;
+          int lo = 0, hi = g.nsten;            // st_pre[lo] <= j < st_pre[hi]
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (st_pre[mid] <= j) lo = mid; else hi = mid;
+          }
+          const int gi = st_first[lo] + (j - st_pre[lo]);
+          V4 p = sl[gi];
+          p.x += (T)st_d[0][lo] * e0;
+          p.y += (T)st_d[1][lo] * e1;
+          p.z += (T)st_d[2][lo] * e2;
+          if (sq) p.w = sq[s.sorted[gi]];
+          src[k] = p;
+        }
+        __syncthreads();
+        // ---- compute: work item = (target, part); a warp sweeps 1/P of the staged sources for
+        // one target with per-lane running sums (compensated for the potential) and reduces once
+        const int P = max(1, (PC_THREADS / 32) / nt);
+        for (int item = warp; item < nt * P; item += PC_THREADS / 32) {
+          const int ti = item / P, part = item - ti * P;
+          const V4 tp = tpos[ti];
+          Acc<T> pot;
+          T fx = 0, fy = 0, fz = 0;
+          for (int k = part * 32 + lane; k < ns; k += 32 * P) {
+            const V4 sp = src[k];
+            const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
             const T r2 = dx * dx + dy * dy + dz * dz;
             if (r2 < rc2 && r2 > T(0)) {
-              const T qs = sq_arr ? (T)sq_arr[s.sorted[k]] : sp.w;
-              const T r = sqrt(r2);
-              const T ir = T(1) / r;
+              const T r = sqrt(r2), ir = T(1) / r;
               T num = erfc(alpha * r);
-              if (gauss) num -= erfc(beta * r);
-              const T pot = num * ir;
-              ph[set].add(qs * pot);
+              T gxp = FORCE ? alpha * exp(-alpha * alpha * r2) : T(0);
+              if (gauss && beta * r < T(6.5)) {          // erfc(6.5) < 4e-20: below every float64 term
+                num -= erfc(beta * r);
+                if (FORCE) gxp -= beta * exp(-beta * beta * r2);
+              }
+              const T pr = num * ir;
+              pot.add(sp.w * pr);
               if (FORCE) {
-                T gx = alpha * exp(-alpha * alpha * r2);
-                if (gauss) gx -= beta * exp(-beta * beta * r2);
-                const T fr = qs * (pot + c2pi * gx) * ir * ir;
+                const T fr = sp.w * (pr + c2pi * gxp) * ir * ir;
                 fx += fr * dx;
                 fy += fr * dy;
                 fz += fr * dz;
               }
             }
           }
+          pot.warp_reduce();
+          if (FORCE) {
+            fx = warp_sum_t(fx);
+            fy = warp_sum_t(fy);
+            fz = warp_sum_t(fz);
+          }
+          if (lane == 0) {
+            const double wp = pot.value();
+            if (P == 1) {
+              tphi[set][ti] += wp;
+              if (FORCE) {
+                tf[0][ti] += (double)fx;
+                tf[1][ti] += (double)fy;
+                tf[2][ti] += (double)fz;
+              }
+            } else {
+              atomicAdd(&tphi[set][ti], wp);
+              if (FORCE) {
+                atomicAdd(&tf[0][ti], (double)fx);
+                atomicAdd(&tf[1][ti], (double)fy);
+                atomicAdd(&tf[2][ti], (double)fz);
+              }
+            }
+          }
         }
+        __syncthreads();
       }
     }
-    const double p0 = warp_sum(ph[0].value());
-    const double p1 = warp_sum(ph[1].value());
-    double Fx = 0, Fy = 0, Fz = 0;
-    if (FORCE) {
-      Fx = warp_sum((double)fx);
-      Fy = warp_sum((double)fy);
-      Fz = warp_sum((double)fz);
-    }
-    if (lane == 0) {
-      if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = p0;
-      eacc[0] += (double)tq * p0;
-      eacc[1] += (double)tq * p1;
+    __syncthreads();
+    // ---- outputs for this batch of targets (float64, one thread per target)
+    for (int k = tid; k < nt; k += PC_THREADS) {
+      const int orig = tso[tb + k];
+      const double qt = (double)tpos[k].w;
+      if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = tphi[0][k];
+      eacc[0] += qt * tphi[0][k];
+      eacc[1] += qt * tphi[1][k];
       if (FORCE && t.force) {
         const size_t gi = t.off ? (size_t)t.off[rep] + orig : (size_t)rep * t.n_fixed + orig;
-        const double f = KE * (double)tq;
-        t.force[3 * gi + 0] += f * Fx;
-        t.force[3 * gi + 1] += f * Fy;
-        t.force[3 * gi + 2] += f * Fz;
+        const double f = KE * qt;
+        t.force[3 * gi + 0] += f * tf[0][k];
+        t.force[3 * gi + 1] += f * tf[1][k];
+        t.force[3 * gi + 2] += f * tf[2][k];
       }
     }
+    __syncthreads();
   }
   double* const dst[2] = {s0.slot >= 0 ? scal + rep * NSCAL + s0.slot : nullptr,
                           s1.slot >= 0 ? scal + rep * NSCAL + s1.slot : nullptr};
+  eacc[0] = warp_sum(eacc[0]);
+  eacc[1] = warp_sum(eacc[1]);
   block_atomic_add<2>(eacc, dst);
 }
 
 // ------------------------------------------------------------------------------------------
 // SPME: charge assignment, influence function, interpolation (cardinal B-splines of order P)
 // ------------------------------------------------------------------------------------------
-// B-spline weights of one site into per-warp shared memory: lanes 0-2 handle axes x, y, z.
+// B-spline weights of one cell-sorted electrolyte site into per-warp shared memory (lanes 0-2
+// handle axes x, y, z).  Its mesh coordinate u = (cell origin) + (local offset) K/L uses the
+// per-cell integer / fraction tables, so only the small local part is formed in precision T.
 template <typename T>
-__device__ __forceinline__ void site_weights(const double r[3], const SpmeGeom& sg, int lane, T (*w)[PMAX],
-                                             T (*dw)[PMAX], int* i0) {
+__device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, const int4& cc, const SpmeGeom& sg,
+                                             const int* __restrict__ splI, const T* __restrict__ splF, int lane,
+                                             T (*w)[PMAX], T (*dw)[PMAX], int* i0) {
   if (lane < 3) {
-    const double u = wrap_d(r[lane], sg.box[lane]) / sg.box[lane] * sg.K[lane];
-    const double fl = floor(u);
+    const T loc = lane == 0 ? p.x : (lane == 1 ? p.y : p.z);
+    const int c = lane == 0 ? cc.x : (lane == 1 ? cc.y : cc.z);
+    const int ti = sg.spl_off[lane] + c;
+    const T u = splF[ti] + loc * (T)sg.kl[lane];
+    const T fl = floor(u);
     T wl[PMAX], dl[PMAX];
-    bspline<T>((T)(u - fl), sg.P, wl, dl);
+    bspline<T>(u - fl, sg.P, wl, dl);
 #pragma unroll
     for (int t = 0; t < PMAX; ++t) {
       w[lane][t] = wl[t];
       dw[lane][t] = dl[t];
     }
-    i0[lane] = (int)fl;
+    i0[lane] = splI[ti] + (int)fl;
   }
   __syncwarp();
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, const double* __restrict__ xyzq,
-                                                     int cap, SpmeGeom sg, T* __restrict__ mesh) {
+__global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, int cap, SpmeGeom sg,
+                                                     const typename Vec4<T>::type* __restrict__ l_loc,
+                                                     const int4* __restrict__ l_cellc, const int* __restrict__ splI,
+                                                     const T* __restrict__ splF, T* __restrict__ mesh) {
   __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
   __shared__ int si0[8][3];
   const int rep = blockIdx.y;
-  const int o = off[rep];
-  const int n = min(off[rep + 1] - o, cap);
+  const int n = min(off[rep + 1] - off[rep], cap);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int iters = (n + nw - 1) / nw;   // uniform trip count keeps the warps of a block in step
-  for (int it = 0; it < iters; ++it) {
-    const int i = first + it * nw;
-    if (i < n) {
-      const double* s = xyzq + 4 * (size_t)(o + i);
-      double r[3] = {s[0], s[1], s[2]};
-      double q = s[3];
-      if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(q))) r[0] = r[1] = r[2] = q = 0.0;
-      site_weights<T>(r, sg, lane, sw[wib], sdw[wib], si0[wib]);
-      for (int task = lane; task < P * P; task += 32) {
-        const int ty = task / P, tz = task - ty * P;
-        const int gy = wrap_index(si0[wib][1] - ty, K2), gz = wrap_index(si0[wib][2] - tz, K3);
-        const T wyz = (T)q * sw[wib][1][ty] * sw[wib][2][tz];
-        for (int tx = 0; tx < P; ++tx) {
-          const int gx = wrap_index(si0[wib][0] - tx, K1);
-          atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], sw[wib][0][tx] * wyz);
-        }
+  for (int i = first; i < n; i += nw) {
+    const size_t k = (size_t)rep * cap + i;
+    const auto p = l_loc[k];
+    site_weights<T>(p, l_cellc[k], sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
+    for (int task = lane; task < P * P; task += 32) {
+      const int ty = task / P, tz = task - ty * P;
+      const int gy = wrap_index(si0[wib][1] - ty, K2), gz = wrap_index(si0[wib][2] - tz, K3);
+      const T wyz = p.w * sw[wib][1][ty] * sw[wib][2][tz];
+      for (int tx = 0; tx < P; ++tx) {
+        const int gx = wrap_index(si0[wib][0] - tx, K1);
+        atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], sw[wib][0][tx] * wyz);
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
 }
 
-// Electrode charges onto the mesh through the fixed stencils; also sums q z, q v and q^2.
+// Electrode charges onto the mesh through the fixed stencils.
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_elec(const double* __restrict__ q, int ne, const int4* __restrict__ base,
-                                                     const T* __restrict__ th, SpmeGeom sg, const double* __restrict__ ez,
-                                                     const double* __restrict__ ev, const double* __restrict__ eplus,
-                                                     T* __restrict__ mesh, double* __restrict__ scal) {
+__global__ void __launch_bounds__(256) k_spread_elec(const T* __restrict__ qT, int ne, const int4* __restrict__ base,
+                                                     const T* __restrict__ th, SpmeGeom sg, T* __restrict__ mesh) {
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   T* m = mesh + (size_t)rep * sg.Mr_s;
-  const double* qr = q + (size_t)rep * ne;
-  double acc[4] = {0, 0, 0, 0};
+  const T* qr = qT + (size_t)rep * ne;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
-    const double qi = qr[i];
+    const T qi = qr[i];
     const int4 b = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
     for (int task = lane; task < P * P; task += 32) {
       const int ty = task / P, tz = task - ty * P;
       const int gy = wrap_index(b.y - ty, K2), gz = wrap_index(b.z - tz, K3);
-      const T wyz = (T)qi * w[PMAX + ty] * w[2 * PMAX + tz];
+      const T wyz = qi * w[PMAX + ty] * w[2 * PMAX + tz];
       for (int tx = 0; tx < P; ++tx) {
         const int gx = wrap_index(b.x - tx, K1);
         atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], w[tx] * wyz);
       }
     }
-    if (lane == 0) {
-      acc[0] += qi * ez[i];
-      acc[1] += qi * ev[i];
-      acc[2] += qi * qi;
-      acc[3] += qi * eplus[i];
-    }
   }
-  double* const dst[4] = {scal + rep * NSCAL + S_QZ_ELEC, scal + rep * NSCAL + S_QV_ELEC,
-                          scal + rep * NSCAL + S_QQ_ELEC, scal + rep * NSCAL + S_QPLUS};
-  block_atomic_add<4>(acc, dst);
 }
 
 // rho^(m) *= G(m) on the half spectrum; optionally E_recip += 1/2 sum_m G |rho^(m)|^2 (full spectrum).
@@ -416,30 +544,30 @@ __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const 
   const bool energy = energy_slot >= 0;
   const int rep = blockIdx.y;
   T2* c = spec + (size_t)rep * Mc_s;
-  double e = 0.0;
+  Acc<T> e;
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Mc; k += (long long)gridDim.x * blockDim.x) {
     T2 v = c[k];
     const T g = G[k];
     if (energy) {
       const int n3 = (int)(k % K3h);
-      const double wgt = (n3 == 0 || 2 * n3 == K3) ? 0.5 : 1.0;
-      e += wgt * (double)g * ((double)v.x * v.x + (double)v.y * v.y);
+      const T wgt = (n3 == 0 || 2 * n3 == K3) ? T(0.5) : T(1);
+      e.add(wgt * g * (v.x * v.x + v.y * v.y));
     }
     v.x *= g;
     v.y *= g;
     c[k] = v;
   }
   if (energy) {
-    e = warp_sum(e);
-    double acc[1] = {e};
+    e.warp_reduce();
+    double acc[1] = {e.value()};
     double* const dst[1] = {scal + rep * NSCAL + energy_slot};
     block_atomic_add<1>(acc, dst);
   }
 }
 
-// b_i = -(KE phi_real_i + phi_mesh_i) (- KE 4 pi / V z_i sum_j Q_j Z_j for the slab), one warp per site.
-// With b32 != nullptr also the float32 split b = hi + lo (hi = fl(b), lo = fl(b - hi)) for the
-// mixed-precision S-apply, rows of stride ld32.
+// b_i = -(KE phi_real_i + phi_mesh_i) (- KE 4 pi / V z_i sum_j Q_j Z_j for the slab), one warp per site,
+// written to b (row stride ldb); with b32 != nullptr also the float32 split b = hi + lo
+// (hi = fl(b), lo = fl(b - hi)) for the mixed-precision S-apply, rows of stride ld32.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int ne, const int4* __restrict__ base,
                                                   const T* __restrict__ th, SpmeGeom sg,
@@ -451,11 +579,10 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const T* m = phi + (size_t)rep * sg.Mr_s;
-  const double qz = scal[rep * NSCAL + S_QZ_ELYT];
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const int4 bs = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
-    T acc = 0;
+    Acc<T> acc;
     for (int task = lane; task < P * P; task += 32) {
       const int ty = task / P, tz = task - ty * P;
       const int gy = wrap_index(bs.y - ty, K2), gz = wrap_index(bs.z - tz, K3);
@@ -464,12 +591,12 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
         const int gx = wrap_index(bs.x - tx, K1);
         s += w[tx] * m[((size_t)gx * K2 + gy) * K3 + gz];
       }
-      acc += s * w[PMAX + ty] * w[2 * PMAX + tz];
+      acc.add(s * w[PMAX + ty] * w[2 * PMAX + tz]);
     }
-    const double pk = warp_sum((double)acc);
+    acc.warp_reduce();
     if (lane == 0) {
       const size_t k = (size_t)rep * ne + i;
-      const double bi = -(KE * phi_real[k] + pk) - slab_coef * ez[i] * qz;
+      const double bi = -(KE * phi_real[k] + acc.value()) - slab_coef * ez[i] * scal[rep * NSCAL + S_QZ_ELYT];
       b[(size_t)rep * ldb + i] = bi;
       if (b32) {
         const float hi = (float)bi;
@@ -480,13 +607,17 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
   }
 }
 
-// k-space force on electrolyte sites: F = -Q grad(phi_mesh) - field terms (written, not added).
+// k-space force on the (cell-sorted) electrolyte sites: F = -Q grad(phi_mesh) + Q E_z z-hat, written
+// (not added) at the original index.  E_z = -dpsi / L_z (finite field) - KE 4 pi / V M_z (slab).
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi, const int* __restrict__ off,
-                                                       const double* __restrict__ xyzq, int cap, SpmeGeom sg,
-                                                       const double* __restrict__ dpsi, double ff_over_lz,
-                                                       double slab_coef, const double* __restrict__ scal,
-                                                       double* __restrict__ F) {
+                                                       int cap, SpmeGeom sg,
+                                                       const typename Vec4<T>::type* __restrict__ l_loc,
+                                                       const int4* __restrict__ l_cellc,
+                                                       const int* __restrict__ l_sorted, const int* __restrict__ splI,
+                                                       const T* __restrict__ splF, const double* __restrict__ dpsi,
+                                                       double ff_over_lz, double slab_coef,
+                                                       const double* __restrict__ scal, double* __restrict__ F) {
   __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
   __shared__ int si0[8][3];
   const int rep = blockIdx.y;
@@ -495,51 +626,47 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const T* m = phi + (size_t)rep * sg.Mr_s;
-  const double sx = sg.K[0] / sg.box[0], sy = sg.K[1] / sg.box[1], sz = sg.K[2] / sg.box[2];
-  const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
-  const double ez = -dpsi[rep] * ff_over_lz - slab_coef * mz;   // field per unit charge along z
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int iters = (n + nw - 1) / nw;
-  for (int it = 0; it < iters; ++it) {
-    const int i = first + it * nw;
-    if (i < n) {
-      const double* s = xyzq + 4 * (size_t)(o + i);
-      double r[3] = {s[0], s[1], s[2]};
-      double q = s[3];
-      if (!(isfinite(r[0]) && isfinite(r[1]) && isfinite(r[2]) && isfinite(q))) r[0] = r[1] = r[2] = q = 0.0;
-      site_weights<T>(r, sg, lane, sw[wib], sdw[wib], si0[wib]);
-      T gx = 0, gy = 0, gz = 0;
-      for (int task = lane; task < P * P; task += 32) {
-        const int ty = task / P, tz = task - ty * P;
-        const int jy = wrap_index(si0[wib][1] - ty, K2), jz = wrap_index(si0[wib][2] - tz, K3);
-        T a = 0, ad = 0;
-        for (int tx = 0; tx < P; ++tx) {
-          const int jx = wrap_index(si0[wib][0] - tx, K1);
-          const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
-          a += sw[wib][0][tx] * ph;
-          ad += sdw[wib][0][tx] * ph;
-        }
-        const T wy = sw[wib][1][ty], wz = sw[wib][2][tz];
-        gx += ad * wy * wz;
-        gy += a * sdw[wib][1][ty] * wz;
-        gz += a * wy * sdw[wib][2][tz];
+  for (int i = first; i < n; i += nw) {
+    const size_t k = (size_t)rep * cap + i;
+    const auto p = l_loc[k];
+    site_weights<T>(p, l_cellc[k], sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
+    T gx = 0, gy = 0, gz = 0;
+    for (int task = lane; task < P * P; task += 32) {
+      const int ty = task / P, tz = task - ty * P;
+      const int jy = wrap_index(si0[wib][1] - ty, K2), jz = wrap_index(si0[wib][2] - tz, K3);
+      T a = 0, ad = 0;
+      for (int tx = 0; tx < P; ++tx) {
+        const int jx = wrap_index(si0[wib][0] - tx, K1);
+        const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
+        a += sw[wib][0][tx] * ph;
+        ad += sdw[wib][0][tx] * ph;
       }
-      const double Gx = warp_sum((double)gx), Gy = warp_sum((double)gy), Gz = warp_sum((double)gz);
-      if (lane == 0) {
-        const size_t k = 3 * (size_t)(o + i);
-        F[k + 0] = -q * Gx * sx;
-        F[k + 1] = -q * Gy * sy;
-        F[k + 2] = -q * Gz * sz + q * ez;
-      }
-      __syncwarp();
+      const T wy = sw[wib][1][ty], wz = sw[wib][2][tz];
+      gx += ad * wy * wz;
+      gy += a * sdw[wib][1][ty] * wz;
+      gz += a * wy * sdw[wib][2][tz];
     }
+    gx = warp_sum_t(gx);
+    gy = warp_sum_t(gy);
+    gz = warp_sum_t(gz);
+    if (lane == 0) {
+      const double q = (double)p.w;
+      const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
+      const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
+      const size_t gi = 3 * (size_t)(o + l_sorted[k]);
+      F[gi + 0] = -q * (double)gx * sg.kl[0];
+      F[gi + 1] = -q * (double)gy * sg.kl[1];
+      F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf;
+    }
+    __syncwarp();
   }
 }
 
 // k-space force on electrode sites through the fixed stencils (written, not added).
 template <typename T>
-__global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi, const double* __restrict__ q,
+__global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi, const T* __restrict__ qT,
                                                        int ne, const int4* __restrict__ base,
                                                        const T* __restrict__ th, const T* __restrict__ dth,
                                                        SpmeGeom sg, const double* __restrict__ dpsi,
@@ -549,9 +676,6 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const T* m = phi + (size_t)rep * sg.Mr_s;
-  const double sx = sg.K[0] / sg.box[0], sy = sg.K[1] / sg.box[1], sz = sg.K[2] / sg.box[2];
-  const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
-  const double ez = -dpsi[rep] * ff_over_lz - slab_coef * mz;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const int4 bs = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
@@ -572,22 +696,26 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
       gy += a * dw[PMAX + ty] * wz;
       gz += a * wy * dw[2 * PMAX + tz];
     }
-    const double Gx = warp_sum((double)gx), Gy = warp_sum((double)gy), Gz = warp_sum((double)gz);
+    gx = warp_sum_t(gx);
+    gy = warp_sum_t(gy);
+    gz = warp_sum_t(gz);
     if (lane == 0) {
-      const double qi = q[(size_t)rep * ne + i];
+      const double qi = (double)qT[(size_t)rep * ne + i];
+      const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
+      const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
       const size_t k = 3 * ((size_t)rep * ne + i);
-      F[k + 0] = -qi * Gx * sx;
-      F[k + 1] = -qi * Gy * sy;
-      F[k + 2] = -qi * Gz * sz + qi * ez;
+      F[k + 0] = -qi * (double)gx * sg.kl[0];
+      F[k + 1] = -qi * (double)gy * sg.kl[1];
+      F[k + 2] = -qi * (double)gz * sg.kl[2] + qi * ezf;
     }
   }
 }
 
 // ------------------------------------------------------------------------------------------
 // S-apply: q_raw = S b + dpsi S v for R replicas per pass, one warp per row (rows grid-strided),
-// S streamed once with 16-byte loads and four loads in flight per lane.
+// S streamed once with 16-byte loads, several loads in flight per lane.
 //   float32 S (mixed): b enters as the float32 split hi + lo, each 4-element group is summed in
-//   float32 and the groups are added with Neumaier compensation; lanes combine in float64.
+//   float32 and the groups are added with TwoSum compensation, lanes combine (sum, error) pairs.
 //   float64 S: float64 FMAs.
 // The epilogue accumulates C^T q_raw and (A^-1 C)^T b for the projection.
 // ------------------------------------------------------------------------------------------
@@ -652,23 +780,36 @@ __global__ void __launch_bounds__(256) k_sapply32(const float* __restrict__ S, i
   }
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const float4* row = reinterpret_cast<const float4*>(S + (size_t)i * ld);
-    CompSum<float> acc[R];
+    Acc<float> acc[R];
     float lo[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) lo[r] = 0.f;
-#pragma unroll 4
-    for (int j = lane; j < n4; j += 32) {
-      const float4 sv = __ldcs(row + j);
+    constexpr int U = (R >= 4) ? 4 : 8;        // float4 loads of S in flight per lane
+    for (int jb = lane; jb < n4; jb += 32 * U) {
+      float4 sv[U];
 #pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const float4 h = yh[r][j], l = yl[r][j];
-        acc[r].add(sv.x * h.x + sv.y * h.y + sv.z * h.z + sv.w * h.w);
-        lo[r] += sv.x * l.x + sv.y * l.y + sv.z * l.z + sv.w * l.w;
+      for (int u = 0; u < U; ++u) {
+        const int j = jb + 32 * u;
+        sv[u] = (j < n4) ? __ldcs(row + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = min(jb + 32 * u, n4 - 1);    // out-of-range slots hold zeros in sv
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float4 h = yh[r][j], l = yl[r][j];
+          acc[r].add(sv[u].x * h.x + sv[u].y * h.y + sv[u].z * h.z + sv[u].w * h.w);
+          lo[r] += sv[u].x * l.x + sv[u].y * l.y + sv[u].z * l.z + sv[u].w * l.w;
+        }
       }
     }
     double tot[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r].value() + (double)lo[r]);
+    for (int r = 0; r < R; ++r) {
+      acc[r].add(lo[r]);
+      acc[r].warp_reduce();
+      tot[r] = acc[r].value();
+    }
     sapply_epilogue<R>(i, lane, rep0, nrep, ne, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
   }
   sapply_reduce<R>(red, rep0, nrep, scal);
@@ -779,7 +920,9 @@ static CellGeom cell_geom(const cpm_ctx* c) {
     g.w[d] = 2 * c->sten[d] + 1;
     g.nsten *= g.w[d];
     g.edge[d] = c->edge[d];
+    g.inv_edge[d] = 1.0 / c->edge[d];
     g.box[d] = c->ebox[d];
+    g.inv_box[d] = 1.0 / c->ebox[d];
   }
   g.rc2 = c->p.rcut * c->p.rcut;
   return g;
@@ -790,7 +933,11 @@ static SpmeGeom spme_geom(const cpm_ctx* c) {
   for (int d = 0; d < 3; ++d) {
     s.K[d] = c->K[d];
     s.box[d] = c->ebox[d];
+    s.kl[d] = c->K[d] / c->ebox[d];
   }
+  s.spl_off[0] = 0;
+  s.spl_off[1] = c->nc[0];
+  s.spl_off[2] = c->nc[0] + c->nc[1];
   s.P = c->P;
   s.Mr_s = c->Mr_s;
   s.Mc_s = c->Mc_s;
@@ -879,22 +1026,27 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   const double ff_over_lz = (c->p.geometry == CPM_FF) ? 1.0 / c->Lz : 0.0;
   const V4* e_loc = c->mixed ? (const V4*)c->e_loc32 : (const V4*)c->e_loc64;
   V4* l_loc = c->mixed ? (V4*)c->l_loc32 : (V4*)c->l_loc64;
+  V4* l_tmp = (V4*)c->l_tmp;
+  T* qT = (T*)c->qT;
   const T* e_th = c->mixed ? (const T*)c->e_th32 : (const T*)c->e_th64;
   const T* e_dth = c->mixed ? (const T*)c->e_dth32 : (const T*)c->e_dth64;
+  const T* splF = c->mixed ? (const T*)c->spl_F32 : (const T*)c->spl_F64;
+  const size_t pc_smem = sizeof(V4) * kPairSrcCap;   // staged sources of the cell-block pair kernel
+  const dim3 gsite((cap + 255) / 256, nrep);
 
   // ---- prepare: cell list ----
   {
-  PhaseTimer pt(c, st, CPM_PH_CELL_LIST);
-  CPM_CUDA(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL * nrep, st));
-  CPM_CUDA(cudaMemsetAsync(c->l_count, 0, sizeof(int) * (size_t)c->ncell * nrep, st));
-  const dim3 gsite((cap + 255) / 256, nrep);
-  k_bin<<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, c->ncell, c->scal, c->status);
-  STEP_LAUNCH();
-  k_scan<<<nrep, 1024, 0, st>>>(c->l_count, c->l_start, c->ncell);
-  STEP_LAUNCH();
-  k_scatter<T><<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->l_cell, c->l_count, c->ncell, c->l_sorted, l_loc,
-                                      c->l_cellc);
-  STEP_LAUNCH();
+    PhaseTimer pt(c, st, CPM_PH_CELL_LIST);
+    CPM_CUDA(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL * nrep, st));
+    CPM_CUDA(cudaMemsetAsync(c->l_count, 0, sizeof(int) * (size_t)c->ncell * nrep, st));
+    k_bin<T><<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, l_tmp, c->ncell, c->scal,
+                                    c->status);
+    STEP_LAUNCH();
+    k_scan<<<nrep, 1024, 0, st>>>(c->l_count, c->l_start, c->ncell);
+    STEP_LAUNCH();
+    k_scatter<T><<<gsite, 256, 0, st>>>(off, cap, g, c->l_cell, l_tmp, c->l_count, c->ncell, c->l_sorted, l_loc,
+                                        c->l_cellc);
+    STEP_LAUNCH();
   }
 
   PairSrc src_elyt{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, nullptr, 0, 0.0, -1};
@@ -909,19 +1061,21 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     double* b = c->b_tmp;                 // aligned internal copy, row stride ld64
     const int ldb = c->ld64;
     // real-space Gaussian-point part of b at the electrode sites
-    PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, nullptr, nullptr, c->phi_real};
+    CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, nullptr, ne, nullptr, nullptr, c->phi_real};
     PairSrc s = src_elyt;
     s.beta = c->p.eta;
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, s, none, g, c->p.alpha, c->scal);
+      k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, s, none, g, c->p.alpha,
+                                                                               kPairSrcCap, c->scal);
       STEP_LAUNCH();
     }
     // SPME part
     {
       PhaseTimer pt(c, st, CPM_PH_B_SPREAD);
       CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
+      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_loc, c->l_cellc, c->spl_I, splF,
+                                                                  (T*)c->mesh_r);
       STEP_LAUNCH();
     }
     {
@@ -980,11 +1134,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // SPME of all charges
     {
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
-      CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, xyzq, cap, sg, (T*)c->mesh_r);
+      k_charge_prep<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal);
       STEP_LAUNCH();
-      k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(q, ne, c->e_base, e_th, sg, c->e_z, c->e_v,
-                                                                 c->e_plus, (T*)c->mesh_r, c->scal);
+      CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_loc, c->l_cellc, c->spl_I, splF,
+                                                                  (T*)c->mesh_r);
+      STEP_LAUNCH();
+      k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(qT, ne, c->e_base, e_th, sg, (T*)c->mesh_r);
       STEP_LAUNCH();
     }
     {
@@ -993,12 +1149,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     }
     PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
     if (f_elyt) {
-      k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, xyzq, cap, sg, dpsi,
+      k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, cap, sg, l_loc,
+                                                                    c->l_cellc, c->l_sorted, c->spl_I, splF, dpsi,
                                                                     ff_over_lz, slab_coef, c->scal, f_elyt);
       STEP_LAUNCH();
     }
     if (f_elec) {
-      k_gather_f_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, q, ne, c->e_base, e_th,
+      k_gather_f_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, qT, ne, c->e_base, e_th,
                                                                    e_dth, sg, dpsi, ff_over_lz, slab_coef, c->scal,
                                                                    f_elec);
       STEP_LAUNCH();
@@ -1007,33 +1164,38 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes)
     {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELYT);
-      PairTgt tg{l_loc, (long long)cap, c->l_cellc, c->l_sorted, off, cap, ne, nullptr, f_elyt, nullptr};
+      CellPairTgt tg{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, off, ne, nullptr,
+                     f_elyt, nullptr};
       PairSrc a = src_elyt;
       a.slot = S_E_LL;
       PairSrc e = src_elec;
-      e.q = q;
+      e.qT = qT;
       e.beta = c->p.eta;
       e.slot = S_E_LE;
       if (f_elyt)
-        k_pair<T, true><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+        k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
+                                                                                kPairSrcCap, c->scal);
       else
-        k_pair<T, false><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+        k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
+                                                                                 kPairSrcCap, c->scal);
       STEP_LAUNCH();
     }
     // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian (energy)
     if (f_elec || (energy && !closed_form)) {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
-      PairTgt tg{e_loc, 0, c->e_cellc, c->e_sorted, nullptr, cap, ne, q, f_elec, nullptr};
+      CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, nullptr, ne, qT, f_elec, nullptr};
       PairSrc a = f_elec ? src_elyt : none;
       a.beta = c->p.eta;
-      PairSrc e = (energy && !closed_form) ? src_elec : none;
-      e.q = q;
+      PairSrc e = src_elec;
+      e.qT = qT;
       e.beta = c->p.eta / std::sqrt(2.0);
-      e.slot = S_E_EE;
+      e.slot = (energy && !closed_form) ? S_E_EE : -1;
       if (f_elec)
-        k_pair<T, true><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+        k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
+                                                                                kPairSrcCap, c->scal);
       else
-        k_pair<T, false><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(tg, a, e, g, c->p.alpha, c->scal);
+        k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
+                                                                                 kPairSrcCap, c->scal);
       STEP_LAUNCH();
     }
     if (energy) {
@@ -1058,6 +1220,10 @@ static int dispatch(cpm_ctx* c, int nrep, const int* off, const double* xyzq, co
     set_error("n_rep %d outside [1, %d]", nrep, c->p.max_replicas);
     return CPM_ERR_CAPACITY;
   }
+  if (reinterpret_cast<uintptr_t>(xyzq) % 32 != 0) {
+    set_error("elyt_xyzq_dev must be 32-byte aligned");
+    return CPM_ERR_ARG;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   return c->mixed ? run<float>(c, nrep, off, xyzq, dpsi, charges, q, b, psibar, f_elyt, f_elec, energy, st)
                   : run<double>(c, nrep, off, xyzq, dpsi, charges, q, b, psibar, f_elyt, f_elec, energy, st);
@@ -1065,9 +1231,21 @@ static int dispatch(cpm_ctx* c, int nrep, const int* off, const double* xyzq, co
 
 }  // namespace cpm
 
+// The float64 cell-block pair kernel stages 64 KiB of sources: raise its dynamic shared memory limit.
+static int pair_cell_attributes() {
+  const int d64 = (int)(sizeof(double4_32a) * cpm::kPairSrcCap), d32 = (int)(sizeof(float4) * cpm::kPairSrcCap);
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<double, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d64));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d64));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
+  return CPM_OK;
+}
+
 int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
+  CPM_TRY(pair_cell_attributes());
   const size_t R = c->p.max_replicas, cap = c->p.max_elyt, ne = c->ne;
   const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
+  const size_t v4 = c->mixed ? sizeof(float4) : sizeof(double4_32a);
   CPM_CUDA(cudaMalloc(&c->mesh_r, tsz * c->Mr_s * R));
   CPM_CUDA(cudaMalloc(&c->mesh_phi, tsz * c->Mr_s * R));
   CPM_CUDA(cudaMalloc(&c->mesh_c, 2 * tsz * c->Mc_s * R));
@@ -1076,9 +1254,11 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaMalloc(&c->l_start, sizeof(int) * R * (c->ncell + 1)));
   CPM_CUDA(cudaMalloc(&c->l_sorted, sizeof(int) * R * cap));
   if (c->mixed)
-    CPM_CUDA(cudaMalloc(&c->l_loc32, sizeof(float4) * R * cap));
+    CPM_CUDA(cudaMalloc(&c->l_loc32, v4 * R * cap));
   else
-    CPM_CUDA(cudaMalloc(&c->l_loc64, sizeof(double4_32a) * R * cap));
+    CPM_CUDA(cudaMalloc(&c->l_loc64, v4 * R * cap));
+  CPM_CUDA(cudaMalloc(&c->l_tmp, v4 * R * cap));
+  CPM_CUDA(cudaMalloc(&c->qT, tsz * R * ne));
   CPM_CUDA(cudaMalloc(&c->l_cellc, sizeof(int4) * R * cap));
   CPM_CUDA(cudaMalloc(&c->phi_real, sizeof(double) * R * ne));
   CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * c->ld64));
@@ -1200,17 +1380,21 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
     cpm::set_error("cpm_step_charges_static: null context or required pointer");
     return CPM_ERR_ARG;
   }
+  if (reinterpret_cast<uintptr_t>(xyzq) % 32 != 0) {
+    cpm::set_error("elyt_xyzq_dev must be 32-byte aligned");
+    return CPM_ERR_ARG;
+  }
   void* base_v = nullptr;
   CPM_TRY(static_scratch(&base_v));
   unsigned char* base = static_cast<unsigned char*>(base_v);
   const size_t tsz = ctx->mixed ? sizeof(float) : sizeof(double);
   const size_t v4 = ctx->mixed ? sizeof(float4) : sizeof(double4_32a);
   const size_t cap = ctx->p.max_elyt, ncell = ctx->ncell;
-  const size_t sizes[] = {tsz * ctx->Mr_s,       tsz * ctx->Mr_s,          2 * tsz * ctx->Mc_s,
-                          sizeof(int) * cap,     sizeof(int) * ncell,      sizeof(int) * (ncell + 1),
-                          sizeof(int) * cap,     v4 * cap,                 sizeof(int4) * cap,
-                          sizeof(double) * ctx->ne, sizeof(double) * ctx->ld64, sizeof(float) * 2 * ctx->ld32,
-                          sizeof(double) * cpm::NSCAL};
+  const size_t sizes[] = {tsz * ctx->Mr_s,          tsz * ctx->Mr_s,             2 * tsz * ctx->Mc_s,
+                          sizeof(int) * cap,        sizeof(int) * ncell,         sizeof(int) * (ncell + 1),
+                          sizeof(int) * cap,        v4 * cap,                    sizeof(int4) * cap,
+                          sizeof(double) * ctx->ne, sizeof(double) * ctx->ld64,  sizeof(float) * 2 * ctx->ld32,
+                          sizeof(double) * cpm::NSCAL, v4 * cap,                 tsz * ctx->ne};
   constexpr int NREG = sizeof(sizes) / sizeof(sizes[0]);
   size_t offs[NREG], total = 0;
   for (int k = 0; k < NREG; ++k) {
@@ -1222,8 +1406,9 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
                    total, CPM_STATIC_SCRATCH_BYTES);
     return CPM_ERR_CAPACITY;
   }
-  // Shallow copy: S, stencils, plans and the status word are shared read-only; every per-call
-  // workspace points into the static array.  One replica, single-batch FFT plan, no profiling.
+  // Shallow copy: S, stencils, tables, plans and the status word are shared read-only; every
+  // per-call workspace points into the static array.  One replica, single-batch FFT plan, no
+  // profiling.
   cpm_ctx t = *ctx;
   t.p.max_replicas = 1;
   t.have_plan[1] = false;
@@ -1244,6 +1429,8 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   t.b_tmp = reinterpret_cast<double*>(base + offs[10]);
   t.b32 = reinterpret_cast<float*>(base + offs[11]);
   t.scal = reinterpret_cast<double*>(base + offs[12]);
+  t.l_tmp = base + offs[13];
+  t.qT = base + offs[14];
   cudaStream_t st = (cudaStream_t)stream;
   // The array keeps the previous call's contents: the S-apply reads the padding of b up to the
   // row stride, so that must be zero.  (The counts, mesh and reduction slots are cleared by the
