@@ -111,26 +111,50 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------------
-# roofline models per phase: algorithmic bytes (HBM) or FP32 operations (ALU) per launch
+# roofline models per phase: algorithmic bytes (HBM-bound kernels) or FP32 flops (ALU-bound pair
+# kernels) per launch.  Phases made of one kernel of this library are the candidates for the
+# dominant kernel; the FFT phases are mostly cuFFT.
 # ----------------------------------------------------------------------------------------------
-def phase_model(phase, s, w):
+PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distance 8, erfc/exp 20, force 12)
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
+# (profiles/k_pair_cell_paper-cell-ff-mixed.md, profiles/k_sapply32_paper-cell-ff-mixed.md); set an
+# entry to None whenever its kernel changes until it is captured again.
+NCU_TRAFFIC_MIXED = {"f_pair_elyt": 0.208384e6, "b_real": 0.109056e6, "s_apply": 36.737536e6}
+SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
+                        "f_pair_elec", "energy")
+
+
+def pair_counts(w):
+    """Ordered (target, source) pairs within r_c for the workload: electrolyte targets with
+    electrolyte and electrode sources (forces), electrode targets with electrolyte sources (b)."""
+    from scipy.spatial import cKDTree
+    import numpy as np
+    box = np.asarray(w.box, float)
+    R = np.mod(w.elyt_xyz[0], box)
+    E = np.mod(w.elec_xyz, box)
+    tl, te = cKDTree(R, boxsize=box), cKDTree(E, boxsize=box)
+    ll = int(tl.count_neighbors(tl, w.rcut)) - len(R)       # ordered pairs, self excluded
+    le = int(tl.count_neighbors(te, w.rcut))
+    return {"f_pair_elyt": ll + le, "b_real": le}
+
+
+def phase_model(phase, s, w, pairs):
     """(bound, algorithmic amount per launch, unit, description) for one profiled phase."""
     ne = s.ne
-    nl = len(w.elyt_q[0])
-    ctx = s.ctx
     mixed = s.params.precision == 1
     fb = 4 if mixed else 8
-    Mr = ctx.mesh_points
-    K = list(w.grid)
-    Mc = K[0] * K[1] * (K[2] // 2 + 1)
     if phase == "s_apply":
         ld = (ne + 3) & ~3
         byt = ne * ld * fb + 8 * ne * 3           # S once, b in, q out, S v
         return "hbm", byt, "GB/s", f"S ({ne}x{ld} x {fb} B) + b, Sv, q (float64)"
-    if phase in ("b_fft", "f_fft"):
-        byt = Mr * fb + 2 * Mc * 2 * fb + Mc * fb + 2 * Mc * 2 * fb + Mr * fb
-        return "hbm", byt, "GB/s", "mesh read/write once per FFT stage and the influence multiply"
+    if phase in pairs:
+        return "alu", PAIR_FLOPS * pairs[phase], "TFLOP/s", f"{pairs[phase]} pairs within r_c x {PAIR_FLOPS} FP32 flops"
     return None
+
+
+def alu_peak_tflops(sm_mhz):
+    """FP32 (non-tensor) peak: 152 SMs x 128 FP32 lanes x 2 flops per FMA x SM clock."""
+    return 152 * 128 * 2 * (sm_mhz or 2070.0) * 1e6 / 1e12
 
 
 def run_gb300(args):
@@ -244,24 +268,34 @@ def run_gb300(args):
     prof = g.cpm_profile_read(s.ctx)
     g.cpm_profile_enable(s.ctx, 0)
     phase_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1] > 0}
-    dom = max(phase_ms, key=phase_ms.get)
-    roof = None
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    # the dominant phase with a bandwidth model, else the largest modelled phase
-    modelled = [p for p in sorted(phase_ms, key=phase_ms.get, reverse=True) if phase_model(p, s, w)]
-    if modelled:
-        p = modelled[0]
-        bound, amount, unit, desc = phase_model(p, s, w)
-        achieved = amount / (phase_ms[p] / 1e3) / 1e9
-        peak = float(peaks.get("hbm_gbs", 6800.0))
-        roof = {"bound": bound, "kernel": p, "achieved": round(achieved, 1), "peak": peak, "unit": unit,
-                "frac": round(achieved / peak, 4), "traffic": None, "algorithmic_bytes_per_launch": amount,
-                "launch_ms": round(phase_ms[p], 5), "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-                "model": desc, "dominant_phase": dom}
+    pairs = pair_counts(w)
+    mixed_prec = args.precision == "mixed"
+
+    def roof_for(p):
+        bound, amount, unit, desc = phase_model(p, s, w, pairs)
+        sec = phase_ms[p] / 1e3
+        if bound == "hbm":
+            achieved, peak = amount / sec / 1e9, float(peaks.get("hbm_gbs", 6800.0))
+            src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"
+        else:
+            achieved, peak = amount / sec / 1e12, alu_peak_tflops(clk.get("sm_mhz"))
+            src = "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock"
+        traffic = NCU_TRAFFIC_MIXED.get(p) if mixed_prec else None
+        return {"bound": bound, "kernel": p, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
+                "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_per_launch": amount,
+                "launch_ms": round(phase_ms[p], 5), "peak_source": src, "model": desc}
+
+    mine = [p for p in SINGLE_KERNEL_PHASES if p in phase_ms]
+    dom = max(mine, key=phase_ms.get)
+    roof = roof_for(dom) if phase_model(dom, s, w, pairs) else None
+    if roof is not None:
+        roof["dominant_phase_overall"] = max(phase_ms, key=phase_ms.get)
+    roof_s = roof_for("s_apply") if "s_apply" in phase_ms else None
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "ns/day", "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -278,7 +312,7 @@ def run_gb300(args):
                    "steps": Ke},
            "gpu_launches": int(launches_per_step * K),
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
-           "roofline": roof}
+           "roofline": roof, "roofline_s_apply": roof_s}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
     if rank == 0:
