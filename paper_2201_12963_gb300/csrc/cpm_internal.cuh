@@ -119,6 +119,7 @@ struct cpm_ctx {
   double* phi_real = nullptr;   // [max_rep][ne]
   double* b_tmp = nullptr;      // [max_rep][ne]
   float* b32 = nullptr;         // [max_rep][2][ld32] float32 high / low split of b (mixed S-apply)
+  float* qraw32 = nullptr;      // [max_rep][ne] tensor-core S-apply output S b (mixed, batched)
   double* scal = nullptr;       // [max_rep][NSCAL]
   int* status = nullptr;        // device status word
   // per-phase event profiler

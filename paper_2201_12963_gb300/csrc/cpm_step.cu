@@ -850,6 +850,199 @@ __global__ void __launch_bounds__(256) k_sapply64(const double* __restrict__ S, 
   sapply_reduce<R>(red, rep0, nrep, scal);
 }
 
+// ------------------------------------------------------------------------------------------
+// Batched S-apply on the 5th-generation tensor cores: D = S Y^T for up to 256 replicas per pass,
+// Y the replicas' right-hand sides.  tcgen05.mma kind::tf32, M = 128 rows of S per CTA, N = the
+// replica tile, K = 8 per instruction, accumulator in TMEM.  Split-TF32 ("3xTF32"): with
+// x_hi = x with its low 13 mantissa bits cleared and x_lo = x - x_hi,
+//   S Y ~= S_hi Y_hi + S_hi Y_lo + S_lo Y_hi   (the dropped S_lo Y_lo term is ~2^-22 relative),
+// accumulated in float32.  Operands are staged into shared memory in the canonical K-major,
+// no-swizzle layout: 8-row x 16-byte core matrices, K-direction core-matrix stride LBO = 128 B,
+// 8-row-group stride SBO = 1024 B for a 32-element K chunk.  Split-K across CTAs; partial tiles
+// are added into D with float32 atomics (D cleared by the host first).
+// ------------------------------------------------------------------------------------------
+constexpr int TC_M = 128, TC_KC = 32, TC_THREADS = 128;
+constexpr int TC_MIN_REPLICAS = 8;     // batches this large take the tensor-core path (mixed precision)
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
+  d |= (uint64_t)1 << 46;                      // descriptor version of sm_100-class tensor cores
+  return d;                                    // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// byte offset of element (row, k) of a K-major operand chunk with TC_KC columns
+__device__ __forceinline__ int tc_off(int row, int k4) { return ((row >> 3) * (TC_KC / 4) + k4) * 128 + (row & 7) * 16; }
+
+template <int NT>
+__global__ void __launch_bounds__(TC_THREADS) k_sapply_tc(const float* __restrict__ S, int ld, int ne,
+                                                          const float* __restrict__ b32, int rep0, int nrep,
+                                                          int chunks_per_split, float* __restrict__ D,
+                                                          int* __restrict__ status) {
+  static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "replica tile");
+  constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
+  constexpr int A_BYTES = TC_M * TC_KC * 4, B_BYTES = NT * TC_KC * 4;
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* sAh = tsm;
+  unsigned char* sAl = tsm + A_BYTES;
+  unsigned char* sBh = tsm + 2 * A_BYTES;
+  unsigned char* sBl = tsm + 2 * A_BYTES + B_BYTES;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int m0 = blockIdx.x * TC_M;
+  const int nchunks = (ld + TC_KC - 1) / TC_KC;
+  const int c_begin = blockIdx.y * chunks_per_split, c_end = min(nchunks, c_begin + chunks_per_split);
+  if (c_begin >= c_end) return;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(TMEM_COLS));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    s_abort = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  const uint32_t idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(NT >> 3) << 17) | ((uint32_t)(TC_M >> 4) << 24);
+  const int ld4 = ld >> 2;
+  int phase = 0;
+  bool ok = true;
+
+  for (int ch = c_begin; ch < c_end && ok; ++ch) {
+    const int k40 = ch * (TC_KC / 4);          // first float4 column of the chunk
+    // ---- stage S rows m0 .. m0+127 (thread = row), split into tf32 hi / lo
+    {
+      const int m = m0 + tid;
+      const float4* row = reinterpret_cast<const float4*>(S + (size_t)min(m, ne - 1) * ld);
+#pragma unroll
+      for (int j = 0; j < TC_KC / 4; ++j) {
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (m < ne && k40 + j < ld4) v = __ldg(row + k40 + j);
+        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+        const float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        *reinterpret_cast<float4*>(sAh + tc_off(tid, j)) = h;
+        *reinterpret_cast<float4*>(sAl + tc_off(tid, j)) = l;
+      }
+    }
+    // ---- stage Y rows (replicas) rep0 .. rep0+NT-1: y = hi32 + lo32 -> tf32 hi / lo
+    for (int n = tid; n < NT; n += TC_THREADS) {
+      const bool live = rep0 + n < nrep;
+      const float4* yh = reinterpret_cast<const float4*>(b32 + (size_t)min(rep0 + n, nrep - 1) * 2 * ld);
+      const float4* yl = reinterpret_cast<const float4*>(b32 + (size_t)min(rep0 + n, nrep - 1) * 2 * ld + ld);
+#pragma unroll
+      for (int j = 0; j < TC_KC / 4; ++j) {
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+        if (live && k40 + j < ld4) {
+          a = yh[k40 + j];
+          c = yl[k40 + j];
+        }
+        const float4 h = make_float4(tf32_hi(a.x), tf32_hi(a.y), tf32_hi(a.z), tf32_hi(a.w));
+        const float4 l = make_float4((a.x - h.x) + c.x, (a.y - h.y) + c.y, (a.z - h.z) + c.z, (a.w - h.w) + c.w);
+        *reinterpret_cast<float4*>(sBh + tc_off(n, j)) = h;
+        *reinterpret_cast<float4*>(sBl + tc_off(n, j)) = l;
+      }
+    }
+    asm volatile("fence.proxy.async.shared::cta;");     // make the staged operands visible to the tensor cores
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+#pragma unroll
+      for (int kk = 0; kk < TC_KC / 8; ++kk) {
+        const uint32_t koff = kk * 256;                  // two core matrices along K per instruction
+        const uint64_t ah = umma_desc(smem_u32(sAh) + koff, 128, 1024);
+        const uint64_t al = umma_desc(smem_u32(sAl) + koff, 128, 1024);
+        const uint64_t bh = umma_desc(smem_u32(sBh) + koff, 128, 1024);
+        const uint64_t bl = umma_desc(smem_u32(sBl) + koff, 128, 1024);
+        const uint32_t acc0 = (ch > c_begin || kk > 0) ? 1u : 0u;
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+                     "l"(ah), "l"(bh), "r"(idesc), "r"(acc0));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+                     "l"(ah), "l"(bl), "r"(idesc), "r"(1u));
+        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(taddr),
+                     "l"(al), "l"(bh), "r"(idesc), "r"(1u));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
+    }
+    // ---- bounded wait for the MMAs (they read the staged operands, so no restaging before)
+    bool done = false;
+    for (int it = 0; it < (1 << 22) && !done; ++it) {
+      uint32_t r;
+      asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                   : "=r"(r) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
+      done = r != 0;
+      if (!done) __nanosleep(32);
+    }
+    if (!done) s_abort = 1;
+    phase ^= 1;
+    __syncthreads();
+    ok = (s_abort == 0);
+  }
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (ok) {
+    const int m = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int n0 = 0; n0 < NT; n0 += 16) {
+      uint32_t r[16];
+      asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                   : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                     "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                   : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)n0));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (m < ne) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const int rep = rep0 + n0 + j;
+          if (rep < nrep) atomicAdd(&D[(size_t)rep * ne + m], __uint_as_float(r[j]));
+        }
+      }
+    }
+  } else if (tid == 0) {
+    latch_error(status, DE_TIMEOUT);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TMEM_COLS));
+}
+
+// q_raw = D + dpsi S v in float64 per (replica, site), with the projection sums C^T q_raw and
+// (A^-1 C)^T b; one thread per site, grid.y = replica.
+__global__ void __launch_bounds__(256) k_qraw_epilogue(const float* __restrict__ D, int ne, const double* __restrict__ b,
+                                                       int ldb, const double* __restrict__ dpsi,
+                                                       const double* __restrict__ Sv, const double* __restrict__ W,
+                                                       const double* __restrict__ c1, double* __restrict__ q,
+                                                       double* __restrict__ scal) {
+  const int rep = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double red[4] = {0, 0, 0, 0};
+  if (i < ne) {
+    const double qr = (double)D[(size_t)rep * ne + i] + dpsi[rep] * Sv[i];
+    q[(size_t)rep * ne + i] = qr;
+    const double bi = b[(size_t)rep * ldb + i];
+    red[0] = qr;
+    red[1] = qr * c1[i];
+    red[2] = W[2 * i] * bi;
+    red[3] = W[2 * i + 1] * bi;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k] = warp_sum(red[k]);
+  double* const dst[4] = {scal + rep * NSCAL + S_CQ0, scal + rep * NSCAL + S_CQ1, scal + rep * NSCAL + S_WB0,
+                          scal + rep * NSCAL + S_WB1};
+  block_atomic_add<4>(red, dst);
+}
+
 // q = q_raw - A^-1 C M C^T q_raw (restores C^T q = 0 to float64 rounding); psibar = -M (A^-1 C)^T (b + dpsi v).
 // Also accumulates q^T b for the closed-form energy.
 __global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne, int nrep, int ncons,
@@ -1014,6 +1207,39 @@ static int convolve(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st) {
   return CPM_OK;
 }
 
+template <int NT>
+static size_t tc_smem_bytes() {
+  return 2 * (size_t)TC_M * TC_KC * 4 + 2 * (size_t)NT * TC_KC * 4;
+}
+
+template <int NT>
+static int launch_tc(cpm_ctx* c, int rep0, int nrep, dim3 grid, int cps, cudaStream_t st) {
+  k_sapply_tc<NT><<<grid, TC_THREADS, tc_smem_bytes<NT>(), st>>>(c->S32, c->ld32, c->ne, c->b32, rep0, nrep, cps,
+                                                                  c->qraw32, c->status);
+  STEP_LAUNCH();
+  return CPM_OK;
+}
+
+// D = S Y^T on the tensor cores for all replicas, in passes of at most 256; split-K so that the
+// grid covers the SMs.
+static int sapply_tensor_core(cpm_ctx* c, int nrep, cudaStream_t st) {
+  CPM_CUDA(cudaMemsetAsync(c->qraw32, 0, sizeof(float) * (size_t)nrep * c->ne, st));
+  const int mtiles = (c->ne + TC_M - 1) / TC_M;
+  const int nchunks = (c->ld32 + TC_KC - 1) / TC_KC;
+  const int splits = std::max(1, std::min(nchunks, (2 * 152 + mtiles - 1) / mtiles));
+  const int cps = (nchunks + splits - 1) / splits;
+  const dim3 grid(mtiles, (nchunks + cps - 1) / cps);
+  for (int r0 = 0; r0 < nrep; r0 += 256) {
+    const int left = nrep - r0;
+    if (left <= 16) CPM_TRY(launch_tc<16>(c, r0, nrep, grid, cps, st));
+    else if (left <= 32) CPM_TRY(launch_tc<32>(c, r0, nrep, grid, cps, st));
+    else if (left <= 64) CPM_TRY(launch_tc<64>(c, r0, nrep, grid, cps, st));
+    else if (left <= 128) CPM_TRY(launch_tc<128>(c, r0, nrep, grid, cps, st));
+    else CPM_TRY(launch_tc<256>(c, r0, nrep, grid, cps, st));
+  }
+  return CPM_OK;
+}
+
 template <typename T>
 static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const double* dpsi, bool charges,
                double* q, double* b_out, double* psibar, double* f_elyt, double* f_elec, double* energy,
@@ -1097,30 +1323,37 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     const int sblocks = std::min(grid_for(ne), 152 * 4);
     {
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
-      for (int r0 = 0; r0 < nrep; r0 += 4) {
-        const int left = nrep - r0;
-        if (c->mixed) {
-          if (left == 1)
-            k_sapply32<1><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
-                                                   c->e_c1, q, c->scal);
-          else if (left == 2)
-            k_sapply32<2><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
-                                                   c->e_c1, q, c->scal);
-          else
-            k_sapply32<4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
-                                                   c->e_c1, q, c->scal);
-        } else {
-          if (left == 1)
-            k_sapply64<1><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
-                                                   q, c->scal);
-          else if (left == 2)
-            k_sapply64<2><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
-                                                   q, c->scal);
-          else
-            k_sapply64<4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W, c->e_c1,
-                                                   q, c->scal);
-        }
+      if (c->mixed && nrep >= TC_MIN_REPLICAS) {
+        CPM_TRY(sapply_tensor_core(c, nrep, st));
+        k_qraw_epilogue<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(c->qraw32, ne, b, ldb, dpsi, c->Sv, c->W,
+                                                                      c->e_c1, q, c->scal);
         STEP_LAUNCH();
+      } else {
+        for (int r0 = 0; r0 < nrep; r0 += 4) {
+          const int left = nrep - r0;
+          if (c->mixed) {
+            if (left == 1)
+              k_sapply32<1><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv,
+                                                     c->W, c->e_c1, q, c->scal);
+            else if (left == 2)
+              k_sapply32<2><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv,
+                                                     c->W, c->e_c1, q, c->scal);
+            else
+              k_sapply32<4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv,
+                                                     c->W, c->e_c1, q, c->scal);
+          } else {
+            if (left == 1)
+              k_sapply64<1><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
+                                                     c->e_c1, q, c->scal);
+            else if (left == 2)
+              k_sapply64<2><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
+                                                     c->e_c1, q, c->scal);
+            else
+              k_sapply64<4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
+                                                     c->e_c1, q, c->scal);
+          }
+          STEP_LAUNCH();
+        }
       }
     }
     PhaseTimer ptp(c, st, CPM_PH_PROJECT);
@@ -1241,8 +1474,23 @@ static int pair_cell_attributes() {
   return CPM_OK;
 }
 
+static int tc_attributes() {
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_tc<16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cpm::tc_smem_bytes<16>()));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_tc<32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cpm::tc_smem_bytes<32>()));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_tc<64>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cpm::tc_smem_bytes<64>()));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_tc<128>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cpm::tc_smem_bytes<128>()));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_tc<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)cpm::tc_smem_bytes<256>()));
+  return CPM_OK;
+}
+
 int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_TRY(pair_cell_attributes());
+  CPM_TRY(tc_attributes());
   const size_t R = c->p.max_replicas, cap = c->p.max_elyt, ne = c->ne;
   const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
   const size_t v4 = c->mixed ? sizeof(float4) : sizeof(double4_32a);
@@ -1266,6 +1514,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaMalloc(&c->b32, sizeof(float) * R * 2 * c->ld32));
   CPM_CUDA(cudaMemset(c->b32, 0, sizeof(float) * R * 2 * c->ld32));
   CPM_CUDA(cudaMalloc(&c->scal, sizeof(double) * R * cpm::NSCAL));
+  if (c->mixed && (int)R >= cpm::TC_MIN_REPLICAS) CPM_CUDA(cudaMalloc(&c->qraw32, sizeof(float) * R * ne));
   CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
   CPM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
   return CPM_OK;
