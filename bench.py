@@ -47,6 +47,27 @@ def parse():
     return ap.parse_args()
 
 
+def replica_seed(base, rank):
+    """Each rank steps its own independent replica (replicas only, no data-path collective)."""
+    return base + 2 * rank
+
+
+def reduce_max(x, device="cpu"):
+    """Maximum of x over all ranks (the slowest rank's time sets the aggregate rate)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_steps_per_s(total_ms_max, steps, world):
+    """Whole-job throughput: all ranks' steps over the slowest rank's timed region."""
+    return world * steps / (total_ms_max / 1e3)
+
+
 def workload(seed):
     import synth
     return synth.config_paper_cell(seed=seed)
@@ -173,7 +194,7 @@ def run_gb300(args):
     import paper_2201_12963_gb300 as g
     from paper_2201_12963_gb300.driver import System
 
-    w = workload(args.seed + 2 * rank)
+    w = workload(replica_seed(args.seed, rank))
     s = System(w, args.precision, device=dev)
 
     # the whole step captured once into a CUDA graph
@@ -220,13 +241,9 @@ def run_gb300(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    tot_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([tot_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
+    tot_ms = reduce_max(sum(step_ms), dev)
     ms_per_step = tot_ms / K
-    steps_per_s = world * K / (tot_ms / 1e3)
+    steps_per_s = aggregate_steps_per_s(tot_ms, K, world)
     value = steps_per_s * NS_PER_DAY_PER_STEP_PER_S
     st = g.cpm_status(s.ctx)
     if st != 0:
@@ -252,11 +269,7 @@ def run_gb300(args):
         torch.cuda.current_stream(dev).synchronize()
     e1.record()
     torch.cuda.synchronize(dev)
-    e2e_s = max(time.perf_counter() - t0, e0.elapsed_time(e1) / 1e3)
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = reduce_max(max(time.perf_counter() - t0, e0.elapsed_time(e1) / 1e3), dev)
     e2e_value = world * Ke / e2e_s * NS_PER_DAY_PER_STEP_PER_S
 
     # ---- per-phase profile of the same step (events inside the library), L2 flushed per step ----

@@ -325,3 +325,39 @@ class Reference:
             real_space(R[tl], E, q, box, rc, a, eta, want_grad=grad)
             real_space(R[tl], R, Q, box, rc, a, None, same=True, want_grad=grad, target_index=tl)
             recip_space(P, P, c, box, a, self.kmax, want_grad=grad, ksub=ksub)
+
+
+# ----------------------------------------------------------------------------------------------
+# sampled checks for workloads too large for a dense oracle solve
+# ----------------------------------------------------------------------------------------------
+def b_at(w, R, Q, idx, kmax=None) -> np.ndarray:
+    """b_i (Eq. 3) at the electrode sites idx only."""
+    box = ewald_box(w)
+    E = np.asarray(w.elec_xyz, np.float64)[idx]
+    phi = real_space(E, R, Q, box, w.rcut, w.alpha, w.eta)
+    phi += recip_space(E, R, Q, box, w.alpha, kmax)
+    b = -KE * phi
+    if w.geometry == "slab":
+        V = float(np.prod(box))
+        b -= KE * (4.0 * math.pi / V) * E[:, 2] * float(np.dot(Q, R[:, 2]))
+    return b
+
+
+def electrolyte_forces_at(w, R, Q, q, dpsi, idx, kmax=None) -> np.ndarray:
+    """Forces on the electrolyte sites idx for given electrode charges q (as in forces())."""
+    box = ewald_box(w)
+    E = np.asarray(w.elec_xyz, np.float64)
+    T = R[idx]
+    _, g_le = real_space(T, E, q, box, w.rcut, w.alpha, w.eta, want_grad=True)
+    _, g_ll = real_space(T, R, Q, box, w.rcut, w.alpha, None, same=True, want_grad=True, target_index=idx)
+    P = np.vstack([E, R])
+    c = np.concatenate([q, Q])
+    _, g_k = recip_space(T, P, c, box, w.alpha, kmax, want_grad=True)
+    F = -KE * Q[idx, None] * (g_le + g_ll + g_k)
+    if w.geometry == "slab":
+        V = float(np.prod(box))
+        mz = float(q @ E[:, 2] + Q @ R[:, 2])
+        F[:, 2] -= KE * (4.0 * math.pi / V) * Q[idx] * mz
+    if w.geometry == "ff":
+        F[:, 2] -= Q[idx] * dpsi / float(w.box[2])
+    return F
