@@ -43,7 +43,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--seed", type=int, default=2000)
+    ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--workload", default="paper", choices=["paper", "large"],
+                    help="paper: the paper-scale cell (default); large: the 10,080-site cell")
     return ap.parse_args()
 
 
@@ -68,13 +70,19 @@ def aggregate_steps_per_s(total_ms_max, steps, world):
     return world * steps / (total_ms_max / 1e3)
 
 
-def workload(seed):
+WORKLOADS = {
+    "paper": ("paper-scale finite-field cell: 3,024 electrode sites (3-layer graphite x 2), 500 CG ion "
+              "pairs (2,000 sites), 38.34x34.44x168 A, SPME 40x36x168 order 5, alpha 0.25, r_c 12 A", 2000),
+    "large": ("scaled finite-field cell: 10,080 electrode sites (3-layer graphite x 2), 5,000 point-ion pairs "
+              "(10,000 sites), 63.90x68.88x154 A, SPME 64x70x160 order 5, alpha 0.25, r_c 12 A", 4000),
+}
+
+
+def workload(seed, kind="paper"):
     import synth
+    if kind == "large":
+        return synth.config_large_ff(seed=seed)
     return synth.config_paper_cell(seed=seed)
-
-
-WORKLOAD_NAME = ("paper-scale finite-field cell: 3,024 electrode sites (3-layer graphite x 2), 500 CG ion "
-                 "pairs (2,000 sites), 38.34x34.44x168 A, SPME 40x36x168 order 5, alpha 0.25, r_c 12 A")
 
 
 # ----------------------------------------------------------------------------------------------
@@ -140,7 +148,8 @@ PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distanc
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
 # (profiles/k_pair_cell_paper-cell-ff-mixed.md, profiles/k_sapply32_paper-cell-ff-mixed.md); set an
 # entry to None whenever its kernel changes until it is captured again.
-NCU_TRAFFIC_MIXED = {"f_pair_elyt": 0.208384e6, "b_real": 0.109056e6, "s_apply": 36.737536e6}
+NCU_TRAFFIC_MIXED = {"paper": {"f_pair_elyt": 0.208384e6, "b_real": 0.109056e6, "s_apply": 36.737536e6},
+                     "large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
 
@@ -194,7 +203,7 @@ def run_gb300(args):
     import paper_2201_12963_gb300 as g
     from paper_2201_12963_gb300.driver import System
 
-    w = workload(replica_seed(args.seed, rank))
+    w = workload(replica_seed(args.seed, rank), args.workload)
     s = System(w, args.precision, device=dev)
 
     # the whole step captured once into a CUDA graph
@@ -298,7 +307,7 @@ def run_gb300(args):
         else:
             achieved, peak = amount / sec / 1e12, alu_peak_tflops(clk.get("sm_mhz"))
             src = "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock"
-        traffic = NCU_TRAFFIC_MIXED.get(p) if mixed_prec else None
+        traffic = NCU_TRAFFIC_MIXED[args.workload].get(p) if mixed_prec else None
         return {"bound": bound, "kernel": p, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_per_launch": amount,
                 "launch_ms": round(phase_ms[p], 5), "peak_source": src, "model": desc}
@@ -314,7 +323,7 @@ def run_gb300(args):
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "geometry": "finite field", "precision": args.precision,
+           "config": {"workload": WORKLOADS[args.workload][0], "geometry": "finite field", "precision": args.precision,
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
                       "graph": "whole step captured in one CUDA graph", "steps_per_s": round(steps_per_s, 1),
@@ -326,9 +335,12 @@ def run_gb300(args):
            "gpu_launches": int(launches_per_step * K),
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
            "roofline": roof, "roofline_s_apply": roof_s}
-    out["batched"] = batched_replicas(args, dev, flush)
+    if args.workload == "paper":
+        out["batched"] = batched_replicas(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args)
+        out["cpu_baseline"] = cpu_baseline(args) if args.workload == "paper" else {
+            "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
+            "sample": "not run: the oracle's dense A for 10,080 sites takes hours on the host"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -389,7 +401,8 @@ def batched_replicas(args, dev, flush):
 def cpu_baseline(args):
     """One full oracle step of the same workload on this host, timed in a child process
     (the oracle's A and its Cholesky factor are built first, untimed)."""
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--seed", str(args.seed)]
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--seed", str(args.seed),
+           "--workload", args.workload]
     r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
     if r.returncode != 0:
         return {"value": None, "unit": "ns/day", "kind": "oracle", "error": r.stderr[-300:]}
@@ -398,7 +411,7 @@ def cpu_baseline(args):
 
 def cpu_baseline_child(args):
     from oracle import cpm as ocpm
-    w = workload(args.seed)
+    w = workload(args.seed, args.workload)
     ref = ocpm.Reference(w)
     t0 = time.perf_counter()
     ref.step(0)
@@ -419,7 +432,7 @@ def run_reference(args):
     if rank != 0:
         return
     from oracle import cpm as ocpm
-    w = workload(args.seed)
+    w = workload(args.seed, args.workload)
     ref = ocpm.Reference(w)
     f1, f2 = 0.03, 0.12
     t = time.perf_counter(); ref.sampled_step(0, f1, 1); t1 = time.perf_counter() - t
@@ -444,7 +457,7 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "ns/day", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOAD_NAME, "geometry": "finite field", "precision": "fp64 oracle"},
+           "config": {"workload": WORKLOADS[args.workload][0], "geometry": "finite field", "precision": "fp64 oracle"},
            "cpu_baseline": {"value": round(value, 6), "unit": "ns/day", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": round(value, 6), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -453,6 +466,8 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.seed is None:
+        args.seed = WORKLOADS[args.workload][1]
     if args.cpu_baseline_child:
         cpu_baseline_child(args)
     elif args.impl == "reference":

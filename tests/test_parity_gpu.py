@@ -211,3 +211,4 @@ def test_batched_tensor_core_s_apply_matches_float64_path():
         ref.w = wr
         q, lam, _ = ref.charges(wr.elyt_xyz[0], wr.elyt_q[0], float(wr.dpsi[0]))
         assert np.max(np.abs(r32["q"][r] - q)) <= 1e-5
+
