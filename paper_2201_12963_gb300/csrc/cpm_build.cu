@@ -599,7 +599,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->e_plus, c->S64, c->S32,
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->l_tmp, c->qT, c->spl_I,
-                  c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32,
+                  c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
                   c->scal, c->status};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -608,6 +608,9 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
       cufftDestroy(c->plan_r2c[b]);
       cufftDestroy(c->plan_c2r[b]);
     }
+  if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+  if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->side) cudaStreamDestroy(c->side);
   if (c->cublas) cublasDestroy(c->cublas);
   if (c->solver) cusolverDnDestroy(c->solver);
   delete c;

@@ -127,6 +127,11 @@ struct cpm_ctx {
   int* prof_phase = nullptr;        // [prof_cap]
   int prof_cap = 0, prof_used = 0;
   long long launches = 0;           // kernels of this library launched by per-step calls
+  // side stream for work independent of the mesh chain (forked and joined with events, so a
+  // captured call becomes a forked CUDA graph)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  double* f_pair = nullptr;     // [max_rep][max_elyt][3] real-space electrolyte forces (original order)
   // libraries
   cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t solver = nullptr;

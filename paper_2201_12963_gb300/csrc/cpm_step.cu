@@ -251,10 +251,9 @@ struct CellPairTgt {
   const int* start;         // [ncell + 1] target cell starts
   long long start_stride;
   const int* sorted;        // sorted -> original index
-  const int* off;           // electrolyte: replica offsets (global force index); nullptr for electrodes
-  int n_fixed;              // electrode count (force / phi index stride)
+  int n_fixed;              // per-replica stride of force (electrolyte: capacity) and phi_out (electrodes)
   const void* qT;           // electrode target charges [rep][n_fixed] in the working precision, or nullptr
-  double* force;            // += KE c_t sum_s c_s g(r) d, [global index][3] or nullptr
+  double* force;            // += KE c_t sum_s c_s g(r) d at [rep * n_fixed + original index][3], or nullptr
   double* phi_out;          // sum over set 0 of c_s kernel(r), [rep][n_fixed] original order, or nullptr
 };
 
@@ -436,7 +435,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       eacc[0] += qt * tphi[0][k];
       eacc[1] += qt * tphi[1][k];
       if (FORCE && t.force) {
-        const size_t gi = t.off ? (size_t)t.off[rep] + orig : (size_t)rep * t.n_fixed + orig;
+        const size_t gi = (size_t)rep * t.n_fixed + orig;
         const double f = KE * qt;
         t.force[3 * gi + 0] += f * tf[0][k];
         t.force[3 * gi + 1] += f * tf[1][k];
@@ -617,7 +616,8 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
                                                        const int* __restrict__ l_sorted, const int* __restrict__ splI,
                                                        const T* __restrict__ splF, const double* __restrict__ dpsi,
                                                        double ff_over_lz, double slab_coef,
-                                                       const double* __restrict__ scal, double* __restrict__ F) {
+                                                       const double* __restrict__ scal,
+                                                       const double* __restrict__ f_pair, double* __restrict__ F) {
   __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
   __shared__ int si0[8][3];
   const int rep = blockIdx.y;
@@ -655,10 +655,12 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
       const double q = (double)p.w;
       const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
       const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
-      const size_t gi = 3 * (size_t)(o + l_sorted[k]);
-      F[gi + 0] = -q * (double)gx * sg.kl[0];
-      F[gi + 1] = -q * (double)gy * sg.kl[1];
-      F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf;
+      const int orig = l_sorted[k];
+      const size_t gi = 3 * (size_t)(o + orig);
+      const double* fp = f_pair + 3 * ((size_t)rep * cap + orig);
+      F[gi + 0] = -q * (double)gx * sg.kl[0] + fp[0];
+      F[gi + 1] = -q * (double)gy * sg.kl[1] + fp[1];
+      F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf + fp[2];
     }
     __syncwarp();
   }
@@ -1287,15 +1289,23 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     double* b = c->b_tmp;                 // aligned internal copy, row stride ld64
     const int ldb = c->ld64;
     // real-space Gaussian-point part of b at the electrode sites
-    CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, nullptr, ne, nullptr, nullptr, c->phi_real};
+    // (on the side stream, concurrent with the mesh chain below; joined before the gather)
+    CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, nullptr, nullptr, c->phi_real};
     PairSrc s = src_elyt;
     s.beta = c->p.eta;
+    const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
+    cudaStream_t sb = fork ? c->side : st;
+    if (fork) {
+      CPM_CUDA(cudaEventRecord(c->ev_fork, st));
+      CPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, s, none, g, c->p.alpha,
+      k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sb>>>(tg, s, none, g, c->p.alpha,
                                                                                kPairSrcCap, c->scal);
       STEP_LAUNCH();
     }
+    if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
     // SPME part
     {
       PhaseTimer pt(c, st, CPM_PH_B_SPREAD);
@@ -1308,6 +1318,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PhaseTimer pt(c, st, CPM_PH_B_FFT);
       CPM_TRY(convolve<T>(c, nrep, closed_form ? S_E_RECIP_L : -1, st));
     }
+    if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     {
       PhaseTimer pt(c, st, CPM_PH_B_GATHER);
       k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
@@ -1364,11 +1375,42 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   }
 
   if (f_elyt || f_elec || energy) {
-    // SPME of all charges
+    const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
+    cudaStream_t sp = fork ? c->side : st;
     {
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
       k_charge_prep<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal);
       STEP_LAUNCH();
+    }
+    // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes), into f_pair;
+    // on the side stream, concurrent with the mesh chain, joined before the force gather
+    if (fork) {
+      CPM_CUDA(cudaEventRecord(c->ev_fork, st));
+      CPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
+    {
+      PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELYT);
+      if (f_elyt) CPM_CUDA(cudaMemsetAsync(c->f_pair, 0, sizeof(double) * 3 * (size_t)cap * nrep, sp));
+      CellPairTgt tg{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, cap, nullptr,
+                     f_elyt ? c->f_pair : nullptr, nullptr};
+      PairSrc a = src_elyt;
+      a.slot = S_E_LL;
+      PairSrc e = src_elec;
+      e.qT = qT;
+      e.beta = c->p.eta;
+      e.slot = S_E_LE;
+      if (f_elyt)
+        k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
+                                                                                kPairSrcCap, c->scal);
+      else
+        k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
+                                                                                 kPairSrcCap, c->scal);
+      STEP_LAUNCH();
+    }
+    if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    // SPME of all charges
+    {
+      PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
       CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
       k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_loc, c->l_cellc, c->spl_I, splF,
                                                                   (T*)c->mesh_r);
@@ -1380,11 +1422,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PhaseTimer pt(c, st, CPM_PH_F_FFT);
       CPM_TRY(convolve<T>(c, nrep, (energy && !closed_form) ? S_E_RECIP : -1, st));
     }
+    if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
     if (f_elyt) {
       k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, cap, sg, l_loc,
                                                                     c->l_cellc, c->l_sorted, c->spl_I, splF, dpsi,
-                                                                    ff_over_lz, slab_coef, c->scal, f_elyt);
+                                                                    ff_over_lz, slab_coef, c->scal, c->f_pair,
+                                                                    f_elyt);
       STEP_LAUNCH();
     }
     if (f_elec) {
@@ -1394,29 +1438,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       STEP_LAUNCH();
     }
     ptg.stop();
-    // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes)
-    {
-      PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELYT);
-      CellPairTgt tg{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, off, ne, nullptr,
-                     f_elyt, nullptr};
-      PairSrc a = src_elyt;
-      a.slot = S_E_LL;
-      PairSrc e = src_elec;
-      e.qT = qT;
-      e.beta = c->p.eta;
-      e.slot = S_E_LE;
-      if (f_elyt)
-        k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal);
-      else
-        k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal);
-      STEP_LAUNCH();
-    }
     // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian (energy)
     if (f_elec || (energy && !closed_form)) {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
-      CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, nullptr, ne, qT, f_elec, nullptr};
+      CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, qT, f_elec, nullptr};
       PairSrc a = f_elec ? src_elyt : none;
       a.beta = c->p.eta;
       PairSrc e = src_elec;
@@ -1513,6 +1538,10 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaMemset(c->b_tmp, 0, sizeof(double) * R * c->ld64));
   CPM_CUDA(cudaMalloc(&c->b32, sizeof(float) * R * 2 * c->ld32));
   CPM_CUDA(cudaMemset(c->b32, 0, sizeof(float) * R * 2 * c->ld32));
+  CPM_CUDA(cudaMalloc(&c->f_pair, sizeof(double) * R * cap * 3));
+  CPM_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
+  CPM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+  CPM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CPM_CUDA(cudaMalloc(&c->scal, sizeof(double) * R * cpm::NSCAL));
   if (c->mixed && (int)R >= cpm::TC_MIN_REPLICAS) CPM_CUDA(cudaMalloc(&c->qraw32, sizeof(float) * R * ne));
   CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
