@@ -44,8 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=None)
-    ap.add_argument("--workload", default="paper", choices=["paper", "large"],
-                    help="paper: the paper-scale cell (default); large: the 10,080-site cell")
+    ap.add_argument("--workload", default="paper", choices=["paper", "large", "dc-large"],
+                    help="paper: the paper-scale cell (default); large: the 10,080-site cell; dc-large: the "
+                         "40,320-site doubled cell (mirror blocks, mesh-operator A)")
     return ap.parse_args()
 
 
@@ -75,14 +76,30 @@ WORKLOADS = {
               "pairs (2,000 sites), 38.34x34.44x168 A, SPME 40x36x168 order 5, alpha 0.25, r_c 12 A", 2000),
     "large": ("scaled finite-field cell: 10,080 electrode sites (3-layer graphite x 2), 5,000 point-ion pairs "
               "(10,000 sites), 63.90x68.88x154 A, SPME 64x70x160 order 5, alpha 0.25, r_c 12 A", 4000),
+    "dc-large": ("large doubled cell: 40,320 electrode sites (two mirrored 125x123x100 A sub-cells, 3-layer "
+                 "60x56 rectangular-lattice electrodes), 25,000 CG ion pairs (100,000 sites), 125x123x200 A, "
+                 "SPME 128x128x200 order 5, alpha 0.25, r_c 12 A; S stored as two 20,160^2 mirror blocks, "
+                 "A's reciprocal part as the SPME mesh operator", 5000),
 }
+GEOMETRY_NAME = {"paper": "finite field", "large": "finite field", "dc-large": "doubled cell"}
 
 
 def workload(seed, kind="paper"):
     import synth
     if kind == "large":
         return synth.config_large_ff(seed=seed)
+    if kind == "dc-large":
+        return synth.config_large_dc(seed=seed)
     return synth.config_paper_cell(seed=seed)
+
+
+def system_options(kind):
+    """Build options of each workload: the doubled cell is built with mirror blocks and the mesh
+    form of A's reciprocal part (the direct Ewald sum over ~10^6 k-vectors is out of reach in
+    float64 at 40,320 sites)."""
+    if kind == "dc-large":
+        return {"matrix_kspace": "mesh", "dc_blocks": "mirror"}
+    return {}
 
 
 # ----------------------------------------------------------------------------------------------
@@ -149,7 +166,7 @@ PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distanc
 # (profiles/k_pair_cell_paper-cell-ff-mixed.md, profiles/k_sapply32_paper-cell-ff-mixed.md); set an
 # entry to None whenever its kernel changes until it is captured again.
 NCU_TRAFFIC_MIXED = {"paper": {"f_pair_elyt": 0.208384e6, "b_real": 0.109056e6, "s_apply": 36.737536e6},
-                     "large": {}}
+                     "large": {}, "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
 
@@ -174,9 +191,11 @@ def phase_model(phase, s, w, pairs):
     mixed = s.params.precision == 1
     fb = 4 if mixed else 8
     if phase == "s_apply":
-        ld = (ne + 3) & ~3
-        byt = ne * ld * fb + 8 * ne * 3           # S once, b in, q out, S v
-        return "hbm", byt, "GB/s", f"S ({ne}x{ld} x {fb} B) + b, Sv, q (float64)"
+        import paper_2201_12963_gb300 as g
+        mirror, s_bytes = g.cpm_matrix_layout(s.ctx)
+        byt = s_bytes + 8 * ne * 3                # S once, b in, q out, S v
+        what = f"two mirror blocks S+- ({ne // 2}^2 each)" if mirror else f"S ({ne}^2)"
+        return "hbm", byt, "GB/s", f"{what} x {fb} B + b, Sv, q (float64)"
     if phase in pairs:
         return "alu", PAIR_FLOPS * pairs[phase], "TFLOP/s", f"{pairs[phase]} pairs within r_c x {PAIR_FLOPS} FP32 flops"
     return None
@@ -204,7 +223,10 @@ def run_gb300(args):
     from paper_2201_12963_gb300.driver import System
 
     w = workload(replica_seed(args.seed, rank), args.workload)
-    s = System(w, args.precision, device=dev)
+    tb = time.perf_counter()
+    s = System(w, args.precision, device=dev, **system_options(args.workload))
+    torch.cuda.synchronize(dev)
+    build_s = time.perf_counter() - tb
 
     # the whole step captured once into a CUDA graph
     side = torch.cuda.Stream(dev)
@@ -323,7 +345,8 @@ def run_gb300(args):
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.workload][0], "geometry": "finite field", "precision": args.precision,
+           "config": {"workload": WORKLOADS[args.workload][0], "geometry": GEOMETRY_NAME[args.workload],
+                      "precision": args.precision, "build_s": round(build_s, 2),
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
                       "graph": "whole step captured in one CUDA graph", "steps_per_s": round(steps_per_s, 1),
@@ -340,7 +363,7 @@ def run_gb300(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args) if args.workload == "paper" else {
             "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
-            "sample": "not run: the oracle's dense A for 10,080 sites takes hours on the host"}
+            "sample": f"not run: the oracle's dense A for {w.n_elec:,} sites takes hours on the host"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -457,7 +480,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "ns/day", "n_gpus": world,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.workload][0], "geometry": "finite field", "precision": "fp64 oracle"},
+           "config": {"workload": WORKLOADS[args.workload][0], "geometry": GEOMETRY_NAME[args.workload],
+                      "precision": "fp64 oracle"},
            "cpu_baseline": {"value": round(value, 6), "unit": "ns/day", "cores": os.cpu_count(), "kind": "oracle",
                             "sample": sample},
            "e2e": {"value": round(value, 6), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}

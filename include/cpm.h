@@ -53,6 +53,26 @@ enum cpm_geometry { CPM_FF = 0, CPM_DOUBLED = 1, CPM_SLAB = 2 };
  * float64. */
 enum cpm_precision { CPM_FP64 = 0, CPM_MIXED = 1 };
 
+/* Reciprocal part of A (cpm_params.matrix_kspace).
+ * CPM_KSPACE_EWALD: the direct Ewald sum over k-vectors up to kmax_build (the converged continuum
+ *   result; its cost grows with N_e^2 times the k-vector count, which is large for big cells).
+ * CPM_KSPACE_MESH: the SPME mesh operator of the per-step calls, A_k = W^T Phi W (W the B-spline
+ *   stencils of the electrode sites, Phi the mesh convolution with the influence function), one
+ *   batched FFT convolution per electrode column.  The matrix then matches the discrete
+ *   electrostatics of b, the forces and the energy exactly; it differs from the Ewald form by the
+ *   mesh discretisation error. */
+enum cpm_matrix_kspace { CPM_KSPACE_EWALD = 0, CPM_KSPACE_MESH = 1 };
+
+/* Doubled-cell storage of S (cpm_params.dc_blocks; CPM_DOUBLED only).  When every sub-cell-1
+ * electrode site is the z-mirror image (x, y, L_z - z) of a sub-cell-0 site, A = [[P, Q], [Q, P]] in
+ * the order (sub-cell 0, images), and the constrained problem separates into two N_e/2-site
+ * problems q+- = S+- (y_0 +- y_1) on the sums and differences of mirror pairs, each with one
+ * neutrality constraint: two half-size factorisations and half the S bytes per step.
+ *   CPM_DC_AUTO    mirror blocks when the electrode is mirror-symmetric, else the full matrix;
+ *   CPM_DC_MIRROR  mirror blocks, CPM_ERR_ARG if the electrode is not mirror-symmetric;
+ *   CPM_DC_FULL    always the full N_e x N_e matrix. */
+enum cpm_dc_blocks { CPM_DC_AUTO = 0, CPM_DC_MIRROR = 1, CPM_DC_FULL = 2 };
+
 enum cpm_status {
   CPM_OK = 0,
   CPM_ERR_ARG = -1,        /* invalid argument (null pointer, size, parameter out of range) */
@@ -79,6 +99,8 @@ typedef struct {
   int32_t precision;    /* enum cpm_precision */
   int32_t max_replicas; /* capacity: largest n_rep accepted by the per-step calls, >= 1 */
   int32_t max_elyt;     /* capacity: largest electrolyte site count of one replica, >= 1 */
+  int32_t matrix_kspace;/* enum cpm_matrix_kspace */
+  int32_t dc_blocks;    /* enum cpm_dc_blocks (CPM_DOUBLED only) */
 } cpm_params;
 
 /*
@@ -94,9 +116,10 @@ typedef struct {
  *   stream          stream for the build work; the call synchronises it before returning.
  *   out             receives the new context (set to NULL on failure).
  * A is built in float64 on the GPU: real-space Gaussian-Gaussian pairs over all images within
- * rcut, reciprocal part as a direct Ewald sum up to kmax_build, self terms, and for CPM_SLAB the
- * dipole term.  Returns CPM_ERR_NOT_SPD if the Cholesky factorisation fails, CPM_ERR_NOMEM if
- * device memory runs out.
+ * rcut, the reciprocal part (direct Ewald sum up to kmax_build, or the SPME mesh operator, see
+ * cpm_matrix_kspace), self terms, and for CPM_SLAB the dipole term.  A mirror-symmetric doubled
+ * cell is stored as two half-size blocks (cpm_dc_blocks).  Returns CPM_ERR_NOT_SPD if a Cholesky
+ * factorisation fails, CPM_ERR_NOMEM if device memory runs out.
  */
 int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
                      const int32_t* elec_side_host, const int32_t* elec_cell_host, void* stream,
@@ -165,12 +188,22 @@ int cpm_capacitance(const cpm_ctx* ctx, double* dq_ddpsi_host);
 /*
  * cpm_copy_matrix - copy a build-time matrix to host memory (diagnostics and tests).
  *   which = 0: S (float64, N_e x N_e row-major); 1: S v (N_e); 2: A^-1 C (N_e x ncons row-major).
+ * Always in the original site order; for mirror blocks the full matrices are assembled on the host
+ * from the blocks.
  */
 int cpm_copy_matrix(const cpm_ctx* ctx, int32_t which, double* host_out);
 
 /* cpm_info - sizes: n_elec, ncons, the mesh point count and the real-space cell count. */
 int cpm_info(const cpm_ctx* ctx, int32_t* n_elec, int32_t* ncons, int64_t* mesh_points,
              int32_t* n_cells);
+
+/*
+ * cpm_matrix_layout - how S is stored: *mirror_blocks = 1 for the two mirror blocks of a
+ * mirror-symmetric doubled cell (cpm_dc_blocks), else 0; *s_bytes = bytes of stored S the S-apply
+ * streams per replica-step (float32 for CPM_MIXED, float64 for CPM_FP64, rows padded to 4).
+ * Either pointer may be NULL.
+ */
+int cpm_matrix_layout(const cpm_ctx* ctx, int32_t* mirror_blocks, int64_t* s_bytes);
 
 /*
  * cpm_status - synchronise `stream`, then return and clear the device status word: CPM_OK, or the

@@ -18,10 +18,12 @@ CPM_FF, CPM_DOUBLED, CPM_SLAB = 0, 1, 2
 CPM_FP64, CPM_MIXED = 0, 1
 GEOMETRY = {"ff": CPM_FF, "dc": CPM_DOUBLED, "slab": CPM_SLAB}
 PRECISION = {"fp64": CPM_FP64, "mixed": CPM_MIXED}
+MATRIX_KSPACE = {"ewald": 0, "mesh": 1}                 # enum cpm_matrix_kspace
+DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
-            "cpm_step_charges_static", "cpm_destroy",
+            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
 PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
           "f_gather", "f_pair_elyt", "f_pair_elec", "energy")
@@ -32,7 +34,8 @@ class CpmParams(ctypes.Structure):
     _fields_ = [("box", ctypes.c_double * 3), ("eta", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("rcut", ctypes.c_double), ("slab_factor", ctypes.c_double), ("kmax_build", ctypes.c_double),
                 ("grid", ctypes.c_int32 * 3), ("spme_order", ctypes.c_int32), ("geometry", ctypes.c_int32),
-                ("precision", ctypes.c_int32), ("max_replicas", ctypes.c_int32), ("max_elyt", ctypes.c_int32)]
+                ("precision", ctypes.c_int32), ("max_replicas", ctypes.c_int32), ("max_elyt", ctypes.c_int32),
+                ("matrix_kspace", ctypes.c_int32), ("dc_blocks", ctypes.c_int32)]
 
 
 class CPMError(RuntimeError):
@@ -66,6 +69,7 @@ def _load():
     lib.cpm_profile_read.argtypes = [vp, pd, pd]
     lib.cpm_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_step_charges_static.argtypes = [vp, pi32, pd, pd, pd, pd, pd, vp]
+    lib.cpm_matrix_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
     lib.cpm_strerror.argtypes = [ctypes.c_int]
@@ -92,7 +96,7 @@ def _check(status: int, where: str):
 
 
 def make_params(box, eta, alpha, rcut, grid, order=5, geometry="ff", precision="fp64", max_replicas=1,
-                max_elyt=1, slab_factor=3.0, kmax_build=0.0) -> CpmParams:
+                max_elyt=1, slab_factor=3.0, kmax_build=0.0, matrix_kspace="ewald", dc_blocks="auto") -> CpmParams:
     p = CpmParams()
     for d in range(3):
         p.box[d] = float(box[d])
@@ -103,6 +107,8 @@ def make_params(box, eta, alpha, rcut, grid, order=5, geometry="ff", precision="
     p.geometry = GEOMETRY[geometry] if isinstance(geometry, str) else int(geometry)
     p.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
     p.max_replicas, p.max_elyt = int(max_replicas), int(max_elyt)
+    p.matrix_kspace = MATRIX_KSPACE[matrix_kspace] if isinstance(matrix_kspace, str) else int(matrix_kspace)
+    p.dc_blocks = DC_BLOCKS[dc_blocks] if isinstance(dc_blocks, str) else int(dc_blocks)
     return p
 
 
@@ -240,6 +246,14 @@ def cpm_copy_matrix(ctx: Context, which: int) -> np.ndarray:
     out = np.zeros(shape, dtype=np.float64)
     _check(_lib.cpm_copy_matrix(ctx.handle, which, out.ctypes.data), "cpm_copy_matrix")
     return out
+
+
+def cpm_matrix_layout(ctx: Context):
+    """(mirror_blocks: bool, S bytes streamed per replica-step)."""
+    m = ctypes.c_int32()
+    nb = ctypes.c_int64()
+    _check(_lib.cpm_matrix_layout(ctx.handle, ctypes.byref(m), ctypes.byref(nb)), "cpm_matrix_layout")
+    return bool(m.value), int(nb.value)
 
 
 def cpm_status(ctx: Context, stream=None) -> int:

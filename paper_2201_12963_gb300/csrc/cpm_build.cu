@@ -5,6 +5,7 @@
 #include "cpm_internal.cuh"
 
 #include <algorithm>
+#include <unordered_map>
 #include <cstdarg>
 #include <cstring>
 #include <vector>
@@ -26,15 +27,18 @@ void set_error(const char* fmt, ...) {
 // A: real-space Gaussian-Gaussian part over every periodic image within rcut (float64).
 //   A_ij = KE sum_n (erfc(alpha r) - erfc(eta r / sqrt 2)) / r,  r = |r_i - r_j + n L| < rcut,
 //   excluding i == j at n = 0; plus the self term KE (sqrt2 eta - 2 alpha)/sqrt(pi) on the diagonal.
+// Rows and columns may be different site sets (rows[i], cols[j]; same = 1 when they coincide, which
+// enables the self exclusion and the self term); X[j * lda + i] = A(rows[i], cols[j]).
 // ------------------------------------------------------------------------------------------
-__global__ void k_build_areal(const double4_32a* __restrict__ pos, int ne, int lda, double bx, double by,
-                              double bz, const double3* __restrict__ shifts, int nshift,
-                              double alpha, double beta, double rc2, double self_term,
-                              double* __restrict__ A) {
+__global__ void k_build_areal(const double4_32a* __restrict__ rows, const double4_32a* __restrict__ cols, int n,
+                              int lda, int same, double bx, double by, double bz,
+                              const double3* __restrict__ shifts, int nshift, double alpha, double beta,
+                              double rc2, double self_term, double* __restrict__ X) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int i = blockIdx.y * blockDim.y + threadIdx.y;
-  if (i >= ne || j >= ne) return;
-  const double4_32a a = pos[i], b = pos[j];
+  if (i >= n || j >= n) return;
+  const bool diag = same && i == j;
+  const double4_32a a = rows[i], b = cols[j];
   double dx = a.x - b.x, dy = a.y - b.y, dz = a.z - b.z;
   dx -= bx * rint(dx / bx);
   dy -= by * rint(dy / by);
@@ -44,13 +48,93 @@ __global__ void k_build_areal(const double4_32a* __restrict__ pos, int ne, int l
     const double3 sh = shifts[k];
     const double x = dx + sh.x, y = dy + sh.y, z = dz + sh.z;
     const double r2 = x * x + y * y + z * z;
-    if (r2 < rc2 && !(i == j && sh.x == 0.0 && sh.y == 0.0 && sh.z == 0.0)) {
+    if (r2 < rc2 && !(diag && sh.x == 0.0 && sh.y == 0.0 && sh.z == 0.0)) {
       const double r = sqrt(r2);
       s += (erfc(alpha * r) - erfc(beta * r)) / r;
     }
   }
-  if (i == j) s += self_term;
-  A[(size_t)j * lda + i] = KE * s;   // symmetric: column-major and row-major coincide
+  if (diag) s += self_term;
+  X[(size_t)j * lda + i] = KE * s;
+}
+
+// ------------------------------------------------------------------------------------------
+// A: reciprocal part through the SPME mesh operator, A_k = W^T Phi W: W_j is the B-spline
+// stencil of site j (the fixed stencils of the per-step gather), Phi the mesh convolution with the
+// influence function G of the per-step calls.  Column j of A_k is the mesh potential of a unit
+// charge on site j gathered at every row site, so the matrix is exactly the discrete operator the
+// per-step b, forces and energy use.  Float64 throughout; one mesh per column of a batch.
+// ------------------------------------------------------------------------------------------
+// mesh[b] = unit charge of site cols[b] spread with its stencil (the p^3 points are distinct since
+// every K_d >= 2p); the meshes were cleared by the caller.
+__global__ void k_unit_spread(const int* __restrict__ cols, int nb, const int4* __restrict__ base,
+                              const double* __restrict__ th, int P, int K1, int K2, int K3, long long Mr_s,
+                              double* __restrict__ mesh) {
+  const int b = blockIdx.x;
+  if (b >= nb) return;
+  const int site = cols[b];
+  const int4 bs = base[site];
+  const double* w = th + (size_t)site * 3 * PMAX;
+  double* m = mesh + (size_t)b * Mr_s;
+  for (int t = threadIdx.x; t < P * P * P; t += blockDim.x) {
+    const int tx = t / (P * P), ty = (t / P) % P, tz = t % P;
+    const int gx = wrap_index(bs.x - tx, K1), gy = wrap_index(bs.y - ty, K2), gz = wrap_index(bs.z - tz, K3);
+    m[((size_t)gx * K2 + gy) * K3 + gz] = w[tx] * w[PMAX + ty] * w[2 * PMAX + tz];
+  }
+}
+
+__global__ void k_mul_g(double2* __restrict__ spec, const double* __restrict__ G, long long Mc, long long Mc_s,
+                        int nb) {
+  const int b = blockIdx.y;
+  if (b >= nb) return;
+  double2* c = spec + (size_t)b * Mc_s;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < Mc; k += (long long)gridDim.x * blockDim.x) {
+    const double g = G[k];
+    double2 v = c[k];
+    v.x *= g;
+    v.y *= g;
+    c[k] = v;
+  }
+}
+
+// X_o[(col0 + b) * lda + r] += sum_g W_{rows_o[r]}(g) phi_b(g), one warp per (row, column b);
+// grid.z selects the output (row set, matrix).
+struct GatherOut {
+  const int* rows[2];
+  double* X[2];
+};
+__global__ void __launch_bounds__(256) k_gather_cols(GatherOut o, int nrows, int lda, int col0, int nb,
+                                                     const int4* __restrict__ base, const double* __restrict__ th,
+                                                     int P, int K1, int K2, int K3, long long Mr_s,
+                                                     const double* __restrict__ phi) {
+  const int b = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const int r = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= nb || r >= nrows) return;
+  const int site = o.rows[blockIdx.z] ? o.rows[blockIdx.z][r] : r;
+  const int4 bs = base[site];
+  const double* w = th + (size_t)site * 3 * PMAX;
+  const double* m = phi + (size_t)b * Mr_s;
+  double acc = 0.0;
+  for (int task = lane; task < P * P; task += 32) {
+    const int ty = task / P, tz = task - ty * P;
+    const int gy = wrap_index(bs.y - ty, K2), gz = wrap_index(bs.z - tz, K3);
+    double s = 0.0;
+    for (int tx = 0; tx < P; ++tx) s += w[tx] * m[((size_t)wrap_index(bs.x - tx, K1) * K2 + gy) * K3 + gz];
+    acc += s * w[PMAX + ty] * w[2 * PMAX + tz];
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) o.X[blockIdx.z][(size_t)(col0 + b) * lda + r] += acc;
+}
+
+// Mirror blocks: (P, Q) -> (P + Q, P - Q) in place, n x n with leading dimension lda.
+__global__ void k_plus_minus(double* __restrict__ Pm, double* __restrict__ Qm, int n, int lda) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= n || j >= n) return;
+  const size_t k = (size_t)j * lda + i;
+  const double a = Pm[k], b = Qm[k];
+  Pm[k] = a + b;
+  Qm[k] = a - b;
 }
 
 // Reciprocal-space factor table for one chunk of half-space k-vectors, column-major [ne x 2kc]:
@@ -197,6 +281,8 @@ static int validate(const cpm_params* p, int32_t ne, const double* xyz, const in
   if (p->max_replicas < 1 || p->max_elyt < 1) return CPM_ERR_ARG;
   if (p->geometry == CPM_SLAB && !(p->slab_factor >= 1.0)) return CPM_ERR_ARG;
   if (p->geometry == CPM_DOUBLED && !cell) return CPM_ERR_ARG;
+  if (p->matrix_kspace != CPM_KSPACE_EWALD && p->matrix_kspace != CPM_KSPACE_MESH) return CPM_ERR_ARG;
+  if (p->dc_blocks < CPM_DC_AUTO || p->dc_blocks > CPM_DC_FULL) return CPM_ERR_ARG;
   for (int i = 0; i < ne; ++i) {
     if (side[i] != 1 && side[i] != -1) return CPM_ERR_ARG;
     if (p->geometry == CPM_DOUBLED && cell[i] != 0 && cell[i] != 1) return CPM_ERR_ARG;
@@ -264,6 +350,433 @@ static int make_plans(cpm_ctx* c) {
     c->have_plan[b] = true;
   }
   return CPM_OK;
+}
+
+// Cholesky factorisation and inverse of the SPD matrix X (n x n, lower triangle, lda) in place,
+// then the upper triangle is filled from the lower one.
+static int cholesky_inverse(cpm_ctx* c, double* X, int n, int lda, const char* what, cudaStream_t st) {
+  int lwork = 0, lwork2 = 0;
+  CPM_LIB(cusolverDnDpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, n, X, lda, &lwork) ==
+              CUSOLVER_STATUS_SUCCESS, "potrf_bufferSize");
+  CPM_LIB(cusolverDnDpotri_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, n, X, lda, &lwork2) ==
+              CUSOLVER_STATUS_SUCCESS, "potri_bufferSize");
+  lwork = std::max(lwork, lwork2);
+  double* work = nullptr;
+  int* dinfo = nullptr;
+  CPM_TRY(dev_alloc(&work, (size_t)lwork));
+  CPM_TRY(dev_alloc(&dinfo, 1));
+  int info = 0;
+  CPM_LIB(cusolverDnDpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, n, X, lda, work, lwork, dinfo) ==
+              CUSOLVER_STATUS_SUCCESS, "cusolverDnDpotrf");
+  CPM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA(cudaStreamSynchronize(st));
+  if (info != 0) {
+    cudaFree(work);
+    cudaFree(dinfo);
+    set_error("Cholesky factorisation of %s failed at column %d (not positive definite)", what, info);
+    return CPM_ERR_NOT_SPD;
+  }
+  CPM_LIB(cusolverDnDpotri(c->solver, CUBLAS_FILL_MODE_LOWER, n, X, lda, work, lwork, dinfo) ==
+              CUSOLVER_STATUS_SUCCESS, "cusolverDnDpotri");
+  CPM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA(cudaStreamSynchronize(st));
+  cudaFree(work);
+  cudaFree(dinfo);
+  if (info != 0) {
+    set_error("inverse of the Cholesky factor of %s failed (info %d)", what, info);
+    return CPM_ERR_NOT_SPD;
+  }
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  k_symmetrize_lower<<<grd, blk, 0, st>>>(X, n, lda);
+  CPM_LAUNCH();
+  return CPM_OK;
+}
+
+// Periodic image shifts within rcut (a box edge shorter than 2 rcut needs more than one image).
+static std::vector<double3> image_shifts(const cpm_ctx* c) {
+  std::vector<double3> shifts;
+  int nmax[3];
+  for (int d = 0; d < 3; ++d) nmax[d] = (int)std::floor(c->p.rcut / c->ebox[d] + 0.5);
+  for (int a = -nmax[0]; a <= nmax[0]; ++a)
+    for (int b = -nmax[1]; b <= nmax[1]; ++b)
+      for (int g = -nmax[2]; g <= nmax[2]; ++g)
+        shifts.push_back(make_double3(a * c->ebox[0], b * c->ebox[1], g * c->ebox[2]));
+  return shifts;
+}
+
+// X(rows, cols) += KE real-space Gaussian-Gaussian sums (+ self terms when same).
+static int real_space_block(cpm_ctx* c, const double4_32a* rows, const double4_32a* cols, int n, int lda, int same,
+                            double* X, cudaStream_t st) {
+  const std::vector<double3> shifts = image_shifts(c);
+  double3* dsh = nullptr;
+  CPM_TRY(upload(&dsh, shifts, st));
+  const double self = (std::sqrt(2.0) * c->p.eta - 2.0 * c->p.alpha) / std::sqrt(PI);
+  dim3 blk(32, 8), grd((n + 31) / 32, (n + 7) / 8);
+  k_build_areal<<<grd, blk, 0, st>>>(rows, cols, n, lda, same, c->ebox[0], c->ebox[1], c->ebox[2], dsh,
+                                     (int)shifts.size(), c->p.alpha, c->p.eta / std::sqrt(2.0),
+                                     c->p.rcut * c->p.rcut, self, X);
+  CPM_LAUNCH();
+  CPM_CUDA(cudaStreamSynchronize(st));
+  cudaFree(dsh);
+  return CPM_OK;
+}
+
+// Half-space k-vectors of the direct Ewald sum, (kx, ky, kz, sqrt(w_k)) with
+// w_k = 2 KE (4 pi / V) exp(-k^2 / 4 alpha^2) / k^2.
+static std::vector<double4_32a> ewald_kvectors(const cpm_ctx* c) {
+  const cpm_params& p = c->p;
+  const double kmax = p.kmax_build > 0 ? p.kmax_build : 2.0 * p.alpha * std::sqrt(27.6);
+  int mmax[3];
+  for (int d = 0; d < 3; ++d) mmax[d] = (int)std::floor(kmax * c->ebox[d] / (2.0 * PI));
+  std::vector<double4_32a> kv;
+  for (int a = -mmax[0]; a <= mmax[0]; ++a)
+    for (int b = -mmax[1]; b <= mmax[1]; ++b)
+      for (int g = -mmax[2]; g <= mmax[2]; ++g) {
+        const bool half = a > 0 || (a == 0 && b > 0) || (a == 0 && b == 0 && g > 0);
+        if (!half) continue;
+        const double kx = 2 * PI * a / c->ebox[0], ky = 2 * PI * b / c->ebox[1], kz = 2 * PI * g / c->ebox[2];
+        const double k2 = kx * kx + ky * ky + kz * kz;
+        if (k2 > kmax * kmax) continue;
+        const double wk = 2.0 * 4.0 * PI / c->V * std::exp(-k2 / (4.0 * p.alpha * p.alpha)) / k2 * KE;
+        kv.push_back(make_double4_32a(kx, ky, kz, std::sqrt(wk)));
+      }
+  return kv;
+}
+
+// Direct Ewald reciprocal sum: X += T_r T_c^T with T_s = [sqrt(w) cos(k.r), sqrt(w) sin(k.r)].
+// rows == cols: DSYRK on the lower triangle; otherwise a full DGEMM.
+static int ewald_kspace_block(cpm_ctx* c, const double4_32a* rows, const double4_32a* cols, int n, int lda,
+                              double* X, cudaStream_t st) {
+  const std::vector<double4_32a> kv = ewald_kvectors(c);
+  if (kv.empty()) return CPM_OK;
+  const int kc = 2048;
+  double4_32a* dkv = nullptr;
+  double *Tr = nullptr, *Tc = nullptr;
+  CPM_TRY(upload(&dkv, kv, st));
+  CPM_TRY(dev_alloc(&Tc, (size_t)n * 2 * kc));
+  if (rows != cols) CPM_TRY(dev_alloc(&Tr, (size_t)n * 2 * kc));
+  const double one = 1.0;
+  for (size_t k0 = 0; k0 < kv.size(); k0 += kc) {
+    const int m = (int)std::min<size_t>(kc, kv.size() - k0);
+    k_build_trig<<<dim3((n + 127) / 128, m), 128, 0, st>>>(cols, n, dkv + k0, m, Tc);
+    CPM_LAUNCH();
+    if (rows == cols) {
+      CPM_LIB(cublasDsyrk(c->cublas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, n, 2 * m, &one, Tc, n, &one, X, lda) ==
+                  CUBLAS_STATUS_SUCCESS, "cublasDsyrk");
+    } else {
+      k_build_trig<<<dim3((n + 127) / 128, m), 128, 0, st>>>(rows, n, dkv + k0, m, Tr);
+      CPM_LAUNCH();
+      CPM_LIB(cublasDgemm(c->cublas, CUBLAS_OP_N, CUBLAS_OP_T, n, n, 2 * m, &one, Tr, n, Tc, n, &one, X, lda) ==
+                  CUBLAS_STATUS_SUCCESS, "cublasDgemm");
+    }
+  }
+  CPM_CUDA(cudaStreamSynchronize(st));
+  cudaFree(Tr);
+  cudaFree(Tc);
+  cudaFree(dkv);
+  return CPM_OK;
+}
+
+// Mesh form of the reciprocal part: for every column site cols[j] (device, ncols of them) and each
+// output o < nout, X_o[j * lda + r] += (W^T Phi W)(rows_o[r], cols[j]) for r < nrows (rows_o = nullptr:
+// r itself).  Columns go through the FFTs in batches.
+static int mesh_kspace(cpm_ctx* c, const int* cols, int ncols, GatherOut o, int nout, int nrows, int lda,
+                       cudaStream_t st) {
+  const size_t per_col = sizeof(double) * c->Mr_s + sizeof(double2) * c->Mc_s;
+  int B = (int)std::max<size_t>(1, std::min<size_t>(((size_t)2 << 30) / per_col, 64));
+  B = std::min(B, ncols);
+  double* mesh = nullptr;
+  double2* spec = nullptr;
+  CPM_TRY(dev_alloc(&mesh, (size_t)B * c->Mr_s));
+  CPM_TRY(dev_alloc(&spec, (size_t)B * c->Mc_s));
+  int n[3] = {c->K[0], c->K[1], c->K[2]};
+  int nr[3] = {n[0], n[1], n[2]};
+  int nh[3] = {n[0], n[1], n[2] / 2 + 1};
+  cufftHandle fwd = 0, inv = 0;
+  CPM_LIB(cufftPlanMany(&fwd, 3, n, nr, 1, (int)c->Mr_s, nh, 1, (int)c->Mc_s, CUFFT_D2Z, B) == CUFFT_SUCCESS,
+          "cufftPlanMany(d2z, build)");
+  CPM_LIB(cufftPlanMany(&inv, 3, n, nh, 1, (int)c->Mc_s, nr, 1, (int)c->Mr_s, CUFFT_Z2D, B) == CUFFT_SUCCESS,
+          "cufftPlanMany(z2d, build)");
+  CPM_LIB(cufftSetStream(fwd, st) == CUFFT_SUCCESS, "cufftSetStream");
+  CPM_LIB(cufftSetStream(inv, st) == CUFFT_SUCCESS, "cufftSetStream");
+  const int gblocks = (int)std::min<long long>((c->Mc + 255) / 256, 152 * 8);
+  int rc = CPM_OK;
+  for (int c0 = 0; c0 < ncols && rc == CPM_OK; c0 += B) {
+    const int nb = std::min(B, ncols - c0);
+    CPM_CUDA(cudaMemsetAsync(mesh, 0, sizeof(double) * (size_t)B * c->Mr_s, st));
+    k_unit_spread<<<nb, 128, 0, st>>>(cols + c0, nb, c->e_base, c->e_th64, c->P, c->K[0], c->K[1], c->K[2], c->Mr_s,
+                                      mesh);
+    CPM_LAUNCH();
+    if (cufftExecD2Z(fwd, mesh, (cufftDoubleComplex*)spec) != CUFFT_SUCCESS) rc = CPM_ERR_LIBRARY;
+    k_mul_g<<<dim3(gblocks, nb), 256, 0, st>>>(spec, c->G64, c->Mc, c->Mc_s, nb);
+    CPM_LAUNCH();
+    if (cufftExecZ2D(inv, (cufftDoubleComplex*)spec, mesh) != CUFFT_SUCCESS) rc = CPM_ERR_LIBRARY;
+    k_gather_cols<<<dim3((nrows * 32 + 255) / 256, nb, nout), 256, 0, st>>>(o, nrows, lda, c0, nb, c->e_base,
+                                                                           c->e_th64, c->P, c->K[0], c->K[1],
+                                                                           c->K[2], c->Mr_s, mesh);
+    CPM_LAUNCH();
+  }
+  CPM_CUDA(cudaStreamSynchronize(st));
+  cufftDestroy(fwd);
+  cufftDestroy(inv);
+  cudaFree(mesh);
+  cudaFree(spec);
+  if (rc != CPM_OK) set_error("cuFFT execution failed while building the mesh part of A");
+  return rc;
+}
+
+static int kspace_block(cpm_ctx* c, const double4_32a* rows_pos, const double4_32a* cols_pos, const int* rows_idx,
+                        const int* cols_idx, int n, int lda, double* X, cudaStream_t st) {
+  if (c->p.matrix_kspace == CPM_KSPACE_MESH) {
+    GatherOut o{{rows_idx, nullptr}, {X, nullptr}};
+    return mesh_kspace(c, cols_idx, n, o, 1, n, lda, st);
+  }
+  return ewald_kspace_block(c, rows_pos, cols_pos, n, lda, X, st);
+}
+
+// Full matrix: A (ne x ne) -> S = A^-1 - A^-1 C (C^T A^-1 C)^-1 C^T A^-1, A^-1 C, S v.
+static int build_full(cpm_ctx* c, const std::vector<double>& v, const std::vector<double>& c1,
+                      const int32_t* side, cudaStream_t st) {
+  const int ne = c->ne;
+  const cpm_params& p = c->p;
+  c->ld64 = c->ld32 = c->ldx = (ne + 3) & ~3;
+  CPM_TRY(dev_alloc(&c->S64, (size_t)ne * c->ld64));
+  double* A = c->S64;
+  CPM_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)ne * c->ld64, st));
+  CPM_TRY(real_space_block(c, c->e_pos64, c->e_pos64, ne, c->ld64, 1, A, st));
+  {
+    std::vector<int> iota(ne);
+    for (int i = 0; i < ne; ++i) iota[i] = i;
+    int* d_iota = nullptr;
+    CPM_TRY(upload(&d_iota, iota, st));
+    const int r = kspace_block(c, c->e_pos64, c->e_pos64, nullptr, d_iota, ne, c->ld64, A, st);
+    cudaFree(d_iota);
+    CPM_TRY(r);
+  }
+  if (p.geometry == CPM_SLAB) {
+    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
+    k_build_slab<<<grd, blk, 0, st>>>(c->e_z, ne, c->ld64, KE * 4.0 * PI / c->V, A);
+    CPM_LAUNCH();
+  }
+  CPM_TRY(cholesky_inverse(c, A, ne, c->ld64, "A", st));
+  // ---------------- projection pieces ----------------
+  CPM_TRY(dev_alloc(&c->W, (size_t)ne * 2));
+  k_build_w<<<(ne * 32 + 255) / 256, 256, 0, st>>>(A, ne, c->ld64, c->e_c1, c->W);
+  CPM_LAUNCH();
+  std::vector<double> Wh((size_t)ne * 2);
+  CPM_CUDA(cudaMemcpyAsync(Wh.data(), c->W, sizeof(double) * ne * 2, cudaMemcpyDeviceToHost, st));
+  CPM_CUDA(cudaStreamSynchronize(st));
+  // C^T W (ncons x ncons) and its inverse M
+  double ctw[4] = {0, 0, 0, 0};
+  for (int i = 0; i < ne; ++i) {
+    ctw[0] += Wh[2 * i];                   // e^T A^-1 e
+    ctw[1] += Wh[2 * i + 1];               // e^T A^-1 e_1
+    ctw[2] += c1[i] * Wh[2 * i];           // e_1^T A^-1 e
+    ctw[3] += c1[i] * Wh[2 * i + 1];       // e_1^T A^-1 e_1
+    c->WTv[0] += Wh[2 * i] * v[i];
+    c->WTv[1] += Wh[2 * i + 1] * v[i];
+  }
+  if (c->ncons == 1) {
+    if (!(ctw[0] > 0)) { set_error("e^T A^-1 e is not positive"); return CPM_ERR_NOT_SPD; }
+    c->Mh[0] = 1.0 / ctw[0];
+  } else {
+    const double det = ctw[0] * ctw[3] - ctw[1] * ctw[2];
+    if (!(std::fabs(det) > 0)) { set_error("C^T A^-1 C is singular"); return CPM_ERR_NOT_SPD; }
+    c->Mh[0] = ctw[3] / det;
+    c->Mh[1] = -ctw[1] / det;
+    c->Mh[2] = -ctw[2] / det;
+    c->Mh[3] = ctw[0] / det;
+  }
+  {
+    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
+    k_build_s<<<grd, blk, 0, st>>>(A, ne, c->ld64, c->W, c->ncons, c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3]);
+    CPM_LAUNCH();
+  }
+  CPM_TRY(dev_alloc(&c->Sv, (size_t)ne));
+  k_matvec64<<<(ne * 32 + 255) / 256, 256, 0, st>>>(c->S64, ne, c->ld64, c->e_v, c->Sv);
+  CPM_LAUNCH();
+  {
+    std::vector<double> svh(ne);
+    CPM_CUDA(cudaMemcpyAsync(svh.data(), c->Sv, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+    c->dqdpsi = 0;
+    for (int i = 0; i < ne; ++i)
+      if (side[i] > 0) c->dqdpsi += svh[i];
+  }
+  if (c->mixed) {
+    CPM_TRY(dev_alloc(&c->S32, (size_t)ne * c->ld32));
+    k_to_float<<<dim3((c->ld32 + 255) / 256, ne), 256, 0, st>>>(c->S64, ne, c->ld64, c->S32, c->ld32);
+    CPM_LAUNCH();
+  }
+  return CPM_OK;
+}
+
+// Doubled cell whose sub-cell-1 electrode is the z-mirror image of the sub-cell-0 one: with the sites
+// ordered (sub-cell 0 in index order, then their images), A = [[P, Q], [Q, P]], P = A(I0, I0),
+// Q = A(I0, m(I0)).  With y+- = y_I0 +- y_m(I0) and the constraints e^T q = e_1^T q = 0 rewritten as
+// 1^T q+ = 1^T q- = 0, the charges are q+- = S+- y+- with S+- the singly-constrained projected
+// inverses of A+- = P +- Q, and q_I0 = (q+ + q-) / 2, q_m(I0) = (q+ - q-) / 2.  Two n x n
+// factorisations replace one 2n x 2n one, and the S-apply streams half the bytes.
+static int build_mirror(cpm_ctx* c, const std::vector<double4_32a>& pos, const std::vector<double>& v,
+                        const int32_t* side, cudaStream_t st) {
+  const int N = c->nh;
+  const int ldh = (N + 3) & ~3;
+  c->ldh = ldh;
+  c->ld64 = c->ld32 = ldh;
+  c->ldx = 2 * ldh;
+  std::vector<double4_32a> pI(N), pJ(N);
+  for (int k = 0; k < N; ++k) {
+    pI[k] = pos[c->h_i0[k]];
+    pJ[k] = pos[c->h_j[k]];
+  }
+  double4_32a *dI = nullptr, *dJ = nullptr;
+  CPM_TRY(upload(&dI, pI, st));
+  CPM_TRY(upload(&dJ, pJ, st));
+  CPM_TRY(upload(&c->m_i0, c->h_i0, st));
+  CPM_TRY(upload(&c->m_j, c->h_j, st));
+  CPM_TRY(dev_alloc(&c->S64, (size_t)2 * N * ldh));
+  double* Pm = c->S64;
+  double* Qm = c->S64 + (size_t)N * ldh;
+  CPM_CUDA(cudaMemsetAsync(c->S64, 0, sizeof(double) * (size_t)2 * N * ldh, st));
+  CPM_TRY(real_space_block(c, dI, dI, N, ldh, 1, Pm, st));
+  CPM_TRY(real_space_block(c, dJ, dI, N, ldh, 0, Qm, st));
+  if (c->p.matrix_kspace == CPM_KSPACE_MESH) {
+    GatherOut o{{c->m_i0, c->m_j}, {Pm, Qm}};
+    CPM_TRY(mesh_kspace(c, c->m_i0, N, o, 2, N, ldh, st));
+  } else {
+    CPM_TRY(ewald_kspace_block(c, dI, dI, N, ldh, Pm, st));
+    CPM_TRY(ewald_kspace_block(c, dJ, dI, N, ldh, Qm, st));
+  }
+  cudaFree(dI);
+  cudaFree(dJ);
+  {
+    dim3 blk(32, 8), grd((N + 31) / 32, (N + 7) / 8);
+    k_plus_minus<<<grd, blk, 0, st>>>(Pm, Qm, N, ldh);
+    CPM_LAUNCH();
+  }
+  CPM_TRY(cholesky_inverse(c, Pm, N, ldh, "A+ = P + Q", st));
+  CPM_TRY(cholesky_inverse(c, Qm, N, ldh, "A- = P - Q", st));
+  // constraint indicator of the S-apply rows: zeros (A+ block), ones (A- block)
+  std::vector<double> c1m(2 * (size_t)N, 0.0);
+  for (int k = 0; k < N; ++k) c1m[N + k] = 1.0;
+  CPM_TRY(upload(&c->e_c1m, c1m, st));
+  // w+- = A+-^-1 1, M+- = 1 / 1^T w+-, S+- = A+-^-1 - w+- M+- w+-^T
+  double* wtmp = nullptr;
+  CPM_TRY(dev_alloc(&wtmp, (size_t)2 * N));
+  std::vector<double> wpm[2];
+  for (int blk = 0; blk < 2; ++blk) {
+    double* X = blk ? Qm : Pm;
+    k_build_w<<<(N * 32 + 255) / 256, 256, 0, st>>>(X, N, ldh, c->e_c1m, wtmp);   // e_c1m[0..N) = 0
+    CPM_LAUNCH();
+    std::vector<double> h(2 * (size_t)N);
+    CPM_CUDA(cudaMemcpyAsync(h.data(), wtmp, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+    double sum = 0;
+    wpm[blk].resize(N);
+    for (int k = 0; k < N; ++k) {
+      wpm[blk][k] = h[2 * k];
+      sum += h[2 * k];
+    }
+    if (!(sum > 0)) {
+      cudaFree(wtmp);
+      set_error("1^T A%c^-1 1 is not positive", blk ? '-' : '+');
+      return CPM_ERR_NOT_SPD;
+    }
+    c->Mh[blk] = 1.0 / sum;
+    dim3 b2(32, 8), grd((N + 31) / 32, (N + 7) / 8);
+    k_build_s<<<grd, b2, 0, st>>>(X, N, ldh, wtmp, 1, c->Mh[blk], 0.0, 0.0, 0.0);
+    CPM_LAUNCH();
+  }
+  CPM_CUDA(cudaStreamSynchronize(st));
+  cudaFree(wtmp);
+  c->Mh[2] = c->Mh[3] = 0.0;
+  // W in the S-apply epilogue's interleaved layout: rows of block + carry (w+, 0), rows of block - (0, w-)
+  std::vector<double> Wint(4 * (size_t)N, 0.0), vpm(2 * (size_t)N);
+  c->WTv[0] = c->WTv[1] = 0.0;
+  for (int k = 0; k < N; ++k) {
+    Wint[2 * k] = wpm[0][k];
+    Wint[2 * (size_t)N + 2 * k + 1] = wpm[1][k];
+    vpm[k] = v[c->h_i0[k]] + v[c->h_j[k]];
+    vpm[N + k] = v[c->h_i0[k]] - v[c->h_j[k]];
+    c->WTv[0] += wpm[0][k] * vpm[k];
+    c->WTv[1] += wpm[1][k] * vpm[N + k];
+  }
+  CPM_TRY(upload(&c->W, Wint, st));
+  double* dv = nullptr;
+  CPM_TRY(upload(&dv, vpm, st));
+  CPM_TRY(dev_alloc(&c->Sv, (size_t)2 * N));
+  k_matvec64<<<(N * 32 + 255) / 256, 256, 0, st>>>(Pm, N, ldh, dv, c->Sv);
+  CPM_LAUNCH();
+  k_matvec64<<<(N * 32 + 255) / 256, 256, 0, st>>>(Qm, N, ldh, dv + N, c->Sv + N);
+  CPM_LAUNCH();
+  {
+    std::vector<double> svh(2 * (size_t)N);
+    CPM_CUDA(cudaMemcpyAsync(svh.data(), c->Sv, sizeof(double) * 2 * N, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+    c->dqdpsi = 0;
+    for (int k = 0; k < N; ++k) {
+      if (side[c->h_i0[k]] > 0) c->dqdpsi += 0.5 * (svh[k] + svh[N + k]);
+      if (side[c->h_j[k]] > 0) c->dqdpsi += 0.5 * (svh[k] - svh[N + k]);
+    }
+  }
+  cudaFree(dv);
+  if (c->mixed) {
+    CPM_TRY(dev_alloc(&c->S32, (size_t)2 * N * ldh));
+    k_to_float<<<dim3((ldh + 255) / 256, 2 * N), 256, 0, st>>>(c->S64, N, ldh, c->S32, ldh);
+    CPM_LAUNCH();
+  }
+  return CPM_OK;
+}
+
+// Pairs every sub-cell-0 site with the sub-cell-1 site at its z-mirror image (x, y, L_z - z)
+// (L_z the doubled length) within 1e-6 A; false if the electrode is not mirror-symmetric.
+static bool find_mirror(cpm_ctx* c, const std::vector<double4_32a>& pos, const int32_t* cell) {
+  const int ne = c->ne;
+  int n0 = 0;
+  for (int i = 0; i < ne; ++i) n0 += cell[i] == 0;
+  if (2 * n0 != ne) return false;
+  const double h = 1e-3, tol = 1e-6;
+  long long nk[3];
+  for (int d = 0; d < 3; ++d) nk[d] = std::max(1LL, (long long)std::ceil(c->ebox[d] / h));
+  auto idx = [&](double x, int d) { return ((long long)std::floor(x / h) % nk[d] + nk[d]) % nk[d]; };
+  auto key = [&](long long a, long long b, long long g) { return (a * nk[1] + b) * nk[2] + g; };
+  std::unordered_map<long long, std::vector<int>> grid;
+  for (int i = 0; i < ne; ++i)
+    if (cell[i] == 1) grid[key(idx(pos[i].x, 0), idx(pos[i].y, 1), idx(pos[i].z, 2))].push_back(i);
+  std::vector<char> used(ne, 0);
+  c->h_i0.clear();
+  c->h_j.clear();
+  for (int i = 0; i < ne; ++i) {
+    if (cell[i] != 0) continue;
+    const double t[3] = {pos[i].x, pos[i].y, wrap_coord(c->ebox[2] - pos[i].z, c->ebox[2])};
+    const long long k0[3] = {idx(t[0], 0), idx(t[1], 1), idx(t[2], 2)};
+    int found = -1;
+    for (int a = -1; a <= 1 && found < 0; ++a)
+      for (int b = -1; b <= 1 && found < 0; ++b)
+        for (int g = -1; g <= 1 && found < 0; ++g) {
+          auto it = grid.find(key((k0[0] + a + nk[0]) % nk[0], (k0[1] + b + nk[1]) % nk[1], (k0[2] + g + nk[2]) % nk[2]));
+          if (it == grid.end()) continue;
+          for (int j : it->second) {
+            if (used[j]) continue;
+            const double r[3] = {pos[j].x, pos[j].y, pos[j].z};
+            bool ok = true;
+            for (int d = 0; d < 3 && ok; ++d) {
+              double dd = r[d] - t[d];
+              dd -= c->ebox[d] * std::rint(dd / c->ebox[d]);
+              ok = std::fabs(dd) < tol;
+            }
+            if (ok) {
+              found = j;
+              break;
+            }
+          }
+        }
+    if (found < 0) return false;
+    used[found] = 1;
+    c->h_i0.push_back(i);
+    c->h_j.push_back(found);
+  }
+  return true;
 }
 
 static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side, const int32_t* cell,
@@ -374,163 +887,31 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
   CPM_TRY(upload(&c->e_c1, c1, st));
   CPM_TRY(upload(&c->e_plus, eplus, st));
 
-  // ---------------- A in float64 ----------------
-  c->ld64 = (ne + 3) & ~3;
-  c->ld32 = (ne + 3) & ~3;
-  CPM_TRY(dev_alloc(&c->S64, (size_t)ne * c->ld64));
-  double* A = c->S64;
-  CPM_CUDA(cudaMemsetAsync(A, 0, sizeof(double) * (size_t)ne * c->ld64, st));
+  // ---------------- SPME influence function (the mesh form of A uses it) ----------------
   {
-    std::vector<double3> shifts;
-    int nmax[3];
-    for (int d = 0; d < 3; ++d) nmax[d] = (int)std::floor(p.rcut / c->ebox[d] + 0.5);
-    for (int a = -nmax[0]; a <= nmax[0]; ++a)
-      for (int b = -nmax[1]; b <= nmax[1]; ++b)
-        for (int g = -nmax[2]; g <= nmax[2]; ++g)
-          shifts.push_back(make_double3(a * c->ebox[0], b * c->ebox[1], g * c->ebox[2]));
-    double3* dsh = nullptr;
-    CPM_TRY(upload(&dsh, shifts, st));
-    const double self = (std::sqrt(2.0) * p.eta - 2.0 * p.alpha) / std::sqrt(PI);
-    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
-    k_build_areal<<<grd, blk, 0, st>>>(c->e_pos64, ne, c->ld64, c->ebox[0], c->ebox[1], c->ebox[2], dsh,
-                                       (int)shifts.size(), p.alpha, p.eta / std::sqrt(2.0),
-                                       p.rcut * p.rcut, self, A);
-    CPM_LAUNCH();
-    CPM_CUDA(cudaStreamSynchronize(st));
-    cudaFree(dsh);
+    std::vector<double> G;
+    influence_host(c, G);
+    CPM_TRY(upload(&c->G64, G, st));
+    std::vector<float> G32(G.begin(), G.end());
+    CPM_TRY(upload(&c->G32, G32, st));
   }
-  // reciprocal part: direct Ewald sum over half-space k (weights 2 * 4 pi / V exp(-k^2/4a^2)/k^2)
-  {
-    const double kmax = p.kmax_build > 0 ? p.kmax_build : 2.0 * p.alpha * std::sqrt(27.6);
-    int mmax[3];
-    for (int d = 0; d < 3; ++d) mmax[d] = (int)std::floor(kmax * c->ebox[d] / (2.0 * PI));
-    std::vector<double4_32a> kv;
-    for (int a = -mmax[0]; a <= mmax[0]; ++a)
-      for (int b = -mmax[1]; b <= mmax[1]; ++b)
-        for (int g = -mmax[2]; g <= mmax[2]; ++g) {
-          const bool half = a > 0 || (a == 0 && b > 0) || (a == 0 && b == 0 && g > 0);
-          if (!half) continue;
-          const double kx = 2 * PI * a / c->ebox[0], ky = 2 * PI * b / c->ebox[1], kz = 2 * PI * g / c->ebox[2];
-          const double k2 = kx * kx + ky * ky + kz * kz;
-          if (k2 > kmax * kmax) continue;
-          const double wk = 2.0 * 4.0 * PI / c->V * std::exp(-k2 / (4.0 * p.alpha * p.alpha)) / k2 * KE;
-          kv.push_back(make_double4_32a(kx, ky, kz, std::sqrt(wk)));
-        }
-    if (!kv.empty()) {
-      const int kc = 2048;
-      double4_32a* dkv = nullptr;
-      double* T = nullptr;
-      CPM_TRY(upload(&dkv, kv, st));
-      CPM_TRY(dev_alloc(&T, (size_t)ne * 2 * kc));
-      CPM_LIB(cublasCreate(&c->cublas) == CUBLAS_STATUS_SUCCESS, "cublasCreate");
-      CPM_LIB(cublasSetStream(c->cublas, st) == CUBLAS_STATUS_SUCCESS, "cublasSetStream");
-      const double one = 1.0;
-      for (size_t k0 = 0; k0 < kv.size(); k0 += kc) {
-        const int n = (int)std::min<size_t>(kc, kv.size() - k0);
-        k_build_trig<<<dim3((ne + 127) / 128, n), 128, 0, st>>>(c->e_pos64, ne, dkv + k0, n, T);
-        CPM_LAUNCH();
-        CPM_LIB(cublasDsyrk(c->cublas, CUBLAS_FILL_MODE_LOWER, CUBLAS_OP_N, ne, 2 * n, &one, T, ne, &one, A,
-                            c->ld64) == CUBLAS_STATUS_SUCCESS, "cublasDsyrk");
-      }
-      CPM_CUDA(cudaStreamSynchronize(st));
-      cudaFree(T);
-      cudaFree(dkv);
-    }
-  }
-  if (p.geometry == CPM_SLAB) {
-    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
-    k_build_slab<<<grd, blk, 0, st>>>(c->e_z, ne, c->ld64, KE * 4.0 * PI / c->V, A);
-    CPM_LAUNCH();
-  }
-
-  // ---------------- Cholesky and inverse (float64) ----------------
+  // ---------------- A, its inverse and the projection pieces (float64) ----------------
+  CPM_LIB(cublasCreate(&c->cublas) == CUBLAS_STATUS_SUCCESS, "cublasCreate");
+  CPM_LIB(cublasSetStream(c->cublas, st) == CUBLAS_STATUS_SUCCESS, "cublasSetStream");
   CPM_LIB(cusolverDnCreate(&c->solver) == CUSOLVER_STATUS_SUCCESS, "cusolverDnCreate");
   CPM_LIB(cusolverDnSetStream(c->solver, st) == CUSOLVER_STATUS_SUCCESS, "cusolverDnSetStream");
-  {
-    int lwork = 0, lwork2 = 0;
-    CPM_LIB(cusolverDnDpotrf_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, &lwork) ==
-                CUSOLVER_STATUS_SUCCESS, "potrf_bufferSize");
-    CPM_LIB(cusolverDnDpotri_bufferSize(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, &lwork2) ==
-                CUSOLVER_STATUS_SUCCESS, "potri_bufferSize");
-    lwork = std::max(lwork, lwork2);
-    double* work = nullptr;
-    int* dinfo = nullptr;
-    CPM_TRY(dev_alloc(&work, (size_t)lwork));
-    CPM_TRY(dev_alloc(&dinfo, 1));
-    int info = 0;
-    CPM_LIB(cusolverDnDpotrf(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, work, lwork, dinfo) ==
-                CUSOLVER_STATUS_SUCCESS, "cusolverDnDpotrf");
-    CPM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CPM_CUDA(cudaStreamSynchronize(st));
-    if (info != 0) {
-      cudaFree(work);
-      cudaFree(dinfo);
-      set_error("Cholesky factorisation of A failed at column %d (A not positive definite)", info);
-      return CPM_ERR_NOT_SPD;
+  c->ldb = (ne + 3) & ~3;
+  c->mirror = false;
+  if (p.geometry == CPM_DOUBLED && p.dc_blocks != CPM_DC_FULL) {
+    c->mirror = find_mirror(c, pos, cell);
+    if (!c->mirror && p.dc_blocks == CPM_DC_MIRROR) {
+      set_error("dc_blocks = CPM_DC_MIRROR, but the sub-cell-1 electrode is not the z-mirror image of sub-cell 0");
+      return CPM_ERR_ARG;
     }
-    CPM_LIB(cusolverDnDpotri(c->solver, CUBLAS_FILL_MODE_LOWER, ne, A, c->ld64, work, lwork, dinfo) ==
-                CUSOLVER_STATUS_SUCCESS, "cusolverDnDpotri");
-    CPM_CUDA(cudaMemcpyAsync(&info, dinfo, sizeof(int), cudaMemcpyDeviceToHost, st));
-    CPM_CUDA(cudaStreamSynchronize(st));
-    cudaFree(work);
-    cudaFree(dinfo);
-    if (info != 0) {
-      set_error("inverse of the Cholesky factor failed (info %d)", info);
-      return CPM_ERR_NOT_SPD;
-    }
-    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
-    k_symmetrize_lower<<<grd, blk, 0, st>>>(A, ne, c->ld64);
-    CPM_LAUNCH();
+    c->nh = ne / 2;
   }
-  // ---------------- projection pieces ----------------
-  CPM_TRY(dev_alloc(&c->W, (size_t)ne * 2));
-  k_build_w<<<(ne * 32 + 255) / 256, 256, 0, st>>>(A, ne, c->ld64, c->e_c1, c->W);
-  CPM_LAUNCH();
-  std::vector<double> Wh((size_t)ne * 2);
-  CPM_CUDA(cudaMemcpyAsync(Wh.data(), c->W, sizeof(double) * ne * 2, cudaMemcpyDeviceToHost, st));
-  CPM_CUDA(cudaStreamSynchronize(st));
-  // C^T W (ncons x ncons) and its inverse M
-  double ctw[4] = {0, 0, 0, 0};
-  for (int i = 0; i < ne; ++i) {
-    ctw[0] += Wh[2 * i];                   // e^T A^-1 e
-    ctw[1] += Wh[2 * i + 1];               // e^T A^-1 e_1
-    ctw[2] += c1[i] * Wh[2 * i];           // e_1^T A^-1 e
-    ctw[3] += c1[i] * Wh[2 * i + 1];       // e_1^T A^-1 e_1
-    c->WTv[0] += Wh[2 * i] * v[i];
-    c->WTv[1] += Wh[2 * i + 1] * v[i];
-  }
-  if (c->ncons == 1) {
-    if (!(ctw[0] > 0)) { set_error("e^T A^-1 e is not positive"); return CPM_ERR_NOT_SPD; }
-    c->Mh[0] = 1.0 / ctw[0];
-  } else {
-    const double det = ctw[0] * ctw[3] - ctw[1] * ctw[2];
-    if (!(std::fabs(det) > 0)) { set_error("C^T A^-1 C is singular"); return CPM_ERR_NOT_SPD; }
-    c->Mh[0] = ctw[3] / det;
-    c->Mh[1] = -ctw[1] / det;
-    c->Mh[2] = -ctw[2] / det;
-    c->Mh[3] = ctw[0] / det;
-  }
-  {
-    dim3 blk(32, 8), grd((ne + 31) / 32, (ne + 7) / 8);
-    k_build_s<<<grd, blk, 0, st>>>(A, ne, c->ld64, c->W, c->ncons, c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3]);
-    CPM_LAUNCH();
-  }
-  CPM_TRY(dev_alloc(&c->Sv, (size_t)ne));
-  k_matvec64<<<(ne * 32 + 255) / 256, 256, 0, st>>>(c->S64, ne, c->ld64, c->e_v, c->Sv);
-  CPM_LAUNCH();
-  {
-    std::vector<double> svh(ne);
-    CPM_CUDA(cudaMemcpyAsync(svh.data(), c->Sv, sizeof(double) * ne, cudaMemcpyDeviceToHost, st));
-    CPM_CUDA(cudaStreamSynchronize(st));
-    c->dqdpsi = 0;
-    for (int i = 0; i < ne; ++i)
-      if (side[i] > 0) c->dqdpsi += svh[i];
-  }
-  if (c->mixed) {
-    CPM_TRY(dev_alloc(&c->S32, (size_t)ne * c->ld32));
-    k_to_float<<<dim3((c->ld32 + 255) / 256, ne), 256, 0, st>>>(c->S64, ne, c->ld64, c->S32, c->ld32);
-    CPM_LAUNCH();
-  }
+  if (c->mirror) CPM_TRY(build_mirror(c, pos, v, side, st));
+  else CPM_TRY(build_full(c, v, c1, side, st));
 
   // ---------------- SPME ----------------
   {
@@ -550,13 +931,6 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
     CPM_TRY(upload(&c->spl_I, sI, st));
     CPM_TRY(upload(&c->spl_F64, sF, st));
     CPM_TRY(upload(&c->spl_F32, sF32, st));
-  }
-  {
-    std::vector<double> G;
-    influence_host(c, G);
-    CPM_TRY(upload(&c->G64, G, st));
-    std::vector<float> G32(G.begin(), G.end());
-    CPM_TRY(upload(&c->G32, G32, st));
   }
   CPM_TRY(make_plans(c));
   CPM_TRY(cpm_internal_alloc_step_buffers(c));
@@ -600,7 +974,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
-                  c->scal, c->status};
+                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int b = 0; b < 2; ++b)
@@ -624,6 +998,47 @@ extern "C" int cpm_capacitance(const cpm_ctx* c, double* out) {
 
 extern "C" int cpm_copy_matrix(const cpm_ctx* c, int32_t which, double* host_out) {
   if (!c || !host_out) return CPM_ERR_ARG;
+  if (c->mirror) {
+    // q_I0 = (q+ + q-) / 2, q_J = (q+ - q-) / 2 with q+- = S+- (y_I0 +- y_J): S(I0, I0) = S(J, J) =
+    // (S+ + S-) / 2, S(I0, J) = S(J, I0) = (S+ - S-) / 2; A^-1 e = (w+, w+), A^-1 e_1 = ((w+ - w-)/2, (w+ + w-)/2)
+    const int N = c->nh, ne = c->ne;
+    const std::vector<int>& I = c->h_i0;
+    const std::vector<int>& J = c->h_j;
+    if (which == 0) {
+      std::vector<double> S((size_t)2 * N * c->ldh);
+      CPM_CUDA(cudaMemcpy(S.data(), c->S64, sizeof(double) * S.size(), cudaMemcpyDeviceToHost));
+      const double* Sp = S.data();
+      const double* Sm = S.data() + (size_t)N * c->ldh;
+      for (int k = 0; k < N; ++k)
+        for (int l = 0; l < N; ++l) {
+          const double sp = Sp[(size_t)k * c->ldh + l], sm = Sm[(size_t)k * c->ldh + l];
+          host_out[(size_t)I[k] * ne + I[l]] = 0.5 * (sp + sm);
+          host_out[(size_t)J[k] * ne + J[l]] = 0.5 * (sp + sm);
+          host_out[(size_t)I[k] * ne + J[l]] = 0.5 * (sp - sm);
+          host_out[(size_t)J[k] * ne + I[l]] = 0.5 * (sp - sm);
+        }
+    } else if (which == 1) {
+      std::vector<double> sv(2 * (size_t)N);
+      CPM_CUDA(cudaMemcpy(sv.data(), c->Sv, sizeof(double) * sv.size(), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < N; ++k) {
+        host_out[I[k]] = 0.5 * (sv[k] + sv[N + k]);
+        host_out[J[k]] = 0.5 * (sv[k] - sv[N + k]);
+      }
+    } else if (which == 2) {
+      std::vector<double> w(4 * (size_t)N);
+      CPM_CUDA(cudaMemcpy(w.data(), c->W, sizeof(double) * w.size(), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < N; ++k) {
+        const double wp = w[2 * k], wm = w[2 * (size_t)N + 2 * k + 1];
+        host_out[(size_t)I[k] * 2 + 0] = wp;
+        host_out[(size_t)J[k] * 2 + 0] = wp;
+        host_out[(size_t)I[k] * 2 + 1] = 0.5 * (wp - wm);
+        host_out[(size_t)J[k] * 2 + 1] = 0.5 * (wp + wm);
+      }
+    } else {
+      return CPM_ERR_ARG;
+    }
+    return CPM_OK;
+  }
   if (which == 0) {
     CPM_CUDA(cudaMemcpy2D(host_out, sizeof(double) * c->ne, c->S64, sizeof(double) * c->ld64,
                           sizeof(double) * c->ne, c->ne, cudaMemcpyDeviceToHost));
@@ -636,6 +1051,16 @@ extern "C" int cpm_copy_matrix(const cpm_ctx* c, int32_t which, double* host_out
       for (int k = 0; k < c->ncons; ++k) host_out[(size_t)i * c->ncons + k] = w[2 * i + k];
   } else {
     return CPM_ERR_ARG;
+  }
+  return CPM_OK;
+}
+
+extern "C" int cpm_matrix_layout(const cpm_ctx* c, int32_t* mirror_blocks, int64_t* s_bytes) {
+  if (!c) return CPM_ERR_ARG;
+  if (mirror_blocks) *mirror_blocks = c->mirror ? 1 : 0;
+  if (s_bytes) {
+    const long long rows = c->mirror ? 2LL * c->nh : (long long)c->ne;
+    *s_bytes = rows * (long long)c->ld64 * (c->mixed ? 4 : 8);
   }
   return CPM_OK;
 }

@@ -11,6 +11,7 @@
 #include <cstdint>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "../../include/cpm.h"
 
@@ -79,14 +80,27 @@ struct cpm_ctx {
   double* e_v = nullptr;        // [ne] geometry vector v
   double* e_c1 = nullptr;       // [ne] e_1 indicator (doubled cell) or zeros
   double* e_plus = nullptr;     // [ne] 1 on side +1 sites, else 0
-  // matrices
+  // matrices.  Full form: S64/S32 [ne][ld] (ld = ld64 = ld32), W [ne][2], Sv [ne].
+  // Mirror form (doubled cell, mirror-symmetric electrode): S64/S32 = [S+ ; S-], each [nh][ldh];
+  // W [2][nh][2] = rows of S+ carry (w+, 0) and rows of S- (0, w-) with w+- = A+-^-1 1; Sv = [S+ v+ ; S- v-];
+  // Mh[0], Mh[1] = 1 / 1^T w+-; WTv = (w+^T v+, w-^T v-).
   int ld64 = 0, ld32 = 0;
-  double* S64 = nullptr;        // [ne][ld64] row-major projected inverse
-  float* S32 = nullptr;         // [ne][ld32] float copy (mixed precision)
-  double* W = nullptr;          // [ne][2] A^-1 C (second column zero unless doubled)
-  double* Sv = nullptr;         // [ne]
+  int ldb = 0;                  // row stride of b_tmp (ne rounded up to 4)
+  int ldx = 0;                  // length of one half (hi or lo) of a replica's b32 row
+  double* S64 = nullptr;        // projected inverse, float64 master
+  float* S32 = nullptr;         // float copy (mixed precision)
+  double* W = nullptr;          // A^-1 C (second column zero unless doubled)
+  double* Sv = nullptr;
   double Mh[4] = {0, 0, 0, 0};  // (C^T A^-1 C)^-1, host
   double WTv[2] = {0, 0};       // (A^-1 C)^T v, host
+  bool mirror = false;          // mirror-block form
+  int nh = 0, ldh = 0;          // sites per sub-cell and the block row stride (mirror form)
+  int* m_i0 = nullptr;          // [nh] original index of block row k (a sub-cell-0 site)
+  int* m_j = nullptr;           // [nh] original index of its mirror image
+  std::vector<int> h_i0, h_j;   // host copies
+  double* e_c1m = nullptr;      // [2 nh] zeros then ones (constraint indicator of the S-apply rows)
+  double* ypm = nullptr;        // [max_rep][2 ldh] y+ = b_I0 + b_m(I0), y- = b_I0 - b_m(I0)
+  double* qpm = nullptr;        // [max_rep][2 nh] q+, q- before the projection
   double dqdpsi = 0;
   // SPME
   int K[3] = {0, 0, 0};
@@ -118,7 +132,7 @@ struct cpm_ctx {
   // per-replica buffers
   double* phi_real = nullptr;   // [max_rep][ne]
   double* b_tmp = nullptr;      // [max_rep][ne]
-  float* b32 = nullptr;         // [max_rep][2][ld32] float32 high / low split of b (mixed S-apply)
+  float* b32 = nullptr;         // [max_rep][2][ldx] float32 high / low split of the S-apply input (mixed)
   float* qraw32 = nullptr;      // [max_rep][ne] tensor-core S-apply output S b (mixed, batched)
   double* scal = nullptr;       // [max_rep][NSCAL]
   int* status = nullptr;        // device status word

@@ -566,13 +566,13 @@ __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const 
 
 // b_i = -(KE phi_real_i + phi_mesh_i) (- KE 4 pi / V z_i sum_j Q_j Z_j for the slab), one warp per site,
 // written to b (row stride ldb); with b32 != nullptr also the float32 split b = hi + lo
-// (hi = fl(b), lo = fl(b - hi)) for the mixed-precision S-apply, rows of stride ld32.
+// (hi = fl(b), lo = fl(b - hi)) for the mixed-precision S-apply, halves of length ldx.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int ne, const int4* __restrict__ base,
                                                   const T* __restrict__ th, SpmeGeom sg,
                                                   const double* __restrict__ phi_real, const double* __restrict__ ez,
                                                   double slab_coef, const double* __restrict__ scal,
-                                                  double* __restrict__ b, float* __restrict__ b32, int ld32,
+                                                  double* __restrict__ b, float* __restrict__ b32, int ldx,
                                                   int ldb) {
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
@@ -599,8 +599,8 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
       b[(size_t)rep * ldb + i] = bi;
       if (b32) {
         const float hi = (float)bi;
-        b32[(size_t)rep * 2 * ld32 + i] = hi;
-        b32[(size_t)rep * 2 * ld32 + ld32 + i] = (float)(bi - (double)hi);
+        b32[(size_t)rep * 2 * ldx + i] = hi;
+        b32[(size_t)rep * 2 * ldx + ldx + i] = (float)(bi - (double)hi);
       }
     }
   }
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
 // The epilogue accumulates C^T q_raw and (A^-1 C)^T b for the projection.
 // ------------------------------------------------------------------------------------------
 template <int R>
-__device__ __forceinline__ void sapply_epilogue(int i, int lane, int rep0, int nrep, int ne, const double (&tot)[R],
+__device__ __forceinline__ void sapply_epilogue(int i, int lane, int rep0, int nrep, int qstride, const double (&tot)[R],
                                                 const double* __restrict__ b, int ldb, const double* __restrict__ dpsi,
                                                 const double* __restrict__ Sv, const double* __restrict__ W,
                                                 const double* __restrict__ c1, double* __restrict__ qout,
@@ -734,7 +734,7 @@ __device__ __forceinline__ void sapply_epilogue(int i, int lane, int rep0, int n
     const int rr = rep0 + r;
     if (rr >= nrep) break;
     const double qr = tot[r] + dpsi[rr] * svi;
-    qout[(size_t)rr * ne + i] = qr;
+    qout[(size_t)rr * qstride + i] = qr;
     const double bi = b[(size_t)rr * ldb + i];
     red[4 * r + 0] += qr;
     red[4 * r + 1] += qr * cc;
@@ -762,11 +762,11 @@ __device__ __forceinline__ void sapply_reduce(const double (&red)[4 * R], int re
 
 template <int R>
 __global__ void __launch_bounds__(256) k_sapply32(const float* __restrict__ S, int ld, int ne,
-                                                  const float* __restrict__ b32, const double* __restrict__ b,
-                                                  int ldb, int rep0, int nrep, const double* __restrict__ dpsi,
-                                                  const double* __restrict__ Sv, const double* __restrict__ W,
-                                                  const double* __restrict__ c1, double* __restrict__ qout,
-                                                  double* __restrict__ scal) {
+                                                  const float* __restrict__ b32, int xstride, int xlo,
+                                                  const double* __restrict__ b, int ldb, int rep0, int nrep,
+                                                  const double* __restrict__ dpsi, const double* __restrict__ Sv,
+                                                  const double* __restrict__ W, const double* __restrict__ c1,
+                                                  double* __restrict__ qout, int qstride, double* __restrict__ scal) {
   const int lane = threadIdx.x & 31;
   const int n4 = ld >> 2;
   double red[4 * R];
@@ -777,8 +777,8 @@ __global__ void __launch_bounds__(256) k_sapply32(const float* __restrict__ S, i
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int rr = min(rep0 + r, nrep - 1);
-    yh[r] = reinterpret_cast<const float4*>(b32 + (size_t)rr * 2 * ld);
-    yl[r] = reinterpret_cast<const float4*>(b32 + (size_t)rr * 2 * ld + ld);
+    yh[r] = reinterpret_cast<const float4*>(b32 + (size_t)rr * xstride);
+    yl[r] = reinterpret_cast<const float4*>(b32 + (size_t)rr * xstride + xlo);
   }
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const float4* row = reinterpret_cast<const float4*>(S + (size_t)i * ld);
@@ -812,7 +812,7 @@ __global__ void __launch_bounds__(256) k_sapply32(const float* __restrict__ S, i
       acc[r].warp_reduce();
       tot[r] = acc[r].value();
     }
-    sapply_epilogue<R>(i, lane, rep0, nrep, ne, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
+    sapply_epilogue<R>(i, lane, rep0, nrep, qstride, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
   }
   sapply_reduce<R>(red, rep0, nrep, scal);
 }
@@ -822,7 +822,7 @@ __global__ void __launch_bounds__(256) k_sapply64(const double* __restrict__ S, 
                                                   const double* __restrict__ b, int ldb, int rep0, int nrep,
                                                   const double* __restrict__ dpsi, const double* __restrict__ Sv,
                                                   const double* __restrict__ W, const double* __restrict__ c1,
-                                                  double* __restrict__ qout, double* __restrict__ scal) {
+                                                  double* __restrict__ qout, int qstride, double* __restrict__ scal) {
   const int lane = threadIdx.x & 31;
   double red[4 * R];
 #pragma unroll
@@ -847,7 +847,7 @@ __global__ void __launch_bounds__(256) k_sapply64(const double* __restrict__ S, 
     double tot[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) tot[r] = warp_sum(acc[r]);
-    sapply_epilogue<R>(i, lane, rep0, nrep, ne, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
+    sapply_epilogue<R>(i, lane, rep0, nrep, qstride, tot, b, ldb, dpsi, Sv, W, c1, qout, red);
   }
   sapply_reduce<R>(red, rep0, nrep, scal);
 }
@@ -1076,6 +1076,66 @@ __global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne,
   block_atomic_add<1>(qb, dst);
 }
 
+// Mirror form, before the S-apply: y+- = b_I0 +- b_J per mirror pair (float64, rows of length
+// 2 ldh: y+ at [0, nh), y- at [ldh, ldh + nh)); with x32 != nullptr also the float32 hi / lo split,
+// halves of length ldx = 2 ldh.  (The dpsi v part enters through S v.)
+__global__ void __launch_bounds__(256) k_mirror_fold(const double* __restrict__ b, int ldb, int nh, int ldh,
+                                                     const int* __restrict__ i0, const int* __restrict__ jm,
+                                                     double* __restrict__ y, float* __restrict__ x32) {
+  const int rep = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nh) return;
+  const double bi = b[(size_t)rep * ldb + i0[k]], bj = b[(size_t)rep * ldb + jm[k]];
+  const double yp = bi + bj, ym = bi - bj;
+  double* yr = y + (size_t)rep * 2 * ldh;
+  yr[k] = yp;
+  yr[ldh + k] = ym;
+  if (x32) {
+    float* xr = x32 + (size_t)rep * 4 * ldh;
+    const float hp = (float)yp, hm = (float)ym;
+    xr[k] = hp;
+    xr[ldh + k] = hm;
+    xr[2 * ldh + k] = (float)(yp - (double)hp);
+    xr[3 * ldh + k] = (float)(ym - (double)hm);
+  }
+}
+
+// Mirror form, after the S-apply: q+- <- q+- - w+- M+- 1^T q+- (the S-apply accumulated
+// S_CQ0 = 1^T q+ + 1^T q- and S_CQ1 = 1^T q-), then q_I0 = (q+ + q-) / 2, q_J = (q+ - q-) / 2.
+// Offsets: with mu+- = -M+- w+-^T (y+- + dpsi v+-) (A+- q+- = y+- + dpsi v+- + mu+- 1), the full
+// problem's A q = b + dpsi v + psibar e + psibar_1 e_1 gives psibar = (mu+ + mu-) / 2, psibar_1 = -mu-.
+// Also accumulates q^T b for the closed-form energy.
+__global__ void __launch_bounds__(256) k_project_mirror(const double* __restrict__ qpm, int nh,
+                                                        const int* __restrict__ i0, const int* __restrict__ jm,
+                                                        const double* __restrict__ W, const double* __restrict__ b,
+                                                        int ldb, int ne, double* __restrict__ scal,
+                                                        const double* __restrict__ dpsi, double mp, double mm,
+                                                        double wtvp, double wtvm, double* __restrict__ q,
+                                                        double* __restrict__ psibar) {
+  const int rep = blockIdx.y;
+  double* s = scal + rep * NSCAL;
+  const double cp = s[S_CQ0] - s[S_CQ1], cm = s[S_CQ1];
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double qb[1] = {0.0};
+  if (k < nh) {
+    const double qp = qpm[(size_t)rep * 2 * nh + k] - W[2 * k] * mp * cp;
+    const double qm = qpm[(size_t)rep * 2 * nh + nh + k] - W[2 * (size_t)nh + 2 * k + 1] * mm * cm;
+    const int i = i0[k], j = jm[k];
+    const double qi = 0.5 * (qp + qm), qj = 0.5 * (qp - qm);
+    q[(size_t)rep * ne + i] = qi;
+    q[(size_t)rep * ne + j] = qj;
+    qb[0] = qi * b[(size_t)rep * ldb + i] + qj * b[(size_t)rep * ldb + j];
+  }
+  if (k == 0 && psibar) {
+    const double mup = -mp * (s[S_WB0] + dpsi[rep] * wtvp), mum = -mm * (s[S_WB1] + dpsi[rep] * wtvm);
+    psibar[rep * 2 + 0] = 0.5 * (mup + mum);
+    psibar[rep * 2 + 1] = -mum;
+  }
+  qb[0] = warp_sum(qb[0]);
+  double* const dst[1] = {s + S_QB};
+  block_atomic_add<1>(qb, dst);
+}
+
 // Per replica (U, H, dH/d(dpsi), Q_+).  closed_form: at the constrained optimum Eq. 3 reduces to
 // U = U_elyt - 1/2 q^T b + 1/2 dpsi q^T v (A q = b + dpsi v + C lam and C^T q = 0); otherwise U is the
 // full Ewald sum of all charges (real space + mesh + self terms).
@@ -1286,8 +1346,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   const bool closed_form = charges && energy != nullptr;
 
   if (charges) {
-    double* b = c->b_tmp;                 // aligned internal copy, row stride ld64
-    const int ldb = c->ld64;
+    double* b = c->b_tmp;                 // aligned internal copy, row stride ldb
+    const int ldb = c->ldb;
     // real-space Gaussian-point part of b at the electrode sites
     // (on the side stream, concurrent with the mesh chain below; joined before the gather)
     CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, nullptr, nullptr, c->phi_real};
@@ -1323,7 +1383,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PhaseTimer pt(c, st, CPM_PH_B_GATHER);
       k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
                                                               c->phi_real, c->e_z, slab_coef, c->scal, b,
-                                                              c->mixed ? c->b32 : nullptr, c->ld32, ldb);
+                                                              (c->mixed && !c->mirror) ? c->b32 : nullptr,
+                                                              c->ldx, ldb);
       STEP_LAUNCH();
       if (b_out) {
         CPM_CUDA(cudaMemcpy2DAsync(b_out, sizeof(double) * ne, b, sizeof(double) * ldb, sizeof(double) * ne, nrep,
@@ -1331,46 +1392,73 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       }
     }
     // q = S b + dpsi S v, then the projection
-    const int sblocks = std::min(grid_for(ne), 152 * 4);
+    // one S-apply over `rows` rows of S (leading dimension ld), inputs x (float32 hi / lo halves or
+    // float64 y), outputs q_raw rows of stride qstride
+    auto sapply = [&](const float* S32, const double* S64, int rows, int ld, const float* x32, int xstride,
+                      int xlo, const double* y64, int ldy, const double* Sv, const double* W, const double* c1,
+                      double* qout, int qstride) -> int {
+      const int sblocks = std::min(grid_for(rows), 152 * 4);
+      for (int r0 = 0; r0 < nrep; r0 += 4) {
+        const int left = nrep - r0;
+        if (c->mixed) {
+          if (left == 1)
+            k_sapply32<1><<<sblocks, 256, 0, st>>>(S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
+                                                   W, c1, qout, qstride, c->scal);
+          else if (left == 2)
+            k_sapply32<2><<<sblocks, 256, 0, st>>>(S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
+                                                   W, c1, qout, qstride, c->scal);
+          else
+            k_sapply32<4><<<sblocks, 256, 0, st>>>(S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
+                                                   W, c1, qout, qstride, c->scal);
+        } else {
+          if (left == 1)
+            k_sapply64<1><<<sblocks, 256, 0, st>>>(S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
+                                                   qstride, c->scal);
+          else if (left == 2)
+            k_sapply64<2><<<sblocks, 256, 0, st>>>(S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
+                                                   qstride, c->scal);
+          else
+            k_sapply64<4><<<sblocks, 256, 0, st>>>(S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
+                                                   qstride, c->scal);
+        }
+        STEP_LAUNCH();
+      }
+      return CPM_OK;
+    };
     {
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
-      if (c->mixed && nrep >= TC_MIN_REPLICAS) {
+      if (c->mirror) {
+        const int nh = c->nh, ldh = c->ldh;
+        k_mirror_fold<<<dim3((nh + 255) / 256, nrep), 256, 0, st>>>(b, ldb, nh, ldh, c->m_i0, c->m_j, c->ypm,
+                                                                    c->mixed ? c->b32 : nullptr);
+        STEP_LAUNCH();
+        for (int blk = 0; blk < 2; ++blk) {
+          const size_t so = (size_t)blk * nh * ldh;
+          CPM_TRY(sapply(c->mixed ? c->S32 + so : nullptr, c->mixed ? nullptr : c->S64 + so, nh, ldh,
+                         c->b32 + (size_t)blk * ldh, 4 * ldh, 2 * ldh, c->ypm + (size_t)blk * ldh, 2 * ldh,
+                         c->Sv + (size_t)blk * nh, c->W + (size_t)blk * 2 * nh, c->e_c1m + (size_t)blk * nh,
+                         c->qpm + (size_t)blk * nh, 2 * nh));
+        }
+      } else if (c->mixed && nrep >= TC_MIN_REPLICAS) {
         CPM_TRY(sapply_tensor_core(c, nrep, st));
         k_qraw_epilogue<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(c->qraw32, ne, b, ldb, dpsi, c->Sv, c->W,
                                                                       c->e_c1, q, c->scal);
         STEP_LAUNCH();
       } else {
-        for (int r0 = 0; r0 < nrep; r0 += 4) {
-          const int left = nrep - r0;
-          if (c->mixed) {
-            if (left == 1)
-              k_sapply32<1><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv,
-                                                     c->W, c->e_c1, q, c->scal);
-            else if (left == 2)
-              k_sapply32<2><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv,
-                                                     c->W, c->e_c1, q, c->scal);
-            else
-              k_sapply32<4><<<sblocks, 256, 0, st>>>(c->S32, c->ld32, ne, c->b32, b, ldb, r0, nrep, dpsi, c->Sv,
-                                                     c->W, c->e_c1, q, c->scal);
-          } else {
-            if (left == 1)
-              k_sapply64<1><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
-                                                     c->e_c1, q, c->scal);
-            else if (left == 2)
-              k_sapply64<2><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
-                                                     c->e_c1, q, c->scal);
-            else
-              k_sapply64<4><<<sblocks, 256, 0, st>>>(c->S64, c->ld64, ne, b, ldb, r0, nrep, dpsi, c->Sv, c->W,
-                                                     c->e_c1, q, c->scal);
-          }
-          STEP_LAUNCH();
-        }
+        CPM_TRY(sapply(c->S32, c->S64, ne, c->ld64, c->b32, 2 * c->ldx, c->ldx, b, ldb, c->Sv, c->W, c->e_c1, q,
+                       ne));
       }
     }
     PhaseTimer ptp(c, st, CPM_PH_PROJECT);
-    k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
-                                                            c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
-                                                            c->WTv[1], psibar);
+    if (c->mirror) {
+      k_project_mirror<<<dim3((c->nh + 255) / 256, nrep), 256, 0, st>>>(c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
+                                                                        ldb, ne, c->scal, dpsi, c->Mh[0], c->Mh[1],
+                                                                        c->WTv[0], c->WTv[1], q, psibar);
+    } else {
+      k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
+                                                              c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
+                                                              c->WTv[1], psibar);
+    }
     STEP_LAUNCH();
   }
 
@@ -1534,10 +1622,15 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaMalloc(&c->qT, tsz * R * ne));
   CPM_CUDA(cudaMalloc(&c->l_cellc, sizeof(int4) * R * cap));
   CPM_CUDA(cudaMalloc(&c->phi_real, sizeof(double) * R * ne));
-  CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * c->ld64));
-  CPM_CUDA(cudaMemset(c->b_tmp, 0, sizeof(double) * R * c->ld64));
-  CPM_CUDA(cudaMalloc(&c->b32, sizeof(float) * R * 2 * c->ld32));
-  CPM_CUDA(cudaMemset(c->b32, 0, sizeof(float) * R * 2 * c->ld32));
+  CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * c->ldb));
+  CPM_CUDA(cudaMemset(c->b_tmp, 0, sizeof(double) * R * c->ldb));
+  CPM_CUDA(cudaMalloc(&c->b32, sizeof(float) * R * 2 * c->ldx));
+  CPM_CUDA(cudaMemset(c->b32, 0, sizeof(float) * R * 2 * c->ldx));
+  if (c->mirror) {
+    CPM_CUDA(cudaMalloc(&c->ypm, sizeof(double) * R * 2 * c->ldh));
+    CPM_CUDA(cudaMemset(c->ypm, 0, sizeof(double) * R * 2 * c->ldh));
+    CPM_CUDA(cudaMalloc(&c->qpm, sizeof(double) * R * 2 * c->nh));
+  }
   CPM_CUDA(cudaMalloc(&c->f_pair, sizeof(double) * R * cap * 3));
   CPM_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
@@ -1671,8 +1764,9 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   const size_t sizes[] = {tsz * ctx->Mr_s,          tsz * ctx->Mr_s,             2 * tsz * ctx->Mc_s,
                           sizeof(int) * cap,        sizeof(int) * ncell,         sizeof(int) * (ncell + 1),
                           sizeof(int) * cap,        v4 * cap,                    sizeof(int4) * cap,
-                          sizeof(double) * ctx->ne, sizeof(double) * ctx->ld64,  sizeof(float) * 2 * ctx->ld32,
-                          sizeof(double) * cpm::NSCAL, v4 * cap,                 tsz * ctx->ne};
+                          sizeof(double) * ctx->ne, sizeof(double) * ctx->ldb,   sizeof(float) * 2 * ctx->ldx,
+                          sizeof(double) * cpm::NSCAL, v4 * cap,                 tsz * ctx->ne,
+                          sizeof(double) * 2 * ctx->ldh, sizeof(double) * 2 * ctx->nh};
   constexpr int NREG = sizeof(sizes) / sizeof(sizes[0]);
   size_t offs[NREG], total = 0;
   for (int k = 0; k < NREG; ++k) {
@@ -1709,12 +1803,15 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   t.scal = reinterpret_cast<double*>(base + offs[12]);
   t.l_tmp = base + offs[13];
   t.qT = base + offs[14];
+  t.ypm = ctx->mirror ? reinterpret_cast<double*>(base + offs[15]) : nullptr;
+  t.qpm = ctx->mirror ? reinterpret_cast<double*>(base + offs[16]) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   // The array keeps the previous call's contents: the S-apply reads the padding of b up to the
   // row stride, so that must be zero.  (The counts, mesh and reduction slots are cleared by the
   // step itself.)
   CPM_CUDA(cudaMemsetAsync(t.b_tmp, 0, sizes[10], st));
   CPM_CUDA(cudaMemsetAsync(t.b32, 0, sizes[11], st));
+  if (ctx->mirror) CPM_CUDA(cudaMemsetAsync(t.ypm, 0, sizes[15], st));
   const int s = ctx->mixed
                     ? cpm::run<float>(&t, 1, off, xyzq, dpsi, true, q, b, psibar, nullptr, nullptr, nullptr, st)
                     : cpm::run<double>(&t, 1, off, xyzq, dpsi, true, q, b, psibar, nullptr, nullptr, nullptr, st);

@@ -13,12 +13,14 @@ import torch
 from . import (Context, cpm_build_matrix, cpm_energy, cpm_forces, cpm_step, cpm_step_charges, make_params)
 
 
-def params_for(w, precision="fp64", grid=None, order=None, max_replicas=None, max_elyt=None, kmax_build=0.0):
+def params_for(w, precision="fp64", grid=None, order=None, max_replicas=None, max_elyt=None, kmax_build=0.0,
+               matrix_kspace="ewald", dc_blocks="auto"):
     counts = [len(q) for q in w.elyt_q]
     return make_params(w.box, w.eta, w.alpha, w.rcut, grid or w.grid, order or w.order, w.geometry, precision,
                        max_replicas=max_replicas or max(1, len(counts)),
                        max_elyt=max_elyt or max(1, max(counts) if counts else 1),
-                       slab_factor=w.slab_factor, kmax_build=kmax_build)
+                       slab_factor=w.slab_factor, kmax_build=kmax_build, matrix_kspace=matrix_kspace,
+                       dc_blocks=dc_blocks)
 
 
 def pack(w):
@@ -35,10 +37,11 @@ def pack(w):
 
 class System:
     def __init__(self, w, precision="fp64", grid=None, order=None, device="cuda", kmax_build=0.0,
-                 max_replicas=None, max_elyt=None):
+                 max_replicas=None, max_elyt=None, matrix_kspace="ewald", dc_blocks="auto"):
         self.w = w
         self.device = torch.device(device)
-        self.params = params_for(w, precision, grid, order, max_replicas, max_elyt, kmax_build)
+        self.params = params_for(w, precision, grid, order, max_replicas, max_elyt, kmax_build, matrix_kspace,
+                                 dc_blocks)
         with torch.cuda.device(self.device):
             self.ctx: Context = cpm_build_matrix(self.params, w.elec_xyz, w.elec_side, w.elec_cell)
         self.ne = self.ctx.n_elec

@@ -235,8 +235,95 @@ def place_electrolyte(rng, lx, ly, zlo, zhi, n_pairs, model="point", dmin=3.0, m
     return np.asarray(xyz, dtype=np.float64), np.asarray(q, dtype=np.float64)
 
 
+def _molecule_sites(rng, n, lx, ly, zlo, zhi, cation, model):
+    """n random molecules (all cations or all anions): sites [n, k, 3] and charges [k]."""
+    c = np.stack([rng.uniform(0, lx, n), rng.uniform(0, ly, n), rng.uniform(zlo, zhi, n)], axis=1)
+    if model == "cg" and cation:
+        b1 = rng.uniform(2.5, 3.0, n)
+        b2 = rng.uniform(2.5, 3.0, n)
+        ang = rng.uniform(math.radians(60.0), math.radians(120.0), n)
+        local = np.zeros((n, 3, 3))
+        local[:, 1, 0] = b1
+        local[:, 2, 0] = b2 * np.cos(ang)
+        local[:, 2, 1] = b2 * np.sin(ang)
+        local -= local.mean(axis=1, keepdims=True)
+        qn = rng.normal(size=(n, 4))
+        qn /= np.linalg.norm(qn, axis=1, keepdims=True)
+        a, b, cc, d = qn.T
+        rot = np.stack([np.stack([a * a + b * b - cc * cc - d * d, 2 * (b * cc - a * d), 2 * (b * d + a * cc)], -1),
+                        np.stack([2 * (b * cc + a * d), a * a - b * b + cc * cc - d * d, 2 * (cc * d - a * b)], -1),
+                        np.stack([2 * (b * d - a * cc), 2 * (cc * d + a * b), a * a - b * b - cc * cc + d * d], -1)],
+                       axis=1)
+        sites = np.einsum("nkj,nij->nki", local, rot) + c[:, None, :]
+        return sites, np.full(3, ION_CHARGE / 3.0)
+    return c[:, None, :], np.array([ION_CHARGE if cation else -ION_CHARGE])
+
+
+def place_electrolyte_batched(rng, lx, ly, zlo, zhi, n_pairs, model="point", dmin=3.0, batch=16384,
+                              max_batches=10000):
+    """Random non-overlapping electrolyte like place_electrolyte, drawn in vectorised batches for
+    large systems: each batch of candidate molecules (cations and anions alternately in draw
+    order) is checked against the placed sites with a k-d tree periodic in x, y, and conflicts
+    inside the batch are resolved by dropping the later-drawn molecule of every conflicting pair.  Returns (xyz [N_l,3], q [N_l]),
+    cations first, then anions."""
+    from scipy.spatial import cKDTree
+    zbox = zhi + dmin + 1.0                       # no wrap in z: the slab sits inside [0, zbox)
+    placed = np.zeros((0, 3))
+    kept = {True: [], False: []}
+    need = {True: n_pairs, False: n_pairs}
+    charges = {}
+    for _ in range(max_batches):
+        if need[True] == 0 and need[False] == 0:
+            break
+        parts = []
+        for cation in (True, False):
+            if need[cation] == 0:
+                continue
+            sites, ch = _molecule_sites(rng, batch, lx, ly, zlo, zhi, cation, model)
+            charges[cation] = ch
+            inside = np.all((sites[:, :, 2] >= zlo) & (sites[:, :, 2] <= zhi), axis=1)
+            ids = 2 * np.arange(batch) + (0 if cation else 1)      # draw order
+            sites = sites[inside]
+            sites[:, :, 0] %= lx
+            sites[:, :, 1] %= ly
+            parts.append((cation, sites, ids[inside]))
+        flat = np.concatenate([p[1].reshape(-1, 3) for p in parts])
+        owner = np.concatenate([np.repeat(p[2], p[1].shape[1]) for p in parts])
+        ok = np.zeros(2 * batch, dtype=bool)
+        for p in parts:
+            ok[p[2]] = True
+        if len(placed):
+            d, _ = cKDTree(placed, boxsize=(lx, ly, zbox)).query(flat, distance_upper_bound=dmin)
+            ok[owner[d < dmin]] = False
+        live = ok[owner]
+        lsites, lowner = flat[live], owner[live]
+        acc = ok.copy()
+        if len(lsites):
+            pairs = cKDTree(lsites, boxsize=(lx, ly, zbox)).query_pairs(dmin, output_type="ndarray")
+            if len(pairs):
+                # of every conflicting pair the later-drawn molecule is dropped
+                oa, ob = lowner[pairs[:, 0]], lowner[pairs[:, 1]]
+                diff = oa != ob
+                acc[np.maximum(oa, ob)[diff]] = False
+        new_sites = []
+        for cation, sites, ids in parts:
+            take = np.flatnonzero(acc[ids])[:need[cation]]
+            need[cation] -= len(take)
+            kept[cation].append(sites[take])
+            new_sites.append(sites[take].reshape(-1, 3))
+        placed = np.concatenate([placed] + new_sites)
+    else:
+        raise RuntimeError("electrolyte placement failed: density too high for min separation")
+    xyz, q = [], []
+    for cation in (True, False):
+        s = np.concatenate(kept[cation])
+        xyz.append(s.reshape(-1, 3))
+        q.append(np.tile(charges[cation], len(s)))
+    return np.concatenate(xyz).astype(np.float64), np.concatenate(q).astype(np.float64)
+
+
 def mirror_to_doubled(w: Workload, electrolyte: str = "mirror", seed: int | None = None,
-                      model: str = "point", n_pairs: int | None = None) -> Workload:
+                      model: str = "point", n_pairs: int | None = None, placer=None) -> Workload:
     """Doubled cell: sub-cell 0 is w, sub-cell 1 its z-mirror image z -> 2 L_z - z.
 
     electrolyte='mirror' reflects the electrolyte as well (mirror-symmetric cell); 'independent'
@@ -261,8 +348,9 @@ def mirror_to_doubled(w: Workload, electrolyte: str = "mirror", seed: int | None
         else:
             rng = np.random.Generator(np.random.PCG64(seed + r))
             npairs = n_pairs if n_pairs is not None else len(w.elyt_q[r]) // (4 if model == "cg" else 2)
-            b, bq = place_electrolyte(rng, lx, ly, lz + ELECTROLYTE_MARGIN, 2 * lz - ELECTROLYTE_MARGIN,
-                                      npairs, model=model, dmin=w.min_sep)
+            b, bq = (placer or place_electrolyte)(rng, lx, ly, lz + ELECTROLYTE_MARGIN,
+                                                  2 * lz - ELECTROLYTE_MARGIN, npairs, model=model,
+                                                  dmin=w.min_sep)
         ex.append(np.concatenate([a, b]))
         eq.append(np.concatenate([w.elyt_q[r], bq]))
     return dataclasses.replace(w, name=w.name + "-dc", box=np.array([lx, ly, 2 * lz]), elec_xyz=xyz,
@@ -370,4 +458,33 @@ def tiny_cell(seed: int = 7, n_pairs: int = 3, nx: int = 2, ny: int = 3, lz: flo
         w.grid = _grid_for(w.box)
     elif geometry == "slab":
         w = dataclasses.replace(w, geometry="slab", grid=_grid_for((lx, ly, 3.0 * lz)))
+    return w
+
+
+def config_large_dc(seed: int = 5000, n_pairs_per_cell: int = 12500, dpsi: float = 2.0,
+                    electrolyte: str = "independent", dmin: float = 2.0) -> Workload:
+    """Large doubled cell: a 125 x 123 x 100 A sub-cell with two three-layer electrodes of a
+    60 x 56 rectangular lattice per layer (2.083 x 2.196 A, alternate layers offset by half a
+    step), 20,160 sites, and its z-mirror image: 40,320 electrode sites in a 125 x 123 x 200 A
+    doubled cell.  12,500 coarse-grained ion pairs per sub-cell (25,000 pairs, 100,000 sites),
+    drawn independently in each sub-cell (seeds `seed`, `seed + 1`) or mirrored
+    (electrolyte='mirror').  SPME mesh 128 x 128 x 200, order 5.
+
+    50,000 sites per 74 A sub-cell gap cannot be placed by rejection sampling at a 2.5 A site
+    separation (hard-sphere packing fraction ~0.36, near the random-sequential-addition limit),
+    so the minimum site separation between molecules is 2.0 A (packing fraction ~0.18).  The
+    sites are drawn with place_electrolyte_batched.
+    """
+    lz = 100.0
+    xyz, side, layer, (lx, ly) = electrode_pair(60, 56, lz, lattice="rect", lxy=(125.0, 123.0))
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ex, eq = place_electrolyte_batched(rng, lx, ly, ELECTROLYTE_MARGIN, lz - ELECTROLYTE_MARGIN,
+                                       n_pairs_per_cell, "cg", dmin)
+    box = np.array([lx, ly, lz])
+    w = Workload("dc-sub-20160", box, xyz, side, None, layer, [ex], [eq], np.array([dpsi]), "ff",
+                 grid=(128, 128, 100), min_sep=dmin)
+    w = mirror_to_doubled(w, electrolyte, seed=seed + 1, model="cg", n_pairs=n_pairs_per_cell,
+                          placer=place_electrolyte_batched)
+    w.grid = (128, 128, 200)
+    w.name = "dc-40320"
     return w

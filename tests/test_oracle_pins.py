@@ -262,6 +262,39 @@ def test_doubled_cell_mirror_symmetry():
     assert np.max(np.abs(q[:n] - q[n:])) < 1e-12
 
 
+def test_doubled_cell_two_mirror_blocks_equal_full_solve():
+    """A mirror-symmetric doubled cell has A = [[P, Q], [Q, P]] (sites ordered sub-cell 0, then
+    images).  With y+- = y_0 +- y_1 the constrained problem separates: q+- minimises
+    1/2 x^T (P +- Q) x - x^T y+- subject to 1^T x = 0, q_0 = (q+ + q-)/2, q_1 = (q+ - q-)/2, and the
+    offsets of Eq. 12 are psibar = (mu+ + mu-)/2, psibar_1 = -mu- (A+- q+- = y+- + mu+- 1).  The
+    GPU stores the doubled cell this way; this pins the reduction on the oracle's own A, with an
+    electrolyte that is not mirrored (q- != 0)."""
+    w = synth.mirror_to_doubled(synth.tiny_cell(seed=9, n_pairs=3), "independent", seed=99)
+    ref = cpm.Reference(w)
+    out = ref.step(want_forces=False, want_energy=False)
+    n = w.n_elec // 2
+    A = ref.A
+    P, Q = A[:n, :n], A[:n, n:]
+    y = out["b"] + float(w.dpsi[0]) * ref.v
+    one = np.ones((n, 1))
+    qpm, mu = [], []
+    for sgn in (+1.0, -1.0):
+        Ab = P + sgn * Q
+        yb = y[:n] + sgn * y[n:]
+        x, lam = cpm.solve_charges(cpm.factorize(Ab), yb, np.zeros(n), 0.0, one)
+        qpm.append(x)
+        mu.append(float(lam[0]))
+    q0 = 0.5 * (qpm[0] + qpm[1])
+    q1 = 0.5 * (qpm[0] - qpm[1])
+    q = out["q"]
+    scale = max(1.0, np.max(np.abs(q)))
+    assert np.max(np.abs(np.concatenate([q0, q1]) - q)) < 1e-12 * scale
+    assert np.max(np.abs(qpm[1])) > 1e-4                               # the difference mode is exercised
+    lam = out["psibar"]
+    assert abs(0.5 * (mu[0] + mu[1]) - lam[0]) < 1e-10
+    assert abs(-mu[1] - lam[1]) < 1e-10
+
+
 def _empty(w):
     return dataclasses.replace(w, elyt_xyz=[np.zeros((0, 3))], elyt_q=[np.zeros(0)])
 

@@ -30,11 +30,16 @@ def _lib():
     return g, System
 
 
-@pytest.mark.parametrize("prec", ["fp64", "mixed"])
-def test_static_scratch_entry_matches_allocating_entry(prec):
+@pytest.mark.parametrize("prec,geometry", [("fp64", "ff"), ("mixed", "ff"), ("mixed", "dc")])
+def test_static_scratch_entry_matches_allocating_entry(prec, geometry):
     g, System = _lib()
-    w = synth.config_plain_ff()
+    if geometry == "ff":
+        w = synth.config_plain_ff()
+    else:                                   # doubled cell stored as mirror blocks
+        w = synth.mirror_to_doubled(synth.tiny_cell(seed=4, n_pairs=4), "independent", seed=40)
+        w.grid = (18, 16, 144)
     s = System(w, prec)
+    assert g.cpm_matrix_layout(s.ctx)[0] == (geometry == "dc")
     s.charges()
     torch.cuda.synchronize()
     q_ref, b_ref, p_ref = s.q.clone(), s.b.clone(), s.psibar.clone()
