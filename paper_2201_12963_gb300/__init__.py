@@ -23,7 +23,8 @@ DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
-            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_destroy",
+            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_autotune",
+            "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
 PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
           "f_gather", "f_pair_elyt", "f_pair_elec", "energy")
@@ -70,6 +71,8 @@ def _load():
     lib.cpm_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_step_charges_static.argtypes = [vp, pi32, pd, pd, pd, pd, pd, vp]
     lib.cpm_matrix_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]
+    lib.cpm_set_sapply_variant.argtypes = [vp, i32]
+    lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, ctypes.POINTER(i32)]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
     lib.cpm_strerror.argtypes = [ctypes.c_int]
@@ -254,6 +257,27 @@ def cpm_matrix_layout(ctx: Context):
     nb = ctypes.c_int64()
     _check(_lib.cpm_matrix_layout(ctx.handle, ctypes.byref(m), ctypes.byref(nb)), "cpm_matrix_layout")
     return bool(m.value), int(nb.value)
+
+
+SAPPLY_VARIANTS = {"rows": 0, "stream": 1}             # enum cpm_sapply_variant
+
+
+def cpm_set_sapply_variant(ctx: Context, variant):
+    v = SAPPLY_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(_lib.cpm_set_sapply_variant(ctx.handle, v), "cpm_set_sapply_variant")
+
+
+def cpm_autotune(ctx: Context, offsets, xyzq, dpsi, q, stream=None) -> str:
+    """Time the available S-apply variants on this input (one replica); keeps and returns the fastest."""
+    import torch
+    ne = ctx.n_elec
+    p_off = _dev(offsets, torch.int32, "offsets", 2)
+    p_x = _dev(xyzq, torch.float64, "xyzq")
+    p_d = _dev(dpsi, torch.float64, "dpsi", 1)
+    out = ctypes.c_int32()
+    _check(_lib.cpm_autotune(ctx.handle, p_off, p_x, p_d, _dev(q, torch.float64, "q", ne), _stream_ptr(stream),
+                             ctypes.byref(out)), "cpm_autotune")
+    return {v: k for k, v in SAPPLY_VARIANTS.items()}[out.value]
 
 
 def cpm_status(ctx: Context, stream=None) -> int:

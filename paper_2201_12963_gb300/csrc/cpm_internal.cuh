@@ -101,6 +101,11 @@ struct cpm_ctx {
   double* e_c1m = nullptr;      // [2 nh] zeros then ones (constraint indicator of the S-apply rows)
   double* ypm = nullptr;        // [max_rep][2 ldh] y+ = b_I0 + b_m(I0), y- = b_I0 - b_m(I0)
   double* qpm = nullptr;        // [max_rep][2 nh] q+, q- before the projection
+  // S-apply variant (enum cpm_sapply_variant) and the streaming variant's row partial sums
+  // ([rows of S], float64, zero between calls: its finish kernel clears what it consumed)
+  int sapply_variant = 0;
+  double* qpart = nullptr;
+  int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
   double dqdpsi = 0;
   // SPME
   int K[3] = {0, 0, 0};

@@ -853,6 +853,97 @@ __global__ void __launch_bounds__(256) k_sapply64(const double* __restrict__ S, 
 }
 
 // ------------------------------------------------------------------------------------------
+// Streaming S-apply (mixed precision, one replica): persistent CTAs, one per SM, each holding the
+// whole right-hand side (float32 hi and lo halves, 8 ld bytes) in shared memory.  The flattened S
+// (rows x ld/4 float4, contiguous) is cut into one equal contiguous span per warp, so every warp
+// streams the same number of bytes whatever the row count; a span covers whole and partial rows,
+// and each row segment's compensated dot product is added into qpart[row] in float64 (at most a
+// few segments per row).  k_sapply_finish then forms q_raw = qpart + dpsi S v with the projection
+// sums and clears qpart for the next call.
+// ------------------------------------------------------------------------------------------
+constexpr int SS_THREADS = 512;
+constexpr int SS_SMEM_MAX = 200 * 1024;      // largest staged right-hand side (bytes)
+
+template <int U>
+__global__ void __launch_bounds__(SS_THREADS, 1) k_sapply_stream(const float* __restrict__ S, int ld, int rows,
+                                                                 const float* __restrict__ xh,
+                                                                 const float* __restrict__ xl,
+                                                                 double* __restrict__ qpart) {
+  extern __shared__ float4 ss_x[];
+  const int n4 = ld >> 2;
+  float4* shi = ss_x;
+  float4* slo = ss_x + n4;
+  const float4* gh = reinterpret_cast<const float4*>(xh);
+  const float4* gl = reinterpret_cast<const float4*>(xl);
+  for (int k = threadIdx.x; k < n4; k += blockDim.x) {
+    shi[k] = gh[k];
+    slo[k] = gl[k];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  const long long wid = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long total = (long long)rows * n4;
+  const long long per = (total + nw - 1) / nw;
+  long long p = wid * per;
+  const long long pend = min(total, p + per);
+  const float4* S4 = reinterpret_cast<const float4*>(S);
+  while (p < pend) {
+    const int row = (int)(p / n4);
+    const long long rbase = (long long)row * n4;
+    const int c0 = (int)(p - rbase);
+    const int c1 = (int)(min(pend, rbase + n4) - rbase);
+    const float4* srow = S4 + rbase;
+    Acc<float> acc;
+    float lo = 0.f;
+    for (int jb = c0 + lane; jb < c1; jb += 32 * U) {
+      float4 sv[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = jb + 32 * u;
+        sv[u] = (j < c1) ? __ldcs(srow + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int j = min(jb + 32 * u, c1 - 1);    // out-of-range slots hold zeros in sv
+        const float4 h = shi[j], l = slo[j];
+        acc.add(sv[u].x * h.x + sv[u].y * h.y + sv[u].z * h.z + sv[u].w * h.w);
+        lo += sv[u].x * l.x + sv[u].y * l.y + sv[u].z * l.z + sv[u].w * l.w;
+      }
+    }
+    acc.add(lo);
+    acc.warp_reduce();
+    if (lane == 0) atomicAdd(&qpart[row], acc.value());
+    p = rbase + c1;
+  }
+}
+
+// q_raw = qpart + dpsi S v (one replica), qpart cleared; the projection sums C^T q_raw and
+// (A^-1 C)^T b as in the S-apply epilogue.
+__global__ void __launch_bounds__(256) k_sapply_finish(int rows, double* __restrict__ qpart,
+                                                       const double* __restrict__ b, const double* __restrict__ dpsi,
+                                                       const double* __restrict__ Sv, const double* __restrict__ W,
+                                                       const double* __restrict__ c1, double* __restrict__ qout,
+                                                       double* __restrict__ scal) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  double red[4] = {0, 0, 0, 0};
+  if (i < rows) {
+    const double qr = qpart[i] + dpsi[0] * Sv[i];
+    qpart[i] = 0.0;
+    qout[i] = qr;
+    const double bi = b[i];
+    red[0] = qr;
+    red[1] = qr * c1[i];
+    red[2] = W[2 * i] * bi;
+    red[3] = W[2 * i + 1] * bi;
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) red[k] = warp_sum(red[k]);
+  double* const dst[4] = {scal + S_CQ0, scal + S_CQ1, scal + S_WB0, scal + S_WB1};
+  block_atomic_add<4>(red, dst);
+}
+
+// ------------------------------------------------------------------------------------------
 // Batched S-apply on the 5th-generation tensor cores: D = S Y^T for up to 256 replicas per pass,
 // Y the replicas' right-hand sides.  tcgen05.mma kind::tf32, M = 128 rows of S per CTA, N = the
 // replica tile, K = 8 per instruction, accumulator in TMEM.  Split-TF32 ("3xTF32"): with
@@ -1302,6 +1393,18 @@ static int sapply_tensor_core(cpm_ctx* c, int nrep, cudaStream_t st) {
   return CPM_OK;
 }
 
+// Streaming S-apply of one block of rows (one replica) followed by its finish kernel.
+static int sapply_stream(cpm_ctx* c, const float* S, int rows, int ld, const float* xh, const float* xl,
+                         double* qpart, const double* b, const double* dpsi, const double* Sv, const double* W,
+                         const double* c1, double* qout, cudaStream_t st) {
+  const size_t smem = sizeof(float) * 2 * (size_t)ld;
+  k_sapply_stream<8><<<c->n_sm, SS_THREADS, smem, st>>>(S, ld, rows, xh, xl, qpart);
+  STEP_LAUNCH();
+  k_sapply_finish<<<(rows + 255) / 256, 256, 0, st>>>(rows, qpart, b, dpsi, Sv, W, c1, qout, c->scal);
+  STEP_LAUNCH();
+  return CPM_OK;
+}
+
 template <typename T>
 static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const double* dpsi, bool charges,
                double* q, double* b_out, double* psibar, double* f_elyt, double* f_elec, double* energy,
@@ -1425,6 +1528,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       }
       return CPM_OK;
     };
+    // streaming variant: mixed precision, one replica, right-hand side fits shared memory
+    const bool stream_ok = c->mixed && nrep == 1 && c->qpart && c->sapply_variant == CPM_SAPPLY_STREAM;
     {
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
       if (c->mirror) {
@@ -1434,11 +1539,22 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         STEP_LAUNCH();
         for (int blk = 0; blk < 2; ++blk) {
           const size_t so = (size_t)blk * nh * ldh;
+          if (stream_ok) {
+            CPM_TRY(sapply_stream(c, c->S32 + so, nh, ldh, c->b32 + (size_t)blk * ldh,
+                                  c->b32 + 2 * (size_t)ldh + (size_t)blk * ldh, c->qpart + (size_t)blk * nh,
+                                  c->ypm + (size_t)blk * ldh, dpsi, c->Sv + (size_t)blk * nh,
+                                  c->W + (size_t)blk * 2 * nh, c->e_c1m + (size_t)blk * nh, c->qpm + (size_t)blk * nh,
+                                  st));
+            continue;
+          }
           CPM_TRY(sapply(c->mixed ? c->S32 + so : nullptr, c->mixed ? nullptr : c->S64 + so, nh, ldh,
                          c->b32 + (size_t)blk * ldh, 4 * ldh, 2 * ldh, c->ypm + (size_t)blk * ldh, 2 * ldh,
                          c->Sv + (size_t)blk * nh, c->W + (size_t)blk * 2 * nh, c->e_c1m + (size_t)blk * nh,
                          c->qpm + (size_t)blk * nh, 2 * nh));
         }
+      } else if (stream_ok) {
+        CPM_TRY(sapply_stream(c, c->S32, ne, c->ld32, c->b32, c->b32 + c->ldx, c->qpart, b, dpsi, c->Sv, c->W, c->e_c1,
+                              q, st));
       } else if (c->mixed && nrep >= TC_MIN_REPLICAS) {
         CPM_TRY(sapply_tensor_core(c, nrep, st));
         k_qraw_epilogue<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(c->qraw32, ne, b, ldb, dpsi, c->Sv, c->W,
@@ -1601,9 +1717,23 @@ static int tc_attributes() {
   return CPM_OK;
 }
 
+static bool stream_available(const cpm_ctx* c) {
+  return c->mixed && sizeof(float) * 2 * (size_t)c->ld32 <= (size_t)cpm::SS_SMEM_MAX;
+}
+
 int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_TRY(pair_cell_attributes());
   CPM_TRY(tc_attributes());
+  CPM_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev));
+  if (stream_available(c)) {
+    CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_stream<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  cpm::SS_SMEM_MAX));
+    const long long rows = c->mirror ? 2LL * c->nh : (long long)c->ne;
+    CPM_CUDA(cudaMalloc(&c->qpart, sizeof(double) * rows));
+    CPM_CUDA(cudaMemset(c->qpart, 0, sizeof(double) * rows));
+    // default before any tuning: stream matrices well above the L2 capacity
+    c->sapply_variant = (rows * c->ld32 * 4LL >= (64LL << 20)) ? CPM_SAPPLY_STREAM : CPM_SAPPLY_ROWS;
+  }
   const size_t R = c->p.max_replicas, cap = c->p.max_elyt, ne = c->ne;
   const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
   const size_t v4 = c->mixed ? sizeof(float4) : sizeof(double4_32a);
@@ -1667,6 +1797,57 @@ extern "C" int cpm_energy(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const
 extern "C" int cpm_step(cpm_ctx* ctx, int32_t n_rep, const int32_t* off, const double* xyzq, const double* dpsi,
                         double* q, double* psibar, double* f_elyt, double* f_elec, double* energy, void* stream) {
   return cpm::dispatch(ctx, n_rep, off, xyzq, dpsi, true, q, nullptr, psibar, f_elyt, f_elec, energy, stream);
+}
+
+extern "C" int cpm_set_sapply_variant(cpm_ctx* c, int32_t variant) {
+  if (!c) return CPM_ERR_ARG;
+  if (variant == CPM_SAPPLY_ROWS) {
+    c->sapply_variant = variant;
+    return CPM_OK;
+  }
+  if (variant == CPM_SAPPLY_STREAM && stream_available(c) && c->qpart) {
+    c->sapply_variant = variant;
+    return CPM_OK;
+  }
+  cpm::set_error("cpm_set_sapply_variant: variant %d is not available for this context", variant);
+  return CPM_ERR_ARG;
+}
+
+extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, const double* dpsi, double* q,
+                            void* stream, int32_t* variant_host) {
+  if (!c || !off || !xyzq || !dpsi || !q) return CPM_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int keep = c->sapply_variant;
+  const int cands[2] = {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM};
+  float best_ms = 0.f;
+  int best = keep;
+  cudaEvent_t e0, e1;
+  CPM_CUDA(cudaEventCreate(&e0));
+  CPM_CUDA(cudaEventCreate(&e1));
+  int rc = CPM_OK;
+  for (int v : cands) {
+    if (cpm_set_sapply_variant(c, v) != CPM_OK) continue;
+    rc = cpm_step_charges(c, 1, off, xyzq, dpsi, q, nullptr, nullptr, st);          // warm-up
+    float ms[5];
+    for (int k = 0; k < 5 && rc == CPM_OK; ++k) {
+      cudaEventRecord(e0, st);
+      rc = cpm_step_charges(c, 1, off, xyzq, dpsi, q, nullptr, nullptr, st);
+      cudaEventRecord(e1, st);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
+      else cudaEventElapsedTime(&ms[k], e0, e1);
+    }
+    if (rc != CPM_OK) break;
+    std::sort(ms, ms + 5);
+    if (best_ms == 0.f || ms[2] < best_ms) {
+      best_ms = ms[2];
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->sapply_variant = (rc == CPM_OK) ? best : keep;
+  if (variant_host) *variant_host = c->sapply_variant;
+  return rc;
 }
 
 extern "C" int cpm_profile_enable(cpm_ctx* c, int32_t capacity) {
@@ -1803,6 +1984,7 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   t.scal = reinterpret_cast<double*>(base + offs[12]);
   t.l_tmp = base + offs[13];
   t.qT = base + offs[14];
+  t.qpart = nullptr;                    // the streaming S-apply's partial sums live in the context
   t.ypm = ctx->mirror ? reinterpret_cast<double*>(base + offs[15]) : nullptr;
   t.qpm = ctx->mirror ? reinterpret_cast<double*>(base + offs[16]) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
