@@ -44,9 +44,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=None)
-    ap.add_argument("--workload", default="paper", choices=["paper", "large", "dc-large"],
-                    help="paper: the paper-scale cell (default); large: the 10,080-site cell; dc-large: the "
-                         "40,320-site doubled cell (mirror blocks, mesh-operator A)")
+    ap.add_argument("--workload", default="paper", choices=["paper", "paper-dc", "paper-slab", "large", "dc-large"],
+                    help="paper: the paper-scale cell (default); paper-dc / paper-slab: the same cell as a doubled "
+                         "cell (6,048 sites, mirror blocks) or a slab (3x z padding); large: the 10,080-site cell; "
+                         "dc-large: the 40,320-site doubled cell (mirror blocks, mesh-operator A)")
     return ap.parse_args()
 
 
@@ -74,6 +75,12 @@ def aggregate_steps_per_s(total_ms_max, steps, world):
 WORKLOADS = {
     "paper": ("paper-scale finite-field cell: 3,024 electrode sites (3-layer graphite x 2), 500 CG ion "
               "pairs (2,000 sites), 38.34x34.44x168 A, SPME 40x36x168 order 5, alpha 0.25, r_c 12 A", 2000),
+    "paper-dc": ("paper-scale doubled cell: the 3,024-site cell and its z-mirror image (6,048 electrode sites, "
+                 "S as two 3,024^2 mirror blocks), 500 CG ion pairs per sub-cell (4,000 sites), 38.34x34.44x336 A, "
+                 "SPME 40x36x336 order 5, alpha 0.25, r_c 12 A", 2000),
+    "paper-slab": ("paper-scale slab: the 3,024-site cell with z padded 3x (38.34x34.44x504 A Ewald box) and the "
+                   "Yeh-Berkowitz dipole correction, 500 CG ion pairs, SPME 40x36x504 order 5, alpha 0.25, r_c 12 A",
+                   2000),
     "large": ("scaled finite-field cell: 10,080 electrode sites (3-layer graphite x 2), 5,000 point-ion pairs "
               "(10,000 sites), 63.90x68.88x154 A, SPME 64x70x160 order 5, alpha 0.25, r_c 12 A", 4000),
     "dc-large": ("large doubled cell: 40,320 electrode sites (two mirrored 125x123x100 A sub-cells, 3-layer "
@@ -81,7 +88,8 @@ WORKLOADS = {
                  "SPME 128x128x200 order 5, alpha 0.25, r_c 12 A; S stored as two 20,160^2 mirror blocks, "
                  "A's reciprocal part as the SPME mesh operator", 5000),
 }
-GEOMETRY_NAME = {"paper": "finite field", "large": "finite field", "dc-large": "doubled cell"}
+GEOMETRY_NAME = {"paper": "finite field", "paper-dc": "doubled cell", "paper-slab": "slab", "large": "finite field",
+                 "dc-large": "doubled cell"}
 
 
 def workload(seed, kind="paper"):
@@ -90,6 +98,10 @@ def workload(seed, kind="paper"):
         return synth.config_large_ff(seed=seed)
     if kind == "dc-large":
         return synth.config_large_dc(seed=seed)
+    if kind == "paper-dc":
+        return synth.config_paper_cell(seed=seed, geometry="dc")
+    if kind == "paper-slab":
+        return synth.config_paper_cell(seed=seed, geometry="slab")
     return synth.config_paper_cell(seed=seed)
 
 
@@ -165,8 +177,10 @@ PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distanc
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
 # (profiles/k_pair_cell_paper-cell-ff-mixed.md, profiles/k_sapply32_paper-cell-ff-mixed.md); set an
 # entry to None whenever its kernel changes until it is captured again.
-NCU_TRAFFIC_MIXED = {"paper": {"f_pair_elyt": 0.208384e6, "b_real": 0.109056e6, "s_apply": 36.737536e6},
-                     "large": {}, "dc-large": {}}
+NCU_TRAFFIC_MIXED = {"paper": {"s_apply": 36.737536e6},
+                     "paper-dc": {}, "paper-slab": {},
+                     "large": {"s_apply": 409.879552e6},
+                     "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
 

@@ -281,20 +281,23 @@ int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const
  *   CPM_SAPPLY_ROWS    one warp per row of S, the right-hand side read through L1;
  *   CPM_SAPPLY_STREAM  one persistent CTA per SM holding the right-hand side in shared memory,
  *                      every warp streaming an equal contiguous span of S (row partial sums are
- *                      added in float64 and finished by a second kernel).  Available when the
- *                      right-hand side fits shared memory (rows of at most 25,600 entries).
+ *                      added in float64 and finished by a second kernel), 8 16-byte loads of S in
+ *                      flight per lane.  Available when the right-hand side fits shared memory
+ *                      (rows of at most 25,600 entries);
+ *   CPM_SAPPLY_STREAM16  the same with 16 loads in flight per lane.
  * Batches of 8 or more replicas use the tensor-core GEMM and 2-7 replicas the row kernel whatever
  * the choice; float64 contexts always use the row kernel. */
-enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1 };
+enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1, CPM_SAPPLY_STREAM16 = 2 };
 
 /* cpm_set_sapply_variant - select the S-apply variant; CPM_ERR_ARG if it is not available for
- * this context (CPM_SAPPLY_STREAM needs CPM_MIXED and rows of at most 25,600 entries). */
+ * this context (the streaming variants need CPM_MIXED and rows of at most 25,600 entries). */
 int cpm_set_sapply_variant(cpm_ctx* ctx, int32_t variant);
 
 /*
  * cpm_autotune - time every available S-apply variant on the given single-replica input (five
- * cpm_step_charges calls each after a warm-up, CUDA events on `stream`), keep the fastest in the
- * context and write it to *variant_host (may be NULL).  The arguments are those of
+ * cpm_step_charges calls each after a warm-up, each started with a cold L2 cache, CUDA events on
+ * `stream`), keep the fastest (median) in the context and write it to *variant_host (may be NULL).
+ * Allocates and frees a scratch buffer of twice the L2 size.  The arguments are those of
  * cpm_step_charges with n_rep = 1; q_dev receives the charges.  Synchronises `stream`; not for
  * use during graph capture.  Without an available alternative it keeps the current variant.
  */

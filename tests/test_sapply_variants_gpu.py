@@ -38,7 +38,7 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         out = ocpm.Reference(w).step(want_forces=False, want_energy=False)
     s = System(w, "mixed", order=8)
     qs = {}
-    for v in ("rows", "stream"):
+    for v in ("rows", "stream", "stream16"):
         g.cpm_set_sapply_variant(s.ctx, v)
         for _ in range(2):                          # the second call checks the cleared partial sums
             s.charges()
@@ -47,8 +47,9 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         assert np.max(np.abs(qs[v] - out["q"])) <= 1e-5
         assert abs(qs[v].sum()) <= 1e-12
     assert np.max(np.abs(qs["rows"] - qs["stream"])) <= 1e-6
+    assert np.max(np.abs(qs["rows"] - qs["stream16"])) <= 1e-6
     choice = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
-    assert choice in ("rows", "stream")
+    assert choice in ("rows", "stream", "stream16")
     s.charges()
     # float32 mesh spreading adds with atomics in no fixed order: repeated mixed-precision runs
     # differ at float32 rounding
