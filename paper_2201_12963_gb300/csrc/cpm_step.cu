@@ -58,7 +58,10 @@ template <typename T> struct Acc;
 template <> struct Acc<double> {
   double s = 0.0, c = 0.0;                     // c: an externally supplied correction (plain sums here)
   __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ void warp_reduce() { s = warp_sum(s); }
+  __device__ __forceinline__ void warp_reduce() {
+    s = warp_sum(s + c);
+    c = 0.0;
+  }
   __device__ __forceinline__ double value() const { return s + c; }
 };
 
@@ -340,7 +343,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   const int* tso = t.sorted + rep * t.loc_stride;
   const T* tq = t.qT ? (const T*)t.qT + (size_t)rep * t.n_fixed : nullptr;
   const bool want_energy = s0.slot >= 0 || s1.slot >= 0;     // uniform over the block
-  double eacc[2] = {0.0, 0.0};
+  Acc<T> ea0, ea1;                  // sum_t c_t phi_t per source set, working precision, compensated
 
   for (int tb = t0; tb < t1; tb += PC_MAXT) {
     const int nt = min(PC_MAXT, t1 - tb);
@@ -513,11 +516,13 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           fz += ifrc[2][item];
         }
       }
-      const double phi0 = p0.value();
-      if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = phi0;
+      if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = p0.value();
       if (want_energy) {
-        eacc[0] += qt * phi0;
-        eacc[1] += qt * p1.value();
+        const T ct = tpos[k].w;
+        ea0.add(ct * p0.s);
+        ea0.c += ct * p0.c;
+        ea1.add(ct * p1.s);
+        ea1.c += ct * p1.c;
       }
       if (FORCE && t.force) {
         const size_t gi = (size_t)rep * t.n_fixed + orig;
@@ -530,11 +535,28 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
     __syncthreads();
   }
   if (!want_energy) return;
-  double* const dst[2] = {s0.slot >= 0 ? scal + rep * NSCAL + s0.slot : nullptr,
-                          s1.slot >= 0 ? scal + rep * NSCAL + s1.slot : nullptr};
-  eacc[0] = warp_sum(eacc[0]);
-  eacc[1] = warp_sum(eacc[1]);
-  block_atomic_add<2>(eacc, dst);
+  // block total in the working precision (compensated), one float64 atomic per slot
+  __shared__ T ered[2][2][PC_THREADS / 32];
+  ea0.warp_reduce();
+  ea1.warp_reduce();
+  if (lane == 0) {
+    ered[0][0][warp] = ea0.s;
+    ered[0][1][warp] = ea0.c;
+    ered[1][0][warp] = ea1.s;
+    ered[1][1][warp] = ea1.c;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    Acc<T> a0, a1;
+    for (int w = 0; w < PC_THREADS / 32; ++w) {
+      a0.add(ered[0][0][w]);
+      a0.c += ered[0][1][w];
+      a1.add(ered[1][0][w]);
+      a1.c += ered[1][1][w];
+    }
+    if (s0.slot >= 0) atomicAdd(scal + rep * NSCAL + s0.slot, a0.value());
+    if (s1.slot >= 0) atomicAdd(scal + rep * NSCAL + s1.slot, a1.value());
+  }
 }
 
 // ------------------------------------------------------------------------------------------
