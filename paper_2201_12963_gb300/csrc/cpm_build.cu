@@ -972,7 +972,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
   void* bufs[] = {c->e_pos64, c->e_loc64, c->e_loc32, c->e_cellc, c->e_sorted, c->e_start, c->e_base,
                   c->e_th64, c->e_dth64, c->e_th32, c->e_dth32, c->e_z, c->e_v, c->e_c1, c->e_plus, c->S64, c->S32,
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
-                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_cellc, c->l_tmp, c->qT, c->spl_I,
+                  c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
                   c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart};
   for (void* b : bufs)

@@ -127,7 +127,6 @@ struct cpm_ctx {
   int* l_sorted = nullptr;      // [max_rep][max_elyt] sorted -> original (relative to offset)
   double4_32a* l_loc64 = nullptr;   // [max_rep][max_elyt] cell-local coordinates + Q
   float4* l_loc32 = nullptr;
-  int4* l_cellc = nullptr;      // [max_rep][max_elyt]
   void* l_tmp = nullptr;        // [max_rep][max_elyt] unsorted cell-local coordinates + Q (working precision)
   void* qT = nullptr;           // [max_rep][ne] electrode charges in the working precision
   // B-spline coordinate of each cell origin along each axis: c K_d / nc_d = spl_I + spl_F

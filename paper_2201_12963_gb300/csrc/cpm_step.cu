@@ -41,6 +41,7 @@ struct SpmeGeom {
   double kl[3];          // K_d / L_d
   long long Mr_s, Mc_s;
   int spl_off[3];        // axis offsets into the cell-origin tables
+  int nc[3];             // real-space cell grid (flat cell index -> cell coordinates)
 };
 
 __device__ __forceinline__ double wrap_d(double x, double L, double invL) {
@@ -184,12 +185,11 @@ __global__ void k_scan(int* __restrict__ l_count, int* __restrict__ l_start, int
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ off, int cap, CellGeom g,
+__global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ off, int cap,
                                                  const int* __restrict__ l_cell,
                                                  const typename Vec4<T>::type* __restrict__ l_tmp,
                                                  int* __restrict__ cursor, int ncell, int* __restrict__ l_sorted,
-                                                 typename Vec4<T>::type* __restrict__ l_loc,
-                                                 int4* __restrict__ l_cellc) {
+                                                 typename Vec4<T>::type* __restrict__ l_loc) {
   const int rep = blockIdx.y;
   const int n = min(off[rep + 1] - off[rep], cap);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -200,8 +200,6 @@ __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ off, in
   const size_t k = (size_t)rep * cap + pos;
   l_sorted[k] = i;
   l_loc[k] = l_tmp[src];
-  const int cz = flat % g.nc[2], cy = (flat / g.nc[2]) % g.nc[1], cx = flat / (g.nc[2] * g.nc[1]);
-  l_cellc[k] = make_int4(cx, cy, cz, flat);
 }
 
 // Electrode charges in the working precision plus their float64 sums q z, q v, q^2, q_+.
@@ -565,6 +563,10 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
 // B-spline weights of one cell-sorted electrolyte site into per-warp shared memory (lanes 0-2
 // handle axes x, y, z).  Its mesh coordinate u = (cell origin) + (local offset) K/L uses the
 // per-cell integer / fraction tables, so only the small local part is formed in precision T.
+__device__ __forceinline__ int4 cell_coords(int flat, const SpmeGeom& sg) {
+  return make_int4(flat / (sg.nc[2] * sg.nc[1]), (flat / sg.nc[2]) % sg.nc[1], flat % sg.nc[2], flat);
+}
+
 template <typename T>
 __device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, const int4& cc, const SpmeGeom& sg,
                                              const int* __restrict__ splI, const T* __restrict__ splF, int lane,
@@ -587,10 +589,12 @@ __device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, co
   __syncwarp();
 }
 
+// Electrolyte charges onto the mesh, in input order: k_bin's cell-local coordinates and cell index
+// per site (no dependence on the sorted cell list, which is built concurrently on the side stream).
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, int cap, SpmeGeom sg,
-                                                     const typename Vec4<T>::type* __restrict__ l_loc,
-                                                     const int4* __restrict__ l_cellc, const int* __restrict__ splI,
+                                                     const typename Vec4<T>::type* __restrict__ l_tmp,
+                                                     const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                      const T* __restrict__ splF, T* __restrict__ mesh) {
   __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
   __shared__ int si0[8][3];
@@ -603,8 +607,8 @@ __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int i = first; i < n; i += nw) {
     const size_t k = (size_t)rep * cap + i;
-    const auto p = l_loc[k];
-    site_weights<T>(p, l_cellc[k], sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
+    const auto p = l_tmp[k];
+    site_weights<T>(p, cell_coords(l_cell[k], sg), sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
     for (int task = lane; task < P * P; task += 32) {
       const int ty = task / P, tz = task - ty * P;
       const int gy = wrap_index(si0[wib][1] - ty, K2), gz = wrap_index(si0[wib][2] - tz, K3);
@@ -714,14 +718,13 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
   }
 }
 
-// k-space force on the (cell-sorted) electrolyte sites: F = -Q grad(phi_mesh) + Q E_z z-hat, written
-// (not added) at the original index.  E_z = -dpsi / L_z (finite field) - KE 4 pi / V M_z (slab).
+// k-space force on the electrolyte sites (input order): F = -Q grad(phi_mesh) + Q E_z z-hat plus the
+// real-space force f_pair, written (not added) at the site's index.  E_z = -dpsi / L_z (finite field) - KE 4 pi / V M_z (slab).
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi, const int* __restrict__ off,
                                                        int cap, SpmeGeom sg,
-                                                       const typename Vec4<T>::type* __restrict__ l_loc,
-                                                       const int4* __restrict__ l_cellc,
-                                                       const int* __restrict__ l_sorted, const int* __restrict__ splI,
+                                                       const typename Vec4<T>::type* __restrict__ l_tmp,
+                                                       const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                        const T* __restrict__ splF, const double* __restrict__ dpsi,
                                                        double ff_over_lz, double slab_coef,
                                                        const double* __restrict__ scal,
@@ -738,8 +741,8 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   for (int i = first; i < n; i += nw) {
     const size_t k = (size_t)rep * cap + i;
-    const auto p = l_loc[k];
-    site_weights<T>(p, l_cellc[k], sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
+    const auto p = l_tmp[k];
+    site_weights<T>(p, cell_coords(l_cell[k], sg), sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
     T gx = 0, gy = 0, gz = 0;
     for (int task = lane; task < P * P; task += 32) {
       const int ty = task / P, tz = task - ty * P;
@@ -763,9 +766,8 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
       const double q = (double)p.w;
       const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
       const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
-      const int orig = l_sorted[k];
-      const size_t gi = 3 * (size_t)(o + orig);
-      const double* fp = f_pair + 3 * ((size_t)rep * cap + orig);
+      const size_t gi = 3 * (size_t)(o + i);
+      const double* fp = f_pair + 3 * k;
       F[gi + 0] = -q * (double)gx * sg.kl[0] + fp[0];
       F[gi + 1] = -q * (double)gy * sg.kl[1] + fp[1];
       F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf + fp[2];
@@ -1392,6 +1394,7 @@ static SpmeGeom spme_geom(const cpm_ctx* c) {
   s.spl_off[0] = 0;
   s.spl_off[1] = c->nc[0];
   s.spl_off[2] = c->nc[0] + c->nc[1];
+  for (int d = 0; d < 3; ++d) s.nc[d] = c->nc[d];
   s.P = c->P;
   s.Mr_s = c->Mr_s;
   s.Mc_s = c->Mc_s;
@@ -1536,6 +1539,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   const size_t pc_smem = sizeof(V4) * kPairSrcCap;   // staged sources of the cell-block pair kernel
   const dim3 gsite((cap + 255) / 256, nrep);
 
+  const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
+  cudaStream_t sside = fork ? c->side : st;
   // ---- prepare: cell list ----
   {
     PhaseTimer pt(c, st, CPM_PH_CELL_LIST);
@@ -1544,11 +1549,18 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     k_bin<T><<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, l_tmp, c->ncell, c->scal,
                                     c->status);
     STEP_LAUNCH();
-    k_scan<<<nrep, 1024, 0, st>>>(c->l_count, c->l_start, c->ncell);
+    // The sorted cell list serves only the real-space pair kernels, which run on the side stream:
+    // fork here, so the counting sort overlaps the mesh work on the main stream (which reads k_bin's
+    // per-site arrays).  Joined before the first main-stream use of the sorted arrays.
+    if (fork) {
+      CPM_CUDA(cudaEventRecord(c->ev_fork, st));
+      CPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
+    k_scan<<<nrep, 1024, 0, sside>>>(c->l_count, c->l_start, c->ncell);
     STEP_LAUNCH();
-    k_scatter<T><<<gsite, 256, 0, st>>>(off, cap, g, c->l_cell, l_tmp, c->l_count, c->ncell, c->l_sorted, l_loc,
-                                        c->l_cellc);
+    k_scatter<T><<<gsite, 256, 0, sside>>>(off, cap, c->l_cell, l_tmp, c->l_count, c->ncell, c->l_sorted, l_loc);
     STEP_LAUNCH();
+    if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
   }
 
   PairSrc src_elyt{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, nullptr, 0, 0.0, -1};
@@ -1567,16 +1579,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, nullptr, nullptr, c->phi_real};
     PairSrc s = src_elyt;
     s.beta = c->p.eta;
-    const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
-    cudaStream_t sb = fork ? c->side : st;
-    if (fork) {
-      CPM_CUDA(cudaEventRecord(c->ev_fork, st));
-      CPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
-    }
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sb>>>(tg, s, none, g, c->p.alpha,
-                                                                               kPairSrcCap, c->scal);
+      k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sside>>>(tg, s, none, g, c->p.alpha,
+                                                                                  kPairSrcCap, c->scal);
       STEP_LAUNCH();
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
@@ -1584,7 +1590,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     {
       PhaseTimer pt(c, st, CPM_PH_B_SPREAD);
       CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_loc, c->l_cellc, c->spl_I, splF,
+      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
                                                                   (T*)c->mesh_r);
       STEP_LAUNCH();
     }
@@ -1691,8 +1697,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   }
 
   if (f_elyt || f_elec || energy) {
-    const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
-    cudaStream_t sp = fork ? c->side : st;
+    cudaStream_t sp = sside;
     {
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
       k_charge_prep<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal);
@@ -1728,7 +1733,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     {
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
       CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_loc, c->l_cellc, c->spl_I, splF,
+      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
                                                                   (T*)c->mesh_r);
       STEP_LAUNCH();
       k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(qT, ne, c->e_base, e_th, sg, (T*)c->mesh_r);
@@ -1741,10 +1746,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
     if (f_elyt) {
-      k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, cap, sg, l_loc,
-                                                                    c->l_cellc, c->l_sorted, c->spl_I, splF, dpsi,
-                                                                    ff_over_lz, slab_coef, c->scal, c->f_pair,
-                                                                    f_elyt);
+      k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, cap, sg, l_tmp,
+                                                                    c->l_cell, c->spl_I, splF, dpsi, ff_over_lz,
+                                                                    slab_coef, c->scal, c->f_pair, f_elyt);
       STEP_LAUNCH();
     }
     if (f_elec) {
@@ -1779,6 +1783,11 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
                                                          ff_over_lz, closed_form ? 1 : 0, energy);
       STEP_LAUNCH();
     }
+  }
+  // every side-stream branch ends joined into the caller's stream (required to end a capture)
+  if (fork) {
+    CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
   }
   return CPM_OK;
 }
@@ -1864,7 +1873,6 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
     CPM_CUDA(cudaMalloc(&c->l_loc64, v4 * R * cap));
   CPM_CUDA(cudaMalloc(&c->l_tmp, v4 * R * cap));
   CPM_CUDA(cudaMalloc(&c->qT, tsz * R * ne));
-  CPM_CUDA(cudaMalloc(&c->l_cellc, sizeof(int4) * R * cap));
   CPM_CUDA(cudaMalloc(&c->phi_real, sizeof(double) * R * ne));
   CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * c->ldb));
   CPM_CUDA(cudaMemset(c->b_tmp, 0, sizeof(double) * R * c->ldb));
@@ -2067,7 +2075,7 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   const size_t cap = ctx->p.max_elyt, ncell = ctx->ncell;
   const size_t sizes[] = {tsz * ctx->Mr_s,          tsz * ctx->Mr_s,             2 * tsz * ctx->Mc_s,
                           sizeof(int) * cap,        sizeof(int) * ncell,         sizeof(int) * (ncell + 1),
-                          sizeof(int) * cap,        v4 * cap,                    sizeof(int4) * cap,
+                          sizeof(int) * cap,        v4 * cap,                    0 /* unused slot */,
                           sizeof(double) * ctx->ne, sizeof(double) * ctx->ldb,   sizeof(float) * 2 * ctx->ldx,
                           sizeof(double) * cpm::NSCAL, v4 * cap,                 tsz * ctx->ne,
                           sizeof(double) * 2 * ctx->ldh, sizeof(double) * 2 * ctx->nh};
@@ -2100,7 +2108,6 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   t.l_sorted = reinterpret_cast<int*>(base + offs[6]);
   t.l_loc32 = ctx->mixed ? reinterpret_cast<float4*>(base + offs[7]) : nullptr;
   t.l_loc64 = ctx->mixed ? nullptr : reinterpret_cast<double4_32a*>(base + offs[7]);
-  t.l_cellc = reinterpret_cast<int4*>(base + offs[8]);
   t.phi_real = reinterpret_cast<double*>(base + offs[9]);
   t.b_tmp = reinterpret_cast<double*>(base + offs[10]);
   t.b32 = reinterpret_cast<float*>(base + offs[11]);
