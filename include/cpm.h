@@ -293,16 +293,30 @@ enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1, CPM_SAPPLY
  * this context (the streaming variants need CPM_MIXED and rows of at most 25,600 entries). */
 int cpm_set_sapply_variant(cpm_ctx* ctx, int32_t variant);
 
+/* Mesh convolution of the mixed-precision path (cpm_set_fft_variant, cpm_autotune):
+ *   CPM_FFT_LIBRARY  cuFFT real-to-complex / complex-to-real with a separate influence kernel;
+ *   CPM_FFT_OWN      this library's float32 transform in five launches (z, y, x with the influence
+ *                    function between the forward and inverse transforms, y, z), each line in
+ *                    shared memory as a four-step direct transform.  Available when the x and y
+ *                    mesh sizes fit the shared-memory tiles (at most 400 points).
+ * Float64 contexts always use the library transform. */
+enum cpm_fft_variant { CPM_FFT_LIBRARY = 0, CPM_FFT_OWN = 1 };
+
+/* cpm_set_fft_variant - select the mesh convolution; CPM_ERR_ARG if it is not available. */
+int cpm_set_fft_variant(cpm_ctx* ctx, int32_t variant);
+
 /*
  * cpm_autotune - time every available S-apply variant on the given single-replica input (five
  * cpm_step_charges calls each after a warm-up, each started with a cold L2 cache, CUDA events on
- * `stream`), keep the fastest (median) in the context and write it to *variant_host (may be NULL).
+ * `stream`), keep the fastest (median) in the context; then, with that S-apply, the two mesh
+ * convolutions (cpm_fft_variant), keeping the faster.  choice_host[2] (may be NULL) receives the
+ * kept (cpm_sapply_variant, cpm_fft_variant).
  * Allocates and frees a scratch buffer of twice the L2 size.  The arguments are those of
  * cpm_step_charges with n_rep = 1; q_dev receives the charges.  Synchronises `stream`; not for
  * use during graph capture.  Without an available alternative it keeps the current variant.
  */
 int cpm_autotune(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const double* elyt_xyzq_dev,
-                 const double* dpsi_dev, double* q_dev, void* stream, int32_t* variant_host);
+                 const double* dpsi_dev, double* q_dev, void* stream, int32_t* choice_host);
 
 /* cpm_destroy - free the context and everything it owns (NULL is accepted). */
 void cpm_destroy(cpm_ctx* ctx);

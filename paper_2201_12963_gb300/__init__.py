@@ -23,7 +23,8 @@ DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
-            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_autotune",
+            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant",
+            "cpm_autotune",
             "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
 PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
@@ -72,7 +73,8 @@ def _load():
     lib.cpm_step_charges_static.argtypes = [vp, pi32, pd, pd, pd, pd, pd, vp]
     lib.cpm_matrix_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_set_sapply_variant.argtypes = [vp, i32]
-    lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, ctypes.POINTER(i32)]
+    lib.cpm_set_fft_variant.argtypes = [vp, i32]
+    lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, pi32]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
     lib.cpm_strerror.argtypes = [ctypes.c_int]
@@ -267,17 +269,28 @@ def cpm_set_sapply_variant(ctx: Context, variant):
     _check(_lib.cpm_set_sapply_variant(ctx.handle, v), "cpm_set_sapply_variant")
 
 
-def cpm_autotune(ctx: Context, offsets, xyzq, dpsi, q, stream=None) -> str:
-    """Time the available S-apply variants on this input (one replica); keeps and returns the fastest."""
+FFT_VARIANTS = {"library": 0, "own": 1}               # enum cpm_fft_variant
+
+
+def cpm_set_fft_variant(ctx: Context, variant):
+    v = FFT_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(_lib.cpm_set_fft_variant(ctx.handle, v), "cpm_set_fft_variant")
+
+
+def cpm_autotune(ctx: Context, offsets, xyzq, dpsi, q, stream=None):
+    """Time the available S-apply kernels and mesh convolutions on this input (one replica); keeps
+    and returns the fastest as (S-apply variant, transform variant) names."""
     import torch
     ne = ctx.n_elec
     p_off = _dev(offsets, torch.int32, "offsets", 2)
     p_x = _dev(xyzq, torch.float64, "xyzq")
     p_d = _dev(dpsi, torch.float64, "dpsi", 1)
-    out = ctypes.c_int32()
+    out = (ctypes.c_int32 * 2)()
     _check(_lib.cpm_autotune(ctx.handle, p_off, p_x, p_d, _dev(q, torch.float64, "q", ne), _stream_ptr(stream),
-                             ctypes.byref(out)), "cpm_autotune")
-    return {v: k for k, v in SAPPLY_VARIANTS.items()}[out.value]
+                             out), "cpm_autotune")
+    names_s = {v: k for k, v in SAPPLY_VARIANTS.items()}
+    names_f = {v: k for k, v in FFT_VARIANTS.items()}
+    return names_s[out[0]], names_f[out[1]]
 
 
 def cpm_status(ctx: Context, stream=None) -> int:

@@ -106,6 +106,13 @@ struct cpm_ctx {
   int sapply_variant = 0;
   double* qpart = nullptr;
   int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
+  // mesh convolution variant (enum cpm_fft_variant) and the tables of this library's own
+  // float32 transform: per-axis four-step split K = n1 n2 and twiddles exp(-2 pi i t / K)
+  int fft_variant = 0;
+  bool fft_own_ok = false;
+  float2* fft_tw = nullptr;
+  int fft_n1[3] = {1, 1, 1};
+  int fft_tw_off[3] = {0, 0, 0};
   double dqdpsi = 0;
   // SPME
   int K[3] = {0, 0, 0};
@@ -259,7 +266,62 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 
 __device__ __forceinline__ void latch_error(int* status, int bit) { atomicOr(status, bit); }
 
+// Running sums in the working precision: float32 with a compensation term (TwoSum), float64 plain.
+template <typename T> struct Acc;
+
+template <> struct Acc<double> {
+  double s = 0.0, c = 0.0;                     // c: an externally supplied correction (plain sums here)
+  __device__ __forceinline__ void add(double x) { s += x; }
+  __device__ __forceinline__ void warp_reduce() {
+    s = warp_sum(s + c);
+    c = 0.0;
+  }
+  __device__ __forceinline__ double value() const { return s + c; }
+};
+
+template <> struct Acc<float> {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float bp = t - s;
+    c += (s - (t - bp)) + (x - bp);
+    s = t;
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
+      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
+      add(s2);
+      c += c2;
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
+
+template <typename T> __device__ __forceinline__ T warp_sum_t(T v) { return warp_sum(v); }
+
+// block-wide sum of up to NV doubles held by lane 0 of every warp; thread 0 adds into dst[k].
+template <int NV>
+__device__ __forceinline__ void block_atomic_add(double (&v)[NV], double* const (&dst)[NV]) {
+  __shared__ double red[NV][32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0)
+    for (int k = 0; k < NV; ++k) red[k][warp] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < NV; ++k) {
+      double s = 0;
+      for (int w = 0; w < nw; ++w) s += red[k][w];
+      if (dst[k] && s != 0.0) atomicAdd(dst[k], s);
+    }
+  }
+}
+
+
 }  // namespace cpm
 
 // Entry points implemented in cpm_step.cu, used by the build (Sv, checks).
 int cpm_internal_alloc_step_buffers(cpm_ctx* c);
+int cpm_internal_fft_setup(cpm_ctx* c);
+int cpm_internal_convolve_own(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st);

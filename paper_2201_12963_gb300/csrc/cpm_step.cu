@@ -52,60 +52,6 @@ __device__ __forceinline__ double wrap_d(double x, double L, double invL) {
 }
 
 // ------------------------------------------------------------------------------------------
-// accumulators: compensated float32 (TwoSum) for T = float, plain float64 for T = double
-// ------------------------------------------------------------------------------------------
-template <typename T> struct Acc;
-
-template <> struct Acc<double> {
-  double s = 0.0, c = 0.0;                     // c: an externally supplied correction (plain sums here)
-  __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ void warp_reduce() {
-    s = warp_sum(s + c);
-    c = 0.0;
-  }
-  __device__ __forceinline__ double value() const { return s + c; }
-};
-
-template <> struct Acc<float> {
-  float s = 0.f, c = 0.f;
-  __device__ __forceinline__ void add(float x) {
-    const float t = s + x;
-    const float bp = t - s;
-    c += (s - (t - bp)) + (x - bp);
-    s = t;
-  }
-  __device__ __forceinline__ void warp_reduce() {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const float s2 = __shfl_xor_sync(0xffffffffu, s, o);
-      const float c2 = __shfl_xor_sync(0xffffffffu, c, o);
-      add(s2);
-      c += c2;
-    }
-  }
-  __device__ __forceinline__ double value() const { return (double)s + (double)c; }
-};
-
-template <typename T> __device__ __forceinline__ T warp_sum_t(T v) { return warp_sum(v); }
-
-// block-wide sum of up to NV doubles held by lane 0 of every warp; thread 0 adds into dst[k].
-template <int NV>
-__device__ __forceinline__ void block_atomic_add(double (&v)[NV], double* const (&dst)[NV]) {
-  __shared__ double red[NV][32];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  if (lane == 0)
-    for (int k = 0; k < NV; ++k) red[k][warp] = v[k];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 0; k < NV; ++k) {
-      double s = 0;
-      for (int w = 0; w < nw; ++w) s += red[k][w];
-      if (dst[k] && s != 0.0) atomicAdd(dst[k], s);
-    }
-  }
-}
-
-// ------------------------------------------------------------------------------------------
 // prepare: counting sort of the electrolyte into cells
 // ------------------------------------------------------------------------------------------
 // Per site: wrap into the box, cell index, cell-local coordinates (float64 arithmetic, stored in
@@ -1452,6 +1398,8 @@ template <> struct FftOps<double> {
 template <typename T>
 static int convolve(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st) {
   using C2 = typename FftOps<T>::C2;
+  if (sizeof(T) == sizeof(float) && c->fft_variant == CPM_FFT_OWN && c->fft_own_ok)
+    return cpm_internal_convolve_own(c, nrep, energy_slot, st);
   const int b = (nrep == c->p.max_replicas && c->have_plan[1]) ? 1 : 0;
   CPM_LIB(cufftSetStream(c->plan_r2c[b], st) == CUFFT_SUCCESS, "cufftSetStream");
   CPM_LIB(cufftSetStream(c->plan_c2r[b], st) == CUFFT_SUCCESS, "cufftSetStream");
@@ -1846,6 +1794,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_TRY(pair_cell_attributes());
   CPM_TRY(tc_attributes());
   CPM_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev));
+  CPM_TRY(cpm_internal_fft_setup(c));
   if (stream_available(c)) {
     CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_stream<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   cpm::SS_SMEM_MAX));
@@ -1935,14 +1884,21 @@ extern "C" int cpm_set_sapply_variant(cpm_ctx* c, int32_t variant) {
   return CPM_ERR_ARG;
 }
 
+extern "C" int cpm_set_fft_variant(cpm_ctx* c, int32_t variant) {
+  if (!c) return CPM_ERR_ARG;
+  if (variant == CPM_FFT_LIBRARY || (variant == CPM_FFT_OWN && c->fft_own_ok)) {
+    c->fft_variant = variant;
+    return CPM_OK;
+  }
+  cpm::set_error("cpm_set_fft_variant: variant %d is not available for this context", variant);
+  return CPM_ERR_ARG;
+}
+
 extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, const double* dpsi, double* q,
-                            void* stream, int32_t* variant_host) {
+                            void* stream, int32_t* choice_host) {
   if (!c || !off || !xyzq || !dpsi || !q) return CPM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int keep = c->sapply_variant;
-  const int cands[3] = {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16};
-  float best_ms = 0.f;
-  int best = keep;
+  const int keep_s = c->sapply_variant, keep_f = c->fft_variant;
   // every timed call starts from a cold L2 (a write of twice its capacity), as inside an MD step
   // whose other work evicts S
   int l2 = 0;
@@ -1954,9 +1910,10 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   CPM_CUDA(cudaEventCreate(&e0));
   CPM_CUDA(cudaEventCreate(&e1));
   int rc = CPM_OK;
-  for (int v : cands) {
-    if (cpm_set_sapply_variant(c, v) != CPM_OK) continue;
-    rc = cpm_step_charges(c, 1, off, xyzq, dpsi, q, nullptr, nullptr, st);          // warm-up
+  // median of five timed charge updates after a warm-up; < 0 if the configuration is unavailable
+  auto time_config = [&](int sv, int fv, float* med) -> bool {
+    if (cpm_set_sapply_variant(c, sv) != CPM_OK || cpm_set_fft_variant(c, fv) != CPM_OK) return false;
+    rc = cpm_step_charges(c, 1, off, xyzq, dpsi, q, nullptr, nullptr, st);
     float ms[5];
     for (int k = 0; k < 5 && rc == CPM_OK; ++k) {
       cudaMemsetAsync(flush, k, flush_bytes, st);
@@ -1966,18 +1923,31 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
       else cudaEventElapsedTime(&ms[k], e0, e1);
     }
-    if (rc != CPM_OK) break;
+    if (rc != CPM_OK) return false;
     std::sort(ms, ms + 5);
-    if (best_ms == 0.f || ms[2] < best_ms) {
-      best_ms = ms[2];
-      best = v;
+    *med = ms[2];
+    return true;
+  };
+  // the S-apply kernel first (library transform), then the transform with the chosen S-apply
+  int best_s = keep_s, best_f = CPM_FFT_LIBRARY;
+  float best_ms = 0.f, t = 0.f;
+  for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16}) {
+    if (time_config(sv, CPM_FFT_LIBRARY, &t) && (best_ms == 0.f || t < best_ms)) {
+      best_ms = t;
+      best_s = sv;
     }
+    if (rc != CPM_OK) break;
   }
+  if (rc == CPM_OK && time_config(best_s, CPM_FFT_OWN, &t) && t < best_ms) best_f = CPM_FFT_OWN;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(flush);
-  c->sapply_variant = (rc == CPM_OK) ? best : keep;
-  if (variant_host) *variant_host = c->sapply_variant;
+  c->sapply_variant = (rc == CPM_OK) ? best_s : keep_s;
+  c->fft_variant = (rc == CPM_OK) ? best_f : keep_f;
+  if (choice_host) {
+    choice_host[0] = c->sapply_variant;
+    choice_host[1] = c->fft_variant;
+  }
   return rc;
 }
 

@@ -48,8 +48,8 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         assert abs(qs[v].sum()) <= 1e-12
     assert np.max(np.abs(qs["rows"] - qs["stream"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["stream16"])) <= 1e-6
-    choice = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
-    assert choice in ("rows", "stream", "stream16")
+    choice, transform = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
+    assert choice in ("rows", "stream", "stream16") and transform in ("library", "own")
     s.charges()
     # float32 mesh spreading adds with atomics in no fixed order: repeated mixed-precision runs
     # differ at float32 rounding
@@ -62,3 +62,46 @@ def test_stream_variant_needs_mixed_precision(plain_ff):
     with pytest.raises(g.CPMError):
         g.cpm_set_sapply_variant(s.ctx, "stream")
     g.cpm_set_sapply_variant(s.ctx, "rows")
+
+
+@pytest.mark.parametrize("case", ["ff", "dc", "slab"])
+def test_own_mesh_transform_matches_library_and_oracle(plain_ff, case):
+    """The library's own float32 mesh convolution (five launches, four-step line transforms) against
+    cuFFT in the same context: charges, forces and energies to float32 rounding, and both against
+    the oracle at the charge and force bars."""
+    import dataclasses
+    g, System = _lib()
+    if case == "ff":
+        w, out = plain_ff[0], plain_ff[2]
+    elif case == "dc":
+        w = _cases(plain_ff)["dc"][0]
+        out = ocpm.Reference(w).step()
+    else:
+        base = synth.tiny_cell(seed=4, n_pairs=4)
+        w = dataclasses.replace(base, geometry="slab", grid=(18, 16, 216))
+        out = ocpm.Reference(w).step()
+    s = System(w, "mixed", order=8)
+    res = {}
+    for v in ("library", "own"):
+        g.cpm_set_fft_variant(s.ctx, v)
+        s.charges()
+        s.forces(elec=True, energy=True)
+        assert g.cpm_status(s.ctx) == 0
+        res[v] = s.results()
+        r = res[v]
+        assert np.max(np.abs(r["q"][0] - out["q"])) <= 1e-5
+        F, Fo = r["F_elyt"][0], out["F_elyt"]
+        assert np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum()) <= 1e-5
+        assert abs(r["energy"][0][0] - out["U"]) <= 2e-6 * abs(out["U"])
+    a, b = res["library"], res["own"]
+    assert np.max(np.abs(a["q"][0] - b["q"][0])) <= 1e-6
+    Fa, Fb = a["F_elyt"][0], b["F_elyt"][0]
+    assert np.sqrt(((Fa - Fb) ** 2).sum() / (Fa ** 2).sum()) <= 2e-6
+    assert abs(a["energy"][0][0] - b["energy"][0][0]) <= 1e-6 * abs(a["energy"][0][0])
+
+
+def test_own_mesh_transform_needs_mixed_precision(plain_ff):
+    g, System = _lib()
+    s = System(plain_ff[0], "fp64")
+    with pytest.raises(g.CPMError):
+        g.cpm_set_fft_variant(s.ctx, "own")
