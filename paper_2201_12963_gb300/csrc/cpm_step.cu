@@ -251,9 +251,9 @@ struct CellPairTgt {
 };
 
 constexpr int PC_MAXT = 64;        // targets per pass of a block
-constexpr int kPairSrcCap = 2048;  // sources staged per pass (dynamic shared memory)
+constexpr int kPairSrcCap = 1024;  // sources staged per pass (dynamic shared memory)
 constexpr int PC_MAXSTEN = kMaxStencil;
-constexpr int PC_THREADS = 256;
+constexpr int PC_THREADS = 128;
 
 template <typename T, bool FORCE>
 __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
