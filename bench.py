@@ -241,7 +241,7 @@ def run_gb300(args):
     s = System(w, args.precision, device=dev, **system_options(args.workload))
     torch.cuda.synchronize(dev)
     build_s = time.perf_counter() - tb
-    sapply_variant, fft_variant = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)   # kernel choices
+    sapply_variant, fft_variant, mesh_variant = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
 
     # the whole step captured once into a CUDA graph
     side = torch.cuda.Stream(dev)
@@ -363,6 +363,7 @@ def run_gb300(args):
            "config": {"workload": WORKLOADS[args.workload][0], "geometry": GEOMETRY_NAME[args.workload],
                       "precision": args.precision, "build_s": round(build_s, 2),
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
+                      "charge_assignment": mesh_variant,
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
                       "graph": "whole step captured in one CUDA graph", "steps_per_s": round(steps_per_s, 1),

@@ -305,13 +305,30 @@ enum cpm_fft_variant { CPM_FFT_LIBRARY = 0, CPM_FFT_OWN = 1 };
 /* cpm_set_fft_variant - select the mesh convolution; CPM_ERR_ARG if it is not available. */
 int cpm_set_fft_variant(cpm_ctx* ctx, int32_t variant);
 
+/* Charge assignment and force interpolation of the mixed-precision path (cpm_set_mesh_variant,
+ * cpm_autotune):
+ *   CPM_MESH_SITES  one warp per site in input order, B-spline stencils added into the mesh with
+ *                   float32 atomics and interpolated from it directly;
+ *   CPM_MESH_BRICK  one block per group of 2 x 2 x 2 real-space cells of the cell-sorted sites: the
+ *                   stencils of the group are accumulated in a shared-memory brick that one TMA
+ *                   tensor reduction adds into a halo-padded mesh (folded onto the periodic mesh
+ *                   before the transform); forces are interpolated from a brick of the padded
+ *                   potential loaded by one TMA tensor copy.
+ * Float64 contexts always use CPM_MESH_SITES. */
+enum cpm_mesh_variant { CPM_MESH_SITES = 0, CPM_MESH_BRICK = 1 };
+
+/* cpm_set_mesh_variant - select the charge assignment; CPM_ERR_ARG if it is not available. */
+int cpm_set_mesh_variant(cpm_ctx* ctx, int32_t variant);
+
 /*
  * cpm_autotune - time every available S-apply variant on the given single-replica input (five
- * cpm_step_charges calls each after a warm-up, each started with a cold L2 cache, CUDA events on
+ * calls each after a warm-up, each started with a cold L2 cache, CUDA events on
  * `stream`), keep the fastest (median) in the context; then, with that S-apply, the two mesh
- * convolutions (cpm_fft_variant), keeping the faster.  choice_host[2] (may be NULL) receives the
- * kept (cpm_sapply_variant, cpm_fft_variant).
- * Allocates and frees a scratch buffer of twice the L2 size.  The arguments are those of
+ * convolutions (cpm_fft_variant), then the two charge assignments (cpm_mesh_variant), keeping the
+ * faster each time.  Each timed call is a whole cpm_step (scratch force and energy outputs).
+ * choice_host[3] (may be NULL) receives the kept (cpm_sapply_variant, cpm_fft_variant,
+ * cpm_mesh_variant).
+ * Allocates and frees a scratch buffer of twice the L2 size and scratch outputs.  The arguments are those of
  * cpm_step_charges with n_rep = 1; q_dev receives the charges.  Synchronises `stream`; not for
  * use during graph capture.  Without an available alternative it keeps the current variant.
  */

@@ -23,7 +23,7 @@ DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
-            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant",
+            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
             "cpm_autotune",
             "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
@@ -74,6 +74,7 @@ def _load():
     lib.cpm_matrix_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_set_sapply_variant.argtypes = [vp, i32]
     lib.cpm_set_fft_variant.argtypes = [vp, i32]
+    lib.cpm_set_mesh_variant.argtypes = [vp, i32]
     lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, pi32]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
@@ -277,20 +278,29 @@ def cpm_set_fft_variant(ctx: Context, variant):
     _check(_lib.cpm_set_fft_variant(ctx.handle, v), "cpm_set_fft_variant")
 
 
+MESH_VARIANTS = {"sites": 0, "brick": 1}              # enum cpm_mesh_variant
+
+
+def cpm_set_mesh_variant(ctx: Context, variant):
+    v = MESH_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(_lib.cpm_set_mesh_variant(ctx.handle, v), "cpm_set_mesh_variant")
+
+
 def cpm_autotune(ctx: Context, offsets, xyzq, dpsi, q, stream=None):
-    """Time the available S-apply kernels and mesh convolutions on this input (one replica); keeps
-    and returns the fastest as (S-apply variant, transform variant) names."""
+    """Time the available S-apply kernels, mesh convolutions and charge assignments on this input
+    (one replica); keeps and returns the fastest as (S-apply, transform, assignment) names."""
     import torch
     ne = ctx.n_elec
     p_off = _dev(offsets, torch.int32, "offsets", 2)
     p_x = _dev(xyzq, torch.float64, "xyzq")
     p_d = _dev(dpsi, torch.float64, "dpsi", 1)
-    out = (ctypes.c_int32 * 2)()
+    out = (ctypes.c_int32 * 3)()
     _check(_lib.cpm_autotune(ctx.handle, p_off, p_x, p_d, _dev(q, torch.float64, "q", ne), _stream_ptr(stream),
                              out), "cpm_autotune")
     names_s = {v: k for k, v in SAPPLY_VARIANTS.items()}
     names_f = {v: k for k, v in FFT_VARIANTS.items()}
-    return names_s[out[0]], names_f[out[1]]
+    names_m = {v: k for k, v in MESH_VARIANTS.items()}
+    return names_s[out[0]], names_f[out[1]], names_m[out[2]]
 
 
 def cpm_status(ctx: Context, stream=None) -> int:

@@ -974,7 +974,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
-                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw};
+                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int b = 0; b < 2; ++b)
@@ -984,6 +984,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
     }
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
+  if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cublas) cublasDestroy(c->cublas);
   if (c->solver) cusolverDnDestroy(c->solver);

@@ -2,6 +2,7 @@
 // plumbing, and small device helpers (cardinal B-splines, warp reductions, cell geometry).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cufft.h>
 #include <cublas_v2.h>
@@ -113,6 +114,17 @@ struct cpm_ctx {
   float2* fft_tw = nullptr;
   int fft_n1[3] = {1, 1, 1};
   int fft_tw_off[3] = {0, 0, 0};
+  // mesh charge assignment / force interpolation variant (enum cpm_mesh_variant) and the
+  // halo-padded mesh of the brick variant with its TMA tensor map
+  int mesh_variant = 0;
+  bool brick_ok = false;
+  int br_S[3] = {1, 1, 1};      // real-space cells per super-cell
+  int br_B[3] = {0, 0, 0};      // box extent (x, y, z)
+  int br_Kp[3] = {0, 0, 0};     // padded mesh extent (x, y, z)
+  long long br_Mp_s = 0;        // per-replica stride of the padded mesh
+  float* br_pad = nullptr;      // [max_rep][br_Mp_s]
+  CUtensorMap br_map;           // 4-D tiled map of br_pad: (z, y, x, replica), box br_B
+  cudaEvent_t ev_sorted = nullptr;   // side stream: sorted cell list complete
   double dqdpsi = 0;
   // SPME
   int K[3] = {0, 0, 0};
@@ -319,9 +331,54 @@ __device__ __forceinline__ void block_atomic_add(double (&v)[NV], double* const 
 }
 
 
+// SPME mesh geometry shared by the mesh kernels.
+struct SpmeGeom {
+  int K[3];
+  int P;
+  double box[3];
+  double kl[3];          // K_d / L_d
+  long long Mr_s, Mc_s;
+  int spl_off[3];        // axis offsets into the cell-origin tables
+  int nc[3];             // real-space cell grid (flat cell index -> cell coordinates)
+};
+
+__device__ __forceinline__ int4 cell_coords(int flat, const SpmeGeom& sg) {
+  return make_int4(flat / (sg.nc[2] * sg.nc[1]), (flat / sg.nc[2]) % sg.nc[1], flat % sg.nc[2], flat);
+}
+
+template <typename T>
+__device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, const int4& cc, const SpmeGeom& sg,
+                                             const int* __restrict__ splI, const T* __restrict__ splF, int lane,
+                                             T (*w)[PMAX], T (*dw)[PMAX], int* i0) {
+  if (lane < 3) {
+    const T loc = lane == 0 ? p.x : (lane == 1 ? p.y : p.z);
+    const int c = lane == 0 ? cc.x : (lane == 1 ? cc.y : cc.z);
+    const int ti = sg.spl_off[lane] + c;
+    const T u = splF[ti] + loc * (T)sg.kl[lane];
+    const T fl = floor(u);
+    T wl[PMAX], dl[PMAX];
+    bspline<T>(u - fl, sg.P, wl, dl);
+#pragma unroll
+    for (int t = 0; t < PMAX; ++t) {
+      w[lane][t] = wl[t];
+      dw[lane][t] = dl[t];
+    }
+    i0[lane] = splI[ti] + (int)fl;
+  }
+  __syncwarp();
+}
+
+// Electrolyte charges onto the mesh, in input order: k_bin's cell-local coordinates and cell index
+// per site (no dependence on the sorted cell list, which is built concurrently on the side stream).
+
 }  // namespace cpm
 
 // Entry points implemented in cpm_step.cu, used by the build (Sv, checks).
 int cpm_internal_alloc_step_buffers(cpm_ctx* c);
 int cpm_internal_fft_setup(cpm_ctx* c);
 int cpm_internal_convolve_own(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st);
+cpm::SpmeGeom cpm_internal_spme_geom(const cpm_ctx* c);
+int cpm_internal_brick_setup(cpm_ctx* c);
+int cpm_internal_spread_brick(cpm_ctx* c, int nrep, const void* l_loc, const float* qT, cudaStream_t st);
+int cpm_internal_gather_f_brick(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const double* dpsi,
+                                double ff_over_lz, double slab_coef, double* F, cudaStream_t st);

@@ -34,15 +34,7 @@ struct CellGeom {
   double rc2;
 };
 
-struct SpmeGeom {
-  int K[3];
-  int P;
-  double box[3];
-  double kl[3];          // K_d / L_d
-  long long Mr_s, Mc_s;
-  int spl_off[3];        // axis offsets into the cell-origin tables
-  int nc[3];             // real-space cell grid (flat cell index -> cell coordinates)
-};
+
 
 __device__ __forceinline__ double wrap_d(double x, double L, double invL) {
   double y = fma(-L, floor(x * invL), x);
@@ -509,34 +501,6 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
 // B-spline weights of one cell-sorted electrolyte site into per-warp shared memory (lanes 0-2
 // handle axes x, y, z).  Its mesh coordinate u = (cell origin) + (local offset) K/L uses the
 // per-cell integer / fraction tables, so only the small local part is formed in precision T.
-__device__ __forceinline__ int4 cell_coords(int flat, const SpmeGeom& sg) {
-  return make_int4(flat / (sg.nc[2] * sg.nc[1]), (flat / sg.nc[2]) % sg.nc[1], flat % sg.nc[2], flat);
-}
-
-template <typename T>
-__device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, const int4& cc, const SpmeGeom& sg,
-                                             const int* __restrict__ splI, const T* __restrict__ splF, int lane,
-                                             T (*w)[PMAX], T (*dw)[PMAX], int* i0) {
-  if (lane < 3) {
-    const T loc = lane == 0 ? p.x : (lane == 1 ? p.y : p.z);
-    const int c = lane == 0 ? cc.x : (lane == 1 ? cc.y : cc.z);
-    const int ti = sg.spl_off[lane] + c;
-    const T u = splF[ti] + loc * (T)sg.kl[lane];
-    const T fl = floor(u);
-    T wl[PMAX], dl[PMAX];
-    bspline<T>(u - fl, sg.P, wl, dl);
-#pragma unroll
-    for (int t = 0; t < PMAX; ++t) {
-      w[lane][t] = wl[t];
-      dw[lane][t] = dl[t];
-    }
-    i0[lane] = splI[ti] + (int)fl;
-  }
-  __syncwarp();
-}
-
-// Electrolyte charges onto the mesh, in input order: k_bin's cell-local coordinates and cell index
-// per site (no dependence on the sorted cell list, which is built concurrently on the side stream).
 template <typename T>
 __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, int cap, SpmeGeom sg,
                                                      const typename Vec4<T>::type* __restrict__ l_tmp,
@@ -1489,6 +1453,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
 
   const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
   cudaStream_t sside = fork ? c->side : st;
+  // brick charge assignment / interpolation (float32 mesh, sorted sites, TMA)
+  const bool brick = c->mixed && c->brick_ok && c->mesh_variant == CPM_MESH_BRICK;
   // ---- prepare: cell list ----
   {
     PhaseTimer pt(c, st, CPM_PH_CELL_LIST);
@@ -1508,7 +1474,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     STEP_LAUNCH();
     k_scatter<T><<<gsite, 256, 0, sside>>>(off, cap, c->l_cell, l_tmp, c->l_count, c->ncell, c->l_sorted, l_loc);
     STEP_LAUNCH();
-    if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    if (fork) {
+      CPM_CUDA(cudaEventRecord(c->ev_sorted, c->side));
+      CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
+    }
   }
 
   PairSrc src_elyt{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, nullptr, 0, 0.0, -1};
@@ -1537,10 +1506,15 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // SPME part
     {
       PhaseTimer pt(c, st, CPM_PH_B_SPREAD);
-      CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                  (T*)c->mesh_r);
-      STEP_LAUNCH();
+      if (brick) {
+        if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_sorted, 0));
+        CPM_TRY(cpm_internal_spread_brick(c, nrep, l_loc, nullptr, st));
+      } else {
+        CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+        k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
+                                                                    (T*)c->mesh_r);
+        STEP_LAUNCH();
+      }
     }
     {
       PhaseTimer pt(c, st, CPM_PH_B_FFT);
@@ -1680,12 +1654,17 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // SPME of all charges
     {
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
-      CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-      k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                  (T*)c->mesh_r);
-      STEP_LAUNCH();
-      k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(qT, ne, c->e_base, e_th, sg, (T*)c->mesh_r);
-      STEP_LAUNCH();
+      if (brick) {
+        if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_sorted, 0));
+        CPM_TRY(cpm_internal_spread_brick(c, nrep, l_loc, (const float*)qT, st));
+      } else {
+        CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
+        k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
+                                                                    (T*)c->mesh_r);
+        STEP_LAUNCH();
+        k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(qT, ne, c->e_base, e_th, sg, (T*)c->mesh_r);
+        STEP_LAUNCH();
+      }
     }
     {
       PhaseTimer pt(c, st, CPM_PH_F_FFT);
@@ -1693,7 +1672,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     }
     if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
-    if (f_elyt) {
+    if (f_elyt && brick) {
+      CPM_TRY(cpm_internal_gather_f_brick(c, nrep, off, l_loc, dpsi, ff_over_lz, slab_coef, f_elyt, st));
+    } else if (f_elyt) {
       k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, cap, sg, l_tmp,
                                                                     c->l_cell, c->spl_I, splF, dpsi, ff_over_lz,
                                                                     slab_coef, c->scal, c->f_pair, f_elyt);
@@ -1790,11 +1771,14 @@ static bool stream_available(const cpm_ctx* c) {
   return c->mixed && sizeof(float) * 2 * (size_t)c->ld32 <= (size_t)cpm::SS_SMEM_MAX;
 }
 
+cpm::SpmeGeom cpm_internal_spme_geom(const cpm_ctx* c) { return cpm::spme_geom(c); }
+
 int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_TRY(pair_cell_attributes());
   CPM_TRY(tc_attributes());
   CPM_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev));
   CPM_TRY(cpm_internal_fft_setup(c));
+  CPM_TRY(cpm_internal_brick_setup(c));
   if (stream_available(c)) {
     CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_stream<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   cpm::SS_SMEM_MAX));
@@ -1836,6 +1820,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+  CPM_CUDA(cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming));
   CPM_CUDA(cudaMalloc(&c->scal, sizeof(double) * R * cpm::NSCAL));
   if (c->mixed && (int)R >= cpm::TC_MIN_REPLICAS) CPM_CUDA(cudaMalloc(&c->qraw32, sizeof(float) * R * ne));
   CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
@@ -1894,11 +1879,21 @@ extern "C" int cpm_set_fft_variant(cpm_ctx* c, int32_t variant) {
   return CPM_ERR_ARG;
 }
 
+extern "C" int cpm_set_mesh_variant(cpm_ctx* c, int32_t variant) {
+  if (!c) return CPM_ERR_ARG;
+  if (variant == CPM_MESH_SITES || (variant == CPM_MESH_BRICK && c->brick_ok)) {
+    c->mesh_variant = variant;
+    return CPM_OK;
+  }
+  cpm::set_error("cpm_set_mesh_variant: variant %d is not available for this context", variant);
+  return CPM_ERR_ARG;
+}
+
 extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, const double* dpsi, double* q,
                             void* stream, int32_t* choice_host) {
   if (!c || !off || !xyzq || !dpsi || !q) return CPM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int keep_s = c->sapply_variant, keep_f = c->fft_variant;
+  const int keep_s = c->sapply_variant, keep_f = c->fft_variant, keep_m = c->mesh_variant;
   // every timed call starts from a cold L2 (a write of twice its capacity), as inside an MD step
   // whose other work evicts S
   int l2 = 0;
@@ -1910,15 +1905,21 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   CPM_CUDA(cudaEventCreate(&e0));
   CPM_CUDA(cudaEventCreate(&e1));
   int rc = CPM_OK;
-  // median of five timed charge updates after a warm-up; < 0 if the configuration is unavailable
-  auto time_config = [&](int sv, int fv, float* med) -> bool {
-    if (cpm_set_sapply_variant(c, sv) != CPM_OK || cpm_set_fft_variant(c, fv) != CPM_OK) return false;
-    rc = cpm_step_charges(c, 1, off, xyzq, dpsi, q, nullptr, nullptr, st);
+  // scratch outputs of the timed steps (forces and energies are part of the step)
+  double *f_scr = nullptr, *e_scr = nullptr;
+  CPM_CUDA(cudaMalloc(&f_scr, sizeof(double) * 3 * (size_t)c->p.max_elyt + 64));
+  CPM_CUDA(cudaMalloc(&e_scr, sizeof(double) * cpm::NENERGY));
+  // median of five timed steps (charges, forces, energy) after a warm-up; false if unavailable
+  auto time_config = [&](int sv, int fv, int mv, float* med) -> bool {
+    if (cpm_set_sapply_variant(c, sv) != CPM_OK || cpm_set_fft_variant(c, fv) != CPM_OK ||
+        cpm_set_mesh_variant(c, mv) != CPM_OK)
+      return false;
+    rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, st);
     float ms[5];
     for (int k = 0; k < 5 && rc == CPM_OK; ++k) {
       cudaMemsetAsync(flush, k, flush_bytes, st);
       cudaEventRecord(e0, st);
-      rc = cpm_step_charges(c, 1, off, xyzq, dpsi, q, nullptr, nullptr, st);
+      rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, st);
       cudaEventRecord(e1, st);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
       else cudaEventElapsedTime(&ms[k], e0, e1);
@@ -1928,25 +1929,37 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
     *med = ms[2];
     return true;
   };
-  // the S-apply kernel first (library transform), then the transform with the chosen S-apply
-  int best_s = keep_s, best_f = CPM_FFT_LIBRARY;
+  // the S-apply kernel first, then the transform, then the charge assignment, each with the
+  // choices made so far
+  int best_s = keep_s, best_f = CPM_FFT_LIBRARY, best_m = CPM_MESH_SITES;
   float best_ms = 0.f, t = 0.f;
   for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16}) {
-    if (time_config(sv, CPM_FFT_LIBRARY, &t) && (best_ms == 0.f || t < best_ms)) {
+    if (time_config(sv, CPM_FFT_LIBRARY, CPM_MESH_SITES, &t) && (best_ms == 0.f || t < best_ms)) {
       best_ms = t;
       best_s = sv;
     }
     if (rc != CPM_OK) break;
   }
-  if (rc == CPM_OK && time_config(best_s, CPM_FFT_OWN, &t) && t < best_ms) best_f = CPM_FFT_OWN;
+  if (rc == CPM_OK && time_config(best_s, CPM_FFT_OWN, CPM_MESH_SITES, &t) && t < best_ms) {
+    best_ms = t;
+    best_f = CPM_FFT_OWN;
+  }
+  if (rc == CPM_OK && time_config(best_s, best_f, CPM_MESH_BRICK, &t) && t < best_ms) {
+    best_ms = t;
+    best_m = CPM_MESH_BRICK;
+  }
+  cudaFree(f_scr);
+  cudaFree(e_scr);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(flush);
   c->sapply_variant = (rc == CPM_OK) ? best_s : keep_s;
   c->fft_variant = (rc == CPM_OK) ? best_f : keep_f;
+  c->mesh_variant = (rc == CPM_OK) ? best_m : keep_m;
   if (choice_host) {
     choice_host[0] = c->sapply_variant;
     choice_host[1] = c->fft_variant;
+    choice_host[2] = c->mesh_variant;
   }
   return rc;
 }
@@ -2085,6 +2098,7 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   t.l_tmp = base + offs[13];
   t.qT = base + offs[14];
   t.qpart = nullptr;                    // the streaming S-apply's partial sums live in the context
+  t.brick_ok = false;                   // so does the padded mesh of the brick charge assignment
   t.ypm = ctx->mirror ? reinterpret_cast<double*>(base + offs[15]) : nullptr;
   t.qpm = ctx->mirror ? reinterpret_cast<double*>(base + offs[16]) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;

@@ -48,8 +48,9 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         assert abs(qs[v].sum()) <= 1e-12
     assert np.max(np.abs(qs["rows"] - qs["stream"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["stream16"])) <= 1e-6
-    choice, transform = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
+    choice, transform, assign = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
     assert choice in ("rows", "stream", "stream16") and transform in ("library", "own")
+    assert assign in ("sites", "brick")
     s.charges()
     # float32 mesh spreading adds with atomics in no fixed order: repeated mixed-precision runs
     # differ at float32 rounding
@@ -105,3 +106,52 @@ def test_own_mesh_transform_needs_mixed_precision(plain_ff):
     s = System(plain_ff[0], "fp64")
     with pytest.raises(g.CPMError):
         g.cpm_set_fft_variant(s.ctx, "own")
+
+
+@pytest.mark.parametrize("case", ["ff", "dc", "slab"])
+def test_brick_charge_assignment_matches_sites_and_oracle(plain_ff, case):
+    """Charge assignment and force interpolation through shared-memory bricks moved by TMA (halo-
+    padded mesh, fold, halo fill) against the per-site atomics in the same context, and both against
+    the oracle: charges, forces (electrolyte and electrode) and energies."""
+    import dataclasses
+    g, System = _lib()
+    if case == "ff":
+        w, out = plain_ff[0], plain_ff[2]
+    elif case == "dc":
+        w = _cases(plain_ff)["dc"][0]
+        out = ocpm.Reference(w).step()
+    else:
+        base = synth.tiny_cell(seed=4, n_pairs=4)
+        w = dataclasses.replace(base, geometry="slab", grid=(18, 16, 216))
+        out = ocpm.Reference(w).step()
+    s = System(w, "mixed", order=8)
+    res = {}
+    for v in ("sites", "brick"):
+        g.cpm_set_mesh_variant(s.ctx, v)
+        for _ in range(2):                       # the second call checks the cleared padded mesh
+            s.charges()
+            s.forces(elec=True, energy=True)
+        assert g.cpm_status(s.ctx) == 0
+        res[v] = s.results()
+        r = res[v]
+        assert np.max(np.abs(r["q"][0] - out["q"])) <= 1e-5
+        F, Fo = r["F_elyt"][0], out["F_elyt"]
+        assert np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum()) <= 1e-5
+        Fe, Feo = r["F_elec"][0], out["F_elec"]
+        assert np.sqrt(((Fe - Feo) ** 2).sum() / (Feo ** 2).sum()) <= 3e-5
+        assert abs(r["energy"][0][0] - out["U"]) <= 2e-6 * abs(out["U"])
+    a, b = res["sites"], res["brick"]
+    assert np.max(np.abs(a["q"][0] - b["q"][0])) <= 1e-6
+    Fa, Fb = a["F_elyt"][0], b["F_elyt"][0]
+    assert np.sqrt(((Fa - Fb) ** 2).sum() / (Fa ** 2).sum()) <= 2e-6
+    # the fused step (charges and forces in one call) through the bricks as well
+    s.step(elec=False, energy=True)
+    assert g.cpm_status(s.ctx) == 0
+    assert np.max(np.abs(s.q.cpu().numpy()[: w.n_elec] - b["q"][0])) <= 1e-6
+
+
+def test_brick_charge_assignment_needs_mixed_precision(plain_ff):
+    g, System = _lib()
+    s = System(plain_ff[0], "fp64")
+    with pytest.raises(g.CPMError):
+        g.cpm_set_mesh_variant(s.ctx, "brick")
