@@ -23,7 +23,7 @@
 
 namespace cpm {
 
-constexpr int BR_THREADS = 128;
+constexpr int BR_THREADS = 256;
 constexpr int BR_WARPS = BR_THREADS / 32;
 constexpr long long BR_WAIT_LIMIT = 1LL << 22;     // mbarrier polls before a load is declared lost
 
@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(BR_THREADS) k_spread_brick(const __grid_consta
   }
 }
 
-// periodic mesh <- padded mesh folded: m[g] = sum over p = g + off (mod K) inside the padded extents.
+// periodic mesh <- padded mesh folded: m[g] = sum over p = g + off (mod K) inside the padded extents
+// (per axis the padded images of g are listed first: one for interior points, two near the faces).
 __global__ void __launch_bounds__(256) k_mesh_fold(const float* __restrict__ pad, float* __restrict__ mesh,
                                                    BrickGeom bg, long long Mr_s) {
   const int rep = blockIdx.y;
@@ -150,21 +151,20 @@ __global__ void __launch_bounds__(256) k_mesh_fold(const float* __restrict__ pad
   const float* pr = pad + (size_t)rep * bg.Mp_s;
   float* mr = mesh + (size_t)rep * Mr_s;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < M; g += (long long)gridDim.x * blockDim.x) {
-    const int gz = (int)(g % bg.K[2]), gy = (int)((g / bg.K[2]) % bg.K[1]), gx = (int)(g / ((long long)bg.K[2] * bg.K[1]));
-    float s = 0.f;
-    for (int mx = -1; mx <= 2; ++mx) {
-      const int px = gx + bg.off + mx * bg.K[0];
-      if (px < 0 || px >= bg.Kp[0]) continue;
-      for (int my = -1; my <= 2; ++my) {
-        const int py = gy + bg.off + my * bg.K[1];
-        if (py < 0 || py >= bg.Kp[1]) continue;
-        for (int mz = -1; mz <= 2; ++mz) {
-          const int pz = gz + bg.off + mz * bg.K[2];
-          if (pz < 0 || pz >= bg.Kp[2]) continue;
-          s += pr[((size_t)px * bg.Kp[1] + py) * bg.Kp[2] + pz];
-        }
-      }
+    const int gi[3] = {(int)(g / ((long long)bg.K[2] * bg.K[1])), (int)((g / bg.K[2]) % bg.K[1]), (int)(g % bg.K[2])};
+    int pv[3][3], np[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      np[d] = 0;
+      for (int p = (gi[d] + bg.off) % bg.K[d]; p < bg.Kp[d]; p += bg.K[d])
+        if (np[d] < 3) pv[d][np[d]++] = p;
     }
+    float s = 0.f;
+    for (int a = 0; a < np[0]; ++a)
+      for (int b = 0; b < np[1]; ++b) {
+        const float* row = pr + ((size_t)pv[0][a] * bg.Kp[1] + pv[1][b]) * bg.Kp[2];
+        for (int e = 0; e < np[2]; ++e) s += row[pv[2][e]];
+      }
     mr[g] = s;
   }
 }
