@@ -209,6 +209,8 @@ def phase_model(phase, s, w, pairs):
         mirror, s_bytes = g.cpm_matrix_layout(s.ctx)
         byt = s_bytes + 8 * ne * 3                # S once, b in, q out, S v
         what = f"two mirror blocks S+- ({ne // 2}^2 each)" if mirror else f"S ({ne}^2)"
+        if s_bytes < (ne // 2 if mirror else ne) ** 2 * fb * (2 if mirror else 1) * 3 // 4:
+            what = "upper-triangle tiles of " + what
         return "hbm", byt, "GB/s", f"{what} x {fb} B + b, Sv, q (float64)"
     if phase in pairs:
         return "alu", PAIR_FLOPS * pairs[phase], "TFLOP/s", f"{pairs[phase]} pairs within r_c x {PAIR_FLOPS} FP32 flops"

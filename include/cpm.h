@@ -200,7 +200,8 @@ int cpm_info(const cpm_ctx* ctx, int32_t* n_elec, int32_t* ncons, int64_t* mesh_
 /*
  * cpm_matrix_layout - how S is stored: *mirror_blocks = 1 for the two mirror blocks of a
  * mirror-symmetric doubled cell (cpm_dc_blocks), else 0; *s_bytes = bytes of stored S the S-apply
- * streams per replica-step (float32 for CPM_MIXED, float64 for CPM_FP64, rows padded to 4).
+ * streams per replica-step with the current S-apply variant (float32 for CPM_MIXED, float64 for
+ * CPM_FP64, rows padded to 4; the packed upper-triangle tiles for CPM_SAPPLY_SYM).
  * Either pointer may be NULL.
  */
 int cpm_matrix_layout(const cpm_ctx* ctx, int32_t* mirror_blocks, int64_t* s_bytes);
@@ -284,10 +285,15 @@ int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const
  *                      added in float64 and finished by a second kernel), 8 16-byte loads of S in
  *                      flight per lane.  Available when the right-hand side fits shared memory
  *                      (rows of at most 25,600 entries);
- *   CPM_SAPPLY_STREAM16  the same with 16 loads in flight per lane.
+ *   CPM_SAPPLY_STREAM16  the same with 16 loads in flight per lane;
+ *   CPM_SAPPLY_SYM     S (or each mirror block) kept as the upper triangle of 128 x 128 float32
+ *                      tiles: one read of an off-diagonal tile serves its rows and, transposed, its
+ *                      columns, so about half the bytes of S are streamed; per-tile partial sums
+ *                      (one writer each) are added by a second kernel.  Same availability as the
+ *                      streaming variants; the packed copy costs half an extra float32 S in memory.
  * Batches of 8 or more replicas use the tensor-core GEMM and 2-7 replicas the row kernel whatever
  * the choice; float64 contexts always use the row kernel. */
-enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1, CPM_SAPPLY_STREAM16 = 2 };
+enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1, CPM_SAPPLY_STREAM16 = 2, CPM_SAPPLY_SYM = 3 };
 
 /* cpm_set_sapply_variant - select the S-apply variant; CPM_ERR_ARG if it is not available for
  * this context (the streaming variants need CPM_MIXED and rows of at most 25,600 entries). */

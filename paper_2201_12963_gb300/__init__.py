@@ -262,7 +262,7 @@ def cpm_matrix_layout(ctx: Context):
     return bool(m.value), int(nb.value)
 
 
-SAPPLY_VARIANTS = {"rows": 0, "stream": 1, "stream16": 2}   # enum cpm_sapply_variant
+SAPPLY_VARIANTS = {"rows": 0, "stream": 1, "stream16": 2, "sym": 3}   # enum cpm_sapply_variant
 
 
 def cpm_set_sapply_variant(ctx: Context, variant):

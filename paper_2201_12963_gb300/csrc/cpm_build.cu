@@ -974,7 +974,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
-                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad};
+                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad, c->sym_S, c->sym_part};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int b = 0; b < 2; ++b)
@@ -1060,8 +1060,13 @@ extern "C" int cpm_matrix_layout(const cpm_ctx* c, int32_t* mirror_blocks, int64
   if (!c) return CPM_ERR_ARG;
   if (mirror_blocks) *mirror_blocks = c->mirror ? 1 : 0;
   if (s_bytes) {
-    const long long rows = c->mirror ? 2LL * c->nh : (long long)c->ne;
-    *s_bytes = rows * (long long)c->ld64 * (c->mixed ? 4 : 8);
+    if (c->sym_ok && c->sapply_variant == CPM_SAPPLY_SYM) {
+      const long long nt = c->sym_nt;
+      *s_bytes = (c->mirror ? 2LL : 1LL) * (nt * (nt + 1) / 2) * 128LL * 128LL * 4LL;
+    } else {
+      const long long rows = c->mirror ? 2LL * c->nh : (long long)c->ne;
+      *s_bytes = rows * (long long)c->ld64 * (c->mixed ? 4 : 8);
+    }
   }
   return CPM_OK;
 }

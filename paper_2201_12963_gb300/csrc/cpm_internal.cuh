@@ -106,6 +106,11 @@ struct cpm_ctx {
   // ([rows of S], float64, zero between calls: its finish kernel clears what it consumed)
   int sapply_variant = 0;
   double* qpart = nullptr;
+  // symmetric packed S (upper-triangle 128 x 128 tiles, float32) and its per-slot partial sums
+  bool sym_ok = false;
+  int sym_nt = 0;
+  float* sym_S = nullptr;
+  float* sym_part = nullptr;
   int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
   // mesh convolution variant (enum cpm_fft_variant) and the tables of this library's own
   // float32 transform: per-axis four-step split K = n1 n2 and twiddles exp(-2 pi i t / K)
@@ -379,6 +384,10 @@ int cpm_internal_fft_setup(cpm_ctx* c);
 int cpm_internal_convolve_own(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st);
 cpm::SpmeGeom cpm_internal_spme_geom(const cpm_ctx* c);
 int cpm_internal_brick_setup(cpm_ctx* c);
+int cpm_internal_sym_setup(cpm_ctx* c);
+int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* xl, const double* b,
+                            const double* dpsi, const double* Sv, const double* W, const double* c1, double* qout,
+                            cudaStream_t st);
 int cpm_internal_spread_brick(cpm_ctx* c, int nrep, const void* l_loc, const float* qT, cudaStream_t st);
 int cpm_internal_gather_f_brick(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const double* dpsi,
                                 double ff_over_lz, double slab_coef, double* F, cudaStream_t st);

@@ -1570,6 +1570,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // streaming variant: mixed precision, one replica, right-hand side fits shared memory
     const bool stream_ok = c->mixed && nrep == 1 && c->qpart &&
                            (c->sapply_variant == CPM_SAPPLY_STREAM || c->sapply_variant == CPM_SAPPLY_STREAM16);
+    const bool sym_ok = c->mixed && nrep == 1 && c->sym_ok && c->sapply_variant == CPM_SAPPLY_SYM;
     {
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
       if (c->mirror) {
@@ -1579,6 +1580,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         STEP_LAUNCH();
         for (int blk = 0; blk < 2; ++blk) {
           const size_t so = (size_t)blk * nh * ldh;
+          if (sym_ok) {
+            CPM_TRY(cpm_internal_sapply_sym(c, blk, c->b32 + (size_t)blk * ldh,
+                                            c->b32 + 2 * (size_t)ldh + (size_t)blk * ldh, c->ypm + (size_t)blk * ldh,
+                                            dpsi, c->Sv + (size_t)blk * nh, c->W + (size_t)blk * 2 * nh,
+                                            c->e_c1m + (size_t)blk * nh, c->qpm + (size_t)blk * nh, st));
+            continue;
+          }
           if (stream_ok) {
             CPM_TRY(sapply_stream(c, c->S32 + so, nh, ldh, c->b32 + (size_t)blk * ldh,
                                   c->b32 + 2 * (size_t)ldh + (size_t)blk * ldh, c->qpart + (size_t)blk * nh,
@@ -1592,6 +1600,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
                          c->Sv + (size_t)blk * nh, c->W + (size_t)blk * 2 * nh, c->e_c1m + (size_t)blk * nh,
                          c->qpm + (size_t)blk * nh, 2 * nh));
         }
+      } else if (sym_ok) {
+        CPM_TRY(cpm_internal_sapply_sym(c, 0, c->b32, c->b32 + c->ldx, b, dpsi, c->Sv, c->W, c->e_c1, q, st));
       } else if (stream_ok) {
         CPM_TRY(sapply_stream(c, c->S32, ne, c->ld32, c->b32, c->b32 + c->ldx, c->qpart, b, dpsi, c->Sv, c->W, c->e_c1,
                               q, st));
@@ -1779,6 +1789,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev));
   CPM_TRY(cpm_internal_fft_setup(c));
   CPM_TRY(cpm_internal_brick_setup(c));
+  CPM_TRY(cpm_internal_sym_setup(c));
   if (stream_available(c)) {
     CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_stream<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   cpm::SS_SMEM_MAX));
@@ -1861,7 +1872,8 @@ extern "C" int cpm_set_sapply_variant(cpm_ctx* c, int32_t variant) {
     c->sapply_variant = variant;
     return CPM_OK;
   }
-  if ((variant == CPM_SAPPLY_STREAM || variant == CPM_SAPPLY_STREAM16) && stream_available(c) && c->qpart) {
+  if (((variant == CPM_SAPPLY_STREAM || variant == CPM_SAPPLY_STREAM16) && stream_available(c) && c->qpart) ||
+      (variant == CPM_SAPPLY_SYM && c->sym_ok)) {
     c->sapply_variant = variant;
     return CPM_OK;
   }
@@ -1933,7 +1945,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   // choices made so far
   int best_s = keep_s, best_f = CPM_FFT_LIBRARY, best_m = CPM_MESH_SITES;
   float best_ms = 0.f, t = 0.f;
-  for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16}) {
+  for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16, CPM_SAPPLY_SYM}) {
     if (time_config(sv, CPM_FFT_LIBRARY, CPM_MESH_SITES, &t) && (best_ms == 0.f || t < best_ms)) {
       best_ms = t;
       best_s = sv;
@@ -2099,6 +2111,7 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
   t.qT = base + offs[14];
   t.qpart = nullptr;                    // the streaming S-apply's partial sums live in the context
   t.brick_ok = false;                   // so does the padded mesh of the brick charge assignment
+  t.sym_ok = false;                     // and the partial sums of the packed S-apply
   t.ypm = ctx->mirror ? reinterpret_cast<double*>(base + offs[15]) : nullptr;
   t.qpm = ctx->mirror ? reinterpret_cast<double*>(base + offs[16]) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;

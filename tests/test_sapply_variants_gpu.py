@@ -38,7 +38,7 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         out = ocpm.Reference(w).step(want_forces=False, want_energy=False)
     s = System(w, "mixed", order=8)
     qs = {}
-    for v in ("rows", "stream", "stream16"):
+    for v in ("rows", "stream", "stream16", "sym"):
         g.cpm_set_sapply_variant(s.ctx, v)
         for _ in range(2):                          # the second call checks the cleared partial sums
             s.charges()
@@ -48,8 +48,9 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         assert abs(qs[v].sum()) <= 1e-12
     assert np.max(np.abs(qs["rows"] - qs["stream"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["stream16"])) <= 1e-6
+    assert np.max(np.abs(qs["rows"] - qs["sym"])) <= 1e-6
     choice, transform, assign = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
-    assert choice in ("rows", "stream", "stream16") and transform in ("library", "own")
+    assert choice in ("rows", "stream", "stream16", "sym") and transform in ("library", "own")
     assert assign in ("sites", "brick")
     s.charges()
     # float32 mesh spreading adds with atomics in no fixed order: repeated mixed-precision runs
