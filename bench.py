@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=None)
+    ap.add_argument("--kernels", default="auto",
+                    help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
+                         "sym,library,sites, to run a fixed kernel choice (profiling captures)")
     ap.add_argument("--workload", default="paper", choices=["paper", "paper-dc", "paper-slab", "large", "dc-large"],
                     help="paper: the paper-scale cell (default); paper-dc / paper-slab: the same cell as a doubled "
                          "cell (6,048 sites, mirror blocks) or a slab (3x z padding); large: the 10,080-site cell; "
@@ -174,12 +177,13 @@ class ClockSampler:
 # dominant kernel; the FFT phases are mostly cuFFT.
 # ----------------------------------------------------------------------------------------------
 PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distance 8, erfc/exp 20, force 12)
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on this workload
-# (profiles/k_pair_cell_paper-cell-ff-mixed.md, profiles/k_sapply32_paper-cell-ff-mixed.md); set an
-# entry to None whenever its kernel changes until it is captured again.
-NCU_TRAFFIC_MIXED = {"paper": {"s_apply": 36.737536e6},
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels, keyed by workload
+# and "phase:kernel variant" (the autotuner may pick another S-apply kernel, whose traffic was not
+# captured: then traffic is null).  Summaries: profiles/k_sapply32_paper-cell-ff-mixed.md,
+# profiles/k_sapply_sym_large-cell-ff-mixed.md.  Set an entry to None whenever its kernel changes.
+NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.737536e6},
                      "paper-dc": {}, "paper-slab": {},
-                     "large": {"s_apply": 409.879552e6},
+                     "large": {"s_apply:sym": 210.907904e6},
                      "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
@@ -243,7 +247,13 @@ def run_gb300(args):
     s = System(w, args.precision, device=dev, **system_options(args.workload))
     torch.cuda.synchronize(dev)
     build_s = time.perf_counter() - tb
-    sapply_variant, fft_variant, mesh_variant = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
+    if args.kernels == "auto":
+        sapply_variant, fft_variant, mesh_variant = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
+    else:
+        sapply_variant, fft_variant, mesh_variant = args.kernels.split(",")
+        g.cpm_set_sapply_variant(s.ctx, sapply_variant)
+        g.cpm_set_fft_variant(s.ctx, fft_variant)
+        g.cpm_set_mesh_variant(s.ctx, mesh_variant)
 
     # the whole step captured once into a CUDA graph
     side = torch.cuda.Stream(dev)
@@ -346,7 +356,8 @@ def run_gb300(args):
         else:
             achieved, peak = amount / sec / 1e12, alu_peak_tflops(clk.get("sm_mhz"))
             src = "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock"
-        traffic = NCU_TRAFFIC_MIXED[args.workload].get(p) if mixed_prec else None
+        key = f"{p}:{sapply_variant}" if p == "s_apply" else p
+        traffic = NCU_TRAFFIC_MIXED[args.workload].get(key) if mixed_prec else None
         return {"bound": bound, "kernel": p, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_per_launch": amount,
                 "launch_ms": round(phase_ms[p], 5), "peak_source": src, "model": desc}
@@ -366,6 +377,7 @@ def run_gb300(args):
                       "precision": args.precision, "build_s": round(build_s, 2),
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
                       "charge_assignment": mesh_variant,
+                      "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
                       "graph": "whole step captured in one CUDA graph", "steps_per_s": round(steps_per_s, 1),
