@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--kernels", default="auto",
                     help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
                          "sym,library,sites, to run a fixed kernel choice (profiling captures)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "paper-dc", "paper-slab", "large", "dc-large"],
+    ap.add_argument("--workload", default="paper", choices=["paper", "paper-dc", "paper-slab", "paper-proximal", "large", "dc-large"],
                     help="paper: the paper-scale cell (default); paper-dc / paper-slab: the same cell as a doubled "
-                         "cell (6,048 sites, mirror blocks) or a slab (3x z padding); large: the 10,080-site cell; "
+                         "cell (6,048 sites, mirror blocks) or a slab (3x z padding); paper-proximal: only the "
+                         "1,008 proximal-layer sites charged; large: the 10,080-site cell; "
                          "dc-large: the 40,320-site doubled cell (mirror blocks, mesh-operator A)")
     return ap.parse_args()
 
@@ -84,6 +85,9 @@ WORKLOADS = {
     "paper-slab": ("paper-scale slab: the 3,024-site cell with z padded 3x (38.34x34.44x504 A Ewald box) and the "
                    "Yeh-Berkowitz dipole correction, 500 CG ion pairs, SPME 40x36x504 order 5, alpha 0.25, r_c 12 A",
                    2000),
+    "paper-proximal": ("paper-scale finite-field cell with only the proximal electrode layers charged (1,008 "
+                       "sites; the further layers are neutral), 500 CG ion pairs, 38.34x34.44x168 A, SPME 40x36x168 "
+                       "order 5, alpha 0.25, r_c 12 A", 2000),
     "large": ("scaled finite-field cell: 10,080 electrode sites (3-layer graphite x 2), 5,000 point-ion pairs "
               "(10,000 sites), 63.90x68.88x154 A, SPME 64x70x160 order 5, alpha 0.25, r_c 12 A", 4000),
     "dc-large": ("large doubled cell: 40,320 electrode sites (two mirrored 125x123x100 A sub-cells, 3-layer "
@@ -91,7 +95,8 @@ WORKLOADS = {
                  "SPME 128x128x200 order 5, alpha 0.25, r_c 12 A; S stored as two 20,160^2 mirror blocks, "
                  "A's reciprocal part as the SPME mesh operator", 5000),
 }
-GEOMETRY_NAME = {"paper": "finite field", "paper-dc": "doubled cell", "paper-slab": "slab", "large": "finite field",
+GEOMETRY_NAME = {"paper": "finite field", "paper-dc": "doubled cell", "paper-slab": "slab",
+                 "paper-proximal": "finite field", "large": "finite field",
                  "dc-large": "doubled cell"}
 
 
@@ -105,6 +110,8 @@ def workload(seed, kind="paper"):
         return synth.config_paper_cell(seed=seed, geometry="dc")
     if kind == "paper-slab":
         return synth.config_paper_cell(seed=seed, geometry="slab")
+    if kind == "paper-proximal":
+        return synth.proximal_only(synth.config_paper_cell(seed=seed))
     return synth.config_paper_cell(seed=seed)
 
 
@@ -182,7 +189,7 @@ PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distanc
 # captured: then traffic is null).  Summaries: profiles/k_sapply32_paper-cell-ff-mixed.md,
 # profiles/k_sapply_sym_large-cell-ff-mixed.md.  Set an entry to None whenever its kernel changes.
 NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.737536e6},
-                     "paper-dc": {}, "paper-slab": {},
+                     "paper-dc": {}, "paper-slab": {}, "paper-proximal": {},
                      "large": {"s_apply:sym": 210.907904e6},
                      "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",

@@ -341,6 +341,30 @@ int cpm_set_mesh_variant(cpm_ctx* ctx, int32_t variant);
 int cpm_autotune(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const double* elyt_xyzq_dev,
                  const double* dpsi_dev, double* q_dev, void* stream, int32_t* choice_host);
 
+/*
+ * cpm_density_z - the x-y averaged charge density rho(z) across the cell (Sec. II.C, Fig. 7), for
+ * the potential profile.  nbins bins of width h = L_z / nbins over the Ewald box in z (slab: the
+ * padded box); rho_dev [n_rep * nbins] float64 (e / A^3) is ADDED to, so repeated calls over a
+ * trajectory accumulate a sum (zero it first; divide by the number of calls through `scale` of
+ * cpm_potential_z).  Electrolyte point charges count in the bin of their wrapped z; each electrode
+ * site's Gaussian charge (Eq. 2, width eta) is integrated over the bins it reaches.  q_dev
+ * [n_rep * N_e] are the electrode charges (e.g. from cpm_step_charges).  nbins >= 4.
+ */
+int cpm_density_z(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev, const double* elyt_xyzq_dev,
+                  const double* q_dev, int32_t nbins, double* rho_dev, void* stream);
+
+/*
+ * cpm_potential_z - the potential profile psi(z) (V) from rho: the 1-D Poisson equation
+ * psi'' = -rho / eps0 (Sec. II.C) with the periodic second difference on the bin centres, solved
+ * exactly (two prefix sums, the same solution as inverting the finite-difference matrix), zero
+ * mean.  The mean of rho (non-zero only for a non-neutral input) is removed first.  CPM_FF adds
+ * the applied ramp dpsi z / L_z, so psi jumps by dpsi across the cell boundary; CPM_DOUBLED and
+ * CPM_SLAB keep psi continuous.  rho is scaled by `scale` (1 / number of accumulated samples).
+ * psi_dev [n_rep * nbins]; dpsi_dev [n_rep]; 4 <= nbins <= 12288.
+ */
+int cpm_potential_z(cpm_ctx* ctx, int32_t n_rep, int32_t nbins, const double* rho_dev, double scale,
+                    const double* dpsi_dev, double* psi_dev, void* stream);
+
 /* cpm_destroy - free the context and everything it owns (NULL is accepted). */
 void cpm_destroy(cpm_ctx* ctx);
 

@@ -24,7 +24,7 @@ DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
             "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
-            "cpm_autotune",
+            "cpm_autotune", "cpm_density_z", "cpm_potential_z",
             "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
 PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
@@ -75,6 +75,8 @@ def _load():
     lib.cpm_set_sapply_variant.argtypes = [vp, i32]
     lib.cpm_set_fft_variant.argtypes = [vp, i32]
     lib.cpm_set_mesh_variant.argtypes = [vp, i32]
+    lib.cpm_density_z.argtypes = [vp, i32, pi32, pd, pd, i32, pd, vp]
+    lib.cpm_potential_z.argtypes = [vp, i32, i32, pd, ctypes.c_double, pd, pd, vp]
     lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, pi32]
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
@@ -301,6 +303,24 @@ def cpm_autotune(ctx: Context, offsets, xyzq, dpsi, q, stream=None):
     names_f = {v: k for k, v in FFT_VARIANTS.items()}
     names_m = {v: k for k, v in MESH_VARIANTS.items()}
     return names_s[out[0]], names_f[out[1]], names_m[out[2]]
+
+
+def cpm_density_z(ctx: Context, n_rep: int, offsets, xyzq, q, nbins: int, rho, stream=None):
+    """Adds the x-y averaged charge density of this configuration into rho [n_rep * nbins]."""
+    import torch
+    _check(_lib.cpm_density_z(ctx.handle, int(n_rep), _dev(offsets, torch.int32, "offsets", n_rep + 1),
+                              _dev(xyzq, torch.float64, "xyzq"), _dev(q, torch.float64, "q", n_rep * ctx.n_elec),
+                              int(nbins), _dev(rho, torch.float64, "rho", n_rep * nbins), _stream_ptr(stream)),
+           "cpm_density_z")
+
+
+def cpm_potential_z(ctx: Context, n_rep: int, nbins: int, rho, scale: float, dpsi, psi, stream=None):
+    """psi [n_rep * nbins] (V) from the 1-D Poisson equation of rho * scale."""
+    import torch
+    _check(_lib.cpm_potential_z(ctx.handle, int(n_rep), int(nbins), _dev(rho, torch.float64, "rho", n_rep * nbins),
+                                float(scale), _dev(dpsi, torch.float64, "dpsi", n_rep),
+                                _dev(psi, torch.float64, "psi", n_rep * nbins), _stream_ptr(stream)),
+           "cpm_potential_z")
 
 
 def cpm_status(ctx: Context, stream=None) -> int:

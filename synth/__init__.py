@@ -488,3 +488,14 @@ def config_large_dc(seed: int = 5000, n_pairs_per_cell: int = 12500, dpsi: float
     w.grid = (128, 128, 200)
     w.name = "dc-40320"
     return w
+
+
+def proximal_only(w: Workload) -> Workload:
+    """The same cell with only the electrode layer nearest the electrolyte (layer 0) charged: the
+    further layers carry no charge, so they drop out of the electrostatics altogether (they would
+    contribute Lennard-Jones interactions only), as in the paper's production runs (Appendix B)."""
+    keep = np.asarray(w.elec_layer) == 0
+    return dataclasses.replace(w, name=w.name + "-proximal", elec_xyz=w.elec_xyz[keep],
+                               elec_side=w.elec_side[keep],
+                               elec_cell=None if w.elec_cell is None else w.elec_cell[keep],
+                               elec_layer=w.elec_layer[keep])

@@ -75,3 +75,26 @@ def test_finite_field_ramp_jumps_by_dpsi_across_the_boundary():
     assert abs((psi[-1] - psi[0]) - 2.0 * (n - 1) / n) <= 1e-12
     assert abs(step - 2.0 / n) <= 1e-12
     assert abs((psi[0] + 2.0 - psi[-1]) - step) <= 1e-12   # periodic image one cell up: +dpsi
+
+
+def test_all_layer_charging_puts_most_charge_on_the_proximal_layers():
+    """With all three layers charged (the snapshot re-run of Appendix B), the proximal layers carry
+    more than 90 % of each electrode's induced charge (Sec. IV.C), and charging only the proximal
+    layers gives each electrode nearly the same total charge."""
+    from oracle import cpm
+    w = synth.config_plain_ff()
+    out = cpm.Reference(w).step(want_forces=False, want_energy=False)
+    q = out["q"]
+    for side in (+1, -1):
+        on = w.elec_side == side
+        total = q[on].sum()
+        prox = q[on & (w.elec_layer == 0)].sum()
+        assert abs(total) > 1e-3
+        assert prox / total > 0.9
+    wp = synth.proximal_only(w)
+    assert wp.n_elec * 3 == w.n_elec
+    outp = cpm.Reference(wp).step(want_forces=False, want_energy=False)
+    qp = outp["q"]
+    for side in (+1, -1):
+        full = q[w.elec_side == side].sum()
+        assert abs(qp[wp.elec_side == side].sum() - full) <= 0.1 * abs(full)
