@@ -5,4 +5,4 @@ system for the electrode charges.  Only the test suite, the smoke check and the 
 baseline leg may import it; the GPU library never does, and the two share no code.
 """
 from .ewald import KE  # noqa: F401
-from . import ewald, cpm, profile  # noqa: F401
+from . import ewald, cpm, profile, md  # noqa: F401

@@ -499,3 +499,68 @@ def proximal_only(w: Workload) -> Workload:
                                elec_side=w.elec_side[keep],
                                elec_cell=None if w.elec_cell is None else w.elec_cell[keep],
                                elec_layer=w.elec_layer[keep])
+
+
+# ----------------------------------------------------------------------------------------------
+# molecular-dynamics inputs (point ions; the rigid three-site cation needs constraints)
+# ----------------------------------------------------------------------------------------------
+KB_EV = 8.617333262e-5                 # Boltzmann constant, eV / K
+AMU_A2_FS2_EV = 103.64269652680505     # 1 amu A^2 / fs^2 in eV
+MD_MASS = (139.2, 144.96)              # amu: cation (BMIm+), anion (PF6-) formula masses
+MD_SIGMA = (3.0, 3.0, 3.37)            # A: cation, anion, electrode carbon (synthetic LJ)
+MD_EPS = (0.02, 0.02, 0.0024)          # eV
+MD_TEMPERATURE = 400.0                 # K (Appendix A)
+MD_DAMP_FS = 100.0                     # fs (Appendix A)
+
+
+@dataclasses.dataclass
+class MDInputs:
+    """Per-site MD labels and initial velocities for replica 0 of a workload.
+
+    types     [N_l] int32: 0 cation, 1 anion (by the sign of the charge); the electrode is type 2
+    groups    [N_l] int32 thermostat group: the sub-cell (z >= L_z / 2) in the doubled cell, else 0
+    vel       [N_l, 3] float64 Maxwell-Boltzmann velocities at `temperature` (A / fs)
+    """
+    types: np.ndarray
+    groups: np.ndarray
+    vel: np.ndarray
+    mass: tuple = MD_MASS
+    sigma: tuple = MD_SIGMA
+    eps: tuple = MD_EPS
+    elec_type: int = 2
+    temperature: float = MD_TEMPERATURE
+    t_damp: float = MD_DAMP_FS
+
+
+def md_inputs(w: Workload, seed: int = 77, temperature: float = MD_TEMPERATURE, r: int = 0) -> MDInputs:
+    q = np.asarray(w.elyt_q[r])
+    if np.any(np.abs(np.abs(q) - ION_CHARGE) > 1e-12):
+        raise ValueError("md_inputs: the MD loop takes single-site ions of charge +-0.78 e")
+    types = np.where(q > 0, 0, 1).astype(np.int32)
+    z = np.asarray(w.elyt_xyz[r])[:, 2]
+    groups = ((z >= 0.5 * w.box[2]) if w.geometry == "dc" else np.zeros(len(q), bool)).astype(np.int32)
+    m = np.asarray(MD_MASS)[types]
+    rng = np.random.Generator(np.random.PCG64(seed))
+    sd = np.sqrt(KB_EV * temperature / (m * AMU_A2_FS2_EV))
+    vel = rng.normal(size=(len(q), 3)) * sd[:, None]
+    return MDInputs(types, groups, vel, temperature=temperature)
+
+
+def md_cell(seed: int = 6000, n_pairs: int = 1000, dpsi: float = 2.0, geometry: str = "ff",
+            nx: int = 9, ny: int = 14, lz: float = 168.0, dmin: float = 3.0) -> Workload:
+    """Point-ion cell for the MD loop: the paper-scale electrode (9 x 14 graphene cells, three
+    layers per electrode, L_z = 168 A) with n_pairs +-0.78 e point-ion pairs (default 1,000 pairs:
+    the 2,000 electrolyte sites of the coarse-grained paper cell, each a single Lennard-Jones site),
+    >= dmin apart, SPME grid 1 A, order 5.  geometry 'ff' or 'dc' (mirror stack, independent
+    second electrolyte)."""
+    xyz, side, layer, (lx, ly) = electrode_pair(nx, ny, lz)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ex, eq = place_electrolyte(rng, lx, ly, ELECTROLYTE_MARGIN, lz - ELECTROLYTE_MARGIN, n_pairs, "point", dmin)
+    box = np.array([lx, ly, lz])
+    w = Workload(f"md-{len(xyz)}-{2 * n_pairs}", box, xyz, side, None, layer, [ex], [eq], np.array([dpsi]),
+                 "ff", grid=_grid_for(box), min_sep=dmin)
+    if geometry == "dc":
+        w = mirror_to_doubled(w, "independent", seed=seed + 1)
+        w.grid = _grid_for(w.box)
+        w.name = f"md-dc-{len(w.elec_xyz)}-{len(w.elyt_q[0])}"
+    return w
