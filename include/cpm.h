@@ -365,6 +365,97 @@ int cpm_density_z(cpm_ctx* ctx, int32_t n_rep, const int32_t* elyt_offsets_dev, 
 int cpm_potential_z(cpm_ctx* ctx, int32_t n_rep, int32_t nbins, const double* rho_dev, double scale,
                     const double* dpsi_dev, double* psi_dev, void* stream);
 
+/* ---------------------------------------------------------------------------------------------
+ * Molecular dynamics around the per-step calls (Appendix A: velocity-Verlet at a 2 fs step, a
+ * Nose-Hoover thermostat on the electrolyte with one thermostat per doubled-cell sub-cell;
+ * Appendix B: charges re-solved every 5 steps and held in between).  The electrode is frozen and
+ * every electrolyte site is a point ion: a position, a charge (the w of xyzq), a mass and a
+ * Lennard-Jones type.  Units: fs, amu, A, eV, K.
+ *
+ * One step: thermostat half step (Trotter splitting of Martyna, Tuckerman, Tobias & Klein 1996:
+ * quarter-step v_xi update, velocity scaling exp(-v_xi dt/2), xi += v_xi dt/2, quarter step;
+ * Q = g k_B T t_damp^2 with g = 3 N_group), v += dt/2 F/m, x += dt v (x and y wrapped into the
+ * cell), forces at the new positions, v += dt/2 F/m, thermostat half step.  The step index n
+ * counts force evaluations (the first one, at the starting positions, is n = 0); when n is a
+ * multiple of charge_every the charges are re-solved (cpm_step), otherwise the previous charges are
+ * kept (cpm_forces).  Forces are the electrostatic forces of cpm_forces plus a synthetic
+ * Lennard-Jones term (Lorentz-Berthelot mixing, force-shifted at lj_cut so energy and force vanish
+ * continuously there; electrolyte-electrolyte and electrolyte-electrode pairs over every periodic
+ * image within lj_cut), evaluated by the same cell list as the real-space Coulomb pairs.
+ * ------------------------------------------------------------------------------------------- */
+#define CPM_MD_MAX_TYPES 8
+#define CPM_MD_NENERGY 8   /* per replica: U, H, U_LJ, KE, E_thermostat, E_total, T (K), Q_+ */
+
+typedef struct {
+  double dt;                             /* time step (fs), > 0 */
+  int32_t charge_every;                  /* k >= 1 */
+  int32_t n_types;                       /* 1 .. CPM_MD_MAX_TYPES */
+  double mass[CPM_MD_MAX_TYPES];         /* amu; > 0 for every type an electrolyte site uses */
+  double lj_sigma[CPM_MD_MAX_TYPES];     /* A, >= 0 */
+  double lj_epsilon[CPM_MD_MAX_TYPES];   /* eV, >= 0 (0: the type takes no Lennard-Jones part) */
+  int32_t elec_type;                     /* Lennard-Jones type of every electrode site, -1: none */
+  int32_t n_groups;                      /* thermostat groups per replica, 1 .. 4 */
+  double lj_cut;                         /* A, 0 < lj_cut <= rcut; 0 switches Lennard-Jones off */
+  double temperature;                    /* K, thermostat target (> 0 when t_damp > 0) */
+  double t_damp;                         /* fs, Nose-Hoover damping time; <= 0: no thermostat (NVE) */
+} cpm_md_params;
+
+typedef struct cpm_md cpm_md;
+
+/*
+ * cpm_md_create - an MD integrator for n_rep replicas of the context's electrode.
+ *   elyt_offsets_host [n_rep+1] int32 site offsets (the layout of every later elyt_xyzq_dev);
+ *   type_host [offsets[n_rep]] int32 in [0, n_types); group_host [offsets[n_rep]] int32 thermostat
+ *   group in [0, n_groups) (NULL: all 0).  Copies them; allocates forces, thermostat state and
+ *   scratch (about 24 bytes per site).  Synchronises `stream`.  The thermostat state starts at
+ *   xi = v_xi = 0 and the step index at 0.  CPM_ERR_ARG for invalid parameters or labels,
+ *   CPM_ERR_CAPACITY when n_rep or a replica exceeds the context's capacity.
+ */
+int cpm_md_create(cpm_ctx* ctx, const cpm_md_params* p, int32_t n_rep, const int32_t* elyt_offsets_host,
+                  const int32_t* type_host, const int32_t* group_host, void* stream, cpm_md** out);
+
+/*
+ * cpm_md_run - advance n_steps >= 0 steps.
+ *   elyt_xyzq_dev [offsets[n_rep]*4] float64 positions (updated in place) and charges (read);
+ *   vel_dev [offsets[n_rep]*3] float64 velocities (A/fs, updated in place); dpsi_dev [n_rep];
+ *   q_dev [n_rep*N_e] electrode charges (the held charges on entry when the next force evaluation
+ *   does not re-solve them; updated at every re-solve); psibar_dev [n_rep*ncons] or NULL;
+ *   energy_dev [n_rep*CPM_MD_NENERGY] or NULL: at the end of the call, per replica U and H (as
+ *   cpm_forces, at the last force evaluation), U_LJ, the kinetic energy, the thermostat energy
+ *   sum_g (Q_g v_xi^2 / 2 + g_g k_B T xi_g), the conserved total KE + H + U_LJ + E_thermostat, the
+ *   instantaneous temperature 2 KE / (g k_B) and Q_+;
+ *   force_dev [offsets[n_rep]*3] or NULL: the forces (eV/A) at the final positions, electrostatic
+ *   plus Lennard-Jones.
+ * The first call (and the first after cpm_md_set_state) evaluates the forces at the starting
+ * positions.  No allocation and no host synchronisation: a call can be captured into a CUDA graph
+ * once the forces are known (a capture before that returns CPM_ERR_ARG).  A captured call does not
+ * advance the step index; the caller counts replays with cpm_md_advance, and replays a captured
+ * block only from step indices congruent modulo charge_every to the one it was captured at.
+ * Uses the context (its cell list, workspaces and side stream) for the call's duration.
+ */
+int cpm_md_run(cpm_md* md, int32_t n_steps, double* elyt_xyzq_dev, double* vel_dev, const double* dpsi_dev,
+               double* q_dev, double* psibar_dev, double* energy_dev, double* force_dev, void* stream);
+
+/* cpm_md_advance - add n_steps (graph replays) to the step index. */
+int cpm_md_advance(cpm_md* md, int64_t n_steps);
+
+/*
+ * cpm_md_get_state / cpm_md_set_state - checkpoint the integrator: the step index and the
+ * thermostat state thermo_host [n_rep*n_groups*2] = (xi, v_xi) per (replica, group) (NULL: not
+ * copied).  Positions, velocities and electrode charges are the caller's buffers.  Both synchronise
+ * `stream`; set_state marks the forces unknown, so the next cpm_md_run evaluates them at the
+ * current positions with the schedule's charges (re-solved when the restored index is a multiple of
+ * charge_every, else the q_dev the caller restored), continuing the checkpointed trajectory.
+ */
+int cpm_md_get_state(const cpm_md* md, int64_t* step, double* thermo_host, void* stream);
+int cpm_md_set_state(cpm_md* md, int64_t step, const double* thermo_host, void* stream);
+
+/* cpm_md_info - electrolyte site count and number of (replica, group) thermostat slots. */
+int cpm_md_info(const cpm_md* md, int32_t* n_sites, int32_t* n_slots);
+
+/* cpm_md_destroy - free the integrator (NULL is accepted; the context is not touched). */
+void cpm_md_destroy(cpm_md* md);
+
 /* cpm_destroy - free the context and everything it owns (NULL is accepted). */
 void cpm_destroy(cpm_ctx* ctx);
 

@@ -25,7 +25,8 @@ EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", 
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
             "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
             "cpm_autotune", "cpm_density_z", "cpm_potential_z",
-            "cpm_destroy",
+            "cpm_md_create", "cpm_md_run", "cpm_md_advance", "cpm_md_get_state", "cpm_md_set_state", "cpm_md_info",
+            "cpm_md_destroy", "cpm_destroy",
             "cpm_strerror", "cpm_last_error")
 PHASES = ("cell_list", "b_real", "b_spread", "b_fft", "b_gather", "s_apply", "project", "f_spread", "f_fft",
           "f_gather", "f_pair_elyt", "f_pair_elec", "energy")
@@ -38,6 +39,20 @@ class CpmParams(ctypes.Structure):
                 ("grid", ctypes.c_int32 * 3), ("spme_order", ctypes.c_int32), ("geometry", ctypes.c_int32),
                 ("precision", ctypes.c_int32), ("max_replicas", ctypes.c_int32), ("max_elyt", ctypes.c_int32),
                 ("matrix_kspace", ctypes.c_int32), ("dc_blocks", ctypes.c_int32)]
+
+
+MD_MAX_TYPES = 8
+MD_NENERGY = 8           # per replica: U, H, U_LJ, KE, E_thermostat, E_total, T, Q_+
+MD_ENERGY_KEYS = ("U", "H", "U_lj", "KE", "E_nh", "E_total", "T", "Q_plus")
+
+
+class CpmMdParams(ctypes.Structure):
+    """Mirror of cpm_md_params in include/cpm.h."""
+    _fields_ = [("dt", ctypes.c_double), ("charge_every", ctypes.c_int32), ("n_types", ctypes.c_int32),
+                ("mass", ctypes.c_double * MD_MAX_TYPES), ("lj_sigma", ctypes.c_double * MD_MAX_TYPES),
+                ("lj_epsilon", ctypes.c_double * MD_MAX_TYPES), ("elec_type", ctypes.c_int32),
+                ("n_groups", ctypes.c_int32), ("lj_cut", ctypes.c_double), ("temperature", ctypes.c_double),
+                ("t_damp", ctypes.c_double)]
 
 
 class CPMError(RuntimeError):
@@ -78,6 +93,14 @@ def _load():
     lib.cpm_density_z.argtypes = [vp, i32, pi32, pd, pd, i32, pd, vp]
     lib.cpm_potential_z.argtypes = [vp, i32, i32, pd, ctypes.c_double, pd, pd, vp]
     lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, pi32]
+    lib.cpm_md_create.argtypes = [vp, ctypes.POINTER(CpmMdParams), i32, pi32, pi32, pi32, vp, ctypes.POINTER(vp)]
+    lib.cpm_md_run.argtypes = [vp, i32, pd, pd, pd, pd, pd, pd, pd, vp]
+    lib.cpm_md_advance.argtypes = [vp, ctypes.c_int64]
+    lib.cpm_md_get_state.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), pd, vp]
+    lib.cpm_md_set_state.argtypes = [vp, ctypes.c_int64, pd, vp]
+    lib.cpm_md_info.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.cpm_md_destroy.argtypes = [vp]
+    lib.cpm_md_destroy.restype = None
     lib.cpm_destroy.argtypes = [vp]
     lib.cpm_destroy.restype = None
     lib.cpm_strerror.argtypes = [ctypes.c_int]
@@ -85,7 +108,7 @@ def _load():
     lib.cpm_last_error.argtypes = []
     lib.cpm_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name not in ("cpm_destroy", "cpm_strerror", "cpm_last_error"):
+        if name not in ("cpm_destroy", "cpm_md_destroy", "cpm_strerror", "cpm_last_error"):
             getattr(lib, name).restype = ctypes.c_int
     return lib
 
@@ -321,6 +344,88 @@ def cpm_potential_z(ctx: Context, n_rep: int, nbins: int, rho, scale: float, dps
                                 float(scale), _dev(dpsi, torch.float64, "dpsi", n_rep),
                                 _dev(psi, torch.float64, "psi", n_rep * nbins), _stream_ptr(stream)),
            "cpm_potential_z")
+
+
+def make_md_params(dt=2.0, charge_every=5, mass=(), sigma=(), eps=(), elec_type=-1, n_groups=1, lj_cut=0.0,
+                   temperature=400.0, t_damp=100.0) -> CpmMdParams:
+    p = CpmMdParams()
+    n = max(len(mass), len(sigma), len(eps))
+    if n < 1 or n > MD_MAX_TYPES:
+        raise ValueError(f"between 1 and {MD_MAX_TYPES} types required")
+    p.dt, p.charge_every, p.n_types = float(dt), int(charge_every), n
+    for t in range(n):
+        p.mass[t] = float(mass[t]) if t < len(mass) else 0.0
+        p.lj_sigma[t] = float(sigma[t]) if t < len(sigma) else 0.0
+        p.lj_epsilon[t] = float(eps[t]) if t < len(eps) else 0.0
+    p.elec_type, p.n_groups = int(elec_type), int(n_groups)
+    p.lj_cut, p.temperature, p.t_damp = float(lj_cut), float(temperature), float(t_damp)
+    return p
+
+
+class MDHandle:
+    """Owning handle of a cpm_md integrator (destroyed with the object; keeps its context alive)."""
+
+    def __init__(self, handle, ctx: Context, params: CpmMdParams, n_rep: int):
+        self.handle, self.ctx, self.params, self.n_rep = handle, ctx, params, n_rep
+        n, s = ctypes.c_int32(), ctypes.c_int32()
+        _check(_lib.cpm_md_info(handle, ctypes.byref(n), ctypes.byref(s)), "cpm_md_info")
+        self.n_sites, self.n_slots = n.value, s.value
+
+    def close(self):
+        h = getattr(self, "handle", None)
+        if h:
+            _lib.cpm_md_destroy(h)
+            self.handle = None
+
+    def __del__(self):
+        self.close()
+
+
+def cpm_md_create(ctx: Context, params: CpmMdParams, offsets, types, groups=None, stream=None) -> MDHandle:
+    off = np.ascontiguousarray(offsets, dtype=np.int32)
+    ty = np.ascontiguousarray(types, dtype=np.int32)
+    gr = None if groups is None else np.ascontiguousarray(groups, dtype=np.int32)
+    n_rep = len(off) - 1
+    if n_rep < 1 or ty.shape != (int(off[-1]),) or (gr is not None and gr.shape != ty.shape):
+        raise ValueError("offsets / types / groups have inconsistent shapes")
+    out = ctypes.c_void_p()
+    _check(_lib.cpm_md_create(ctx.handle, ctypes.byref(params), n_rep, off.ctypes.data, ty.ctypes.data,
+                              None if gr is None else gr.ctypes.data, _stream_ptr(stream), ctypes.byref(out)),
+           "cpm_md_create")
+    return MDHandle(out.value, ctx, params, n_rep)
+
+
+def cpm_md_run(md: MDHandle, n_steps: int, xyzq, vel, dpsi, q, psibar=None, energy=None, force=None, stream=None):
+    import torch
+    R, ne, n = md.n_rep, md.ctx.n_elec, md.n_sites
+    _check(_lib.cpm_md_run(md.handle, int(n_steps), _dev(xyzq, torch.float64, "xyzq", 4 * n),
+                           _dev(vel, torch.float64, "vel", 3 * n), _dev(dpsi, torch.float64, "dpsi", R),
+                           _dev(q, torch.float64, "q", R * ne),
+                           _dev(psibar, torch.float64, "psibar", R * md.ctx.ncons, True),
+                           _dev(energy, torch.float64, "energy", R * MD_NENERGY, True),
+                           _dev(force, torch.float64, "force", 3 * n, True), _stream_ptr(stream)),
+           "cpm_md_run")
+
+
+def cpm_md_advance(md: MDHandle, n_steps: int):
+    _check(_lib.cpm_md_advance(md.handle, int(n_steps)), "cpm_md_advance")
+
+
+def cpm_md_get_state(md: MDHandle, stream=None):
+    """(step index, thermostat state [n_rep * n_groups, 2] of (xi, v_xi))."""
+    step = ctypes.c_int64()
+    th = np.zeros((md.n_slots, 2), dtype=np.float64)
+    _check(_lib.cpm_md_get_state(md.handle, ctypes.byref(step), th.ctypes.data, _stream_ptr(stream)),
+           "cpm_md_get_state")
+    return int(step.value), th
+
+
+def cpm_md_set_state(md: MDHandle, step: int, thermo=None, stream=None):
+    th = None if thermo is None else np.ascontiguousarray(thermo, dtype=np.float64).reshape(-1)
+    if th is not None and th.size != 2 * md.n_slots:
+        raise ValueError(f"thermostat state needs {2 * md.n_slots} values")
+    _check(_lib.cpm_md_set_state(md.handle, int(step), None if th is None else th.ctypes.data, _stream_ptr(stream)),
+           "cpm_md_set_state")
 
 
 def cpm_status(ctx: Context, stream=None) -> int:

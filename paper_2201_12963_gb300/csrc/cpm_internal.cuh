@@ -21,7 +21,7 @@ namespace cpm {
 constexpr double KE = 14.3996454784;        // e^2 / (4 pi eps0), eV A
 constexpr double PI = 3.14159265358979323846;
 constexpr int PMAX = 8;                     // largest supported B-spline order
-constexpr int NSCAL = 16;                   // per-replica float64 scalar slots
+constexpr int NSCAL = 18;                   // per-replica float64 scalar slots
 constexpr int kMaxStencil = 512;            // neighbour-cell stencil entries of the pair kernel
 
 // Per-replica scalar slots (float64 accumulators, zeroed at the start of every call).
@@ -41,7 +41,19 @@ enum Slot {
   S_WB1 = 12,      // (A^-1 e_1)^T b
   S_E_RECIP_L = 13,// 1/2 sum_m G |rho_elyt^(m)|^2 (eV), electrolyte charges alone
   S_QB = 14,       // q^T b (after the projection)
-  S_QPLUS = 15     // sum of q over side +1 sites
+  S_QPLUS = 15,    // sum of q over side +1 sites
+  S_E_LJ = 16      // Lennard-Jones energy of the electrolyte (eV), when an MD run enables it
+};
+
+// Lennard-Jones interactions of an MD run (cpm_md_run), evaluated by the step's force pass on the
+// same cell list while the run holds the context (ctx->lj set for its duration).
+constexpr int kLjMaxTypes = 8;
+struct LjSetup {
+  const int* type = nullptr;    // [offsets[n_rep]] LJ type per electrolyte site (replica-major)
+  int elec_type = -1;           // type of every electrode site, -1: no electrode interaction
+  double cut = 0.0;             // force-shifted cutoff (A), <= rcut
+  double sig_half[kLjMaxTypes] = {};   // sigma / 2 (Lorentz-Berthelot: sigma_ab = half_a + half_b)
+  double sqrt_eps[kLjMaxTypes] = {};   // sqrt(eps) (eps_ab = sqrt_eps_a sqrt_eps_b)
 };
 constexpr int NENERGY = 4;                  // per-replica energy outputs: U, H, dH/d(dpsi), Q_+
 
@@ -174,6 +186,7 @@ struct cpm_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* f_pair = nullptr;     // [max_rep][max_elyt][3] real-space electrolyte forces (original order)
+  const cpm::LjSetup* lj = nullptr;  // Lennard-Jones of a running MD loop (added into f_pair), or none
   // libraries
   cublasHandle_t cublas = nullptr;
   cusolverDnHandle_t solver = nullptr;
@@ -388,6 +401,7 @@ int cpm_internal_sym_setup(cpm_ctx* c);
 int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* xl, const double* b,
                             const double* dpsi, const double* Sv, const double* W, const double* c1, double* qout,
                             cudaStream_t st);
+int cpm_internal_lj(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const void* e_loc, cudaStream_t st);
 int cpm_internal_spread_brick(cpm_ctx* c, int nrep, const void* l_loc, const float* qT, cudaStream_t st);
 int cpm_internal_gather_f_brick(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const double* dpsi,
                                 double ff_over_lz, double slab_coef, double* F, cudaStream_t st);

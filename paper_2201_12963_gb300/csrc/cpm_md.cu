@@ -1,0 +1,727 @@
+// Molecular dynamics around the CPM step (Appendix A: velocity-Verlet at 2 fs with a Nose-Hoover
+// thermostat on the electrolyte, one per sub-cell of the doubled cell; Appendix B: electrode charges
+// re-solved every 5 steps and held in between).  The electrode is frozen; each electrolyte site is
+// a point ion with a Lennard-Jones type.
+//
+// Integrator (per step, all on the caller's stream):
+//   thermostat half step(s) -> combined velocity scale s per (replica, group)      k_md_nh
+//   v = s v + dt/2 F/m ; x += dt v ; x, y wrapped into the cell                    k_md_kick_drift
+//   forces at the new positions: cpm_step (charges re-solved when the step index is a multiple of
+//     k) or cpm_forces (charges held), the Lennard-Jones term added by the same force pass
+//   v += dt/2 F/m and the kinetic energy per (replica, group)                      k_md_kick_ke
+// The thermostat is one Nose-Hoover variable per group, propagated by the symmetric Trotter
+// splitting of Martyna, Tuckerman, Tobias and Klein (Mol. Phys. 87, 1117 (1996)): a half step is a
+// quarter-step update of v_xi, the scaling exp(-v_xi dt / 2), xi += v_xi dt / 2 and a second
+// quarter step; Q = g k_B T tau^2 with g = 3 N_group.  The trailing half step of one time step and
+// the leading half step of the next are taken together, so their velocity scales multiply into the
+// next kick; the last trailing scale of a call is applied by k_md_scale.
+//
+// Lennard-Jones: Lorentz-Berthelot mixing, force-shifted at the cutoff (energy and force continuous),
+// electrolyte-electrolyte and electrolyte-electrode pairs, summed over every periodic image within
+// the cutoff by the step's cell list (cutoff <= the real-space Coulomb cutoff).  Forces are added
+// into the real-space pair-force buffer on the side stream, after the Coulomb pair kernel, so the
+// force gather of the step adds them to the electrolyte forces.
+#include "cpm_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+namespace cpm {
+
+constexpr double KB_EV = 8.617333262e-5;             // Boltzmann constant, eV / K
+constexpr double MVV2E = 103.64269652680505;         // 1 amu A^2 / fs^2 in eV
+constexpr int LJ_THREADS = 128;
+constexpr int LJ_MAXT = 64;                          // targets per pass of a block
+constexpr int kLjSrcCap = 1024;                      // sources staged per pass
+constexpr int kMdMaxGroups = 4;
+
+struct LjGrid {
+  const void* l_loc;          // cell-sorted cell-local electrolyte coordinates (working precision)
+  const int* l_start;         // [rep][ncell + 1]
+  const int* l_sorted;        // [rep][cap] sorted -> replica-local index
+  const void* e_loc;          // cell-sorted cell-local electrode coordinates, or nullptr (no electrode LJ)
+  const int* e_start;         // [ncell + 1]
+  const int* off;             // [n_rep + 1] replica offsets
+  const int* type;            // [offsets[n_rep]] LJ types
+  int cap;
+  int elec_type;
+  int nc[3], w[3], sten[3], nsten;
+  double edge[3];
+  double cut;
+  double sig_half[kLjMaxTypes], sqrt_eps[kLjMaxTypes];
+  double* f_pair;             // [rep][cap][3] += forces (replica-local original order)
+  double* scal;               // [rep][NSCAL]: S_E_LJ += energy
+};
+
+template <typename T>
+__global__ void __launch_bounds__(LJ_THREADS) k_lj_cell(const LjGrid a) {
+  using V4 = typename Vec4<T>::type;
+  extern __shared__ __align__(32) unsigned char lj_dyn[];
+  V4* src = reinterpret_cast<V4*>(lj_dyn);
+  T* src_sh = reinterpret_cast<T*>(src + kLjSrcCap);
+  T* src_se = src_sh + kLjSrcCap;
+  __shared__ V4 tpos[LJ_MAXT];
+  __shared__ T tsh[LJ_MAXT], tse[LJ_MAXT];
+  __shared__ T ifrc[3][LJ_MAXT], iu[LJ_MAXT];
+  __shared__ int st_first[kMaxStencil];
+  __shared__ int st_pre[kMaxStencil + 1];
+  __shared__ short st_d[3][kMaxStencil];
+  __shared__ T par_sh[kLjMaxTypes], par_se[kLjMaxTypes];
+  __shared__ double ered[LJ_THREADS / 32];
+
+  const int rep = blockIdx.y, cell = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ncell = a.nc[0] * a.nc[1] * a.nc[2];
+  const int* tst = a.l_start + (size_t)rep * (ncell + 1);
+  const int t0 = tst[cell], t1 = tst[cell + 1];
+  if (t1 <= t0) return;                                     // whole block: empty cell
+  if (tid == 0) {
+#pragma unroll
+    for (int t = 0; t < kLjMaxTypes; ++t) {
+      par_sh[t] = (T)a.sig_half[t];
+      par_se[t] = (T)a.sqrt_eps[t];
+    }
+  }
+  const int o = a.off[rep];
+  const V4* tl = (const V4*)a.l_loc + (size_t)rep * a.cap;
+  const int* tso = a.l_sorted + (size_t)rep * a.cap;
+  const int cz = cell % a.nc[2], cy = (cell / a.nc[2]) % a.nc[1], cx = cell / (a.nc[2] * a.nc[1]);
+  const T e0 = (T)a.edge[0], e1 = (T)a.edge[1], e2 = (T)a.edge[2];
+  const T cut = (T)a.cut, cut2 = cut * cut, icut = T(1) / cut, icut2 = icut * icut;
+  double eblock = 0.0;
+  __syncthreads();
+
+  for (int tb = t0; tb < t1; tb += LJ_MAXT) {
+    const int nt = min(LJ_MAXT, t1 - tb);
+    const int P = max(1, (LJ_THREADS / 32) / nt);           // parts per target: items nt * P <= LJ_MAXT
+    for (int k = tid; k < nt; k += LJ_THREADS) {
+      tpos[k] = tl[tb + k];
+      const int ty = min(kLjMaxTypes - 1, max(0, a.type[o + tso[tb + k]]));
+      tsh[k] = par_sh[ty];
+      tse[k] = par_se[ty];
+    }
+    for (int k = tid; k < nt * P; k += LJ_THREADS) ifrc[0][k] = ifrc[1][k] = ifrc[2][k] = iu[k] = T(0);
+    for (int set = 0; set < 2; ++set) {
+      if (set == 1 && (a.e_loc == nullptr || a.elec_type < 0)) break;
+      const V4* sl = set ? (const V4*)a.e_loc : tl;
+      const int* sst = set ? a.e_start : tst;
+      const T wgt = set ? T(1) : T(0.5);                    // electrolyte pairs are seen from both ends
+      __syncthreads();
+      // stencil cells whose box can hold a source within the cutoff of some point of this cell
+      for (int si = tid; si < a.nsten; si += LJ_THREADS) {
+        const int dx = si % a.w[0] - a.sten[0];
+        const int r1 = si / a.w[0];
+        const int dy = r1 % a.w[1] - a.sten[1];
+        const int dz = r1 / a.w[1] - a.sten[2];
+        const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)max(0, abs(dz) - 1) * e2;
+        int c = 0, f = 0;
+        if (gx * gx + gy * gy + gz * gz < cut2) {
+          const int flat = (wrap_index(cx + dx, a.nc[0]) * a.nc[1] + wrap_index(cy + dy, a.nc[1])) * a.nc[2] +
+                           wrap_index(cz + dz, a.nc[2]);
+          f = sst[flat];
+          c = sst[flat + 1] - f;
+        }
+        st_first[si] = f;
+        st_pre[si + 1] = c;
+        st_d[0][si] = (short)dx;
+        st_d[1][si] = (short)dy;
+        st_d[2][si] = (short)dz;
+      }
+      __syncthreads();
+      if (warp == 0) {                                      // inclusive scan of the counts
+        int run = 0;
+        for (int b = 0; b < a.nsten; b += 32) {
+          const int k = b + lane;
+          int v = k < a.nsten ? st_pre[k + 1] : 0;
+#pragma unroll
+          for (int s = 1; s < 32; s <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, v, s);
+            if (lane >= s) v += u;
+          }
+          if (k < a.nsten) st_pre[k + 1] = run + v;
+          run += __shfl_sync(0xffffffffu, v, 31);
+        }
+        if (lane == 0) st_pre[0] = 0;
+      }
+      __syncthreads();
+      const int total = st_pre[a.nsten];
+      for (int c0 = 0; c0 < total; c0 += kLjSrcCap) {
+        const int ns = min(kLjSrcCap, total - c0);
+        for (int k = tid; k < ns; k += LJ_THREADS) {
+          const int j = c0 + k;
+          int lo = 0, hi = a.nsten;                         // st_pre[lo] <= j < st_pre[hi]
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (st_pre[mid] <= j) lo = mid; else hi = mid;
+          }
+          const int gi = st_first[lo] + (j - st_pre[lo]);
+          V4 p = sl[gi];
+          p.x += (T)st_d[0][lo] * e0;
+          p.y += (T)st_d[1][lo] * e1;
+          p.z += (T)st_d[2][lo] * e2;
+          src[k] = p;
+          const int ty = set ? a.elec_type : min(kLjMaxTypes - 1, max(0, a.type[o + tso[gi]]));
+          src_sh[k] = par_sh[ty];
+          src_se[k] = par_se[ty];
+        }
+        __syncthreads();
+        for (int item = warp; item < nt * P; item += LJ_THREADS / 32) {
+          const int ti = item / P, part = item - ti * P;
+          const V4 tp = tpos[ti];
+          const T sh = tsh[ti], se = tse[ti];
+          T fx = 0, fy = 0, fz = 0, u = 0;
+          for (int k = part * 32 + lane; k < ns; k += 32 * P) {
+            const V4 sp = src[k];
+            const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            const T eps = se * src_se[k];
+            if (r2 < cut2 && r2 > T(0) && eps > T(0)) {
+              const T sig = sh + src_sh[k];
+              const T sg2 = sig * sig;
+              const T ir2 = T(1) / r2;
+              const T s2 = sg2 * ir2, s6 = s2 * s2 * s2;
+              const T c2 = sg2 * icut2, c6 = c2 * c2 * c2;
+              const T fc = T(24) * eps * (T(2) * c6 * c6 - c6) * icut;     // LJ force magnitude at the cutoff
+              const T r = sqrt(r2);
+              const T fr = T(24) * eps * ir2 * (T(2) * s6 * s6 - s6) - fc / r;
+              fx += fr * dx;
+              fy += fr * dy;
+              fz += fr * dz;
+              u += wgt * (T(4) * eps * ((s6 * s6 - s6) - (c6 * c6 - c6)) + (r - cut) * fc);
+            }
+          }
+          fx = warp_sum_t(fx);
+          fy = warp_sum_t(fy);
+          fz = warp_sum_t(fz);
+          u = warp_sum_t(u);
+          if (lane == 0) {                                  // the item's slot belongs to this warp alone
+            ifrc[0][item] += fx;
+            ifrc[1][item] += fy;
+            ifrc[2][item] += fz;
+            iu[item] += u;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    __syncthreads();
+    for (int k = tid; k < nt; k += LJ_THREADS) {
+      T fx = 0, fy = 0, fz = 0, u = 0;
+      for (int part = 0; part < P; ++part) {
+        const int item = k * P + part;
+        fx += ifrc[0][item];
+        fy += ifrc[1][item];
+        fz += ifrc[2][item];
+        u += iu[item];
+      }
+      double* f = a.f_pair + 3 * ((size_t)rep * a.cap + tso[tb + k]);
+      f[0] += (double)fx;
+      f[1] += (double)fy;
+      f[2] += (double)fz;
+      eblock += (double)u;
+    }
+    __syncthreads();
+  }
+  eblock = warp_sum(eblock);
+  if (lane == 0) ered[warp] = eblock;
+  __syncthreads();
+  if (tid == 0) {
+    double s = 0.0;
+    for (int w = 0; w < LJ_THREADS / 32; ++w) s += ered[w];
+    if (s != 0.0) atomicAdd(a.scal + rep * NSCAL + S_E_LJ, s);
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// integrator kernels (float64)
+// ------------------------------------------------------------------------------------------
+// Per-type table in device memory: [0, kLjMaxTypes) dt / 2 / (m MVV2E), the velocity change per
+// unit force in half a step; [kLjMaxTypes, 2 kLjMaxTypes) m MVV2E / 2, the kinetic energy per v^2.
+constexpr int MD_HALF_M = kLjMaxTypes;
+
+__global__ void __launch_bounds__(256) k_md_kick_drift(int n, double* __restrict__ xyzq, double* __restrict__ vel,
+                                                       const double* __restrict__ F, const int* __restrict__ type,
+                                                       const int* __restrict__ slot, const double* __restrict__ s,
+                                                       const double* __restrict__ mt, double dt, double bx, double by) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double h = mt[type[j]];
+  const double sc = s ? s[slot[j]] : 1.0;
+  double* v = vel + 3 * (size_t)j;
+  double* x = xyzq + 4 * (size_t)j;
+  const double v0 = fma(sc, v[0], h * F[3 * (size_t)j + 0]);
+  const double v1 = fma(sc, v[1], h * F[3 * (size_t)j + 1]);
+  const double v2 = fma(sc, v[2], h * F[3 * (size_t)j + 2]);
+  v[0] = v0;
+  v[1] = v1;
+  v[2] = v2;
+  double x0 = fma(dt, v0, x[0]), x1 = fma(dt, v1, x[1]);
+  x0 -= bx * floor(x0 / bx);
+  x1 -= by * floor(x1 / by);
+  x[0] = x0 < bx ? x0 : 0.0;
+  x[1] = x1 < by ? x1 : 0.0;
+  x[2] = fma(dt, v2, x[2]);
+}
+
+// v += dt/2 F/m (kick != 0) and the kinetic energy per (replica, group) slot into ke (zeroed before).
+__global__ void __launch_bounds__(256) k_md_kick_ke(int n, double* __restrict__ vel, const double* __restrict__ F,
+                                                    const int* __restrict__ type, const int* __restrict__ slot,
+                                                    const double* __restrict__ mt, int kick, double* __restrict__ ke) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const bool valid = j < n;
+  double e = 0.0;
+  int sl = -1;
+  if (valid) {
+    const int ty = type[j];
+    double* v = vel + 3 * (size_t)j;
+    double v0 = v[0], v1 = v[1], v2 = v[2];
+    if (kick) {
+      const double h = mt[ty];
+      v0 = fma(h, F[3 * (size_t)j + 0], v0);
+      v1 = fma(h, F[3 * (size_t)j + 1], v1);
+      v2 = fma(h, F[3 * (size_t)j + 2], v2);
+      v[0] = v0;
+      v[1] = v1;
+      v[2] = v2;
+    }
+    e = mt[MD_HALF_M + ty] * (v0 * v0 + v1 * v1 + v2 * v2);
+    sl = slot[j];
+  }
+  // segmented warp reduction over the (few) distinct slots of this warp
+  unsigned todo = __ballot_sync(0xffffffffu, valid);
+  while (todo) {
+    const int leader = __ffs(todo) - 1;
+    const int s = __shfl_sync(0xffffffffu, sl, leader);
+    const bool mine = valid && sl == s;
+    const double part = warp_sum(mine ? e : 0.0);
+    if (lane == leader) atomicAdd(&ke[s], part);
+    todo &= ~__ballot_sync(0xffffffffu, mine);
+  }
+}
+
+constexpr int NH_LEAD = 1, NH_TRAIL = 2;
+
+// One thread per (replica, group): thermostat half step(s) on the kinetic energy ke; writes the
+// combined velocity scale and the kinetic energy after it.
+__global__ void k_md_nh(int nslots, int mode, const double* __restrict__ ke, double* __restrict__ thermo,
+                        const double* __restrict__ ndof, const double* __restrict__ Qm, double kT, double dt,
+                        double* __restrict__ s_out, double* __restrict__ kcur) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nslots) return;
+  double K = ke[i];
+  double xi = thermo[2 * i], vxi = thermo[2 * i + 1];
+  double stot = 1.0;
+  const double g = ndof[i], Q = Qm[i];
+  if (g > 0.0 && Q > 0.0) {
+    for (int half = 0; half < 2; ++half) {
+      if (!(mode & (half == 0 ? NH_TRAIL : NH_LEAD))) continue;
+      vxi += 0.25 * dt * (2.0 * K - g * kT) / Q;
+      const double s = exp(-0.5 * dt * vxi);
+      K *= s * s;
+      xi += 0.5 * dt * vxi;
+      vxi += 0.25 * dt * (2.0 * K - g * kT) / Q;
+      stot *= s;
+    }
+  }
+  thermo[2 * i] = xi;
+  thermo[2 * i + 1] = vxi;
+  s_out[i] = stot;
+  kcur[i] = K;
+}
+
+__global__ void __launch_bounds__(256) k_md_scale(int n, double* __restrict__ vel, const int* __restrict__ slot,
+                                                  const double* __restrict__ s) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double sc = s[slot[j]];
+  double* v = vel + 3 * (size_t)j;
+  v[0] *= sc;
+  v[1] *= sc;
+  v[2] *= sc;
+}
+
+// Per replica: U, H, U_LJ, KE, thermostat energy, conserved total, temperature, Q_+.
+__global__ void k_md_energy(int nrep, int ngroups, const double* __restrict__ e_coul, const double* __restrict__ scal,
+                            const double* __restrict__ K, const double* __restrict__ thermo,
+                            const double* __restrict__ ndof, const double* __restrict__ Qm, double kT, int thermostat,
+                            double* __restrict__ out) {
+  const int rep = blockIdx.x * blockDim.x + threadIdx.x;
+  if (rep >= nrep) return;
+  double ke = 0.0, enh = 0.0, g = 0.0;
+  for (int k = 0; k < ngroups; ++k) {
+    const int i = rep * ngroups + k;
+    ke += K[i];
+    g += ndof[i];
+    if (thermostat && Qm[i] > 0.0) enh += 0.5 * Qm[i] * thermo[2 * i + 1] * thermo[2 * i + 1] + ndof[i] * kT * thermo[2 * i];
+  }
+  const double U = e_coul[NENERGY * rep + 0], H = e_coul[NENERGY * rep + 1];
+  const double ulj = scal[rep * NSCAL + S_E_LJ];
+  double* o = out + CPM_MD_NENERGY * rep;
+  o[0] = U;
+  o[1] = H;
+  o[2] = ulj;
+  o[3] = ke;
+  o[4] = enh;
+  o[5] = ke + H + ulj + enh;
+  o[6] = g > 0.0 ? 2.0 * ke / (g * KB_EV) : 0.0;
+  o[7] = e_coul[NENERGY * rep + 3];
+}
+
+}  // namespace cpm
+
+using namespace cpm;
+
+#define MD_LAUNCH(ctx) \
+  do {                 \
+    ++(ctx)->launches; \
+    CPM_LAUNCH();      \
+  } while (0)
+
+static int lj_attributes() {
+  const int d64 = (int)((sizeof(double4_32a) + 2 * sizeof(double)) * kLjSrcCap);
+  const int d32 = (int)((sizeof(float4) + 2 * sizeof(float)) * kLjSrcCap);
+  CPM_CUDA(cudaFuncSetAttribute(k_lj_cell<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, d64));
+  CPM_CUDA(cudaFuncSetAttribute(k_lj_cell<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
+  return CPM_OK;
+}
+
+int cpm_internal_lj(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const void* e_loc, cudaStream_t st) {
+  const LjSetup& s = *c->lj;
+  LjGrid a;
+  a.l_loc = l_loc;
+  a.l_start = c->l_start;
+  a.l_sorted = c->l_sorted;
+  a.e_loc = s.elec_type >= 0 ? e_loc : nullptr;
+  a.e_start = c->e_start;
+  a.off = off;
+  a.type = s.type;
+  a.cap = c->p.max_elyt;
+  a.elec_type = s.elec_type;
+  a.nsten = 1;
+  for (int d = 0; d < 3; ++d) {
+    a.nc[d] = c->nc[d];
+    a.sten[d] = c->sten[d];
+    a.w[d] = 2 * c->sten[d] + 1;
+    a.nsten *= a.w[d];
+    a.edge[d] = c->edge[d];
+  }
+  a.cut = s.cut;
+  for (int t = 0; t < kLjMaxTypes; ++t) {
+    a.sig_half[t] = s.sig_half[t];
+    a.sqrt_eps[t] = s.sqrt_eps[t];
+  }
+  a.f_pair = c->f_pair;
+  a.scal = c->scal;
+  const dim3 grid(c->ncell, nrep);
+  if (c->mixed) {
+    k_lj_cell<float><<<grid, LJ_THREADS, (sizeof(float4) + 2 * sizeof(float)) * kLjSrcCap, st>>>(a);
+  } else {
+    k_lj_cell<double><<<grid, LJ_THREADS, (sizeof(double4_32a) + 2 * sizeof(double)) * kLjSrcCap, st>>>(a);
+  }
+  MD_LAUNCH(c);
+  return CPM_OK;
+}
+
+struct cpm_md {
+  cpm_ctx* ctx = nullptr;
+  cpm_md_params p;
+  int nrep = 0, n = 0, ngroups = 1, nslots = 0;
+  int* off = nullptr;          // [nrep + 1]
+  int* type = nullptr;         // [n]
+  int* slot = nullptr;         // [n] rep * ngroups + group
+  double* F = nullptr;         // [n][3] forces at the current positions
+  double* e_coul = nullptr;    // [nrep][NENERGY]
+  double* thermo = nullptr;    // [nslots][2] (xi, v_xi)
+  double* ke = nullptr;        // [nslots]
+  double* kcur = nullptr;      // [nslots]
+  double* s = nullptr;         // [nslots]
+  double* ndof = nullptr;      // [nslots]
+  double* Qm = nullptr;        // [nslots]
+  double* mt = nullptr;        // [2 * kLjMaxTypes] per-type table (MD_HALF_M)
+  LjSetup lj;
+  long long step = 0;
+  bool forces_valid = false;
+};
+
+static void md_free(cpm_md* m) {
+  if (!m) return;
+  void* ptrs[] = {m->off, m->type, m->slot, m->F, m->e_coul, m->thermo, m->ke, m->kcur, m->s, m->ndof, m->Qm, m->mt};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete m;
+}
+
+static int md_check_params(const cpm_ctx* c, const cpm_md_params* p) {
+  if (!(p->dt > 0.0 && std::isfinite(p->dt)) || p->charge_every < 1 || p->n_types < 1 ||
+      p->n_types > CPM_MD_MAX_TYPES || p->n_groups < 1 || p->n_groups > kMdMaxGroups) {
+    set_error("cpm_md_create: dt > 0, charge_every >= 1, 1 <= n_types <= %d, 1 <= n_groups <= %d required",
+              CPM_MD_MAX_TYPES, kMdMaxGroups);
+    return CPM_ERR_ARG;
+  }
+  for (int t = 0; t < p->n_types; ++t) {
+    if (!(p->lj_sigma[t] >= 0.0 && std::isfinite(p->lj_sigma[t]) && p->lj_epsilon[t] >= 0.0 &&
+          std::isfinite(p->lj_epsilon[t]) && std::isfinite(p->mass[t]))) {
+      set_error("cpm_md_create: type %d: sigma, epsilon must be finite and >= 0", t);
+      return CPM_ERR_ARG;
+    }
+  }
+  if (p->elec_type < -1 || p->elec_type >= p->n_types) {
+    set_error("cpm_md_create: elec_type %d outside [-1, n_types)", p->elec_type);
+    return CPM_ERR_ARG;
+  }
+  if (!(p->lj_cut == 0.0 || (p->lj_cut > 0.0 && p->lj_cut <= c->p.rcut))) {
+    set_error("cpm_md_create: lj_cut must be 0 or in (0, rcut = %g]", c->p.rcut);
+    return CPM_ERR_ARG;
+  }
+  if (p->t_damp > 0.0 && !(p->temperature > 0.0 && std::isfinite(p->temperature) && std::isfinite(p->t_damp))) {
+    set_error("cpm_md_create: a thermostat needs temperature > 0");
+    return CPM_ERR_ARG;
+  }
+  return CPM_OK;
+}
+
+extern "C" int cpm_md_create(cpm_ctx* c, const cpm_md_params* p, int32_t n_rep, const int32_t* off_h,
+                             const int32_t* type_h, const int32_t* group_h, void* stream, cpm_md** out) {
+  if (out) *out = nullptr;
+  if (!c || !p || !off_h || !type_h || !out) {
+    set_error("cpm_md_create: null argument");
+    return CPM_ERR_ARG;
+  }
+  CPM_TRY(md_check_params(c, p));
+  if (n_rep < 1 || n_rep > c->p.max_replicas) {
+    set_error("cpm_md_create: n_rep %d outside [1, %d]", n_rep, c->p.max_replicas);
+    return CPM_ERR_CAPACITY;
+  }
+  if (off_h[0] != 0) {
+    set_error("cpm_md_create: offsets[0] must be 0");
+    return CPM_ERR_ARG;
+  }
+  for (int r = 0; r < n_rep; ++r) {
+    const int cnt = off_h[r + 1] - off_h[r];
+    if (cnt < 0 || cnt > c->p.max_elyt) {
+      set_error("cpm_md_create: replica %d has %d sites (capacity %d)", r, cnt, c->p.max_elyt);
+      return cnt < 0 ? CPM_ERR_ARG : CPM_ERR_CAPACITY;
+    }
+  }
+  const int n = off_h[n_rep];
+  const int G = p->n_groups;
+  std::vector<int> slot(std::max(1, n));
+  std::vector<double> ndof((size_t)n_rep * G, 0.0);
+  for (int r = 0; r < n_rep; ++r) {
+    for (int j = off_h[r]; j < off_h[r + 1]; ++j) {
+      const int t = type_h[j], g = group_h ? group_h[j] : 0;
+      if (t < 0 || t >= p->n_types || !(p->mass[t] > 0.0) || g < 0 || g >= G) {
+        set_error("cpm_md_create: site %d: type %d (mass > 0 required) or group %d out of range", j, t, g);
+        return CPM_ERR_ARG;
+      }
+      slot[j] = r * G + g;
+      ndof[(size_t)r * G + g] += 3.0;
+    }
+  }
+  std::vector<double> Qm(ndof.size(), 0.0);
+  if (p->t_damp > 0.0)
+    for (size_t i = 0; i < Qm.size(); ++i) Qm[i] = ndof[i] * KB_EV * p->temperature * p->t_damp * p->t_damp;
+
+  cpm_md* m = new cpm_md();
+  m->ctx = c;
+  m->p = *p;
+  m->nrep = n_rep;
+  m->n = n;
+  m->ngroups = G;
+  m->nslots = n_rep * G;
+  std::vector<double> mt(2 * kLjMaxTypes, 0.0);
+  for (int t = 0; t < kLjMaxTypes; ++t) {
+    const bool used = t < p->n_types;
+    mt[t] = used && p->mass[t] > 0.0 ? 0.5 * p->dt / (p->mass[t] * MVV2E) : 0.0;
+    mt[MD_HALF_M + t] = used ? 0.5 * p->mass[t] * MVV2E : 0.0;
+    m->lj.sig_half[t] = used ? 0.5 * p->lj_sigma[t] : 0.0;
+    m->lj.sqrt_eps[t] = used ? std::sqrt(p->lj_epsilon[t]) : 0.0;
+  }
+  m->lj.elec_type = p->elec_type;
+  m->lj.cut = p->lj_cut;
+  cudaStream_t st = (cudaStream_t)stream;
+  auto fail = [&](int status) {
+    md_free(m);
+    return status;
+  };
+  const size_t ns = (size_t)m->nslots;
+  const size_t n1 = (size_t)std::max(1, n);
+#define MD_ALLOC(ptr, bytes)                                                         \
+  do {                                                                               \
+    cudaError_t e_ = cudaMalloc(&(ptr), (bytes));                                    \
+    if (e_ != cudaSuccess) {                                                         \
+      set_error("cpm_md_create: cudaMalloc: %s", cudaGetErrorString(e_));            \
+      return fail(e_ == cudaErrorMemoryAllocation ? CPM_ERR_NOMEM : CPM_ERR_CUDA);   \
+    }                                                                                \
+  } while (0)
+  MD_ALLOC(m->off, sizeof(int) * (n_rep + 1));
+  MD_ALLOC(m->type, sizeof(int) * n1);
+  MD_ALLOC(m->slot, sizeof(int) * n1);
+  MD_ALLOC(m->F, sizeof(double) * 3 * n1);
+  MD_ALLOC(m->e_coul, sizeof(double) * NENERGY * n_rep);
+  MD_ALLOC(m->thermo, sizeof(double) * 2 * ns);
+  MD_ALLOC(m->ke, sizeof(double) * ns);
+  MD_ALLOC(m->kcur, sizeof(double) * ns);
+  MD_ALLOC(m->s, sizeof(double) * ns);
+  MD_ALLOC(m->ndof, sizeof(double) * ns);
+  MD_ALLOC(m->Qm, sizeof(double) * ns);
+  MD_ALLOC(m->mt, sizeof(double) * 2 * kLjMaxTypes);
+#undef MD_ALLOC
+  auto up = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (bytes == 0) return CPM_OK;
+    CPM_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st));
+    return CPM_OK;
+  };
+  int rc = CPM_OK;
+  if ((rc = up(m->off, off_h, sizeof(int) * (n_rep + 1))) || (rc = up(m->type, type_h, sizeof(int) * n)) ||
+      (rc = up(m->slot, slot.data(), sizeof(int) * n)) || (rc = up(m->ndof, ndof.data(), sizeof(double) * ns)) ||
+      (rc = up(m->Qm, Qm.data(), sizeof(double) * ns)) || (rc = up(m->mt, mt.data(), sizeof(double) * mt.size())))
+    return fail(rc);
+  if (cudaMemsetAsync(m->thermo, 0, sizeof(double) * 2 * ns, st) != cudaSuccess ||
+      cudaMemsetAsync(m->F, 0, sizeof(double) * 3 * n1, st) != cudaSuccess ||
+      cudaMemsetAsync(m->e_coul, 0, sizeof(double) * NENERGY * n_rep, st) != cudaSuccess) {
+    set_error("cpm_md_create: cudaMemsetAsync failed");
+    return fail(CPM_ERR_CUDA);
+  }
+  if ((rc = lj_attributes()) != CPM_OK) return fail(rc);
+  if (cudaStreamSynchronize(st) != cudaSuccess) {
+    set_error("cpm_md_create: stream synchronisation failed");
+    return fail(CPM_ERR_CUDA);
+  }
+  m->lj.type = m->type;
+  *out = m;
+  return CPM_OK;
+}
+
+namespace {
+// Sets ctx->lj for the duration of an MD call.
+struct LjScope {
+  cpm_ctx* c;
+  LjScope(cpm_ctx* c_, const LjSetup* lj) : c(c_) { c->lj = lj; }
+  ~LjScope() { c->lj = nullptr; }
+};
+}  // namespace
+
+extern "C" int cpm_md_run(cpm_md* m, int32_t n_steps, double* xyzq, double* vel, const double* dpsi, double* q,
+                          double* psibar, double* energy, double* force, void* stream) {
+  if (!m || !xyzq || !vel || !dpsi || !q || n_steps < 0) {
+    set_error("cpm_md_run: null pointer or negative step count");
+    return CPM_ERR_ARG;
+  }
+  cpm_ctx* c = m->ctx;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  CPM_CUDA(cudaStreamIsCapturing(st, &cap));
+  const bool capturing = cap == cudaStreamCaptureStatusActive;
+  if (capturing && !m->forces_valid) {
+    set_error("cpm_md_run: run once outside a capture first (the forces at the start are not known)");
+    return CPM_ERR_ARG;
+  }
+  LjScope scope(c, m->p.lj_cut > 0.0 ? &m->lj : nullptr);
+  const int k = m->p.charge_every;
+  const long long step0 = m->step;
+  auto force_eval = [&](bool want_energy) -> int {
+    double* en = want_energy ? m->e_coul : nullptr;
+    if (m->step % k == 0) return cpm_step(c, m->nrep, m->off, xyzq, dpsi, q, psibar, m->F, nullptr, en, stream);
+    return cpm_forces(c, m->nrep, m->off, xyzq, dpsi, q, m->F, nullptr, en, stream);
+  };
+  const bool thermostat = m->p.t_damp > 0.0;
+  const bool want_energy = energy != nullptr;
+  if (!m->forces_valid || (n_steps == 0 && want_energy)) {
+    CPM_TRY(force_eval(want_energy && n_steps == 0));
+    m->forces_valid = true;
+  }
+  const int n = m->n;
+  const int nb = std::max(1, (n + 255) / 256);
+  const double kT = KB_EV * m->p.temperature;
+  const double dt = m->p.dt;
+  const size_t kbytes = sizeof(double) * m->nslots;
+  const int nhb = (m->nslots + 127) / 128;
+  CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
+  k_md_kick_ke<<<nb, 256, 0, st>>>(n, vel, m->F, m->type, m->slot, m->mt, 0, m->ke);
+  MD_LAUNCH(c);
+  if (thermostat && n_steps > 0) {
+    k_md_nh<<<nhb, 128, 0, st>>>(m->nslots, NH_LEAD, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur);
+    MD_LAUNCH(c);
+  }
+  for (int i = 0; i < n_steps; ++i) {
+    k_md_kick_drift<<<nb, 256, 0, st>>>(n, xyzq, vel, m->F, m->type, m->slot, thermostat ? m->s : nullptr, m->mt,
+                                        dt, c->p.box[0], c->p.box[1]);
+    MD_LAUNCH(c);
+    ++m->step;
+    CPM_TRY(force_eval(want_energy && i == n_steps - 1));
+    CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
+    k_md_kick_ke<<<nb, 256, 0, st>>>(n, vel, m->F, m->type, m->slot, m->mt, 1, m->ke);
+    MD_LAUNCH(c);
+    if (thermostat) {
+      const int mode = i == n_steps - 1 ? NH_TRAIL : (NH_TRAIL | NH_LEAD);
+      k_md_nh<<<nhb, 128, 0, st>>>(m->nslots, mode, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur);
+      MD_LAUNCH(c);
+    }
+  }
+  if (thermostat && n_steps > 0) {
+    k_md_scale<<<nb, 256, 0, st>>>(n, vel, m->slot, m->s);
+    MD_LAUNCH(c);
+  }
+  if (want_energy) {
+    k_md_energy<<<(m->nrep + 127) / 128, 128, 0, st>>>(m->nrep, m->ngroups, m->e_coul, c->scal,
+                                                        (thermostat && n_steps > 0) ? m->kcur : m->ke, m->thermo,
+                                                        m->ndof, m->Qm, kT, thermostat ? 1 : 0, energy);
+    MD_LAUNCH(c);
+  }
+  if (force) CPM_CUDA(cudaMemcpyAsync(force, m->F, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, st));
+  if (capturing) m->step = step0;          // a captured call runs on replay: cpm_md_advance counts those
+  return CPM_OK;
+}
+
+extern "C" int cpm_md_advance(cpm_md* m, int64_t n_steps) {
+  if (!m || n_steps < 0) {
+    set_error("cpm_md_advance: null handle or negative count");
+    return CPM_ERR_ARG;
+  }
+  m->step += n_steps;
+  return CPM_OK;
+}
+
+extern "C" int cpm_md_get_state(const cpm_md* m, int64_t* step, double* thermo_host, void* stream) {
+  if (!m) {
+    set_error("cpm_md_get_state: null handle");
+    return CPM_ERR_ARG;
+  }
+  if (step) *step = m->step;
+  if (thermo_host) {
+    cudaStream_t st = (cudaStream_t)stream;
+    CPM_CUDA(cudaMemcpyAsync(thermo_host, m->thermo, sizeof(double) * 2 * m->nslots, cudaMemcpyDeviceToHost, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+  }
+  return CPM_OK;
+}
+
+extern "C" int cpm_md_set_state(cpm_md* m, int64_t step, const double* thermo_host, void* stream) {
+  if (!m || step < 0) {
+    set_error("cpm_md_set_state: null handle or negative step");
+    return CPM_ERR_ARG;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  if (thermo_host) {
+    CPM_CUDA(cudaMemcpyAsync(m->thermo, thermo_host, sizeof(double) * 2 * m->nslots, cudaMemcpyHostToDevice, st));
+    CPM_CUDA(cudaStreamSynchronize(st));
+  }
+  m->step = step;
+  m->forces_valid = false;
+  return CPM_OK;
+}
+
+extern "C" int cpm_md_info(const cpm_md* m, int32_t* n_sites, int32_t* n_slots) {
+  if (!m) {
+    set_error("cpm_md_info: null handle");
+    return CPM_ERR_ARG;
+  }
+  if (n_sites) *n_sites = m->n;
+  if (n_slots) *n_slots = m->nslots;
+  return CPM_OK;
+}
+
+extern "C" void cpm_md_destroy(cpm_md* m) { md_free(m); }

@@ -1659,6 +1659,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
                                                                                  kPairSrcCap, c->scal);
       STEP_LAUNCH();
+      // Lennard-Jones of a running MD loop: same cell list, added into f_pair behind the Coulomb pairs
+      if (c->lj && f_elyt) CPM_TRY(cpm_internal_lj(c, nrep, off, l_loc, e_loc, sp));
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
     // SPME of all charges

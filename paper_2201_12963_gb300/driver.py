@@ -88,3 +88,83 @@ class System:
                 "F_elyt": [fl[off[r]:off[r + 1]] for r in range(R)],
                 "F_elec": self.f_elec.cpu().numpy().reshape(R, ne, 3),
                 "energy": self.energy.cpu().numpy().reshape(R, 4)}
+
+
+class MD:
+    """The MD loop of a System through cpm_md_*: velocities, energies and forces on the device,
+    positions and charges in the System's buffers.  `inputs` is one synth.MDInputs-like object per
+    replica (types, groups, vel, mass, sigma, eps, elec_type, temperature, t_damp)."""
+
+    def __init__(self, system: System, inputs, dt=2.0, charge_every=5, lj_cut=None, t_damp=None,
+                 temperature=None, n_groups=None):
+        from . import cpm_md_create, make_md_params
+        self.s = system
+        inputs = list(inputs) if isinstance(inputs, (list, tuple)) else [inputs]
+        if len(inputs) != system.n_rep:
+            raise ValueError("one MD input per replica required")
+        mi = inputs[0]
+        types = np.concatenate([np.asarray(m.types, np.int32) for m in inputs])
+        groups = np.concatenate([np.asarray(m.groups, np.int32) for m in inputs])
+        vel = np.concatenate([np.asarray(m.vel, np.float64).reshape(-1, 3) for m in inputs])
+        self.n_groups = int(n_groups or (groups.max() + 1 if groups.size else 1))
+        self.params = make_md_params(dt=dt, charge_every=charge_every, mass=mi.mass, sigma=mi.sigma, eps=mi.eps,
+                                     elec_type=mi.elec_type, n_groups=self.n_groups,
+                                     lj_cut=system.w.rcut if lj_cut is None else lj_cut,
+                                     temperature=mi.temperature if temperature is None else temperature,
+                                     t_damp=mi.t_damp if t_damp is None else t_damp)
+        off = system.offsets.cpu().numpy()
+        with torch.cuda.device(system.device):
+            self.md = cpm_md_create(system.ctx, self.params, off, types, groups)
+        f64 = dict(dtype=torch.float64, device=system.device)
+        n = int(off[-1])
+        self.vel = torch.from_numpy(vel.reshape(-1)).to(system.device) if n else torch.zeros(3, **f64)
+        self.energy = torch.zeros(8 * system.n_rep, **f64)
+        self.force = torch.zeros(max(1, n) * 3, **f64)
+
+    def run(self, n_steps, energy=True, force=False, stream=None):
+        from . import cpm_md_run
+        s = self.s
+        cpm_md_run(self.md, n_steps, s.xyzq, self.vel, s.dpsi, s.q, s.psibar, self.energy if energy else None,
+                   self.force if force else None, stream=stream)
+
+    def energies(self) -> list:
+        """Per replica {U, H, U_lj, KE, E_nh, E_total, T, Q_plus} of the last run with energy=True."""
+        from . import MD_ENERGY_KEYS
+        e = self.energy.cpu().numpy().reshape(-1, 8)
+        return [dict(zip(MD_ENERGY_KEYS, map(float, row))) for row in e]
+
+    def checkpoint(self) -> dict:
+        """Everything needed to continue the trajectory (host copies)."""
+        from . import cpm_md_get_state
+        step, thermo = cpm_md_get_state(self.md)
+        s = self.s
+        return {"step": step, "thermo": thermo, "xyzq": s.xyzq.cpu().numpy().copy(), "vel": self.vel.cpu().numpy().copy(),
+                "q": s.q.cpu().numpy().copy()}
+
+    def restore(self, ck: dict):
+        from . import cpm_md_set_state
+        s = self.s
+        s.xyzq.copy_(torch.from_numpy(ck["xyzq"]))
+        self.vel.copy_(torch.from_numpy(ck["vel"]))
+        s.q.copy_(torch.from_numpy(ck["q"]))
+        torch.cuda.synchronize(s.device)
+        cpm_md_set_state(self.md, ck["step"], ck["thermo"])
+
+    def capture(self, n_steps, energy=False):
+        """A CUDA graph of one cpm_md_run of n_steps (capture on a side stream).  Replaying it
+        advances n_steps; call `replay` to keep the library's step index in step."""
+        from . import cpm_md_advance
+        st = torch.cuda.Stream(self.s.device)
+        st.wait_stream(torch.cuda.current_stream(self.s.device))
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(st):
+            with torch.cuda.graph(g, stream=st):
+                self.run(n_steps, energy=energy, stream=st)
+        torch.cuda.current_stream(self.s.device).wait_stream(st)
+
+        def replay(times=1):
+            for _ in range(times):
+                g.replay()
+            cpm_md_advance(self.md, n_steps * times)
+        replay.graph = g
+        return replay
