@@ -45,8 +45,8 @@ enum Slot {
   S_E_LJ = 16      // Lennard-Jones energy of the electrolyte (eV), when an MD run enables it
 };
 
-// Lennard-Jones interactions of an MD run (cpm_md_run), evaluated by the step's force pass on the
-// same cell list while the run holds the context (ctx->lj set for its duration).
+// Lennard-Jones interactions of an MD run (cpm_md_run), evaluated by the step's electrolyte-target
+// pair kernel while the run holds the context (ctx->lj set for its duration).
 constexpr int kLjMaxTypes = 8;
 struct LjSetup {
   const int* type = nullptr;    // [offsets[n_rep]] LJ type per electrolyte site (replica-major)
@@ -401,7 +401,6 @@ int cpm_internal_sym_setup(cpm_ctx* c);
 int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* xl, const double* b,
                             const double* dpsi, const double* Sv, const double* W, const double* c1, double* qout,
                             cudaStream_t st);
-int cpm_internal_lj(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const void* e_loc, cudaStream_t st);
 int cpm_internal_spread_brick(cpm_ctx* c, int nrep, const void* l_loc, const float* qT, cudaStream_t st);
 int cpm_internal_gather_f_brick(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const double* dpsi,
                                 double ff_over_lz, double slab_coef, double* F, cudaStream_t st);

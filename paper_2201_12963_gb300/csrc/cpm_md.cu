@@ -18,9 +18,10 @@
 //
 // Lennard-Jones: Lorentz-Berthelot mixing, force-shifted at the cutoff (energy and force continuous),
 // electrolyte-electrolyte and electrolyte-electrode pairs, summed over every periodic image within
-// the cutoff by the step's cell list (cutoff <= the real-space Coulomb cutoff).  Forces are added
-// into the real-space pair-force buffer on the side stream, after the Coulomb pair kernel, so the
-// force gather of the step adds them to the electrolyte forces.
+// the cutoff (<= the real-space Coulomb cutoff).  The run hands the parameters to the context for
+// its duration; the step's real-space pair kernel for electrolyte targets evaluates them on the
+// same staged sources as the Coulomb pairs (k_pair_cell with LJ), so the force gather of the step
+// returns the sum.
 #include "cpm_internal.cuh"
 
 #include <algorithm>
@@ -31,207 +32,7 @@ namespace cpm {
 
 constexpr double KB_EV = 8.617333262e-5;             // Boltzmann constant, eV / K
 constexpr double MVV2E = 103.64269652680505;         // 1 amu A^2 / fs^2 in eV
-constexpr int LJ_THREADS = 128;
-constexpr int LJ_MAXT = 64;                          // targets per pass of a block
-constexpr int kLjSrcCap = 1024;                      // sources staged per pass
 constexpr int kMdMaxGroups = 4;
-
-struct LjGrid {
-  const void* l_loc;          // cell-sorted cell-local electrolyte coordinates (working precision)
-  const int* l_start;         // [rep][ncell + 1]
-  const int* l_sorted;        // [rep][cap] sorted -> replica-local index
-  const void* e_loc;          // cell-sorted cell-local electrode coordinates, or nullptr (no electrode LJ)
-  const int* e_start;         // [ncell + 1]
-  const int* off;             // [n_rep + 1] replica offsets
-  const int* type;            // [offsets[n_rep]] LJ types
-  int cap;
-  int elec_type;
-  int nc[3], w[3], sten[3], nsten;
-  double edge[3];
-  double cut;
-  double sig_half[kLjMaxTypes], sqrt_eps[kLjMaxTypes];
-  double* f_pair;             // [rep][cap][3] += forces (replica-local original order)
-  double* scal;               // [rep][NSCAL]: S_E_LJ += energy
-};
-
-template <typename T>
-__global__ void __launch_bounds__(LJ_THREADS) k_lj_cell(const LjGrid a) {
-  using V4 = typename Vec4<T>::type;
-  extern __shared__ __align__(32) unsigned char lj_dyn[];
-  V4* src = reinterpret_cast<V4*>(lj_dyn);
-  T* src_sh = reinterpret_cast<T*>(src + kLjSrcCap);
-  T* src_se = src_sh + kLjSrcCap;
-  __shared__ V4 tpos[LJ_MAXT];
-  __shared__ T tsh[LJ_MAXT], tse[LJ_MAXT];
-  __shared__ T ifrc[3][LJ_MAXT], iu[LJ_MAXT];
-  __shared__ int st_first[kMaxStencil];
-  __shared__ int st_pre[kMaxStencil + 1];
-  __shared__ short st_d[3][kMaxStencil];
-  __shared__ T par_sh[kLjMaxTypes], par_se[kLjMaxTypes];
-  __shared__ double ered[LJ_THREADS / 32];
-
-  const int rep = blockIdx.y, cell = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int ncell = a.nc[0] * a.nc[1] * a.nc[2];
-  const int* tst = a.l_start + (size_t)rep * (ncell + 1);
-  const int t0 = tst[cell], t1 = tst[cell + 1];
-  if (t1 <= t0) return;                                     // whole block: empty cell
-  if (tid == 0) {
-#pragma unroll
-    for (int t = 0; t < kLjMaxTypes; ++t) {
-      par_sh[t] = (T)a.sig_half[t];
-      par_se[t] = (T)a.sqrt_eps[t];
-    }
-  }
-  const int o = a.off[rep];
-  const V4* tl = (const V4*)a.l_loc + (size_t)rep * a.cap;
-  const int* tso = a.l_sorted + (size_t)rep * a.cap;
-  const int cz = cell % a.nc[2], cy = (cell / a.nc[2]) % a.nc[1], cx = cell / (a.nc[2] * a.nc[1]);
-  const T e0 = (T)a.edge[0], e1 = (T)a.edge[1], e2 = (T)a.edge[2];
-  const T cut = (T)a.cut, cut2 = cut * cut, icut = T(1) / cut, icut2 = icut * icut;
-  double eblock = 0.0;
-  __syncthreads();
-
-  for (int tb = t0; tb < t1; tb += LJ_MAXT) {
-    const int nt = min(LJ_MAXT, t1 - tb);
-    const int P = max(1, (LJ_THREADS / 32) / nt);           // parts per target: items nt * P <= LJ_MAXT
-    for (int k = tid; k < nt; k += LJ_THREADS) {
-      tpos[k] = tl[tb + k];
-      const int ty = min(kLjMaxTypes - 1, max(0, a.type[o + tso[tb + k]]));
-      tsh[k] = par_sh[ty];
-      tse[k] = par_se[ty];
-    }
-    for (int k = tid; k < nt * P; k += LJ_THREADS) ifrc[0][k] = ifrc[1][k] = ifrc[2][k] = iu[k] = T(0);
-    for (int set = 0; set < 2; ++set) {
-      if (set == 1 && (a.e_loc == nullptr || a.elec_type < 0)) break;
-      const V4* sl = set ? (const V4*)a.e_loc : tl;
-      const int* sst = set ? a.e_start : tst;
-      const T wgt = set ? T(1) : T(0.5);                    // electrolyte pairs are seen from both ends
-      __syncthreads();
-      // stencil cells whose box can hold a source within the cutoff of some point of this cell
-      for (int si = tid; si < a.nsten; si += LJ_THREADS) {
-        const int dx = si % a.w[0] - a.sten[0];
-        const int r1 = si / a.w[0];
-        const int dy = r1 % a.w[1] - a.sten[1];
-        const int dz = r1 / a.w[1] - a.sten[2];
-        const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)max(0, abs(dz) - 1) * e2;
-        int c = 0, f = 0;
-        if (gx * gx + gy * gy + gz * gz < cut2) {
-          const int flat = (wrap_index(cx + dx, a.nc[0]) * a.nc[1] + wrap_index(cy + dy, a.nc[1])) * a.nc[2] +
-                           wrap_index(cz + dz, a.nc[2]);
-          f = sst[flat];
-          c = sst[flat + 1] - f;
-        }
-        st_first[si] = f;
-        st_pre[si + 1] = c;
-        st_d[0][si] = (short)dx;
-        st_d[1][si] = (short)dy;
-        st_d[2][si] = (short)dz;
-      }
-      __syncthreads();
-      if (warp == 0) {                                      // inclusive scan of the counts
-        int run = 0;
-        for (int b = 0; b < a.nsten; b += 32) {
-          const int k = b + lane;
-          int v = k < a.nsten ? st_pre[k + 1] : 0;
-#pragma unroll
-          for (int s = 1; s < 32; s <<= 1) {
-            const int u = __shfl_up_sync(0xffffffffu, v, s);
-            if (lane >= s) v += u;
-          }
-          if (k < a.nsten) st_pre[k + 1] = run + v;
-          run += __shfl_sync(0xffffffffu, v, 31);
-        }
-        if (lane == 0) st_pre[0] = 0;
-      }
-      __syncthreads();
-      const int total = st_pre[a.nsten];
-      for (int c0 = 0; c0 < total; c0 += kLjSrcCap) {
-        const int ns = min(kLjSrcCap, total - c0);
-        for (int k = tid; k < ns; k += LJ_THREADS) {
-          const int j = c0 + k;
-          int lo = 0, hi = a.nsten;                         // st_pre[lo] <= j < st_pre[hi]
-          while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (st_pre[mid] <= j) lo = mid; else hi = mid;
-          }
-          const int gi = st_first[lo] + (j - st_pre[lo]);
-          V4 p = sl[gi];
-          p.x += (T)st_d[0][lo] * e0;
-          p.y += (T)st_d[1][lo] * e1;
-          p.z += (T)st_d[2][lo] * e2;
-          src[k] = p;
-          const int ty = set ? a.elec_type : min(kLjMaxTypes - 1, max(0, a.type[o + tso[gi]]));
-          src_sh[k] = par_sh[ty];
-          src_se[k] = par_se[ty];
-        }
-        __syncthreads();
-        for (int item = warp; item < nt * P; item += LJ_THREADS / 32) {
-          const int ti = item / P, part = item - ti * P;
-          const V4 tp = tpos[ti];
-          const T sh = tsh[ti], se = tse[ti];
-          T fx = 0, fy = 0, fz = 0, u = 0;
-          for (int k = part * 32 + lane; k < ns; k += 32 * P) {
-            const V4 sp = src[k];
-            const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            const T eps = se * src_se[k];
-            if (r2 < cut2 && r2 > T(0) && eps > T(0)) {
-              const T sig = sh + src_sh[k];
-              const T sg2 = sig * sig;
-              const T ir2 = T(1) / r2;
-              const T s2 = sg2 * ir2, s6 = s2 * s2 * s2;
-              const T c2 = sg2 * icut2, c6 = c2 * c2 * c2;
-              const T fc = T(24) * eps * (T(2) * c6 * c6 - c6) * icut;     // LJ force magnitude at the cutoff
-              const T r = sqrt(r2);
-              const T fr = T(24) * eps * ir2 * (T(2) * s6 * s6 - s6) - fc / r;
-              fx += fr * dx;
-              fy += fr * dy;
-              fz += fr * dz;
-              u += wgt * (T(4) * eps * ((s6 * s6 - s6) - (c6 * c6 - c6)) + (r - cut) * fc);
-            }
-          }
-          fx = warp_sum_t(fx);
-          fy = warp_sum_t(fy);
-          fz = warp_sum_t(fz);
-          u = warp_sum_t(u);
-          if (lane == 0) {                                  // the item's slot belongs to this warp alone
-            ifrc[0][item] += fx;
-            ifrc[1][item] += fy;
-            ifrc[2][item] += fz;
-            iu[item] += u;
-          }
-        }
-        __syncthreads();
-      }
-    }
-    __syncthreads();
-    for (int k = tid; k < nt; k += LJ_THREADS) {
-      T fx = 0, fy = 0, fz = 0, u = 0;
-      for (int part = 0; part < P; ++part) {
-        const int item = k * P + part;
-        fx += ifrc[0][item];
-        fy += ifrc[1][item];
-        fz += ifrc[2][item];
-        u += iu[item];
-      }
-      double* f = a.f_pair + 3 * ((size_t)rep * a.cap + tso[tb + k]);
-      f[0] += (double)fx;
-      f[1] += (double)fy;
-      f[2] += (double)fz;
-      eblock += (double)u;
-    }
-    __syncthreads();
-  }
-  eblock = warp_sum(eblock);
-  if (lane == 0) ered[warp] = eblock;
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < LJ_THREADS / 32; ++w) s += ered[w];
-    if (s != 0.0) atomicAdd(a.scal + rep * NSCAL + S_E_LJ, s);
-  }
-}
 
 // ------------------------------------------------------------------------------------------
 // integrator kernels (float64)
@@ -378,51 +179,6 @@ using namespace cpm;
     ++(ctx)->launches; \
     CPM_LAUNCH();      \
   } while (0)
-
-static int lj_attributes() {
-  const int d64 = (int)((sizeof(double4_32a) + 2 * sizeof(double)) * kLjSrcCap);
-  const int d32 = (int)((sizeof(float4) + 2 * sizeof(float)) * kLjSrcCap);
-  CPM_CUDA(cudaFuncSetAttribute(k_lj_cell<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, d64));
-  CPM_CUDA(cudaFuncSetAttribute(k_lj_cell<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
-  return CPM_OK;
-}
-
-int cpm_internal_lj(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const void* e_loc, cudaStream_t st) {
-  const LjSetup& s = *c->lj;
-  LjGrid a;
-  a.l_loc = l_loc;
-  a.l_start = c->l_start;
-  a.l_sorted = c->l_sorted;
-  a.e_loc = s.elec_type >= 0 ? e_loc : nullptr;
-  a.e_start = c->e_start;
-  a.off = off;
-  a.type = s.type;
-  a.cap = c->p.max_elyt;
-  a.elec_type = s.elec_type;
-  a.nsten = 1;
-  for (int d = 0; d < 3; ++d) {
-    a.nc[d] = c->nc[d];
-    a.sten[d] = c->sten[d];
-    a.w[d] = 2 * c->sten[d] + 1;
-    a.nsten *= a.w[d];
-    a.edge[d] = c->edge[d];
-  }
-  a.cut = s.cut;
-  for (int t = 0; t < kLjMaxTypes; ++t) {
-    a.sig_half[t] = s.sig_half[t];
-    a.sqrt_eps[t] = s.sqrt_eps[t];
-  }
-  a.f_pair = c->f_pair;
-  a.scal = c->scal;
-  const dim3 grid(c->ncell, nrep);
-  if (c->mixed) {
-    k_lj_cell<float><<<grid, LJ_THREADS, (sizeof(float4) + 2 * sizeof(float)) * kLjSrcCap, st>>>(a);
-  } else {
-    k_lj_cell<double><<<grid, LJ_THREADS, (sizeof(double4_32a) + 2 * sizeof(double)) * kLjSrcCap, st>>>(a);
-  }
-  MD_LAUNCH(c);
-  return CPM_OK;
-}
 
 struct cpm_md {
   cpm_ctx* ctx = nullptr;
@@ -585,7 +341,6 @@ extern "C" int cpm_md_create(cpm_ctx* c, const cpm_md_params* p, int32_t n_rep, 
     set_error("cpm_md_create: cudaMemsetAsync failed");
     return fail(CPM_ERR_CUDA);
   }
-  if ((rc = lj_attributes()) != CPM_OK) return fail(rc);
   if (cudaStreamSynchronize(st) != cudaSuccess) {
     set_error("cpm_md_create: stream synchronisation failed");
     return fail(CPM_ERR_CUDA);

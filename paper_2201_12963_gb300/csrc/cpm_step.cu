@@ -247,14 +247,36 @@ constexpr int kPairSrcCap = 1024;  // sources staged per pass (dynamic shared me
 constexpr int PC_MAXSTEN = kMaxStencil;
 constexpr int PC_THREADS = 128;
 
-template <typename T, bool FORCE>
+// Lennard-Jones of an MD run, fused into the electrolyte-target force pass (LJ = true): the same
+// staged sources and pair list within r_c serve both interactions.  Lorentz-Berthelot mixing,
+// force-shifted at `cut` (<= r_c); electrolyte pairs count half their energy (seen from both ends).
+struct PairLj {
+  const int* type = nullptr;    // [offsets[n_rep]] per electrolyte site
+  const int* off = nullptr;     // [n_rep + 1]
+  int elec_type = -1;           // type of the electrode sources, -1: none
+  double cut = 0.0;
+  double sig_half[kLjMaxTypes] = {};
+  double sqrt_eps[kLjMaxTypes] = {};
+};
+
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <typename T, bool FORCE, bool LJ = false>
 __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
                                                           const CellGeom g, const double alpha_d, int src_cap,
-                                                          double* __restrict__ scal) {
+                                                          double* __restrict__ scal, const PairLj lj) {
   using V4 = typename Vec4<T>::type;
+  using V2 = typename Vec2<T>::type;
+  static_assert(!LJ || FORCE, "the Lennard-Jones pass computes forces");
   extern __shared__ __align__(32) unsigned char pc_dyn[];
   V4* src = reinterpret_cast<V4*>(pc_dyn);
+  V2* src_lj = reinterpret_cast<V2*>(src + src_cap);          // LJ: (sigma / 2, sqrt eps) per staged source
   __shared__ V4 tpos[PC_MAXT];
+  __shared__ V2 tlj[LJ ? PC_MAXT : 1];
+  __shared__ T ilj[LJ ? 4 : 1][LJ ? PC_MAXT : 1];            // LJ force (3) and energy per item
+  __shared__ T lpar[2][kLjMaxTypes];
   // per work item (target, part) of the current target batch, in the working precision:
   // compensated potential (sum, error) per source set, and the force sums
   __shared__ T ipot[2][PC_MAXT][2];
@@ -280,6 +302,17 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   const T* tq = t.qT ? (const T*)t.qT + (size_t)rep * t.n_fixed : nullptr;
   const bool want_energy = s0.slot >= 0 || s1.slot >= 0;     // uniform over the block
   Acc<T> ea0, ea1;                  // sum_t c_t phi_t per source set, working precision, compensated
+  const int lj_o = LJ ? lj.off[rep] : 0;
+  const T ljc = (T)lj.cut, ljc2 = ljc * ljc, ljic = LJ ? T(1) / ljc : T(0);
+  double elj = 0.0;                 // LJ energy of this block's targets
+  if (LJ && tid == 0) {
+#pragma unroll
+    for (int k = 0; k < kLjMaxTypes; ++k) {
+      lpar[0][k] = (T)lj.sig_half[k];
+      lpar[1][k] = (T)lj.sqrt_eps[k];
+    }
+  }
+  if (LJ) __syncthreads();
 
   for (int tb = t0; tb < t1; tb += PC_MAXT) {
     const int nt = min(PC_MAXT, t1 - tb);
@@ -288,10 +321,18 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       V4 p = tl[tb + k];
       if (tq) p.w = tq[tso[tb + k]];
       tpos[k] = p;
+      if (LJ) {
+        const int ty = min(kLjMaxTypes - 1, max(0, lj.type[lj_o + tso[tb + k]]));
+        V2 par;
+        par.x = lpar[0][ty];
+        par.y = lpar[1][ty];
+        tlj[k] = par;
+      }
     }
     for (int k = tid; k < nt * P; k += PC_THREADS) {
       ipot[0][k][0] = ipot[0][k][1] = ipot[1][k][0] = ipot[1][k][1] = T(0);
       ifrc[0][k] = ifrc[1][k] = ifrc[2][k] = T(0);
+      if (LJ) ilj[0][k] = ilj[1][k] = ilj[2][k] = ilj[3][k] = T(0);
     }
     for (int set = 0; set < 2; ++set) {
       // fields of the selected source set, read into registers (no local copy of the parameters)
@@ -302,7 +343,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       const void* s_q = set ? s1.qT : s0.qT;
       const T* sq = s_q ? (const T*)s_q + (size_t)rep * (set ? s1.q_stride : s0.q_stride) : nullptr;
       const int* s_sorted = set ? s1.sorted : s0.sorted;
+      const int* s_sorted_r = s_sorted + rep * (set ? s1.loc_stride : s0.loc_stride);
       const double s_beta = set ? s1.beta : s0.beta;
+      const T ljw = set ? T(1) : T(0.5);      // electrolyte-electrolyte LJ pairs are seen from both ends
       const bool gauss = s_beta > 0.0;
       const T beta = (T)s_beta;
       __syncthreads();
@@ -362,6 +405,13 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           p.z += (T)st_d[2][lo] * e2;
           if (sq) p.w = sq[s_sorted[gi]];
           src[k] = p;
+          if (LJ) {
+            const int ty = set ? lj.elec_type : min(kLjMaxTypes - 1, max(0, lj.type[lj_o + s_sorted_r[gi]]));
+            V2 par;
+            par.x = ty >= 0 ? lpar[0][ty] : T(0);
+            par.y = ty >= 0 ? lpar[1][ty] : T(0);
+            src_lj[k] = par;
+          }
         }
         __syncthreads();
         // ---- compute: work item = (target, part); a warp sweeps 1/P of the staged sources for
@@ -375,19 +425,42 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           const V4 tp = tpos[ti];
           Acc<T> pot;
           T fx = 0, fy = 0, fz = 0;
+          T lx = 0, ly = 0, lz = 0, lu = 0;      // Lennard-Jones force and energy (LJ only)
+          V2 tpar;
+          if (LJ) tpar = tlj[ti];
           int head = 0, cnt = 0;                 // queued entries: ring[(head .. head + cnt) mod 64]
           auto consume = [&](int n) {
             if (lane < n) {
-              const V4 sp = src[ring[(head + lane) & 63]];
+              const int idx = ring[(head + lane) & 63];
+              const V4 sp = src[idx];
               const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
+              const T r2 = dx * dx + dy * dy + dz * dz;
               T pr, fr = T(0);
-              PairMath<T>::template eval<FORCE>(dx * dx + dy * dy + dz * dz, alpha, beta, gauss, pr, fr);
+              PairMath<T>::template eval<FORCE>(r2, alpha, beta, gauss, pr, fr);
               pot.add(sp.w * pr);
               if (FORCE) {
                 fr *= sp.w;
                 fx += fr * dx;
                 fy += fr * dy;
                 fz += fr * dz;
+              }
+              if (LJ) {
+                const V2 spar = src_lj[idx];
+                const T eps = tpar.y * spar.y;
+                if (r2 < ljc2 && eps > T(0)) {
+                  const T sig = tpar.x + spar.x;
+                  const T sg2 = sig * sig;
+                  const T ir2 = T(1) / r2;
+                  const T s2 = sg2 * ir2, s6 = s2 * s2 * s2;
+                  const T c2 = sg2 * ljic * ljic, c6 = c2 * c2 * c2;
+                  const T fc = T(24) * eps * (T(2) * c6 * c6 - c6) * ljic;   // force magnitude at the cutoff
+                  const T r = sqrt(r2);
+                  const T fl = T(24) * eps * ir2 * (T(2) * s6 * s6 - s6) - fc / r;
+                  lx += fl * dx;
+                  ly += fl * dy;
+                  lz += fl * dz;
+                  lu += ljw * (T(4) * eps * ((s6 * s6 - s6) - (c6 * c6 - c6)) + (r - ljc) * fc);
+                }
               }
             }
             head = (head + n) & 63;
@@ -415,6 +488,18 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
             fx = warp_sum_t(fx);
             fy = warp_sum_t(fy);
             fz = warp_sum_t(fz);
+          }
+          if (LJ) {
+            lx = warp_sum_t(lx);
+            ly = warp_sum_t(ly);
+            lz = warp_sum_t(lz);
+            lu = warp_sum_t(lu);
+            if (lane == 0) {
+              ilj[0][item] += lx;
+              ilj[1][item] += ly;
+              ilj[2][item] += lz;
+              ilj[3][item] += lu;
+            }
           }
           if (lane == 0) {                       // the item's slot belongs to this warp alone
             T* a = ipot[set][item];
@@ -460,15 +545,41 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         ea1.add(ct * p1.s);
         ea1.c += ct * p1.c;
       }
+      double ljf[3] = {0.0, 0.0, 0.0};
+      if (LJ) {
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        for (int part = 0; part < P; ++part) {
+          const int item = k * P + part;
+          a0 += ilj[0][item];
+          a1 += ilj[1][item];
+          a2 += ilj[2][item];
+          a3 += ilj[3][item];
+        }
+        ljf[0] = (double)a0;
+        ljf[1] = (double)a1;
+        ljf[2] = (double)a2;
+        elj += (double)a3;
+      }
       if (FORCE && t.force) {
         const size_t gi = (size_t)rep * t.n_fixed + orig;
         const double f = KE * qt;
-        t.force[3 * gi + 0] += f * (double)fx;
-        t.force[3 * gi + 1] += f * (double)fy;
-        t.force[3 * gi + 2] += f * (double)fz;
+        t.force[3 * gi + 0] += f * (double)fx + ljf[0];
+        t.force[3 * gi + 1] += f * (double)fy + ljf[1];
+        t.force[3 * gi + 2] += f * (double)fz + ljf[2];
       }
     }
     __syncthreads();
+  }
+  if (LJ) {
+    __shared__ double ljred[PC_THREADS / 32];
+    elj = warp_sum(elj);
+    if (lane == 0) ljred[warp] = elj;
+    __syncthreads();
+    if (tid == 0) {
+      double e = 0.0;
+      for (int w = 0; w < PC_THREADS / 32; ++w) e += ljred[w];
+      if (e != 0.0) atomicAdd(scal + rep * NSCAL + S_E_LJ, e);
+    }
   }
   if (!want_energy) return;
   // block total in the working precision (compensated), one float64 atomic per slot
@@ -1499,7 +1610,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
       k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sside>>>(tg, s, none, g, c->p.alpha,
-                                                                                  kPairSrcCap, c->scal);
+                                                                                  kPairSrcCap, c->scal, PairLj{});
       STEP_LAUNCH();
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
@@ -1652,15 +1763,28 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       e.qT = qT;
       e.beta = c->p.eta;
       e.slot = S_E_LE;
-      if (f_elyt)
+      if (f_elyt && c->lj) {
+        // Lennard-Jones of a running MD loop, fused: the same staged sources and pair list
+        PairLj lj;
+        lj.type = c->lj->type;
+        lj.off = off;
+        lj.elec_type = c->lj->elec_type;
+        lj.cut = c->lj->cut;
+        for (int k = 0; k < kLjMaxTypes; ++k) {
+          lj.sig_half[k] = c->lj->sig_half[k];
+          lj.sqrt_eps[k] = c->lj->sqrt_eps[k];
+        }
+        const size_t smem_lj = (sizeof(V4) + sizeof(typename Vec2<T>::type)) * kPairSrcCap;
+        k_pair_cell<T, true, true><<<dim3(c->ncell, nrep), PC_THREADS, smem_lj, sp>>>(tg, a, e, g, c->p.alpha,
+                                                                                      kPairSrcCap, c->scal, lj);
+      } else if (f_elyt) {
         k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal);
-      else
+                                                                                kPairSrcCap, c->scal, PairLj{});
+      } else {
         k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal);
+                                                                                 kPairSrcCap, c->scal, PairLj{});
+      }
       STEP_LAUNCH();
-      // Lennard-Jones of a running MD loop: same cell list, added into f_pair behind the Coulomb pairs
-      if (c->lj && f_elyt) CPM_TRY(cpm_internal_lj(c, nrep, off, l_loc, e_loc, sp));
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
     // SPME of all charges
@@ -1711,10 +1835,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       e.slot = (energy && !closed_form) ? S_E_EE : -1;
       if (f_elec)
         k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal);
+                                                                                kPairSrcCap, c->scal, PairLj{});
       else
         k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal);
+                                                                                 kPairSrcCap, c->scal, PairLj{});
       STEP_LAUNCH();
     }
     if (energy) {
@@ -1762,6 +1886,12 @@ static int pair_cell_attributes() {
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d64));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
+  const int l64 = (int)((sizeof(double4_32a) + sizeof(double2)) * cpm::kPairSrcCap);
+  const int l32 = (int)((sizeof(float4) + sizeof(float2)) * cpm::kPairSrcCap);
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                l64));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                l32));
   return CPM_OK;
 }
 
