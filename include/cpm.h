@@ -126,6 +126,34 @@ int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const double* elec_xyz
                      cpm_ctx** out);
 
 /*
+ * Matrix images: S is the expensive part of a context (assembling A, a dense Cholesky
+ * factorisation and inverse: seconds to a minute at tens of thousands of sites) and depends only
+ * on the electrode and the parameters below, so it can be kept (on disk, by the caller) and a later
+ * context built from it.  The paper has no counterpart (it precomputes S once per run, Sec. II.A).
+ *
+ * cpm_matrix_key - 64-bit FNV-1a hash of every input that determines A: box, eta, alpha, rcut, the
+ *   slab factor (CPM_SLAB), kmax_build (Ewald form), geometry, matrix_kspace, dc_blocks
+ *   (CPM_DOUBLED), grid and spme_order (mesh form), and the electrode arrays exactly as passed
+ *   (n_elec, xyz, side, cell).  Precision, capacities and the per-step mesh of the Ewald form do not
+ *   enter.  Host only; the same validation as cpm_build_matrix.
+ * cpm_matrix_image - with host_out NULL, *bytes receives the image size; otherwise the context's
+ *   image (a header with the key and the layout, then S or the two mirror blocks in float64 rows of
+ *   the stored stride, A^-1 C, S v) is written to host_out, whose size *bytes must be at least that.
+ *   Synchronous.
+ * cpm_build_matrix_from_image - cpm_build_matrix without assembling or factorising A: S, A^-1 C,
+ *   S v and the projection scalars come from an image made by cpm_matrix_image.  CPM_ERR_ARG when
+ *   the image's key or layout does not match these inputs (a stale or foreign image is refused,
+ *   never used).  Everything else (electrode stencils, cell lists, meshes, plans, workspaces, the
+ *   float32 copy of S for CPM_MIXED) is built as usual.
+ */
+int cpm_matrix_key(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host, const int32_t* elec_side_host,
+                   const int32_t* elec_cell_host, uint64_t* key);
+int cpm_matrix_image(const cpm_ctx* ctx, void* host_out, int64_t* bytes);
+int cpm_build_matrix_from_image(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
+                                const int32_t* elec_side_host, const int32_t* elec_cell_host, const void* image_host,
+                                int64_t image_bytes, void* stream, cpm_ctx** out);
+
+/*
  * cpm_step_charges - one CPM charge update for n_rep replicas sharing the electrode (Sec. II.A,
  * "the main computational burden ... is to obtain b"): cell list, real-space b, SPME spread,
  * FFT, influence function, inverse FFT, gather at the electrode sites, S-apply and the

@@ -21,7 +21,7 @@ PRECISION = {"fp64": CPM_FP64, "mixed": CPM_MIXED}
 MATRIX_KSPACE = {"ewald": 0, "mesh": 1}                 # enum cpm_matrix_kspace
 DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 
-EXPORTED = ("cpm_build_matrix", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
+EXPORTED = ("cpm_build_matrix", "cpm_matrix_key", "cpm_matrix_image", "cpm_build_matrix_from_image", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
             "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
             "cpm_autotune", "cpm_density_z", "cpm_potential_z",
@@ -73,6 +73,10 @@ def _load():
     lib = ctypes.CDLL(path)
     vp, i32, pd, pi32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p, ctypes.c_void_p
     lib.cpm_build_matrix.argtypes = [ctypes.POINTER(CpmParams), i32, pd, pi32, pi32, vp, ctypes.POINTER(vp)]
+    lib.cpm_matrix_key.argtypes = [ctypes.POINTER(CpmParams), i32, pd, pi32, pi32, ctypes.POINTER(ctypes.c_uint64)]
+    lib.cpm_matrix_image.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int64)]
+    lib.cpm_build_matrix_from_image.argtypes = [ctypes.POINTER(CpmParams), i32, pd, pi32, pi32, vp, ctypes.c_int64,
+                                                vp, ctypes.POINTER(vp)]
     lib.cpm_step_charges.argtypes = [vp, i32, pi32, pd, pd, pd, pd, pd, vp]
     lib.cpm_forces.argtypes = [vp, i32, pi32, pd, pd, pd, pd, pd, pd, vp]
     lib.cpm_energy.argtypes = [vp, i32, pi32, pd, pd, pd, pd, vp]
@@ -200,6 +204,46 @@ def cpm_build_matrix(params: CpmParams, elec_xyz, elec_side, elec_cell=None, str
     s = _lib.cpm_build_matrix(ctypes.byref(params), n, xyz.ctypes.data, side.ctypes.data,
                               None if cell is None else cell.ctypes.data, st, ctypes.byref(out))
     _check(s, "cpm_build_matrix")
+    return Context(out.value, params)
+
+
+def _electrode_arrays(elec_xyz, elec_side, elec_cell):
+    xyz = np.ascontiguousarray(elec_xyz, dtype=np.float64)
+    side = np.ascontiguousarray(elec_side, dtype=np.int32)
+    cell = None if elec_cell is None else np.ascontiguousarray(elec_cell, dtype=np.int32)
+    n = xyz.shape[0]
+    if xyz.shape != (n, 3) or side.shape != (n,) or (cell is not None and cell.shape != (n,)):
+        raise ValueError("electrode arrays have inconsistent shapes")
+    return xyz, side, cell, n
+
+
+def cpm_matrix_key(params: CpmParams, elec_xyz, elec_side, elec_cell=None) -> int:
+    """64-bit key of the inputs that determine A (names cached matrix images)."""
+    xyz, side, cell, n = _electrode_arrays(elec_xyz, elec_side, elec_cell)
+    key = ctypes.c_uint64()
+    _check(_lib.cpm_matrix_key(ctypes.byref(params), n, xyz.ctypes.data, side.ctypes.data,
+                               None if cell is None else cell.ctypes.data, ctypes.byref(key)), "cpm_matrix_key")
+    return int(key.value)
+
+
+def cpm_matrix_image(ctx: Context) -> bytes:
+    """The context's matrix image (S, A^-1 C, S v and the projection scalars, with its key)."""
+    nb = ctypes.c_int64()
+    _check(_lib.cpm_matrix_image(ctx.handle, None, ctypes.byref(nb)), "cpm_matrix_image")
+    buf = np.empty(int(nb.value), dtype=np.uint8)
+    _check(_lib.cpm_matrix_image(ctx.handle, buf.ctypes.data, ctypes.byref(nb)), "cpm_matrix_image")
+    return buf
+
+
+def cpm_build_matrix_from_image(params: CpmParams, elec_xyz, elec_side, elec_cell, image, stream=None) -> Context:
+    xyz, side, cell, n = _electrode_arrays(elec_xyz, elec_side, elec_cell)
+    img = np.ascontiguousarray(np.frombuffer(image, dtype=np.uint8) if isinstance(image, (bytes, bytearray))
+                               else image, dtype=np.uint8)
+    out = ctypes.c_void_p()
+    s = _lib.cpm_build_matrix_from_image(ctypes.byref(params), n, xyz.ctypes.data, side.ctypes.data,
+                                         None if cell is None else cell.ctypes.data, img.ctypes.data, img.size,
+                                         _stream_ptr(stream), ctypes.byref(out))
+    _check(s, "cpm_build_matrix_from_image")
     return Context(out.value, params)
 
 

@@ -535,6 +535,8 @@ static int kspace_block(cpm_ctx* c, const double4_32a* rows_pos, const double4_3
 }
 
 // Full matrix: A (ne x ne) -> S = A^-1 - A^-1 C (C^T A^-1 C)^-1 C^T A^-1, A^-1 C, S v.
+static int finish_s32(cpm_ctx* c, int rows, cudaStream_t st);
+
 static int build_full(cpm_ctx* c, const std::vector<double>& v, const std::vector<double>& c1,
                       const int32_t* side, cudaStream_t st) {
   const int ne = c->ne;
@@ -603,12 +605,7 @@ static int build_full(cpm_ctx* c, const std::vector<double>& v, const std::vecto
     for (int i = 0; i < ne; ++i)
       if (side[i] > 0) c->dqdpsi += svh[i];
   }
-  if (c->mixed) {
-    CPM_TRY(dev_alloc(&c->S32, (size_t)ne * c->ld32));
-    k_to_float<<<dim3((c->ld32 + 255) / 256, ne), 256, 0, st>>>(c->S64, ne, c->ld64, c->S32, c->ld32);
-    CPM_LAUNCH();
-  }
-  return CPM_OK;
+  return finish_s32(c, ne, st);
 }
 
 // Doubled cell whose sub-cell-1 electrode is the z-mirror image of the sub-cell-0 one: with the sites
@@ -720,12 +717,7 @@ static int build_mirror(cpm_ctx* c, const std::vector<double4_32a>& pos, const s
     }
   }
   cudaFree(dv);
-  if (c->mixed) {
-    CPM_TRY(dev_alloc(&c->S32, (size_t)2 * N * ldh));
-    k_to_float<<<dim3((ldh + 255) / 256, 2 * N), 256, 0, st>>>(c->S64, N, ldh, c->S32, ldh);
-    CPM_LAUNCH();
-  }
-  return CPM_OK;
+  return finish_s32(c, 2 * N, st);
 }
 
 // Pairs every sub-cell-0 site with the sub-cell-1 site at its z-mirror image (x, y, L_z - z)
@@ -779,8 +771,117 @@ static bool find_mirror(cpm_ctx* c, const std::vector<double4_32a>& pos, const i
   return true;
 }
 
+// ------------------------------------------------------------------------------------------
+// matrix image: S (or the two mirror blocks), A^-1 C, S v and the projection scalars, so that a
+// context can be rebuilt without assembling and factorising A (cpm_matrix_image and
+// cpm_build_matrix_from_image).  The key is FNV-1a 64 (Fowler, Noll, Vo) over every input that
+// determines A; an image is accepted only by a build whose inputs give the same key.
+// ------------------------------------------------------------------------------------------
+struct ImageHeader {
+  char magic[8];                 // "CPMSIMG1"
+  uint64_t key;
+  int32_t ne, ncons, mirror, nh, ld64, reserved;
+  int64_t nS, nW, nSv;           // float64 counts of the three arrays that follow the header
+  double Mh[4], WTv[2], dqdpsi;
+};
+constexpr char kImageMagic[8] = {'C', 'P', 'M', 'S', 'I', 'M', 'G', '1'};
+
+struct Fnv1a {
+  uint64_t h = 1469598103934665603ull;
+  void add(const void* data, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; ++i) {
+      h ^= b[i];
+      h *= 1099511628211ull;
+    }
+  }
+};
+
+static uint64_t matrix_key(const cpm_params* p, int32_t ne, const double* xyz, const int32_t* side,
+                           const int32_t* cell) {
+  Fnv1a f;
+  const int32_t version = 1;
+  f.add(&version, sizeof version);
+  f.add(p->box, sizeof p->box);
+  f.add(&p->eta, sizeof(double));
+  f.add(&p->alpha, sizeof(double));
+  f.add(&p->rcut, sizeof(double));
+  const double sf = p->geometry == CPM_SLAB ? p->slab_factor : 0.0;
+  f.add(&sf, sizeof sf);
+  const double km = p->matrix_kspace == CPM_KSPACE_EWALD ? p->kmax_build : 0.0;
+  f.add(&km, sizeof km);
+  f.add(&p->geometry, sizeof(int32_t));
+  f.add(&p->matrix_kspace, sizeof(int32_t));
+  const int32_t dcb = p->geometry == CPM_DOUBLED ? p->dc_blocks : 0;
+  f.add(&dcb, sizeof dcb);
+  if (p->matrix_kspace == CPM_KSPACE_MESH) {
+    f.add(p->grid, sizeof p->grid);
+    f.add(&p->spme_order, sizeof(int32_t));
+  }
+  f.add(&ne, sizeof ne);
+  f.add(xyz, sizeof(double) * 3 * (size_t)ne);
+  f.add(side, sizeof(int32_t) * (size_t)ne);
+  if (p->geometry == CPM_DOUBLED && cell) f.add(cell, sizeof(int32_t) * (size_t)ne);
+  return f.h;
+}
+
+// float32 copy of S for the mixed path (rows of the stored form: N_e, or 2 N_e/2 for mirror blocks)
+static int finish_s32(cpm_ctx* c, int rows, cudaStream_t st) {
+  if (!c->mixed) return CPM_OK;
+  CPM_TRY(dev_alloc(&c->S32, (size_t)rows * c->ld32));
+  k_to_float<<<dim3((c->ld32 + 255) / 256, rows), 256, 0, st>>>(c->S64, rows, c->ld64, c->S32, c->ld32);
+  CPM_LAUNCH();
+  return CPM_OK;
+}
+
+// Instead of build_full / build_mirror: the same device state from an image.
+static int load_image(cpm_ctx* c, const void* image, int64_t bytes, uint64_t key, cudaStream_t st) {
+  if (bytes < (int64_t)sizeof(ImageHeader)) {
+    set_error("matrix image: %lld bytes is shorter than its header", (long long)bytes);
+    return CPM_ERR_ARG;
+  }
+  ImageHeader h;
+  std::memcpy(&h, image, sizeof h);
+  const int ne = c->ne;
+  const int rows = c->mirror ? 2 * c->nh : ne;
+  const int ld = c->mirror ? ((c->nh + 3) & ~3) : ((ne + 3) & ~3);
+  const int64_t nS = (int64_t)rows * ld, nW = c->mirror ? 4LL * c->nh : 2LL * ne, nSv = rows;
+  if (std::memcmp(h.magic, kImageMagic, 8) != 0 || h.key != key || h.ne != ne || h.ncons != c->ncons ||
+      h.mirror != (c->mirror ? 1 : 0) || h.nh != c->nh || h.ld64 != ld || h.nS != nS || h.nW != nW || h.nSv != nSv ||
+      bytes != (int64_t)sizeof(ImageHeader) + 8 * (nS + nW + nSv)) {
+    set_error("matrix image does not belong to these parameters and electrode (key or layout differs)");
+    return CPM_ERR_ARG;
+  }
+  c->ld64 = c->ld32 = ld;
+  if (c->mirror) {
+    c->ldh = ld;
+    c->ldx = 2 * ld;
+    CPM_TRY(upload(&c->m_i0, c->h_i0, st));
+    CPM_TRY(upload(&c->m_j, c->h_j, st));
+    std::vector<double> c1m(2 * (size_t)c->nh, 0.0);
+    for (int k = 0; k < c->nh; ++k) c1m[c->nh + k] = 1.0;
+    CPM_TRY(upload(&c->e_c1m, c1m, st));
+  } else {
+    c->ldx = ld;
+  }
+  const double* src = reinterpret_cast<const double*>(static_cast<const char*>(image) + sizeof(ImageHeader));
+  CPM_TRY(dev_alloc(&c->S64, (size_t)nS));
+  CPM_TRY(dev_alloc(&c->W, (size_t)nW));
+  CPM_TRY(dev_alloc(&c->Sv, (size_t)nSv));
+  CPM_CUDA(cudaMemcpyAsync(c->S64, src, sizeof(double) * nS, cudaMemcpyHostToDevice, st));
+  CPM_CUDA(cudaMemcpyAsync(c->W, src + nS, sizeof(double) * nW, cudaMemcpyHostToDevice, st));
+  CPM_CUDA(cudaMemcpyAsync(c->Sv, src + nS + nW, sizeof(double) * nSv, cudaMemcpyHostToDevice, st));
+  for (int k = 0; k < 4; ++k) c->Mh[k] = h.Mh[k];
+  c->WTv[0] = h.WTv[0];
+  c->WTv[1] = h.WTv[1];
+  c->dqdpsi = h.dqdpsi;
+  CPM_TRY(finish_s32(c, rows, st));
+  CPM_CUDA(cudaStreamSynchronize(st));
+  return CPM_OK;
+}
+
 static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side, const int32_t* cell,
-                 cudaStream_t st) {
+                 cudaStream_t st, const void* image = nullptr, int64_t image_bytes = 0) {
   const cpm_params& p = c->p;
   c->ne = ne;
   c->ncons = (p.geometry == CPM_DOUBLED) ? 2 : 1;
@@ -910,7 +1011,8 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
     }
     c->nh = ne / 2;
   }
-  if (c->mirror) CPM_TRY(build_mirror(c, pos, v, side, st));
+  if (image) CPM_TRY(load_image(c, image, image_bytes, matrix_key(&p, ne, xyz, side, cell), st));
+  else if (c->mirror) CPM_TRY(build_mirror(c, pos, v, side, st));
   else CPM_TRY(build_full(c, v, c1, side, st));
 
   // ---------------- SPME ----------------
@@ -956,7 +1058,92 @@ extern "C" int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const doubl
   cpm_ctx* c = new (std::nothrow) cpm_ctx();
   if (!c) return CPM_ERR_NOMEM;
   c->p = *p;
+  c->key = cpm::matrix_key(p, n_elec, elec_xyz_host, elec_side_host, elec_cell_host);
   const int s = cpm::build(c, n_elec, elec_xyz_host, elec_side_host, elec_cell_host, (cudaStream_t)stream);
+  if (s != CPM_OK) {
+    cudaStreamSynchronize((cudaStream_t)stream);
+    cpm_destroy(c);
+    return s;
+  }
+  *out = c;
+  return CPM_OK;
+}
+
+extern "C" int cpm_matrix_key(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
+                              const int32_t* elec_side_host, const int32_t* elec_cell_host, uint64_t* key) {
+  if (!key) return CPM_ERR_ARG;
+  const int v = cpm::validate(p, n_elec, elec_xyz_host, elec_side_host, elec_cell_host);
+  if (v != CPM_OK) {
+    cpm::set_error("cpm_matrix_key: invalid parameters or electrode input");
+    return v;
+  }
+  *key = cpm::matrix_key(p, n_elec, elec_xyz_host, elec_side_host, elec_cell_host);
+  return CPM_OK;
+}
+
+extern "C" int cpm_matrix_image(const cpm_ctx* c, void* host_out, int64_t* bytes) {
+  if (!c || !bytes) {
+    cpm::set_error("cpm_matrix_image: null argument");
+    return CPM_ERR_ARG;
+  }
+  const int rows = c->mirror ? 2 * c->nh : c->ne;
+  const int64_t nS = (int64_t)rows * c->ld64, nW = c->mirror ? 4LL * c->nh : 2LL * c->ne, nSv = rows;
+  const int64_t need = (int64_t)sizeof(cpm::ImageHeader) + 8 * (nS + nW + nSv);
+  if (!host_out) {
+    *bytes = need;
+    return CPM_OK;
+  }
+  if (*bytes < need) {
+    cpm::set_error("cpm_matrix_image: buffer of %lld bytes, %lld needed", (long long)*bytes, (long long)need);
+    return CPM_ERR_ARG;
+  }
+  cpm::ImageHeader h;
+  std::memset(&h, 0, sizeof h);
+  std::memcpy(h.magic, cpm::kImageMagic, 8);
+  h.key = c->key;
+  h.ne = c->ne;
+  h.ncons = c->ncons;
+  h.mirror = c->mirror ? 1 : 0;
+  h.nh = c->nh;
+  h.ld64 = c->ld64;
+  h.nS = nS;
+  h.nW = nW;
+  h.nSv = nSv;
+  for (int k = 0; k < 4; ++k) h.Mh[k] = c->Mh[k];
+  h.WTv[0] = c->WTv[0];
+  h.WTv[1] = c->WTv[1];
+  h.dqdpsi = c->dqdpsi;
+  char* dst = static_cast<char*>(host_out);
+  std::memcpy(dst, &h, sizeof h);
+  double* body = reinterpret_cast<double*>(dst + sizeof h);
+  CPM_CUDA(cudaMemcpy(body, c->S64, sizeof(double) * nS, cudaMemcpyDeviceToHost));
+  CPM_CUDA(cudaMemcpy(body + nS, c->W, sizeof(double) * nW, cudaMemcpyDeviceToHost));
+  CPM_CUDA(cudaMemcpy(body + nS + nW, c->Sv, sizeof(double) * nSv, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return CPM_OK;
+}
+
+extern "C" int cpm_build_matrix_from_image(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
+                                           const int32_t* elec_side_host, const int32_t* elec_cell_host,
+                                           const void* image_host, int64_t image_bytes, void* stream,
+                                           cpm_ctx** out) {
+  if (!out) return CPM_ERR_ARG;
+  *out = nullptr;
+  if (!image_host) {
+    cpm::set_error("cpm_build_matrix_from_image: null image");
+    return CPM_ERR_ARG;
+  }
+  const int v = cpm::validate(p, n_elec, elec_xyz_host, elec_side_host, elec_cell_host);
+  if (v != CPM_OK) {
+    cpm::set_error("cpm_build_matrix_from_image: invalid parameters or electrode input");
+    return v;
+  }
+  cpm_ctx* c = new (std::nothrow) cpm_ctx();
+  if (!c) return CPM_ERR_NOMEM;
+  c->p = *p;
+  c->key = cpm::matrix_key(p, n_elec, elec_xyz_host, elec_side_host, elec_cell_host);
+  const int s = cpm::build(c, n_elec, elec_xyz_host, elec_side_host, elec_cell_host, (cudaStream_t)stream,
+                           image_host, image_bytes);
   if (s != CPM_OK) {
     cudaStreamSynchronize((cudaStream_t)stream);
     cpm_destroy(c);

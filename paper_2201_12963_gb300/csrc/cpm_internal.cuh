@@ -143,6 +143,7 @@ struct cpm_ctx {
   CUtensorMap br_map;           // 4-D tiled map of br_pad: (z, y, x, replica), box br_B
   cudaEvent_t ev_sorted = nullptr;   // side stream: sorted cell list complete
   double dqdpsi = 0;
+  uint64_t key = 0;             // FNV-1a 64 of the inputs that determine A (matrix images)
   // SPME
   int K[3] = {0, 0, 0};
   int P = 5;

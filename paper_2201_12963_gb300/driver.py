@@ -10,7 +10,10 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from . import (Context, cpm_build_matrix, cpm_energy, cpm_forces, cpm_step, cpm_step_charges, make_params)
+import os
+
+from . import (CPMError, Context, cpm_build_matrix, cpm_build_matrix_from_image, cpm_energy, cpm_forces,
+               cpm_matrix_image, cpm_matrix_key, cpm_step, cpm_step_charges, make_params)
 
 
 def params_for(w, precision="fp64", grid=None, order=None, max_replicas=None, max_elyt=None, kmax_build=0.0,
@@ -35,15 +38,38 @@ def pack(w):
     return offsets, xyzq
 
 
+def build_context(params, w, cache_dir=None):
+    """cpm_build_matrix, or, with cache_dir, a context from the matrix image cached there under the
+    key of its inputs (written after a fresh build; an image the library refuses is rebuilt)."""
+    if cache_dir is None:
+        return cpm_build_matrix(params, w.elec_xyz, w.elec_side, w.elec_cell), False
+    key = cpm_matrix_key(params, w.elec_xyz, w.elec_side, w.elec_cell)
+    path = os.path.join(cache_dir, f"cpm-matrix-{key:016x}.img")
+    if os.path.exists(path):
+        try:
+            with open(path, "rb") as f:
+                image = np.frombuffer(f.read(), dtype=np.uint8)
+            return cpm_build_matrix_from_image(params, w.elec_xyz, w.elec_side, w.elec_cell, image), True
+        except CPMError:
+            pass
+    ctx = cpm_build_matrix(params, w.elec_xyz, w.elec_side, w.elec_cell)
+    os.makedirs(cache_dir, exist_ok=True)
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "wb") as f:
+        f.write(cpm_matrix_image(ctx).tobytes())
+    os.replace(tmp, path)
+    return ctx, False
+
+
 class System:
     def __init__(self, w, precision="fp64", grid=None, order=None, device="cuda", kmax_build=0.0,
-                 max_replicas=None, max_elyt=None, matrix_kspace="ewald", dc_blocks="auto"):
+                 max_replicas=None, max_elyt=None, matrix_kspace="ewald", dc_blocks="auto", cache_dir=None):
         self.w = w
         self.device = torch.device(device)
         self.params = params_for(w, precision, grid, order, max_replicas, max_elyt, kmax_build, matrix_kspace,
                                  dc_blocks)
         with torch.cuda.device(self.device):
-            self.ctx: Context = cpm_build_matrix(self.params, w.elec_xyz, w.elec_side, w.elec_cell)
+            self.ctx, self.from_cache = build_context(self.params, w, cache_dir)
         self.ne = self.ctx.n_elec
         self.load(w)
 
