@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--kernels", default="auto",
                     help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
                          "sym,library,sites, to run a fixed kernel choice (profiling captures)")
+    ap.add_argument("--pair-group", type=int, default=0,
+                    help="z cells per block of the real-space pair kernels (default: the autotuner's choice)")
     ap.add_argument("--charge-every", type=int, default=5,
                     help="MD workloads: re-solve the electrode charges every k steps (Appendix B: 5)")
     ap.add_argument("--workload", default="paper", choices=["paper", "paper-dc", "paper-slab", "paper-proximal", "large",
@@ -281,6 +283,8 @@ def build_system(args, w, dev):
         g.cpm_set_sapply_variant(s.ctx, variants[0])
         g.cpm_set_fft_variant(s.ctx, variants[1])
         g.cpm_set_mesh_variant(s.ctx, variants[2])
+    if args.pair_group > 0:
+        g.cpm_set_pair_group(s.ctx, args.pair_group)
     return s, build_s, variants
 
 
@@ -427,7 +431,7 @@ def run_gb300(args):
            "config": {"workload": WORKLOADS[args.workload][0], "geometry": GEOMETRY_NAME[args.workload],
                       "precision": args.precision, "build_s": round(build_s, 2),
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
-                      "charge_assignment": mesh_variant,
+                      "charge_assignment": mesh_variant, "pair_group_z": g.cpm_get_pair_group(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
@@ -561,7 +565,7 @@ def run_md(args):
                       "precision": args.precision, "build_s": round(build_s, 2), "charge_every": k,
                       "timestep_fs": synth.PAPER_TIMESTEP_FS, "thermostat": "Nose-Hoover 400 K, 100 fs",
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
-                      "charge_assignment": mesh_variant,
+                      "charge_assignment": mesh_variant, "pair_group_z": g.cpm_get_pair_group(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": f"flushed between replays of the {k}-step block (256 MiB write); CUDA-event time per block",

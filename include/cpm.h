@@ -355,11 +355,22 @@ enum cpm_mesh_variant { CPM_MESH_SITES = 0, CPM_MESH_BRICK = 1 };
 int cpm_set_mesh_variant(cpm_ctx* ctx, int32_t variant);
 
 /*
+ * cpm_set_pair_group / cpm_get_pair_group - z cells per block of the real-space pair kernels.  A
+ * block computes the targets of gz consecutive cells along z (contiguous in the cell-sorted list)
+ * against the sources of their joint stencil, so its setup, stencil scan and source staging serve
+ * gz times the targets for (gz + 2 s) / (1 + 2 s) times the sources (s the stencil half-width), at
+ * the price of more distance checks per target.  Default 1; cpm_autotune times 1, 2 and 4.
+ * CPM_ERR_ARG if gz is outside 1..8 or its stencil exceeds the kernel's tables.
+ */
+int cpm_set_pair_group(cpm_ctx* ctx, int32_t gz);
+int cpm_get_pair_group(const cpm_ctx* ctx, int32_t* gz);
+
+/*
  * cpm_autotune - time every available S-apply variant on the given single-replica input (five
  * calls each after a warm-up, each started with a cold L2 cache, CUDA events on
  * `stream`), keep the fastest (median) in the context; then, with that S-apply, the two mesh
- * convolutions (cpm_fft_variant), then the two charge assignments (cpm_mesh_variant), keeping the
- * faster each time.  Each timed call is a whole cpm_step (scratch force and energy outputs).
+ * convolutions (cpm_fft_variant), then the two charge assignments (cpm_mesh_variant), then the pair
+ * kernels' z groups of 1, 2 and 4 cells (cpm_set_pair_group), keeping the faster each time.  Each timed call is a whole cpm_step (scratch force and energy outputs).
  * choice_host[3] (may be NULL) receives the kept (cpm_sapply_variant, cpm_fft_variant,
  * cpm_mesh_variant).
  * Allocates and frees a scratch buffer of twice the L2 size and scratch outputs.  The arguments are those of

@@ -116,6 +116,7 @@ struct cpm_ctx {
   double* qpm = nullptr;        // [max_rep][2 nh] q+, q- before the projection
   // S-apply variant (enum cpm_sapply_variant) and the streaming variant's row partial sums
   // ([rows of S], float64, zero between calls: its finish kernel clears what it consumed)
+  int pair_gz = 1;               // real-space pair kernels: z cells per block (cpm_set_pair_group)
   int sapply_variant = 0;
   double* qpart = nullptr;
   // symmetric packed S (upper-triangle 128 x 128 tiles, float32) and its per-slot partial sums

@@ -27,6 +27,7 @@ struct CellGeom {
   int w[3];      // stencil widths 2 * sten + 1
   int sten[3];
   int nsten;
+  int gz, ngz;   // pair kernels: z cells per block (a contiguous run of the sorted list), z groups
   double edge[3];
   double inv_edge[3];
   double box[3];
@@ -287,15 +288,21 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   __shared__ int wq[PC_THREADS / 32][64];       // per-warp ring of staged sources within r_c
 
   const int rep = blockIdx.y;
-  const int cell = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // this block's targets: the cells (cx, cy, cz .. cz + gzb - 1), contiguous in the sorted list;
+  // coordinates are taken relative to the origin of cell (cx, cy, cz)
+  const int czg = blockIdx.x % g.ngz, cy = (blockIdx.x / g.ngz) % g.nc[1], cx = blockIdx.x / (g.ngz * g.nc[1]);
+  const int cz = czg * g.gz;
+  const int gzb = min(g.gz, g.nc[2] - cz);
+  const int cell = (cx * g.nc[1] + cy) * g.nc[2] + cz;
   const int* tst = t.start + rep * t.start_stride;
-  const int t0 = tst[cell], t1 = tst[cell + 1];
-  if (t1 <= t0) return;                                    // whole block: empty cell
+  const int t0 = tst[cell], t1 = tst[cell + gzb];
+  if (t1 <= t0) return;                                    // whole block: empty cells
+  const int wz = gzb + 2 * g.sten[2];                      // stencil extent in z for this group
+  const int nsten = g.w[0] * g.w[1] * wz;
   const T alpha = (T)alpha_d;
   const T c2pi = (T)1.1283791670955126;
   const T rc2 = (T)g.rc2;
-  const int cz = cell % g.nc[2], cy = (cell / g.nc[2]) % g.nc[1], cx = cell / (g.nc[2] * g.nc[1]);
   const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
   const V4* tl = (const V4*)t.loc + rep * t.loc_stride;
   const int* tso = t.sorted + rep * t.loc_stride;
@@ -320,6 +327,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
     for (int k = tid; k < nt; k += PC_THREADS) {
       V4 p = tl[tb + k];
       if (tq) p.w = tq[tso[tb + k]];
+      int j = 0;                                           // z cell of the target within the group
+      while (j + 1 < gzb && tb + k >= tst[cell + j + 1]) ++j;
+      p.z += (T)j * e2;
       tpos[k] = p;
       if (LJ) {
         const int ty = min(kLjMaxTypes - 1, max(0, lj.type[lj_o + tso[tb + k]]));
@@ -350,12 +360,13 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       const T beta = (T)s_beta;
       __syncthreads();
       // ---- stencil cells whose box can hold a source within r_c of some point of this cell
-      for (int si = tid; si < g.nsten; si += PC_THREADS) {
+      for (int si = tid; si < nsten; si += PC_THREADS) {
         const int dx = si % g.w[0] - g.sten[0];
         const int r1 = si / g.w[0];
         const int dy = r1 % g.w[1] - g.sten[1];
-        const int dz = r1 / g.w[1] - g.sten[2];
-        const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)max(0, abs(dz) - 1) * e2;
+        const int dz = r1 / g.w[1] - g.sten[2];            // -sten .. gzb - 1 + sten
+        const int gapz = dz < 0 ? -dz - 1 : max(0, dz - gzb);
+        const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)gapz * e2;
         int c = 0, f = 0;
         if (gx * gx + gy * gy + gz * gz < rc2) {
           const int flat = (wrap_index(cx + dx, g.nc[0]) * g.nc[1] + wrap_index(cy + dy, g.nc[1])) * g.nc[2] +
@@ -373,27 +384,27 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       // ---- inclusive scan of the counts (one warp, nsten <= PC_MAXSTEN)
       if (warp == 0) {
         int run = 0;
-        for (int b = 0; b < g.nsten; b += 32) {
+        for (int b = 0; b < nsten; b += 32) {
           const int k = b + lane;
-          int v = k < g.nsten ? st_pre[k + 1] : 0;
+          int v = k < nsten ? st_pre[k + 1] : 0;
 #pragma unroll
           for (int o = 1; o < 32; o <<= 1) {
             const int u = __shfl_up_sync(FULL, v, o);
             if (lane >= o) v += u;
           }
-          if (k < g.nsten) st_pre[k + 1] = run + v;
+          if (k < nsten) st_pre[k + 1] = run + v;
           run += __shfl_sync(FULL, v, 31);
         }
         if (lane == 0) st_pre[0] = 0;
       }
       __syncthreads();
-      const int total = st_pre[g.nsten];
+      const int total = st_pre[nsten];
       for (int c0 = 0; c0 < total; c0 += src_cap) {
         const int ns = min(src_cap, total - c0);
         // ---- stage: k -> stencil entry by binary search over the prefix sums
         for (int k = tid; k < ns; k += PC_THREADS) {
           const int j = c0 + k;
-          int lo = 0, hi = g.nsten;            // st_pre[lo] <= j < st_pre[hi]
+          int lo = 0, hi = nsten;              // st_pre[lo] <= j < st_pre[hi]
           while (hi - lo > 1) {
             const int mid = (lo + hi) >> 1;
             if (st_pre[mid] <= j) lo = mid; else hi = mid;
@@ -613,10 +624,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
 // handle axes x, y, z).  Its mesh coordinate u = (cell origin) + (local offset) K/L uses the
 // per-cell integer / fraction tables, so only the small local part is formed in precision T.
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, int cap, SpmeGeom sg,
-                                                     const typename Vec4<T>::type* __restrict__ l_tmp,
-                                                     const int* __restrict__ l_cell, const int* __restrict__ splI,
-                                                     const T* __restrict__ splF, T* __restrict__ mesh) {
+__device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, const int* __restrict__ off, int cap,
+                                                  const SpmeGeom sg,
+                                                  const typename Vec4<T>::type* __restrict__ l_tmp,
+                                                  const int* __restrict__ l_cell, const int* __restrict__ splI,
+                                                  const T* __restrict__ splF, T* __restrict__ mesh) {
   __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
   __shared__ int si0[8][3];
   const int rep = blockIdx.y;
@@ -624,8 +636,8 @@ __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   T* m = mesh + (size_t)rep * sg.Mr_s;
-  const int nw = (gridDim.x * blockDim.x) >> 5;
-  const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (nbx * blockDim.x) >> 5;
+  const int first = (bx * blockDim.x + threadIdx.x) >> 5;
   for (int i = first; i < n; i += nw) {
     const size_t k = (size_t)rep * cap + i;
     const auto p = l_tmp[k];
@@ -645,14 +657,15 @@ __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off
 
 // Electrode charges onto the mesh through the fixed stencils.
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_elec(const T* __restrict__ qT, int ne, const int4* __restrict__ base,
-                                                     const T* __restrict__ th, SpmeGeom sg, T* __restrict__ mesh) {
+__device__ __forceinline__ void spread_elec_sites(int bx, int nbx, const T* __restrict__ qT, int ne,
+                                                  const int4* __restrict__ base, const T* __restrict__ th,
+                                                  const SpmeGeom sg, T* __restrict__ mesh) {
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const T* qr = qT + (size_t)rep * ne;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
+  for (int i = (bx * blockDim.x + threadIdx.x) >> 5; i < ne; i += (nbx * blockDim.x) >> 5) {
     const T qi = qr[i];
     const int4 b = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
@@ -669,6 +682,35 @@ __global__ void __launch_bounds__(256) k_spread_elec(const T* __restrict__ qT, i
 }
 
 // rho^(m) *= G(m) on the half spectrum; optionally E_recip += 1/2 sum_m G |rho^(m)|^2 (full spectrum).
+// Electrolyte charges onto the mesh (warp per site, input order), electrode charges through their
+// fixed stencils, and both in one launch (blocks [0, nb_elyt) take the electrolyte).
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, int cap, SpmeGeom sg,
+                                                     const typename Vec4<T>::type* __restrict__ l_tmp,
+                                                     const int* __restrict__ l_cell, const int* __restrict__ splI,
+                                                     const T* __restrict__ splF, T* __restrict__ mesh) {
+  spread_elyt_sites<T>(blockIdx.x, gridDim.x, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_elec(const T* __restrict__ qT, int ne, const int4* __restrict__ base,
+                                                     const T* __restrict__ th, SpmeGeom sg, T* __restrict__ mesh) {
+  spread_elec_sites<T>(blockIdx.x, gridDim.x, qT, ne, base, th, sg, mesh);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_spread_all(int nb_elyt, const int* __restrict__ off, int cap, SpmeGeom sg,
+                                                    const typename Vec4<T>::type* __restrict__ l_tmp,
+                                                    const int* __restrict__ l_cell, const int* __restrict__ splI,
+                                                    const T* __restrict__ splF, const T* __restrict__ qT, int ne,
+                                                    const int4* __restrict__ base, const T* __restrict__ th,
+                                                    T* __restrict__ mesh) {
+  if ((int)blockIdx.x < nb_elyt)
+    spread_elyt_sites<T>(blockIdx.x, nb_elyt, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
+  else
+    spread_elec_sites<T>(blockIdx.x - nb_elyt, gridDim.x - nb_elyt, qT, ne, base, th, sg, mesh);
+}
+
 template <typename T, typename T2>
 __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const T* __restrict__ G, long long Mc,
                                                    long long Mc_s, int K3h, int K3, int energy_slot,
@@ -1269,33 +1311,62 @@ __global__ void __launch_bounds__(256) k_qraw_epilogue(const float* __restrict__
 
 // q = q_raw - A^-1 C M C^T q_raw (restores C^T q = 0 to float64 rounding); psibar = -M (A^-1 C)^T (b + dpsi v).
 // Also accumulates q^T b for the closed-form energy.
+// The force pass's view of the final charges, produced by the projection of the same call (the
+// work of k_charge_prep, without its own launch): q in the working precision and the float64
+// sums q z, q v, q^2, q_+.
+template <typename T> struct ChargePrep {
+  T* qT;                       // [nrep][ne]
+  const double* ez;
+  const double* ev;
+  const double* eplus;
+};
+
+template <typename T>
+__device__ __forceinline__ void prep_site(const ChargePrep<T>& cp, int rep, int ne, int i, double qi,
+                                          double (&acc)[5]) {
+  if (!cp.qT) return;                    // no force pass follows in this call
+  cp.qT[(size_t)rep * ne + i] = (T)qi;
+  acc[1] += qi * cp.ez[i];
+  acc[2] += qi * cp.ev[i];
+  acc[3] += qi * qi;
+  acc[4] += qi * cp.eplus[i];
+}
+
+template <typename T>
+__device__ __forceinline__ void project_sums(double (&acc)[5], double* s) {
+#pragma unroll
+  for (int k = 0; k < 5; ++k) acc[k] = warp_sum(acc[k]);
+  double* const dst[5] = {s + S_QB, s + S_QZ_ELEC, s + S_QV_ELEC, s + S_QQ_ELEC, s + S_QPLUS};
+  block_atomic_add<5>(acc, dst);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne, int nrep, int ncons,
                                                  const double* __restrict__ W, const double* __restrict__ b, int ldb,
                                                  double* __restrict__ scal, const double* __restrict__ dpsi,
                                                  double m00, double m01, double m10, double m11, double wtv0,
-                                                 double wtv1, double* __restrict__ psibar) {
+                                                 double wtv1, double* __restrict__ psibar, ChargePrep<T> cp) {
   const int rep = blockIdx.y;
   double* s = scal + rep * NSCAL;
   const double c0 = s[S_CQ0], cq1 = (ncons == 2) ? s[S_CQ1] : 0.0;
   const double a0 = m00 * c0 + m01 * cq1, a1 = m10 * c0 + m11 * cq1;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double qb[1] = {0.0};
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (i < ne) {
     double corr = W[2 * i] * a0;
     if (ncons == 2) corr += W[2 * i + 1] * a1;
     const size_t k = (size_t)rep * ne + i;
     const double qi = q[k] - corr;
     q[k] = qi;
-    qb[0] = qi * b[(size_t)rep * ldb + i];
+    acc[0] = qi * b[(size_t)rep * ldb + i];
+    prep_site(cp, rep, ne, i, qi, acc);
   }
   if (i == 0 && psibar) {
     const double y0 = s[S_WB0] + dpsi[rep] * wtv0, y1 = (ncons == 2) ? s[S_WB1] + dpsi[rep] * wtv1 : 0.0;
     psibar[rep * ncons + 0] = -(m00 * y0 + m01 * y1);
     if (ncons == 2) psibar[rep * ncons + 1] = -(m10 * y0 + m11 * y1);
   }
-  qb[0] = warp_sum(qb[0]);
-  double* const dst[1] = {s + S_QB};
-  block_atomic_add<1>(qb, dst);
+  project_sums<T>(acc, s);
 }
 
 // Mirror form, before the S-apply: y+- = b_I0 +- b_J per mirror pair (float64, rows of length
@@ -1327,35 +1398,36 @@ __global__ void __launch_bounds__(256) k_mirror_fold(const double* __restrict__ 
 // Offsets: with mu+- = -M+- w+-^T (y+- + dpsi v+-) (A+- q+- = y+- + dpsi v+- + mu+- 1), the full
 // problem's A q = b + dpsi v + psibar e + psibar_1 e_1 gives psibar = (mu+ + mu-) / 2, psibar_1 = -mu-.
 // Also accumulates q^T b for the closed-form energy.
+template <typename T>
 __global__ void __launch_bounds__(256) k_project_mirror(const double* __restrict__ qpm, int nh,
                                                         const int* __restrict__ i0, const int* __restrict__ jm,
                                                         const double* __restrict__ W, const double* __restrict__ b,
                                                         int ldb, int ne, double* __restrict__ scal,
                                                         const double* __restrict__ dpsi, double mp, double mm,
                                                         double wtvp, double wtvm, double* __restrict__ q,
-                                                        double* __restrict__ psibar) {
+                                                        double* __restrict__ psibar, ChargePrep<T> cp) {
   const int rep = blockIdx.y;
   double* s = scal + rep * NSCAL;
-  const double cp = s[S_CQ0] - s[S_CQ1], cm = s[S_CQ1];
+  const double cpl = s[S_CQ0] - s[S_CQ1], cm = s[S_CQ1];
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  double qb[1] = {0.0};
+  double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (k < nh) {
-    const double qp = qpm[(size_t)rep * 2 * nh + k] - W[2 * k] * mp * cp;
+    const double qp = qpm[(size_t)rep * 2 * nh + k] - W[2 * k] * mp * cpl;
     const double qm = qpm[(size_t)rep * 2 * nh + nh + k] - W[2 * (size_t)nh + 2 * k + 1] * mm * cm;
     const int i = i0[k], j = jm[k];
     const double qi = 0.5 * (qp + qm), qj = 0.5 * (qp - qm);
     q[(size_t)rep * ne + i] = qi;
     q[(size_t)rep * ne + j] = qj;
-    qb[0] = qi * b[(size_t)rep * ldb + i] + qj * b[(size_t)rep * ldb + j];
+    acc[0] = qi * b[(size_t)rep * ldb + i] + qj * b[(size_t)rep * ldb + j];
+    prep_site(cp, rep, ne, i, qi, acc);
+    prep_site(cp, rep, ne, j, qj, acc);
   }
   if (k == 0 && psibar) {
     const double mup = -mp * (s[S_WB0] + dpsi[rep] * wtvp), mum = -mm * (s[S_WB1] + dpsi[rep] * wtvm);
     psibar[rep * 2 + 0] = 0.5 * (mup + mum);
     psibar[rep * 2 + 1] = -mum;
   }
-  qb[0] = warp_sum(qb[0]);
-  double* const dst[1] = {s + S_QB};
-  block_atomic_add<1>(qb, dst);
+  project_sums<T>(acc, s);
 }
 
 // Per replica (U, H, dH/d(dpsi), Q_+).  closed_form: at the constrained optimum Eq. 3 reduces to
@@ -1402,8 +1474,13 @@ static CellGeom cell_geom(const cpm_ctx* c) {
     g.inv_box[d] = 1.0 / c->ebox[d];
   }
   g.rc2 = c->p.rcut * c->p.rcut;
+  g.gz = c->pair_gz;
+  g.ngz = (g.nc[2] + g.gz - 1) / g.gz;
   return g;
 }
+
+// Blocks of a pair-kernel launch per replica: one per (x, y) column and group of gz cells in z.
+static int pair_blocks(const CellGeom& g) { return g.nc[0] * g.nc[1] * g.ngz; }
 
 static SpmeGeom spme_geom(const cpm_ctx* c) {
   SpmeGeom s;
@@ -1609,7 +1686,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     s.beta = c->p.eta;
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sside>>>(tg, s, none, g, c->p.alpha,
+      k_pair_cell<T, false><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sside>>>(tg, s, none, g, c->p.alpha,
                                                                                   kPairSrcCap, c->scal, PairLj{});
       STEP_LAUNCH();
     }
@@ -1727,21 +1804,25 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       }
     }
     PhaseTimer ptp(c, st, CPM_PH_PROJECT);
+    // when the force pass follows, the projection also leaves the charges in its working precision
+    // and their sums (the work of k_charge_prep)
+    const bool forces_follow = f_elyt || f_elec || energy;
+    const ChargePrep<T> cprep{forces_follow ? qT : nullptr, c->e_z, c->e_v, c->e_plus};
     if (c->mirror) {
-      k_project_mirror<<<dim3((c->nh + 255) / 256, nrep), 256, 0, st>>>(c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
+      k_project_mirror<T><<<dim3((c->nh + 255) / 256, nrep), 256, 0, st>>>(c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
                                                                         ldb, ne, c->scal, dpsi, c->Mh[0], c->Mh[1],
-                                                                        c->WTv[0], c->WTv[1], q, psibar);
+                                                                        c->WTv[0], c->WTv[1], q, psibar, cprep);
     } else {
-      k_project<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
+      k_project<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
                                                               c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
-                                                              c->WTv[1], psibar);
+                                                              c->WTv[1], psibar, cprep);
     }
     STEP_LAUNCH();
   }
 
   if (f_elyt || f_elec || energy) {
     cudaStream_t sp = sside;
-    {
+    if (!charges) {                      // charges given by the caller (cpm_forces, cpm_energy)
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
       k_charge_prep<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal);
       STEP_LAUNCH();
@@ -1775,13 +1856,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
           lj.sqrt_eps[k] = c->lj->sqrt_eps[k];
         }
         const size_t smem_lj = (sizeof(V4) + sizeof(typename Vec2<T>::type)) * kPairSrcCap;
-        k_pair_cell<T, true, true><<<dim3(c->ncell, nrep), PC_THREADS, smem_lj, sp>>>(tg, a, e, g, c->p.alpha,
+        k_pair_cell<T, true, true><<<dim3(pair_blocks(g), nrep), PC_THREADS, smem_lj, sp>>>(tg, a, e, g, c->p.alpha,
                                                                                       kPairSrcCap, c->scal, lj);
       } else if (f_elyt) {
-        k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
+        k_pair_cell<T, true><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
                                                                                 kPairSrcCap, c->scal, PairLj{});
       } else {
-        k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
+        k_pair_cell<T, false><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
                                                                                  kPairSrcCap, c->scal, PairLj{});
       }
       STEP_LAUNCH();
@@ -1795,10 +1876,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         CPM_TRY(cpm_internal_spread_brick(c, nrep, l_loc, (const float*)qT, st));
       } else {
         CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-        k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                    (T*)c->mesh_r);
-        STEP_LAUNCH();
-        k_spread_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>(qT, ne, c->e_base, e_th, sg, (T*)c->mesh_r);
+        const int nb_l = grid_for(cap), nb_e = grid_for(ne);
+        k_spread_all<T><<<dim3(nb_l + nb_e, nrep), 256, 0, st>>>(nb_l, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
+                                                                 qT, ne, c->e_base, e_th, (T*)c->mesh_r);
         STEP_LAUNCH();
       }
     }
@@ -1834,10 +1914,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       e.beta = c->p.eta / std::sqrt(2.0);
       e.slot = (energy && !closed_form) ? S_E_EE : -1;
       if (f_elec)
-        k_pair_cell<T, true><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
+        k_pair_cell<T, true><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
                                                                                 kPairSrcCap, c->scal, PairLj{});
       else
-        k_pair_cell<T, false><<<dim3(c->ncell, nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
+        k_pair_cell<T, false><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
                                                                                  kPairSrcCap, c->scal, PairLj{});
       STEP_LAUNCH();
     }
@@ -1915,10 +1995,18 @@ static bool stream_available(const cpm_ctx* c) {
 
 cpm::SpmeGeom cpm_internal_spme_geom(const cpm_ctx* c) { return cpm::spme_geom(c); }
 
+// A z group of gz cells per pair-kernel block is possible while its stencil fits the kernel's tables.
+static bool pair_group_ok(const cpm_ctx* c, int gz) {
+  return gz >= 1 && gz <= 8 && (2 * c->sten[0] + 1) * (2 * c->sten[1] + 1) * (gz + 2 * c->sten[2]) <= cpm::kMaxStencil;
+}
+
 int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_TRY(pair_cell_attributes());
   CPM_TRY(tc_attributes());
   CPM_CUDA(cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->dev));
+  // one cell per pair-kernel block unless the autotuner finds a z group faster: the per-source
+  // distance checks, not the staging the groups share, dominate the kernel (measured on GB300)
+  c->pair_gz = 1;
   CPM_TRY(cpm_internal_fft_setup(c));
   CPM_TRY(cpm_internal_brick_setup(c));
   CPM_TRY(cpm_internal_sym_setup(c));
@@ -2013,6 +2101,21 @@ extern "C" int cpm_set_sapply_variant(cpm_ctx* c, int32_t variant) {
   return CPM_ERR_ARG;
 }
 
+extern "C" int cpm_set_pair_group(cpm_ctx* c, int32_t gz) {
+  if (!c || !pair_group_ok(c, gz)) {
+    cpm::set_error("cpm_set_pair_group: %d z cells per block is outside 1..8 or exceeds the stencil tables", gz);
+    return CPM_ERR_ARG;
+  }
+  c->pair_gz = gz;
+  return CPM_OK;
+}
+
+extern "C" int cpm_get_pair_group(const cpm_ctx* c, int32_t* gz) {
+  if (!c || !gz) return CPM_ERR_ARG;
+  *gz = c->pair_gz;
+  return CPM_OK;
+}
+
 extern "C" int cpm_set_fft_variant(cpm_ctx* c, int32_t variant) {
   if (!c) return CPM_ERR_ARG;
   if (variant == CPM_FFT_LIBRARY || (variant == CPM_FFT_OWN && c->fft_own_ok)) {
@@ -2037,7 +2140,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
                             void* stream, int32_t* choice_host) {
   if (!c || !off || !xyzq || !dpsi || !q) return CPM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int keep_s = c->sapply_variant, keep_f = c->fft_variant, keep_m = c->mesh_variant;
+  const int keep_s = c->sapply_variant, keep_f = c->fft_variant, keep_m = c->mesh_variant, keep_g = c->pair_gz;
   // every timed call starts from a cold L2 (a write of twice its capacity), as inside an MD step
   // whose other work evicts S
   int l2 = 0;
@@ -2092,6 +2195,17 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
     best_ms = t;
     best_m = CPM_MESH_BRICK;
   }
+  // then the z group of the real-space pair kernels
+  int best_g = keep_g;
+  for (int gz : {1, 2, 4}) {
+    if (rc != CPM_OK || gz == keep_g || !pair_group_ok(c, gz)) continue;
+    c->pair_gz = gz;
+    if (time_config(best_s, best_f, best_m, &t) && t < best_ms) {
+      best_ms = t;
+      best_g = gz;
+    }
+  }
+  c->pair_gz = (rc == CPM_OK) ? best_g : keep_g;
   cudaFree(f_scr);
   cudaFree(e_scr);
   cudaEventDestroy(e0);

@@ -156,3 +156,45 @@ def test_brick_charge_assignment_needs_mixed_precision(plain_ff):
     s = System(plain_ff[0], "fp64")
     with pytest.raises(g.CPMError):
         g.cpm_set_mesh_variant(s.ctx, "brick")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("case", ["ff", "dc", "slab"])
+def test_pair_kernel_z_groups_match_single_cells_and_oracle(plain_ff, case, prec):
+    """Blocks of 1, 2, 4 and 3 cells along z (3 leaves a shorter last group) give the same b,
+    charges, forces on both site kinds and energies: only the order of the sums changes."""
+    g, System = _lib()
+    if case == "ff":
+        w, out = plain_ff[0], plain_ff[2]
+    elif case == "dc":
+        w, out = _cases(plain_ff)["dc"][0], None
+    else:
+        w = synth.tiny_cell(seed=9, n_pairs=4, geometry="slab")
+        w.grid = (18, 16, 216)
+        out = None
+    if out is None:
+        out = ocpm.Reference(w).step()
+    s = System(w, prec, order=8)
+    res = {}
+    for gz in (1, 2, 3, 4):
+        g.cpm_set_pair_group(s.ctx, gz)
+        assert g.cpm_get_pair_group(s.ctx) == gz
+        s.step(elec=True, energy=True)
+        s.energies()
+        r = s.results()
+        assert g.cpm_status(s.ctx) == 0
+        res[gz] = r
+        assert np.max(np.abs(r["q"][0] - out["q"])) <= 1e-5
+        F, Fo = r["F_elyt"][0], out["F_elyt"]
+        assert np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum()) <= 1e-5
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    for gz in (2, 3, 4):
+        a, b = res[gz], res[1]
+        assert np.max(np.abs(a["b"] - b["b"])) <= tol * np.max(np.abs(b["b"]))
+        assert np.max(np.abs(a["q"] - b["q"])) <= tol
+        for key in ("F_elyt", "F_elec"):
+            x, y = np.asarray(a[key]).reshape(-1, 3), np.asarray(b[key]).reshape(-1, 3)
+            assert np.sqrt(((x - y) ** 2).sum() / (y ** 2).sum()) <= tol
+        assert np.max(np.abs(a["energy"] - b["energy"])) <= tol * np.max(np.abs(b["energy"]))
+    with pytest.raises(g.CPMError):
+        g.cpm_set_pair_group(s.ctx, 0)
