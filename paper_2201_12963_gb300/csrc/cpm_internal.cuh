@@ -298,6 +298,33 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
 
 __device__ __forceinline__ void latch_error(int* status, int bit) { atomicOr(status, bit); }
 
+// Programmatic dependent launch: kernels of the per-step chains are launched with the
+// programmatic-serialization attribute (launch_pdl), so the next kernel is scheduled while the
+// previous one drains; each such kernel first waits (griddepcontrol.wait) until its predecessor
+// grid has completed and its memory is visible, then lets its own successor be scheduled.  With
+// the wait first, the order of memory effects is that of plain stream order.  Without a
+// programmatic predecessor both instructions return at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Running sums in the working precision: float32 with a compensation term (TwoSum), float64 plain.
 template <typename T> struct Acc;
 

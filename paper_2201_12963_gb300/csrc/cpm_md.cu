@@ -45,6 +45,7 @@ __global__ void __launch_bounds__(256) k_md_kick_drift(int n, double* __restrict
                                                        const double* __restrict__ F, const int* __restrict__ type,
                                                        const int* __restrict__ slot, const double* __restrict__ s,
                                                        const double* __restrict__ mt, double dt, double bx, double by) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double h = mt[type[j]];
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(256) k_md_kick_drift(int n, double* __restrict
 __global__ void __launch_bounds__(256) k_md_kick_ke(int n, double* __restrict__ vel, const double* __restrict__ F,
                                                     const int* __restrict__ type, const int* __restrict__ slot,
                                                     const double* __restrict__ mt, int kick, double* __restrict__ ke) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const bool valid = j < n;
@@ -109,6 +111,7 @@ constexpr int NH_LEAD = 1, NH_TRAIL = 2;
 __global__ void k_md_nh(int nslots, int mode, const double* __restrict__ ke, double* __restrict__ thermo,
                         const double* __restrict__ ndof, const double* __restrict__ Qm, double kT, double dt,
                         double* __restrict__ s_out, double* __restrict__ kcur) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nslots) return;
   double K = ke[i];
@@ -134,6 +137,7 @@ __global__ void k_md_nh(int nslots, int mode, const double* __restrict__ ke, dou
 
 __global__ void __launch_bounds__(256) k_md_scale(int n, double* __restrict__ vel, const int* __restrict__ slot,
                                                   const double* __restrict__ s) {
+  pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
   const double sc = s[slot[j]];
@@ -148,6 +152,7 @@ __global__ void k_md_energy(int nrep, int ngroups, const double* __restrict__ e_
                             const double* __restrict__ K, const double* __restrict__ thermo,
                             const double* __restrict__ ndof, const double* __restrict__ Qm, double kT, int thermostat,
                             double* __restrict__ out) {
+  pdl_enter();
   const int rep = blockIdx.x * blockDim.x + threadIdx.x;
   if (rep >= nrep) return;
   double ke = 0.0, enh = 0.0, g = 0.0;
@@ -395,35 +400,35 @@ extern "C" int cpm_md_run(cpm_md* m, int32_t n_steps, double* xyzq, double* vel,
   const size_t kbytes = sizeof(double) * m->nslots;
   const int nhb = (m->nslots + 127) / 128;
   CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
-  k_md_kick_ke<<<nb, 256, 0, st>>>(n, vel, m->F, m->type, m->slot, m->mt, 0, m->ke);
+  CPM_CUDA(launch_pdl(k_md_kick_ke, nb, 256, 0, st, n, vel, m->F, m->type, m->slot, m->mt, 0, m->ke));
   MD_LAUNCH(c);
   if (thermostat && n_steps > 0) {
-    k_md_nh<<<nhb, 128, 0, st>>>(m->nslots, NH_LEAD, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur);
+    CPM_CUDA(launch_pdl(k_md_nh, nhb, 128, 0, st, m->nslots, NH_LEAD, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur));
     MD_LAUNCH(c);
   }
   for (int i = 0; i < n_steps; ++i) {
-    k_md_kick_drift<<<nb, 256, 0, st>>>(n, xyzq, vel, m->F, m->type, m->slot, thermostat ? m->s : nullptr, m->mt,
-                                        dt, c->p.box[0], c->p.box[1]);
+    CPM_CUDA(launch_pdl(k_md_kick_drift, nb, 256, 0, st, n, xyzq, vel, m->F, m->type, m->slot, thermostat ? m->s : nullptr, m->mt,
+                                        dt, c->p.box[0], c->p.box[1]));
     MD_LAUNCH(c);
     ++m->step;
     CPM_TRY(force_eval(want_energy && i == n_steps - 1));
     CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
-    k_md_kick_ke<<<nb, 256, 0, st>>>(n, vel, m->F, m->type, m->slot, m->mt, 1, m->ke);
+    CPM_CUDA(launch_pdl(k_md_kick_ke, nb, 256, 0, st, n, vel, m->F, m->type, m->slot, m->mt, 1, m->ke));
     MD_LAUNCH(c);
     if (thermostat) {
       const int mode = i == n_steps - 1 ? NH_TRAIL : (NH_TRAIL | NH_LEAD);
-      k_md_nh<<<nhb, 128, 0, st>>>(m->nslots, mode, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur);
+      CPM_CUDA(launch_pdl(k_md_nh, nhb, 128, 0, st, m->nslots, mode, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur));
       MD_LAUNCH(c);
     }
   }
   if (thermostat && n_steps > 0) {
-    k_md_scale<<<nb, 256, 0, st>>>(n, vel, m->slot, m->s);
+    CPM_CUDA(launch_pdl(k_md_scale, nb, 256, 0, st, n, vel, m->slot, m->s));
     MD_LAUNCH(c);
   }
   if (want_energy) {
-    k_md_energy<<<(m->nrep + 127) / 128, 128, 0, st>>>(m->nrep, m->ngroups, m->e_coul, c->scal,
+    CPM_CUDA(launch_pdl(k_md_energy, (m->nrep + 127) / 128, 128, 0, st, m->nrep, m->ngroups, m->e_coul, c->scal,
                                                         (thermostat && n_steps > 0) ? m->kcur : m->ke, m->thermo,
-                                                        m->ndof, m->Qm, kT, thermostat ? 1 : 0, energy);
+                                                        m->ndof, m->Qm, kT, thermostat ? 1 : 0, energy));
     MD_LAUNCH(c);
   }
   if (force) CPM_CUDA(cudaMemcpyAsync(force, m->F, sizeof(double) * 3 * (size_t)n, cudaMemcpyDeviceToDevice, st));

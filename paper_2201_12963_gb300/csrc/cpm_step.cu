@@ -54,6 +54,7 @@ __global__ void __launch_bounds__(256) k_bin(const int* __restrict__ off, const 
                                              CellGeom g, double lz_phys, int* __restrict__ l_cell,
                                              int* __restrict__ l_count, typename Vec4<T>::type* __restrict__ l_tmp,
                                              int ncell, double* __restrict__ scal, int* __restrict__ status) {
+  pdl_enter();
   using V4 = typename Vec4<T>::type;
   const int rep = blockIdx.y;
   const int o = off[rep];
@@ -96,6 +97,7 @@ __global__ void __launch_bounds__(256) k_bin(const int* __restrict__ off, const 
 
 // exclusive scan of the per-cell counts (one block per replica); counts become scatter cursors
 __global__ void k_scan(int* __restrict__ l_count, int* __restrict__ l_start, int ncell) {
+  pdl_enter();
   const int rep = blockIdx.x;
   int* cnt = l_count + (size_t)rep * ncell;
   int* st = l_start + (size_t)rep * (ncell + 1);
@@ -129,6 +131,7 @@ __global__ void __launch_bounds__(256) k_scatter(const int* __restrict__ off, in
                                                  const typename Vec4<T>::type* __restrict__ l_tmp,
                                                  int* __restrict__ cursor, int ncell, int* __restrict__ l_sorted,
                                                  typename Vec4<T>::type* __restrict__ l_loc) {
+  pdl_enter();
   const int rep = blockIdx.y;
   const int n = min(off[rep + 1] - off[rep], cap);
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -147,6 +150,7 @@ __global__ void __launch_bounds__(256) k_charge_prep(const double* __restrict__ 
                                                      const double* __restrict__ ez, const double* __restrict__ ev,
                                                      const double* __restrict__ eplus, T* __restrict__ qT,
                                                      double* __restrict__ scal) {
+  pdl_enter();
   const int rep = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[4] = {0, 0, 0, 0};
@@ -268,6 +272,7 @@ template <typename T, bool FORCE, bool LJ = false>
 __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
                                                           const CellGeom g, const double alpha_d, int src_cap,
                                                           double* __restrict__ scal, const PairLj lj) {
+  pdl_enter();
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   static_assert(!LJ || FORCE, "the Lennard-Jones pass computes forces");
@@ -689,6 +694,7 @@ __global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off
                                                      const typename Vec4<T>::type* __restrict__ l_tmp,
                                                      const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                      const T* __restrict__ splF, T* __restrict__ mesh) {
+  pdl_enter();
   spread_elyt_sites<T>(blockIdx.x, gridDim.x, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
 }
 
@@ -705,6 +711,7 @@ __global__ void __launch_bounds__(256) k_spread_all(int nb_elyt, const int* __re
                                                     const T* __restrict__ splF, const T* __restrict__ qT, int ne,
                                                     const int4* __restrict__ base, const T* __restrict__ th,
                                                     T* __restrict__ mesh) {
+  pdl_enter();
   if ((int)blockIdx.x < nb_elyt)
     spread_elyt_sites<T>(blockIdx.x, nb_elyt, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
   else
@@ -715,6 +722,7 @@ template <typename T, typename T2>
 __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const T* __restrict__ G, long long Mc,
                                                    long long Mc_s, int K3h, int K3, int energy_slot,
                                                    double* __restrict__ scal) {
+  pdl_enter();
   const bool energy = energy_slot >= 0;
   const int rep = blockIdx.y;
   T2* c = spec + (size_t)rep * Mc_s;
@@ -749,6 +757,7 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
                                                   double slab_coef, const double* __restrict__ scal,
                                                   double* __restrict__ b, float* __restrict__ b32, int ldx,
                                                   int ldb) {
+  pdl_enter();
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
@@ -792,6 +801,7 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
                                                        double ff_over_lz, double slab_coef,
                                                        const double* __restrict__ scal,
                                                        const double* __restrict__ f_pair, double* __restrict__ F) {
+  pdl_enter();
   __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
   __shared__ int si0[8][3];
   const int rep = blockIdx.y;
@@ -847,6 +857,7 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
                                                        SpmeGeom sg, const double* __restrict__ dpsi,
                                                        double ff_over_lz, double slab_coef,
                                                        const double* __restrict__ scal, double* __restrict__ F) {
+  pdl_enter();
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
@@ -940,6 +951,7 @@ __global__ void __launch_bounds__(256) k_sapply32(const float* __restrict__ S, i
                                                   const double* __restrict__ dpsi, const double* __restrict__ Sv,
                                                   const double* __restrict__ W, const double* __restrict__ c1,
                                                   double* __restrict__ qout, int qstride, double* __restrict__ scal) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   const int n4 = ld >> 2;
   double red[4 * R];
@@ -996,6 +1008,7 @@ __global__ void __launch_bounds__(256) k_sapply64(const double* __restrict__ S, 
                                                   const double* __restrict__ dpsi, const double* __restrict__ Sv,
                                                   const double* __restrict__ W, const double* __restrict__ c1,
                                                   double* __restrict__ qout, int qstride, double* __restrict__ scal) {
+  pdl_enter();
   const int lane = threadIdx.x & 31;
   double red[4 * R];
 #pragma unroll
@@ -1042,6 +1055,7 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_sapply_stream(const float* __
                                                                  const float* __restrict__ xh,
                                                                  const float* __restrict__ xl,
                                                                  double* __restrict__ qpart) {
+  pdl_enter();
   extern __shared__ float4 ss_x[];
   const int n4 = ld >> 2;
   float4* shi = ss_x;
@@ -1098,6 +1112,7 @@ __global__ void __launch_bounds__(256) k_sapply_finish(int rows, double* __restr
                                                        const double* __restrict__ Sv, const double* __restrict__ W,
                                                        const double* __restrict__ c1, double* __restrict__ qout,
                                                        double* __restrict__ scal) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double red[4] = {0, 0, 0, 0};
   if (i < rows) {
@@ -1290,6 +1305,7 @@ __global__ void __launch_bounds__(256) k_qraw_epilogue(const float* __restrict__
                                                        const double* __restrict__ Sv, const double* __restrict__ W,
                                                        const double* __restrict__ c1, double* __restrict__ q,
                                                        double* __restrict__ scal) {
+  pdl_enter();
   const int rep = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double red[4] = {0, 0, 0, 0};
@@ -1346,6 +1362,7 @@ __global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne,
                                                  double* __restrict__ scal, const double* __restrict__ dpsi,
                                                  double m00, double m01, double m10, double m11, double wtv0,
                                                  double wtv1, double* __restrict__ psibar, ChargePrep<T> cp) {
+  pdl_enter();
   const int rep = blockIdx.y;
   double* s = scal + rep * NSCAL;
   const double c0 = s[S_CQ0], cq1 = (ncons == 2) ? s[S_CQ1] : 0.0;
@@ -1375,6 +1392,7 @@ __global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne,
 __global__ void __launch_bounds__(256) k_mirror_fold(const double* __restrict__ b, int ldb, int nh, int ldh,
                                                      const int* __restrict__ i0, const int* __restrict__ jm,
                                                      double* __restrict__ y, float* __restrict__ x32) {
+  pdl_enter();
   const int rep = blockIdx.y;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= nh) return;
@@ -1406,6 +1424,7 @@ __global__ void __launch_bounds__(256) k_project_mirror(const double* __restrict
                                                         const double* __restrict__ dpsi, double mp, double mm,
                                                         double wtvp, double wtvm, double* __restrict__ q,
                                                         double* __restrict__ psibar, ChargePrep<T> cp) {
+  pdl_enter();
   const int rep = blockIdx.y;
   double* s = scal + rep * NSCAL;
   const double cpl = s[S_CQ0] - s[S_CQ1], cm = s[S_CQ1];
@@ -1436,6 +1455,7 @@ __global__ void __launch_bounds__(256) k_project_mirror(const double* __restrict
 __global__ void k_energy_final(int nrep, const double* __restrict__ scal, const double* __restrict__ dpsi,
                                double alpha, double eta, double slab_e_coef, double ff_over_lz, int closed_form,
                                double* __restrict__ energy) {
+  pdl_enter();
   const int rep = blockIdx.x * blockDim.x + threadIdx.x;
   if (rep >= nrep) return;
   const double* s = scal + rep * NSCAL;
@@ -1563,8 +1583,8 @@ static int convolve(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st) {
     CPM_LIB(FftOps<T>::fwd(c->plan_r2c[b], mr + r * c->Mr_s, mc + r * c->Mc_s) == CUFFT_SUCCESS, "cufftExec(r2c)");
   const T* G = c->mixed ? (const T*)c->G32 : (const T*)c->G64;
   const int blocks = (int)std::min<long long>((c->Mc + 255) / 256, 152 * 8);
-  k_influence<T, C2><<<dim3(blocks, nrep), 256, 0, st>>>(mc, G, c->Mc, c->Mc_s, c->K[2] / 2 + 1, c->K[2],
-                                                         energy_slot, c->scal);
+  CPM_CUDA(launch_pdl(k_influence<T, C2>, dim3(blocks, nrep), 256, 0, st, mc, G, c->Mc, c->Mc_s, c->K[2] / 2 + 1, c->K[2],
+                                                         energy_slot, c->scal));
   STEP_LAUNCH();
   for (int r = 0; r < nexec; ++r)
     CPM_LIB(FftOps<T>::inv(c->plan_c2r[b], mc + r * c->Mc_s, mp + r * c->Mr_s) == CUFFT_SUCCESS, "cufftExec(c2r)");
@@ -1610,11 +1630,11 @@ static int sapply_stream(cpm_ctx* c, const float* S, int rows, int ld, const flo
                          const double* c1, double* qout, cudaStream_t st) {
   const size_t smem = sizeof(float) * 2 * (size_t)ld;
   if (c->sapply_variant == CPM_SAPPLY_STREAM16)
-    k_sapply_stream<16><<<c->n_sm, SS_THREADS, smem, st>>>(S, ld, rows, xh, xl, qpart);
+    CPM_CUDA(launch_pdl(k_sapply_stream<16>, c->n_sm, SS_THREADS, smem, st, S, ld, rows, xh, xl, qpart));
   else
-    k_sapply_stream<8><<<c->n_sm, SS_THREADS, smem, st>>>(S, ld, rows, xh, xl, qpart);
+    CPM_CUDA(launch_pdl(k_sapply_stream<8>, c->n_sm, SS_THREADS, smem, st, S, ld, rows, xh, xl, qpart));
   STEP_LAUNCH();
-  k_sapply_finish<<<(rows + 255) / 256, 256, 0, st>>>(rows, qpart, b, dpsi, Sv, W, c1, qout, c->scal);
+  CPM_CUDA(launch_pdl(k_sapply_finish, (rows + 255) / 256, 256, 0, st, rows, qpart, b, dpsi, Sv, W, c1, qout, c->scal));
   STEP_LAUNCH();
   return CPM_OK;
 }
@@ -1648,8 +1668,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     PhaseTimer pt(c, st, CPM_PH_CELL_LIST);
     CPM_CUDA(cudaMemsetAsync(c->scal, 0, sizeof(double) * NSCAL * nrep, st));
     CPM_CUDA(cudaMemsetAsync(c->l_count, 0, sizeof(int) * (size_t)c->ncell * nrep, st));
-    k_bin<T><<<gsite, 256, 0, st>>>(off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, l_tmp, c->ncell, c->scal,
-                                    c->status);
+    CPM_CUDA(launch_pdl(k_bin<T>, gsite, 256, 0, st, off, xyzq, cap, g, c->Lz, c->l_cell, c->l_count, l_tmp, c->ncell, c->scal,
+                                    c->status));
     STEP_LAUNCH();
     // The sorted cell list serves only the real-space pair kernels, which run on the side stream:
     // fork here, so the counting sort overlaps the mesh work on the main stream (which reads k_bin's
@@ -1658,9 +1678,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       CPM_CUDA(cudaEventRecord(c->ev_fork, st));
       CPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
     }
-    k_scan<<<nrep, 1024, 0, sside>>>(c->l_count, c->l_start, c->ncell);
+    CPM_CUDA(launch_pdl(k_scan, nrep, 1024, 0, sside, c->l_count, c->l_start, c->ncell));
     STEP_LAUNCH();
-    k_scatter<T><<<gsite, 256, 0, sside>>>(off, cap, c->l_cell, l_tmp, c->l_count, c->ncell, c->l_sorted, l_loc);
+    CPM_CUDA(launch_pdl(k_scatter<T>, gsite, 256, 0, sside, off, cap, c->l_cell, l_tmp, c->l_count, c->ncell, c->l_sorted, l_loc));
     STEP_LAUNCH();
     if (fork) {
       CPM_CUDA(cudaEventRecord(c->ev_sorted, c->side));
@@ -1686,8 +1706,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     s.beta = c->p.eta;
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      k_pair_cell<T, false><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sside>>>(tg, s, none, g, c->p.alpha,
-                                                                                  kPairSrcCap, c->scal, PairLj{});
+      CPM_CUDA(launch_pdl(k_pair_cell<T, false>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sside, tg, s, none, g, c->p.alpha,
+                                                                                  kPairSrcCap, c->scal, PairLj{}));
       STEP_LAUNCH();
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
@@ -1699,8 +1719,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         CPM_TRY(cpm_internal_spread_brick(c, nrep, l_loc, nullptr, st));
       } else {
         CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-        k_spread_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>(off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                    (T*)c->mesh_r);
+        CPM_CUDA(launch_pdl(k_spread_elyt<T>, dim3(grid_for(cap), nrep), 256, 0, st, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
+                                                                    (T*)c->mesh_r));
         STEP_LAUNCH();
       }
     }
@@ -1711,10 +1731,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     {
       PhaseTimer pt(c, st, CPM_PH_B_GATHER);
-      k_gather_b<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
+      CPM_CUDA(launch_pdl(k_gather_b<T>, dim3(grid_for(ne), nrep), 256, 0, st, (const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
                                                               c->phi_real, c->e_z, slab_coef, c->scal, b,
                                                               (c->mixed && !c->mirror) ? c->b32 : nullptr,
-                                                              c->ldx, ldb);
+                                                              c->ldx, ldb));
       STEP_LAUNCH();
       if (b_out) {
         CPM_CUDA(cudaMemcpy2DAsync(b_out, sizeof(double) * ne, b, sizeof(double) * ldb, sizeof(double) * ne, nrep,
@@ -1732,24 +1752,24 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         const int left = nrep - r0;
         if (c->mixed) {
           if (left == 1)
-            k_sapply32<1><<<sblocks, 256, 0, st>>>(S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
-                                                   W, c1, qout, qstride, c->scal);
+            CPM_CUDA(launch_pdl(k_sapply32<1>, sblocks, 256, 0, st, S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
+                                                   W, c1, qout, qstride, c->scal));
           else if (left == 2)
-            k_sapply32<2><<<sblocks, 256, 0, st>>>(S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
-                                                   W, c1, qout, qstride, c->scal);
+            CPM_CUDA(launch_pdl(k_sapply32<2>, sblocks, 256, 0, st, S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
+                                                   W, c1, qout, qstride, c->scal));
           else
-            k_sapply32<4><<<sblocks, 256, 0, st>>>(S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
-                                                   W, c1, qout, qstride, c->scal);
+            CPM_CUDA(launch_pdl(k_sapply32<4>, sblocks, 256, 0, st, S32, ld, rows, x32, xstride, xlo, y64, ldy, r0, nrep, dpsi, Sv,
+                                                   W, c1, qout, qstride, c->scal));
         } else {
           if (left == 1)
-            k_sapply64<1><<<sblocks, 256, 0, st>>>(S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
-                                                   qstride, c->scal);
+            CPM_CUDA(launch_pdl(k_sapply64<1>, sblocks, 256, 0, st, S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
+                                                   qstride, c->scal));
           else if (left == 2)
-            k_sapply64<2><<<sblocks, 256, 0, st>>>(S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
-                                                   qstride, c->scal);
+            CPM_CUDA(launch_pdl(k_sapply64<2>, sblocks, 256, 0, st, S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
+                                                   qstride, c->scal));
           else
-            k_sapply64<4><<<sblocks, 256, 0, st>>>(S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
-                                                   qstride, c->scal);
+            CPM_CUDA(launch_pdl(k_sapply64<4>, sblocks, 256, 0, st, S64, ld, rows, y64, ldy, r0, nrep, dpsi, Sv, W, c1, qout,
+                                                   qstride, c->scal));
         }
         STEP_LAUNCH();
       }
@@ -1763,8 +1783,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
       if (c->mirror) {
         const int nh = c->nh, ldh = c->ldh;
-        k_mirror_fold<<<dim3((nh + 255) / 256, nrep), 256, 0, st>>>(b, ldb, nh, ldh, c->m_i0, c->m_j, c->ypm,
-                                                                    c->mixed ? c->b32 : nullptr);
+        CPM_CUDA(launch_pdl(k_mirror_fold, dim3((nh + 255) / 256, nrep), 256, 0, st, b, ldb, nh, ldh, c->m_i0, c->m_j, c->ypm,
+                                                                    c->mixed ? c->b32 : nullptr));
         STEP_LAUNCH();
         for (int blk = 0; blk < 2; ++blk) {
           const size_t so = (size_t)blk * nh * ldh;
@@ -1795,8 +1815,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
                               q, st));
       } else if (c->mixed && nrep >= TC_MIN_REPLICAS) {
         CPM_TRY(sapply_tensor_core(c, nrep, st));
-        k_qraw_epilogue<<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(c->qraw32, ne, b, ldb, dpsi, c->Sv, c->W,
-                                                                      c->e_c1, q, c->scal);
+        CPM_CUDA(launch_pdl(k_qraw_epilogue, dim3((ne + 255) / 256, nrep), 256, 0, st, c->qraw32, ne, b, ldb, dpsi, c->Sv, c->W,
+                                                                      c->e_c1, q, c->scal));
         STEP_LAUNCH();
       } else {
         CPM_TRY(sapply(c->S32, c->S64, ne, c->ld64, c->b32, 2 * c->ldx, c->ldx, b, ldb, c->Sv, c->W, c->e_c1, q,
@@ -1809,13 +1829,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     const bool forces_follow = f_elyt || f_elec || energy;
     const ChargePrep<T> cprep{forces_follow ? qT : nullptr, c->e_z, c->e_v, c->e_plus};
     if (c->mirror) {
-      k_project_mirror<T><<<dim3((c->nh + 255) / 256, nrep), 256, 0, st>>>(c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
+      CPM_CUDA(launch_pdl(k_project_mirror<T>, dim3((c->nh + 255) / 256, nrep), 256, 0, st, c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
                                                                         ldb, ne, c->scal, dpsi, c->Mh[0], c->Mh[1],
-                                                                        c->WTv[0], c->WTv[1], q, psibar, cprep);
+                                                                        c->WTv[0], c->WTv[1], q, psibar, cprep));
     } else {
-      k_project<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
+      CPM_CUDA(launch_pdl(k_project<T>, dim3((ne + 255) / 256, nrep), 256, 0, st, q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
                                                               c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
-                                                              c->WTv[1], psibar, cprep);
+                                                              c->WTv[1], psibar, cprep));
     }
     STEP_LAUNCH();
   }
@@ -1824,7 +1844,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     cudaStream_t sp = sside;
     if (!charges) {                      // charges given by the caller (cpm_forces, cpm_energy)
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
-      k_charge_prep<T><<<dim3((ne + 255) / 256, nrep), 256, 0, st>>>(q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal);
+      CPM_CUDA(launch_pdl(k_charge_prep<T>, dim3((ne + 255) / 256, nrep), 256, 0, st, q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal));
       STEP_LAUNCH();
     }
     // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes), into f_pair;
@@ -1856,14 +1876,14 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
           lj.sqrt_eps[k] = c->lj->sqrt_eps[k];
         }
         const size_t smem_lj = (sizeof(V4) + sizeof(typename Vec2<T>::type)) * kPairSrcCap;
-        k_pair_cell<T, true, true><<<dim3(pair_blocks(g), nrep), PC_THREADS, smem_lj, sp>>>(tg, a, e, g, c->p.alpha,
-                                                                                      kPairSrcCap, c->scal, lj);
+        CPM_CUDA(launch_pdl(k_pair_cell<T, true, true>, dim3(pair_blocks(g), nrep), PC_THREADS, smem_lj, sp, tg, a, e, g, c->p.alpha,
+                                                                                      kPairSrcCap, c->scal, lj));
       } else if (f_elyt) {
-        k_pair_cell<T, true><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal, PairLj{});
+        CPM_CUDA(launch_pdl(k_pair_cell<T, true>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp, tg, a, e, g, c->p.alpha,
+                                                                                kPairSrcCap, c->scal, PairLj{}));
       } else {
-        k_pair_cell<T, false><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp>>>(tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal, PairLj{});
+        CPM_CUDA(launch_pdl(k_pair_cell<T, false>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp, tg, a, e, g, c->p.alpha,
+                                                                                 kPairSrcCap, c->scal, PairLj{}));
       }
       STEP_LAUNCH();
     }
@@ -1877,8 +1897,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       } else {
         CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
         const int nb_l = grid_for(cap), nb_e = grid_for(ne);
-        k_spread_all<T><<<dim3(nb_l + nb_e, nrep), 256, 0, st>>>(nb_l, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                 qT, ne, c->e_base, e_th, (T*)c->mesh_r);
+        CPM_CUDA(launch_pdl(k_spread_all<T>, dim3(nb_l + nb_e, nrep), 256, 0, st, nb_l, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
+                                                                 qT, ne, c->e_base, e_th, (T*)c->mesh_r));
         STEP_LAUNCH();
       }
     }
@@ -1891,15 +1911,15 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     if (f_elyt && brick) {
       CPM_TRY(cpm_internal_gather_f_brick(c, nrep, off, l_loc, dpsi, ff_over_lz, slab_coef, f_elyt, st));
     } else if (f_elyt) {
-      k_gather_f_elyt<T><<<dim3(grid_for(cap), nrep), 256, 0, st>>>((const T*)c->mesh_phi, off, cap, sg, l_tmp,
+      CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for(cap), nrep), 256, 0, st, (const T*)c->mesh_phi, off, cap, sg, l_tmp,
                                                                     c->l_cell, c->spl_I, splF, dpsi, ff_over_lz,
-                                                                    slab_coef, c->scal, c->f_pair, f_elyt);
+                                                                    slab_coef, c->scal, c->f_pair, f_elyt));
       STEP_LAUNCH();
     }
     if (f_elec) {
-      k_gather_f_elec<T><<<dim3(grid_for(ne), nrep), 256, 0, st>>>((const T*)c->mesh_phi, qT, ne, c->e_base, e_th,
+      CPM_CUDA(launch_pdl(k_gather_f_elec<T>, dim3(grid_for(ne), nrep), 256, 0, st, (const T*)c->mesh_phi, qT, ne, c->e_base, e_th,
                                                                    e_dth, sg, dpsi, ff_over_lz, slab_coef, c->scal,
-                                                                   f_elec);
+                                                                   f_elec));
       STEP_LAUNCH();
     }
     ptg.stop();
@@ -1914,18 +1934,18 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       e.beta = c->p.eta / std::sqrt(2.0);
       e.slot = (energy && !closed_form) ? S_E_EE : -1;
       if (f_elec)
-        k_pair_cell<T, true><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal, PairLj{});
+        CPM_CUDA(launch_pdl(k_pair_cell<T, true>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st, tg, a, e, g, c->p.alpha,
+                                                                                kPairSrcCap, c->scal, PairLj{}));
       else
-        k_pair_cell<T, false><<<dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st>>>(tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal, PairLj{});
+        CPM_CUDA(launch_pdl(k_pair_cell<T, false>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st, tg, a, e, g, c->p.alpha,
+                                                                                 kPairSrcCap, c->scal, PairLj{}));
       STEP_LAUNCH();
     }
     if (energy) {
       PhaseTimer pt(c, st, CPM_PH_ENERGY);
       const double slab_e = (c->p.geometry == CPM_SLAB) ? KE * 2.0 * PI / c->V : 0.0;
-      k_energy_final<<<(nrep + 127) / 128, 128, 0, st>>>(nrep, c->scal, dpsi, c->p.alpha, c->p.eta, slab_e,
-                                                         ff_over_lz, closed_form ? 1 : 0, energy);
+      CPM_CUDA(launch_pdl(k_energy_final, (nrep + 127) / 128, 128, 0, st, nrep, c->scal, dpsi, c->p.alpha, c->p.eta, slab_e,
+                                                         ff_over_lz, closed_form ? 1 : 0, energy));
       STEP_LAUNCH();
     }
   }

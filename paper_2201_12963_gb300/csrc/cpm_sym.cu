@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(SY_THREADS, 1) k_sapply_sym(const float* __res
                                                              const float* __restrict__ xh,
                                                              const float* __restrict__ xl, float* __restrict__ part,
                                                              int npad) {
+  pdl_enter();
   extern __shared__ __align__(16) float sy_sm[];
   float* sxh = sy_sm;                        // [npad]
   float* sxl = sxh + npad;                   // [npad]
@@ -133,6 +134,7 @@ __global__ void __launch_bounds__(256) k_sym_finish(int rows, int nt, int npad, 
                                                     const double* __restrict__ Sv, const double* __restrict__ W,
                                                     const double* __restrict__ c1, double* __restrict__ qout,
                                                     double* __restrict__ scal) {
+  pdl_enter();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double red[4] = {0, 0, 0, 0};
   if (i < rows) {
@@ -190,10 +192,10 @@ int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* x
   const int n = c->mirror ? c->nh : c->ne;
   const int nt = c->sym_nt, npad = nt * SY_T;
   const float* Sp = c->sym_S + (size_t)blk * sy_tiles(nt) * SY_T * SY_T;
-  k_sapply_sym<<<c->n_sm, SY_THREADS, sym_smem(npad), st>>>(Sp, nt, n, xh, xl, c->sym_part, npad);
+  CPM_CUDA(launch_pdl(k_sapply_sym, c->n_sm, SY_THREADS, sym_smem(npad), st, Sp, nt, n, xh, xl, c->sym_part, npad));
   ++c->launches;
   CPM_LAUNCH();
-  k_sym_finish<<<(n + 255) / 256, 256, 0, st>>>(n, nt, npad, c->sym_part, b, dpsi, Sv, W, c1, qout, c->scal);
+  CPM_CUDA(launch_pdl(k_sym_finish, (n + 255) / 256, 256, 0, st, n, nt, npad, c->sym_part, b, dpsi, Sv, W, c1, qout, c->scal));
   ++c->launches;
   CPM_LAUNCH();
   return CPM_OK;
