@@ -207,11 +207,11 @@ class ClockSampler:
 PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distance 8, erfc/exp 20, force 12)
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels, keyed by workload
 # and "phase:kernel variant" (the autotuner may pick another S-apply kernel, whose traffic was not
-# captured: then traffic is null).  Summaries: profiles/k_sapply32_paper-cell-ff-mixed.md,
+# captured: then traffic is null).  Summaries: profiles/dram_k_sapply32_k_pair_cell_paper-cell-ff-mixed.md,
 # profiles/k_sapply_sym_large-cell-ff-mixed.md.  Set an entry to None whenever its kernel changes.
-NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.737536e6},
+NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.738304e6, "f_pair_elyt": 0.211328e6, "b_real": 0.11456e6},
                      "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {}, "paper-dc-md": {},
-                     "large": {"s_apply:sym": 210.907904e6},
+                     "large": {"s_apply:sym": None},
                      "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
