@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--kernels", default="auto",
                     help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
                          "sym,library,sites, to run a fixed kernel choice (profiling captures)")
+    ap.add_argument("--pair-variant", default="auto", choices=["auto", "cell", "warp-elec", "warp-elyt", "warp"],
+                    help="real-space pair kernels: one block per cell, or one warp per target for electrode "
+                         "targets, electrolyte targets or both (default: autotuned)")
     ap.add_argument("--pair-group", type=int, default=0,
                     help="z cells per block of the real-space pair kernels (default: the autotuner's choice)")
     ap.add_argument("--charge-every", type=int, default=5,
@@ -285,6 +288,8 @@ def build_system(args, w, dev):
         g.cpm_set_mesh_variant(s.ctx, variants[2])
     if args.pair_group > 0:
         g.cpm_set_pair_group(s.ctx, args.pair_group)
+    if args.pair_variant != "auto":
+        g.cpm_set_pair_variant(s.ctx, args.pair_variant)
     return s, build_s, variants
 
 
@@ -432,6 +437,7 @@ def run_gb300(args):
                       "precision": args.precision, "build_s": round(build_s, 2),
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
                       "charge_assignment": mesh_variant, "pair_group_z": g.cpm_get_pair_group(s.ctx),
+                      "pair_kernel": g.cpm_get_pair_variant(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
@@ -566,6 +572,7 @@ def run_md(args):
                       "timestep_fs": synth.PAPER_TIMESTEP_FS, "thermostat": "Nose-Hoover 400 K, 100 fs",
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
                       "charge_assignment": mesh_variant, "pair_group_z": g.cpm_get_pair_group(s.ctx),
+                      "pair_kernel": g.cpm_get_pair_variant(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
                       "l2": f"flushed between replays of the {k}-step block (256 MiB write); CUDA-event time per block",

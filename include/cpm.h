@@ -365,15 +365,34 @@ int cpm_set_mesh_variant(cpm_ctx* ctx, int32_t variant);
 int cpm_set_pair_group(cpm_ctx* ctx, int32_t gz);
 int cpm_get_pair_group(const cpm_ctx* ctx, int32_t* gz);
 
+/* Real-space pair kernels (the real-space part of b, the electrolyte and electrode forces, the
+ * Gaussian-Gaussian energy) come in two forms:
+ *   cell blocks      one block per cell (or z group of cells, cpm_set_pair_group): the sources of
+ *                    the cells within r_c of the cell are staged in shared memory and shared by its
+ *                    targets;
+ *   warp per target  the stencil cells within r_c of the target point itself, sources read from
+ *                    global memory through the caches, no block-wide staging or barriers.
+ * Both compact the sources within r_c into a per-warp queue before the screened kernels, and give the
+ * same results up to the order of the sums.  The variant is a mask of the target kinds that use the
+ * warp form: electrode targets (real-space b, electrode forces) and electrolyte targets (electrolyte
+ * forces, with the MD loop's Lennard-Jones).  Default CPM_PAIR_CELL; cpm_autotune times all four. */
+enum cpm_pair_variant { CPM_PAIR_CELL = 0, CPM_PAIR_WARP_ELEC = 1, CPM_PAIR_WARP_ELYT = 2, CPM_PAIR_WARP = 3 };
+int cpm_set_pair_variant(cpm_ctx* ctx, int32_t variant);
+int cpm_get_pair_variant(const cpm_ctx* ctx, int32_t* variant);
+
 /*
- * cpm_autotune - time every available S-apply variant on the given single-replica input (five
- * calls each after a warm-up, each started with a cold L2 cache, CUDA events on
- * `stream`), keep the fastest (median) in the context; then, with that S-apply, the two mesh
+ * cpm_autotune - time every available S-apply variant on the given single-replica input (nine
+ * replays each of the whole step captured as a CUDA graph on a private stream, after a warm-up,
+ * each started with a cold L2 cache, CUDA events; direct calls when the profiler is on), keep the
+ * fastest (median) in the context; then, with that S-apply, the two mesh
  * convolutions (cpm_fft_variant), then the two charge assignments (cpm_mesh_variant), then the pair
- * kernels' z groups of 1, 2 and 4 cells (cpm_set_pair_group), keeping the faster each time.  Each timed call is a whole cpm_step (scratch force and energy outputs).
- * choice_host[3] (may be NULL) receives the kept (cpm_sapply_variant, cpm_fft_variant,
- * cpm_mesh_variant).
- * Allocates and frees a scratch buffer of twice the L2 size and scratch outputs.  The arguments are those of
+ * kernels' z groups of 1, 2 and 4 cells (cpm_set_pair_group), then the four pair-kernel variant
+ * masks (cpm_pair_variant), keeping the faster each time.  Each timed call is a whole cpm_step
+ * (scratch force and energy outputs).  choice_host[3] (may be NULL) receives the kept
+ * (cpm_sapply_variant, cpm_fft_variant, cpm_mesh_variant); cpm_get_pair_group and
+ * cpm_get_pair_variant report the rest.
+ * Allocates and frees a scratch buffer of twice the L2 size, scratch outputs, a stream and the
+ * timing graphs.  The arguments are those of
  * cpm_step_charges with n_rep = 1; q_dev receives the charges.  Synchronises `stream`; not for
  * use during graph capture.  Without an available alternative it keeps the current variant.
  */

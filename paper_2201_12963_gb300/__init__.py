@@ -24,7 +24,7 @@ DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 EXPORTED = ("cpm_build_matrix", "cpm_matrix_key", "cpm_matrix_image", "cpm_build_matrix_from_image", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
             "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
-            "cpm_set_pair_group", "cpm_get_pair_group",
+            "cpm_set_pair_group", "cpm_get_pair_group", "cpm_set_pair_variant", "cpm_get_pair_variant",
             "cpm_autotune", "cpm_density_z", "cpm_potential_z",
             "cpm_md_create", "cpm_md_run", "cpm_md_advance", "cpm_md_get_state", "cpm_md_set_state", "cpm_md_info",
             "cpm_md_destroy", "cpm_destroy",
@@ -97,6 +97,8 @@ def _load():
     lib.cpm_set_mesh_variant.argtypes = [vp, i32]
     lib.cpm_set_pair_group.argtypes = [vp, i32]
     lib.cpm_get_pair_group.argtypes = [vp, ctypes.POINTER(i32)]
+    lib.cpm_set_pair_variant.argtypes = [vp, i32]
+    lib.cpm_get_pair_variant.argtypes = [vp, ctypes.POINTER(i32)]
     lib.cpm_density_z.argtypes = [vp, i32, pi32, pd, pd, i32, pd, vp]
     lib.cpm_potential_z.argtypes = [vp, i32, i32, pd, ctypes.c_double, pd, pd, vp]
     lib.cpm_autotune.argtypes = [vp, pi32, pd, pd, pd, vp, pi32]
@@ -366,6 +368,20 @@ def cpm_get_pair_group(ctx: Context) -> int:
     v = ctypes.c_int32()
     _check(_lib.cpm_get_pair_group(ctx.handle, ctypes.byref(v)), "cpm_get_pair_group")
     return int(v.value)
+
+
+PAIR_VARIANTS = {"cell": 0, "warp-elec": 1, "warp-elyt": 2, "warp": 3}   # enum cpm_pair_variant
+
+
+def cpm_set_pair_variant(ctx: Context, variant):
+    v = PAIR_VARIANTS[variant] if isinstance(variant, str) else int(variant)
+    _check(_lib.cpm_set_pair_variant(ctx.handle, v), "cpm_set_pair_variant")
+
+
+def cpm_get_pair_variant(ctx: Context) -> str:
+    v = ctypes.c_int32()
+    _check(_lib.cpm_get_pair_variant(ctx.handle, ctypes.byref(v)), "cpm_get_pair_variant")
+    return {k: x for x, k in PAIR_VARIANTS.items()}[int(v.value)]
 
 
 def cpm_autotune(ctx: Context, offsets, xyzq, dpsi, q, stream=None):

@@ -117,6 +117,7 @@ struct cpm_ctx {
   // S-apply variant (enum cpm_sapply_variant) and the streaming variant's row partial sums
   // ([rows of S], float64, zero between calls: its finish kernel clears what it consumed)
   int pair_gz = 1;               // real-space pair kernels: z cells per block (cpm_set_pair_group)
+  int pair_variant = 0;         // enum cpm_pair_variant
   int sapply_variant = 0;
   double* qpart = nullptr;
   // symmetric packed S (upper-triangle 128 x 128 tiles, float32) and its per-slot partial sums

@@ -622,6 +622,274 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   }
 }
 
+// Warp-per-target variant of the real-space pair kernels (same inputs and outputs as k_pair_cell).
+// A warp takes one target at a time (grid-stride over the cell-sorted targets): it lists the
+// stencil cells whose box lies within r_c of the target point itself (tighter than the cell-to-cell
+// test of k_pair_cell), scans their source counts, then sweeps the candidates 32 at a time straight
+// from global memory (L1 / L2: neighbouring warps read the same cells), compacting those within r_c
+// into a per-warp ring for the screened kernels.  No block-wide staging, no block barriers until
+// the final energy reduction.
+constexpr int PW_THREADS = 256;
+constexpr int PW_WARPS = PW_THREADS / 32;
+
+// per-warp shared memory: stencil prefix [ns + 1], first source [ns], packed offsets [ns], ring
+template <typename T>
+__host__ __device__ constexpr size_t pw_warp_bytes(int ns) {
+  // multiple of 32 bytes, so that every warp's ring of (32-byte float64) positions stays aligned
+  return ((sizeof(int) * (3 * (size_t)ns + 1) + 64 * (sizeof(typename Vec4<T>::type) +
+                                                      sizeof(typename Vec2<T>::type))) + 31) & ~(size_t)31;
+}
+
+template <typename T, bool FORCE, bool LJ = false>
+__global__ void __launch_bounds__(PW_THREADS) k_pair_warp(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
+                                                          const CellGeom g, const double alpha_d, double* __restrict__ scal,
+                                                          const PairLj lj) {
+  pdl_enter();
+  using V4 = typename Vec4<T>::type;
+  using V2 = typename Vec2<T>::type;
+  static_assert(!LJ || FORCE, "the Lennard-Jones pass computes forces");
+  extern __shared__ __align__(32) unsigned char pw_dyn[];
+  __shared__ T lpar[2][kLjMaxTypes];
+  __shared__ double ered[3][PW_WARPS];
+  const int rep = blockIdx.y;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int ns = g.nsten;
+  unsigned char* wbase = pw_dyn + (size_t)warp * pw_warp_bytes<T>(ns);
+  V4* rsrc = reinterpret_cast<V4*>(wbase);                              // ring: source positions
+  V2* rlj = reinterpret_cast<V2*>(rsrc + 64);                           // ring: LJ parameters
+  int* wpre = reinterpret_cast<int*>(rlj + 64);                         // [ns + 1]
+  int* wfirst = wpre + ns + 1;                                          // [ns]
+  int* wdoff = wfirst + ns;                                             // [ns] packed (dx, dy, dz)
+  if (LJ && tid == 0) {
+#pragma unroll
+    for (int k = 0; k < kLjMaxTypes; ++k) {
+      lpar[0][k] = (T)lj.sig_half[k];
+      lpar[1][k] = (T)lj.sqrt_eps[k];
+    }
+  }
+  __syncthreads();
+  const int ncell = g.nc[0] * g.nc[1] * g.nc[2];
+  const int* tst = t.start + rep * t.start_stride;
+  const int n_t = tst[ncell];
+  const V4* tl = (const V4*)t.loc + rep * t.loc_stride;
+  const int* tso = t.sorted + rep * t.loc_stride;
+  const T* tq = t.qT ? (const T*)t.qT + (size_t)rep * t.n_fixed : nullptr;
+  const bool want_energy = s0.slot >= 0 || s1.slot >= 0;
+  const T alpha = (T)alpha_d;
+  const T rc2 = (T)g.rc2;
+  const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
+  const int lj_o = LJ ? lj.off[rep] : 0;
+  const T ljc = (T)lj.cut, ljc2 = ljc * ljc, ljic = LJ ? T(1) / ljc : T(0);
+  Acc<T> ea0, ea1;                                                      // lane 0 of each warp
+  double elj = 0.0;
+  for (int k = blockIdx.x * PW_WARPS + warp; k < n_t; k += gridDim.x * PW_WARPS) {
+    // the target's cell: the last c with tst[c] <= k
+    int lo = 0, hi = ncell;
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (tst[mid] <= k) lo = mid; else hi = mid;
+    }
+    const int cell = lo;
+    const int cz = cell % g.nc[2], cy = (cell / g.nc[2]) % g.nc[1], cx = cell / (g.nc[2] * g.nc[1]);
+    V4 tp = tl[k];
+    const int orig = tso[k];
+    if (tq) tp.w = tq[orig];
+    V2 tpar;
+    if (LJ) {
+      const int ty = min(kLjMaxTypes - 1, max(0, lj.type[lj_o + orig]));
+      tpar.x = lpar[0][ty];
+      tpar.y = lpar[1][ty];
+    }
+    Acc<T> pot[2];
+    T fx = 0, fy = 0, fz = 0;
+    T lx = 0, ly = 0, lz = 0, lu = 0;
+    for (int set = 0; set < 2; ++set) {
+      const void* s_loc = set ? s1.loc : s0.loc;
+      if (!s_loc) continue;
+      const long long s_ls = set ? s1.loc_stride : s0.loc_stride;
+      const V4* sl = (const V4*)s_loc + rep * s_ls;
+      const int* sst = (set ? s1.start : s0.start) + rep * (set ? s1.start_stride : s0.start_stride);
+      const void* s_q = set ? s1.qT : s0.qT;
+      const T* sq = s_q ? (const T*)s_q + (size_t)rep * (set ? s1.q_stride : s0.q_stride) : nullptr;
+      const int* s_sorted = set ? s1.sorted : s0.sorted;
+      const int* s_sorted_r = s_sorted + rep * s_ls;
+      const double s_beta = set ? s1.beta : s0.beta;
+      const bool gauss = s_beta > 0.0;
+      const T beta = (T)s_beta;
+      const T ljw = set ? T(1) : T(0.5);
+      // ---- stencil cells within r_c of the target point, and their source counts
+      int run = 0;
+      for (int b = 0; b < ns; b += 32) {
+        const int si = b + lane;
+        int cnt = 0, f = 0, pack = 0;
+        if (si < ns) {
+          const int dx = si % g.w[0] - g.sten[0];
+          const int r1 = si / g.w[0];
+          const int dy = r1 % g.w[1] - g.sten[1];
+          const int dz = r1 / g.w[1] - g.sten[2];
+          const T bx = (T)dx * e0, by = (T)dy * e1, bz = (T)dz * e2;
+          const T qx = fmax(T(0), fmax(bx - tp.x, tp.x - (bx + e0)));
+          const T qy = fmax(T(0), fmax(by - tp.y, tp.y - (by + e1)));
+          const T qz = fmax(T(0), fmax(bz - tp.z, tp.z - (bz + e2)));
+          if (qx * qx + qy * qy + qz * qz < rc2) {
+            const int flat = (wrap_index(cx + dx, g.nc[0]) * g.nc[1] + wrap_index(cy + dy, g.nc[1])) * g.nc[2] +
+                             wrap_index(cz + dz, g.nc[2]);
+            f = sst[flat];
+            cnt = sst[flat + 1] - f;
+          }
+          pack = ((dx + 128) << 16) | ((dy + 128) << 8) | (dz + 128);
+        }
+        int v = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(FULL, v, o);
+          if (lane >= o) v += u;
+        }
+        if (si < ns) {
+          wpre[si + 1] = run + v;
+          wfirst[si] = f;
+          wdoff[si] = pack;
+        }
+        run += __shfl_sync(FULL, v, 31);
+      }
+      if (lane == 0) wpre[0] = 0;
+      __syncwarp();
+      const int total = run;
+      // ---- candidates 32 at a time; those within r_c go to the ring
+      int head = 0, cnt = 0;
+      auto consume = [&](int n) {
+        if (lane < n) {
+          const int slot = (head + lane) & 63;
+          const V4 sp = rsrc[slot];
+          const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          T pr, fr = T(0);
+          PairMath<T>::template eval<FORCE>(r2, alpha, beta, gauss, pr, fr);
+          pot[set].add(sp.w * pr);
+          if (FORCE) {
+            fr *= sp.w;
+            fx += fr * dx;
+            fy += fr * dy;
+            fz += fr * dz;
+          }
+          if (LJ) {
+            const V2 spar = rlj[slot];
+            const T eps = tpar.y * spar.y;
+            if (r2 < ljc2 && eps > T(0)) {
+              const T sig = tpar.x + spar.x;
+              const T sg2 = sig * sig;
+              const T ir2 = T(1) / r2;
+              const T s2 = sg2 * ir2, s6 = s2 * s2 * s2;
+              const T c2 = sg2 * ljic * ljic, c6 = c2 * c2 * c2;
+              const T fc = T(24) * eps * (T(2) * c6 * c6 - c6) * ljic;
+              const T r = sqrt(r2);
+              const T fl = T(24) * eps * ir2 * (T(2) * s6 * s6 - s6) - fc / r;
+              lx += fl * dx;
+              ly += fl * dy;
+              lz += fl * dz;
+              lu += ljw * (T(4) * eps * ((s6 * s6 - s6) - (c6 * c6 - c6)) + (r - ljc) * fc);
+            }
+          }
+        }
+        head = (head + n) & 63;
+        cnt -= n;
+        __syncwarp();
+      };
+      for (int jb = 0; jb < total; jb += 32) {
+        const int j = jb + lane;
+        bool hit = false;
+        V4 p;
+        V2 par;
+        if (j < total) {
+          int a = 0, bnd = ns;                                          // wpre[a] <= j < wpre[bnd]
+          while (bnd - a > 1) {
+            const int mid = (a + bnd) >> 1;
+            if (wpre[mid] <= j) a = mid; else bnd = mid;
+          }
+          const int gi = wfirst[a] + (j - wpre[a]);
+          const int pk = wdoff[a];
+          p = sl[gi];
+          p.x += (T)(((pk >> 16) & 255) - 128) * e0;
+          p.y += (T)(((pk >> 8) & 255) - 128) * e1;
+          p.z += (T)((pk & 255) - 128) * e2;
+          const T dx = tp.x - p.x, dy = tp.y - p.y, dz = tp.z - p.z;
+          const T r2 = dx * dx + dy * dy + dz * dz;
+          hit = r2 < rc2 && r2 > T(0);
+          if (hit && sq) p.w = sq[s_sorted[gi]];
+          if (LJ && hit) {
+            const int ty = set ? lj.elec_type : min(kLjMaxTypes - 1, max(0, lj.type[lj_o + s_sorted_r[gi]]));
+            par.x = ty >= 0 ? lpar[0][ty] : T(0);
+            par.y = ty >= 0 ? lpar[1][ty] : T(0);
+          }
+        }
+        const unsigned bal = __ballot_sync(FULL, hit);
+        if (hit) {
+          const int slot = (head + cnt + __popc(bal & ((1u << lane) - 1u))) & 63;
+          rsrc[slot] = p;
+          if (LJ) rlj[slot] = par;
+        }
+        cnt += __popc(bal);
+        __syncwarp();
+        if (cnt >= 32) consume(32);
+      }
+      if (cnt > 0) consume(cnt);
+      __syncwarp();
+    }
+    // ---- this target's outputs
+    pot[0].warp_reduce();
+    pot[1].warp_reduce();
+    if (FORCE) {
+      fx = warp_sum_t(fx);
+      fy = warp_sum_t(fy);
+      fz = warp_sum_t(fz);
+    }
+    if (LJ) {
+      lx = warp_sum_t(lx);
+      ly = warp_sum_t(ly);
+      lz = warp_sum_t(lz);
+      lu = warp_sum_t(lu);
+    }
+    if (lane == 0) {
+      if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = pot[0].value();
+      if (want_energy) {
+        const T ct = tp.w;
+        ea0.add(ct * pot[0].s);
+        ea0.c += ct * pot[0].c;
+        ea1.add(ct * pot[1].s);
+        ea1.c += ct * pot[1].c;
+      }
+      if (LJ) elj += (double)lu;
+      if (FORCE && t.force) {
+        const size_t gi = (size_t)rep * t.n_fixed + orig;
+        const double f = KE * (double)tp.w;
+        t.force[3 * gi + 0] += f * (double)fx + (LJ ? (double)lx : 0.0);
+        t.force[3 * gi + 1] += f * (double)fy + (LJ ? (double)ly : 0.0);
+        t.force[3 * gi + 2] += f * (double)fz + (LJ ? (double)lz : 0.0);
+      }
+    }
+    __syncwarp();
+  }
+  // ---- block totals: one float64 atomic per energy slot per block
+  if (!want_energy && !LJ) return;
+  if (lane == 0) {
+    ered[0][warp] = ea0.value();
+    ered[1][warp] = ea1.value();
+    ered[2][warp] = elj;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0;
+    for (int w = 0; w < PW_WARPS; ++w) {
+      a0 += ered[0][w];
+      a1 += ered[1][w];
+      a2 += ered[2][w];
+    }
+    if (s0.slot >= 0 && a0 != 0.0) atomicAdd(scal + rep * NSCAL + s0.slot, a0);
+    if (s1.slot >= 0 && a1 != 0.0) atomicAdd(scal + rep * NSCAL + s1.slot, a1);
+    if (LJ && a2 != 0.0) atomicAdd(scal + rep * NSCAL + S_E_LJ, a2);
+  }
+}
+
 // ------------------------------------------------------------------------------------------
 // SPME: charge assignment, influence function, interpolation (cardinal B-splines of order P)
 // ------------------------------------------------------------------------------------------
@@ -1639,6 +1907,30 @@ static int sapply_stream(cpm_ctx* c, const float* S, int rows, int ld, const flo
   return CPM_OK;
 }
 
+// One real-space pair launch with the context's kernel variant (cpm_pair_variant).
+// elec_targets: the electrode-target kernels (real-space b, electrode forces) rather than the
+// electrolyte-target ones; each kind follows its bit of the variant mask.
+template <typename T, bool FORCE, bool LJ>
+static int launch_pair(cpm_ctx* c, bool elec_targets, const CellPairTgt& tg, const PairSrc& a, const PairSrc& e,
+                       const CellGeom& g, int nrep, int max_targets, const PairLj& lj, cudaStream_t s) {
+  using V4 = typename Vec4<T>::type;
+  using V2 = typename Vec2<T>::type;
+  const int bit = elec_targets ? CPM_PAIR_WARP_ELEC : CPM_PAIR_WARP_ELYT;
+  if (c->pair_variant & bit) {
+    const size_t smem = PW_WARPS * pw_warp_bytes<T>(g.nsten);
+    const int blocks = std::max(1, std::min((max_targets + PW_WARPS - 1) / PW_WARPS, c->n_sm * 8));
+    CPM_CUDA(launch_pdl(k_pair_warp<T, FORCE, LJ>, dim3(blocks, nrep), PW_THREADS, smem, s, tg, a, e, g, c->p.alpha,
+                        c->scal, lj));
+  } else {
+    const size_t smem = (sizeof(V4) + (LJ ? sizeof(V2) : 0)) * kPairSrcCap;
+    CPM_CUDA(launch_pdl(k_pair_cell<T, FORCE, LJ>, dim3(pair_blocks(g), nrep), PC_THREADS, smem, s, tg, a, e, g,
+                        c->p.alpha, kPairSrcCap, c->scal, lj));
+  }
+  ++c->launches;
+  CPM_LAUNCH();
+  return CPM_OK;
+}
+
 template <typename T>
 static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const double* dpsi, bool charges,
                double* q, double* b_out, double* psibar, double* f_elyt, double* f_elec, double* energy,
@@ -1706,9 +1998,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     s.beta = c->p.eta;
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      CPM_CUDA(launch_pdl(k_pair_cell<T, false>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sside, tg, s, none, g, c->p.alpha,
-                                                                                  kPairSrcCap, c->scal, PairLj{}));
-      STEP_LAUNCH();
+      CPM_TRY((launch_pair<T, false, false>(c, true, tg, s, none, g, nrep, ne, PairLj{}, sside)));
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
     // SPME part
@@ -1875,17 +2165,12 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
           lj.sig_half[k] = c->lj->sig_half[k];
           lj.sqrt_eps[k] = c->lj->sqrt_eps[k];
         }
-        const size_t smem_lj = (sizeof(V4) + sizeof(typename Vec2<T>::type)) * kPairSrcCap;
-        CPM_CUDA(launch_pdl(k_pair_cell<T, true, true>, dim3(pair_blocks(g), nrep), PC_THREADS, smem_lj, sp, tg, a, e, g, c->p.alpha,
-                                                                                      kPairSrcCap, c->scal, lj));
+        CPM_TRY((launch_pair<T, true, true>(c, false, tg, a, e, g, nrep, cap, lj, sp)));
       } else if (f_elyt) {
-        CPM_CUDA(launch_pdl(k_pair_cell<T, true>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp, tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal, PairLj{}));
+        CPM_TRY((launch_pair<T, true, false>(c, false, tg, a, e, g, nrep, cap, PairLj{}, sp)));
       } else {
-        CPM_CUDA(launch_pdl(k_pair_cell<T, false>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, sp, tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal, PairLj{}));
+        CPM_TRY((launch_pair<T, false, false>(c, false, tg, a, e, g, nrep, cap, PairLj{}, sp)));
       }
-      STEP_LAUNCH();
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
     // SPME of all charges
@@ -1934,12 +2219,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       e.beta = c->p.eta / std::sqrt(2.0);
       e.slot = (energy && !closed_form) ? S_E_EE : -1;
       if (f_elec)
-        CPM_CUDA(launch_pdl(k_pair_cell<T, true>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st, tg, a, e, g, c->p.alpha,
-                                                                                kPairSrcCap, c->scal, PairLj{}));
+        CPM_TRY((launch_pair<T, true, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
       else
-        CPM_CUDA(launch_pdl(k_pair_cell<T, false>, dim3(pair_blocks(g), nrep), PC_THREADS, pc_smem, st, tg, a, e, g, c->p.alpha,
-                                                                                 kPairSrcCap, c->scal, PairLj{}));
-      STEP_LAUNCH();
+        CPM_TRY((launch_pair<T, false, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
     }
     if (energy) {
       PhaseTimer pt(c, st, CPM_PH_ENERGY);
@@ -1992,6 +2274,15 @@ static int pair_cell_attributes() {
                                 l64));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 l32));
+  // warp-per-target variant: per-warp stencil tables for the largest stencil
+  const int w64 = (int)(cpm::PW_WARPS * cpm::pw_warp_bytes<double>(cpm::kMaxStencil));
+  const int w32 = (int)(cpm::PW_WARPS * cpm::pw_warp_bytes<float>(cpm::kMaxStencil));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<double, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, w64));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<double, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, w64));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, w64));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, w32));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, w32));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, w32));
   return CPM_OK;
 }
 
@@ -2136,6 +2427,21 @@ extern "C" int cpm_get_pair_group(const cpm_ctx* c, int32_t* gz) {
   return CPM_OK;
 }
 
+extern "C" int cpm_set_pair_variant(cpm_ctx* c, int32_t variant) {
+  if (!c || variant < CPM_PAIR_CELL || variant > CPM_PAIR_WARP) {
+    cpm::set_error("cpm_set_pair_variant: unknown variant %d", variant);
+    return CPM_ERR_ARG;
+  }
+  c->pair_variant = variant;
+  return CPM_OK;
+}
+
+extern "C" int cpm_get_pair_variant(const cpm_ctx* c, int32_t* variant) {
+  if (!c || !variant) return CPM_ERR_ARG;
+  *variant = c->pair_variant;
+  return CPM_OK;
+}
+
 extern "C" int cpm_set_fft_variant(cpm_ctx* c, int32_t variant) {
   if (!c) return CPM_ERR_ARG;
   if (variant == CPM_FFT_LIBRARY || (variant == CPM_FFT_OWN && c->fft_own_ok)) {
@@ -2160,7 +2466,8 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
                             void* stream, int32_t* choice_host) {
   if (!c || !off || !xyzq || !dpsi || !q) return CPM_ERR_ARG;
   cudaStream_t st = (cudaStream_t)stream;
-  const int keep_s = c->sapply_variant, keep_f = c->fft_variant, keep_m = c->mesh_variant, keep_g = c->pair_gz;
+  const int keep_s = c->sapply_variant, keep_f = c->fft_variant, keep_m = c->mesh_variant, keep_g = c->pair_gz,
+            keep_p = c->pair_variant;
   // every timed call starts from a cold L2 (a write of twice its capacity), as inside an MD step
   // whose other work evicts S
   int l2 = 0;
@@ -2176,24 +2483,50 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   double *f_scr = nullptr, *e_scr = nullptr;
   CPM_CUDA(cudaMalloc(&f_scr, sizeof(double) * 3 * (size_t)c->p.max_elyt + 64));
   CPM_CUDA(cudaMalloc(&e_scr, sizeof(double) * cpm::NENERGY));
-  // median of five timed steps (charges, forces, energy) after a warm-up; false if unavailable
+  // Median of nine timed steps (charges, forces, energy) after a warm-up; false if unavailable.
+  // The step is timed as the replay of a CUDA graph captured on a private stream, as it runs in an
+  // MD loop (direct calls would add the host's launch work); without graphs (profiler on), direct.
+  cudaStream_t cs = nullptr;
+  CPM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const bool use_graph = c->prof_cap == 0;
   auto time_config = [&](int sv, int fv, int mv, float* med) -> bool {
     if (cpm_set_sapply_variant(c, sv) != CPM_OK || cpm_set_fft_variant(c, fv) != CPM_OK ||
         cpm_set_mesh_variant(c, mv) != CPM_OK)
       return false;
     rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, st);
-    float ms[5];
-    for (int k = 0; k < 5 && rc == CPM_OK; ++k) {
-      cudaMemsetAsync(flush, k, flush_bytes, st);
-      cudaEventRecord(e0, st);
-      rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, st);
-      cudaEventRecord(e1, st);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
-      else cudaEventElapsedTime(&ms[k], e0, e1);
+    if (rc == CPM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CPM_ERR_CUDA;
+    cudaGraph_t gr = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    if (rc == CPM_OK && use_graph) {
+      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        rc = CPM_ERR_CUDA;
+      } else {
+        const int r2 = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &gr);
+        if (r2 != CPM_OK) rc = r2;
+        else if (ec != cudaSuccess || cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) rc = CPM_ERR_CUDA;
+      }
     }
+    constexpr int NT = 9;
+    float ms[NT];
+    cudaStream_t ts = use_graph ? cs : st;
+    for (int k = 0; k < NT + 1 && rc == CPM_OK; ++k) {
+      cudaMemsetAsync(flush, k, flush_bytes, ts);
+      cudaEventRecord(e0, ts);
+      if (use_graph) {
+        if (cudaGraphLaunch(ge, ts) != cudaSuccess) rc = CPM_ERR_CUDA;
+      } else {
+        rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, ts);
+      }
+      cudaEventRecord(e1, ts);
+      if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
+      else if (k > 0) cudaEventElapsedTime(&ms[k - 1], e0, e1);     // the first replay warms up
+    }
+    if (ge) cudaGraphExecDestroy(ge);
+    if (gr) cudaGraphDestroy(gr);
     if (rc != CPM_OK) return false;
-    std::sort(ms, ms + 5);
-    *med = ms[2];
+    std::sort(ms, ms + NT);
+    *med = ms[NT / 2];
     return true;
   };
   // the S-apply kernel first, then the transform, then the charge assignment, each with the
@@ -2226,10 +2559,22 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
     }
   }
   c->pair_gz = (rc == CPM_OK) ? best_g : keep_g;
+  // and the warp-per-target pair kernels against the cell blocks, per target kind
+  int best_p = keep_p;
+  for (int pv : {CPM_PAIR_CELL, CPM_PAIR_WARP_ELEC, CPM_PAIR_WARP_ELYT, CPM_PAIR_WARP}) {
+    if (rc != CPM_OK || pv == keep_p) continue;
+    c->pair_variant = pv;
+    if (time_config(best_s, best_f, best_m, &t) && t < best_ms) {
+      best_ms = t;
+      best_p = pv;
+    }
+  }
+  c->pair_variant = (rc == CPM_OK) ? best_p : keep_p;
   cudaFree(f_scr);
   cudaFree(e_scr);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  cudaStreamDestroy(cs);
   cudaFree(flush);
   c->sapply_variant = (rc == CPM_OK) ? best_s : keep_s;
   c->fft_variant = (rc == CPM_OK) ? best_f : keep_f;

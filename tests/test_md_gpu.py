@@ -230,3 +230,25 @@ def test_md_create_rejects_bad_input():
         g.cpm_md_create(s.ctx, p, off, np.full(len(mi.types), 2))      # type 2 has no mass
     with pytest.raises(g.CPMError):
         g.cpm_md_create(s.ctx, p, off, mi.types, np.full(len(mi.types), 3))   # group outside n_groups
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_lennard_jones_warp_kernel_against_oracle(prec):
+    """The warp-per-target pair kernel with the fused Lennard-Jones term."""
+    g, System, MD = _lib()
+    w = _cell(n_pairs=6)
+    mi = synth.md_inputs(w, seed=3)
+    res = {}
+    for cut in (0.0, 7.0):
+        s = System(w, prec, order=8)
+        g.cpm_set_pair_variant(s.ctx, "warp")
+        m = MD(s, mi, dt=2.0, charge_every=1, lj_cut=cut, t_damp=0.0)
+        m.run(0, energy=True, force=True)
+        assert g.cpm_status(s.ctx) == 0
+        res[cut] = (m.force.cpu().numpy().reshape(-1, 3).copy(), m.energies()[0])
+    U, F = omd.lj_energy_forces(w.elyt_xyz[0], mi.types, w.elec_xyz, mi.elec_type, mi.sigma, mi.eps, 7.0,
+                                np.asarray(w.box))
+    F_lj = res[7.0][0] - res[0.0][0]
+    tol = 1e-10 if prec == "fp64" else 2e-5
+    assert np.sqrt(((F_lj - F) ** 2).sum() / (F ** 2).sum()) <= tol
+    assert abs(res[7.0][1]["U_lj"] - U) <= tol * max(1.0, abs(U))

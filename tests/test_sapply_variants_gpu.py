@@ -161,8 +161,9 @@ def test_brick_charge_assignment_needs_mixed_precision(plain_ff):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 @pytest.mark.parametrize("case", ["ff", "dc", "slab"])
 def test_pair_kernel_z_groups_match_single_cells_and_oracle(plain_ff, case, prec):
-    """Blocks of 1, 2, 4 and 3 cells along z (3 leaves a shorter last group) give the same b,
-    charges, forces on both site kinds and energies: only the order of the sums changes."""
+    """Blocks of 1, 2, 4 and 3 cells along z (3 leaves a shorter last group) and the
+    warp-per-target kernels give the same b, charges, forces on both site kinds and energies: only
+    the order of the sums changes."""
     g, System = _lib()
     if case == "ff":
         w, out = plain_ff[0], plain_ff[2]
@@ -176,9 +177,14 @@ def test_pair_kernel_z_groups_match_single_cells_and_oracle(plain_ff, case, prec
         out = ocpm.Reference(w).step()
     s = System(w, prec, order=8)
     res = {}
-    for gz in (1, 2, 3, 4):
-        g.cpm_set_pair_group(s.ctx, gz)
-        assert g.cpm_get_pair_group(s.ctx) == gz
+    for gz in (1, 2, 3, 4, "warp", "warp-elec"):
+        if isinstance(gz, str):
+            g.cpm_set_pair_group(s.ctx, 1)
+            g.cpm_set_pair_variant(s.ctx, gz)
+            assert g.cpm_get_pair_variant(s.ctx) == gz
+        else:
+            g.cpm_set_pair_group(s.ctx, gz)
+            assert g.cpm_get_pair_group(s.ctx) == gz
         s.step(elec=True, energy=True)
         s.energies()
         r = s.results()
@@ -188,7 +194,7 @@ def test_pair_kernel_z_groups_match_single_cells_and_oracle(plain_ff, case, prec
         F, Fo = r["F_elyt"][0], out["F_elyt"]
         assert np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum()) <= 1e-5
     tol = 1e-12 if prec == "fp64" else 2e-6
-    for gz in (2, 3, 4):
+    for gz in (2, 3, 4, "warp", "warp-elec"):
         a, b = res[gz], res[1]
         assert np.max(np.abs(a["b"] - b["b"])) <= tol * np.max(np.abs(b["b"]))
         assert np.max(np.abs(a["q"] - b["q"])) <= tol
