@@ -252,3 +252,38 @@ def test_lennard_jones_warp_kernel_against_oracle(prec):
     tol = 1e-10 if prec == "fp64" else 2e-5
     assert np.sqrt(((F_lj - F) ** 2).sum() / (F ** 2).sum()) <= tol
     assert abs(res[7.0][1]["U_lj"] - U) <= tol * max(1.0, abs(U))
+
+
+def test_replica_batch_equals_replicas_alone():
+    """Two replicas (different electrolytes and potential differences) in one integrator: each
+    follows the trajectory it has when run alone (thermostat slots and offsets per replica)."""
+    g, System, MD = _lib()
+    w0 = _cell(n_pairs=4, seed=7)
+    w1 = _cell(n_pairs=5, seed=11)
+    wb = dataclasses.replace(w0, elyt_xyz=[w0.elyt_xyz[0], w1.elyt_xyz[0]], elyt_q=[w0.elyt_q[0], w1.elyt_q[0]],
+                             dpsi=np.array([1.0, 2.5]))
+    mis = [synth.md_inputs(wb, seed=31, r=0), synth.md_inputs(wb, seed=32, r=1)]
+    s = System(wb, "fp64", order=8)
+    m = MD(s, mis, dt=2.0, charge_every=2, lj_cut=7.0, t_damp=40.0)
+    m.run(6, energy=True)
+    assert g.cpm_status(s.ctx) == 0
+    ck = m.checkpoint()
+    off = s.offsets.cpu().numpy()
+    e_b = m.energies()
+    for r in range(2):
+        wr = wb.replica(r)
+        sr = System(wr, "fp64", order=8)
+        mr = MD(sr, [mis[r]], dt=2.0, charge_every=2, lj_cut=7.0, t_damp=40.0)
+        mr.run(6, energy=True)
+        cr = mr.checkpoint()
+        box = np.asarray(wb.box)
+        xb = ck["xyzq"][off[r]:off[r + 1], :3]
+        assert np.max(np.abs(_wrapdiff(xb, cr["xyzq"][:, :3], box))) <= 1e-9
+        vb = ck["vel"].reshape(-1, 3)[off[r]:off[r + 1]]
+        assert np.max(np.abs(vb - cr["vel"].reshape(-1, 3))) <= 1e-9 * np.max(np.abs(vb))
+        ne = w0.n_elec
+        assert np.max(np.abs(ck["q"][r * ne:(r + 1) * ne] - cr["q"])) <= 1e-9
+        assert np.max(np.abs(ck["thermo"][r] - cr["thermo"][0])) <= 1e-9 * max(1.0, np.max(np.abs(cr["thermo"])))
+        er = mr.energies()[0]
+        for key in ("KE", "H", "U_lj", "E_total"):
+            assert abs(e_b[r][key] - er[key]) <= 1e-8 * max(1.0, abs(er[key])), key
