@@ -250,7 +250,7 @@ struct CellPairTgt {
 constexpr int PC_MAXT = 64;        // targets per pass of a block
 constexpr int kPairSrcCap = 1024;  // sources staged per pass (dynamic shared memory)
 constexpr int PC_MAXSTEN = kMaxStencil;
-constexpr int PC_THREADS = 128;
+constexpr int PC_THREADS = 256;
 
 // Lennard-Jones of an MD run, fused into the electrolyte-target force pass (LJ = true): the same
 // staged sources and pair list within r_c serve both interactions.  Lorentz-Berthelot mixing,
