@@ -440,6 +440,7 @@ def run_gb300(args):
                       "pair_kernel": g.cpm_get_pair_variant(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
+                      "data_ns_per_day": round(value * (2 if GEOMETRY_NAME[args.workload] == "doubled cell" else 1), 2),
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
                       "graph": "whole step captured in one CUDA graph", "steps_per_s": round(steps_per_s, 1),
                       "replica_steps_per_s": round(steps_per_s, 1), "wall_s": round(wall, 3)},
@@ -605,6 +606,7 @@ def run_md(args):
                       "pair_kernel": g.cpm_get_pair_variant(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
+                      "data_ns_per_day": round(value * (2 if GEOMETRY_NAME[args.workload] == "doubled cell" else 1), 2),
                       "l2": f"flushed between replays of the {k}-step block (256 MiB write); CUDA-event time per block",
                       "graph": f"one CUDA graph per {k}-step block (energy record at its end)",
                       "steps_per_s": round(steps_per_s, 1), "wall_s": round(wall, 3),
