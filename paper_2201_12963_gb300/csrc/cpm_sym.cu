@@ -129,18 +129,47 @@ __global__ void __launch_bounds__(SY_THREADS, 1) k_sapply_sym(const float* __res
 }
 
 // q_raw = sum of the nt slots + dpsi S v, with the projection sums (one replica).
-__global__ void __launch_bounds__(256) k_sym_finish(int rows, int nt, int npad, const float* __restrict__ part,
-                                                    const double* __restrict__ b, const double* __restrict__ dpsi,
-                                                    const double* __restrict__ Sv, const double* __restrict__ W,
-                                                    const double* __restrict__ c1, double* __restrict__ qout,
-                                                    double* __restrict__ scal) {
+// Row totals from the per-tile-row partial slots: 32 rows per block, eight threads per row each
+// summing every eighth slot (compensated float32), combined in shared memory; then the row's q_raw
+// and its contributions to the projection sums.
+constexpr int SF_ROWS = 32, SF_SPLIT = 8;
+__global__ void __launch_bounds__(SF_ROWS * SF_SPLIT) k_sym_finish(int rows, int nt, int npad,
+                                                                  const float* __restrict__ part,
+                                                                  const double* __restrict__ b,
+                                                                  const double* __restrict__ dpsi,
+                                                                  const double* __restrict__ Sv,
+                                                                  const double* __restrict__ W,
+                                                                  const double* __restrict__ c1,
+                                                                  double* __restrict__ qout, double* __restrict__ scal) {
   pdl_enter();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  double red[4] = {0, 0, 0, 0};
+  __shared__ float ps[SF_SPLIT][SF_ROWS][2];
+  const int r = threadIdx.x & (SF_ROWS - 1), k = threadIdx.x / SF_ROWS;
+  const int i = blockIdx.x * SF_ROWS + r;
+  Acc<float> a;
   if (i < rows) {
-    Acc<float> a;
-    for (int s = 0; s < nt; ++s) a.add(part[(size_t)s * npad + i]);
-    const double qr = a.value() + dpsi[0] * Sv[i];
+    // four independent loads in flight per round: the slots sit in different DRAM pages
+    for (int s = k; s < nt; s += 4 * SF_SPLIT) {
+      float v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int su = s + u * SF_SPLIT;
+        v[u] = su < nt ? part[(size_t)su * npad + i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a.add(v[u]);
+    }
+  }
+  ps[k][r][0] = a.s;
+  ps[k][r][1] = a.c;
+  __syncthreads();
+  double red[4] = {0, 0, 0, 0};
+  if (k == 0 && i < rows) {
+    Acc<float> t;
+    for (int j = 0; j < SF_SPLIT; ++j) {
+      t.add(ps[j][r][0]);
+      t.c += ps[j][r][1];
+    }
+    const double qr = t.value() + dpsi[0] * Sv[i];
     qout[i] = qr;
     const double bi = b[i];
     red[0] = qr;
@@ -149,7 +178,7 @@ __global__ void __launch_bounds__(256) k_sym_finish(int rows, int nt, int npad, 
     red[3] = W[2 * i + 1] * bi;
   }
 #pragma unroll
-  for (int k = 0; k < 4; ++k) red[k] = warp_sum(red[k]);
+  for (int q = 0; q < 4; ++q) red[q] = warp_sum(red[q]);
   double* const dst[4] = {scal + S_CQ0, scal + S_CQ1, scal + S_WB0, scal + S_WB1};
   block_atomic_add<4>(red, dst);
 }
@@ -195,7 +224,8 @@ int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* x
   CPM_CUDA(launch_pdl(k_sapply_sym, c->n_sm, SY_THREADS, sym_smem(npad), st, Sp, nt, n, xh, xl, c->sym_part, npad));
   ++c->launches;
   CPM_LAUNCH();
-  CPM_CUDA(launch_pdl(k_sym_finish, (n + 255) / 256, 256, 0, st, n, nt, npad, c->sym_part, b, dpsi, Sv, W, c1, qout, c->scal));
+  CPM_CUDA(launch_pdl(k_sym_finish, (n + SF_ROWS - 1) / SF_ROWS, SF_ROWS * SF_SPLIT, 0, st, n, nt, npad, c->sym_part, b,
+                      dpsi, Sv, W, c1, qout, c->scal));
   ++c->launches;
   CPM_LAUNCH();
   return CPM_OK;
