@@ -36,6 +36,8 @@ def _cell(geometry="ff", seed=7, n_pairs=4):
     w = synth.tiny_cell(seed=seed, n_pairs=n_pairs, geometry=geometry)
     # alpha 0.35: no visible energy jumps at the real-space cutoff; fine order-8 mesh: SPME close to Ewald
     lx, ly, lz = w.box
+    if geometry == "slab":
+        lz = lz * w.slab_factor                        # the mesh spans the padded Ewald box
     grid = tuple(int(2 * round(L / 0.45 / 2)) for L in (lx, ly, lz))
     return dataclasses.replace(w, alpha=0.35, grid=grid, order=8)
 
@@ -75,7 +77,7 @@ def test_lennard_jones_forces_and_energy_against_oracle(prec):
     assert res[0.0][1]["U_lj"] == 0.0
 
 
-@pytest.mark.parametrize("geometry,k,t_damp", [("ff", 1, 0.0), ("ff", 3, 50.0), ("dc", 2, 50.0)])
+@pytest.mark.parametrize("geometry,k,t_damp", [("ff", 1, 0.0), ("ff", 3, 50.0), ("dc", 2, 50.0), ("slab", 2, 50.0)])
 def test_trajectory_against_oracle(geometry, k, t_damp):
     g, System, MD = _lib()
     w = _cell(geometry)
