@@ -464,34 +464,6 @@ def run_gb300(args):
         dist.destroy_process_group()
 
 
-def tune_md_pairs(g, m, s, k, dev, flush):
-    """The real-space pair kernels inside the MD loop (Lennard-Jones fused, most steps at fixed
-    charges): time graph replays of one k-step block for each pair-kernel form and z group, L2
-    flushed before each, and keep the fastest (median of five)."""
-    import torch
-    best = None
-    for pv, gz in (("cell", 1), ("cell", 2), ("warp-elyt", 1), ("warp", 1)):
-        g.cpm_set_pair_variant(s.ctx, pv)
-        g.cpm_set_pair_group(s.ctx, gz)
-        replay = m.capture(k, energy=False)
-        replay(2)
-        ts = []
-        for _ in range(5):
-            flush.zero_()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record()
-            replay.graph.replay()
-            e1.record()
-            torch.cuda.synchronize(dev)
-            ts.append(e0.elapsed_time(e1))
-        g.cpm_md_advance(m.md, 5 * k)
-        med = sorted(ts)[2]
-        if best is None or med < best[0]:
-            best = (med, pv, gz)
-    g.cpm_set_pair_variant(s.ctx, best[1])
-    g.cpm_set_pair_group(s.ctx, best[2])
-
-
 def run_md(args):
     """MD workloads: a timed step is one velocity-Verlet time step of the whole MD loop (thermostat,
     kicks, drift, CPM electrostatics with charges re-solved every k steps and held in between,
@@ -521,7 +493,7 @@ def run_md(args):
         raise RuntimeError(f"device status after warm-up: {g.cpm_strerror(st)}")
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     if args.pair_variant == "auto" and args.pair_group == 0:
-        tune_md_pairs(g, m, s, k, dev, flush)
+        m.tune()                                  # pair-kernel form and z group on the MD block itself
     l0 = g.cpm_counters(s.ctx)
     m.run(k, energy=True)
     torch.cuda.synchronize(dev)

@@ -176,6 +176,37 @@ class MD:
         torch.cuda.synchronize(s.device)
         cpm_md_set_state(self.md, ck["step"], ck["thermo"])
 
+    def tune(self, flush_bytes=256 << 20, replays=5):
+        """Choose the real-space pair-kernel form and z group for this MD loop (the step autotuner
+        times a charge re-solve without the Lennard-Jones term; here most steps keep their
+        charges): graph replays of one charge_every-step block per candidate, a buffer larger than
+        L2 written before each, median of `replays`.  Returns (variant, z group)."""
+        from . import cpm_md_advance, cpm_set_pair_group, cpm_set_pair_variant
+        k = self.params.charge_every
+        flush = torch.empty(flush_bytes, dtype=torch.uint8, device=self.s.device)
+        best = None
+        for pv, gz in (("cell", 1), ("cell", 2), ("warp-elyt", 1), ("warp", 1)):
+            cpm_set_pair_variant(self.s.ctx, pv)
+            cpm_set_pair_group(self.s.ctx, gz)
+            replay = self.capture(k, energy=False)
+            replay(2)
+            ts = []
+            for _ in range(replays):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                replay.graph.replay()
+                e1.record()
+                torch.cuda.synchronize(self.s.device)
+                ts.append(e0.elapsed_time(e1))
+            cpm_md_advance(self.md, replays * k)
+            med = sorted(ts)[len(ts) // 2]
+            if best is None or med < best[0]:
+                best = (med, pv, gz)
+        cpm_set_pair_variant(self.s.ctx, best[1])
+        cpm_set_pair_group(self.s.ctx, best[2])
+        return best[1], best[2]
+
     def capture(self, n_steps, energy=False):
         """A CUDA graph of one cpm_md_run of n_steps (capture on a side stream).  Replaying it
         advances n_steps; call `replay` to keep the library's step index in step."""
