@@ -297,6 +297,19 @@ __device__ __forceinline__ int wrap_index(int i, int n) {
   return i < 0 ? i + n : i;
 }
 
+// Periodic wrap of a stencil index j = base - t of the per-site mesh kernels, whose base lies in
+// [0, K + 1] and t in [0, p) with K >= 2 p: j is within [-K, 2K), so one conditional add or
+// subtract suffices (no integer division); the final clamp keeps any input in bounds.
+__device__ __forceinline__ int wrap_near(int j, int n) {
+  j += j < 0 ? n : 0;
+  j -= j >= n ? n : 0;
+  return min(max(j, 0), n - 1);
+}
+
+// Row and column of stencil task t of a p x p tile: (t + 1/2) / p is never within 1 / (2p) of an
+// integer, so the float product rounds to the exact quotient.
+__device__ __forceinline__ int task_row(int t, float inv_p) { return (int)(((float)t + 0.5f) * inv_p); }
+
 __device__ __forceinline__ void latch_error(int* status, int bit) { atomicOr(status, bit); }
 
 // Programmatic dependent launch: kernels of the per-step chains are launched with the

@@ -908,6 +908,7 @@ __device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, const int* __
   const int n = min(off[rep + 1] - off[rep], cap);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const float inv_p = 1.0f / (float)P;
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const int nw = (nbx * blockDim.x) >> 5;
   const int first = (bx * blockDim.x + threadIdx.x) >> 5;
@@ -916,11 +917,11 @@ __device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, const int* __
     const auto p = l_tmp[k];
     site_weights<T>(p, cell_coords(l_cell[k], sg), sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
     for (int task = lane; task < P * P; task += 32) {
-      const int ty = task / P, tz = task - ty * P;
-      const int gy = wrap_index(si0[wib][1] - ty, K2), gz = wrap_index(si0[wib][2] - tz, K3);
+      const int ty = task_row(task, inv_p), tz = task - ty * P;
+      const int gy = wrap_near(si0[wib][1] - ty, K2), gz = wrap_near(si0[wib][2] - tz, K3);
       const T wyz = p.w * sw[wib][1][ty] * sw[wib][2][tz];
       for (int tx = 0; tx < P; ++tx) {
-        const int gx = wrap_index(si0[wib][0] - tx, K1);
+        const int gx = wrap_near(si0[wib][0] - tx, K1);
         atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], sw[wib][0][tx] * wyz);
       }
     }
@@ -936,6 +937,7 @@ __device__ __forceinline__ void spread_elec_sites(int bx, int nbx, const T* __re
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const float inv_p = 1.0f / (float)P;
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const T* qr = qT + (size_t)rep * ne;
   for (int i = (bx * blockDim.x + threadIdx.x) >> 5; i < ne; i += (nbx * blockDim.x) >> 5) {
@@ -943,11 +945,11 @@ __device__ __forceinline__ void spread_elec_sites(int bx, int nbx, const T* __re
     const int4 b = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
     for (int task = lane; task < P * P; task += 32) {
-      const int ty = task / P, tz = task - ty * P;
-      const int gy = wrap_index(b.y - ty, K2), gz = wrap_index(b.z - tz, K3);
+      const int ty = task_row(task, inv_p), tz = task - ty * P;
+      const int gy = wrap_near(b.y - ty, K2), gz = wrap_near(b.z - tz, K3);
       const T wyz = qi * w[PMAX + ty] * w[2 * PMAX + tz];
       for (int tx = 0; tx < P; ++tx) {
-        const int gx = wrap_index(b.x - tx, K1);
+        const int gx = wrap_near(b.x - tx, K1);
         atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], w[tx] * wyz);
       }
     }
@@ -1029,17 +1031,18 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const float inv_p = 1.0f / (float)P;
   const T* m = phi + (size_t)rep * sg.Mr_s;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const int4 bs = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
     Acc<T> acc;
     for (int task = lane; task < P * P; task += 32) {
-      const int ty = task / P, tz = task - ty * P;
-      const int gy = wrap_index(bs.y - ty, K2), gz = wrap_index(bs.z - tz, K3);
+      const int ty = task_row(task, inv_p), tz = task - ty * P;
+      const int gy = wrap_near(bs.y - ty, K2), gz = wrap_near(bs.z - tz, K3);
       T s = 0;
       for (int tx = 0; tx < P; ++tx) {
-        const int gx = wrap_index(bs.x - tx, K1);
+        const int gx = wrap_near(bs.x - tx, K1);
         s += w[tx] * m[((size_t)gx * K2 + gy) * K3 + gz];
       }
       acc.add(s * w[PMAX + ty] * w[2 * PMAX + tz]);
@@ -1077,6 +1080,7 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
   const int n = min(off[rep + 1] - o, cap);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const float inv_p = 1.0f / (float)P;
   const T* m = phi + (size_t)rep * sg.Mr_s;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1086,11 +1090,11 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
     site_weights<T>(p, cell_coords(l_cell[k], sg), sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
     T gx = 0, gy = 0, gz = 0;
     for (int task = lane; task < P * P; task += 32) {
-      const int ty = task / P, tz = task - ty * P;
-      const int jy = wrap_index(si0[wib][1] - ty, K2), jz = wrap_index(si0[wib][2] - tz, K3);
+      const int ty = task_row(task, inv_p), tz = task - ty * P;
+      const int jy = wrap_near(si0[wib][1] - ty, K2), jz = wrap_near(si0[wib][2] - tz, K3);
       T a = 0, ad = 0;
       for (int tx = 0; tx < P; ++tx) {
-        const int jx = wrap_index(si0[wib][0] - tx, K1);
+        const int jx = wrap_near(si0[wib][0] - tx, K1);
         const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
         a += sw[wib][0][tx] * ph;
         ad += sdw[wib][0][tx] * ph;
@@ -1129,6 +1133,7 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
+  const float inv_p = 1.0f / (float)P;
   const T* m = phi + (size_t)rep * sg.Mr_s;
   for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
     const int4 bs = base[i];
@@ -1136,11 +1141,11 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
     const T* dw = dth + (size_t)i * 3 * PMAX;
     T gx = 0, gy = 0, gz = 0;
     for (int task = lane; task < P * P; task += 32) {
-      const int ty = task / P, tz = task - ty * P;
-      const int jy = wrap_index(bs.y - ty, K2), jz = wrap_index(bs.z - tz, K3);
+      const int ty = task_row(task, inv_p), tz = task - ty * P;
+      const int jy = wrap_near(bs.y - ty, K2), jz = wrap_near(bs.z - tz, K3);
       T a = 0, ad = 0;
       for (int tx = 0; tx < P; ++tx) {
-        const int jx = wrap_index(bs.x - tx, K1);
+        const int jx = wrap_near(bs.x - tx, K1);
         const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
         a += w[tx] * ph;
         ad += dw[tx] * ph;
