@@ -429,6 +429,41 @@ __device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, co
   __syncwarp();
 }
 
+// B-spline weights of a batch of up to kSiteBatch electrolyte sites per warp: lane 3 s + d computes
+// axis d of site s (s < nb), so one pass of the recursion serves nb sites instead of one (the
+// stencil sweeps that follow use all 32 lanes per site).  Writes w / dw [s][d][t], the base mesh
+// index b0 [s][d] and the charge q [s]; ends with __syncwarp.
+constexpr int kSiteBatch = 10;
+template <typename T>
+__device__ __forceinline__ void batch_weights(int i0, int n, int nb, size_t kbase,
+                                              const typename Vec4<T>::type* __restrict__ l_tmp,
+                                              const int* __restrict__ l_cell, const SpmeGeom& sg,
+                                              const int* __restrict__ splI, const T* __restrict__ splF, int lane,
+                                              T (*w)[3][PMAX], T (*dw)[3][PMAX], int (*b0)[3], T* q) {
+  const int s = lane / 3, d = lane - 3 * s;
+  if (s < nb && i0 + s < n) {
+    const size_t k = kbase + i0 + s;
+    const auto p = l_tmp[k];
+    const int4 cc = cell_coords(l_cell[k], sg);
+    const T loc = d == 0 ? p.x : (d == 1 ? p.y : p.z);
+    const int c = d == 0 ? cc.x : (d == 1 ? cc.y : cc.z);
+    const int ti = (d == 0 ? sg.spl_off[0] : (d == 1 ? sg.spl_off[1] : sg.spl_off[2])) + c;
+    const T kl = (T)(d == 0 ? sg.kl[0] : (d == 1 ? sg.kl[1] : sg.kl[2]));
+    const T u = splF[ti] + loc * kl;
+    const T fl = floor(u);
+    T wl[PMAX], dl[PMAX];
+    bspline<T>(u - fl, sg.P, wl, dl);
+#pragma unroll
+    for (int t = 0; t < PMAX; ++t) {
+      w[s][d][t] = wl[t];
+      if (dw) dw[s][d][t] = dl[t];
+    }
+    b0[s][d] = splI[ti] + (int)fl;
+    if (d == 0) q[s] = p.w;
+  }
+  __syncwarp();
+}
+
 // Electrolyte charges onto the mesh, in input order: k_bin's cell-local coordinates and cell index
 // per site (no dependence on the sorted cell list, which is built concurrently on the side stream).
 

@@ -897,13 +897,14 @@ __global__ void __launch_bounds__(PW_THREADS) k_pair_warp(const CellPairTgt t, c
 // handle axes x, y, z).  Its mesh coordinate u = (cell origin) + (local offset) K/L uses the
 // per-cell integer / fraction tables, so only the small local part is formed in precision T.
 template <typename T>
-__device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, const int* __restrict__ off, int cap,
+__device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, int nb, const int* __restrict__ off, int cap,
                                                   const SpmeGeom sg,
                                                   const typename Vec4<T>::type* __restrict__ l_tmp,
                                                   const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                   const T* __restrict__ splF, T* __restrict__ mesh) {
-  __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
-  __shared__ int si0[8][3];
+  __shared__ T sw[8][kSiteBatch][3][PMAX];
+  __shared__ int si0[8][kSiteBatch][3];
+  __shared__ T sq[8][kSiteBatch];
   const int rep = blockIdx.y;
   const int n = min(off[rep + 1] - off[rep], cap);
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -912,17 +913,22 @@ __device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, const int* __
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const int nw = (nbx * blockDim.x) >> 5;
   const int first = (bx * blockDim.x + threadIdx.x) >> 5;
-  for (int i = first; i < n; i += nw) {
-    const size_t k = (size_t)rep * cap + i;
-    const auto p = l_tmp[k];
-    site_weights<T>(p, cell_coords(l_cell[k], sg), sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
-    for (int task = lane; task < P * P; task += 32) {
-      const int ty = task_row(task, inv_p), tz = task - ty * P;
-      const int gy = wrap_near(si0[wib][1] - ty, K2), gz = wrap_near(si0[wib][2] - tz, K3);
-      const T wyz = p.w * sw[wib][1][ty] * sw[wib][2][tz];
-      for (int tx = 0; tx < P; ++tx) {
-        const int gx = wrap_near(si0[wib][0] - tx, K1);
-        atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], sw[wib][0][tx] * wyz);
+  // warp-batches of nb consecutive sites: the weights of the batch in one pass, then each site's stencil
+  for (int i0 = first * nb; i0 < n; i0 += nw * nb) {
+    batch_weights<T>(i0, n, nb, (size_t)rep * cap, l_tmp, l_cell, sg, splI, splF, lane, sw[wib], nullptr, si0[wib],
+                     sq[wib]);
+    const int cnt = min(nb, n - i0);
+    for (int si = 0; si < cnt; ++si) {
+      const T qv = sq[wib][si];
+      const int* b0 = si0[wib][si];
+      for (int task = lane; task < P * P; task += 32) {
+        const int ty = task_row(task, inv_p), tz = task - ty * P;
+        const int gy = wrap_near(b0[1] - ty, K2), gz = wrap_near(b0[2] - tz, K3);
+        const T wyz = qv * sw[wib][si][1][ty] * sw[wib][si][2][tz];
+        for (int tx = 0; tx < P; ++tx) {
+          const int gx = wrap_near(b0[0] - tx, K1);
+          atomicAdd(&m[((size_t)gx * K2 + gy) * K3 + gz], sw[wib][si][0][tx] * wyz);
+        }
       }
     }
     __syncwarp();
@@ -960,12 +966,12 @@ __device__ __forceinline__ void spread_elec_sites(int bx, int nbx, const T* __re
 // Electrolyte charges onto the mesh (warp per site, input order), electrode charges through their
 // fixed stencils, and both in one launch (blocks [0, nb_elyt) take the electrolyte).
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_elyt(const int* __restrict__ off, int cap, SpmeGeom sg,
+__global__ void __launch_bounds__(256) k_spread_elyt(int nb, const int* __restrict__ off, int cap, SpmeGeom sg,
                                                      const typename Vec4<T>::type* __restrict__ l_tmp,
                                                      const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                      const T* __restrict__ splF, T* __restrict__ mesh) {
   pdl_enter();
-  spread_elyt_sites<T>(blockIdx.x, gridDim.x, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
+  spread_elyt_sites<T>(blockIdx.x, gridDim.x, nb, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
 }
 
 template <typename T>
@@ -975,7 +981,8 @@ __global__ void __launch_bounds__(256) k_spread_elec(const T* __restrict__ qT, i
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_spread_all(int nb_elyt, const int* __restrict__ off, int cap, SpmeGeom sg,
+__global__ void __launch_bounds__(256) k_spread_all(int nb_elyt, int nb, const int* __restrict__ off, int cap,
+                                                    SpmeGeom sg,
                                                     const typename Vec4<T>::type* __restrict__ l_tmp,
                                                     const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                     const T* __restrict__ splF, const T* __restrict__ qT, int ne,
@@ -983,7 +990,7 @@ __global__ void __launch_bounds__(256) k_spread_all(int nb_elyt, const int* __re
                                                     T* __restrict__ mesh) {
   pdl_enter();
   if ((int)blockIdx.x < nb_elyt)
-    spread_elyt_sites<T>(blockIdx.x, nb_elyt, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
+    spread_elyt_sites<T>(blockIdx.x, nb_elyt, nb, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
   else
     spread_elec_sites<T>(blockIdx.x - nb_elyt, gridDim.x - nb_elyt, qT, ne, base, th, sg, mesh);
 }
@@ -1064,7 +1071,7 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
 // k-space force on the electrolyte sites (input order): F = -Q grad(phi_mesh) + Q E_z z-hat plus the
 // real-space force f_pair, written (not added) at the site's index.  E_z = -dpsi / L_z (finite field) - KE 4 pi / V M_z (slab).
 template <typename T>
-__global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi, const int* __restrict__ off,
+__global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restrict__ phi, const int* __restrict__ off,
                                                        int cap, SpmeGeom sg,
                                                        const typename Vec4<T>::type* __restrict__ l_tmp,
                                                        const int* __restrict__ l_cell, const int* __restrict__ splI,
@@ -1073,8 +1080,9 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
                                                        const double* __restrict__ scal,
                                                        const double* __restrict__ f_pair, double* __restrict__ F) {
   pdl_enter();
-  __shared__ T sw[8][3][PMAX], sdw[8][3][PMAX];
-  __shared__ int si0[8][3];
+  __shared__ T sw[8][kSiteBatch][3][PMAX], sdw[8][kSiteBatch][3][PMAX];
+  __shared__ int si0[8][kSiteBatch][3];
+  __shared__ T sq[8][kSiteBatch];
   const int rep = blockIdx.y;
   const int o = off[rep];
   const int n = min(off[rep + 1] - o, cap);
@@ -1084,38 +1092,44 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(const T* __restrict__ phi
   const T* m = phi + (size_t)rep * sg.Mr_s;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  for (int i = first; i < n; i += nw) {
-    const size_t k = (size_t)rep * cap + i;
-    const auto p = l_tmp[k];
-    site_weights<T>(p, cell_coords(l_cell[k], sg), sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib]);
-    T gx = 0, gy = 0, gz = 0;
-    for (int task = lane; task < P * P; task += 32) {
-      const int ty = task_row(task, inv_p), tz = task - ty * P;
-      const int jy = wrap_near(si0[wib][1] - ty, K2), jz = wrap_near(si0[wib][2] - tz, K3);
-      T a = 0, ad = 0;
-      for (int tx = 0; tx < P; ++tx) {
-        const int jx = wrap_near(si0[wib][0] - tx, K1);
-        const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
-        a += sw[wib][0][tx] * ph;
-        ad += sdw[wib][0][tx] * ph;
+  const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
+  const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
+  for (int i0 = first * nb; i0 < n; i0 += nw * nb) {
+    batch_weights<T>(i0, n, nb, (size_t)rep * cap, l_tmp, l_cell, sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib],
+                     sq[wib]);
+    const int cnt = min(nb, n - i0);
+    for (int si = 0; si < cnt; ++si) {
+      const int* b0 = si0[wib][si];
+      const T (*w)[PMAX] = sw[wib][si];
+      const T (*dw)[PMAX] = sdw[wib][si];
+      T gx = 0, gy = 0, gz = 0;
+      for (int task = lane; task < P * P; task += 32) {
+        const int ty = task_row(task, inv_p), tz = task - ty * P;
+        const int jy = wrap_near(b0[1] - ty, K2), jz = wrap_near(b0[2] - tz, K3);
+        T a = 0, ad = 0;
+        for (int tx = 0; tx < P; ++tx) {
+          const int jx = wrap_near(b0[0] - tx, K1);
+          const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
+          a += w[0][tx] * ph;
+          ad += dw[0][tx] * ph;
+        }
+        const T wy = w[1][ty], wz = w[2][tz];
+        gx += ad * wy * wz;
+        gy += a * dw[1][ty] * wz;
+        gz += a * wy * dw[2][tz];
       }
-      const T wy = sw[wib][1][ty], wz = sw[wib][2][tz];
-      gx += ad * wy * wz;
-      gy += a * sdw[wib][1][ty] * wz;
-      gz += a * wy * sdw[wib][2][tz];
-    }
-    gx = warp_sum_t(gx);
-    gy = warp_sum_t(gy);
-    gz = warp_sum_t(gz);
-    if (lane == 0) {
-      const double q = (double)p.w;
-      const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
-      const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
-      const size_t gi = 3 * (size_t)(o + i);
-      const double* fp = f_pair + 3 * k;
-      F[gi + 0] = -q * (double)gx * sg.kl[0] + fp[0];
-      F[gi + 1] = -q * (double)gy * sg.kl[1] + fp[1];
-      F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf + fp[2];
+      gx = warp_sum_t(gx);
+      gy = warp_sum_t(gy);
+      gz = warp_sum_t(gz);
+      if (lane == 0) {
+        const int i = i0 + si;
+        const double q = (double)sq[wib][si];
+        const size_t gi = 3 * (size_t)(o + i);
+        const double* fp = f_pair + 3 * ((size_t)rep * cap + i);
+        F[gi + 0] = -q * (double)gx * sg.kl[0] + fp[0];
+        F[gi + 1] = -q * (double)gy * sg.kl[1] + fp[1];
+        F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf + fp[2];
+      }
     }
     __syncwarp();
   }
@@ -1818,6 +1832,14 @@ struct PhaseTimer {
   ~PhaseTimer() { stop(); }
 };
 
+// Electrolyte sites per warp-batch of the mesh kernels: one while the sites leave SMs idle, up to
+// kSiteBatch once every SM has about that many sites per resident warp.
+static int site_batch(const cpm_ctx* c, int cap, int nrep) {
+  const long long sites = (long long)cap * nrep;
+  const long long warps = (long long)std::max(1, c->n_sm) * 32;
+  return (int)std::max(1LL, std::min<long long>(kSiteBatch, sites / warps));
+}
+
 static int grid_for(long long warps_needed, int per_block_warps = 8, int max_blocks = 152 * 16) {
   long long b = (warps_needed + per_block_warps - 1) / per_block_warps;
   return (int)std::max(1LL, std::min<long long>(b, max_blocks));
@@ -1955,6 +1977,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   const T* splF = c->mixed ? (const T*)c->spl_F32 : (const T*)c->spl_F64;
   const size_t pc_smem = sizeof(V4) * kPairSrcCap;   // staged sources of the cell-block pair kernel
   const dim3 gsite((cap + 255) / 256, nrep);
+  const int sb = site_batch(c, cap, nrep);        // electrolyte sites per warp-batch of the mesh kernels
 
   const bool fork = c->prof_cap == 0;      // the profiler times phases one after another
   cudaStream_t sside = fork ? c->side : st;
@@ -2014,8 +2037,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         CPM_TRY(cpm_internal_spread_brick(c, nrep, l_loc, nullptr, st));
       } else {
         CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-        CPM_CUDA(launch_pdl(k_spread_elyt<T>, dim3(grid_for(cap), nrep), 256, 0, st, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                    (T*)c->mesh_r));
+        CPM_CUDA(launch_pdl(k_spread_elyt<T>, dim3(grid_for((cap + sb - 1) / sb), nrep), 256, 0, st, sb, off, cap, sg,
+                            l_tmp, c->l_cell, c->spl_I, splF, (T*)c->mesh_r));
         STEP_LAUNCH();
       }
     }
@@ -2186,9 +2209,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
         CPM_TRY(cpm_internal_spread_brick(c, nrep, l_loc, (const float*)qT, st));
       } else {
         CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
-        const int nb_l = grid_for(cap), nb_e = grid_for(ne);
-        CPM_CUDA(launch_pdl(k_spread_all<T>, dim3(nb_l + nb_e, nrep), 256, 0, st, nb_l, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF,
-                                                                 qT, ne, c->e_base, e_th, (T*)c->mesh_r));
+        const int nb_l = grid_for((cap + sb - 1) / sb), nb_e = grid_for(ne);
+        CPM_CUDA(launch_pdl(k_spread_all<T>, dim3(nb_l + nb_e, nrep), 256, 0, st, nb_l, sb, off, cap, sg, l_tmp, c->l_cell,
+                            c->spl_I, splF, qT, ne, c->e_base, e_th, (T*)c->mesh_r));
         STEP_LAUNCH();
       }
     }
@@ -2201,9 +2224,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     if (f_elyt && brick) {
       CPM_TRY(cpm_internal_gather_f_brick(c, nrep, off, l_loc, dpsi, ff_over_lz, slab_coef, f_elyt, st));
     } else if (f_elyt) {
-      CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for(cap), nrep), 256, 0, st, (const T*)c->mesh_phi, off, cap, sg, l_tmp,
-                                                                    c->l_cell, c->spl_I, splF, dpsi, ff_over_lz,
-                                                                    slab_coef, c->scal, c->f_pair, f_elyt));
+      CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for((cap + sb - 1) / sb), nrep), 256, 0, st, sb,
+                          (const T*)c->mesh_phi, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF, dpsi, ff_over_lz,
+                          slab_coef, c->scal, c->f_pair, f_elyt));
       STEP_LAUNCH();
     }
     if (f_elec) {
