@@ -313,15 +313,13 @@ __device__ __forceinline__ int task_row(int t, float inv_p) { return (int)(((flo
 __device__ __forceinline__ void latch_error(int* status, int bit) { atomicOr(status, bit); }
 
 // Programmatic dependent launch: kernels of the per-step chains are launched with the
-// programmatic-serialization attribute (launch_pdl), so the next kernel is scheduled while the
-// previous one drains; each such kernel first waits (griddepcontrol.wait) until its predecessor
-// grid has completed and its memory is visible, then lets its own successor be scheduled.  With
-// the wait first, the order of memory effects is that of plain stream order.  Without a
-// programmatic predecessor both instructions return at once.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;" ::: "memory");
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
+// programmatic-serialization attribute (launch_pdl), so the next kernel's launch overlaps the
+// previous one's exit; each such kernel first waits (griddepcontrol.wait) until its predecessor
+// grid has completed and its memory is visible.  With the wait first, the order of memory effects
+// is that of plain stream order.  No kernel triggers its dependents early: blocks of a successor
+// resident while a long predecessor runs were measured to slow it.  Without a programmatic
+// predecessor the wait returns at once.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
