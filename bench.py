@@ -213,9 +213,9 @@ PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distanc
 # captured: then traffic is null).  Summaries: profiles/dram_k_sapply32_k_pair_cell_paper-cell-ff-mixed.md,
 # profiles/dram_k_sapply_sym_k_pair_cell_large-cell-ff-mixed.md (the S-apply phase there is the packed
 # kernel plus its finishing kernel, so its traffic is the sum of both).  Set an entry to None whenever its kernel changes.
-NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.738304e6, "f_pair_elyt": 0.211328e6, "b_real": 0.11456e6},
+NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.74e6, "f_pair_elyt": 0.21248e6, "b_real": 0.1157e6},
                      "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {}, "paper-dc-md": {},
-                     "large": {"s_apply:sym": 212.27e6, "f_pair_elyt": 0.749824e6},
+                     "large": {"s_apply:sym": 212.28e6, "f_pair_elyt": 0.7493e6},
                      "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
