@@ -306,7 +306,6 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   const int wz = gzb + 2 * g.sten[2];                      // stencil extent in z for this group
   const int nsten = g.w[0] * g.w[1] * wz;
   const T alpha = (T)alpha_d;
-  const T c2pi = (T)1.1283791670955126;
   const T rc2 = (T)g.rc2;
   const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
   const V4* tl = (const V4*)t.loc + rep * t.loc_stride;
@@ -1975,7 +1974,6 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
   const T* e_th = c->mixed ? (const T*)c->e_th32 : (const T*)c->e_th64;
   const T* e_dth = c->mixed ? (const T*)c->e_dth32 : (const T*)c->e_dth64;
   const T* splF = c->mixed ? (const T*)c->spl_F32 : (const T*)c->spl_F64;
-  const size_t pc_smem = sizeof(V4) * kPairSrcCap;   // staged sources of the cell-block pair kernel
   const dim3 gsite((cap + 255) / 256, nrep);
   const int sb = site_batch(c, cap, nrep);        // electrolyte sites per warp-batch of the mesh kernels
 
