@@ -63,3 +63,38 @@ def test_batched_replicas():
 
 def test_plain_cell_grid():
     assert synth.config_plain_ff().grid == (18, 18, 60)
+
+
+def test_md_cell_point_ions_and_inputs():
+    w = synth.md_cell()
+    assert w.n_elec == 3024 and np.allclose(w.box, [38.34, 34.44, 168.0])
+    R, Q = w.elyt_xyz[0], w.elyt_q[0]
+    assert R.shape == (2000, 3) and abs(Q.sum()) < 1e-12
+    assert np.all(np.abs(np.abs(Q) - synth.ION_CHARGE) < 1e-12)
+    assert np.all((R[:, 2] >= 13.0) & (R[:, 2] <= 155.0))
+    assert _min_sep_xy_periodic(R, w.box) >= 3.0
+    mi = synth.md_inputs(w, seed=5)
+    assert np.array_equal(mi.types, np.where(Q > 0, 0, 1)) and not np.any(mi.groups)
+    # Maxwell-Boltzmann: <m v_d^2> = k_B T per component (2,000 x 3 samples: ~2 % spread)
+    m = np.asarray(mi.mass)[mi.types]
+    kt = (m[:, None] * mi.vel ** 2).mean() * synth.AMU_A2_FS2_EV
+    assert abs(kt / (synth.KB_EV * mi.temperature) - 1.0) < 0.06
+    assert abs(mi.vel.mean()) < 5 * mi.vel.std() / np.sqrt(mi.vel.size)
+
+
+def test_md_doubled_cell_thermostat_groups():
+    w = synth.md_cell(geometry="dc")
+    mi = synth.md_inputs(w)
+    z = w.elyt_xyz[0][:, 2]
+    assert w.n_elec == 6048 and len(z) == 4000
+    assert np.array_equal(mi.groups, (z >= 0.5 * w.box[2]).astype(np.int32))
+    assert mi.groups.sum() == 2000
+    # every ion stays inside its own sub-cell's electrolyte region (the electrodes separate them)
+    assert np.all((z[mi.groups == 0] > 13.0) & (z[mi.groups == 0] < 155.0))
+    assert np.all((z[mi.groups == 1] > 181.0) & (z[mi.groups == 1] < 323.0))
+
+
+def test_md_inputs_refuse_molecular_electrolytes():
+    import pytest
+    with pytest.raises(ValueError):
+        synth.md_inputs(synth.config_paper_cell())
