@@ -44,6 +44,7 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--oracle-out", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--kernels", default="auto",
                     help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
@@ -455,9 +456,16 @@ def run_gb300(args):
     if args.workload == "paper":
         out["batched"] = batched_replicas(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args) if args.workload == "paper" else {
-            "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
-            "sample": f"not run: the oracle's dense A for {w.n_elec:,} sites takes hours on the host"}
+        if args.workload == "paper":
+            out["cpu_baseline"], ref = cpu_baseline(args)
+            if ref is not None:
+                torch.cuda.synchronize(dev)
+                out["accuracy"] = accuracy_against(ref, s.q.cpu().numpy(), s.f_elyt.cpu().numpy(),
+                                                   s.energy[:4].cpu().numpy())
+        else:
+            out["cpu_baseline"] = {
+                "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
+                "sample": f"not run: the oracle's dense A for {w.n_elec:,} sites takes hours on the host"}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -593,7 +601,7 @@ def run_md(args):
            "phase_ms": {kk: round(v, 5) for kk, v in phase_ms.items()},
            "roofline": roof, "roofline_s_apply": roof_s}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args) if args.workload == "paper-md" else {
+        out["cpu_baseline"] = cpu_baseline(args)[0] if args.workload == "paper-md" else {
             "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
             "sample": "not run for this workload (see the paper-md line)"}
     if rank == 0:
@@ -655,13 +663,39 @@ def batched_replicas(args, dev, flush):
 # ----------------------------------------------------------------------------------------------
 def cpu_baseline(args):
     """One full oracle step of the same workload on this host, timed in a child process
-    (the oracle's A and its Cholesky factor are built first, untimed)."""
+    (the oracle's A and its Cholesky factor are built first, untimed).  The child also leaves its
+    charges, electrolyte forces and energies in a scratch file: the GPU run's errors against them
+    are the line's `accuracy`."""
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
     cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--seed", str(args.seed),
-           "--workload", args.workload]
-    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
-    if r.returncode != 0:
-        return {"value": None, "unit": "ns/day", "kind": "oracle", "error": r.stderr[-300:]}
-    return json.loads(r.stdout.strip().splitlines()[-1])
+           "--workload", args.workload, "--oracle-out", path]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
+        if r.returncode != 0:
+            return {"value": None, "unit": "ns/day", "kind": "oracle", "error": r.stderr[-300:]}, None
+        import numpy as np
+        with np.load(path) as z:
+            ref = {k: z[k] for k in z.files}
+        return json.loads(r.stdout.strip().splitlines()[-1]), ref
+    finally:
+        if os.path.exists(path):
+            os.remove(path)
+
+
+def accuracy_against(ref, q, f_elyt, energy):
+    """Errors of one GPU step against the oracle's step on the same input: max |dq| (e), RMS
+    relative force error on the electrolyte, relative error of U and of H."""
+    import numpy as np
+    q = np.asarray(q).reshape(-1)[: ref["q"].size]
+    F = np.asarray(f_elyt).reshape(-1, 3)[: ref["F_elyt"].shape[0]]
+    Fo = ref["F_elyt"]
+    return {"dq_max_e": float(np.abs(q - ref["q"]).max()),
+            "force_rms_rel": float(np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum())),
+            "energy_U_rel": float(abs(energy[0] - ref["U"]) / abs(ref["U"])),
+            "energy_H_rel": float(abs(energy[1] - ref["H"]) / abs(ref["H"])),
+            "reference": "FP64 CPU oracle (direct Ewald sums, KKT solve) on the same input"}
 
 
 def cpu_baseline_child(args):
@@ -669,8 +703,11 @@ def cpu_baseline_child(args):
     w = workload(args.seed, args.workload)
     ref = ocpm.Reference(w)
     t0 = time.perf_counter()
-    ref.step(0)
+    out = ref.step(0)
     dt = time.perf_counter() - t0
+    if args.oracle_out:
+        import numpy as np
+        np.savez(args.oracle_out, q=out["q"], F_elyt=out["F_elyt"], U=out["U"], H=out["H"])
     print(json.dumps({"value": round(NS_PER_DAY_PER_STEP_PER_S / dt, 6), "unit": "ns/day", "cores": os.cpu_count(),
                       "kind": "oracle", "seconds_per_step": round(dt, 3),
                       "sample": "one full FP64 oracle step (direct Ewald b, KKT solve with a prebuilt Cholesky "
