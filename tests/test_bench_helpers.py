@@ -1,0 +1,36 @@
+"""The benchmark's host-side helpers (CPU only): throughput aggregation, the FP32 peak model, the
+accuracy comparison against the oracle, and the consistency of the workload tables."""
+import numpy as np
+
+import bench
+
+
+def test_aggregate_and_units():
+    # 4 ranks x 100 steps in 50 ms (slowest rank): 8,000 steps/s; 2 fs per step
+    assert abs(bench.aggregate_steps_per_s(50.0, 100, 4) - 8000.0) < 1e-9
+    assert abs(bench.NS_PER_DAY_PER_STEP_PER_S - 2e-6 * 86400) < 1e-12
+    assert abs(bench.alu_peak_tflops(2070.0) - 152 * 128 * 2 * 2.07e9 / 1e12) < 1e-9
+
+
+def test_accuracy_against_the_oracle_record():
+    rng = np.random.default_rng(1)
+    ref = {"q": rng.normal(size=50), "F_elyt": rng.normal(size=(20, 3)), "U": np.float64(-12.5),
+           "H": np.float64(-20.0)}
+    q = ref["q"] + np.r_[3e-7, np.zeros(49)]
+    F = ref["F_elyt"] * 1.001
+    acc = bench.accuracy_against(ref, np.r_[q, [9.0]], np.r_[F.reshape(-1), [5.0, 5.0, 5.0]],
+                                 np.array([-12.5 * (1 + 2e-6), -20.0, 0.0, 0.0]))
+    assert abs(acc["dq_max_e"] - 3e-7) < 1e-15                    # trailing padding ignored
+    assert abs(acc["force_rms_rel"] - 1e-3) < 1e-12
+    assert abs(acc["energy_U_rel"] - 2e-6) < 1e-12 and acc["energy_H_rel"] == 0.0
+
+
+def test_workload_tables_are_consistent():
+    for name in bench.WORKLOADS:
+        assert name in bench.GEOMETRY_NAME and name in bench.NCU_TRAFFIC_MIXED
+        assert isinstance(bench.WORKLOADS[name][1], int)
+    assert set(bench.MD_WORKLOADS) <= set(bench.WORKLOADS)
+    w = bench.workload(bench.WORKLOADS["paper-md"][1], "paper-md")
+    assert w.n_elec == 3024 and len(w.elyt_q[0]) == 2000 and bench.GEOMETRY_NAME["paper-md"] == "finite field"
+    w = bench.workload(bench.WORKLOADS["paper"][1], "paper")
+    assert w.n_elec == 3024 and w.grid == (40, 36, 168) and w.order == 5
