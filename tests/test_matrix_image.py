@@ -117,3 +117,18 @@ def test_driver_file_cache_round_trips(g, tmp_path):
     f.write_bytes(f.read_bytes()[:-16])
     c = System(w, "mixed", order=8, cache_dir=str(tmp_path))
     assert not c.from_cache
+
+
+@pytest.mark.gpu
+def test_slab_mesh_form_image_round_trips(g):
+    """The slab geometry with the mesh form of A (whose key includes the mesh and order)."""
+    from paper_2201_12963_gb300.driver import System
+    w = synth.tiny_cell(n_pairs=4, geometry="slab")
+    w = dataclasses.replace(w, grid=(20, 16, 216))
+    a = System(w, "mixed", order=8, matrix_kspace="mesh")
+    img = g.cpm_matrix_image(a.ctx)
+    ctx_b = g.cpm_build_matrix_from_image(a.params, w.elec_xyz, w.elec_side, None, img)
+    assert np.array_equal(g.cpm_copy_matrix(ctx_b, 0), g.cpm_copy_matrix(a.ctx, 0))
+    other = g.make_params(w.box, w.eta, w.alpha, w.rcut, (20, 16, 224), 8, "slab", "mixed", matrix_kspace="mesh")
+    with pytest.raises(g.CPMError):
+        g.cpm_build_matrix_from_image(other, w.elec_xyz, w.elec_side, None, img)

@@ -289,3 +289,34 @@ def test_replica_batch_equals_replicas_alone():
         er = mr.energies()[0]
         for key in ("KE", "H", "U_lj", "E_total"):
             assert abs(e_b[r][key] - er[key]) <= 1e-8 * max(1.0, abs(er[key])), key
+
+
+def test_replica_without_electrolyte():
+    """A replica with no electrolyte sites runs beside a populated one: its thermostat slot has no
+    degrees of freedom (left untouched), its charges follow its potential difference alone, and
+    the populated replica is unaffected."""
+    g, System, MD = _lib()
+    w0 = _cell(n_pairs=4, seed=7)
+    empty = np.zeros((0, 3))
+    wb = dataclasses.replace(w0, elyt_xyz=[w0.elyt_xyz[0], empty], elyt_q=[w0.elyt_q[0], np.zeros(0)],
+                             dpsi=np.array([1.0, 2.0]))
+    mi0 = synth.md_inputs(wb, seed=41, r=0)
+    mi1 = synth.md_inputs(wb, seed=42, r=1)
+    s = System(wb, "fp64", order=8)
+    m = MD(s, [mi0, mi1], dt=2.0, charge_every=2, lj_cut=7.0, t_damp=40.0)
+    m.run(4, energy=True)
+    assert g.cpm_status(s.ctx) == 0
+    ck = m.checkpoint()
+    assert np.all(ck["thermo"][1] == 0.0)
+    e = m.energies()
+    assert e[1]["KE"] == 0.0 and e[1]["T"] == 0.0 and np.isfinite(e[1]["H"])
+    sr = System(wb.replica(0), "fp64", order=8)
+    mr = MD(sr, [mi0], dt=2.0, charge_every=2, lj_cut=7.0, t_damp=40.0)
+    mr.run(4, energy=True)
+    cr = mr.checkpoint()
+    n0 = len(w0.elyt_q[0])
+    assert np.max(np.abs(_wrapdiff(ck["xyzq"][:n0, :3], cr["xyzq"][:, :3], np.asarray(wb.box)))) <= 1e-9
+    # the empty replica's charges: the response to its potential difference alone (b = 0)
+    ne = w0.n_elec
+    sv = g.cpm_copy_matrix(s.ctx, 1)
+    assert np.max(np.abs(ck["q"][ne:] - 2.0 * sv)) <= 1e-9
