@@ -4,11 +4,11 @@
 // a point ion with a Lennard-Jones type.
 //
 // Integrator (per step, all on the caller's stream):
-//   thermostat half step(s) -> combined velocity scale s per (replica, group)      k_md_nh
+//   thermostat half step(s) -> combined velocity scale s per (replica, group)      k_md_kick_ke (last block)
 //   v = s v + dt/2 F/m ; x += dt v ; x, y wrapped into the cell                    k_md_kick_drift
 //   forces at the new positions: cpm_step (charges re-solved when the step index is a multiple of
 //     k) or cpm_forces (charges held), the Lennard-Jones term added by the same force pass
-//   v += dt/2 F/m and the kinetic energy per (replica, group)                      k_md_kick_ke
+//   v += dt/2 F/m and the kinetic energy per (replica, group), then the thermostat   k_md_kick_ke
 // The thermostat is one Nose-Hoover variable per group, propagated by the symmetric Trotter
 // splitting of Martyna, Tuckerman, Tobias and Klein (Mol. Phys. 87, 1117 (1996)): a half step is a
 // quarter-step update of v_xi, the scaling exp(-v_xi dt / 2), xi += v_xi dt / 2 and a second
@@ -66,10 +66,52 @@ __global__ void __launch_bounds__(256) k_md_kick_drift(int n, double* __restrict
   x[2] = fma(dt, v2, x[2]);
 }
 
-// v += dt/2 F/m (kick != 0) and the kinetic energy per (replica, group) slot into ke (zeroed before).
+constexpr int NH_LEAD = 1, NH_TRAIL = 2;
+
+// Thermostat half step(s) of slot i on its kinetic energy K: the trailing half of one time step
+// (NH_TRAIL) and / or the leading half of the next (NH_LEAD); writes the combined velocity scale
+// and the kinetic energy after it.
+__device__ __forceinline__ void nh_update(int i, int mode, double K, double* __restrict__ thermo,
+                                          const double* __restrict__ ndof, const double* __restrict__ Qm, double kT,
+                                          double dt, double* __restrict__ s_out, double* __restrict__ kcur) {
+  double xi = thermo[2 * i], vxi = thermo[2 * i + 1];
+  double stot = 1.0;
+  const double g = ndof[i], Q = Qm[i];
+  if (g > 0.0 && Q > 0.0) {
+    for (int half = 0; half < 2; ++half) {
+      if (!(mode & (half == 0 ? NH_TRAIL : NH_LEAD))) continue;
+      vxi += 0.25 * dt * (2.0 * K - g * kT) / Q;
+      const double s = exp(-0.5 * dt * vxi);
+      K *= s * s;
+      xi += 0.5 * dt * vxi;
+      vxi += 0.25 * dt * (2.0 * K - g * kT) / Q;
+      stot *= s;
+    }
+  }
+  thermo[2 * i] = xi;
+  thermo[2 * i + 1] = vxi;
+  s_out[i] = stot;
+  kcur[i] = K;
+}
+
+struct MdThermo {              // the thermostat step fused into k_md_kick_ke (mode 0: none)
+  int mode, nslots;
+  double* thermo;
+  const double* ndof;
+  const double* Qm;
+  double kT, dt;
+  double* s_out;
+  double* kcur;
+  unsigned int* done;          // blocks finished (the last one runs the thermostat and resets it)
+};
+
+// v += dt/2 F/m (kick != 0) and the kinetic energy per (replica, group) slot into ke (zero on
+// entry).  With a thermostat step (th.mode != 0) the last block to finish applies it to every slot
+// and zeroes ke for the next accumulation.
 __global__ void __launch_bounds__(256) k_md_kick_ke(int n, double* __restrict__ vel, const double* __restrict__ F,
                                                     const int* __restrict__ type, const int* __restrict__ slot,
-                                                    const double* __restrict__ mt, int kick, double* __restrict__ ke) {
+                                                    const double* __restrict__ mt, int kick, double* __restrict__ ke,
+                                                    MdThermo th) {
   pdl_enter();
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -102,37 +144,20 @@ __global__ void __launch_bounds__(256) k_md_kick_ke(int n, double* __restrict__ 
     if (lane == leader) atomicAdd(&ke[s], part);
     todo &= ~__ballot_sync(0xffffffffu, mine);
   }
-}
-
-constexpr int NH_LEAD = 1, NH_TRAIL = 2;
-
-// One thread per (replica, group): thermostat half step(s) on the kinetic energy ke; writes the
-// combined velocity scale and the kinetic energy after it.
-__global__ void k_md_nh(int nslots, int mode, const double* __restrict__ ke, double* __restrict__ thermo,
-                        const double* __restrict__ ndof, const double* __restrict__ Qm, double kT, double dt,
-                        double* __restrict__ s_out, double* __restrict__ kcur) {
-  pdl_enter();
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= nslots) return;
-  double K = ke[i];
-  double xi = thermo[2 * i], vxi = thermo[2 * i + 1];
-  double stot = 1.0;
-  const double g = ndof[i], Q = Qm[i];
-  if (g > 0.0 && Q > 0.0) {
-    for (int half = 0; half < 2; ++half) {
-      if (!(mode & (half == 0 ? NH_TRAIL : NH_LEAD))) continue;
-      vxi += 0.25 * dt * (2.0 * K - g * kT) / Q;
-      const double s = exp(-0.5 * dt * vxi);
-      K *= s * s;
-      xi += 0.5 * dt * vxi;
-      vxi += 0.25 * dt * (2.0 * K - g * kT) / Q;
-      stot *= s;
-    }
+  if (th.mode == 0) return;                       // uniform over the grid
+  __shared__ bool last;
+  __threadfence();                                // this block's sums are visible before its ticket
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(th.done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < th.nslots; i += blockDim.x) {
+    const double K = __ldcg(ke + i);
+    nh_update(i, th.mode, K, th.thermo, th.ndof, th.Qm, th.kT, th.dt, th.s_out, th.kcur);
+    ke[i] = 0.0;
   }
-  thermo[2 * i] = xi;
-  thermo[2 * i + 1] = vxi;
-  s_out[i] = stot;
-  kcur[i] = K;
+  if (threadIdx.x == 0) *th.done = 0u;
 }
 
 __global__ void __launch_bounds__(256) k_md_scale(int n, double* __restrict__ vel, const int* __restrict__ slot,
@@ -195,7 +220,7 @@ struct cpm_md {
   double* F = nullptr;         // [n][3] forces at the current positions
   double* e_coul = nullptr;    // [nrep][NENERGY]
   double* thermo = nullptr;    // [nslots][2] (xi, v_xi)
-  double* ke = nullptr;        // [nslots]
+  double* ke = nullptr;        // [nslots + 1]: kinetic energies, then the block counter of the fused thermostat
   double* kcur = nullptr;      // [nslots]
   double* s = nullptr;         // [nslots]
   double* ndof = nullptr;      // [nslots]
@@ -323,7 +348,7 @@ extern "C" int cpm_md_create(cpm_ctx* c, const cpm_md_params* p, int32_t n_rep, 
   MD_ALLOC(m->F, sizeof(double) * 3 * n1);
   MD_ALLOC(m->e_coul, sizeof(double) * NENERGY * n_rep);
   MD_ALLOC(m->thermo, sizeof(double) * 2 * ns);
-  MD_ALLOC(m->ke, sizeof(double) * ns);
+  MD_ALLOC(m->ke, sizeof(double) * (ns + 1));
   MD_ALLOC(m->kcur, sizeof(double) * ns);
   MD_ALLOC(m->s, sizeof(double) * ns);
   MD_ALLOC(m->ndof, sizeof(double) * ns);
@@ -398,28 +423,26 @@ extern "C" int cpm_md_run(cpm_md* m, int32_t n_steps, double* xyzq, double* vel,
   const double kT = KB_EV * m->p.temperature;
   const double dt = m->p.dt;
   const size_t kbytes = sizeof(double) * m->nslots;
-  const int nhb = (m->nslots + 127) / 128;
-  CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
-  CPM_CUDA(launch_pdl(k_md_kick_ke, nb, 256, 0, st, n, vel, m->F, m->type, m->slot, m->mt, 0, m->ke));
+  // With a thermostat each kick_ke launch ends by zeroing ke and its block counter, so only the
+  // first one of the call needs them cleared; without one ke is cleared before every launch.
+  MdThermo th{0, m->nslots, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur,
+              reinterpret_cast<unsigned int*>(m->ke + m->nslots)};
+  CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes + sizeof(double), st));
+  th.mode = thermostat && n_steps > 0 ? NH_LEAD : 0;
+  CPM_CUDA(launch_pdl(k_md_kick_ke, nb, 256, 0, st, n, vel, m->F, m->type, m->slot, m->mt, 0, m->ke, th));
   MD_LAUNCH(c);
-  if (thermostat && n_steps > 0) {
-    CPM_CUDA(launch_pdl(k_md_nh, nhb, 128, 0, st, m->nslots, NH_LEAD, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur));
-    MD_LAUNCH(c);
-  }
   for (int i = 0; i < n_steps; ++i) {
     CPM_CUDA(launch_pdl(k_md_kick_drift, nb, 256, 0, st, n, xyzq, vel, m->F, m->type, m->slot, thermostat ? m->s : nullptr, m->mt,
                                         dt, c->p.box[0], c->p.box[1]));
     MD_LAUNCH(c);
     ++m->step;
     CPM_TRY(force_eval(want_energy && i == n_steps - 1));
-    CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
-    CPM_CUDA(launch_pdl(k_md_kick_ke, nb, 256, 0, st, n, vel, m->F, m->type, m->slot, m->mt, 1, m->ke));
+    if (thermostat)
+      th.mode = i == n_steps - 1 ? NH_TRAIL : (NH_TRAIL | NH_LEAD);
+    else
+      CPM_CUDA(cudaMemsetAsync(m->ke, 0, kbytes, st));
+    CPM_CUDA(launch_pdl(k_md_kick_ke, nb, 256, 0, st, n, vel, m->F, m->type, m->slot, m->mt, 1, m->ke, th));
     MD_LAUNCH(c);
-    if (thermostat) {
-      const int mode = i == n_steps - 1 ? NH_TRAIL : (NH_TRAIL | NH_LEAD);
-      CPM_CUDA(launch_pdl(k_md_nh, nhb, 128, 0, st, m->nslots, mode, m->ke, m->thermo, m->ndof, m->Qm, kT, dt, m->s, m->kcur));
-      MD_LAUNCH(c);
-    }
   }
   if (thermostat && n_steps > 0) {
     CPM_CUDA(launch_pdl(k_md_scale, nb, 256, 0, st, n, vel, m->slot, m->s));
