@@ -453,8 +453,9 @@ def run_gb300(args):
            "gpu_launches": int(launches_per_step * K),
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
            "roofline": roof, "roofline_s_apply": roof_s}
+    q_batched = None
     if args.workload == "paper":
-        out["batched"] = batched_replicas(args, dev, flush)
+        out["batched"], q_batched = batched_replicas(args, dev, flush)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         if args.workload == "paper":
             out["cpu_baseline"], ref = cpu_baseline(args)
@@ -462,6 +463,11 @@ def run_gb300(args):
                 torch.cuda.synchronize(dev)
                 out["accuracy"] = accuracy_against(ref, s.q.cpu().numpy(), s.f_elyt.cpu().numpy(),
                                                    s.energy[:4].cpu().numpy())
+                if q_batched is not None and "q_batched" in ref:
+                    try:
+                        out["batched"]["accuracy"] = batched_accuracy(ref["q_batched"], q_batched)
+                    except Exception as e:      # the line is printed whatever this comparison does
+                        out["batched"]["accuracy"] = {"error": f"{type(e).__name__}: {e}"[:300]}
         else:
             out["cpu_baseline"] = {
                 "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
@@ -639,7 +645,8 @@ def graph_step_ms(s, flush, steps, dev):
 def batched_replicas(args, dev, flush):
     """Replica throughput: 64 replicas of the 672-site plain cell (400-600 point-ion pairs each,
     dpsi 0-4 V) in one batched step (mixed precision, tensor-core S-apply), against the plain
-    float64 path stepping one replica of the same cell."""
+    float64 path stepping one replica of the same cell.  Returns the line's object and the
+    batched step's charges [64, 672]."""
     import synth
     import paper_2201_12963_gb300 as g
     from paper_2201_12963_gb300.driver import System
@@ -648,6 +655,7 @@ def batched_replicas(args, dev, flush):
     sb = System(wb, "mixed", device=dev)
     ms_b = graph_step_ms(sb, flush, steps, dev)
     st = g.cpm_status(sb.ctx)
+    q_b = sb.results()["q"]
     w1 = wb.replica(0)
     s1 = System(w1, "fp64", device=dev)
     ms_1 = graph_step_ms(s1, flush, steps, dev)
@@ -655,7 +663,32 @@ def batched_replicas(args, dev, flush):
                         "mesh 18x18x60 order 5", "replicas": 64, "precision": "mixed, tcgen05 split-TF32 S-apply",
             "ms_per_step": round(ms_b, 5), "replica_steps_per_s": round(64 * 1e3 / ms_b, 1),
             "plain_fp64_one_replica": {"ms_per_step": round(ms_1, 5), "steps_per_s": round(1e3 / ms_1, 1)},
-            "speedup_replica_steps": round((64 / ms_b) / (1 / ms_1), 2), "status": st}
+            "speedup_replica_steps": round((64 / ms_b) / (1 / ms_1), 2), "status": st}, q_b
+
+
+def batched_oracle_charges(n_rep=64):
+    """The oracle's charges [n_rep, 672] for every replica of the batched workload (one A and
+    Cholesky factor for the shared electrode, one b and KKT solve per replica)."""
+    import numpy as np
+    import synth
+    from oracle import cpm as ocpm
+    wb = synth.config_batched(n_rep=n_rep)
+    ref = ocpm.Reference(wb.replica(0))
+    out = np.zeros((n_rep, wb.n_elec))
+    for r in range(n_rep):
+        out[r] = ref.charges(wb.elyt_xyz[r], wb.elyt_q[r], float(wb.dpsi[r]))[0]
+    return out
+
+
+def batched_accuracy(q_ref, q):
+    """Per-replica max |dq| (e) of the batched step's charges against the oracle's."""
+    import numpy as np
+    q_ref = np.asarray(q_ref)
+    q = np.asarray(q).reshape(q_ref.shape[0], -1)[:, : q_ref.shape[1]]
+    dq = np.abs(q - q_ref).max(axis=1)
+    return {"dq_max_e": float(dq.max()), "dq_max_e_per_replica": [float(f"{x:.3g}") for x in dq],
+            "replicas_within_1e-5_e": int((dq <= 1e-5).sum()), "replicas": int(dq.size),
+            "reference": "FP64 CPU oracle (direct Ewald b, KKT solve) per replica on the same input"}
 
 
 # ----------------------------------------------------------------------------------------------
@@ -707,7 +740,10 @@ def cpu_baseline_child(args):
     dt = time.perf_counter() - t0
     if args.oracle_out:
         import numpy as np
-        np.savez(args.oracle_out, q=out["q"], F_elyt=out["F_elyt"], U=out["U"], H=out["H"])
+        extra = {}
+        if args.workload == "paper":       # untimed: the batched line's per-replica accuracy
+            extra["q_batched"] = batched_oracle_charges()
+        np.savez(args.oracle_out, q=out["q"], F_elyt=out["F_elyt"], U=out["U"], H=out["H"], **extra)
     print(json.dumps({"value": round(NS_PER_DAY_PER_STEP_PER_S / dt, 6), "unit": "ns/day", "cores": os.cpu_count(),
                       "kind": "oracle", "seconds_per_step": round(dt, 3),
                       "sample": "one full FP64 oracle step (direct Ewald b, KKT solve with a prebuilt Cholesky "

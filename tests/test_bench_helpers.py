@@ -1,5 +1,6 @@
 """The benchmark's host-side helpers (CPU only): throughput aggregation, the FP32 peak model, the
-accuracy comparison against the oracle, and the consistency of the workload tables."""
+accuracy comparisons against the oracle (single step and per replica of the batch), and the
+consistency of the workload tables."""
 import numpy as np
 
 import bench
@@ -34,3 +35,21 @@ def test_workload_tables_are_consistent():
     assert w.n_elec == 3024 and len(w.elyt_q[0]) == 2000 and bench.GEOMETRY_NAME["paper-md"] == "finite field"
     w = bench.workload(bench.WORKLOADS["paper"][1], "paper")
     assert w.n_elec == 3024 and w.grid == (40, 36, 168) and w.order == 5
+
+
+def test_batched_accuracy_per_replica():
+    rng = np.random.default_rng(2)
+    q_ref = rng.normal(size=(3, 5))
+    q = q_ref.copy()
+    q[0, 2] += 1e-6
+    q[2, 4] -= 2e-5
+    acc = bench.batched_accuracy(q_ref, q.reshape(-1))
+    assert acc["dq_max_e_per_replica"] == [1e-6, 0.0, 2e-5]
+    assert abs(acc["dq_max_e"] - 2e-5) < 1e-15 and acc["replicas_within_1e-5_e"] == 2 and acc["replicas"] == 3
+
+
+def test_batched_oracle_charges_are_neutral_per_replica():
+    q = bench.batched_oracle_charges(n_rep=2)
+    assert q.shape == (2, 672) and np.all(np.isfinite(q))
+    assert np.max(np.abs(q.sum(axis=1))) <= 1e-12
+    assert np.max(np.abs(q[0] - q[1])) > 1e-3          # different electrolytes and dpsi (0 and 4 V)
