@@ -248,10 +248,20 @@ __global__ void __launch_bounds__(BR_THREADS) k_gather_f_brick(const __grid_cons
       if (!done) __nanosleep(32);
     }
     ok = (int)done;
-    if (!done) latch_error(status, DE_TIMEOUT);
+    if (!done) {
+      latch_error(status, DE_TIMEOUT);
+      // a second bounded wait for the copy still in flight into this block's shared memory
+      for (long long it = 0; it < BR_WAIT_LIMIT && !done; ++it) {
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(done)
+                     : "r"(br_smem(&mbar)), "r"(0)
+                     : "memory");
+        if (!done) __nanosleep(32);
+      }
+    }
   }
   __syncthreads();
-  if (!ok) return;       // the copy may still be in flight: the block ends without touching the brick
+  if (!ok) return;       // the brick is not used after a timed-out load
   const int P = sg.P;
   const int o = off[rep];
   const V4* lr = loc + (size_t)rep * cap;

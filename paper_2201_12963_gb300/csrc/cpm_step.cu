@@ -1552,7 +1552,18 @@ __global__ void __launch_bounds__(TC_THREADS) k_sapply_tc(const float* __restric
       done = r != 0;
       if (!done) __nanosleep(32);
     }
-    if (!done) s_abort = 1;
+    if (!done) {
+      s_abort = 1;
+      // a second bounded wait for MMAs still in flight: they read the staged operands and write
+      // the TMEM accumulator that is freed below
+      for (int it = 0; it < (1 << 22) && !done; ++it) {
+        uint32_t r;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                     : "=r"(r) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
+        done = r != 0;
+        if (!done) __nanosleep(32);
+      }
+    }
     phase ^= 1;
     __syncthreads();
     ok = (s_abort == 0);
