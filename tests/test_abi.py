@@ -3,6 +3,8 @@ no call here touches a GPU)."""
 import ctypes
 import os
 import re
+import subprocess
+import sys
 
 import numpy as np
 import pytest
@@ -66,3 +68,49 @@ def test_invalid_parameters_rejected_before_any_device_work(pkg):
     with pytest.raises(pkg.CPMError) as ei:
         pkg.cpm_build_matrix(pdc, xyz, side, None, stream=0)   # doubled cell needs sub-cell labels
     assert ei.value.status == -1
+
+
+def test_host_tensors_are_rejected(pkg):
+    """The entry points take device memory only: host tensors raise before any call, so there is
+    no path on which the step runs anywhere but in the library's kernels."""
+    torch = pytest.importorskip("torch")
+    off = torch.tensor([0, 2], dtype=torch.int32)
+    xyzq = torch.zeros(8, dtype=torch.float64)
+    dpsi = torch.zeros(1, dtype=torch.float64)
+    q = torch.zeros(4, dtype=torch.float64)
+    for fn in (pkg.cpm_step_charges, pkg.cpm_step, pkg.cpm_forces):
+        with pytest.raises(TypeError, match="CUDA"):
+            fn(None, 1, off, xyzq, dpsi, q)
+    with pytest.raises(TypeError, match="CUDA"):
+        pkg.cpm_energy(None, 1, off, xyzq, dpsi, q, torch.zeros(4, dtype=torch.float64))
+
+
+def test_import_fails_without_the_library(tmp_path):
+    """Importing the package with the shared library absent raises ImportError (no fallback)."""
+    code = (
+        "import importlib.util, sys\n"
+        f"spec = importlib.util.spec_from_file_location('paper_2201_12963_gb300.build', "
+        f"{os.path.join(ROOT, 'paper_2201_12963_gb300', 'build.py')!r})\n"
+        "mod = importlib.util.module_from_spec(spec)\n"
+        "spec.loader.exec_module(mod)\n"
+        f"mod.LIBDIR = {str(tmp_path)!r}\n"
+        "sys.modules['paper_2201_12963_gb300.build'] = mod\n"
+        "try:\n"
+        "    import paper_2201_12963_gb300\n"
+        "except ImportError as e:\n"
+        "    print('ImportError:', e)\n"
+        "    sys.exit(0)\n"
+        "sys.exit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "not built" in r.stdout
+
+
+def test_system_fails_loudly_without_a_gpu(pkg):
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    import synth
+    from paper_2201_12963_gb300.driver import System
+    with pytest.raises((RuntimeError, pkg.CPMError)):
+        System(synth.tiny_cell(seed=7, n_pairs=2), "fp64")
