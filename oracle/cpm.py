@@ -36,7 +36,8 @@ from .ewald import (KE, SQRT2, SQRT_PI, default_kmax, image_shifts, real_space, 
 # geometry helpers (Sec. II.B)
 # ----------------------------------------------------------------------------------------------
 def ewald_box(w) -> np.ndarray:
-    """Periodic box used by the Ewald sums: the slab geometry pads z by slab_factor."""
+    """Periodic box used by the Ewald sums: the slab geometry pads z by slab_factor.
+    Sec. II.B (slab comparison geometry: vacuum padding in z)."""
     box = np.asarray(w.box, np.float64).copy()
     if w.geometry == "slab":
         box[2] *= w.slab_factor
@@ -67,7 +68,8 @@ def constraints(w) -> np.ndarray:
 # A and b (Eq. 3)
 # ----------------------------------------------------------------------------------------------
 def real_space_matrix(pa, pb, box, rcut, alpha, beta, same=False, chunk=512) -> np.ndarray:
-    """Sum over periodic images within r_c of the real-space kernel between every pair (a, b)."""
+    """Sum over periodic images within r_c of the real-space kernel between every pair (a, b).
+    Sec. II.B: the real-space part of the Ewald split of Eq. 3's pair terms."""
     box = np.asarray(box, np.float64)
     na, nb = pa.shape[0], pb.shape[0]
     M = np.zeros((na, nb))
@@ -108,7 +110,8 @@ def elastance(w, kmax=None) -> np.ndarray:
 
 def elastance_apply(w, q, kmax=None) -> np.ndarray:
     """A q without forming A: the potential (V) at each electrode site due to the Gaussian
-    charges q (used for residual checks where N_e is too large for a dense A)."""
+    charges q (used for residual checks where N_e is too large for a dense A).
+    Eq. 3 (A), Eq. 4 (Psi = A q - b)."""
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)
     phi = real_space(E, E, q, box, w.rcut, w.alpha, w.eta / SQRT2, same=True)
@@ -139,7 +142,8 @@ def b_vector(w, R, Q, kmax=None) -> np.ndarray:
 # charges (Eqs. 5-15, as the constrained minimiser)
 # ----------------------------------------------------------------------------------------------
 def factorize(A):
-    """Dense Cholesky factor of A (raises numpy.linalg.LinAlgError if A is not SPD)."""
+    """Dense Cholesky factor of A (raises numpy.linalg.LinAlgError if A is not SPD).
+    Eq. 3: A is the matrix of a positive electrostatic self-energy of the Gaussians (Sec. II.A)."""
     return cho_factor(A, lower=True, check_finite=True)
 
 
@@ -148,6 +152,7 @@ def solve_charges(cho, b, v, dpsi, C):
 
     Stationarity: A q - y = C lam, so q = A^-1 (y + C lam) and
     lam = -(C^T A^-1 C)^-1 C^T A^-1 y.  lam holds the offset potentials (psibar[, psibar_1]).
+    Eqs. 4-7 (one constraint), Eq. 12 (doubled cell: the second offset).
     """
     y = b + dpsi * v
     ainv_y = cho_solve(cho, y)
@@ -204,6 +209,8 @@ def energies(w, R, Q, q, dpsi, kmax=None) -> dict:
              + eta/sqrt(2 pi) sum q^2 ] (+ KE 2 pi/V M_z^2 for the slab),
     H = U - dpsi q^T v (+ dpsi/L_z sum_j Q_j Z_j for the finite field); also the explicit
     derivative dH/d(dpsi) at fixed charges and the total charge Q_+ of the side +1 electrode.
+    Eqs. 1 and 3; finite field: the field term of Sec. II.B (Eqs. 10-11, with the sign that Eq. 11
+    implies); slab: the Yeh-Berkowitz term.
     """
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)
@@ -280,12 +287,13 @@ class Reference:
         self.v = geometry_vector(w)
 
     def charges(self, R, Q, dpsi):
+        """b (Eq. 3) for the electrolyte (R, Q) and the constrained charges (Eqs. 4-7, 12)."""
         b = b_vector(self.w, R, Q, self.kmax)
         q, lam = solve_charges(self.cho, b, self.v, dpsi, self.C)
         return q, lam, b
 
     def step(self, r=0, want_forces=True, want_energy=True) -> dict:
-        """Charges, offsets, b, energies and forces for replica r."""
+        """Charges, offsets, b, energies and forces for replica r.  Sec. II.A-B: one full step of the method."""
         w = self.w
         R, Q, dpsi = w.elyt_xyz[r], w.elyt_q[r], float(w.dpsi[r])
         q, lam, b = self.charges(R, Q, dpsi)
@@ -300,7 +308,8 @@ class Reference:
         """A bounded timing sample of step(r): every real-space sum restricted to a random fraction
         `frac` of its target sites and every reciprocal sum to a random fraction `frac` of the
         k-vectors, with the KKT solve in full.  Its cost is close to `frac` times that of a full
-        step; the values it produces are partial sums and are not returned."""
+        step; the values it produces are partial sums and are not returned.
+        Sec. II.A-B (the sums of step(), partially)."""
         w = self.w
         rng = np.random.default_rng(seed)
         R, Q, dpsi = w.elyt_xyz[r], w.elyt_q[r], float(w.dpsi[r])
@@ -344,7 +353,8 @@ def b_at(w, R, Q, idx, kmax=None) -> np.ndarray:
 
 
 def electrolyte_forces_at(w, R, Q, q, dpsi, idx, kmax=None) -> np.ndarray:
-    """Forces on the electrolyte sites idx for given electrode charges q (as in forces())."""
+    """Forces on the electrolyte sites idx for given electrode charges q (as in forces()).
+    minus the gradient of Eq. 3 at fixed q (Sec. II.A)."""
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)
     T = R[idx]

@@ -45,12 +45,14 @@ KMAX_EXPONENT = 27.6        # reciprocal terms below exp(-27.6) ~ 1e-12 of the l
 
 
 def default_kmax(alpha: float) -> float:
-    """Reciprocal cutoff |k| <= 2 alpha sqrt(27.6): exp(-k^2/4 alpha^2) <= 1e-12."""
+    """Reciprocal cutoff |k| <= 2 alpha sqrt(27.6): exp(-k^2/4 alpha^2) <= 1e-12.
+    Sec. II.B (Ewald summation, reciprocal part)."""
     return 2.0 * alpha * math.sqrt(KMAX_EXPONENT)
 
 
 def screened(r, alpha, beta):
-    """(erfc(alpha r) - erfc(beta r)) / r; beta=None means a point charge (erfc(beta r) = 0)."""
+    """(erfc(alpha r) - erfc(beta r)) / r; beta=None means a point charge (erfc(beta r) = 0).
+    Eqs. 1-2 under the Ewald split (Sec. II.B)."""
     f = erfc(alpha * r)
     if beta is not None:
         f = f - erfc(beta * r)
@@ -58,7 +60,7 @@ def screened(r, alpha, beta):
 
 
 def screened_dr(r, alpha, beta):
-    """d/dr of screened(r, alpha, beta)."""
+    """d/dr of screened(r, alpha, beta).  Eqs. 1-2 under the Ewald split (Sec. II.B)."""
     g = -erfc(alpha * r) / (r * r) - (2.0 * alpha / SQRT_PI) * np.exp(-(alpha * r) ** 2) / r
     if beta is not None:
         g = g + erfc(beta * r) / (r * r) + (2.0 * beta / SQRT_PI) * np.exp(-(beta * r) ** 2) / r
@@ -69,6 +71,7 @@ def image_shifts(box, rcut) -> np.ndarray:
     """Lattice vectors n*L that can bring a minimum-image difference within rcut.
 
     A wrapped difference has |d| <= L/2 per axis, so image n matters only if |n| L - L/2 < r_c.
+    Sec. II.B: the cell is periodic in x, y and z.
     """
     nmax = [int(math.floor(rcut / L + 0.5)) for L in box]
     rng = [np.arange(-n, n + 1) for n in nmax]
@@ -86,6 +89,7 @@ def real_space(targets, sources, charges, box, rcut, alpha, beta, same=False, wa
     source set (target i is source target_index[i], default i) and each target's own zero-shift
     term is excluded.
     Returns phi [nt] (without KE) and, if want_grad, grad [nt, 3] = d phi / d r_target.
+    Eqs. 1-2 under the Ewald split (Sec. II.B).
     """
     targets = np.asarray(targets, np.float64)
     sources = np.asarray(sources, np.float64)
@@ -124,7 +128,8 @@ def real_space(targets, sources, charges, box, rcut, alpha, beta, same=False, wa
 
 
 def kvectors(box, kmax) -> np.ndarray:
-    """Half-space set of nonzero reciprocal vectors k = 2 pi m / L with |k| <= kmax."""
+    """Half-space set of nonzero reciprocal vectors k = 2 pi m / L with |k| <= kmax.
+    Sec. II.B (Ewald summation, reciprocal part)."""
     box = np.asarray(box, np.float64)
     mmax = [int(math.floor(kmax * L / (2 * math.pi))) for L in box]
     rng = [np.arange(-n, n + 1) for n in mmax]
@@ -136,7 +141,8 @@ def kvectors(box, kmax) -> np.ndarray:
 
 
 def recip_weights(k, box, alpha):
-    """Per half-space vector: 2 * (4 pi / V) exp(-k^2/4 alpha^2) / k^2 (factor 2 for -k)."""
+    """Per half-space vector: 2 * (4 pi / V) exp(-k^2/4 alpha^2) / k^2 (factor 2 for -k).
+    Sec. II.B (Ewald summation, reciprocal part)."""
     V = float(np.prod(box))
     k2 = (k * k).sum(1)
     return 2.0 * (4.0 * math.pi / V) * np.exp(-k2 / (4.0 * alpha * alpha)) / k2
@@ -148,6 +154,7 @@ def recip_space(targets, sources, charges, box, alpha, kmax=None, want_grad=Fals
     phi(r) = sum_{k half} w_k [Re S(k) cos(k.r) + Im S(k) sin(k.r)],
     grad   = sum_{k half} w_k k [Im S(k) cos(k.r) - Re S(k) sin(k.r)],  w_k from recip_weights.
     ksub (timing samples only) maps the number of k-vectors to a selection of them.
+    Sec. II.B (Ewald summation, reciprocal part).
     """
     targets = np.asarray(targets, np.float64)
     sources = np.asarray(sources, np.float64)
@@ -175,7 +182,8 @@ def recip_space(targets, sources, charges, box, alpha, kmax=None, want_grad=Fals
 
 def recip_matrix(positions, box, alpha, kmax=None, kchunk=2048):
     """Reciprocal-space interaction matrix M_ab = sum_{k half} w_k cos(k.(r_a - r_b))
-    = C diag(w) C^T + S diag(w) S^T with C = cos(r k^T), S = sin(r k^T)."""
+    = C diag(w) C^T + S diag(w) S^T with C = cos(r k^T), S = sin(r k^T).
+    Sec. II.B; the reciprocal part of A in Eq. 3."""
     positions = np.asarray(positions, np.float64)
     kmax = default_kmax(alpha) if kmax is None else kmax
     k_all = kvectors(box, kmax)

@@ -49,7 +49,8 @@ MVV2E = 103.64269652680505          # 1 amu A^2 / fs^2 in eV (amu 1.66053906660e
 # synthetic Lennard-Jones
 # ----------------------------------------------------------------------------------------------
 def lj_pair(r, sigma, eps, cut):
-    """Force-shifted LJ energy and force magnitude (eV, eV/A; positive = repulsive) at distance r."""
+    """Force-shifted LJ energy and force magnitude (eV, eV/A; positive = repulsive) at distance r.
+    Appendix A (non-Coulomb pair term; synthetic Lennard-Jones stand-in)."""
     def u(x):
         s6 = (sigma / x) ** 6
         return 4.0 * eps * (s6 * s6 - s6)
@@ -65,7 +66,8 @@ def lj_pair(r, sigma, eps, cut):
 def lj_energy_forces(R, types, E, elec_type, sigma, eps, cut, box):
     """U_LJ (eV) and the forces on the electrolyte sites (eV/A) by a direct sum over all pairs and
     all periodic images within `cut` (electrolyte-electrolyte pairs once, electrolyte-electrode
-    pairs once; electrode sites carry type `elec_type` and feel no force, being frozen)."""
+    pairs once; electrode sites carry type `elec_type` and feel no force, being frozen).
+    Appendix A (non-Coulomb pair term; synthetic Lennard-Jones stand-in)."""
     R = np.asarray(R, np.float64)
     E = np.asarray(E, np.float64)
     box = np.asarray(box, np.float64)
@@ -104,6 +106,7 @@ def lj_energy_forces(R, types, E, elec_type, sigma, eps, cut, box):
 # ----------------------------------------------------------------------------------------------
 @dataclasses.dataclass
 class MDParams:
+    """Integrator settings: step, charge schedule, masses, Lennard-Jones, thermostat (Appendices A-B)."""
     dt: float = 2.0                  # fs
     charge_every: int = 5            # k
     mass: tuple = (139.2, 144.96)    # amu per type
@@ -117,6 +120,7 @@ class MDParams:
 
 @dataclasses.dataclass
 class MDState:
+    """Positions, velocities, charges, forces, thermostat variables and step index (Appendix A)."""
     R: np.ndarray                    # [N, 3] electrolyte positions
     V: np.ndarray                    # [N, 3] velocities, A / fs
     q: np.ndarray                    # [N_e] electrode charges
@@ -167,7 +171,7 @@ class Integrator:
         return F, q, en
 
     def kinetic(self, V):
-        """Per-group kinetic energy (eV)."""
+        """Per-group kinetic energy (eV).  Appendix A (thermostat input)."""
         k = 0.5 * MVV2E * self.m * (V * V).sum(1)
         return np.array([k[self.groups == g].sum() for g in range(self.n_groups)])
 
@@ -192,10 +196,12 @@ class Integrator:
         R[:, :2] -= box[:2] * np.floor(R[:, :2] / box[:2])
 
     def start(self, st: MDState):
-        """Forces at the current positions (charges re-solved if the step index is a multiple of k)."""
+        """Forces at the current positions (charges re-solved if the step index is a multiple of k).
+        Appendix B (charge update schedule)."""
         self.F, st.q, self.energies = self._forces(st.R, st.q, st.step)
 
     def run(self, st: MDState, n_steps: int):
+        """Advance n velocity-Verlet steps with the thermostat half steps around them (Appendices A-B)."""
         if self.F is None:
             self.start(st)
         dt, acc = self.p.dt, (1.0 / MVV2E) / self.m[:, None]
@@ -213,7 +219,8 @@ class Integrator:
         return st
 
     def conserved(self, st: MDState) -> dict:
-        """Energy terms at the current state: KE, H, U_LJ, thermostat energy and their total."""
+        """Energy terms at the current state: KE, H, U_LJ, thermostat energy and their total.
+        Appendix A (Nose-Hoover extended energy)."""
         K = self.kinetic(st.V)
         e_nh = 0.0
         if self.p.t_damp > 0:
@@ -227,5 +234,6 @@ class Integrator:
 
 
 def initial_state(R, V, n_elec, n_groups, step=0) -> MDState:
+    """State at step 0 from positions and velocities, thermostats at rest (Appendix A)."""
     return MDState(np.array(R, np.float64), np.array(V, np.float64), np.zeros(n_elec), np.zeros(n_groups),
                    np.zeros(n_groups), step)

@@ -27,7 +27,8 @@ from .ewald import KE
 
 
 def charge_density_z(box_z, area, nbins, elyt_z, elyt_q, elec_z, elec_q, eta) -> np.ndarray:
-    """rho [nbins] in e / A^3 on bins of width box_z / nbins over [0, box_z)."""
+    """rho [nbins] in e / A^3 on bins of width box_z / nbins over [0, box_z).
+    Sec. II.C; 0.34 A bins as in Appendix B."""
     h = box_z / nbins
     rho = np.zeros(nbins)
     zw = np.mod(np.asarray(elyt_z, np.float64), box_z)
@@ -43,14 +44,16 @@ def charge_density_z(box_z, area, nbins, elyt_z, elyt_q, elec_z, elec_q, eta) ->
 
 
 def second_difference_matrix(nbins, h) -> np.ndarray:
-    """Periodic (psi_{i+1} - 2 psi_i + psi_{i-1}) / h^2 as a dense matrix."""
+    """Periodic (psi_{i+1} - 2 psi_i + psi_{i-1}) / h^2 as a dense matrix.
+    Sec. II.C, Eq. 16 (low-order finite differences)."""
     D = -2.0 * np.eye(nbins) + np.eye(nbins, k=1) + np.eye(nbins, k=-1)
     D[0, -1] = D[-1, 0] = 1.0
     return D / (h * h)
 
 
 def potential_z(rho, box_z, geometry="ff", dpsi=0.0) -> np.ndarray:
-    """psi [nbins] in V at the bin centres (zero-mean periodic part, plus the finite-field ramp)."""
+    """psi [nbins] in V at the bin centres (zero-mean periodic part, plus the finite-field ramp).
+    Sec. II.C, Eq. 16 with the boundary condition of each geometry."""
     nbins = len(rho)
     h = box_z / nbins
     D = second_difference_matrix(nbins, h)
