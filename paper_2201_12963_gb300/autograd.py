@@ -2,14 +2,16 @@
 
 CPMEnergy(xyz, dpsi, system) -> H per replica, the constant-potential energy
 H = U - dpsi q^T v (+ dpsi/L_z sum_j Q_j Z_j for the finite field) at the charges q solved in the
-forward pass.  Because q minimises the energy under the neutrality constraints, dH/dq is
+forward pass (Eq. 3, with the field term of Eqs. 10-11 and the potentials of Eq. 5).  Because q
+minimises the energy under the neutrality constraints (Eqs. 6-7, 12), dH/dq is
 parallel to the constraints and the charge response drops out of every derivative (envelope
 theorem):
     dH/dR_j   = -F_j                  (the electrostatic force; backward launches cpm_forces)
     dH/d dpsi = -q^T v (+ sum Q_j Z_j / L_z)
 
 CPMCharge(dpsi, system) -> Q_+ per replica, the total charge of the side +1 electrode, with
-dQ_+/d dpsi = e_+^T S v (cpm_capacitance), the differential capacitance of the cell.
+dQ_+/d dpsi = e_+^T S v (cpm_capacitance; S of Eqs. 8-9 / 13-15), the differential capacitance of
+the cell (Sec. IV.D).
 
 Both functions drive the C ABI through a driver.System whose electrolyte charges and replica
 layout stay fixed; only positions and potential differences are inputs.

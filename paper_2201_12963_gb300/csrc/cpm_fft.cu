@@ -1,4 +1,5 @@
-// SPME convolution on the mesh in float32 without the FFT library: forward 3-D real-to-complex
+// SPME convolution (the reciprocal-space part of the Ewald sums behind Eq. 3, Sec. II.B) on the
+// mesh in float32 without the FFT library: forward 3-D real-to-complex
 // transform, multiplication by the influence function G (with the reciprocal energy), inverse
 // transform, as five launches that each keep their lines in shared memory:
 //   z: real-to-complex per mesh line (warp per line)

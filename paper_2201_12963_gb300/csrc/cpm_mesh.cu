@@ -1,5 +1,6 @@
 // SPME charge assignment and force interpolation through shared-memory bricks moved by the
-// Tensor Memory Accelerator (float32 mesh, mixed precision).
+// Tensor Memory Accelerator (float32 mesh, mixed precision): the reciprocal-space part of the Ewald
+// sums behind Eq. 3 (Sec. II.B), for b and for the forces.
 //
 // The mesh gets a halo-padded twin: padded index p = g + P per axis, where g in [-P, K) is the
 // unwrapped mesh index of a B-spline stencil point, so no stencil of a site ever wraps.  A block

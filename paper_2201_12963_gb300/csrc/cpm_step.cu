@@ -1,10 +1,16 @@
 // Per-step constant-potential electrostatics on the GPU (templated on the working precision T):
 //
 //   prepare   bin the electrolyte into the real-space cell grid (counting sort, cell-local coords)
+//             k_bin, k_scan, k_scatter
 //   charges   b = -(electrolyte potential at the electrode sites) (Eq. 3): real-space
-//             Gaussian-point pairs + SPME (spread, FFT, influence function, inverse FFT, gather),
-//             then q = S (b + dpsi v) and the neutrality projection (Eqs. 8-9 / 13-15)
-//   forces    SPME of all charges + real-space pair forces, finite-field / slab terms, energies
+//             Gaussian-point pairs (Eqs. 1-2 under the Ewald split, Sec. II.B; k_pair_cell,
+//             k_pair_warp) + SPME (k_spread_*, FFT, k_influence, inverse FFT, k_gather_b),
+//             then q = S (b + dpsi v) (k_sapply32 / 64 / stream / tc, cpm_sym.cu; the finite-field
+//             v of Eq. 11, the doubled cell's of Eqs. 12-15) and the neutrality projection
+//             (k_project, k_project_mirror; Eqs. 7-9 / 13-15)
+//   forces    SPME of all charges + real-space pair forces (k_gather_f_*, k_pair_* with forces),
+//             finite-field (Eqs. 10-11) / slab (Yeh-Berkowitz) terms, energies (k_energy_final:
+//             Eq. 3 at the constrained optimum)
 //
 // Precision.  T = float is the mixed path.  GB300 issues float64 arithmetic at a small fraction of
 // the float32 rate, so in the float kernels every per-lane sum is a compensated float32 sum

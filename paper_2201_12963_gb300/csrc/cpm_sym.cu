@@ -1,4 +1,6 @@
-// S-apply from symmetric packed storage (mixed precision, one replica).
+// S-apply from symmetric packed storage (mixed precision, one replica): q = S (b + dpsi v) with
+// S = O A^-1 (Eqs. 8-9) or, per mirror block of the doubled cell, the block's projected inverse
+// (Eqs. 13-15).
 //
 // S (or each mirror block S+-) is symmetric, so only its upper triangle of 128 x 128 tiles is kept:
 // tile (I, J), I <= J, at packed index I nt - I (I - 1) / 2 + (J - I), each tile row-major
