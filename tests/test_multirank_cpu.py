@@ -46,3 +46,15 @@ def test_single_process_needs_no_process_group():
     assert not dist.is_initialized()
     assert bench.reduce_max(3.5) == 3.5
     assert bench.aggregate_steps_per_s(1000.0, 50, 1) == pytest.approx(50.0)
+
+
+def test_reference_arm_runs_on_rank_0_only():
+    """Under torchrun the reference arm's non-zero ranks exit 0 without work or output."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=root, env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-500:]
+    assert r.stdout.strip() == ""
