@@ -160,6 +160,43 @@ def test_pure_reciprocal_gaussian_energy_and_b():
     assert np.max(np.abs(b + KE * pot)) < 1e-10 * np.max(np.abs(b))
 
 
+@pytest.mark.parametrize("box", [(10.0, 10.0, 10.0), (9.0, 10.5, 12.0)])
+def test_mixed_energy_equals_direct_lattice_sum(box):
+    """U of Eq. 3 for Gaussian (Eq. 2) and point charges against a plain sum over whole periodic
+    images, with no Ewald split: pair kernels erf(eta r / sqrt 2) / r (Gaussian-Gaussian),
+    erf(eta r) / r (Gaussian-point), 1 / r (point-point), plus the Gaussian self-energy
+    q^2 eta / sqrt(2 pi).  The cell (a point charge +1 with six Gaussians of -1/6 at +-1 A along each
+    axis) is neutral with no dipole and no quadrupole, so the image sum over growing boxes
+    converges absolutely to the tin-foil lattice energy; eta = 1 A^-1 keeps every intra-cell
+    kernel 5-16 % away from 1 / r."""
+    box = np.asarray(box)
+    eta, d = 1.0, 1.0
+    c0 = np.array([4.7, 5.1, 5.3])
+    E = c0 + d * np.vstack([np.eye(3), -np.eye(3)])
+    q = np.full(6, -1.0 / 6.0)
+    R, Q = c0[None, :], np.array([1.0])
+    w = synth.Workload("pin", box, E, np.array([1, 1, 1, -1, -1, -1]), None, np.zeros(6, np.int32), [R], [Q],
+                       np.array([0.0]), "dc", eta=eta, alpha=0.6, rcut=9.5)
+    U = cpm.energies(w, R, Q, q, 0.0)["U"]
+    P, c, gauss = np.vstack([E, R]), np.concatenate([q, Q]), [True] * 6 + [False]
+    m = np.arange(-6, 7)
+    shifts = np.stack(np.meshgrid(m, m, m, indexing="ij"), -1).reshape(-1, 3) * box
+    total = eta / math.sqrt(2 * math.pi) * float(q @ q)
+    for a in range(7):
+        for b in range(7):
+            r = np.linalg.norm(P[a] - P[b] + shifts, axis=1)
+            if a == b:
+                r = r[r > 0]
+            if gauss[a] and gauss[b]:
+                kern = erf(eta * r / math.sqrt(2)) / r
+            elif gauss[a] or gauss[b]:
+                kern = erf(eta * r) / r
+            else:
+                kern = 1.0 / r
+            total += 0.5 * c[a] * c[b] * kern.sum()
+    assert abs(KE * total - U) <= 1e-10 * abs(U)
+
+
 def test_alpha_invariance():
     """A (on neutral charge vectors), b and U are physical: they may not depend on the Ewald
     splitting parameter alpha.  A itself carries an alpha-dependent multiple of e e^T (the
