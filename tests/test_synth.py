@@ -98,3 +98,55 @@ def test_md_inputs_refuse_molecular_electrolytes():
     import pytest
     with pytest.raises(ValueError):
         synth.md_inputs(synth.config_paper_cell())
+
+
+def _paper_parameters():
+    import os
+    vals = {}
+    with open(os.path.join(os.path.dirname(__file__), "golden", "paper_parameters.txt")) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                key, value = line.split()[:2]
+                vals[key] = float(value)
+    return vals
+
+
+def test_generators_and_defaults_use_the_parameters_the_paper_fixes(monkeypatch):
+    """tests/golden/paper_parameters.txt holds the values the paper prints (each with its section);
+    the paper-scale cell, the MD settings and the geometry vector must use them."""
+    import dataclasses
+    import inspect
+    import sys
+    from oracle import cpm
+    from oracle.md import MDParams
+    p = _paper_parameters()
+    w = synth.config_paper_cell()
+    assert w.eta == p["gaussian_eta_per_A"]
+    Q = w.elyt_q[0]
+    n_pairs = int((Q < 0).sum())
+    assert n_pairs == 500 and np.allclose(Q[Q < 0], -p["ion_charge_e"])
+    assert abs(Q[Q > 0].sum() / n_pairs - p["ion_charge_e"]) < 1e-12     # three sites per cation
+    zs = np.unique(np.round(w.elec_xyz[:, 2], 9))
+    assert np.allclose(np.diff(zs[:3]), p["interlayer_spacing_A"])
+    assert np.allclose(np.diff(zs[-3:]), p["interlayer_spacing_A"])
+    layer = w.elec_xyz[np.isclose(w.elec_xyz[:, 2], zs[0])]
+    assert abs(_min_sep_xy_periodic(layer, w.box) - p["cc_bond_A"]) < 1e-9
+    # ion-pair number density in the accessible slab against 1.267 g/cm^3 of BMIm-PF6 (284.18 g/mol)
+    rho_paper = p["bulk_density_g_cm3"] / 284.18 * 6.02214076e23 / 1e24
+    lx, ly, lz = w.box
+    rho = n_pairs / (lx * ly * (lz - 2 * synth.ELECTROLYTE_MARGIN))
+    assert abs(rho / rho_paper - 1.0) < 0.01
+    # the MD loop: 2 fs steps, charges re-solved every 5 steps (oracle, library driver, benchmark)
+    assert synth.PAPER_TIMESTEP_FS == p["timestep_fs"] == MDParams().dt
+    assert MDParams().charge_every == p["charge_update_every"]
+    import __graft_entry__
+    __graft_entry__.build()                     # the driver module loads the library
+    from paper_2201_12963_gb300.driver import MD
+    sig = inspect.signature(MD.__init__).parameters
+    assert sig["dt"].default == p["timestep_fs"] and sig["charge_every"].default == p["charge_update_every"]
+    import bench
+    monkeypatch.setattr(sys, "argv", ["bench.py"])
+    assert bench.parse().charge_every == p["charge_update_every"]
+    # d = +-1/2 on the two electrodes (Eq. 5)
+    v = cpm.geometry_vector(dataclasses.replace(w, geometry="slab"))
+    assert np.allclose(np.abs(v), p["d_entry_magnitude"])
