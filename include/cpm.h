@@ -365,6 +365,19 @@ int cpm_set_mesh_variant(cpm_ctx* ctx, int32_t variant);
 int cpm_set_pair_group(cpm_ctx* ctx, int32_t gz);
 int cpm_get_pair_group(const cpm_ctx* ctx, int32_t* gz);
 
+/*
+ * cpm_set_wait_test - test hook for the bounded device waits (on != 0: on; default off).  The
+ * only spin-waits of the library are the mbarrier waits of the tcgen05 S-apply (batched replicas,
+ * mixed precision) and of the TMA brick force gather (cpm_mesh_variant brick).  Each polls a
+ * bounded number of times; if it gives up it latches CPM_ERR_TIMEOUT, waits once more with the same
+ * bound for the tensor-core work or copy still in flight, and leaves without using its result.
+ * With the hook on, the first of those waits gives up without polling, so a call that reaches one
+ * of the two kernels returns invalid results and latches CPM_ERR_TIMEOUT (read by the next call
+ * or by cpm_status); turning it off restores normal calls.  It takes effect at launch, so a CUDA
+ * graph keeps the setting it was captured with.  CPM_ERR_ARG for a null context.
+ */
+int cpm_set_wait_test(cpm_ctx* ctx, int32_t on);
+
 /* Real-space pair kernels (the real-space part of b, the electrolyte and electrode forces, the
  * Gaussian-Gaussian energy) come in two forms:
  *   cell blocks      one block per cell (or z group of cells, cpm_set_pair_group): the sources of

@@ -25,6 +25,7 @@ EXPORTED = ("cpm_build_matrix", "cpm_matrix_key", "cpm_matrix_image", "cpm_build
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
             "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
             "cpm_set_pair_group", "cpm_get_pair_group", "cpm_set_pair_variant", "cpm_get_pair_variant",
+            "cpm_set_wait_test",
             "cpm_autotune", "cpm_density_z", "cpm_potential_z",
             "cpm_md_create", "cpm_md_run", "cpm_md_advance", "cpm_md_get_state", "cpm_md_set_state", "cpm_md_info",
             "cpm_md_destroy", "cpm_destroy",
@@ -96,6 +97,7 @@ def _load():
     lib.cpm_set_fft_variant.argtypes = [vp, i32]
     lib.cpm_set_mesh_variant.argtypes = [vp, i32]
     lib.cpm_set_pair_group.argtypes = [vp, i32]
+    lib.cpm_set_wait_test.argtypes = [vp, i32]
     lib.cpm_get_pair_group.argtypes = [vp, ctypes.POINTER(i32)]
     lib.cpm_set_pair_variant.argtypes = [vp, i32]
     lib.cpm_get_pair_variant.argtypes = [vp, ctypes.POINTER(i32)]
@@ -358,6 +360,11 @@ MESH_VARIANTS = {"sites": 0, "brick": 1}              # enum cpm_mesh_variant
 def cpm_set_mesh_variant(ctx: Context, variant):
     v = MESH_VARIANTS[variant] if isinstance(variant, str) else int(variant)
     _check(_lib.cpm_set_mesh_variant(ctx.handle, v), "cpm_set_mesh_variant")
+
+
+def cpm_set_wait_test(ctx: Context, on: bool):
+    """Test hook: the first bounded device waits give up at once (see include/cpm.h)."""
+    _check(_lib.cpm_set_wait_test(ctx.handle, 1 if on else 0), "cpm_set_wait_test")
 
 
 def cpm_set_pair_group(ctx: Context, gz: int):

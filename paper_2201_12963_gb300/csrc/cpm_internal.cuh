@@ -117,6 +117,7 @@ struct cpm_ctx {
   // S-apply variant (enum cpm_sapply_variant) and the streaming variant's row partial sums
   // ([rows of S], float64, zero between calls: its finish kernel clears what it consumed)
   int pair_gz = 1;               // real-space pair kernels: z cells per block (cpm_set_pair_group)
+  bool wait_test = false;       // cpm_set_wait_test: the first bounded mbarrier waits give up at once
   int pair_variant = 0;         // enum cpm_pair_variant
   int sapply_variant = 0;
   double* qpart = nullptr;

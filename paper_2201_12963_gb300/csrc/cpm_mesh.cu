@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(BR_THREADS) k_gather_f_brick(const __grid_cons
                                                                const double* __restrict__ dpsi, double ff_over_lz,
                                                                double slab_coef, const double* __restrict__ scal,
                                                                const double* __restrict__ f_pair,
-                                                               double* __restrict__ F, int* status) {
+                                                               double* __restrict__ F, int short_wait, int* status) {
   extern __shared__ __align__(128) float br_dyn[];
   __shared__ float sw[BR_WARPS][3][PMAX], sdw[BR_WARPS][3][PMAX];
   __shared__ int si0[BR_WARPS][3];
@@ -238,10 +238,12 @@ __global__ void __launch_bounds__(BR_THREADS) k_gather_f_brick(const __grid_cons
         "l"(reinterpret_cast<uint64_t>(&map)), "r"(bs[2]), "r"(bs[1]), "r"(bs[0]), "r"(rep), "r"(br_smem(&mbar))
         : "memory");
   }
-  // bounded wait for the brick (phase 0)
+  // bounded wait for the brick (phase 0); short_wait (cpm_set_wait_test) makes it give up without
+  // polling
   if (threadIdx.x == 0) {
     uint32_t done = 0;
-    for (long long it = 0; it < BR_WAIT_LIMIT && !done; ++it) {
+    const long long first_limit = short_wait ? 0 : BR_WAIT_LIMIT;
+    for (long long it = 0; it < first_limit && !done; ++it) {
       asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                    : "=r"(done)
                    : "r"(br_smem(&mbar)), "r"(0)
@@ -442,7 +444,7 @@ int cpm_internal_gather_f_brick(cpm_ctx* c, int nrep, const int* off, const void
   CPM_LAUNCH();
   k_gather_f_brick<float4><<<dim3(nsuper(c), nrep), BR_THREADS, box_bytes, st>>>(
       c->br_map, bg, sg, off, c->p.max_elyt, (const float4*)l_loc, c->l_start, c->l_sorted, c->spl_I, c->spl_F32,
-      dpsi, ff_over_lz, slab_coef, c->scal, c->f_pair, F, c->status);
+      dpsi, ff_over_lz, slab_coef, c->scal, c->f_pair, F, c->wait_test ? 1 : 0, c->status);
   ++c->launches;
   CPM_LAUNCH();
   return CPM_OK;

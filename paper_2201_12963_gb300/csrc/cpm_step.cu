@@ -1456,7 +1456,7 @@ template <int NT>
 __global__ void __launch_bounds__(TC_THREADS) k_sapply_tc(const float* __restrict__ S, int ld, int ne,
                                                           const float* __restrict__ b32, int rep0, int nrep,
                                                           int chunks_per_split, float* __restrict__ D,
-                                                          int* __restrict__ status) {
+                                                          int short_wait, int* __restrict__ status) {
   static_assert(NT % 16 == 0 && NT >= 16 && NT <= 256, "replica tile");
   constexpr int TMEM_COLS = NT < 32 ? 32 : NT;
   constexpr int A_BYTES = TC_M * TC_KC * 4, B_BYTES = NT * TC_KC * 4;
@@ -1549,9 +1549,11 @@ __global__ void __launch_bounds__(TC_THREADS) k_sapply_tc(const float* __restric
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(&mbar)));
     }
-    // ---- bounded wait for the MMAs (they read the staged operands, so no restaging before)
+    // ---- bounded wait for the MMAs (they read the staged operands, so no restaging before);
+    // short_wait (cpm_set_wait_test) makes it give up without polling
     bool done = false;
-    for (int it = 0; it < (1 << 22) && !done; ++it) {
+    const int first_limit = short_wait ? 0 : (1 << 22);
+    for (int it = 0; it < first_limit && !done; ++it) {
       uint32_t r;
       asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
                    : "=r"(r) : "r"(smem_u32(&mbar)), "r"(phase) : "memory");
@@ -1910,7 +1912,7 @@ static size_t tc_smem_bytes() {
 template <int NT>
 static int launch_tc(cpm_ctx* c, int rep0, int nrep, dim3 grid, int cps, cudaStream_t st) {
   k_sapply_tc<NT><<<grid, TC_THREADS, tc_smem_bytes<NT>(), st>>>(c->S32, c->ld32, c->ne, c->b32, rep0, nrep, cps,
-                                                                  c->qraw32, c->status);
+                                                                  c->qraw32, c->wait_test ? 1 : 0, c->status);
   STEP_LAUNCH();
   return CPM_OK;
 }
@@ -2461,6 +2463,15 @@ extern "C" int cpm_set_pair_group(cpm_ctx* c, int32_t gz) {
     return CPM_ERR_ARG;
   }
   c->pair_gz = gz;
+  return CPM_OK;
+}
+
+extern "C" int cpm_set_wait_test(cpm_ctx* c, int32_t on) {
+  if (!c) {
+    cpm::set_error("cpm_set_wait_test: null context");
+    return CPM_ERR_ARG;
+  }
+  c->wait_test = on != 0;
   return CPM_OK;
 }
 

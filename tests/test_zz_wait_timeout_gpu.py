@@ -1,0 +1,61 @@
+"""Bounded device waits (GPU): a wait that gives up latches CPM_ERR_TIMEOUT and leaves the context
+usable.
+
+The library's only spin-waits are the mbarrier waits of the tcgen05 S-apply (batched replicas,
+mixed precision) and of the TMA brick force gather.  The test hook cpm_set_wait_test makes the
+first of those waits give up without polling; the kernel then latches the timeout, waits once more
+(bounded) for its own tensor-core work or copy still in flight, and leaves without using it.  So
+the forced timeout causes no fault: the call's results are invalid, cpm_status reports
+CPM_ERR_TIMEOUT, and with the hook off the next call gives the results of a normal one.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TIMEOUT = -7        # CPM_ERR_TIMEOUT
+
+
+def _lib():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2201_12963_gb300 as g
+    from paper_2201_12963_gb300.driver import System
+    return g, System
+
+
+def test_tensor_core_s_apply_timeout_is_latched_and_recoverable():
+    g, System = _lib()
+    s = System(synth.config_batched(n_rep=16), "mixed")      # >= 8 replicas: tcgen05 S-apply
+    s.charges()
+    assert g.cpm_status(s.ctx) == 0
+    q0 = s.q.cpu().numpy().copy()
+    g.cpm_set_wait_test(s.ctx, True)
+    s.charges()
+    assert g.cpm_status(s.ctx) == TIMEOUT
+    g.cpm_set_wait_test(s.ctx, False)
+    s.charges()
+    assert g.cpm_status(s.ctx) == 0
+    # float32 mesh spreads add with atomics in no fixed order: repeated runs differ at rounding
+    assert np.max(np.abs(s.q.cpu().numpy() - q0)) <= 1e-6
+
+
+def test_brick_gather_timeout_is_latched_and_recoverable(plain_ff):
+    g, System = _lib()
+    s = System(plain_ff[0], "mixed", order=8)
+    g.cpm_set_mesh_variant(s.ctx, "brick")                   # TMA brick force gather
+    s.charges()
+    s.forces(elec=True, energy=True)
+    assert g.cpm_status(s.ctx) == 0
+    F0 = s.results()["F_elyt"][0].copy()
+    g.cpm_set_wait_test(s.ctx, True)
+    s.forces(elec=True, energy=True)
+    assert g.cpm_status(s.ctx) == TIMEOUT
+    g.cpm_set_wait_test(s.ctx, False)
+    s.forces(elec=True, energy=True)
+    assert g.cpm_status(s.ctx) == 0
+    F = s.results()["F_elyt"][0]
+    assert np.sqrt(((F - F0) ** 2).sum() / (F0 ** 2).sum()) <= 2e-6
