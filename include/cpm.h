@@ -118,8 +118,11 @@ typedef struct {
  * A is built in float64 on the GPU: real-space Gaussian-Gaussian pairs over all images within
  * rcut, the reciprocal part (direct Ewald sum up to kmax_build, or the SPME mesh operator, see
  * cpm_matrix_kspace), self terms, and for CPM_SLAB the dipole term.  A mirror-symmetric doubled
- * cell is stored as two half-size blocks (cpm_dc_blocks).  Returns CPM_ERR_NOT_SPD if a Cholesky
- * factorisation fails, CPM_ERR_NOMEM if device memory runs out.
+ * cell is stored as two half-size blocks (cpm_dc_blocks).  Returns CPM_ERR_ARG before any device
+ * work for invalid parameters or labels and for two sites within 1e-6 A of each other (periodic
+ * images included: their Gaussian-Gaussian kernel would be 0/0), CPM_ERR_NONFINITE for a non-finite
+ * coordinate, CPM_ERR_NOT_SPD if a Cholesky factorisation fails, CPM_ERR_NOMEM if device memory runs
+ * out.
  */
 int cpm_build_matrix(const cpm_params* p, int32_t n_elec, const double* elec_xyz_host,
                      const int32_t* elec_side_host, const int32_t* elec_cell_host, void* stream,

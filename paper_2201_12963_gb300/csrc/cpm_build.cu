@@ -267,6 +267,54 @@ template <typename T> static int upload(T** d, const std::vector<T>& h, cudaStre
   return CPM_OK;
 }
 
+// True if two electrode sites lie within tol of each other (periodic images included).  A
+// coincident pair makes the Gaussian-Gaussian kernel (erfc(alpha r) - erfc(eta r / sqrt 2)) / r
+// of A a 0/0 and A singular.  Sites are wrapped into the box and hashed on cells of edge h >> tol,
+// so a pair within tol shares a cell or sits in adjacent ones (the last cell of an axis is
+// adjacent to the first).
+static bool coincident_sites(const double box[3], int32_t ne, const double* xyz, double tol) {
+  const double h = 1e-3;
+  long long n[3];
+  for (int d = 0; d < 3; ++d) n[d] = std::max(1LL, (long long)std::ceil(box[d] / h));
+  std::vector<double> w(3 * (size_t)ne);
+  std::vector<long long> cid(3 * (size_t)ne);
+  for (int i = 0; i < ne; ++i)
+    for (int d = 0; d < 3; ++d) {
+      double x = std::fmod(xyz[3 * i + d], box[d]);
+      if (x < 0) x += box[d];
+      if (x >= box[d]) x -= box[d];
+      w[3 * i + d] = x;
+      cid[3 * i + d] = std::min((long long)(x / h), n[d] - 1);
+    }
+  auto key = [&](long long a, long long b, long long c) {
+    return (uint64_t)((a * n[1] + b) * n[2] + c);
+  };
+  std::unordered_map<uint64_t, std::vector<int>> grid;
+  grid.reserve(2 * (size_t)ne);
+  for (int i = 0; i < ne; ++i) {
+    for (int da = -1; da <= 1; ++da)
+      for (int db = -1; db <= 1; ++db)
+        for (int dc = -1; dc <= 1; ++dc) {
+          const long long a = (cid[3 * i] + da + n[0]) % n[0];
+          const long long b = (cid[3 * i + 1] + db + n[1]) % n[1];
+          const long long c = (cid[3 * i + 2] + dc + n[2]) % n[2];
+          auto it = grid.find(key(a, b, c));
+          if (it == grid.end()) continue;
+          for (int j : it->second) {
+            double r2 = 0;
+            for (int d = 0; d < 3; ++d) {
+              double dx = w[3 * i + d] - w[3 * j + d];
+              dx -= box[d] * std::round(dx / box[d]);
+              r2 += dx * dx;
+            }
+            if (r2 < tol * tol) return true;
+          }
+        }
+    grid[key(cid[3 * i], cid[3 * i + 1], cid[3 * i + 2])].push_back(i);
+  }
+  return false;
+}
+
 static int validate(const cpm_params* p, int32_t ne, const double* xyz, const int32_t* side,
                     const int32_t* cell) {
   if (!p || !xyz || !side || ne < 2) return CPM_ERR_ARG;
@@ -289,6 +337,7 @@ static int validate(const cpm_params* p, int32_t ne, const double* xyz, const in
     for (int d = 0; d < 3; ++d)
       if (!std::isfinite(xyz[3 * i + d])) return CPM_ERR_NONFINITE;
   }
+  if (coincident_sites(p->box, ne, xyz, 1e-6)) return CPM_ERR_ARG;
   return CPM_OK;
 }
 

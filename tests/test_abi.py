@@ -114,3 +114,40 @@ def test_system_fails_loudly_without_a_gpu(pkg):
     from paper_2201_12963_gb300.driver import System
     with pytest.raises((RuntimeError, pkg.CPMError)):
         System(synth.tiny_cell(seed=7, n_pairs=2), "fp64")
+
+
+def test_coincident_electrode_sites_are_rejected(pkg):
+    """Two Gaussian sites at one point (also through a periodic image) make A's Gaussian-Gaussian
+    kernel 0/0: the build refuses them before any device work."""
+    xyz = np.array([[0.5, 0.5, 1.0], [1.5, 0.5, 1.0], [0.5, 0.5, 9.0], [1.5, 0.5, 9.0]])
+    side = np.array([-1, -1, 1, 1])
+    p = pkg.make_params((10, 10, 10), 1.979, 0.25, 5.0, (16, 16, 16))
+    pkg.cpm_matrix_key(p, xyz, side)                        # distinct sites: accepted
+    for j, shift in ((0, (0.0, 0.0, 0.0)), (0, (10.0, 0.0, 0.0)), (1, (0.0, -10.0, 0.0)), (2, (0.0, 0.0, 3e-7))):
+        dup = np.vstack([xyz, xyz[j] + np.array(shift)])
+        with pytest.raises(pkg.CPMError) as ei:
+            pkg.cpm_matrix_key(p, dup, np.r_[side, side[j]])
+        assert ei.value.status == -1
+        with pytest.raises(pkg.CPMError) as ei:
+            pkg.cpm_build_matrix(p, dup, np.r_[side, side[j]], stream=0)
+        assert ei.value.status == -1
+    near = np.vstack([xyz, xyz[0] + np.array([2e-6, 0.0, 0.0])])  # beyond the 1e-6 A tolerance
+    pkg.cpm_matrix_key(p, near, np.r_[side, -1])
+
+
+def test_every_generated_electrode_passes_validation(pkg):
+    """The coincidence check accepts the electrodes of every workload the tests and the benchmark
+    build (the large cells with a token electrolyte: only the electrode matters here)."""
+    import synth
+    from paper_2201_12963_gb300.driver import params_for
+    ws = [synth.config_plain_ff(), synth.config_paper_cell(), synth.config_paper_cell(geometry="dc"),
+          synth.config_paper_cell(geometry="slab"), synth.proximal_only(synth.config_paper_cell()),
+          synth.config_large_ff(n_pairs=10), synth.config_large_dc(n_pairs_per_cell=10), synth.md_cell(),
+          synth.md_cell(geometry="dc")]
+    for w in ws:
+        pkg.cpm_matrix_key(params_for(w), w.elec_xyz, w.elec_side, w.elec_cell)
+    # the small test cells, with the meshes their tests use
+    w = synth.tiny_cell(seed=4, n_pairs=4)
+    pkg.cpm_matrix_key(params_for(w, grid=(20, 16, 72), order=8), w.elec_xyz, w.elec_side, w.elec_cell)
+    w = synth.mirror_to_doubled(w, "independent", seed=40)
+    pkg.cpm_matrix_key(params_for(w, grid=(18, 16, 144), order=8), w.elec_xyz, w.elec_side, w.elec_cell)
