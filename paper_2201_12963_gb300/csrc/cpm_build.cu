@@ -286,8 +286,10 @@ static bool coincident_sites(const double box[3], int32_t ne, const double* xyz,
       w[3 * i + d] = x;
       cid[3 * i + d] = std::min((long long)(x / h), n[d] - 1);
     }
+  // unsigned arithmetic: for a very large box the key may wrap, which only merges hash cells
+  // (more distance checks), never reports a false pair
   auto key = [&](long long a, long long b, long long c) {
-    return (uint64_t)((a * n[1] + b) * n[2] + c);
+    return ((uint64_t)a * (uint64_t)n[1] + (uint64_t)b) * (uint64_t)n[2] + (uint64_t)c;
   };
   std::unordered_map<uint64_t, std::vector<int>> grid;
   grid.reserve(2 * (size_t)ne);
