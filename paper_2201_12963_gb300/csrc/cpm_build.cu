@@ -269,13 +269,16 @@ template <typename T> static int upload(T** d, const std::vector<T>& h, cudaStre
 
 // True if two electrode sites lie within tol of each other (periodic images included).  A
 // coincident pair makes the Gaussian-Gaussian kernel (erfc(alpha r) - erfc(eta r / sqrt 2)) / r
-// of A a 0/0 and A singular.  Sites are wrapped into the box and hashed on cells of edge h >> tol,
-// so a pair within tol shares a cell or sits in adjacent ones (the last cell of an axis is
-// adjacent to the first).
+// of A a 0/0 and A singular.  Sites are wrapped into the box and hashed on cells of edge
+// h >= 1e-3 A >> tol (at most 2^20 cells per axis), so a pair within tol shares a cell or sits in
+// adjacent ones (the last cell of an axis is adjacent to the first).
 static bool coincident_sites(const double box[3], int32_t ne, const double* xyz, double tol) {
-  const double h = 1e-3;
   long long n[3];
-  for (int d = 0; d < 3; ++d) n[d] = std::max(1LL, (long long)std::ceil(box[d] / h));
+  double h[3];
+  for (int d = 0; d < 3; ++d) {
+    h[d] = std::max(1e-3, box[d] / 1048576.0);
+    n[d] = std::max(1LL, std::min(1048576LL, (long long)std::ceil(box[d] / h[d])));
+  }
   std::vector<double> w(3 * (size_t)ne);
   std::vector<long long> cid(3 * (size_t)ne);
   for (int i = 0; i < ne; ++i)
@@ -284,10 +287,8 @@ static bool coincident_sites(const double box[3], int32_t ne, const double* xyz,
       if (x < 0) x += box[d];
       if (x >= box[d]) x -= box[d];
       w[3 * i + d] = x;
-      cid[3 * i + d] = std::min((long long)(x / h), n[d] - 1);
+      cid[3 * i + d] = std::min((long long)(x / h[d]), n[d] - 1);
     }
-  // unsigned arithmetic: for a very large box the key may wrap, which only merges hash cells
-  // (more distance checks), never reports a false pair
   auto key = [&](long long a, long long b, long long c) {
     return ((uint64_t)a * (uint64_t)n[1] + (uint64_t)b) * (uint64_t)n[2] + (uint64_t)c;
   };

@@ -133,6 +133,10 @@ def test_coincident_electrode_sites_are_rejected(pkg):
         assert ei.value.status == -1
     near = np.vstack([xyz, xyz[0] + np.array([2e-6, 0.0, 0.0])])  # beyond the 1e-6 A tolerance
     pkg.cpm_matrix_key(p, near, np.r_[side, -1])
+    big = pkg.make_params((1e12, 10, 10), 1.979, 0.25, 5.0, (16, 16, 16))    # hash grid capped per axis
+    pkg.cpm_matrix_key(big, xyz, side)
+    with pytest.raises(pkg.CPMError):
+        pkg.cpm_matrix_key(big, np.vstack([xyz, xyz[3] + np.array([1e12, 0.0, 0.0])]), np.r_[side, 1])
 
 
 def test_every_generated_electrode_passes_validation(pkg):
