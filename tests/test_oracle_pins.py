@@ -421,3 +421,32 @@ def test_forces_are_minus_energy_gradient(geometry):
             assert abs(fd - F_e[i, c]) < 1e-6 * max(scale, np.max(np.abs(F_e)))
     total = F_l.sum(0) + F_e.sum(0)
     assert np.max(np.abs(total)) < 1e-9 * scale
+
+
+@pytest.mark.parametrize("geometry", ["ff", "dc", "slab"])
+def test_sampled_checkers_equal_the_dense_oracle(geometry):
+    """The matrix-free and sampled helpers that check the full-size GPU runs (elastance_apply,
+    b_at, electrolyte_forces_at) against the dense oracle they restate (Eq. 3 for A and b, the
+    fixed-charge forces of Sec. II.A), which the pins above tie to the paper and to physics:
+    a dropped slab or finite-field term, a wrong target index or a missing self term fails here."""
+    base = synth.tiny_cell(seed=4, n_pairs=4)
+    if geometry == "dc":
+        w = synth.mirror_to_doubled(base, "independent", seed=40)
+    elif geometry == "slab":
+        w = dataclasses.replace(base, geometry="slab")
+    else:
+        w = base
+    R, Q, dpsi = w.elyt_xyz[0], w.elyt_q[0], float(w.dpsi[0])
+    rng = np.random.default_rng(11)
+    # a charge vector that is neither neutral nor mirror-symmetric, so every column of A counts
+    q = 0.02 * rng.standard_normal(w.n_elec)
+    A = cpm.elastance(w)
+    Aq = A @ q
+    assert np.max(np.abs(cpm.elastance_apply(w, q) - Aq)) <= 1e-12 * np.max(np.abs(Aq))
+    b = cpm.b_vector(w, R, Q)
+    ie = rng.choice(w.n_elec, 19, replace=False)
+    assert np.max(np.abs(cpm.b_at(w, R, Q, ie) - b[ie])) <= 1e-12 * np.max(np.abs(b))
+    F_l, _ = cpm.forces(w, R, Q, q, dpsi)
+    il = rng.choice(len(Q), 5, replace=False)
+    F_at = cpm.electrolyte_forces_at(w, R, Q, q, dpsi, il)
+    assert np.max(np.abs(F_at - F_l[il])) <= 1e-12 * np.max(np.abs(F_l))
