@@ -295,8 +295,10 @@ int cpm_counters(const cpm_ctx* ctx, int64_t* kernel_launches);
  * stencils and the FFT plans.  Arguments are those of cpm_step_charges with n_rep = 1:
  * elyt_offsets_dev [2], q_dev / b_dev [N_e], psibar_dev [ncons].
  *
- * - The first call on a device looks up the array's device address (cudaGetSymbolAddress, with
- *   that device current); make that first call before any stream capture.
+ * - The array's device address is looked up (cudaGetSymbolAddress, with the device current) when
+ *   a context is built on that device, so a context built after a cudaDeviceReset sees the
+ *   array where the reloaded library put it.  On a device with no context built since the
+ *   library was loaded, the first call does the lookup: make that call before any stream capture.
  * - Returns CPM_ERR_CAPACITY (see cpm_last_error) when the context's mesh, electrolyte capacity
  *   and electrode count need more scratch than CPM_STATIC_SCRATCH_BYTES.
  * - Every call shares the one array and it keeps the previous call's contents (each call clears

@@ -470,6 +470,7 @@ __device__ __forceinline__ void batch_weights(int i0, int n, int nb, size_t kbas
 
 // Entry points implemented in cpm_step.cu, used by the build (Sv, checks).
 int cpm_internal_alloc_step_buffers(cpm_ctx* c);
+int cpm_internal_static_scratch_setup();   // device address of cpm_step_charges_static's array
 int cpm_internal_fft_setup(cpm_ctx* c);
 int cpm_internal_convolve_own(cpm_ctx* c, int nrep, int energy_slot, cudaStream_t st);
 cpm::SpmeGeom cpm_internal_spme_geom(const cpm_ctx* c);

@@ -186,10 +186,11 @@ __global__ void __launch_bounds__(256) k_charge_prep(const double* __restrict__ 
 // Screened kernels of one pair at squared distance r2 (0 < r2 < rc^2): the potential factor
 // pr = (erfc(alpha r) - erfc(beta r)) / r (beta = 0: point source, erfc(beta r) = 1 dropped) and the
 // force factor fr = [pr + 2/sqrt(pi) (alpha e^{-alpha^2 r^2} - beta e^{-beta^2 r^2})] / r^2.
-// float64: the library erfc and exp.  float32: erfc(x) = t P(t) e^{-x^2}, t = 1 / (1 + p x), the
-// rational approximation of Abramowitz & Stegun 7.1.26 (Hastings), so that one exponential serves
-// both the potential and the force term; its absolute error is below 1.5e-7 for all x >= 0
-// (relative error below 3e-5 for x < 2, growing to 7e-4 at the cutoff x = alpha r_c = 3).
+// float64: the library erfc and exp.  float32: erfc(x) = t P(t) e^{-x^2}, t = 1 / (1 + p x), P of
+// degree 7 (Hastings' form, as in Abramowitz & Stegun 7.1.26, with coefficients fitted here to the
+// relative error of erfc(x) e^{x^2} on 0 <= x <= 6.5 by erfc_fit.py: below 4e-8, under the float32
+// rounding of the evaluation), so that one exponential serves both the potential and the force
+// term and float32 pair sums carry no systematic approximation error.
 template <typename T> struct PairMath;
 template <> struct PairMath<double> {
   template <bool FORCE>
@@ -208,9 +209,15 @@ template <> struct PairMath<double> {
 };
 template <> struct PairMath<float> {
   __device__ __forceinline__ static float erfc_e(float x, float e) {     // e = exp(-x^2)
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, x, 1.0f));
-    const float poly = fmaf(fmaf(fmaf(fmaf(1.061405429f, t, -1.453152027f), t, 1.421413741f), t, -0.284496736f), t,
-                            0.254829592f);
+    const float t = __fdividef(1.0f, fmaf(0.42f, x, 1.0f));
+    float poly = 7.600673979e-02f;
+    poly = fmaf(poly, t, -3.450624826e-01f);
+    poly = fmaf(poly, t, 4.849799364e-01f);
+    poly = fmaf(poly, t, -1.730866602e-01f);
+    poly = fmaf(poly, t, 2.924322982e-01f);
+    poly = fmaf(poly, t, 1.871011462e-01f);
+    poly = fmaf(poly, t, 2.408978217e-01f);
+    poly = fmaf(poly, t, 2.367312164e-01f);
     return t * poly * e;
   }
   template <bool FORCE>
@@ -2412,6 +2419,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   if (c->mixed && (int)R >= cpm::TC_MIN_REPLICAS) CPM_CUDA(cudaMalloc(&c->qraw32, sizeof(float) * R * ne));
   CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
   CPM_CUDA(cudaMemset(c->status, 0, sizeof(int)));
+  CPM_TRY(cpm_internal_static_scratch_setup());
   return CPM_OK;
 }
 
@@ -2695,8 +2703,12 @@ constexpr int kMaxDevices = 64;
 void* g_static_addr[kMaxDevices] = {};   // device address of the array, per device ordinal
 }  // namespace
 
-// Host code cannot use the array's name as a device address; look it up once per device.
-static int static_scratch(void** out) {
+// Host code cannot use the array's name as a device address: its address on the current device is
+// looked up with cudaGetSymbolAddress.  The lookup runs whenever a context is built on that device
+// (refresh = true: a cudaDeviceReset invalidates every earlier context and may move the array, and
+// a new build is the only way on), else on the first call on a device with no context built since
+// the library was loaded.
+static int static_scratch(void** out, bool refresh) {
   int dev = 0;
   CPM_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) {
@@ -2704,10 +2716,11 @@ static int static_scratch(void** out) {
     return CPM_ERR_ARG;
   }
   std::lock_guard<std::mutex> lock(g_static_mu);
-  if (!g_static_addr[dev]) {
+  if (refresh || !g_static_addr[dev]) {
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_cpm_static_scratch);
     if (e != cudaSuccess || !p) {
+      g_static_addr[dev] = nullptr;
       cpm::set_error("cudaGetSymbolAddress(static scratch): %s", cudaGetErrorString(e));
       return CPM_ERR_CUDA;
     }
@@ -2715,6 +2728,12 @@ static int static_scratch(void** out) {
   }
   *out = g_static_addr[dev];
   return CPM_OK;
+}
+
+// Set-up at context build (current device = the context's device).
+int cpm_internal_static_scratch_setup() {
+  void* p = nullptr;
+  return static_scratch(&p, true);
 }
 
 extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const double* xyzq, const double* dpsi,
@@ -2728,7 +2747,7 @@ extern "C" int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* off, const d
     return CPM_ERR_ARG;
   }
   void* base_v = nullptr;
-  CPM_TRY(static_scratch(&base_v));
+  CPM_TRY(static_scratch(&base_v, false));
   unsigned char* base = static_cast<unsigned char*>(base_v);
   const size_t tsz = ctx->mixed ? sizeof(float) : sizeof(double);
   const size_t v4 = ctx->mixed ? sizeof(float4) : sizeof(double4_32a);

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import synth
+from kkt_checks import check_psibar
 from oracle import cpm as ocpm
 
 pytestmark = pytest.mark.gpu
@@ -32,7 +33,9 @@ TOL = {"fp64": dict(q=1e-5, f=1e-5, e=1e-7, b=1e-6),
        "mixed": dict(q=1e-5, f=1e-5, e=2e-6, b=5e-5)}
 
 
-def _check(res, ref, prec, r=0, tol=None):
+def _check(res, ref, prec, r=0, tol=None, oracle=None):
+    """Element-wise comparison of a GPU result with the oracle's step `ref`; `oracle` (the
+    oracle.cpm.Reference that produced it) enables the offset-potential checks."""
     t = dict(TOL[prec])
     if tol:
         t.update(tol)
@@ -40,7 +43,9 @@ def _check(res, ref, prec, r=0, tol=None):
     assert np.max(np.abs(q - qo)) <= t["q"]
     assert abs(q.sum()) <= 1e-12 * max(1.0, np.abs(q).sum())
     assert np.max(np.abs(res["b"][r] - ref["b"])) <= t["b"] * np.sqrt(np.mean(ref["b"] ** 2))
-    assert np.max(np.abs(res["psibar"][r] - ref["psibar"])) <= 1e-4
+    if oracle is not None:
+        # the oracle holds the single-replica view of replica r
+        check_psibar(res["psibar"][r], res["b"][r], float(oracle.w.dpsi[0]), oracle, ref["psibar"], ref["b"])
     F, Fo = res["F_elyt"][r], ref["F_elyt"]
     assert np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum()) <= t["f"]
     Fe, Feo = res["F_elec"][r], ref["F_elec"]
@@ -65,7 +70,7 @@ def _run(w, prec, **kw):
 def test_plain_finite_field_cell(plain_ff, prec):
     w, ref, out = plain_ff
     s, res = _run(w, prec, order=8)
-    _check(res, out, prec)
+    _check(res, out, prec, oracle=ref)
 
 
 def test_projected_inverse_and_capacitance(plain_ff):
@@ -89,9 +94,10 @@ def test_doubled_cell_and_slab(prec, geometry):
         w.grid = (18, 16, 144)
     else:
         w = dataclasses.replace(base, geometry="slab", grid=(18, 16, 216))
-    ref = ocpm.Reference(w).step()
+    oracle = ocpm.Reference(w)
+    ref = oracle.step()
     s, res = _run(w, prec, order=8)
-    _check(res, ref, prec)
+    _check(res, ref, prec, oracle=oracle)
     if geometry == "dc":
         n = w.n_elec // 2
         assert abs(res["q"][0][n:].sum()) <= 1e-12      # sub-cell 1 neutral on its own (Eq. 12)
@@ -117,7 +123,7 @@ def test_batched_ragged_replicas_match_per_replica_oracle():
         ref.w = wr
         out = ref.step()
         # the paper's 1 A, order-5 mesh on a dense point-ion electrolyte
-        _check(res, out, "mixed", r=r, tol=dict(f=5e-5, e=1e-4, b=2e-5))
+        _check(res, out, "mixed", r=r, tol=dict(f=5e-5, e=1e-4, b=2e-5), oracle=ref)
 
 
 def test_fused_step_equals_separate_calls(plain_ff):
@@ -184,7 +190,7 @@ def test_paper_mesh_errors(plain_ff):
     w, ref, out = plain_ff
     for prec in ("fp64", "mixed"):
         s, res = _run(w, prec)
-        _check(res, out, prec, tol=dict(f=5e-5, e=3e-5, b=1e-5))
+        _check(res, out, prec, tol=dict(f=5e-5, e=3e-5, b=1e-5), oracle=ref)
 
 
 def test_batched_tensor_core_s_apply_matches_float64_path():

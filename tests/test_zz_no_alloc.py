@@ -4,8 +4,9 @@ Some callers cannot call cudaMalloc while they run (allocator-free regions of a 
 real-time loops with a no-allocation rule); cpm_step_charges_static serves them from a static
 device array.  Its charges, b and offsets must match the allocating cpm_step_charges on the
 same context and inputs, on two calls in a row (the array keeps the previous call's contents,
-so the second call checks that everything that must start at zero is cleared).  A context whose
-scratch does not fit the array is rejected with CPM_ERR_CAPACITY.
+so the second call checks that everything that must start at zero is cleared), and calls after
+the first leave the device's free memory unchanged.  A context whose scratch does not fit the
+array is rejected with CPM_ERR_CAPACITY.
 
 This file is named to run last, so a failure here leaves every other test already run.
 """
@@ -43,6 +44,16 @@ def test_static_scratch_entry_matches_allocating_entry(prec, geometry):
     s.charges()
     torch.cuda.synchronize()
     q_ref, b_ref, p_ref = s.q.clone(), s.b.clone(), s.psibar.clone()
+    # the contract itself: after a first call, further calls leave the device's free memory as it
+    # was (any cudaMalloc, or a library routine that allocates, would take at least one page)
+    qa, ba, pa = torch.empty_like(s.q), torch.empty_like(s.b), torch.empty_like(s.psibar)
+    g.cpm_step_charges_static(s.ctx, s.offsets, s.xyzq, s.dpsi, qa, ba, pa)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for _ in range(2):
+        g.cpm_step_charges_static(s.ctx, s.offsets, s.xyzq, s.dpsi, qa, ba, pa)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
     for _ in range(2):
         q = torch.full_like(s.q, float("nan"))
         b = torch.full_like(s.b, float("nan"))
