@@ -29,7 +29,7 @@ import numpy as np
 from scipy.linalg import cho_factor, cho_solve
 
 from .ewald import (KE, SQRT2, SQRT_PI, default_kmax, image_shifts, real_space, recip_matrix,
-                    recip_space, screened)
+                    recip_space, screened, recip_space_separable)
 
 
 # ----------------------------------------------------------------------------------------------
@@ -108,21 +108,33 @@ def elastance(w, kmax=None) -> np.ndarray:
     return A
 
 
-def elastance_apply(w, q, kmax=None) -> np.ndarray:
-    """A q without forming A: the potential (V) at each electrode site due to the Gaussian
-    charges q (used for residual checks where N_e is too large for a dense A).
+def elastance_apply(w, q, kmax=None, idx=None, kspace="direct") -> np.ndarray:
+    """A q without forming A: the potential (V) at each electrode site (or at the sites idx only)
+    due to the Gaussian charges q (used for residual checks where N_e is too large for a dense A).
+    kspace="separable" evaluates the reciprocal sum through recip_space_separable (the same sum).
     Eq. 3 (A), Eq. 4 (Psi = A q - b)."""
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)
-    phi = real_space(E, E, q, box, w.rcut, w.alpha, w.eta / SQRT2, same=True)
-    phi += recip_space(E, E, q, box, w.alpha, kmax)
-    phi += (SQRT2 * w.eta - 2.0 * w.alpha) / SQRT_PI * q
+    T = E if idx is None else E[idx]
+    rec = _recip(kspace)
+    phi = real_space(T, E, q, box, w.rcut, w.alpha, w.eta / SQRT2, same=True, target_index=idx)
+    phi += rec(T, E, q, box, w.alpha, kmax)
+    qt = q if idx is None else q[idx]
+    phi += (SQRT2 * w.eta - 2.0 * w.alpha) / SQRT_PI * qt
     phi *= KE
     if w.geometry == "slab":
         V = float(np.prod(box))
-        z = E[:, 2]
-        phi += KE * (4.0 * math.pi / V) * z * float(z @ q)
+        phi += KE * (4.0 * math.pi / V) * T[:, 2] * float(E[:, 2] @ q)
     return phi
+
+
+def _recip(kspace):
+    """The reciprocal-sum routine: the direct cos/sin sum or its per-axis factorised form."""
+    if kspace == "direct":
+        return recip_space
+    if kspace == "separable":
+        return recip_space_separable
+    raise ValueError(f"kspace must be 'direct' or 'separable', got {kspace!r}")
 
 
 def b_vector(w, R, Q, kmax=None) -> np.ndarray:
@@ -339,12 +351,12 @@ class Reference:
 # ----------------------------------------------------------------------------------------------
 # sampled checks for workloads too large for a dense oracle solve
 # ----------------------------------------------------------------------------------------------
-def b_at(w, R, Q, idx, kmax=None) -> np.ndarray:
-    """b_i (Eq. 3) at the electrode sites idx only."""
+def b_at(w, R, Q, idx, kmax=None, kspace="direct") -> np.ndarray:
+    """b_i (Eq. 3) at the electrode sites idx only (kspace as in elastance_apply)."""
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)[idx]
     phi = real_space(E, R, Q, box, w.rcut, w.alpha, w.eta)
-    phi += recip_space(E, R, Q, box, w.alpha, kmax)
+    phi += _recip(kspace)(E, R, Q, box, w.alpha, kmax)
     b = -KE * phi
     if w.geometry == "slab":
         V = float(np.prod(box))
@@ -352,9 +364,9 @@ def b_at(w, R, Q, idx, kmax=None) -> np.ndarray:
     return b
 
 
-def electrolyte_forces_at(w, R, Q, q, dpsi, idx, kmax=None) -> np.ndarray:
-    """Forces on the electrolyte sites idx for given electrode charges q (as in forces()).
-    minus the gradient of Eq. 3 at fixed q (Sec. II.A)."""
+def electrolyte_forces_at(w, R, Q, q, dpsi, idx, kmax=None, kspace="direct") -> np.ndarray:
+    """Forces on the electrolyte sites idx for given electrode charges q (as in forces()):
+    minus the gradient of Eq. 3 at fixed q (Sec. II.A); kspace as in elastance_apply."""
     box = ewald_box(w)
     E = np.asarray(w.elec_xyz, np.float64)
     T = R[idx]
@@ -362,7 +374,7 @@ def electrolyte_forces_at(w, R, Q, q, dpsi, idx, kmax=None) -> np.ndarray:
     _, g_ll = real_space(T, R, Q, box, w.rcut, w.alpha, None, same=True, want_grad=True, target_index=idx)
     P = np.vstack([E, R])
     c = np.concatenate([q, Q])
-    _, g_k = recip_space(T, P, c, box, w.alpha, kmax, want_grad=True)
+    _, g_k = _recip(kspace)(T, P, c, box, w.alpha, kmax, want_grad=True)
     F = -KE * Q[idx, None] * (g_le + g_ll + g_k)
     if w.geometry == "slab":
         V = float(np.prod(box))

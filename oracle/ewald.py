@@ -198,3 +198,66 @@ def recip_matrix(positions, box, alpha, kmax=None, kchunk=2048):
         s = np.sin(p) * sw
         M += c @ c.T + s @ s.T
     return M
+
+
+def recip_space_separable(targets, sources, charges, box, alpha, kmax=None, want_grad=False, schunk=4096,
+                          tchunk=4096):
+    """The sum of recip_space (same half-space k-vectors, weights and cutoff), evaluated through the
+    factorisation exp(i k.r) = exp(i k_x x) exp(i k_y y) exp(i k_z z) of every plane wave with
+    k = 2 pi (m_x/L_x, m_y/L_y, m_z/L_z): one table of exp(2 pi i m x / L) per axis and site, the
+    structure factor S(m) = sum_a c_a X_a(m_x) Y_a(m_y) Z_a(m_z) as matrix products over the
+    sources, and the potential sum_k w_k Re[S(k) exp(-i k.r)] likewise over the targets.  Used
+    where recip_space's cos/sin per (site, k) is out of reach (10^5 sites x 10^5-10^6 k-vectors);
+    equal to recip_space to rounding (pinned in the tests).  Sec. II.B (Ewald summation,
+    reciprocal part)."""
+    targets = np.asarray(targets, np.float64)
+    sources = np.asarray(sources, np.float64)
+    charges = np.asarray(charges, np.float64)
+    box = np.asarray(box, np.float64)
+    kmax = default_kmax(alpha) if kmax is None else kmax
+    mmax = [int(math.floor(kmax * L / (2 * math.pi))) for L in box]
+    mx = np.arange(0, mmax[0] + 1)
+    my = np.arange(-mmax[1], mmax[1] + 1)
+    mz = np.arange(-mmax[2], mmax[2] + 1)
+    # the half-space set and weights of kvectors() / recip_weights() on the (m_x, m_y, m_z) block
+    MX, MY, MZ = np.meshgrid(mx, my, mz, indexing="ij")
+    half = (MX > 0) | ((MX == 0) & (MY > 0)) | ((MX == 0) & (MY == 0) & (MZ > 0))
+    kx, ky, kz = (2 * math.pi * MX / box[0], 2 * math.pi * MY / box[1], 2 * math.pi * MZ / box[2])
+    k2 = kx * kx + ky * ky + kz * kz
+    keep = half & (k2 <= kmax * kmax)
+    wk = np.zeros(MX.shape)
+    V = float(np.prod(box))
+    wk[keep] = 2.0 * (4.0 * math.pi / V) * np.exp(-k2[keep] / (4.0 * alpha * alpha)) / k2[keep]
+
+    def tables(p):
+        ph = 2 * math.pi * p / box[None, :]
+        return (np.exp(1j * ph[:, 0:1] * mx[None, :]), np.exp(1j * ph[:, 1:2] * my[None, :]),
+                np.exp(1j * ph[:, 2:3] * mz[None, :]))
+
+    S = np.zeros(MX.shape, complex)
+    for a in range(0, sources.shape[0], schunk):
+        X, Y, Z = tables(sources[a:a + schunk])
+        cX = charges[a:a + schunk, None] * X
+        for i in range(mx.size):
+            S[i] += (cX[:, i:i + 1] * Y).T @ Z
+    G = wk * S
+    nt = targets.shape[0]
+    phi = np.zeros(nt)
+    grad = np.zeros((nt, 3)) if want_grad else None
+    Gs = [G] + ([G * MY, G * MZ] if want_grad else [])
+    for a in range(0, nt, tchunk):
+        X, Y, Z = tables(targets[a:a + tchunk])
+        Xc, Yc, Zc = np.conj(X), np.conj(Y), np.conj(Z)
+        acc = [np.zeros(Xc.shape[0], complex) for _ in range(4 if want_grad else 1)]
+        for i in range(mx.size):
+            part = [((Gi[i] @ Zc.T).T * Yc).sum(axis=1) * Xc[:, i] for Gi in Gs]
+            acc[0] += part[0]
+            if want_grad:
+                acc[1] += mx[i] * part[0]
+                acc[2] += part[1]
+                acc[3] += part[2]
+        phi[a:a + tchunk] = acc[0].real
+        if want_grad:
+            for d in range(3):
+                grad[a:a + tchunk, d] = (2 * math.pi / box[d]) * acc[d + 1].imag
+    return (phi, grad) if want_grad else phi

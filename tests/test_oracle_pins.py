@@ -423,12 +423,14 @@ def test_forces_are_minus_energy_gradient(geometry):
     assert np.max(np.abs(total)) < 1e-9 * scale
 
 
+@pytest.mark.parametrize("kspace", ["direct", "separable"])
 @pytest.mark.parametrize("geometry", ["ff", "dc", "slab"])
-def test_sampled_checkers_equal_the_dense_oracle(geometry):
+def test_sampled_checkers_equal_the_dense_oracle(geometry, kspace):
     """The matrix-free and sampled helpers that check the full-size GPU runs (elastance_apply,
-    b_at, electrolyte_forces_at) against the dense oracle they restate (Eq. 3 for A and b, the
-    fixed-charge forces of Sec. II.A), which the pins above tie to the paper and to physics:
-    a dropped slab or finite-field term, a wrong target index or a missing self term fails here."""
+    b_at, electrolyte_forces_at, with either form of the reciprocal sum) against the dense oracle
+    they restate (Eq. 3 for A and b, the fixed-charge forces of Sec. II.A), which the pins above
+    tie to the paper and to physics: a dropped slab or finite-field term, a wrong target index or
+    a missing self term fails here."""
     base = synth.tiny_cell(seed=4, n_pairs=4)
     if geometry == "dc":
         w = synth.mirror_to_doubled(base, "independent", seed=40)
@@ -442,11 +444,27 @@ def test_sampled_checkers_equal_the_dense_oracle(geometry):
     q = 0.02 * rng.standard_normal(w.n_elec)
     A = cpm.elastance(w)
     Aq = A @ q
-    assert np.max(np.abs(cpm.elastance_apply(w, q) - Aq)) <= 1e-12 * np.max(np.abs(Aq))
-    b = cpm.b_vector(w, R, Q)
+    assert np.max(np.abs(cpm.elastance_apply(w, q, kspace=kspace) - Aq)) <= 1e-12 * np.max(np.abs(Aq))
     ie = rng.choice(w.n_elec, 19, replace=False)
-    assert np.max(np.abs(cpm.b_at(w, R, Q, ie) - b[ie])) <= 1e-12 * np.max(np.abs(b))
+    assert np.max(np.abs(cpm.elastance_apply(w, q, idx=ie, kspace=kspace) - Aq[ie])) <= 1e-12 * np.max(np.abs(Aq))
+    b = cpm.b_vector(w, R, Q)
+    assert np.max(np.abs(cpm.b_at(w, R, Q, ie, kspace=kspace) - b[ie])) <= 1e-12 * np.max(np.abs(b))
     F_l, _ = cpm.forces(w, R, Q, q, dpsi)
     il = rng.choice(len(Q), 5, replace=False)
-    F_at = cpm.electrolyte_forces_at(w, R, Q, q, dpsi, il)
+    F_at = cpm.electrolyte_forces_at(w, R, Q, q, dpsi, il, kspace=kspace)
     assert np.max(np.abs(F_at - F_l[il])) <= 1e-12 * np.max(np.abs(F_l))
+
+
+@pytest.mark.parametrize("box", [(17.04, 17.22, 60.0), (38.34, 34.44, 336.0), (12.0, 13.0, 9.0)])
+def test_separable_reciprocal_sum_equals_direct_sum(box):
+    """recip_space_separable (per-axis plane-wave tables) is the same sum as recip_space
+    (cos/sin per site and k-vector): potentials and gradients agree to rounding."""
+    rng = np.random.default_rng(5)
+    box = np.asarray(box)
+    src = rng.random((300, 3)) * box
+    c = rng.standard_normal(300)
+    tgt = rng.random((40, 3)) * box
+    p1, g1 = ewald.recip_space(tgt, src, c, box, 0.3, want_grad=True)
+    p2, g2 = ewald.recip_space_separable(tgt, src, c, box, 0.3, want_grad=True)
+    assert np.max(np.abs(p1 - p2)) <= 1e-13 * np.max(np.abs(p1))
+    assert np.max(np.abs(g1 - g2)) <= 1e-13 * np.max(np.abs(g1))
