@@ -3,13 +3,21 @@
 
 A step is one whole pass of the per-timestep CPM electrostatics (cpm_step: cell list, b from
 real-space pairs + SPME, q = S(b + dpsi v) with the neutrality projection, SPME + real-space
-forces on all electrolyte sites, float64 energies); with --workload paper-md it is one time step
-of the whole MD loop (cpm_md_run).  Default: the paper-scale finite-field cell:
-3,024 graphite electrode sites (9 x 14 cells x 3 layers x 2 electrodes, 38.34 x 34.44 x 168 A),
-500 coarse-grained ion pairs (2,000 sites), SPME mesh 40 x 36 x 168 (1 A), order 5, alpha 0.25,
-r_c 12 A, eta 1.979.  ns/day assumes one step per 2 fs timestep (Appendix A of the paper).
+forces on all sites -- electrolyte and electrode --, float64 energies), captured in one CUDA graph;
+with --workload paper-md it is one time step of the whole MD loop (cpm_md_run).
 
-  python bench.py [--gpus N --steps K --warmup W --precision mixed|fp64 --impl gb300|reference]
+Default workload: the large doubled cell -- 40,320 electrode sites (two mirrored 125 x 123 x 100 A
+sub-cells with three-layer electrodes), 25,000 coarse-grained ion pairs (100,000 sites), SPME mesh
+128 x 128 x 200 order 5, alpha 0.25, r_c 12 A, eta 1.979; S stored as two 20,160^2 mirror blocks.
+ns/day assumes one step per 2 fs timestep (Appendix A of the paper); a doubled cell simulates two
+cells, so its data ns/day is twice that.
+
+The line also carries, on one GPU: the same workload on the plain float64 path (`plain_fp64`), the
+errors of the timed step against the float64 path and against the FP64 oracle (`accuracy`), the
+paper-scale cell (`paper_cell`), 64 batched replicas on the tensor-core S-apply (`batched`) and the
+oracle timed on the host's cores (`cpu_baseline`).
+
+  python bench.py [--gpus N --steps K --warmup W --workload W --precision mixed|fp64 --impl gb300|reference]
 
 N > 1 runs under torchrun: every rank steps an independent replica (different seed) on its own
 GPU; there is no collective on the data path (replicas only), value is the aggregate.
@@ -21,9 +29,11 @@ import argparse
 import json
 import math
 import os
+import pickle
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -35,16 +45,20 @@ NS_PER_DAY_PER_STEP_PER_S = 2.0e-6 * 86400.0        # 2 fs per step -> ns/day pe
 L2_FLUSH_BYTES = 256 << 20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-baseline-child", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--oracle-out", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="only the main line: no float64 comparison, accuracy, paper-cell, batched or CPU objects")
+    ap.add_argument("--child", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--workload-file", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--child-out", default=None, help=argparse.SUPPRESS)
+    ap.add_argument("--child-in", default=None, help=argparse.SUPPRESS)
     ap.add_argument("--seed", type=int, default=None)
     ap.add_argument("--kernels", default="auto",
                     help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
@@ -56,15 +70,16 @@ def parse():
                     help="z cells per block of the real-space pair kernels (default: the autotuner's choice)")
     ap.add_argument("--charge-every", type=int, default=5,
                     help="MD workloads: re-solve the electrode charges every k steps (Appendix B: 5)")
-    ap.add_argument("--workload", default="paper", choices=["paper", "paper-dc", "paper-slab", "paper-proximal", "large",
-                                                            "dc-large", "paper-md", "paper-dc-md"],
-                    help="paper: the paper-scale cell (default); paper-dc / paper-slab: the same cell as a doubled "
+    ap.add_argument("--workload", default="dc-large",
+                    choices=["paper", "paper-dc", "paper-slab", "paper-proximal", "large", "dc-large", "paper-md",
+                             "paper-dc-md"],
+                    help="dc-large (default): the 40,320-site doubled cell (mirror blocks, mesh-operator A); "
+                         "paper: the paper-scale cell; paper-dc / paper-slab: the same cell as a doubled "
                          "cell (6,048 sites, mirror blocks) or a slab (3x z padding); paper-proximal: only the "
-                         "1,008 proximal-layer sites charged; large: the 10,080-site cell; "
-                         "dc-large: the 40,320-site doubled cell (mirror blocks, mesh-operator A); paper-md / "
+                         "1,008 proximal-layer sites charged; large: the 10,080-site cell; paper-md / "
                          "paper-dc-md: the whole MD loop (velocity-Verlet, Nose-Hoover, Lennard-Jones, charges "
                          "re-solved every --charge-every steps) on point-ion versions of the paper cells")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 def replica_seed(base, rank):
@@ -119,6 +134,9 @@ GEOMETRY_NAME = {"paper": "finite field", "paper-dc": "doubled cell", "paper-sla
                  "paper-proximal": "finite field", "large": "finite field",
                  "dc-large": "doubled cell", "paper-md": "finite field", "paper-dc-md": "doubled cell"}
 MD_WORKLOADS = ("paper-md", "paper-dc-md")
+# workloads whose oracle step fits the host in seconds to a minute (dense A and its Cholesky factor);
+# the others are checked and timed through sampled sums
+DENSE_ORACLE = ("paper", "paper-dc", "paper-slab", "paper-proximal", "paper-md", "paper-dc-md")
 
 
 def workload(seed, kind="paper"):
@@ -138,6 +156,14 @@ def workload(seed, kind="paper"):
     if kind == "paper-dc-md":
         return synth.md_cell(seed=seed, geometry="dc")
     return synth.config_paper_cell(seed=seed)
+
+
+def load_workload(args):
+    """The workload of a child process: from the parent's pickle (config 5 takes ~20 s to draw)."""
+    if args.workload_file:
+        with open(args.workload_file, "rb") as f:
+            return pickle.load(f)
+    return workload(args.seed, args.workload)
 
 
 def system_options(kind):
@@ -204,27 +230,25 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------------------------
-# roofline models per phase: algorithmic bytes (HBM-bound kernels) or FP32 flops (ALU-bound pair
-# kernels) per launch.  Phases made of one kernel of this library are the candidates for the
-# dominant kernel; the FFT phases are mostly cuFFT.
+# roofline models per phase: algorithmic bytes (HBM-bound kernels), FP32 flops (ALU-bound pair
+# kernels) or tensor flops (the batched tcgen05 S-apply) per launch.  Phases made of one kernel of
+# this library are the candidates for the dominant kernel; the FFT phases are mostly cuFFT.
 # ----------------------------------------------------------------------------------------------
 PAIR_FLOPS = 40            # FP32 flops per pair interaction within r_c (distance 8, erfc/exp 20, force 12)
+TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tf32 / bf16 tensor rate of GB300
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels, keyed by workload
 # and "phase:kernel variant" (the autotuner may pick another S-apply kernel, whose traffic was not
-# captured: then traffic is null).  Summaries: profiles/dram_k_sapply32_k_pair_cell_paper-cell-ff-mixed.md,
-# profiles/dram_k_sapply_sym_k_pair_cell_large-cell-ff-mixed.md (the S-apply phase there is the packed
-# kernel plus its finishing kernel, so its traffic is the sum of both).  Set an entry to None whenever its kernel changes.
-NCU_TRAFFIC_MIXED = {"paper": {"s_apply:rows": 36.74e6, "f_pair_elyt": 0.21248e6, "b_real": 0.1157e6},
-                     "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {}, "paper-dc-md": {},
-                     "large": {"s_apply:sym": 212.28e6, "f_pair_elyt": 0.7493e6},
-                     "dc-large": {}}
+# captured: then traffic is null).  Set an entry to None whenever its kernel changes.
+NCU_TRAFFIC_MIXED = {"paper": {}, "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {},
+                     "paper-dc-md": {}, "large": {}, "dc-large": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
 
 
 def pair_counts(w):
     """Ordered (target, source) pairs within r_c for the workload: electrolyte targets with
-    electrolyte and electrode sources (forces), electrode targets with electrolyte sources (b)."""
+    electrolyte and electrode sources (forces), electrode targets with electrolyte sources (b) and,
+    for electrode forces, with electrolyte and electrode sources."""
     from scipy.spatial import cKDTree
     import numpy as np
     box = np.asarray(w.box, float)
@@ -233,7 +257,8 @@ def pair_counts(w):
     tl, te = cKDTree(R, boxsize=box), cKDTree(E, boxsize=box)
     ll = int(tl.count_neighbors(tl, w.rcut)) - len(R)       # ordered pairs, self excluded
     le = int(tl.count_neighbors(te, w.rcut))
-    return {"f_pair_elyt": ll + le, "b_real": le}
+    ee = int(te.count_neighbors(te, w.rcut)) - len(E)
+    return {"f_pair_elyt": ll + le, "b_real": le, "f_pair_elec": le + ee}
 
 
 def phase_model(phase, s, w, pairs):
@@ -272,17 +297,19 @@ def setup_ranks():
     return world, rank, local, torch.device("cuda", local)
 
 
-def build_system(args, w, dev):
+def build_system(args, w, dev, precision=None, image=None, tune=True):
     """Build the context (timed) and pick the kernels (autotuned or fixed by --kernels)."""
     import torch
     import paper_2201_12963_gb300 as g
     from paper_2201_12963_gb300.driver import System
     tb = time.perf_counter()
-    s = System(w, args.precision, device=dev, **system_options(args.workload))
+    s = System(w, precision or args.precision, device=dev, image=image, **system_options(args.workload))
     torch.cuda.synchronize(dev)
     build_s = time.perf_counter() - tb
+    variants = ("default", "default", "default")
     if args.kernels == "auto":
-        variants = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
+        if tune:
+            variants = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
     else:
         variants = tuple(args.kernels.split(","))
         g.cpm_set_sapply_variant(s.ctx, variants[0])
@@ -302,24 +329,26 @@ def load_peaks():
         return {}
 
 
-def roofline(args, s, w, phase_ms, clk, sapply_variant):
+def roofline(workload_kind, s, w, phase_ms, clk):
     """Roofline objects of the dominant single-kernel phase and of the S-apply (per launch, from the
     library's per-phase CUDA events)."""
     peaks = load_peaks()
     pairs = pair_counts(w)
-    mixed_prec = args.precision == "mixed"
+    mixed_prec = s.params.precision == 1
+    sapply_variant = s.sapply_variant
 
     def roof_for(p):
         bound, amount, unit, desc = phase_model(p, s, w, pairs)
         sec = phase_ms[p] / 1e3
         if bound == "hbm":
             achieved, peak = amount / sec / 1e9, float(peaks.get("hbm_gbs", 6800.0))
-            src = "measured (MEASURED_PEAKS.json hbm_gbs)" if "hbm_gbs" in peaks else "fallback"
+            src = ("of measured (MEASURED_PEAKS.json hbm_gbs, burst copy)" if "hbm_gbs" in peaks
+                   else "of fallback (6.8 TB/s)")
         else:
             achieved, peak = amount / sec / 1e12, alu_peak_tflops(clk.get("sm_mhz"))
-            src = "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock"
+            src = "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock under load"
         key = f"{p}:{sapply_variant}" if p == "s_apply" else p
-        traffic = NCU_TRAFFIC_MIXED[args.workload].get(key) if mixed_prec else None
+        traffic = NCU_TRAFFIC_MIXED.get(workload_kind, {}).get(key) if mixed_prec else None
         return {"bound": bound, "kernel": p, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_per_launch": amount,
                 "launch_ms": round(phase_ms[p], 5), "peak_source": src, "model": desc}
@@ -330,53 +359,44 @@ def roofline(args, s, w, phase_ms, clk, sapply_variant):
     if roof is not None:
         roof["dominant_phase_overall"] = max(phase_ms, key=phase_ms.get)
     roof_s = roof_for("s_apply") if "s_apply" in phase_ms else None
-    return roof, roof_s
+    roof_pair = roof_for("f_pair_elyt") if "f_pair_elyt" in phase_ms else None
+    return roof, roof_s, roof_pair
 
 
-def run_gb300(args):
-    import numpy as np
+# ----------------------------------------------------------------------------------------------
+# timing helpers
+# ----------------------------------------------------------------------------------------------
+def capture_step(s, elec, dev):
+    """Warm the step up on a side stream, then capture one cpm_step in a CUDA graph."""
     import torch
-    import torch.distributed as dist
-    import paper_2201_12963_gb300 as g
-
-    if args.workload in MD_WORKLOADS:
-        return run_md(args)
-    world, rank, local, dev = setup_ranks()
-    w = workload(replica_seed(args.seed, rank), args.workload)
-    s, build_s, (sapply_variant, fft_variant, mesh_variant) = build_system(args, w, dev)
-
-    # the whole step captured once into a CUDA graph
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream(dev))
     with torch.cuda.stream(side):
         for _ in range(3):
-            s.step(elec=False, energy=True)
+            s.step(elec=elec, energy=True)
     torch.cuda.current_stream(dev).wait_stream(side)
     torch.cuda.synchronize(dev)
-    st = g.cpm_status(s.ctx)
-    if st != 0:
-        raise RuntimeError(f"device status after warm-up: {g.cpm_strerror(st)}")
-    l0 = g.cpm_counters(s.ctx)
-    s.step(elec=False, energy=True)
-    torch.cuda.synchronize(dev)
-    launches_per_step = g.cpm_counters(s.ctx) - l0
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph):
-        s.step(elec=False, energy=True)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+        s.step(elec=elec, energy=True)
+    return graph
 
-    for _ in range(max(3, args.warmup)):
+
+def time_replays(graph, flush, K, dev, warmup=3, world=1, clocks=None):
+    """Replays of graph with L2 flushed before each, CUDA events around each replay on the launching
+    stream; (total ms, per-step ms list, host wall seconds)."""
+    import torch
+    import torch.distributed as dist
+    for _ in range(max(3, warmup)):
         graph.replay()
     torch.cuda.synchronize(dev)
-
-    K = args.steps
     ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    clocks = ClockSampler(local)
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize(dev)
-    clocks.start()
+    if clocks is not None:
+        clocks.start()
     wall0 = time.perf_counter()
     for k in range(K):
         flush.zero_()
@@ -387,95 +407,609 @@ def run_gb300(args):
     wall = time.perf_counter() - wall0
     if world > 1:
         dist.barrier()
-    clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    tot_ms = reduce_max(sum(step_ms), dev)
-    ms_per_step = tot_ms / K
-    steps_per_s = aggregate_steps_per_s(tot_ms, K, world)
-    value = steps_per_s * NS_PER_DAY_PER_STEP_PER_S
-    st = g.cpm_status(s.ctx)
-    if st != 0:
-        raise RuntimeError(f"device status after the timed region: {g.cpm_strerror(st)}")
+    return sum(step_ms), step_ms, wall
 
-    # ---- end to end through the public API with host buffers ----
-    Ke = min(K, 50)
-    off, xyzq = __import__("paper_2201_12963_gb300.driver", fromlist=["pack"]).pack(w)
+
+def profile_phases(s, flush, K, elec):
+    """Per-phase device times (ms per launch) of K direct calls, L2 flushed before each call."""
+    import paper_2201_12963_gb300 as g
+    g.cpm_profile_enable(s.ctx, 16 * K + 16)
+    for _ in range(K):
+        flush.zero_()
+        s.step(elec=elec, energy=True)
+    prof = g.cpm_profile_read(s.ctx)
+    g.cpm_profile_enable(s.ctx, 0)
+    return {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1] > 0}
+
+
+def end_to_end(s, w, graph, dev, steps, world, elec):
+    """The same step through the public API with host buffers: every step copies the electrolyte
+    positions and charges in from pinned host memory and the electrode charges, forces and energies
+    back; (ns/day, bytes in, bytes out)."""
+    import torch
+    from paper_2201_12963_gb300.driver import pack
+    off, xyzq = pack(w)
     h_xyzq = torch.from_numpy(xyzq).pin_memory()
-    nl = int(off[-1])
+    nl, ne = int(off[-1]), s.ne
+    h_q = torch.empty(ne, dtype=torch.float64).pin_memory()
     h_f = torch.empty(3 * nl, dtype=torch.float64).pin_memory()
+    h_fe = torch.empty(3 * ne, dtype=torch.float64).pin_memory()
     h_e = torch.empty(4, dtype=torch.float64).pin_memory()
     torch.cuda.synchronize(dev)
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     e0.record()
-    for _ in range(Ke):
+    for _ in range(steps):
         s.xyzq.copy_(h_xyzq, non_blocking=True)
         graph.replay()
+        h_q.copy_(s.q[:ne], non_blocking=True)
         h_f.copy_(s.f_elyt[: 3 * nl], non_blocking=True)
+        if elec:
+            h_fe.copy_(s.f_elec[: 3 * ne], non_blocking=True)
         h_e.copy_(s.energy[:4], non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
     e1.record()
     torch.cuda.synchronize(dev)
     e2e_s = reduce_max(max(time.perf_counter() - t0, e0.elapsed_time(e1) / 1e3), dev)
-    e2e_value = world * Ke / e2e_s * NS_PER_DAY_PER_STEP_PER_S
+    d2h = 8 * (ne + 3 * nl + (3 * ne if elec else 0) + 4)
+    return world * steps / e2e_s * NS_PER_DAY_PER_STEP_PER_S, int(xyzq.nbytes), int(d2h)
 
-    # ---- per-phase profile of the same step (events inside the library), L2 flushed per step ----
-    Kp = min(K, 50)
-    g.cpm_profile_enable(s.ctx, 16 * Kp + 16)
-    for _ in range(Kp):
-        flush.zero_()
-        s.step(elec=False, energy=True)
-    prof = g.cpm_profile_read(s.ctx)
-    g.cpm_profile_enable(s.ctx, 0)
-    phase_ms = {k: v[0] / max(1, v[1]) for k, v in prof.items() if v[1] > 0}
-    roof, roof_s = roofline(args, s, w, phase_ms, clk, sapply_variant)
 
+def step_results(s, elec):
+    """q, electrolyte forces, electrode forces and energies of the last step (host copies)."""
+    r = s.results()
+    return {"q": r["q"][0], "F_elyt": r["F_elyt"][0], "F_elec": r["F_elec"][0] if elec else None,
+            "energy": r["energy"][0]}
+
+
+def precision_errors(mixed, fp64):
+    """The timed (mixed-precision) step against the float64 GPU path on the same input and mesh:
+    the float32 error, apart from the mesh discretisation that both share."""
+    import numpy as np
+
+    def rms(a, b):
+        return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+    out = {"dq_max_e": float(np.abs(mixed["q"] - fp64["q"]).max()),
+           "force_rms_rel_elyt": rms(mixed["F_elyt"], fp64["F_elyt"]),
+           "energy_U_rel": float(abs(mixed["energy"][0] - fp64["energy"][0]) / abs(fp64["energy"][0])),
+           "energy_H_rel": float(abs(mixed["energy"][1] - fp64["energy"][1]) / abs(fp64["energy"][1]))}
+    if mixed["F_elec"] is not None and fp64["F_elec"] is not None:
+        out["force_rms_rel_elec"] = rms(mixed["F_elec"], fp64["F_elec"])
+    return out
+
+
+# ----------------------------------------------------------------------------------------------
+# the GPU arm
+# ----------------------------------------------------------------------------------------------
+def run_gb300(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2201_12963_gb300 as g
+
+    if args.workload in MD_WORKLOADS:
+        return run_md(args)
+    world, rank, local, dev = setup_ranks()
+    w = workload(replica_seed(args.seed, rank), args.workload)
+    s, build_s, (sapply_variant, fft_variant, mesh_variant) = build_system(args, w, dev)
+    s.sapply_variant = sapply_variant
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # ---- the timed step: charges, forces on all sites, energies; one CUDA graph ----
+    graph = capture_step(s, True, dev)
+    st = g.cpm_status(s.ctx)
+    if st != 0:
+        raise RuntimeError(f"device status after warm-up: {g.cpm_strerror(st)}")
+    l0 = g.cpm_counters(s.ctx)
+    s.step(elec=True, energy=True)
+    torch.cuda.synchronize(dev)
+    launches_per_step = g.cpm_counters(s.ctx) - l0
+    K = args.steps
+    clocks = ClockSampler(local)
+    tot_ms, step_ms, wall = time_replays(graph, flush, K, dev, args.warmup, world, clocks)
+    clk = clocks.stop()
+    tot_ms = reduce_max(tot_ms, dev)
+    ms_per_step = tot_ms / K
+    steps_per_s = aggregate_steps_per_s(tot_ms, K, world)
+    value = steps_per_s * NS_PER_DAY_PER_STEP_PER_S
+    st = g.cpm_status(s.ctx)
+    if st != 0:
+        raise RuntimeError(f"device status after the timed region: {g.cpm_strerror(st)}")
+    mixed_res = step_results(s, True)
+
+    # the same step without electrode forces (a frozen electrode in MD needs none)
+    graph_fe = capture_step(s, False, dev)
+    Kf = min(K, 300)
+    tot_fe, _, _ = time_replays(graph_fe, flush, Kf, dev, 3, world)
+    tot_fe = reduce_max(tot_fe, dev)
+    del graph_fe
+
+    e2e_value, h2d, d2h = end_to_end(s, w, graph, dev, min(K, 50), world, True)
+    phase_ms = profile_phases(s, flush, min(K, 50), True)
+    roof, roof_s, roof_pair = roofline(args.workload, s, w, phase_ms, clk)
+    geo = GEOMETRY_NAME[args.workload]
     out = {"metric": METRIC, "value": round(value, 2), "unit": "ns/day", "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "mixed" else "f64",
            "data": "synthetic",
-           "config": {"workload": WORKLOADS[args.workload][0], "geometry": GEOMETRY_NAME[args.workload],
-                      "precision": args.precision, "build_s": round(build_s, 2),
+           "config": {"workload": WORKLOADS[args.workload][0], "geometry": geo, "precision": args.precision,
+                      "precision_detail": ("float32 pair, mesh and S-apply arithmetic with compensated sums; "
+                                           "float64 A, factorisation, projection and energy accumulation"
+                                           if args.precision == "mixed" else "float64 throughout"),
+                      "forces": "all sites (electrolyte and electrode)", "build_s": round(build_s, 2),
                       "s_apply_variant": sapply_variant, "mesh_transform": fft_variant,
                       "charge_assignment": mesh_variant, "pair_group_z": g.cpm_get_pair_group(s.ctx),
                       "pair_kernel": g.cpm_get_pair_variant(s.ctx),
                       "kernel_choice": "autotuned" if args.kernels == "auto" else "fixed by --kernels",
                       "replicas_per_gpu": 1, "parallelism": f"replicas x{world} (no collective)",
-                      "data_ns_per_day": round(value * (2 if GEOMETRY_NAME[args.workload] == "doubled cell" else 1), 2),
+                      "data_ns_per_day": round(value * (2 if geo == "doubled cell" else 1), 2),
                       "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
                       "graph": "whole step captured in one CUDA graph", "steps_per_s": round(steps_per_s, 1),
                       "replica_steps_per_s": round(steps_per_s, 1), "wall_s": round(wall, 3)},
            "clocks": clk,
-           "e2e": {"value": round(e2e_value, 2), "unit": "ns/day",
-                   "h2d_bytes_per_step": int(xyzq.nbytes), "d2h_bytes_per_step": int(8 * 3 * nl + 32),
-                   "steps": Ke},
+           "e2e": {"value": round(e2e_value, 2), "unit": "ns/day", "h2d_bytes_per_step": h2d,
+                   "d2h_bytes_per_step": d2h, "steps": min(K, 50),
+                   "note": "per step: electrolyte xyzq in from pinned host memory; electrode charges, "
+                           "electrolyte and electrode forces and energies out"},
            "gpu_launches": int(launches_per_step * K),
+           "frozen_electrode": {"ms_per_step": round(tot_fe / Kf, 5),
+                                "value": round(world * Kf / (tot_fe / 1e3) * NS_PER_DAY_PER_STEP_PER_S, 2),
+                                "unit": "ns/day", "steps": Kf,
+                                "note": "the same step without electrode forces (forces on electrolyte sites only)"},
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
-           "roofline": roof, "roofline_s_apply": roof_s}
-    q_batched = None
-    if args.workload == "paper":
-        out["batched"], q_batched = batched_replicas(args, dev, flush)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        if args.workload == "paper":
-            out["cpu_baseline"], ref = cpu_baseline(args)
-            if ref is not None:
-                torch.cuda.synchronize(dev)
-                out["accuracy"] = accuracy_against(ref, s.q.cpu().numpy(), s.f_elyt.cpu().numpy(),
-                                                   s.energy[:4].cpu().numpy())
-                if q_batched is not None and "q_batched" in ref:
-                    try:
-                        out["batched"]["accuracy"] = batched_accuracy(ref["q_batched"], q_batched)
-                    except Exception as e:      # the line is printed whatever this comparison does
-                        out["batched"]["accuracy"] = {"error": f"{type(e).__name__}: {e}"[:300]}
-        else:
-            out["cpu_baseline"] = {
-                "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
-                "sample": f"not run: the oracle's dense A for {w.n_elec:,} sites takes hours on the host"}
+           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair}
+    del graph
+    if rank == 0 and world == 1 and not args.no_extras:
+        extras(args, w, s, mixed_res, dev, flush, out)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def extras(args, w, s, mixed_res, dev, flush, out):
+    """Everything beside the main line (rank 0, one GPU).  The GPU sub-runs come first; the CPU
+    oracle work runs afterwards in child processes (two at a time at most), so that host load does
+    not disturb any GPU timing."""
+    import numpy as np
+    import torch
+    tmp = tempfile.mkdtemp(prefix="cpm-bench-")
+    wfile = os.path.join(tmp, "workload.pkl")
+    with open(wfile, "wb") as f:
+        pickle.dump(w, f)
+    # charges, b and offsets of one charge update: the inputs of the oracle comparison
+    s.charges()
+    r = s.results()
+    np.savez(os.path.join(tmp, "gpu.npz"), q=mixed_res["q"], F_elyt=mixed_res["F_elyt"], energy=mixed_res["energy"],
+             q_c=r["q"][0], b_c=r["b"][0], psibar_c=r["psibar"][0])
+    # ---- GPU: the same workload on the plain float64 path ----
+    try:
+        out["plain_fp64"], fp64_res = plain_fp64(args, w, s, dev, flush)
+        prec = precision_errors(mixed_res, fp64_res)
+    except Exception as e:                # the line is printed whatever this sub-run does
+        out["plain_fp64"], prec = {"error": f"{type(e).__name__}: {e}"[:300]}, None
+    torch.cuda.empty_cache()
+    # ---- GPU: the paper-scale cell and the batched replicas ----
+    paper_pending = None
+    if args.workload == "dc-large":
+        try:
+            out["paper_cell"], paper_pending = paper_cell(args, dev, flush, tmp)
+        except Exception as e:
+            out["paper_cell"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    torch.cuda.empty_cache()
+    q_batched = None
+    try:
+        out["batched"], q_batched = batched_replicas(args, dev, flush)
+    except Exception as e:
+        out["batched"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    # ---- CPU: the oracle ----
+    acc = {"vs_plain_fp64_gpu": prec}
+    first = []
+    if args.workload in DENSE_ORACLE:
+        first.append(("oracle", spawn_child(args, "oracle-step", wfile, os.path.join(tmp, "oracle.npz"),
+                                            batched=args.workload == "paper")))
+    else:
+        first.append(("accuracy", spawn_child(args, "accuracy-large", wfile, os.path.join(tmp, "acc.json"),
+                                              os.path.join(tmp, "gpu.npz"))))
+    if paper_pending is not None:
+        a2, pwfile = paper_pending[2], paper_pending[3]
+        first.append(("paper", spawn_child(a2, "oracle-step", pwfile, os.path.join(tmp, "paper_oracle.npz"),
+                                           batched=True)))
+    done = {name: finish_child(c) for name, c in first}
+    if "oracle" in done:
+        ok, ref = done["oracle"]
+        if ok:
+            acc["vs_oracle"] = accuracy_against(ref, mixed_res)
+            out["cpu_baseline"] = ref["cpu_baseline"]
+            if args.workload == "paper" and q_batched is not None and "q_batched" in ref:
+                out["batched"]["accuracy"] = batched_accuracy(ref["q_batched"], q_batched)
+        else:
+            acc["vs_oracle"] = {"error": ref}
+    if "accuracy" in done:
+        ok, res = done["accuracy"]
+        acc["vs_oracle"] = res if ok else {"error": res}
+    out["accuracy"] = acc
+    if paper_pending is not None:
+        finish_paper_cell(out["paper_cell"], done["paper"], paper_pending[1], out.get("batched"), q_batched)
+    if not args.no_cpu_baseline and args.workload not in DENSE_ORACLE:
+        ok, res = finish_child(spawn_child(args, "oracle-sample", wfile, os.path.join(tmp, "cpu_all.json"),
+                                           cores=os.cpu_count() or 1))
+        base = res if ok else {"value": None, "unit": "ns/day", "kind": "oracle", "error": res}
+        ok1, res1 = finish_child(spawn_child(args, "oracle-sample", wfile, os.path.join(tmp, "cpu_1.json"), cores=1))
+        base["one_core"] = res1 if ok1 else {"error": res1}
+        out["cpu_baseline"] = base
+
+
+def plain_fp64(args, w, s_mixed, dev, flush):
+    """The same workload and mesh on the float64 path: S from the mixed context's matrix image
+    (no second assembly and factorisation of A), the float64 kernels, the same graph timing."""
+    import torch
+    import paper_2201_12963_gb300 as g
+    t0 = time.perf_counter()
+    image = g.cpm_matrix_image(s_mixed.ctx)
+    s, build_s, _ = build_system(args, w, dev, precision="fp64", image=image, tune=False)
+    del image
+    graph = capture_step(s, True, dev)
+    K = min(args.steps, 100)
+    tot, _, _ = time_replays(graph, flush, K, dev, 3)
+    res = step_results(s, True)
+    st = g.cpm_status(s.ctx)
+    ms = tot / K
+    obj = {"ms_per_step": round(ms, 5), "value": round(1e3 / ms * NS_PER_DAY_PER_STEP_PER_S, 3), "unit": "ns/day",
+           "steps": K, "status": st, "build_from_image_s": round(time.perf_counter() - t0, 2),
+           "note": "float64 pair, mesh, S-apply and energies; same mesh and kernels' structure, default variants"}
+    del graph, s
+    return obj, res
+
+
+def spawn_child(args, mode, wfile, out_path, in_path=None, cores=None, batched=False):
+    """Start `bench.py --child mode` (CPU oracle work) in the background; batched: the oracle step
+    child also solves the batched replicas' charges (untimed)."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--child", mode, "--workload", args.workload,
+           "--seed", str(args.seed), "--workload-file", wfile, "--child-out", out_path]
+    if in_path:
+        cmd += ["--child-in", in_path]
+    env = dict(os.environ)
+    env["CUDA_VISIBLE_DEVICES"] = ""            # host work only
+    if cores is not None:
+        n = str(cores)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = n
+        env["CPM_ORACLE_PROCS"] = n
+    if batched:
+        env["CPM_BENCH_BATCHED"] = "1"
+    p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True, env=env)
+    return p, out_path
+
+
+def finish_child(child, timeout=900):
+    """(ok, result): a child's output file, or its error."""
+    p, out_path = child
+    try:
+        so, se = p.communicate(timeout=timeout)
+    except subprocess.TimeoutExpired:
+        p.kill()
+        return False, "timed out"
+    if p.returncode != 0 or not os.path.exists(out_path):
+        return False, (se or so or f"exit {p.returncode}")[-300:]
+    if out_path.endswith(".npz"):
+        import numpy as np
+        with np.load(out_path, allow_pickle=False) as z:
+            ref = {k: z[k] for k in z.files}
+        ref["cpu_baseline"] = json.loads(str(ref.pop("cpu_baseline_json")))
+        return True, ref
+    with open(out_path) as f:
+        return True, json.load(f)
+
+
+def paper_cell(args, dev, flush, tmp):
+    """The paper-scale finite-field cell (3,024 sites) beside the default workload: mixed step
+    timing with its rooflines and the float64 path; the oracle step (one full FP64 step, also the
+    batched replicas' charges) runs later in a child, and finish_paper_cell adds its results."""
+    import torch
+    import paper_2201_12963_gb300 as g
+    a2 = argparse.Namespace(**vars(args))
+    a2.workload, a2.seed = "paper", WORKLOADS["paper"][1]
+    w = workload(a2.seed, "paper")
+    wfile = os.path.join(tmp, "paper.pkl")
+    with open(wfile, "wb") as f:
+        pickle.dump(w, f)
+    s, build_s, (sv, fv, mv) = build_system(a2, w, dev)
+    s.sapply_variant = sv
+    graph = capture_step(s, True, dev)
+    K = min(args.steps, 500)
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    tot, _, _ = time_replays(graph, flush, K, dev, 3, 1, clocks)
+    clk = clocks.stop()
+    mixed_res = step_results(s, True)
+    st = g.cpm_status(s.ctx)
+    graph_fe = capture_step(s, False, dev)
+    tot_fe, _, _ = time_replays(graph_fe, flush, K, dev, 3)
+    del graph_fe
+    phase_ms = profile_phases(s, flush, min(K, 50), True)
+    roof, roof_s, roof_pair = roofline("paper", s, w, phase_ms, clk)
+    ms = tot / K
+    obj = {"workload": WORKLOADS["paper"][0], "precision": a2.precision, "ms_per_step": round(ms, 5),
+           "value": round(1e3 / ms * NS_PER_DAY_PER_STEP_PER_S, 2), "unit": "ns/day", "steps": K, "status": st,
+           "frozen_electrode_ms_per_step": round(tot_fe / K, 5),
+           "kernels": {"s_apply": sv, "transform": fv, "assignment": mv, "pair": g.cpm_get_pair_variant(s.ctx),
+                       "pair_group_z": g.cpm_get_pair_group(s.ctx)},
+           "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
+           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair, "clocks": clk}
+    del graph
+    try:
+        obj["plain_fp64"], fp64_res = plain_fp64(a2, w, s, dev, flush)
+        obj["accuracy"] = {"vs_plain_fp64_gpu": precision_errors(mixed_res, fp64_res)}
+    except Exception as e:
+        obj["plain_fp64"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+        obj["accuracy"] = {}
+    return obj, (None, mixed_res, a2, wfile)
+
+
+def finish_paper_cell(obj, done, mixed_res, batched_obj, q_batched):
+    """The paper cell's oracle comparison and CPU time, and the batched replicas' accuracy."""
+    ok, ref = done
+    if not ok:
+        obj["accuracy"]["vs_oracle"] = {"error": ref}
+        return
+    obj["accuracy"]["vs_oracle"] = accuracy_against(ref, mixed_res)
+    obj["cpu_baseline"] = ref["cpu_baseline"]
+    if batched_obj is not None and q_batched is not None and "q_batched" in ref:
+        try:
+            batched_obj["accuracy"] = batched_accuracy(ref["q_batched"], q_batched)
+        except Exception as e:
+            batched_obj["accuracy"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+
+
+def graph_step_ms(s, flush, steps, dev, elec=True):
+    """Mean CUDA-event time per replay of one captured cpm_step, L2 flushed before every replay."""
+    graph = capture_step(s, elec, dev)
+    tot, _, _ = time_replays(graph, flush, steps, dev, 3)
+    return tot / steps
+
+
+def batched_replicas(args, dev, flush):
+    """Replica throughput: 64 replicas of the 672-site plain cell (400-600 point-ion pairs each,
+    dpsi 0-4 V) in one batched step (mixed precision, tensor-core S-apply), against the plain
+    float64 path stepping one replica of the same cell.  Returns the line's object and the
+    batched step's charges [64, 672]."""
+    import synth
+    import paper_2201_12963_gb300 as g
+    from paper_2201_12963_gb300.driver import System
+    steps = max(10, min(args.steps, 200))
+    wb = synth.config_batched(n_rep=64)
+    sb = System(wb, "mixed", device=dev)
+    ms_b = graph_step_ms(sb, flush, steps, dev)
+    st = g.cpm_status(sb.ctx)
+    q_b = sb.results()["q"]
+    phase_ms = profile_phases(sb, flush, 20, True)
+    peaks = load_peaks()
+    ne, R = sb.ne, 64
+    flops = 2 * 3 * ne * ne * R                   # three tf32 products (hi.hi + hi.lo + lo.hi) of S Y
+    t_s = phase_ms.get("s_apply")
+    peak = float(peaks.get("bf16_tflops", 1900.0)) * TF32_OVER_BF16
+    roof = None
+    if t_s:
+        ach = flops / (t_s / 1e3) / 1e12
+        roof = {"bound": "tensor", "kernel": "s_apply (k_sapply_tc + float64 epilogue)", "achieved": round(ach, 3),
+                "peak": round(peak, 1), "unit": "TFLOP/s", "frac": round(ach / peak, 5), "traffic": None,
+                "algorithmic_per_launch": flops, "launch_ms": round(t_s, 5),
+                "peak_source": "measured bf16 burst (MEASURED_PEAKS.json) x nominal tf32/bf16 ratio 1.1/2.25",
+                "model": f"2 x 3 x {ne} x {ne} x {R} flops (split-TF32: three products)"}
+    w1 = wb.replica(0)
+    s1 = System(w1, "fp64", device=dev)
+    ms_1 = graph_step_ms(s1, flush, steps, dev)
+    return {"workload": "64 replicas x 672-site plain cell (17.04x17.22x60 A), 400-600 point-ion pairs each, "
+                        "mesh 18x18x60 order 5, forces on all sites",
+            "replicas": 64, "precision": "mixed, tcgen05 split-TF32 S-apply",
+            "ms_per_step": round(ms_b, 5), "replica_steps_per_s": round(64 * 1e3 / ms_b, 1),
+            "plain_fp64_one_replica": {"ms_per_step": round(ms_1, 5), "steps_per_s": round(1e3 / ms_1, 1)},
+            "speedup_replica_steps": round((64 / ms_b) / (1 / ms_1), 2), "status": st,
+            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()}, "roofline": roof}, q_b
+
+
+def batched_oracle_charges(n_rep=64):
+    """The oracle's charges [n_rep, 672] for every replica of the batched workload (one A and
+    Cholesky factor for the shared electrode, one b and KKT solve per replica)."""
+    import numpy as np
+    import synth
+    from oracle import cpm as ocpm
+    wb = synth.config_batched(n_rep=n_rep)
+    ref = ocpm.Reference(wb.replica(0))
+    out = np.zeros((n_rep, wb.n_elec))
+    for r in range(n_rep):
+        out[r] = ref.charges(wb.elyt_xyz[r], wb.elyt_q[r], float(wb.dpsi[r]))[0]
+    return out
+
+
+def batched_accuracy(q_ref, q):
+    """Per-replica max |dq| (e) of the batched step's charges against the oracle's."""
+    import numpy as np
+    q_ref = np.asarray(q_ref)
+    q = np.asarray(q).reshape(q_ref.shape[0], -1)[:, : q_ref.shape[1]]
+    dq = np.abs(q - q_ref).max(axis=1)
+    return {"dq_max_e": float(dq.max()), "dq_max_e_per_replica": [float(f"{x:.3g}") for x in dq],
+            "replicas_within_1e-5_e": int((dq <= 1e-5).sum()), "replicas": int(dq.size),
+            "reference": "FP64 CPU oracle (direct Ewald b, KKT solve) per replica on the same input"}
+
+
+def accuracy_against(ref, res):
+    """Errors of one GPU step against the oracle's step on the same input: max |dq| (e), RMS
+    relative force error on the electrolyte, relative error of U and of H."""
+    import numpy as np
+    q = np.asarray(res["q"]).reshape(-1)[: ref["q"].size]
+    F = np.asarray(res["F_elyt"]).reshape(-1, 3)[: ref["F_elyt"].shape[0]]
+    Fo = ref["F_elyt"]
+    e = res["energy"]
+    return {"dq_max_e": float(np.abs(q - ref["q"]).max()),
+            "force_rms_rel": float(np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum())),
+            "energy_U_rel": float(abs(e[0] - ref["U"]) / abs(ref["U"])),
+            "energy_H_rel": float(abs(e[1] - ref["H"]) / abs(ref["H"])),
+            "reference": "FP64 CPU oracle (direct Ewald sums, dense KKT solve) on the same input"}
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle children
+# ----------------------------------------------------------------------------------------------
+def child_oracle_step(args):
+    """One full oracle step (dense A and its Cholesky factor built first, untimed): its results
+    and its time, as an .npz."""
+    import numpy as np
+    from oracle import cpm as ocpm
+    w = load_workload(args)
+    ref = ocpm.Reference(w)
+    t0 = time.perf_counter()
+    out = ref.step(0)
+    dt = time.perf_counter() - t0
+    extra = {}
+    if os.environ.get("CPM_BENCH_BATCHED") == "1":        # untimed: the batched line's per-replica accuracy
+        extra["q_batched"] = batched_oracle_charges()
+    base = {"value": round(NS_PER_DAY_PER_STEP_PER_S / dt, 6), "unit": "ns/day", "cores": os.cpu_count(),
+            "kind": "oracle", "seconds_per_step": round(dt, 3),
+            "sample": "one full FP64 oracle step (direct Ewald b, KKT solve with a prebuilt Cholesky factor, "
+                      "full-Ewald energy and forces) of the workload; numpy, BLAS threads = all cores, "
+                      "elementwise work single-threaded"}
+    np.savez(args.child_out, q=out["q"], F_elyt=out["F_elyt"], U=out["U"], H=out["H"], psibar=out["psibar"],
+             b=out["b"], cpu_baseline_json=json.dumps(base), **extra)
+
+
+def child_accuracy_large(args):
+    """The timed step of a workload too large for a dense oracle solve, against the oracle at
+    sampled sites (reciprocal sums through the per-axis plane-wave tables): b at 64 electrode sites,
+    electrolyte forces at 64 sites from the GPU's charges, and the KKT residual
+    A q - b - dpsi v - C psibar at 256 electrode sites from the GPU's charges, b and offsets."""
+    import numpy as np
+    from oracle import cpm as ocpm
+    w = load_workload(args)
+    with np.load(args.child_in) as z:
+        gpu = {k: z[k] for k in z.files}
+    R, Q, dpsi = w.elyt_xyz[0], w.elyt_q[0], float(w.dpsi[0])
+    rng = np.random.default_rng(7)
+    ie = np.sort(rng.choice(w.n_elec, 64, replace=False))
+    il = np.sort(rng.choice(len(Q), 64, replace=False))
+    ik = np.sort(rng.choice(w.n_elec, 256, replace=False))
+    t0 = time.perf_counter()
+    b_ref = ocpm.b_at(w, R, Q, ie, kspace="separable")
+    F_ref = ocpm.electrolyte_forces_at(w, R, Q, gpu["q"], dpsi, il, kspace="separable")
+    Aq = ocpm.elastance_apply(w, gpu["q_c"], idx=ik, kspace="separable")
+    C = ocpm.constraints(w)[ik]
+    v = ocpm.geometry_vector(w)[ik]
+    resid = Aq - gpu["b_c"][ik] - dpsi * v - C @ gpu["psibar_c"]
+    fit = np.linalg.lstsq(C, resid, rcond=None)[0]
+    F = gpu["F_elyt"][il]
+    out = {"b_max_abs_V": float(np.abs(gpu["b_c"][ie] - b_ref).max()),
+           "b_rms_V": float(np.sqrt(np.mean(gpu["b_c"] ** 2))),
+           "b_max_rel_to_rms": float(np.abs(gpu["b_c"][ie] - b_ref).max() / np.sqrt(np.mean(gpu["b_c"] ** 2))),
+           "force_rms_rel_elyt": float(np.sqrt(((F - F_ref) ** 2).sum() / (F_ref ** 2).sum())),
+           "kkt_residual_max_V": float(np.abs(resid).max()),
+           "kkt_residual_offset_fit_V": [float(x) for x in fit],
+           "kkt_residual_after_offsets_max_V": float(np.abs(resid - C @ fit).max()),
+           "sites": {"b": 64, "forces": 64, "kkt": 256}, "seconds": round(time.perf_counter() - t0, 1),
+           "reference": "FP64 oracle at sampled sites: direct real-space sums and the direct reciprocal sum "
+                        "(per-axis plane-wave tables, pinned to the cos/sin sum), alpha 0.25, r_c 12 A; the "
+                        "GPU's A is the mesh operator of its own SPME (the direct sum is out of reach at this "
+                        "size), so the residual also carries the mesh error of A; the full Ewald energy at this "
+                        "size is not evaluated (all-pairs real-space sums over 1.4e5 sites)"}
+    with open(args.child_out, "w") as f:
+        json.dump(out, f)
+
+
+def _sample_worker(payload):
+    """One sampled oracle step in a worker process: (seconds)."""
+    wfile, frac, seed = payload
+    import numpy as np
+    from oracle import cpm as ocpm
+    with open(wfile, "rb") as f:
+        w = pickle.load(f)
+    q = np.zeros(w.n_elec)
+    t0 = time.perf_counter()
+    ocpm.sampled_step_sums(w, w.elyt_xyz[0], w.elyt_q[0], frac, seed, q=q)
+    return time.perf_counter() - t0
+
+
+class SampledOracle:
+    """The oracle's per-step sums of a workload too large for its dense A (b, energies and forces
+    at given electrode charges; the KKT solve is left out because A cannot be formed), run as
+    bounded samples (a fraction f of the real-space targets and of the k-vectors) on `procs`
+    worker processes at once.  With every worker taking fraction f, a sample costs
+    T(f) = a + b f; a full step on `procs` cores, one worker per 1/procs of the work, costs
+    a + b / procs."""
+
+    def __init__(self, wfile, procs):
+        import multiprocessing as mp
+        self.wfile, self.procs = wfile, max(1, procs)
+        self.pool = mp.get_context("spawn").Pool(self.procs) if self.procs > 1 else None
+        self.seed = 0
+
+    def sample(self, frac):
+        self.seed += self.procs
+        jobs = [(self.wfile, frac, self.seed + k) for k in range(self.procs)]
+        t0 = time.perf_counter()
+        if self.pool is None:
+            _sample_worker(jobs[0])
+        else:
+            self.pool.map(_sample_worker, jobs)
+        return time.perf_counter() - t0
+
+    def fit(self, f1, f2):
+        t1, t2 = self.sample(f1), self.sample(f2)
+        b = max(1e-9, (t2 - t1) / (f2 - f1))
+        return max(0.0, t1 - b * f1), b
+
+    def calibrate(self, work_s=10.0):
+        """(a, b, fractions, times): two short samples for a first T(f), a third whose f-part is
+        about work_s seconds, and the least-squares line through the three."""
+        import numpy as np
+        fs = [2e-5, 8e-5]
+        ts = [self.sample(f) for f in fs]
+        b0 = max(1e-9, (ts[1] - ts[0]) / (fs[1] - fs[0]))
+        fs.append(min(0.5, work_s / b0))
+        ts.append(self.sample(fs[2]))
+        b, a = np.polyfit(fs, ts, 1)
+        return max(0.0, float(a)), max(1e-9, float(b)), fs, ts
+
+    def close(self):
+        if self.pool is not None:
+            self.pool.close()
+            self.pool.join()
+
+
+def oracle_procs():
+    """Worker processes for the sampled oracle: the cores asked for, bounded by host memory
+    (about 3 GB per worker at 10^5 sources)."""
+    want = int(os.environ.get("CPM_ORACLE_PROCS", str(os.cpu_count() or 1)))
+    try:
+        mem_gb = os.sysconf("SC_PAGE_SIZE") * os.sysconf("SC_PHYS_PAGES") / 2 ** 30
+        want = min(want, max(1, int(mem_gb // 6)))
+    except (ValueError, OSError):
+        pass
+    return max(1, want)
+
+
+def child_oracle_sample(args):
+    """cpu_baseline of a large workload: the sampled oracle on the cores given (one worker each),
+    scaled to a full step through the two-point fit."""
+    procs = oracle_procs()
+    so = SampledOracle(args.workload_file, procs)
+    try:
+        a, b, fs, ts = so.calibrate()
+        t_full = a + b / procs
+    finally:
+        so.close()
+    w = load_workload(args)
+    base = {"value": round(NS_PER_DAY_PER_STEP_PER_S / t_full, 8), "unit": "ns/day", "cores": procs,
+            "kind": "oracle", "seconds_per_step": round(t_full, 1),
+            "sample": (f"{procs} worker process(es), one core each (BLAS threads {os.environ.get('OMP_NUM_THREADS', 'default')}); "
+                       f"each sample restricts every real-space sum to a random fraction f of its target sites and "
+                       f"every reciprocal sum to a fraction f of the k-vectors, all workers at once; samples at "
+                       f"f = {', '.join(f'{x:.2e}' for x in fs)} ({', '.join(f'{x:.1f}' for x in ts)} s) give "
+                       f"T(f) = {a:.2f} s + {b:.0f} s x f; a full step is "
+                       f"a + b/{procs}. The KKT solve is not included: the oracle's dense A for "
+                       f"{w.n_elec:,} sites cannot be formed on the host (its reciprocal part alone is "
+                       f"~10^16 flops), so the electrode charges are held fixed")}
+    with open(args.child_out, "w") as f:
+        json.dump(base, f)
 
 
 def run_md(args):
@@ -494,6 +1028,7 @@ def run_md(args):
     w = workload(replica_seed(args.seed, rank), args.workload)
     mi = synth.md_inputs(w, seed=replica_seed(args.seed, rank) + 1)
     s, build_s, (sapply_variant, fft_variant, mesh_variant) = build_system(args, w, dev)
+    s.sapply_variant = sapply_variant
     k = max(1, args.charge_every)
     m = MD(s, mi, dt=synth.PAPER_TIMESTEP_FS, charge_every=k, lj_cut=w.rcut)
     m.run(0, energy=True)
@@ -579,7 +1114,7 @@ def run_md(args):
     g.cpm_profile_enable(s.ctx, 0)
     g.cpm_status(s.ctx)
     phase_ms = {kk: v[0] / max(1, v[1]) for kk, v in prof.items() if v[1] > 0}
-    roof, roof_s = roofline(args, s, w, phase_ms, clk, sapply_variant)
+    roof, roof_s, roof_pair = roofline(args.workload, s, w, phase_ms, clk)
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "ns/day", "n_gpus": world, "steps": K,
            "warmup": warm, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -605,194 +1140,94 @@ def run_md(args):
                    "note": f"per {k}-step block: state in, block, state and energy record out"},
            "gpu_launches": int(launches_per_block * blocks),
            "phase_ms": {kk: round(v, 5) for kk, v in phase_ms.items()},
-           "roofline": roof, "roofline_s_apply": roof_s}
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args)[0] if args.workload == "paper-md" else {
-            "value": None, "unit": "ns/day", "kind": "oracle", "cores": os.cpu_count(),
-            "sample": "not run for this workload (see the paper-md line)"}
+           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not args.no_extras:
+        tmp = tempfile.mkdtemp(prefix="cpm-bench-")
+        wfile = os.path.join(tmp, "workload.pkl")
+        with open(wfile, "wb") as f:
+            pickle.dump(w, f)
+        ok, ref = finish_child(spawn_child(args, "oracle-step", wfile, os.path.join(tmp, "oracle.npz")))
+        if ok:
+            base = ref["cpu_baseline"]
+            base["sample"] += ("; for the MD workload this is the charge re-solve step, an upper bound of the "
+                               "oracle's MD step (its Lennard-Jones and integration cost are not added)")
+            out["cpu_baseline"] = base
+        else:
+            out["cpu_baseline"] = {"value": None, "unit": "ns/day", "kind": "oracle", "error": ref}
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
 
 
-def graph_step_ms(s, flush, steps, dev):
-    """Capture one cpm_step of System s in a CUDA graph; mean CUDA-event time per replay with L2
-    flushed before every replay."""
-    import torch
-    side = torch.cuda.Stream(dev)
-    side.wait_stream(torch.cuda.current_stream(dev))
-    with torch.cuda.stream(side):
-        for _ in range(3):
-            s.step(elec=False, energy=True)
-    torch.cuda.current_stream(dev).wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        s.step(elec=False, energy=True)
-    for _ in range(3):
-        graph.replay()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
-    torch.cuda.synchronize(dev)
-    for a, b in ev:
-        flush.zero_()
-        a.record()
-        graph.replay()
-        b.record()
-    torch.cuda.synchronize(dev)
-    return sum(a.elapsed_time(b) for a, b in ev) / steps
-
-
-def batched_replicas(args, dev, flush):
-    """Replica throughput: 64 replicas of the 672-site plain cell (400-600 point-ion pairs each,
-    dpsi 0-4 V) in one batched step (mixed precision, tensor-core S-apply), against the plain
-    float64 path stepping one replica of the same cell.  Returns the line's object and the
-    batched step's charges [64, 672]."""
-    import synth
-    import paper_2201_12963_gb300 as g
-    from paper_2201_12963_gb300.driver import System
-    steps = max(10, min(args.steps, 100))
-    wb = synth.config_batched(n_rep=64)
-    sb = System(wb, "mixed", device=dev)
-    ms_b = graph_step_ms(sb, flush, steps, dev)
-    st = g.cpm_status(sb.ctx)
-    q_b = sb.results()["q"]
-    w1 = wb.replica(0)
-    s1 = System(w1, "fp64", device=dev)
-    ms_1 = graph_step_ms(s1, flush, steps, dev)
-    return {"workload": "64 replicas x 672-site plain cell (17.04x17.22x60 A), 400-600 point-ion pairs each, "
-                        "mesh 18x18x60 order 5", "replicas": 64, "precision": "mixed, tcgen05 split-TF32 S-apply",
-            "ms_per_step": round(ms_b, 5), "replica_steps_per_s": round(64 * 1e3 / ms_b, 1),
-            "plain_fp64_one_replica": {"ms_per_step": round(ms_1, 5), "steps_per_s": round(1e3 / ms_1, 1)},
-            "speedup_replica_steps": round((64 / ms_b) / (1 / ms_1), 2), "status": st}, q_b
-
-
-def batched_oracle_charges(n_rep=64):
-    """The oracle's charges [n_rep, 672] for every replica of the batched workload (one A and
-    Cholesky factor for the shared electrode, one b and KKT solve per replica)."""
-    import numpy as np
-    import synth
-    from oracle import cpm as ocpm
-    wb = synth.config_batched(n_rep=n_rep)
-    ref = ocpm.Reference(wb.replica(0))
-    out = np.zeros((n_rep, wb.n_elec))
-    for r in range(n_rep):
-        out[r] = ref.charges(wb.elyt_xyz[r], wb.elyt_q[r], float(wb.dpsi[r]))[0]
-    return out
-
-
-def batched_accuracy(q_ref, q):
-    """Per-replica max |dq| (e) of the batched step's charges against the oracle's."""
-    import numpy as np
-    q_ref = np.asarray(q_ref)
-    q = np.asarray(q).reshape(q_ref.shape[0], -1)[:, : q_ref.shape[1]]
-    dq = np.abs(q - q_ref).max(axis=1)
-    return {"dq_max_e": float(dq.max()), "dq_max_e_per_replica": [float(f"{x:.3g}") for x in dq],
-            "replicas_within_1e-5_e": int((dq <= 1e-5).sum()), "replicas": int(dq.size),
-            "reference": "FP64 CPU oracle (direct Ewald b, KKT solve) per replica on the same input"}
-
 
 # ----------------------------------------------------------------------------------------------
-# CPU oracle timings
+# the reference arm: the FP64 oracle on the host's cores
 # ----------------------------------------------------------------------------------------------
-def cpu_baseline(args):
-    """One full oracle step of the same workload on this host, timed in a child process
-    (the oracle's A and its Cholesky factor are built first, untimed).  The child also leaves its
-    charges, electrolyte forces and energies in a scratch file: the GPU run's errors against them
-    are the line's `accuracy`."""
-    import tempfile
-    fd, path = tempfile.mkstemp(suffix=".npz")
-    os.close(fd)
-    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-baseline-child", "--seed", str(args.seed),
-           "--workload", args.workload, "--oracle-out", path]
-    try:
-        r = subprocess.run(cmd, capture_output=True, text=True, timeout=900)
-        if r.returncode != 0:
-            return {"value": None, "unit": "ns/day", "kind": "oracle", "error": r.stderr[-300:]}, None
-        import numpy as np
-        with np.load(path) as z:
-            ref = {k: z[k] for k in z.files}
-        return json.loads(r.stdout.strip().splitlines()[-1]), ref
-    finally:
-        if os.path.exists(path):
-            os.remove(path)
-
-
-def accuracy_against(ref, q, f_elyt, energy):
-    """Errors of one GPU step against the oracle's step on the same input: max |dq| (e), RMS
-    relative force error on the electrolyte, relative error of U and of H."""
-    import numpy as np
-    q = np.asarray(q).reshape(-1)[: ref["q"].size]
-    F = np.asarray(f_elyt).reshape(-1, 3)[: ref["F_elyt"].shape[0]]
-    Fo = ref["F_elyt"]
-    return {"dq_max_e": float(np.abs(q - ref["q"]).max()),
-            "force_rms_rel": float(np.sqrt(((F - Fo) ** 2).sum() / (Fo ** 2).sum())),
-            "energy_U_rel": float(abs(energy[0] - ref["U"]) / abs(ref["U"])),
-            "energy_H_rel": float(abs(energy[1] - ref["H"]) / abs(ref["H"])),
-            "reference": "FP64 CPU oracle (direct Ewald sums, KKT solve) on the same input"}
-
-
-def cpu_baseline_child(args):
-    from oracle import cpm as ocpm
-    w = workload(args.seed, args.workload)
-    ref = ocpm.Reference(w)
-    t0 = time.perf_counter()
-    out = ref.step(0)
-    dt = time.perf_counter() - t0
-    if args.oracle_out:
-        import numpy as np
-        extra = {}
-        if args.workload == "paper":       # untimed: the batched line's per-replica accuracy
-            extra["q_batched"] = batched_oracle_charges()
-        np.savez(args.oracle_out, q=out["q"], F_elyt=out["F_elyt"], U=out["U"], H=out["H"], **extra)
-    print(json.dumps({"value": round(NS_PER_DAY_PER_STEP_PER_S / dt, 6), "unit": "ns/day", "cores": os.cpu_count(),
-                      "kind": "oracle", "seconds_per_step": round(dt, 3),
-                      "sample": "one full FP64 oracle step (direct Ewald b, KKT solve with a prebuilt Cholesky "
-                                "factor, full-Ewald energy and forces) of the benchmark workload; numpy, "
-                                "BLAS threads = all cores, elementwise work single-threaded"
-                                + ("; for the MD workload this is the charge re-solve step, an upper bound of the "
-                                   "oracle's MD step (its Lennard-Jones and integration cost are not added)"
-                                   if args.workload in MD_WORKLOADS else "")}))
-
-
 def run_reference(args):
-    """The reference arm: the FP64 oracle, each step a bounded sample (a random fraction f of the
-    real-space targets and of the k-vectors), scaled to a full step through a two-point fit
-    t(f) = a + b f made during the warm-up."""
+    """The oracle timed on this host, on the GPU arm's workload, metric and unit.  Workloads with
+    a dense oracle: one full step (its A and Cholesky factor built first, untimed) gives the value,
+    and each timed step is a bounded sample of it (a random fraction f of the real-space targets
+    and of the k-vectors, KKT solve in full).  Larger workloads: the sampled oracle on all cores
+    (SampledOracle), the value from its two-point fit, each timed step one sample of it.
+    ms_per_step is the measured time of the timed (sampled) steps."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if rank != 0:
         return
     from oracle import cpm as ocpm
     w = workload(args.seed, args.workload)
-    ref = ocpm.Reference(w)
-    f1, f2 = 0.03, 0.12
-    t = time.perf_counter(); ref.sampled_step(0, f1, 1); t1 = time.perf_counter() - t
-    t = time.perf_counter(); ref.sampled_step(0, f2, 2); t2 = time.perf_counter() - t
-    b = max(1e-9, (t2 - t1) / (f2 - f1))
-    a = max(0.0, t1 - b * f1)
-    budget = 150.0 / max(1, args.steps + args.warmup)      # keep the whole run within a few minutes
-    f = min(0.5, max(0.01, (budget - a) / b))
-    for k in range(max(0, args.warmup - 2)):
-        ref.sampled_step(0, f, 10 + k)
+    K, W = max(1, args.steps), max(0, args.warmup)
+    budget = 120.0                                     # seconds for the warm-up and timed samples
+    if args.workload in DENSE_ORACLE:
+        ref = ocpm.Reference(w)
+        t0 = time.perf_counter()
+        ref.step(0)
+        t_full = time.perf_counter() - t0
+        procs = os.cpu_count() or 1
+        sampler = lambda f, seed: ref.sampled_step(0, f, seed)   # noqa: E731
+        f_step = min(1.0, max(1e-4, budget / (K + W) / t_full))
+        how = (f"value: one full FP64 oracle step ({t_full:.2f} s: direct Ewald b, KKT solve with a prebuilt "
+               f"Cholesky factor, full-Ewald energy and forces; numpy, BLAS threads = all cores, elementwise work "
+               f"single-threaded); each timed step: a sample with a random fraction f = {f_step:.4f} of the "
+               f"real-space targets and of the k-vectors, KKT solve in full")
+        so = None
+    else:
+        tmp = tempfile.mkdtemp(prefix="cpm-ref-")
+        wfile = os.path.join(tmp, "workload.pkl")
+        with open(wfile, "wb") as f:
+            pickle.dump(w, f)
+        procs = oracle_procs()
+        so = SampledOracle(wfile, procs)
+        a, b, fs, ts = so.calibrate()
+        t_full = a + b / procs
+        f_step = max(1e-7, (budget / (K + W) - a) / b)
+        sampler = lambda f, seed: so.sample(f)       # noqa: E731
+        how = (f"value: {procs} worker processes (one core each) of the oracle's per-step sums, samples at "
+               f"f = {', '.join(f'{x:.2e}' for x in fs)} (a random fraction f of the real-space targets and of the "
+               f"k-vectors per worker) fit T(f) = {a:.2f} s + {b:.0f} s x f, full step = a + b/{procs}; the KKT "
+               f"solve is left out (the dense A for {w.n_elec:,} sites cannot be formed on the host); each "
+               f"timed step: one sample at f = {f_step:.2e}")
+    for k in range(W):
+        sampler(f_step, 10 + k)
     ts = []
-    for k in range(args.steps):
+    for k in range(K):
         t = time.perf_counter()
-        ref.sampled_step(0, f, 100 + k)
+        sampler(f_step, 1000 + k)
         ts.append(time.perf_counter() - t)
-    tmean = sum(ts) / len(ts)
-    t_full = a + (tmean - a) / f
+    if so is not None:
+        so.close()
     value = NS_PER_DAY_PER_STEP_PER_S / t_full
-    sample = (f"per step: real-space sums over a random {f:.3f} of the target sites and reciprocal sums "
-              f"over a random {f:.3f} of the k-vectors, KKT solve in full; full-step time estimated as "
-              f"a + (t - a)/f with a = {a:.3f} s from a two-point fit (t(f) = a + b f)")
-    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": "ns/day", "n_gpus": world,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_full * 1e3, 1),
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+    ms_sample = 1e3 * sum(ts) / len(ts)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": "ns/day", "n_gpus": world,
+           "steps": K, "warmup": W, "ms_per_step": round(ms_sample, 3), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": WORKLOADS[args.workload][0], "geometry": GEOMETRY_NAME[args.workload],
-                      "precision": "fp64 oracle"},
-           "cpu_baseline": {"value": round(value, 6), "unit": "ns/day", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": sample},
-           "e2e": {"value": round(value, 6), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+                      "precision": "fp64 oracle", "full_step_ms": round(t_full * 1e3, 1),
+                      "ms_per_step_is": "the measured time of the timed sampled steps"},
+           "cpu_baseline": {"value": round(value, 8), "unit": "ns/day", "cores": procs, "kind": "oracle",
+                            "sample": how},
+           "e2e": {"value": round(value, 8), "unit": "ns/day", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
 
@@ -800,8 +1235,12 @@ def main():
     args = parse()
     if args.seed is None:
         args.seed = WORKLOADS[args.workload][1]
-    if args.cpu_baseline_child:
-        cpu_baseline_child(args)
+    if args.child == "oracle-step":
+        child_oracle_step(args)
+    elif args.child == "accuracy-large":
+        child_accuracy_large(args)
+    elif args.child == "oracle-sample":
+        child_oracle_sample(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

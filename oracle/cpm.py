@@ -323,29 +323,42 @@ class Reference:
         step; the values it produces are partial sums and are not returned.
         Sec. II.A-B (the sums of step(), partially)."""
         w = self.w
-        rng = np.random.default_rng(seed)
         R, Q, dpsi = w.elyt_xyz[r], w.elyt_q[r], float(w.dpsi[r])
-        box = ewald_box(w)
-        E = np.asarray(w.elec_xyz, np.float64)
-        a, eta, rc = w.alpha, w.eta, w.rcut
-        te = np.flatnonzero(rng.random(E.shape[0]) < frac)
-        tl = np.flatnonzero(rng.random(R.shape[0]) < frac)
+        sampled_step_sums(w, R, Q, frac, seed, self.kmax,
+                          solve=lambda b: solve_charges(self.cho, b, self.v, dpsi, self.C)[0])
 
-        def ksub(n):
-            return rng.random(n) < frac
 
-        b = np.zeros(E.shape[0])
-        b[te] = -KE * real_space(E[te], R, Q, box, rc, a, eta)
-        b -= KE * recip_space(E, R, Q, box, a, self.kmax, ksub=ksub)
-        q, _ = solve_charges(self.cho, b, self.v, dpsi, self.C)
-        P = np.vstack([E, R])
-        c = np.concatenate([q, Q])
-        for grad in (False, True):       # step() evaluates energies, then forces
-            real_space(E[te], E, q, box, rc, a, eta / SQRT2, same=True, want_grad=grad, target_index=te)
-            real_space(E[te], R, Q, box, rc, a, eta, want_grad=grad)
-            real_space(R[tl], E, q, box, rc, a, eta, want_grad=grad)
-            real_space(R[tl], R, Q, box, rc, a, None, same=True, want_grad=grad, target_index=tl)
-            recip_space(P, P, c, box, a, self.kmax, want_grad=grad, ksub=ksub)
+def sampled_step_sums(w, R, Q, frac, seed, kmax=None, solve=None, q=None):
+    """The sums of one step (b; then, at the electrode charges, the energy and force sums) with
+    every real-space sum restricted to a random fraction `frac` of its target sites and every
+    reciprocal sum to a random fraction `frac` of the k-vectors: a bounded timing sample whose
+    cost is close to `frac` times that of the full sums.  The charges come from solve(b) (the KKT
+    solve, Reference.sampled_step) or are given as q where the dense A cannot be formed (tens of
+    thousands of sites).  The values are partial sums and are not returned.
+    Sec. II.A-B (the sums of a step, partially)."""
+    rng = np.random.default_rng(seed)
+    box = ewald_box(w)
+    E = np.asarray(w.elec_xyz, np.float64)
+    a, eta, rc = w.alpha, w.eta, w.rcut
+    te = np.flatnonzero(rng.random(E.shape[0]) < frac)
+    tl = np.flatnonzero(rng.random(R.shape[0]) < frac)
+
+    def ksub(n):
+        return rng.random(n) < frac
+
+    b = np.zeros(E.shape[0])
+    b[te] = -KE * real_space(E[te], R, Q, box, rc, a, eta)
+    b -= KE * recip_space(E, R, Q, box, a, kmax, ksub=ksub)
+    if solve is not None:
+        q = solve(b)
+    P = np.vstack([E, R])
+    c = np.concatenate([q, Q])
+    for grad in (False, True):       # a step evaluates energies, then forces
+        real_space(E[te], E, q, box, rc, a, eta / SQRT2, same=True, want_grad=grad, target_index=te)
+        real_space(E[te], R, Q, box, rc, a, eta, want_grad=grad)
+        real_space(R[tl], E, q, box, rc, a, eta, want_grad=grad)
+        real_space(R[tl], R, Q, box, rc, a, None, same=True, want_grad=grad, target_index=tl)
+        recip_space(P, P, c, box, a, kmax, want_grad=grad, ksub=ksub)
 
 
 # ----------------------------------------------------------------------------------------------

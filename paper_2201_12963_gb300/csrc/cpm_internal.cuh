@@ -126,6 +126,7 @@ struct cpm_ctx {
   int sym_nt = 0;
   float* sym_S = nullptr;
   float* sym_part = nullptr;
+  int* sym_cnt = nullptr;       // per row block: slots written in this call (zero between calls)
   int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
   // mesh convolution variant (enum cpm_fft_variant) and the tables of this library's own
   // float32 transform: per-axis four-step split K = n1 n2 and twiddles exp(-2 pi i t / K)
@@ -267,6 +268,10 @@ template <typename T> struct CompSum {
 // w[t] = M_p(f + t) belongs to mesh point (floor(u) - t); dw[t] = d M_p / du there.
 // Recursion M_n(x) = [x M_{n-1}(x) + (n - x) M_{n-1}(x - 1)] / (n - 1), and
 // M_n'(x) = M_{n-1}(x) - M_{n-1}(x - 1) (Essmann et al., J. Chem. Phys. 103, 8577 (1995)).
+// In float32 the weights are rescaled to sum to one (the partition of unity of the B-splines):
+// the rounded reciprocals 1/(n - 1) of the recursion scale every weight of every site by the same
+// factor, 1 + O(p 2^-24), which would bias each charge's mesh self-energy (hundreds of eV in a
+// cell, cancelled by the exact Ewald self term) by the same relative amount.
 template <typename T>
 __device__ __forceinline__ void bspline(T f, int p, T* w, T* dw) {
 #pragma unroll
@@ -290,6 +295,14 @@ __device__ __forceinline__ void bspline(T f, int p, T* w, T* dw) {
       const T b = (t > 0) ? w[t - 1] : T(0);
       w[t] = ((f + T(t)) * a + (T(n) - f - T(t)) * b) * inv;
     }
+  }
+  if (sizeof(T) == sizeof(float)) {
+    T sum = 0;
+#pragma unroll
+    for (int t = 0; t < PMAX; ++t) sum += (t < p) ? w[t] : T(0);
+    const T norm = T(1) / sum;
+#pragma unroll
+    for (int t = 0; t < PMAX; ++t) w[t] *= norm;
   }
 }
 

@@ -63,13 +63,20 @@ def build_context(params, w, cache_dir=None):
 
 class System:
     def __init__(self, w, precision="fp64", grid=None, order=None, device="cuda", kmax_build=0.0,
-                 max_replicas=None, max_elyt=None, matrix_kspace="ewald", dc_blocks="auto", cache_dir=None):
+                 max_replicas=None, max_elyt=None, matrix_kspace="ewald", dc_blocks="auto", cache_dir=None,
+                 image=None):
+        """image: a matrix image (cpm_matrix_image of a context with the same electrode and build
+        parameters, of either precision) to build from instead of assembling and factorising A."""
         self.w = w
         self.device = torch.device(device)
         self.params = params_for(w, precision, grid, order, max_replicas, max_elyt, kmax_build, matrix_kspace,
                                  dc_blocks)
         with torch.cuda.device(self.device):
-            self.ctx, self.from_cache = build_context(self.params, w, cache_dir)
+            if image is not None:
+                self.ctx = cpm_build_matrix_from_image(self.params, w.elec_xyz, w.elec_side, w.elec_cell, image)
+                self.from_cache = True
+            else:
+                self.ctx, self.from_cache = build_context(self.params, w, cache_dir)
         self.ne = self.ctx.n_elec
         self.load(w)
 

@@ -19,8 +19,8 @@ def test_accuracy_against_the_oracle_record():
            "H": np.float64(-20.0)}
     q = ref["q"] + np.r_[3e-7, np.zeros(49)]
     F = ref["F_elyt"] * 1.001
-    acc = bench.accuracy_against(ref, np.r_[q, [9.0]], np.r_[F.reshape(-1), [5.0, 5.0, 5.0]],
-                                 np.array([-12.5 * (1 + 2e-6), -20.0, 0.0, 0.0]))
+    acc = bench.accuracy_against(ref, {"q": np.r_[q, [9.0]], "F_elyt": np.r_[F.reshape(-1), [5.0, 5.0, 5.0]],
+                                       "energy": np.array([-12.5 * (1 + 2e-6), -20.0, 0.0, 0.0])})
     assert abs(acc["dq_max_e"] - 3e-7) < 1e-15                    # trailing padding ignored
     assert abs(acc["force_rms_rel"] - 1e-3) < 1e-12
     assert abs(acc["energy_U_rel"] - 2e-6) < 1e-12 and acc["energy_H_rel"] == 0.0
@@ -46,6 +46,30 @@ def test_batched_accuracy_per_replica():
     acc = bench.batched_accuracy(q_ref, q.reshape(-1))
     assert acc["dq_max_e_per_replica"] == [1e-6, 0.0, 2e-5]
     assert abs(acc["dq_max_e"] - 2e-5) < 1e-15 and acc["replicas_within_1e-5_e"] == 2 and acc["replicas"] == 3
+
+
+def test_precision_errors_against_the_float64_path():
+    rng = np.random.default_rng(3)
+    f64 = {"q": rng.normal(size=40), "F_elyt": rng.normal(size=(10, 3)), "F_elec": rng.normal(size=(40, 3)),
+           "energy": np.array([-30.0, -31.0, 0.5, 1.0])}
+    mix = {"q": f64["q"] + 2e-7, "F_elyt": f64["F_elyt"] * (1 + 1e-6), "F_elec": f64["F_elec"] * (1 - 3e-6),
+           "energy": f64["energy"] * np.array([1 + 1e-7, 1 - 2e-7, 1.0, 1.0])}
+    e = bench.precision_errors(mix, f64)
+    assert abs(e["dq_max_e"] - 2e-7) < 1e-15
+    assert abs(e["force_rms_rel_elyt"] - 1e-6) < 1e-12 and abs(e["force_rms_rel_elec"] - 3e-6) < 1e-12
+    assert abs(e["energy_U_rel"] - 1e-7) < 1e-13 and abs(e["energy_H_rel"] - 2e-7) < 1e-13
+
+
+def test_sampled_oracle_time_model():
+    """A full step on p workers is a + b/p from the per-worker sample time T(f) = a + b f."""
+    class Fake(bench.SampledOracle):
+        def __init__(self):
+            self.procs, self.pool, self.seed = 4, None, 0
+
+        def sample(self, frac):
+            return 0.5 + 800.0 * frac
+    a, b = Fake().fit(0.001, 0.004)
+    assert abs(a - 0.5) < 1e-9 and abs(b - 800.0) < 1e-6
 
 
 def test_batched_oracle_charges_are_neutral_per_replica():

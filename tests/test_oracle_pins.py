@@ -468,3 +468,16 @@ def test_separable_reciprocal_sum_equals_direct_sum(box):
     p2, g2 = ewald.recip_space_separable(tgt, src, c, box, 0.3, want_grad=True)
     assert np.max(np.abs(p1 - p2)) <= 1e-13 * np.max(np.abs(p1))
     assert np.max(np.abs(g1 - g2)) <= 1e-13 * np.max(np.abs(g1))
+
+
+def test_hard_truncated_ewald_split_gives_an_indefinite_elastance():
+    """The premise of the GPU build's CPM_ERR_NOT_SPD test: with alpha = 0.01 / A and r_c = 2 A
+    the truncated sums no longer represent the positive Coulomb energy of Gaussians, and A has
+    negative eigenvalues (in the single cell and, z-mirrored, in both mirror blocks P +- Q)."""
+    w = dataclasses.replace(synth.tiny_cell(seed=1, n_pairs=2), alpha=0.01, rcut=2.0)
+    assert np.linalg.eigvalsh(cpm.elastance(w))[0] < -1.0
+    wd = synth.mirror_to_doubled(w, "mirror")
+    A = cpm.elastance(wd)
+    n = w.n_elec
+    P, Q = A[:n, :n], A[:n, n:]
+    assert np.linalg.eigvalsh(P + Q)[0] < -1.0 and np.linalg.eigvalsh(P - Q)[0] < -1.0

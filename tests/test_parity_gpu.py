@@ -218,3 +218,28 @@ def test_batched_tensor_core_s_apply_matches_float64_path():
         q, lam, _ = ref.charges(wr.elyt_xyz[0], wr.elyt_q[0], float(wr.dpsi[0]))
         assert np.max(np.abs(r32["q"][r] - q)) <= 1e-5
 
+
+
+def _indefinite_cell():
+    """The tiny cell with alpha = 0.01 / A and r_c = 2 A: the Ewald split is truncated so hard
+    (no reciprocal vector below 2 alpha sqrt(27.6), real space cut at 2 A) that A is indefinite
+    (its smallest eigenvalue is -7.2 V/e on the oracle: test_oracle_pins)."""
+    return dataclasses.replace(synth.tiny_cell(seed=1, n_pairs=2), alpha=0.01, rcut=2.0)
+
+
+@pytest.mark.parametrize("blocks", ["full", "mirror"])
+def test_indefinite_elastance_is_refused(blocks):
+    """The build's Cholesky factorisation refuses an A that is not positive definite with
+    CPM_ERR_NOT_SPD (also for the two mirror blocks of a doubled cell), and the library stays
+    usable: a normal build afterwards succeeds."""
+    g, System = _lib()
+    w = _indefinite_cell()
+    if blocks == "mirror":
+        w = synth.mirror_to_doubled(w, "mirror")
+        w.grid = (18, 16, 144)
+    with pytest.raises(g.CPMError) as ei:
+        System(w, "fp64", dc_blocks=blocks if w.geometry == "dc" else "auto")
+    assert ei.value.status == -3
+    s = System(synth.tiny_cell(seed=1, n_pairs=2), "fp64")
+    s.charges()
+    assert g.cpm_status(s.ctx) == 0

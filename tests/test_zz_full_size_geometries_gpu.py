@@ -60,9 +60,13 @@ def test_paper_scale_cell_all_geometries(geometry):
         _graph_step(s)
         assert g.cpm_status(s.ctx) == 0
         r = s.results()
-        q, psibar = r["q"][0], r["psibar"][0]
+        q = r["q"][0]
+        # b and the offsets of one charge update (a second call: the float32 mesh sums with
+        # atomics differ between calls at rounding level -- up to ~2e-6 e in q here --, so q, b
+        # and psibar are taken from the same call where they are compared with each other)
         s.charges()
-        b_gpu = s.results()["b"][0]
+        r2 = s.results()
+        b_gpu, psibar, q2 = r2["b"][0], r2["psibar"][0], r2["q"][0]
         oracle = f_oracle.result()
     rng = np.random.default_rng(1)
     il = rng.choice(len(Q), 48, replace=False)
@@ -76,6 +80,7 @@ def test_paper_scale_cell_all_geometries(geometry):
     # charges against the oracle's KKT solution: the spec bar
     dq = float(np.max(np.abs(q - q_ref)))
     assert dq <= 1e-5
+    assert np.max(np.abs(q2 - q_ref)) <= 1e-5
     C = oracle.C
     assert np.max(np.abs(C.T @ q)) <= 1e-12 * max(1.0, np.abs(q).sum())
     check_psibar(psibar, b_gpu, dpsi, oracle, psibar_ref, b_ref)
@@ -83,5 +88,5 @@ def test_paper_scale_cell_all_geometries(geometry):
     assert np.sqrt(((F - F_ref) ** 2).sum() / (F_ref ** 2).sum()) <= 5e-5
     assert abs(r["energy"][0, 0] - e["U"]) <= 3e-5 * abs(e["U"])
     assert abs(r["energy"][0, 1] - e["H"]) <= 3e-5 * abs(e["H"])
-    resid = oracle.A @ q - b_gpu - dpsi * oracle.v - C @ psibar
+    resid = oracle.A @ q2 - b_gpu - dpsi * oracle.v - C @ psibar
     print(f"{geometry}: max|dq| {dq:.3e} e, KKT residual max {np.max(np.abs(resid)):.3e} V")
