@@ -72,13 +72,14 @@ def parse(argv=None):
                     help="MD workloads: re-solve the electrode charges every k steps (Appendix B: 5)")
     ap.add_argument("--workload", default="dc-large",
                     choices=["paper", "paper-dc", "paper-slab", "paper-proximal", "large", "dc-large", "paper-md",
-                             "paper-dc-md"],
+                             "paper-dc-md", "batched"],
                     help="dc-large (default): the 40,320-site doubled cell (mirror blocks, mesh-operator A); "
                          "paper: the paper-scale cell; paper-dc / paper-slab: the same cell as a doubled "
                          "cell (6,048 sites, mirror blocks) or a slab (3x z padding); paper-proximal: only the "
                          "1,008 proximal-layer sites charged; large: the 10,080-site cell; paper-md / "
                          "paper-dc-md: the whole MD loop (velocity-Verlet, Nose-Hoover, Lennard-Jones, charges "
-                         "re-solved every --charge-every steps) on point-ion versions of the paper cells")
+                         "re-solved every --charge-every steps) on point-ion versions of the paper cells; batched: "
+                         "64 replicas of the 672-site plain cell in one batched step (replica-steps/s)")
     return ap.parse_args(argv)
 
 
@@ -125,6 +126,8 @@ WORKLOADS = {
                  "point-ion pairs +-0.78 e (2,000 Lennard-Jones sites, the site count of the CG cell), "
                  "38.34x34.44x168 A, SPME 40x36x168 order 5, alpha 0.25, r_c 12 A; velocity-Verlet 2 fs, "
                  "Nose-Hoover 400 K / 100 fs, force-shifted LJ 12 A, charges re-solved every k steps", 6000),
+    "batched": ("64 replicas x 672-site plain cell (17.04x17.22x60 A), 400-600 point-ion pairs each, dpsi 0-4 V, "
+                "mesh 18x18x60 order 5, one batched step with the tcgen05 split-TF32 S-apply", 3000),
     "paper-dc-md": ("MD on the paper-scale doubled cell: 6,048 electrode sites (S as two 3,024^2 mirror blocks), "
                     "1,000 point-ion pairs per sub-cell (4,000 LJ sites), 38.34x34.44x336 A, SPME 40x36x336 order 5; "
                     "velocity-Verlet 2 fs, one Nose-Hoover thermostat per sub-cell (400 K / 100 fs), LJ 12 A, "
@@ -132,7 +135,8 @@ WORKLOADS = {
 }
 GEOMETRY_NAME = {"paper": "finite field", "paper-dc": "doubled cell", "paper-slab": "slab",
                  "paper-proximal": "finite field", "large": "finite field",
-                 "dc-large": "doubled cell", "paper-md": "finite field", "paper-dc-md": "doubled cell"}
+                 "dc-large": "doubled cell", "paper-md": "finite field", "paper-dc-md": "doubled cell",
+                 "batched": "finite field"}
 MD_WORKLOADS = ("paper-md", "paper-dc-md")
 # workloads whose oracle step fits the host in seconds to a minute (dense A and its Cholesky factor);
 # the others are checked and timed through sampled sums
@@ -141,6 +145,8 @@ DENSE_ORACLE = ("paper", "paper-dc", "paper-slab", "paper-proximal", "paper-md",
 
 def workload(seed, kind="paper"):
     import synth
+    if kind == "batched":
+        return synth.config_batched(n_rep=64)
     if kind == "large":
         return synth.config_large_ff(seed=seed)
     if kind == "dc-large":
@@ -240,7 +246,7 @@ TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tf32 / bf16 tensor rate of GB300
 # and "phase:kernel variant" (the autotuner may pick another S-apply kernel, whose traffic was not
 # captured: then traffic is null).  Set an entry to None whenever its kernel changes.
 NCU_TRAFFIC_MIXED = {"paper": {}, "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {},
-                     "paper-dc-md": {}, "large": {}, "dc-large": {}}
+                     "paper-dc-md": {}, "large": {}, "dc-large": {}, "batched": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
 
@@ -490,6 +496,8 @@ def run_gb300(args):
 
     if args.workload in MD_WORKLOADS:
         return run_md(args)
+    if args.workload == "batched":
+        return run_batched(args)
     world, rank, local, dev = setup_ranks()
     w = workload(replica_seed(args.seed, rank), args.workload)
     s, build_s, (sapply_variant, fft_variant, mesh_variant) = build_system(args, w, dev)
@@ -1010,6 +1018,34 @@ def child_oracle_sample(args):
                        f"~10^16 flops), so the electrode charges are held fixed")}
     with open(args.child_out, "w") as f:
         json.dump(base, f)
+
+
+def run_batched(args):
+    """--workload batched: the 64-replica step as the line itself (replica-steps/s), for profiling and
+    for a batched-only run; the default line carries the same object as `batched`."""
+    import torch
+    import torch.distributed as dist
+    world, rank, local, dev = setup_ranks()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    obj, _ = batched_replicas(args, dev, flush)
+    clk = clocks.stop()
+    ms = reduce_max(obj["ms_per_step"], dev)
+    value = world * 64 * 1e3 / ms
+    out = {"metric": METRIC, "value": round(value, 1), "unit": "replica-steps/s", "n_gpus": world,
+           "steps": max(10, min(args.steps, 200)), "warmup": 3, "ms_per_step": round(ms, 5), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOADS["batched"][0], "geometry": "finite field", "precision": "mixed",
+                      "forces": "all sites (electrolyte and electrode)", "replicas_per_gpu": 64,
+                      "parallelism": f"replicas x{world} (no collective)",
+                      "l2": "flushed between steps (256 MiB write); per-step CUDA-event time",
+                      "graph": "whole step captured in one CUDA graph"},
+           "clocks": clk, "batched": obj, "roofline": obj.get("roofline")}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_md(args):

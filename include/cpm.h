@@ -406,7 +406,7 @@ int cpm_get_pair_variant(const cpm_ctx* ctx, int32_t* variant);
  * convolutions (cpm_fft_variant), then the two charge assignments (cpm_mesh_variant), then the pair
  * kernels' z groups of 1, 2 and 4 cells (cpm_set_pair_group), then the four pair-kernel variant
  * masks (cpm_pair_variant), keeping the faster each time.  Each timed call is a whole cpm_step
- * (scratch force and energy outputs).  choice_host[3] (may be NULL) receives the kept
+ * with forces on all sites, electrolyte and electrode (scratch force and energy outputs).  choice_host[3] (may be NULL) receives the kept
  * (cpm_sapply_variant, cpm_fft_variant, cpm_mesh_variant); cpm_get_pair_group and
  * cpm_get_pair_variant report the rest.
  * Allocates and frees a scratch buffer of twice the L2 size, scratch outputs, a stream and the

@@ -932,6 +932,67 @@ static int load_image(cpm_ctx* c, const void* image, int64_t bytes, uint64_t key
   return CPM_OK;
 }
 
+// Electrode-electrode real-space force list (mixed precision): the electrode is frozen, so the
+// Gaussian-Gaussian pair term of the electrode forces, F_i = KE q_i sum_j q_j G_ij with
+// G_ij = [k(r) + 2/sqrt(pi) (alpha e^{-alpha^2 r^2} - beta e^{-beta^2 r^2})] d_ij / r^2,
+// k(r) = (erfc(alpha r) - erfc(beta r)) / r, beta = eta / sqrt 2, d_ij = r_i - r_j (every periodic
+// image within r_c, Sec. II.B), depends on the charges only through q_i q_j: G is evaluated once
+// here in float64 and kept in float32, one CSR row per target in original order, entry
+// (G_x, G_y, G_z, j).  The cell grid of the build (edge >= r_c / 2, stencil half-width sten)
+// enumerates the images: an unwrapped neighbour cell index maps to a cell and an image shift.
+static int build_ee_list(cpm_ctx* c, const std::vector<double4_32a>& pos, const std::vector<int4>& cc,
+                         const std::vector<int>& start, const std::vector<int>& sorted, cudaStream_t st) {
+  const int ne = c->ne;
+  const double rc2 = c->p.rcut * c->p.rcut, alpha = c->p.alpha, beta = c->p.eta / std::sqrt(2.0);
+  const double two_over_sqrt_pi = 2.0 / std::sqrt(M_PI);
+  std::vector<int> ptr(ne + 1, 0);
+  std::vector<float4> ent;
+  ent.reserve((size_t)ne * 64);
+  for (int i = 0; i < ne; ++i) {
+    const int4 ci = cc[i];
+    for (int dx = -c->sten[0]; dx <= c->sten[0]; ++dx)
+      for (int dy = -c->sten[1]; dy <= c->sten[1]; ++dy)
+        for (int dz = -c->sten[2]; dz <= c->sten[2]; ++dz) {
+          const int u[3] = {ci.x + dx, ci.y + dy, ci.z + dz};
+          int w[3];
+          double sh[3];
+          for (int d = 0; d < 3; ++d) {
+            const int m = (int)std::floor((double)u[d] / c->nc[d]);
+            w[d] = u[d] - m * c->nc[d];
+            sh[d] = m * c->ebox[d];
+          }
+          const int cell = (w[0] * c->nc[1] + w[1]) * c->nc[2] + w[2];
+          for (int k = start[cell]; k < start[cell + 1]; ++k) {
+            const int j = sorted[k];
+            const double ddx = pos[i].x - (pos[j].x + sh[0]), ddy = pos[i].y - (pos[j].y + sh[1]),
+                         ddz = pos[i].z - (pos[j].z + sh[2]);
+            const double r2 = ddx * ddx + ddy * ddy + ddz * ddz;
+            if (r2 >= rc2 || r2 == 0.0) continue;      // (r = 0 only for i itself: coincident sites are refused)
+            const double r = std::sqrt(r2);
+            const double kr = (std::erfc(alpha * r) - std::erfc(beta * r)) / r;
+            const double fr = (kr + two_over_sqrt_pi * (alpha * std::exp(-alpha * alpha * r2) -
+                                                        beta * std::exp(-beta * beta * r2))) / r2;
+            float4 e;
+            e.x = (float)(fr * ddx);
+            e.y = (float)(fr * ddy);
+            e.z = (float)(fr * ddz);
+            std::memcpy(&e.w, &j, sizeof(int));
+            ent.push_back(e);
+          }
+        }
+    ptr[i + 1] = (int)ent.size();
+    if (ent.size() > (size_t)INT32_MAX - 4096) {
+      set_error("electrode pair list above 2^31 entries");
+      return CPM_ERR_ARG;
+    }
+  }
+  if (ent.empty()) ent.push_back(make_float4(0.f, 0.f, 0.f, 0.f));   // never a null pointer
+  CPM_TRY(upload(&c->ee_ptr, ptr, st));
+  CPM_TRY(upload(&c->ee_g, ent, st));
+  c->ee_nnz = ptr[ne];
+  return CPM_OK;
+}
+
 static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side, const int32_t* cell,
                  cudaStream_t st, const void* image = nullptr, int64_t image_bytes = 0) {
   const cpm_params& p = c->p;
@@ -1039,6 +1100,7 @@ static int build(cpm_ctx* c, int32_t ne, const double* xyz, const int32_t* side,
   CPM_TRY(upload(&c->e_v, v, st));
   CPM_TRY(upload(&c->e_c1, c1, st));
   CPM_TRY(upload(&c->e_plus, eplus, st));
+  if (c->mixed) CPM_TRY(build_ee_list(c, pos, cc, start, sorted, st));
 
   // ---------------- SPME influence function (the mesh form of A uses it) ----------------
   {
@@ -1213,7 +1275,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
-                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad, c->sym_S, c->sym_part, c->sym_cnt};
+                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad, c->sym_S, c->sym_part, c->ee_ptr, c->ee_g};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int b = 0; b < 2; ++b)

@@ -126,7 +126,11 @@ struct cpm_ctx {
   int sym_nt = 0;
   float* sym_S = nullptr;
   float* sym_part = nullptr;
-  int* sym_cnt = nullptr;       // per row block: slots written in this call (zero between calls)
+  // electrode-electrode real-space force list of the frozen electrode (mixed precision): CSR rows
+  // per target (original order), entries (G_x, G_y, G_z, source index as int bits)
+  int* ee_ptr = nullptr;
+  float4* ee_g = nullptr;
+  long long ee_nnz = 0;
   int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
   // mesh convolution variant (enum cpm_fft_variant) and the tables of this library's own
   // float32 transform: per-axis four-step split K = n1 n2 and twiddles exp(-2 pi i t / K)

@@ -634,6 +634,39 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   }
 }
 
+// Electrode-electrode real-space forces of the frozen electrode from the precomputed list
+// (cpm_build: ee_ptr / ee_g): F_i += KE q_i sum_j q_j G_ij.  One warp per target row (grid-stride),
+// grid.y = replica; each lane sums its share of the row in float32 (a few tens of terms), the
+// lanes are combined in float64.  The list is streamed once per replica-step (16 bytes per pair);
+// the charges are gathered through the caches.
+__global__ void __launch_bounds__(256) k_ee_forces(const int* __restrict__ ptr, const float4* __restrict__ g, int ne,
+                                                   const float* __restrict__ qT, double* __restrict__ f) {
+  pdl_enter();
+  const int rep = blockIdx.y;
+  const int lane = threadIdx.x & 31;
+  const float* q = qT + (size_t)rep * ne;
+  const int nw = gridDim.x * (blockDim.x >> 5);
+  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < ne; i += nw) {
+    const int a = ptr[i], e = ptr[i + 1];
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    for (int k = a + lane; k < e; k += 32) {
+      const float4 v = __ldcs(g + k);
+      const float qj = __ldg(q + __float_as_int(v.w));
+      sx = fmaf(qj, v.x, sx);
+      sy = fmaf(qj, v.y, sy);
+      sz = fmaf(qj, v.z, sz);
+    }
+    const double tx = warp_sum((double)sx), ty = warp_sum((double)sy), tz = warp_sum((double)sz);
+    if (lane == 0) {
+      const double c = KE * (double)q[i];
+      double* fi = f + 3 * ((size_t)rep * ne + i);
+      fi[0] += c * tx;
+      fi[1] += c * ty;
+      fi[2] += c * tz;
+    }
+  }
+}
+
 // Warp-per-target variant of the real-space pair kernels (same inputs and outputs as k_pair_cell).
 // A warp takes one target at a time (grid-stride over the cell-sorted targets): it lists the
 // stencil cells whose box lies within r_c of the target point itself (tighter than the cell-to-cell
@@ -1059,11 +1092,14 @@ __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int
     for (int task = lane; task < P * P; task += 32) {
       const int ty = task_row(task, inv_p), tz = task - ty * P;
       const int gy = wrap_near(bs.y - ty, K2), gz = wrap_near(bs.z - tz, K3);
+      T ph[PMAX];
+#pragma unroll
+      for (int tx = 0; tx < PMAX; ++tx)
+        ph[tx] = tx < P ? m[((size_t)wrap_near(bs.x - tx, K1) * K2 + gy) * K3 + gz] : T(0);
       T s = 0;
-      for (int tx = 0; tx < P; ++tx) {
-        const int gx = wrap_near(bs.x - tx, K1);
-        s += w[tx] * m[((size_t)gx * K2 + gy) * K3 + gz];
-      }
+#pragma unroll
+      for (int tx = 0; tx < PMAX; ++tx)
+        if (tx < P) s += w[tx] * ph[tx];
       acc.add(s * w[PMAX + ty] * w[2 * PMAX + tz]);
     }
     acc.warp_reduce();
@@ -1118,12 +1154,18 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
       for (int task = lane; task < P * P; task += 32) {
         const int ty = task_row(task, inv_p), tz = task - ty * P;
         const int jy = wrap_near(b0[1] - ty, K2), jz = wrap_near(b0[2] - tz, K3);
+        // the P mesh loads of the x line issued together (unrolled to the largest order)
+        T ph[PMAX];
+#pragma unroll
+        for (int tx = 0; tx < PMAX; ++tx)
+          ph[tx] = tx < P ? m[((size_t)wrap_near(b0[0] - tx, K1) * K2 + jy) * K3 + jz] : T(0);
         T a = 0, ad = 0;
-        for (int tx = 0; tx < P; ++tx) {
-          const int jx = wrap_near(b0[0] - tx, K1);
-          const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
-          a += w[0][tx] * ph;
-          ad += dw[0][tx] * ph;
+#pragma unroll
+        for (int tx = 0; tx < PMAX; ++tx) {
+          if (tx < P) {
+            a += w[0][tx] * ph[tx];
+            ad += dw[0][tx] * ph[tx];
+          }
         }
         const T wy = w[1][ty], wz = w[2][tz];
         gx += ad * wy * wz;
@@ -1169,12 +1211,17 @@ __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi
     for (int task = lane; task < P * P; task += 32) {
       const int ty = task_row(task, inv_p), tz = task - ty * P;
       const int jy = wrap_near(bs.y - ty, K2), jz = wrap_near(bs.z - tz, K3);
+      T ph[PMAX];
+#pragma unroll
+      for (int tx = 0; tx < PMAX; ++tx)
+        ph[tx] = tx < P ? m[((size_t)wrap_near(bs.x - tx, K1) * K2 + jy) * K3 + jz] : T(0);
       T a = 0, ad = 0;
-      for (int tx = 0; tx < P; ++tx) {
-        const int jx = wrap_near(bs.x - tx, K1);
-        const T ph = m[((size_t)jx * K2 + jy) * K3 + jz];
-        a += w[tx] * ph;
-        ad += dw[tx] * ph;
+#pragma unroll
+      for (int tx = 0; tx < PMAX; ++tx) {
+        if (tx < P) {
+          a += w[tx] * ph[tx];
+          ad += dw[tx] * ph[tx];
+        }
       }
       const T wy = w[PMAX + ty], wz = w[2 * PMAX + tz];
       gx += ad * wy * wz;
@@ -2260,9 +2307,12 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       STEP_LAUNCH();
     }
     ptg.stop();
-    // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian (energy)
+    // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian (forces, and
+    // the energy of the full sum).  With forces only and the precomputed electrode pair list (mixed
+    // precision, frozen electrode), the Gaussian-Gaussian forces come from the list instead.
     if (f_elec || (energy && !closed_form)) {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
+      const bool ee_list = c->ee_g != nullptr && f_elec && !(energy && !closed_form) && sizeof(T) == sizeof(float);
       CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, qT, f_elec, nullptr};
       PairSrc a = f_elec ? src_elyt : none;
       a.beta = c->p.eta;
@@ -2270,10 +2320,17 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       e.qT = qT;
       e.beta = c->p.eta / std::sqrt(2.0);
       e.slot = (energy && !closed_form) ? S_E_EE : -1;
+      if (ee_list) e = none;
       if (f_elec)
         CPM_TRY((launch_pair<T, true, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
       else
         CPM_TRY((launch_pair<T, false, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
+      if (ee_list) {
+        const int blocks = std::max(1, std::min((ne + 7) / 8, c->n_sm * 8));
+        CPM_CUDA(launch_pdl(k_ee_forces, dim3(blocks, nrep), 256, 0, st, (const int*)c->ee_ptr, (const float4*)c->ee_g,
+                            ne, (const float*)qT, f_elec));
+        STEP_LAUNCH();
+      }
     }
     if (energy) {
       PhaseTimer pt(c, st, CPM_PH_ENERGY);
@@ -2542,8 +2599,9 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   CPM_CUDA(cudaEventCreate(&e1));
   int rc = CPM_OK;
   // scratch outputs of the timed steps (forces and energies are part of the step)
-  double *f_scr = nullptr, *e_scr = nullptr;
+  double *f_scr = nullptr, *fe_scr = nullptr, *e_scr = nullptr;
   CPM_CUDA(cudaMalloc(&f_scr, sizeof(double) * 3 * (size_t)c->p.max_elyt + 64));
+  CPM_CUDA(cudaMalloc(&fe_scr, sizeof(double) * 3 * (size_t)c->ne + 64));
   CPM_CUDA(cudaMalloc(&e_scr, sizeof(double) * cpm::NENERGY));
   // Median of nine timed steps (charges, forces, energy) after a warm-up; false if unavailable.
   // The step is timed as the replay of a CUDA graph captured on a private stream, as it runs in an
@@ -2555,7 +2613,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
     if (cpm_set_sapply_variant(c, sv) != CPM_OK || cpm_set_fft_variant(c, fv) != CPM_OK ||
         cpm_set_mesh_variant(c, mv) != CPM_OK)
       return false;
-    rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, st);
+    rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, st);
     if (rc == CPM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CPM_ERR_CUDA;
     cudaGraph_t gr = nullptr;
     cudaGraphExec_t ge = nullptr;
@@ -2563,7 +2621,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
       if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         rc = CPM_ERR_CUDA;
       } else {
-        const int r2 = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, cs);
+        const int r2 = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, cs);
         const cudaError_t ec = cudaStreamEndCapture(cs, &gr);
         if (r2 != CPM_OK) rc = r2;
         else if (ec != cudaSuccess || cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) rc = CPM_ERR_CUDA;
@@ -2578,7 +2636,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
       if (use_graph) {
         if (cudaGraphLaunch(ge, ts) != cudaSuccess) rc = CPM_ERR_CUDA;
       } else {
-        rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, nullptr, e_scr, ts);
+        rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, ts);
       }
       cudaEventRecord(e1, ts);
       if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
@@ -2633,6 +2691,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   }
   c->pair_variant = (rc == CPM_OK) ? best_p : keep_p;
   cudaFree(f_scr);
+  cudaFree(fe_scr);
   cudaFree(e_scr);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

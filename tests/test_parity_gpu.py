@@ -224,7 +224,7 @@ def _indefinite_cell():
     """The tiny cell with alpha = 0.01 / A and r_c = 2 A: the Ewald split is truncated so hard
     (no reciprocal vector below 2 alpha sqrt(27.6), real space cut at 2 A) that A is indefinite
     (its smallest eigenvalue is -7.2 V/e on the oracle: test_oracle_pins)."""
-    return dataclasses.replace(synth.tiny_cell(seed=1, n_pairs=2), alpha=0.01, rcut=2.0)
+    return dataclasses.replace(synth.tiny_cell(seed=1, n_pairs=2), alpha=0.01, rcut=2.0, grid=(20, 16, 72))
 
 
 @pytest.mark.parametrize("blocks", ["full", "mirror"])
@@ -236,10 +236,45 @@ def test_indefinite_elastance_is_refused(blocks):
     w = _indefinite_cell()
     if blocks == "mirror":
         w = synth.mirror_to_doubled(w, "mirror")
-        w.grid = (18, 16, 144)
+        w.grid = (20, 16, 144)
     with pytest.raises(g.CPMError) as ei:
         System(w, "fp64", dc_blocks=blocks if w.geometry == "dc" else "auto")
     assert ei.value.status == -3
-    s = System(synth.tiny_cell(seed=1, n_pairs=2), "fp64")
+    s = System(synth.tiny_cell(seed=1, n_pairs=2), "fp64", grid=(20, 16, 72))
     s.charges()
     assert g.cpm_status(s.ctx) == 0
+
+
+def _rms_rel(a, b):
+    return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
+
+
+@pytest.mark.parametrize("case", ["plain", "dc", "batched"])
+def test_electrode_forces_from_the_precomputed_pair_list(plain_ff, case):
+    """cpm_step with electrode forces (closed-form energy) in mixed precision takes the
+    Gaussian-Gaussian forces of the frozen electrode from the pair list precomputed at build;
+    cpm_forces with the full energy computes them in the pair kernels.  Both must agree, and
+    with the oracle's electrode forces."""
+    g, System = _lib()
+    if case == "plain":
+        w, _, out = plain_ff
+    elif case == "dc":
+        w = synth.mirror_to_doubled(synth.tiny_cell(seed=4, n_pairs=4), "independent", seed=40)
+        w.grid = (18, 16, 144)
+        out = ocpm.Reference(w).step()
+    else:
+        w = synth.config_batched(n_rep=3)
+        out = None
+    a = System(w, "mixed", order=8)
+    a.step(elec=True, energy=True)
+    ra = a.results()
+    assert g.cpm_status(a.ctx) == 0
+    b = System(w, "mixed", order=8)
+    b.q.copy_(a.q)
+    b.forces(elec=True, energy=True)
+    rb = b.results()
+    for r in range(w.n_rep):
+        assert _rms_rel(ra["F_elec"][r], rb["F_elec"][r]) <= 3e-6
+        assert _rms_rel(ra["F_elyt"][r], rb["F_elyt"][r]) <= 1e-6
+    if out is not None:
+        assert _rms_rel(ra["F_elec"][0], out["F_elec"]) <= 3e-5
