@@ -101,34 +101,72 @@ __global__ void __launch_bounds__(256) k_bin(const int* __restrict__ off, const 
   block_atomic_add<2>(acc, dst);
 }
 
-// exclusive scan of the per-cell counts (one block per replica); counts become scatter cursors
-__global__ void k_scan(int* __restrict__ l_count, int* __restrict__ l_start, int ncell) {
+// exclusive scan of the per-cell counts (one block per replica); counts become scatter cursors.
+// Each warp owns a contiguous segment of 32 x SCAN_V cells per round: its lanes load the segment
+// coalesced, all loads in flight at once, scan it 32 cells at a time with shuffles, then the warp
+// totals are scanned across the block and added.
+constexpr int SCAN_V = 16;
+__global__ void __launch_bounds__(1024) k_scan(int* __restrict__ l_count, int* __restrict__ l_start, int ncell) {
   pdl_enter();
   const int rep = blockIdx.x;
   int* cnt = l_count + (size_t)rep * ncell;
   int* st = l_start + (size_t)rep * (ncell + 1);
-  __shared__ int part[1024];
-  const int nt = blockDim.x;
-  const int chunk = (ncell + nt - 1) / nt;
-  const int b = threadIdx.x * chunk, e = min(ncell, b + chunk);
-  int s = 0;
-  for (int k = b; k < e; ++k) s += cnt[k];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < nt; o <<= 1) {
-    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+  __shared__ int wtot[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int carry = 0;
+  for (int base = 0; base < ncell; base += nwarps * 32 * SCAN_V) {
+    const int seg = base + warp * 32 * SCAN_V;
+    int c[SCAN_V];
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+      const int idx = seg + j * 32 + lane;
+      c[j] = idx < ncell ? cnt[idx] : 0;
+    }
+    // c[j] becomes the exclusive prefix of element (j, lane) within the warp's segment
+    int run = 0;
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+      int x = c[j];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += u;
+      }
+      const int excl = run + x - c[j];
+      run += __shfl_sync(FULL, x, 31);
+      c[j] = excl;
+    }
+    if (lane == 0) wtot[warp] = run;
     __syncthreads();
-    part[threadIdx.x] += v;
+    if (warp == 0) {
+      int x = lane < nwarps ? wtot[lane] : 0;
+      const int own = x;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(FULL, x, o);
+        if (lane >= o) x += u;
+      }
+      if (lane < nwarps) wtot[lane] = x - own;        // exclusive offset of each warp's segment
+    }
+    __syncthreads();
+    const int off = carry + wtot[warp];
+#pragma unroll
+    for (int j = 0; j < SCAN_V; ++j) {
+      const int idx = seg + j * 32 + lane;
+      if (idx < ncell) {
+        st[idx] = off + c[j];
+        cnt[idx] = off + c[j];
+      }
+    }
+    // the round's total: the last warp's offset plus its segment total
+    const int last_off = wtot[nwarps - 1];
+    __syncthreads();
+    if (warp == nwarps - 1 && lane == 0) wtot[0] = last_off + run;
+    __syncthreads();
+    carry += wtot[0];
     __syncthreads();
   }
-  int run = part[threadIdx.x] - s;
-  for (int k = b; k < e; ++k) {
-    const int c = cnt[k];
-    st[k] = run;
-    cnt[k] = run;
-    run += c;
-  }
-  if (threadIdx.x == nt - 1) st[ncell] = part[nt - 1];
+  if (threadIdx.x == 0) st[ncell] = carry;
 }
 
 template <typename T>
@@ -649,12 +687,24 @@ __global__ void __launch_bounds__(256) k_ee_forces(const int* __restrict__ ptr, 
   for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < ne; i += nw) {
     const int a = ptr[i], e = ptr[i + 1];
     float sx = 0.f, sy = 0.f, sz = 0.f;
-    for (int k = a + lane; k < e; k += 32) {
-      const float4 v = __ldcs(g + k);
-      const float qj = __ldg(q + __float_as_int(v.w));
-      sx = fmaf(qj, v.x, sx);
-      sy = fmaf(qj, v.y, sy);
-      sz = fmaf(qj, v.z, sz);
+    // four entries per lane per round: the list loads, then the charge gathers, are all issued
+    // before any is used
+    for (int k0 = a + lane; k0 < e; k0 += 128) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int k = k0 + 32 * u;
+        v[u] = k < e ? __ldcs(g + k) : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+      }
+      float qj[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) qj[u] = __ldg(q + __float_as_int(v[u].w));
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        sx = fmaf(qj[u], v[u].x, sx);
+        sy = fmaf(qj[u], v[u].y, sy);
+        sz = fmaf(qj[u], v[u].z, sz);
+      }
     }
     const double tx = warp_sum((double)sx), ty = warp_sum((double)sy), tz = warp_sum((double)sz);
     if (lane == 0) {

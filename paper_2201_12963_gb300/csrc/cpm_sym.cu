@@ -149,16 +149,16 @@ __global__ void __launch_bounds__(SF_ROWS * SF_SPLIT) k_sym_finish(int rows, int
   const int i = blockIdx.x * SF_ROWS + r;
   Acc<float> a;
   if (i < rows) {
-    // four independent loads in flight per round: the slots sit in different DRAM pages
-    for (int s = k; s < nt; s += 4 * SF_SPLIT) {
-      float v[4];
+    // eight independent loads in flight per round: the slots sit in different DRAM pages
+    for (int s = k; s < nt; s += 8 * SF_SPLIT) {
+      float v[8];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < 8; ++u) {
         const int su = s + u * SF_SPLIT;
         v[u] = su < nt ? part[(size_t)su * npad + i] : 0.f;
       }
 #pragma unroll
-      for (int u = 0; u < 4; ++u) a.add(v[u]);
+      for (int u = 0; u < 8; ++u) a.add(v[u]);
     }
   }
   ps[k][r][0] = a.s;
