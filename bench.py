@@ -253,8 +253,9 @@ SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", 
 
 def pair_counts(w):
     """Ordered (target, source) pairs within r_c for the workload: electrolyte targets with
-    electrolyte and electrode sources (forces), electrode targets with electrolyte sources (b) and,
-    for electrode forces, with electrolyte and electrode sources."""
+    electrolyte and electrode sources (forces), electrode targets with electrolyte sources (b and,
+    in the same pass, the field for the electrode forces) and electrode targets with electrode
+    sources (the electrode-electrode forces)."""
     from scipy.spatial import cKDTree
     import numpy as np
     box = np.asarray(w.box, float)
@@ -264,7 +265,7 @@ def pair_counts(w):
     ll = int(tl.count_neighbors(tl, w.rcut)) - len(R)       # ordered pairs, self excluded
     le = int(tl.count_neighbors(te, w.rcut))
     ee = int(te.count_neighbors(te, w.rcut)) - len(E)
-    return {"f_pair_elyt": ll + le, "b_real": le, "f_pair_elec": le + ee}
+    return {"f_pair_elyt": ll + le, "b_real": le, "f_pair_elec": ee}
 
 
 def phase_model(phase, s, w, pairs):
@@ -280,6 +281,16 @@ def phase_model(phase, s, w, pairs):
         if s_bytes < (ne // 2 if mirror else ne) ** 2 * fb * (2 if mirror else 1) * 3 // 4:
             what = "upper-triangle tiles of " + what
         return "hbm", byt, "GB/s", f"{what} x {fb} B + b, Sv, q (float64)"
+    if phase == "f_pair_elec" and mixed:
+        # the frozen electrode's precomputed pair list, streamed once
+        import paper_2201_12963_gb300 as g
+        npairs, table = g.cpm_pair_list_layout(s.ctx)
+        if npairs:
+            eb = 4 if table else 16
+            byt = npairs * eb + 4 * (ne + 1) + ne * (4 + 48)
+            form = "compressed list: j and an index into a table of distinct G" if table else "full list: G and j"
+            return ("hbm", byt, "GB/s", f"{npairs} electrode pairs x {eb} B ({form}) + row starts, charges and "
+                    f"forces (float64, read and written)")
     if phase in pairs:
         return "alu", PAIR_FLOPS * pairs[phase], "TFLOP/s", f"{pairs[phase]} pairs within r_c x {PAIR_FLOPS} FP32 flops"
     return None

@@ -232,10 +232,21 @@ int cpm_info(const cpm_ctx* ctx, int32_t* n_elec, int32_t* ncons, int64_t* mesh_
  * cpm_matrix_layout - how S is stored: *mirror_blocks = 1 for the two mirror blocks of a
  * mirror-symmetric doubled cell (cpm_dc_blocks), else 0; *s_bytes = bytes of stored S the S-apply
  * streams per replica-step with the current S-apply variant (float32 for CPM_MIXED, float64 for
- * CPM_FP64, rows padded to 4; the packed upper-triangle tiles for CPM_SAPPLY_SYM).
+ * CPM_FP64, rows padded to 4; the packed upper-triangle tiles for CPM_SAPPLY_SYM and
+ * CPM_SAPPLY_SYM_TMA).
  * Either pointer may be NULL.
  */
 int cpm_matrix_layout(const cpm_ctx* ctx, int32_t* mirror_blocks, int64_t* s_bytes);
+
+/*
+ * cpm_pair_list_layout - the electrode-electrode force list of the frozen electrode (Sec. II.B
+ * real-space sum; mixed precision builds it): *pairs = ordered pairs within r_c (periodic images
+ * included), *table = distinct G vectors of the compressed form (a lattice electrode: entries of
+ * 4 bytes, j | t << 16, with the table in shared memory), or 0 for the full form (16 bytes per
+ * pair: G and j); *pairs = *table = 0 without a list (float64 contexts).  Either pointer may be
+ * NULL.
+ */
+int cpm_pair_list_layout(const cpm_ctx* ctx, int64_t* pairs, int32_t* table);
 
 /*
  * cpm_status - synchronise `stream`, then return and clear the device status word: CPM_OK, or the
@@ -321,12 +332,18 @@ int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const
  *   CPM_SAPPLY_STREAM16  the same with 16 loads in flight per lane;
  *   CPM_SAPPLY_SYM     S (or each mirror block) kept as the upper triangle of 128 x 128 float32
  *                      tiles: one read of an off-diagonal tile serves its rows and, transposed, its
- *                      columns, so about half the bytes of S are streamed; per-tile partial sums
- *                      (one writer each) are added by a second kernel.  Same availability as the
- *                      streaming variants; the packed copy costs half an extra float32 S in memory.
+ *                      columns, so about half the bytes of S are streamed; each tile's row and
+ *                      column sums are added into a float64 row vector with atomics, and a second
+ *                      kernel finishes the rows.  Same availability as the streaming variants; the
+ *                      packed copy costs half an extra float32 S in memory;
+ *   CPM_SAPPLY_SYM_TMA the same packed tiles moved into shared memory by bulk asynchronous copies
+ *                      (three 64 KB stages per CTA, all requested at the start; bounded mbarrier
+ *                      waits that latch CPM_ERR_TIMEOUT), the right-hand side read per tile.
+ *                      Available where CPM_SAPPLY_SYM is.
  * Batches of 8 or more replicas use the tensor-core GEMM and 2-7 replicas the row kernel whatever
  * the choice; float64 contexts always use the row kernel. */
-enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1, CPM_SAPPLY_STREAM16 = 2, CPM_SAPPLY_SYM = 3 };
+enum cpm_sapply_variant { CPM_SAPPLY_ROWS = 0, CPM_SAPPLY_STREAM = 1, CPM_SAPPLY_STREAM16 = 2, CPM_SAPPLY_SYM = 3,
+                          CPM_SAPPLY_SYM_TMA = 4 };
 
 /* cpm_set_sapply_variant - select the S-apply variant; CPM_ERR_ARG if it is not available for
  * this context (the streaming variants need CPM_MIXED and rows of at most 25,600 entries). */

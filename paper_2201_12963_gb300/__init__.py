@@ -23,7 +23,7 @@ DC_BLOCKS = {"auto": 0, "mirror": 1, "full": 2}        # enum cpm_dc_blocks
 
 EXPORTED = ("cpm_build_matrix", "cpm_matrix_key", "cpm_matrix_image", "cpm_build_matrix_from_image", "cpm_step_charges", "cpm_forces", "cpm_energy", "cpm_step", "cpm_capacitance",
             "cpm_copy_matrix", "cpm_info", "cpm_status", "cpm_profile_enable", "cpm_profile_read", "cpm_counters",
-            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
+            "cpm_step_charges_static", "cpm_matrix_layout", "cpm_pair_list_layout", "cpm_set_sapply_variant", "cpm_set_fft_variant", "cpm_set_mesh_variant",
             "cpm_set_pair_group", "cpm_get_pair_group", "cpm_set_pair_variant", "cpm_get_pair_variant",
             "cpm_set_wait_test",
             "cpm_autotune", "cpm_density_z", "cpm_potential_z",
@@ -93,6 +93,7 @@ def _load():
     lib.cpm_counters.argtypes = [vp, ctypes.POINTER(ctypes.c_int64)]
     lib.cpm_step_charges_static.argtypes = [vp, pi32, pd, pd, pd, pd, pd, vp]
     lib.cpm_matrix_layout.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_int64)]
+    lib.cpm_pair_list_layout.argtypes = [vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(i32)]
     lib.cpm_set_sapply_variant.argtypes = [vp, i32]
     lib.cpm_set_fft_variant.argtypes = [vp, i32]
     lib.cpm_set_mesh_variant.argtypes = [vp, i32]
@@ -338,7 +339,16 @@ def cpm_matrix_layout(ctx: Context):
     return bool(m.value), int(nb.value)
 
 
-SAPPLY_VARIANTS = {"rows": 0, "stream": 1, "stream16": 2, "sym": 3}   # enum cpm_sapply_variant
+def cpm_pair_list_layout(ctx: Context):
+    """(ordered electrode pairs in the frozen-electrode force list, distinct G vectors of its
+    compressed form or 0 for the full form)."""
+    n = ctypes.c_int64()
+    t = ctypes.c_int32()
+    _check(_lib.cpm_pair_list_layout(ctx.handle, ctypes.byref(n), ctypes.byref(t)), "cpm_pair_list_layout")
+    return int(n.value), int(t.value)
+
+
+SAPPLY_VARIANTS = {"rows": 0, "stream": 1, "stream16": 2, "sym": 3, "sym-tma": 4}   # enum cpm_sapply_variant
 
 
 def cpm_set_sapply_variant(ctx: Context, variant):

@@ -987,9 +987,71 @@ static int build_ee_list(cpm_ctx* c, const std::vector<double4_32a>& pos, const 
     }
   }
   if (ent.empty()) ent.push_back(make_float4(0.f, 0.f, 0.f, 0.f));   // never a null pointer
+  c->ee_nnz = ptr[ne];
+  // Compressed form: on a lattice electrode the pair vectors, hence the float32 G, repeat, and a
+  // few hundred to a few thousand distinct values occur.  With at most 2^16 sites and fewer than
+  // kEeTabMax distinct G (compared bit for bit, so both forms give the same products), an entry
+  // becomes j | t << 16, t indexing a table of the distinct G: 4 bytes per pair instead of 16.
+  if (ne <= 65536) {
+    struct Key {
+      uint32_t x, y, z;
+      bool operator==(const Key& o) const { return x == o.x && y == o.y && z == o.z; }
+    };
+    struct KeyHash {
+      size_t operator()(const Key& k) const {
+        return (size_t)k.x * 0x9E3779B97F4A7C15ull ^ ((size_t)k.y * 0xC2B2AE3D27D4EB4Full + k.z);
+      }
+    };
+    std::unordered_map<Key, int, KeyHash> seen;
+    std::vector<float4> tab;
+    // rows padded to a multiple of 4 entries (the zero table entry, j = 0), so that the kernel
+    // reads them as aligned 16-byte chunks
+    std::vector<int> ptr4(ne + 1, 0);
+    std::vector<unsigned> idx;
+    idx.reserve(ent.size() + 3 * (size_t)ne);
+    const unsigned kPad = 0xFFFFFFFFu;         // placeholder until the zero entry's index is known
+    bool fits = true;
+    for (int i = 0; i < ne && fits; ++i) {
+      for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
+        Key key;
+        std::memcpy(&key.x, &ent[k].x, 4);
+        std::memcpy(&key.y, &ent[k].y, 4);
+        std::memcpy(&key.z, &ent[k].z, 4);
+        auto it = seen.find(key);
+        int t;
+        if (it == seen.end()) {
+          t = (int)tab.size();
+          if (t + 1 >= kEeTabMax) {        // one slot stays free for the zero entry
+            fits = false;
+            break;
+          }
+          seen.emplace(key, t);
+          tab.push_back(make_float4(ent[k].x, ent[k].y, ent[k].z, 0.f));
+        } else {
+          t = it->second;
+        }
+        int j;
+        std::memcpy(&j, &ent[k].w, sizeof(int));
+        idx.push_back((unsigned)j | ((unsigned)t << 16));
+      }
+      while (idx.size() % 4) idx.push_back(kPad);
+      ptr4[i + 1] = (int)idx.size();
+    }
+    if (fits && idx.size() <= (size_t)INT32_MAX - 4096) {
+      const unsigned zero = (unsigned)tab.size() << 16;                 // j = 0 with G = 0
+      tab.push_back(make_float4(0.f, 0.f, 0.f, 0.f));
+      for (unsigned& v : idx)
+        if (v == kPad) v = zero;
+      if (idx.empty()) idx.assign(4, zero);                             // never a null pointer
+      CPM_TRY(upload(&c->ee_ptr, ptr4, st));
+      CPM_TRY(upload(&c->ee_idx, idx, st));
+      CPM_TRY(upload(&c->ee_tab, tab, st));
+      c->ee_ntab = (int)tab.size();
+      return CPM_OK;
+    }
+  }
   CPM_TRY(upload(&c->ee_ptr, ptr, st));
   CPM_TRY(upload(&c->ee_g, ent, st));
-  c->ee_nnz = ptr[ne];
   return CPM_OK;
 }
 
@@ -1275,7 +1337,8 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->W, c->Sv, c->G64, c->G32, c->mesh_r, c->mesh_c, c->mesh_phi, c->l_cell, c->l_count,
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
-                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad, c->sym_S, c->sym_part, c->ee_ptr, c->ee_g};
+                  c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad, c->sym_S, c->ee_ptr, c->ee_g,
+                  c->ee_idx, c->ee_tab, c->e_field};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int b = 0; b < 2; ++b)
@@ -1286,6 +1349,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
   if (c->ev_fork) cudaEventDestroy(c->ev_fork);
   if (c->ev_join) cudaEventDestroy(c->ev_join);
   if (c->ev_sorted) cudaEventDestroy(c->ev_sorted);
+  if (c->ev_ee) cudaEventDestroy(c->ev_ee);
   if (c->side) cudaStreamDestroy(c->side);
   if (c->cublas) cublasDestroy(c->cublas);
   if (c->solver) cusolverDnDestroy(c->solver);
@@ -1361,7 +1425,7 @@ extern "C" int cpm_matrix_layout(const cpm_ctx* c, int32_t* mirror_blocks, int64
   if (!c) return CPM_ERR_ARG;
   if (mirror_blocks) *mirror_blocks = c->mirror ? 1 : 0;
   if (s_bytes) {
-    if (c->sym_ok && c->sapply_variant == CPM_SAPPLY_SYM) {
+    if (c->sym_ok && (c->sapply_variant == CPM_SAPPLY_SYM || c->sapply_variant == CPM_SAPPLY_SYM_TMA)) {
       const long long nt = c->sym_nt;
       *s_bytes = (c->mirror ? 2LL : 1LL) * (nt * (nt + 1) / 2) * 128LL * 128LL * 4LL;
     } else {
@@ -1369,6 +1433,14 @@ extern "C" int cpm_matrix_layout(const cpm_ctx* c, int32_t* mirror_blocks, int64
       *s_bytes = rows * (long long)c->ld64 * (c->mixed ? 4 : 8);
     }
   }
+  return CPM_OK;
+}
+
+extern "C" int cpm_pair_list_layout(const cpm_ctx* c, int64_t* pairs, int32_t* table) {
+  if (!c) return CPM_ERR_ARG;
+  const bool any = c->ee_g != nullptr || c->ee_idx != nullptr;
+  if (pairs) *pairs = any ? c->ee_nnz : 0;
+  if (table) *table = c->ee_idx ? c->ee_ntab : 0;
   return CPM_OK;
 }
 

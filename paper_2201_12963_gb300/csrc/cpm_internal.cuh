@@ -23,6 +23,8 @@ constexpr double PI = 3.14159265358979323846;
 constexpr int PMAX = 8;                     // largest supported B-spline order
 constexpr int NSCAL = 18;                   // per-replica float64 scalar slots
 constexpr int kMaxStencil = 512;            // neighbour-cell stencil entries of the pair kernel
+constexpr int kEeTabMax = 4096;             // distinct G vectors of the compressed electrode pair list
+                                            // (float4, in 64 KB of shared memory), zero entry included
 
 // Per-replica scalar slots (float64 accumulators, zeroed at the start of every call).
 enum Slot {
@@ -125,11 +127,16 @@ struct cpm_ctx {
   bool sym_ok = false;
   int sym_nt = 0;
   float* sym_S = nullptr;
-  float* sym_part = nullptr;
   // electrode-electrode real-space force list of the frozen electrode (mixed precision): CSR rows
-  // per target (original order), entries (G_x, G_y, G_z, source index as int bits)
+  // per target (original order), entries (G_x, G_y, G_z, source index as int bits); or, when the
+  // G vectors take few distinct values (a lattice electrode), the compressed form: entries
+  // j | t << 16 with t indexing the table ee_tab of distinct G (last entry zero), each row padded
+  // with zero entries to a multiple of 4 (ee_ptr then holds the padded row starts)
   int* ee_ptr = nullptr;
   float4* ee_g = nullptr;
+  unsigned* ee_idx = nullptr;
+  float4* ee_tab = nullptr;
+  int ee_ntab = 0;
   long long ee_nnz = 0;
   int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
   // mesh convolution variant (enum cpm_fft_variant) and the tables of this library's own
@@ -150,6 +157,7 @@ struct cpm_ctx {
   float* br_pad = nullptr;      // [max_rep][br_Mp_s]
   CUtensorMap br_map;           // 4-D tiled map of br_pad: (z, y, x, replica), box br_B
   cudaEvent_t ev_sorted = nullptr;   // side stream: sorted cell list complete
+  cudaEvent_t ev_ee = nullptr;       // side stream: electrode pair-list field complete
   double dqdpsi = 0;
   uint64_t key = 0;             // FNV-1a 64 of the inputs that determine A (matrix images)
   // SPME
@@ -180,6 +188,7 @@ struct cpm_ctx {
   float* spl_F32 = nullptr;
   // per-replica buffers
   double* phi_real = nullptr;   // [max_rep][ne]
+  double* e_field = nullptr;    // [max_rep][ne][3] electrolyte real-space field at the electrode sites (b pass)
   double* b_tmp = nullptr;      // [max_rep][ne]
   float* b32 = nullptr;         // [max_rep][2][ldx] float32 high / low split of the S-apply input (mixed)
   float* qraw32 = nullptr;      // [max_rep][ne] tensor-core S-apply output S b (mixed, batched)
@@ -448,19 +457,23 @@ __device__ __forceinline__ void site_weights(const typename Vec4<T>::type& p, co
 // B-spline weights of a batch of up to kSiteBatch electrolyte sites per warp: lane 3 s + d computes
 // axis d of site s (s < nb), so one pass of the recursion serves nb sites instead of one (the
 // stencil sweeps that follow use all 32 lanes per site).  Writes w / dw [s][d][t], the base mesh
-// index b0 [s][d] and the charge q [s]; ends with __syncwarp.
+// index b0 [s][d] and the charge q [s]; ends with __syncwarp.  Sites are taken in input order
+// (l_tmp, l_cell), or with srt != nullptr in cell-sorted order (l_tmp then holds the sorted
+// cell-local coordinates and srt the sorted -> input index map), which keeps neighbouring sites'
+// stencils in the same cache lines.
 constexpr int kSiteBatch = 10;
 template <typename T>
 __device__ __forceinline__ void batch_weights(int i0, int n, int nb, size_t kbase,
                                               const typename Vec4<T>::type* __restrict__ l_tmp,
                                               const int* __restrict__ l_cell, const SpmeGeom& sg,
                                               const int* __restrict__ splI, const T* __restrict__ splF, int lane,
-                                              T (*w)[3][PMAX], T (*dw)[3][PMAX], int (*b0)[3], T* q) {
+                                              T (*w)[3][PMAX], T (*dw)[3][PMAX], int (*b0)[3], T* q,
+                                              const int* __restrict__ srt = nullptr) {
   const int s = lane / 3, d = lane - 3 * s;
   if (s < nb && i0 + s < n) {
     const size_t k = kbase + i0 + s;
     const auto p = l_tmp[k];
-    const int4 cc = cell_coords(l_cell[k], sg);
+    const int4 cc = cell_coords(l_cell[srt ? kbase + srt[k] : k], sg);
     const T loc = d == 0 ? p.x : (d == 1 ? p.y : p.z);
     const int c = d == 0 ? cc.x : (d == 1 ? cc.y : cc.z);
     const int ti = (d == 0 ? sg.spl_off[0] : (d == 1 ? sg.spl_off[1] : sg.spl_off[2])) + c;
@@ -486,6 +499,17 @@ __device__ __forceinline__ void batch_weights(int i0, int n, int nb, size_t kbas
 }  // namespace cpm
 
 // Entry points implemented in cpm_step.cu, used by the build (Sv, checks).
+namespace cpm {
+// Blocks of the float64-heavy per-site kernels (S-apply finish, projections): 4 warps, so that a
+// block's float64 reductions, on GB300's narrow float64 pipe, are spread over more SMs.
+constexpr int FIN_THREADS = 128;
+// q_raw = qpart + dpsi S v for one replica's rows, qpart cleared, with the projection sums
+// (defined in cpm_step.cu; launched by the streaming and the packed S-apply).
+__global__ void k_sapply_finish(int rows, double* __restrict__ qpart, const double* __restrict__ b,
+                                const double* __restrict__ dpsi, const double* __restrict__ Sv,
+                                const double* __restrict__ W, const double* __restrict__ c1,
+                                double* __restrict__ qout, double* __restrict__ scal);
+}  // namespace cpm
 int cpm_internal_alloc_step_buffers(cpm_ctx* c);
 int cpm_internal_static_scratch_setup();   // device address of cpm_step_charges_static's array
 int cpm_internal_fft_setup(cpm_ctx* c);

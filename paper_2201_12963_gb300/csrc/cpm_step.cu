@@ -296,6 +296,8 @@ struct CellPairTgt {
   const void* qT;           // electrode target charges [rep][n_fixed] in the working precision, or nullptr
   double* force;            // += KE c_t sum_s c_s g(r) d at [rep * n_fixed + original index][3], or nullptr
   double* phi_out;          // sum over set 0 of c_s kernel(r), [rep][n_fixed] original order, or nullptr
+  double* field;            // FORCE: = KE sum_s c_s g(r) d over both sets, the force per unit target charge,
+                            // at [rep * n_fixed + original index][3] (written, not added), or nullptr
 };
 
 constexpr int PC_MAXT = 64;        // targets per pass of a block
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   __shared__ T ifrc[3][PC_MAXT];
   __shared__ int st_first[PC_MAXSTEN];
   __shared__ int st_pre[PC_MAXSTEN + 1];
-  __shared__ short st_d[3][PC_MAXSTEN];
+  __shared__ T st_sh[3][PC_MAXSTEN];                // image / neighbour-cell shift of each stencil cell
   __shared__ int wq[PC_THREADS / 32][64];       // per-warp ring of staged sources within r_c
 
   const int rep = blockIdx.y;
@@ -415,11 +417,15 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       const T beta = (T)s_beta;
       __syncthreads();
       // ---- stencil cells whose box can hold a source within r_c of some point of this cell
+      const float inv_w0 = 1.0f / (float)g.w[0], inv_w1 = 1.0f / (float)g.w[1];
       for (int si = tid; si < nsten; si += PC_THREADS) {
-        const int dx = si % g.w[0] - g.sten[0];
-        const int r1 = si / g.w[0];
-        const int dy = r1 % g.w[1] - g.sten[1];
-        const int dz = r1 / g.w[1] - g.sten[2];            // -sten .. gzb - 1 + sten
+        // si = (dz' w1 + dy') w0 + dx' with small non-negative integers: the quotients by float
+        // reciprocals are exact (si < 2^12)
+        const int r1 = (int)(((float)si + 0.5f) * inv_w0);
+        const int dx = si - r1 * g.w[0] - g.sten[0];
+        const int r2 = (int)(((float)r1 + 0.5f) * inv_w1);
+        const int dy = r1 - r2 * g.w[1] - g.sten[1];
+        const int dz = r2 - g.sten[2];                      // -sten .. gzb - 1 + sten
         const int gapz = dz < 0 ? -dz - 1 : max(0, dz - gzb);
         const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)gapz * e2;
         int c = 0, f = 0;
@@ -431,9 +437,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         }
         st_first[si] = f;
         st_pre[si + 1] = c;                 // counts, scanned below
-        st_d[0][si] = (short)dx;
-        st_d[1][si] = (short)dy;
-        st_d[2][si] = (short)dz;
+        st_sh[0][si] = (T)dx * e0;
+        st_sh[1][si] = (T)dy * e1;
+        st_sh[2][si] = (T)dz * e2;
       }
       __syncthreads();
       // ---- inclusive scan of the counts (one warp, nsten <= PC_MAXSTEN)
@@ -466,9 +472,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           }
           const int gi = st_first[lo] + (j - st_pre[lo]);
           V4 p = sl[gi];
-          p.x += (T)st_d[0][lo] * e0;
-          p.y += (T)st_d[1][lo] * e1;
-          p.z += (T)st_d[2][lo] * e2;
+          p.x += st_sh[0][lo];
+          p.y += st_sh[1][lo];
+          p.z += st_sh[2][lo];
           if (sq) p.w = sq[s_sorted[gi]];
           src[k] = p;
           if (LJ) {
@@ -604,6 +610,12 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         }
       }
       if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = p0.value();
+      if (FORCE && t.field) {
+        double* fo = t.field + 3 * ((size_t)rep * t.n_fixed + orig);
+        fo[0] = KE * (double)fx;
+        fo[1] = KE * (double)fy;
+        fo[2] = KE * (double)fz;
+      }
       if (want_energy) {
         const T ct = tpos[k].w;
         ea0.add(ct * p0.s);
@@ -673,46 +685,166 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
 }
 
 // Electrode-electrode real-space forces of the frozen electrode from the precomputed list
-// (cpm_build: ee_ptr / ee_g): F_i += KE q_i sum_j q_j G_ij.  One warp per target row (grid-stride),
+// (cpm_build: ee_ptr / ee_g): F_i += KE q_i sum_j q_j G_ij (mulq), or the field E_i += KE sum_j q_j G_ij
+// when the force is formed later as q_i times the total field.  One warp per target row (grid-stride),
 // grid.y = replica; each lane sums its share of the row in float32 (a few tens of terms), the
 // lanes are combined in float64.  The list is streamed once per replica-step (16 bytes per pair);
 // the charges are gathered through the caches.
 __global__ void __launch_bounds__(256) k_ee_forces(const int* __restrict__ ptr, const float4* __restrict__ g, int ne,
-                                                   const float* __restrict__ qT, double* __restrict__ f) {
+                                                   const float* __restrict__ qT, double* __restrict__ f, int grp,
+                                                   int mulq) {
   pdl_enter();
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const float* q = qT + (size_t)rep * ne;
-  const int nw = gridDim.x * (blockDim.x >> 5);
-  for (int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < ne; i += nw) {
-    const int a = ptr[i], e = ptr[i + 1];
-    float sx = 0.f, sy = 0.f, sz = 0.f;
-    // four entries per lane per round: the list loads, then the charge gathers, are all issued
-    // before any is used
-    for (int k0 = a + lane; k0 < e; k0 += 128) {
-      float4 v[4];
+  const int nwarp = gridDim.x * (blockDim.x >> 5);
+  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  // a warp takes grp (1..32) consecutive rows at a time; after each row's float32 reduction lane r
+  // keeps row r's sums, and the float64 epilogue (a few instructions, costly on GB300's narrow
+  // float64 pipe) then runs once per group, one lane per row
+  for (int i0 = warp * grp; i0 < ne; i0 += nwarp * grp) {
+    float mx = 0.f, my = 0.f, mz = 0.f;              // lane r: row i0 + r
+    const int nrow = min(grp, ne - i0);
+    for (int r = 0; r < nrow; ++r) {
+      const int a = ptr[i0 + r], e = ptr[i0 + r + 1];
+      Acc<float> sx, sy, sz;
+      // four entries per lane per round: the list loads, then the charge gathers, all issued
+      // before any is used
+      for (int k0 = a + lane; k0 < e; k0 += 128) {
+        float4 v[4];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int k = k0 + 32 * u;
-        v[u] = k < e ? __ldcs(g + k) : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+        for (int u = 0; u < 4; ++u) {
+          const int k = k0 + 32 * u;
+          v[u] = k < e ? __ldcs(g + k) : make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+        }
+        float qj[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) qj[u] = __ldg(q + __float_as_int(v[u].w));
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          sx.add(qj[u] * v[u].x);
+          sy.add(qj[u] * v[u].y);
+          sz.add(qj[u] * v[u].z);
+        }
       }
-      float qj[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) qj[u] = __ldg(q + __float_as_int(v[u].w));
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        sx = fmaf(qj[u], v[u].x, sx);
-        sy = fmaf(qj[u], v[u].y, sy);
-        sz = fmaf(qj[u], v[u].z, sz);
+      sx.warp_reduce();
+      sy.warp_reduce();
+      sz.warp_reduce();
+      if (lane == r) {
+        mx = sx.s + sx.c;
+        my = sy.s + sy.c;
+        mz = sz.s + sz.c;
       }
     }
-    const double tx = warp_sum((double)sx), ty = warp_sum((double)sy), tz = warp_sum((double)sz);
-    if (lane == 0) {
-      const double c = KE * (double)q[i];
+    if (lane < nrow) {
+      const int i = i0 + lane;
+      const double c = mulq ? KE * (double)q[i] : KE;
       double* fi = f + 3 * ((size_t)rep * ne + i);
-      fi[0] += c * tx;
-      fi[1] += c * ty;
-      fi[2] += c * tz;
+      fi[0] += c * (double)mx;
+      fi[1] += c * (double)my;
+      fi[2] += c * (double)mz;
+    }
+  }
+}
+
+// The same forces from the compressed list (lattice electrode): entry = j | t << 16, t indexing the
+// table of distinct G vectors (cpm_build: ee_idx / ee_tab, the last entry zero), staged in shared
+// memory; rows padded to a multiple of four entries, read as 16-byte chunks, four chunks in flight
+// per lane.  LPR lanes share a row, 32 / LPR rows per pass of a warp; each lane sums the four
+// products of a chunk in float32 and adds the chunks with compensation.  The list is streamed once
+// per replica-step (4 bytes per pair); the charges are gathered through the caches.
+template <int LPR>
+__global__ void __launch_bounds__(256) k_ee_forces_tab(const int* __restrict__ ptr, const uint4* __restrict__ ent,
+                                                       const float4* __restrict__ tab, int ntab, int ne,
+                                                       const float* __restrict__ qT, double* __restrict__ f, int grp,
+                                                       int mulq) {
+  extern __shared__ float4 ee_sh[];
+  constexpr int RPP = 32 / LPR;                        // rows per pass of a warp
+  for (int k = threadIdx.x; k < ntab; k += blockDim.x) ee_sh[k] = tab[k];   // built once, not by the step
+  pdl_enter();
+  __syncthreads();
+  const int rep = blockIdx.y;
+  const int lane = threadIdx.x & 31, seg = lane / LPR, li = lane % LPR;
+  const unsigned pz = (unsigned)(ntab - 1) << 16;     // j = 0 with the zero table entry
+  const uint4 pad = make_uint4(pz, pz, pz, pz);
+  const float* q = qT + (size_t)rep * ne;
+  const int nwarp = gridDim.x * (blockDim.x >> 5);
+  const int warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  for (int i0 = warp * grp; i0 < ne; i0 += nwarp * grp) {
+    const int nrow = min(grp, ne - i0);
+    float mx = 0.f, my = 0.f, mz = 0.f;                // lane r: row i0 + r
+    for (int r0 = 0; r0 < nrow; r0 += RPP) {
+      const int r = r0 + seg;
+      int a = 0, e = 0;                                // the row's 16-byte chunks
+      if (r < nrow) {
+        a = ptr[i0 + r] >> 2;
+        e = ptr[i0 + r + 1] >> 2;
+      }
+      Acc<float> sx, sy, sz;
+      for (int c0 = a + li; c0 < e; c0 += 4 * LPR) {
+        uint4 v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int c = c0 + u * LPR;
+          v[u] = c < e ? __ldcs(ent + c) : pad;
+        }
+        float qj[16];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          qj[4 * u + 0] = __ldg(q + (v[u].x & 0xffffu));
+          qj[4 * u + 1] = __ldg(q + (v[u].y & 0xffffu));
+          qj[4 * u + 2] = __ldg(q + (v[u].z & 0xffffu));
+          qj[4 * u + 3] = __ldg(q + (v[u].w & 0xffffu));
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const unsigned w[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+          float px = 0.f, py = 0.f, pz4 = 0.f;
+#pragma unroll
+          for (int h = 0; h < 4; ++h) {
+            const float4 gv = ee_sh[w[h] >> 16];
+            px = fmaf(qj[4 * u + h], gv.x, px);
+            py = fmaf(qj[4 * u + h], gv.y, py);
+            pz4 = fmaf(qj[4 * u + h], gv.z, pz4);
+          }
+          sx.add(px);
+          sy.add(py);
+          sz.add(pz4);
+        }
+      }
+      // compensated sum over the row's LPR lanes (every lane of the segment ends with it)
+#pragma unroll
+      for (int o = LPR / 2; o > 0; o >>= 1) {
+        const float x1 = __shfl_xor_sync(FULL, sx.s, o), x2 = __shfl_xor_sync(FULL, sx.c, o);
+        const float y1 = __shfl_xor_sync(FULL, sy.s, o), y2 = __shfl_xor_sync(FULL, sy.c, o);
+        const float z1 = __shfl_xor_sync(FULL, sz.s, o), z2 = __shfl_xor_sync(FULL, sz.c, o);
+        sx.add(x1);
+        sx.c += x2;
+        sy.add(y1);
+        sy.c += y2;
+        sz.add(z1);
+        sz.c += z2;
+      }
+      // segment g's row goes to lane r0 + g
+#pragma unroll
+      for (int g = 0; g < RPP; ++g) {
+        const float vx = __shfl_sync(FULL, sx.s + sx.c, g * LPR);
+        const float vy = __shfl_sync(FULL, sy.s + sy.c, g * LPR);
+        const float vz = __shfl_sync(FULL, sz.s + sz.c, g * LPR);
+        if (lane == r0 + g) {
+          mx = vx;
+          my = vy;
+          mz = vz;
+        }
+      }
+    }
+    if (lane < nrow) {                                 // float64 epilogue once per group of rows
+      const int i = i0 + lane;
+      const double c = mulq ? KE * (double)q[i] : KE;
+      double* fi = f + 3 * ((size_t)rep * ne + i);
+      fi[0] += c * (double)mx;
+      fi[1] += c * (double)my;
+      fi[2] += c * (double)mz;
     }
   }
 }
@@ -946,6 +1078,12 @@ __global__ void __launch_bounds__(PW_THREADS) k_pair_warp(const CellPairTgt t, c
     }
     if (lane == 0) {
       if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = pot[0].value();
+      if (FORCE && t.field) {
+        double* fo = t.field + 3 * ((size_t)rep * t.n_fixed + orig);
+        fo[0] = KE * (double)fx;
+        fo[1] = KE * (double)fy;
+        fo[2] = KE * (double)fz;
+      }
       if (want_energy) {
         const T ct = tp.w;
         ea0.add(ct * pot[0].s);
@@ -996,7 +1134,8 @@ __device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, int nb, const
                                                   const SpmeGeom sg,
                                                   const typename Vec4<T>::type* __restrict__ l_tmp,
                                                   const int* __restrict__ l_cell, const int* __restrict__ splI,
-                                                  const T* __restrict__ splF, T* __restrict__ mesh) {
+                                                  const T* __restrict__ splF, T* __restrict__ mesh,
+                                                  const int* __restrict__ srt = nullptr) {
   __shared__ T sw[8][kSiteBatch][3][PMAX];
   __shared__ int si0[8][kSiteBatch][3];
   __shared__ T sq[8][kSiteBatch];
@@ -1005,19 +1144,23 @@ __device__ __forceinline__ void spread_elyt_sites(int bx, int nbx, int nb, const
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const float inv_p = 1.0f / (float)P;
+  // the lane's (y, z) stencil tasks (lane and lane + 32), computed once: the int <-> float
+  // conversions of the row index stay out of the per-site loops
+  const int ty0 = task_row(lane, inv_p), tz0 = lane - ty0 * P;
+  const int ty1 = task_row(lane + 32, inv_p), tz1 = lane + 32 - ty1 * P;
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const int nw = (nbx * blockDim.x) >> 5;
   const int first = (bx * blockDim.x + threadIdx.x) >> 5;
   // warp-batches of nb consecutive sites: the weights of the batch in one pass, then each site's stencil
   for (int i0 = first * nb; i0 < n; i0 += nw * nb) {
     batch_weights<T>(i0, n, nb, (size_t)rep * cap, l_tmp, l_cell, sg, splI, splF, lane, sw[wib], nullptr, si0[wib],
-                     sq[wib]);
+                     sq[wib], srt);
     const int cnt = min(nb, n - i0);
     for (int si = 0; si < cnt; ++si) {
       const T qv = sq[wib][si];
       const int* b0 = si0[wib][si];
       for (int task = lane; task < P * P; task += 32) {
-        const int ty = task_row(task, inv_p), tz = task - ty * P;
+        const int ty = task < 32 ? ty0 : ty1, tz = task < 32 ? tz0 : tz1;
         const int gy = wrap_near(b0[1] - ty, K2), gz = wrap_near(b0[2] - tz, K3);
         const T wyz = qv * sw[wib][si][1][ty] * sw[wib][si][2][tz];
         for (int tx = 0; tx < P; ++tx) {
@@ -1039,6 +1182,10 @@ __device__ __forceinline__ void spread_elec_sites(int bx, int nbx, const T* __re
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const float inv_p = 1.0f / (float)P;
+  // the lane's (y, z) stencil tasks (lane and lane + 32), computed once: the int <-> float
+  // conversions of the row index stay out of the per-site loops
+  const int ty0 = task_row(lane, inv_p), tz0 = lane - ty0 * P;
+  const int ty1 = task_row(lane + 32, inv_p), tz1 = lane + 32 - ty1 * P;
   T* m = mesh + (size_t)rep * sg.Mr_s;
   const T* qr = qT + (size_t)rep * ne;
   for (int i = (bx * blockDim.x + threadIdx.x) >> 5; i < ne; i += (nbx * blockDim.x) >> 5) {
@@ -1046,7 +1193,7 @@ __device__ __forceinline__ void spread_elec_sites(int bx, int nbx, const T* __re
     const int4 b = base[i];
     const T* w = th + (size_t)i * 3 * PMAX;
     for (int task = lane; task < P * P; task += 32) {
-      const int ty = task_row(task, inv_p), tz = task - ty * P;
+      const int ty = task < 32 ? ty0 : ty1, tz = task < 32 ? tz0 : tz1;
       const int gy = wrap_near(b.y - ty, K2), gz = wrap_near(b.z - tz, K3);
       const T wyz = qi * w[PMAX + ty] * w[2 * PMAX + tz];
       for (int tx = 0; tx < P; ++tx) {
@@ -1082,10 +1229,10 @@ __global__ void __launch_bounds__(256) k_spread_all(int nb_elyt, int nb, const i
                                                     const int* __restrict__ l_cell, const int* __restrict__ splI,
                                                     const T* __restrict__ splF, const T* __restrict__ qT, int ne,
                                                     const int4* __restrict__ base, const T* __restrict__ th,
-                                                    T* __restrict__ mesh) {
+                                                    T* __restrict__ mesh, const int* __restrict__ srt) {
   pdl_enter();
   if ((int)blockIdx.x < nb_elyt)
-    spread_elyt_sites<T>(blockIdx.x, nb_elyt, nb, off, cap, sg, l_tmp, l_cell, splI, splF, mesh);
+    spread_elyt_sites<T>(blockIdx.x, nb_elyt, nb, off, cap, sg, l_tmp, l_cell, splI, splF, mesh, srt);
   else
     spread_elec_sites<T>(blockIdx.x - nb_elyt, gridDim.x - nb_elyt, qT, ne, base, th, sg, mesh);
 }
@@ -1122,40 +1269,58 @@ __global__ void __launch_bounds__(256) k_influence(T2* __restrict__ spec, const 
 // b_i = -(KE phi_real_i + phi_mesh_i) (- KE 4 pi / V z_i sum_j Q_j Z_j for the slab), one warp per site,
 // written to b (row stride ldb); with b32 != nullptr also the float32 split b = hi + lo
 // (hi = fl(b), lo = fl(b - hi)) for the mixed-precision S-apply, halves of length ldx.
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_b(const T* __restrict__ phi, int ne, const int4* __restrict__ base,
                                                   const T* __restrict__ th, SpmeGeom sg,
                                                   const double* __restrict__ phi_real, const double* __restrict__ ez,
                                                   double slab_coef, const double* __restrict__ scal,
                                                   double* __restrict__ b, float* __restrict__ b32, int ldx,
-                                                  int ldb) {
+                                                  int ldb, int grp) {
   pdl_enter();
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const float inv_p = 1.0f / (float)P;
+  // the lane's (y, z) stencil tasks (lane and lane + 32), computed once: the int <-> float
+  // conversions of the row index stay out of the per-site loops
+  const int ty0 = task_row(lane, inv_p), tz0 = lane - ty0 * P;
+  const int ty1 = task_row(lane + 32, inv_p), tz1 = lane + 32 - ty1 * P;
   const T* m = phi + (size_t)rep * sg.Mr_s;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
-    const int4 bs = base[i];
-    const T* w = th + (size_t)i * 3 * PMAX;
-    Acc<T> acc;
-    for (int task = lane; task < P * P; task += 32) {
-      const int ty = task_row(task, inv_p), tz = task - ty * P;
-      const int gy = wrap_near(bs.y - ty, K2), gz = wrap_near(bs.z - tz, K3);
-      T ph[PMAX];
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  // grp (1..32) consecutive sites per warp: each site's stencil over the lanes (compensated), lane s
+  // keeping site s's sum; the float64 epilogue once per group, one lane per site
+  for (int i0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * grp; i0 < ne; i0 += nwarp * grp) {
+    const int ns = min(grp, ne - i0);
+    T ks = 0, kc = 0;
+    for (int si = 0; si < ns; ++si) {
+      const int i = i0 + si;
+      const int4 bs = base[i];
+      const T* w = th + (size_t)i * 3 * PMAX;
+      Acc<T> acc;
+      for (int task = lane; task < P * P; task += 32) {
+        const int ty = task < 32 ? ty0 : ty1, tz = task < 32 ? tz0 : tz1;
+        const int gy = wrap_near(bs.y - ty, K2), gz = wrap_near(bs.z - tz, K3);
+        T ph[PMAX];
 #pragma unroll
-      for (int tx = 0; tx < PMAX; ++tx)
-        ph[tx] = tx < P ? m[((size_t)wrap_near(bs.x - tx, K1) * K2 + gy) * K3 + gz] : T(0);
-      T s = 0;
+        for (int tx = 0; tx < PMAX; ++tx)
+          ph[tx] = tx < P ? m[((size_t)wrap_near(bs.x - tx, K1) * K2 + gy) * K3 + gz] : T(0);
+        T sx = 0;
 #pragma unroll
-      for (int tx = 0; tx < PMAX; ++tx)
-        if (tx < P) s += w[tx] * ph[tx];
-      acc.add(s * w[PMAX + ty] * w[2 * PMAX + tz]);
+        for (int tx = 0; tx < PMAX; ++tx)
+          if (tx < P) sx += w[tx] * ph[tx];
+        acc.add(sx * w[PMAX + ty] * w[2 * PMAX + tz]);
+      }
+      acc.warp_reduce();
+      if (lane == si) {
+        ks = acc.s;
+        kc = acc.c;
+      }
     }
-    acc.warp_reduce();
-    if (lane == 0) {
+    if (lane < ns) {
+      const int i = i0 + lane;
       const size_t k = (size_t)rep * ne + i;
-      const double bi = -(KE * phi_real[k] + acc.value()) - slab_coef * ez[i] * scal[rep * NSCAL + S_QZ_ELYT];
+      const double bi = -(KE * phi_real[k] + ((double)ks + (double)kc)) - slab_coef * ez[i] * scal[rep * NSCAL + S_QZ_ELYT];
       b[(size_t)rep * ldb + i] = bi;
       if (b32) {
         const float hi = (float)bi;
@@ -1176,7 +1341,8 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
                                                        const T* __restrict__ splF, const double* __restrict__ dpsi,
                                                        double ff_over_lz, double slab_coef,
                                                        const double* __restrict__ scal,
-                                                       const double* __restrict__ f_pair, double* __restrict__ F) {
+                                                       const double* __restrict__ f_pair, double* __restrict__ F,
+                                                       const int* __restrict__ srt) {
   pdl_enter();
   __shared__ T sw[8][kSiteBatch][3][PMAX], sdw[8][kSiteBatch][3][PMAX];
   __shared__ int si0[8][kSiteBatch][3];
@@ -1187,6 +1353,10 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const float inv_p = 1.0f / (float)P;
+  // the lane's (y, z) stencil tasks (lane and lane + 32), computed once: the int <-> float
+  // conversions of the row index stay out of the per-site loops
+  const int ty0 = task_row(lane, inv_p), tz0 = lane - ty0 * P;
+  const int ty1 = task_row(lane + 32, inv_p), tz1 = lane + 32 - ty1 * P;
   const T* m = phi + (size_t)rep * sg.Mr_s;
   const int nw = (gridDim.x * blockDim.x) >> 5;
   const int first = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -1194,15 +1364,16 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
   const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
   for (int i0 = first * nb; i0 < n; i0 += nw * nb) {
     batch_weights<T>(i0, n, nb, (size_t)rep * cap, l_tmp, l_cell, sg, splI, splF, lane, sw[wib], sdw[wib], si0[wib],
-                     sq[wib]);
+                     sq[wib], srt);
     const int cnt = min(nb, n - i0);
+    T kx = 0, ky = 0, kz = 0;                  // lane si: site si's mesh gradient sums
     for (int si = 0; si < cnt; ++si) {
       const int* b0 = si0[wib][si];
       const T (*w)[PMAX] = sw[wib][si];
       const T (*dw)[PMAX] = sdw[wib][si];
       T gx = 0, gy = 0, gz = 0;
       for (int task = lane; task < P * P; task += 32) {
-        const int ty = task_row(task, inv_p), tz = task - ty * P;
+        const int ty = task < 32 ? ty0 : ty1, tz = task < 32 ? tz0 : tz1;
         const int jy = wrap_near(b0[1] - ty, K2), jz = wrap_near(b0[2] - tz, K3);
         // the P mesh loads of the x line issued together (unrolled to the largest order)
         T ph[PMAX];
@@ -1225,70 +1396,100 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
       gx = warp_sum_t(gx);
       gy = warp_sum_t(gy);
       gz = warp_sum_t(gz);
-      if (lane == 0) {
-        const int i = i0 + si;
-        const double q = (double)sq[wib][si];
-        const size_t gi = 3 * (size_t)(o + i);
-        const double* fp = f_pair + 3 * ((size_t)rep * cap + i);
-        F[gi + 0] = -q * (double)gx * sg.kl[0] + fp[0];
-        F[gi + 1] = -q * (double)gy * sg.kl[1] + fp[1];
-        F[gi + 2] = -q * (double)gz * sg.kl[2] + q * ezf + fp[2];
+      if (lane == si) {
+        kx = gx;
+        ky = gy;
+        kz = gz;
       }
+    }
+    // the float64 epilogue once per batch, one lane per site (float64 instructions are costly on
+    // GB300's narrow float64 pipe, so none is issued per site by a single lane)
+    if (lane < cnt) {
+      const int i = srt ? srt[(size_t)rep * cap + i0 + lane] : i0 + lane;      // input index
+      const double q = (double)sq[wib][lane];
+      const size_t gi = 3 * (size_t)(o + i);
+      const double* fp = f_pair + 3 * ((size_t)rep * cap + i);
+      F[gi + 0] = -q * (double)kx * sg.kl[0] + fp[0];
+      F[gi + 1] = -q * (double)ky * sg.kl[1] + fp[1];
+      F[gi + 2] = -q * (double)kz * sg.kl[2] + q * ezf + fp[2];
     }
     __syncwarp();
   }
 }
 
-// k-space force on electrode sites through the fixed stencils (written, not added).
+// k-space force on electrode sites through the fixed stencils (written, not added).  A warp takes
+// grp (1..32) consecutive sites: each site's stencil over the lanes, reduced in float32, lane s
+// keeping site s's sums; the float64 epilogue then runs once per group, one lane per site.
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi, const T* __restrict__ qT,
                                                        int ne, const int4* __restrict__ base,
                                                        const T* __restrict__ th, const T* __restrict__ dth,
                                                        SpmeGeom sg, const double* __restrict__ dpsi,
                                                        double ff_over_lz, double slab_coef,
-                                                       const double* __restrict__ scal, double* __restrict__ F) {
+                                                       const double* __restrict__ scal,
+                                                       const double* __restrict__ efield, double* __restrict__ F,
+                                                       int grp) {
   pdl_enter();
   const int rep = blockIdx.y;
   const int lane = threadIdx.x & 31;
   const int P = sg.P, K1 = sg.K[0], K2 = sg.K[1], K3 = sg.K[2];
   const float inv_p = 1.0f / (float)P;
+  // the lane's (y, z) stencil tasks (lane and lane + 32), computed once: the int <-> float
+  // conversions of the row index stay out of the per-site loops
+  const int ty0 = task_row(lane, inv_p), tz0 = lane - ty0 * P;
+  const int ty1 = task_row(lane + 32, inv_p), tz1 = lane + 32 - ty1 * P;
   const T* m = phi + (size_t)rep * sg.Mr_s;
-  for (int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < ne; i += (gridDim.x * blockDim.x) >> 5) {
-    const int4 bs = base[i];
-    const T* w = th + (size_t)i * 3 * PMAX;
-    const T* dw = dth + (size_t)i * 3 * PMAX;
-    T gx = 0, gy = 0, gz = 0;
-    for (int task = lane; task < P * P; task += 32) {
-      const int ty = task_row(task, inv_p), tz = task - ty * P;
-      const int jy = wrap_near(bs.y - ty, K2), jz = wrap_near(bs.z - tz, K3);
-      T ph[PMAX];
+  const int nwarp = (gridDim.x * blockDim.x) >> 5;
+  for (int i0 = ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) * grp; i0 < ne; i0 += nwarp * grp) {
+    const int ns = min(grp, ne - i0);
+    T kx = 0, ky = 0, kz = 0;
+    for (int si = 0; si < ns; ++si) {
+      const int i = i0 + si;
+      const int4 bs = base[i];
+      const T* w = th + (size_t)i * 3 * PMAX;
+      const T* dw = dth + (size_t)i * 3 * PMAX;
+      T gx = 0, gy = 0, gz = 0;
+      for (int task = lane; task < P * P; task += 32) {
+        const int ty = task < 32 ? ty0 : ty1, tz = task < 32 ? tz0 : tz1;
+        const int jy = wrap_near(bs.y - ty, K2), jz = wrap_near(bs.z - tz, K3);
+        T ph[PMAX];
 #pragma unroll
-      for (int tx = 0; tx < PMAX; ++tx)
-        ph[tx] = tx < P ? m[((size_t)wrap_near(bs.x - tx, K1) * K2 + jy) * K3 + jz] : T(0);
-      T a = 0, ad = 0;
+        for (int tx = 0; tx < PMAX; ++tx)
+          ph[tx] = tx < P ? m[((size_t)wrap_near(bs.x - tx, K1) * K2 + jy) * K3 + jz] : T(0);
+        T a = 0, ad = 0;
 #pragma unroll
-      for (int tx = 0; tx < PMAX; ++tx) {
-        if (tx < P) {
-          a += w[tx] * ph[tx];
-          ad += dw[tx] * ph[tx];
+        for (int tx = 0; tx < PMAX; ++tx) {
+          if (tx < P) {
+            a += w[tx] * ph[tx];
+            ad += dw[tx] * ph[tx];
+          }
         }
+        const T wy = w[PMAX + ty], wz = w[2 * PMAX + tz];
+        gx += ad * wy * wz;
+        gy += a * dw[PMAX + ty] * wz;
+        gz += a * wy * dw[2 * PMAX + tz];
       }
-      const T wy = w[PMAX + ty], wz = w[2 * PMAX + tz];
-      gx += ad * wy * wz;
-      gy += a * dw[PMAX + ty] * wz;
-      gz += a * wy * dw[2 * PMAX + tz];
+      gx = warp_sum_t(gx);
+      gy = warp_sum_t(gy);
+      gz = warp_sum_t(gz);
+      if (lane == si) {
+        kx = gx;
+        ky = gy;
+        kz = gz;
+      }
     }
-    gx = warp_sum_t(gx);
-    gy = warp_sum_t(gy);
-    gz = warp_sum_t(gz);
-    if (lane == 0) {
+    if (lane < ns) {
+      const int i = i0 + lane;
       const double qi = (double)qT[(size_t)rep * ne + i];
       const double mz = scal[rep * NSCAL + S_QZ_ELYT] + scal[rep * NSCAL + S_QZ_ELEC];
       const double ezf = -dpsi[rep] * ff_over_lz - slab_coef * mz;
       const size_t k = 3 * ((size_t)rep * ne + i);
-      F[k + 0] = -qi * (double)gx * sg.kl[0];
-      F[k + 1] = -qi * (double)gy * sg.kl[1];
-      F[k + 2] = -qi * (double)gz * sg.kl[2] + qi * ezf;
+      // + the electrolyte's real-space field at the site, when the b pass computed it
+      const double rx = efield ? efield[k + 0] : 0.0, ry = efield ? efield[k + 1] : 0.0,
+                   rz = efield ? efield[k + 2] : 0.0;
+      F[k + 0] = qi * (rx - (double)kx * sg.kl[0]);
+      F[k + 1] = qi * (ry - (double)ky * sg.kl[1]);
+      F[k + 2] = qi * (rz - (double)kz * sg.kl[2] + ezf);
     }
   }
 }
@@ -1503,7 +1704,7 @@ __global__ void __launch_bounds__(SS_THREADS, 1) k_sapply_stream(const float* __
 
 // q_raw = qpart + dpsi S v (one replica), qpart cleared; the projection sums C^T q_raw and
 // (A^-1 C)^T b as in the S-apply epilogue.
-__global__ void __launch_bounds__(256) k_sapply_finish(int rows, double* __restrict__ qpart,
+__global__ void __launch_bounds__(FIN_THREADS) k_sapply_finish(int rows, double* __restrict__ qpart,
                                                        const double* __restrict__ b, const double* __restrict__ dpsi,
                                                        const double* __restrict__ Sv, const double* __restrict__ W,
                                                        const double* __restrict__ c1, double* __restrict__ qout,
@@ -1766,7 +1967,7 @@ __device__ __forceinline__ void project_sums(double (&acc)[5], double* s) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) k_project(double* __restrict__ q, int ne, int nrep, int ncons,
+__global__ void __launch_bounds__(FIN_THREADS) k_project(double* __restrict__ q, int ne, int nrep, int ncons,
                                                  const double* __restrict__ W, const double* __restrict__ b, int ldb,
                                                  double* __restrict__ scal, const double* __restrict__ dpsi,
                                                  double m00, double m01, double m10, double m11, double wtv0,
@@ -1826,7 +2027,7 @@ __global__ void __launch_bounds__(256) k_mirror_fold(const double* __restrict__ 
 // problem's A q = b + dpsi v + psibar e + psibar_1 e_1 gives psibar = (mu+ + mu-) / 2, psibar_1 = -mu-.
 // Also accumulates q^T b for the closed-form energy.
 template <typename T>
-__global__ void __launch_bounds__(256) k_project_mirror(const double* __restrict__ qpm, int nh,
+__global__ void __launch_bounds__(FIN_THREADS) k_project_mirror(const double* __restrict__ qpm, int nh,
                                                         const int* __restrict__ i0, const int* __restrict__ jm,
                                                         const double* __restrict__ W, const double* __restrict__ b,
                                                         int ldb, int ne, double* __restrict__ scal,
@@ -1962,6 +2163,15 @@ static int site_batch(const cpm_ctx* c, int cap, int nrep) {
   return (int)std::max(1LL, std::min<long long>(kSiteBatch, sites / warps));
 }
 
+// Electrode sites (or pair-list rows) per warp in the electrode gathers and k_ee_forces: as many
+// as keep about 32 warps per SM busy, at most 8 -- the float64 epilogue of a group runs once, one
+// lane per site (float64 instructions are costly on GB300's narrow float64 pipe), while small
+// electrodes keep one site per warp for parallelism.
+static int elec_group(const cpm_ctx* c, int ne, int nrep) {
+  const long long warps = (long long)std::max(1, c->n_sm) * 32;
+  return (int)std::max(1LL, std::min<long long>(8, (long long)ne * nrep / warps));
+}
+
 static int grid_for(long long warps_needed, int per_block_warps = 8, int max_blocks = 152 * 16) {
   long long b = (warps_needed + per_block_warps - 1) / per_block_warps;
   return (int)std::max(1LL, std::min<long long>(b, max_blocks));
@@ -2051,7 +2261,7 @@ static int sapply_stream(cpm_ctx* c, const float* S, int rows, int ld, const flo
   else
     CPM_CUDA(launch_pdl(k_sapply_stream<8>, c->n_sm, SS_THREADS, smem, st, S, ld, rows, xh, xl, qpart));
   STEP_LAUNCH();
-  CPM_CUDA(launch_pdl(k_sapply_finish, (rows + 255) / 256, 256, 0, st, rows, qpart, b, dpsi, Sv, W, c1, qout, c->scal));
+  CPM_CUDA(launch_pdl(k_sapply_finish, (rows + FIN_THREADS - 1) / FIN_THREADS, FIN_THREADS, 0, st, rows, qpart, b, dpsi, Sv, W, c1, qout, c->scal));
   STEP_LAUNCH();
   return CPM_OK;
 }
@@ -2136,18 +2346,27 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
 
   // closed-form energy when the charges are solved in this call (cpm_step): U_elyt - q^T b / 2 + dpsi q^T v / 2
   const bool closed_form = charges && energy != nullptr;
+  // electrolyte real-space field at the electrode sites from the b pass (electrode forces of cpm_step)
+  const bool elec_field = charges && f_elec != nullptr && c->e_field != nullptr;
 
   if (charges) {
     double* b = c->b_tmp;                 // aligned internal copy, row stride ldb
     const int ldb = c->ldb;
     // real-space Gaussian-point part of b at the electrode sites
-    // (on the side stream, concurrent with the mesh chain below; joined before the gather)
-    CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, nullptr, nullptr, c->phi_real};
+    // (on the side stream, concurrent with the mesh chain below; joined before the gather).  When
+    // electrode forces follow in this call, the same pairs also give the electrolyte's real-space
+    // field at the electrode sites: the electrode force is its charge times that field, so the
+    // force pass needs no second sweep over these pairs.
+    CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, nullptr, nullptr, c->phi_real,
+                   elec_field ? c->e_field : nullptr};
     PairSrc s = src_elyt;
     s.beta = c->p.eta;
     {
       PhaseTimer pt(c, st, CPM_PH_B_REAL);
-      CPM_TRY((launch_pair<T, false, false>(c, true, tg, s, none, g, nrep, ne, PairLj{}, sside)));
+      if (elec_field)
+        CPM_TRY((launch_pair<T, true, false>(c, true, tg, s, none, g, nrep, ne, PairLj{}, sside)));
+      else
+        CPM_TRY((launch_pair<T, false, false>(c, true, tg, s, none, g, nrep, ne, PairLj{}, sside)));
     }
     if (fork) CPM_CUDA(cudaEventRecord(c->ev_join, c->side));
     // SPME part
@@ -2170,10 +2389,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     {
       PhaseTimer pt(c, st, CPM_PH_B_GATHER);
-      CPM_CUDA(launch_pdl(k_gather_b<T>, dim3(grid_for(ne), nrep), 256, 0, st, (const T*)c->mesh_phi, ne, c->e_base, e_th, sg,
-                                                              c->phi_real, c->e_z, slab_coef, c->scal, b,
-                                                              (c->mixed && !c->mirror) ? c->b32 : nullptr,
-                                                              c->ldx, ldb));
+      const int grp = elec_group(c, ne, nrep);
+      CPM_CUDA(launch_pdl(k_gather_b<T>, dim3(grid_for((ne + grp - 1) / grp), nrep), 256, 0, st, (const T*)c->mesh_phi, ne,
+                          c->e_base, e_th, sg, c->phi_real, c->e_z, slab_coef, c->scal, b,
+                          (c->mixed && !c->mirror) ? c->b32 : nullptr, c->ldx, ldb, grp));
       STEP_LAUNCH();
       if (b_out) {
         CPM_CUDA(cudaMemcpy2DAsync(b_out, sizeof(double) * ne, b, sizeof(double) * ldb, sizeof(double) * ne, nrep,
@@ -2217,7 +2436,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // streaming variant: mixed precision, one replica, right-hand side fits shared memory
     const bool stream_ok = c->mixed && nrep == 1 && c->qpart &&
                            (c->sapply_variant == CPM_SAPPLY_STREAM || c->sapply_variant == CPM_SAPPLY_STREAM16);
-    const bool sym_ok = c->mixed && nrep == 1 && c->sym_ok && c->sapply_variant == CPM_SAPPLY_SYM;
+    const bool sym_ok = c->mixed && nrep == 1 && c->sym_ok &&
+                        (c->sapply_variant == CPM_SAPPLY_SYM || c->sapply_variant == CPM_SAPPLY_SYM_TMA);
     {
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
       if (c->mirror) {
@@ -2268,11 +2488,11 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     const bool forces_follow = f_elyt || f_elec || energy;
     const ChargePrep<T> cprep{forces_follow ? qT : nullptr, c->e_z, c->e_v, c->e_plus};
     if (c->mirror) {
-      CPM_CUDA(launch_pdl(k_project_mirror<T>, dim3((c->nh + 255) / 256, nrep), 256, 0, st, c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
+      CPM_CUDA(launch_pdl(k_project_mirror<T>, dim3((c->nh + FIN_THREADS - 1) / FIN_THREADS, nrep), FIN_THREADS, 0, st, c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
                                                                         ldb, ne, c->scal, dpsi, c->Mh[0], c->Mh[1],
                                                                         c->WTv[0], c->WTv[1], q, psibar, cprep));
     } else {
-      CPM_CUDA(launch_pdl(k_project<T>, dim3((ne + 255) / 256, nrep), 256, 0, st, q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
+      CPM_CUDA(launch_pdl(k_project<T>, dim3((ne + FIN_THREADS - 1) / FIN_THREADS, nrep), FIN_THREADS, 0, st, q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
                                                               c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
                                                               c->WTv[1], psibar, cprep));
     }
@@ -2286,11 +2506,50 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       CPM_CUDA(launch_pdl(k_charge_prep<T>, dim3((ne + 255) / 256, nrep), 256, 0, st, q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal));
       STEP_LAUNCH();
     }
+    // Electrode-electrode forces of the frozen electrode from the pair list precomputed at build
+    // (mixed precision, forces without the full-sum energy).  In cpm_step they are added to the
+    // electrolyte field of the b pass, on the side stream ahead of the electrolyte pair forces,
+    // and the electrode gather forms q_i times the total field; otherwise they are added to the
+    // forces after the gather.
+    const bool ee_list = (c->ee_g != nullptr || c->ee_idx != nullptr) && f_elec && !(energy && !closed_form) &&
+                         sizeof(T) == sizeof(float);
+    const bool ee_field = ee_list && elec_field;
+    auto launch_ee = [&](cudaStream_t s_ee, double* dst, int mulq) -> int {
+      if (c->ee_idx) {
+        // 8 lanes per row when the rows fill the resident warps, else 32; row groups of 4 or 1 rows
+        // per warp pass (a multiple of the rows one pass takes)
+        const bool wide = (long long)ne * nrep * 8 < (long long)c->n_sm * 24 * 32;
+        const int rpp = wide ? 1 : 4;
+        const int grp = std::max(rpp, (elec_group(c, ne, nrep) + rpp - 1) / rpp * rpp);
+        const int blocks = std::max(1, std::min((ne + 8 * grp - 1) / (8 * grp), c->n_sm * 8));
+        const size_t smem = sizeof(float4) * (size_t)c->ee_ntab;
+        if (wide)
+          CPM_CUDA(launch_pdl(k_ee_forces_tab<32>, dim3(blocks, nrep), 256, smem, s_ee, (const int*)c->ee_ptr,
+                              (const uint4*)c->ee_idx, (const float4*)c->ee_tab, c->ee_ntab, ne, (const float*)qT,
+                              dst, grp, mulq));
+        else
+          CPM_CUDA(launch_pdl(k_ee_forces_tab<8>, dim3(blocks, nrep), 256, smem, s_ee, (const int*)c->ee_ptr,
+                              (const uint4*)c->ee_idx, (const float4*)c->ee_tab, c->ee_ntab, ne, (const float*)qT,
+                              dst, grp, mulq));
+      } else {
+        const int grp = elec_group(c, ne, nrep);
+        const int blocks = std::max(1, std::min((ne + 8 * grp - 1) / (8 * grp), c->n_sm * 8));
+        CPM_CUDA(launch_pdl(k_ee_forces, dim3(blocks, nrep), 256, 0, s_ee, (const int*)c->ee_ptr,
+                            (const float4*)c->ee_g, ne, (const float*)qT, dst, grp, mulq));
+      }
+      STEP_LAUNCH();
+      return CPM_OK;
+    };
     // real space, electrolyte targets: point-point (elyt) + Gaussian-point (electrodes), into f_pair;
     // on the side stream, concurrent with the mesh chain, joined before the force gather
     if (fork) {
       CPM_CUDA(cudaEventRecord(c->ev_fork, st));
       CPM_CUDA(cudaStreamWaitEvent(c->side, c->ev_fork, 0));
+    }
+    if (ee_field) {
+      PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
+      CPM_TRY(launch_ee(sp, c->e_field, 0));
+      if (fork) CPM_CUDA(cudaEventRecord(c->ev_ee, c->side));
     }
     {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELYT);
@@ -2331,8 +2590,13 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       } else {
         CPM_CUDA(cudaMemsetAsync(c->mesh_r, 0, mesh_bytes, st));
         const int nb_l = grid_for((cap + sb - 1) / sb), nb_e = grid_for(ne);
-        CPM_CUDA(launch_pdl(k_spread_all<T>, dim3(nb_l + nb_e, nrep), 256, 0, st, nb_l, sb, off, cap, sg, l_tmp, c->l_cell,
-                            c->spl_I, splF, qT, ne, c->e_base, e_th, (T*)c->mesh_r));
+        // electrolyte sites in cell-sorted order: neighbouring sites' atomics hit the same lines
+        // (the sorted list reached the main stream at the b pass's join; in a call without
+        // charges the join comes below, so input order is used there)
+        const bool sorted_ok = charges || !fork;
+        CPM_CUDA(launch_pdl(k_spread_all<T>, dim3(nb_l + nb_e, nrep), 256, 0, st, nb_l, sb, off, cap, sg,
+                            sorted_ok ? (const V4*)l_loc : (const V4*)l_tmp, c->l_cell, c->spl_I, splF, qT, ne,
+                            c->e_base, e_th, (T*)c->mesh_r, sorted_ok ? (const int*)c->l_sorted : nullptr));
         STEP_LAUNCH();
       }
     }
@@ -2340,46 +2604,50 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PhaseTimer pt(c, st, CPM_PH_F_FFT);
       CPM_TRY(convolve<T>(c, nrep, (energy && !closed_form) ? S_E_RECIP : -1, st));
     }
-    if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     PhaseTimer ptg(c, st, CPM_PH_F_GATHER);
+    // electrode sites first: they wait only for the pair-list field (when it is used), not for
+    // the electrolyte pair forces
+    if (f_elec) {
+      if (fork && ee_field) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_ee, 0));
+      const int grp = elec_group(c, ne, nrep);
+      CPM_CUDA(launch_pdl(k_gather_f_elec<T>, dim3(grid_for((ne + grp - 1) / grp), nrep), 256, 0, st, (const T*)c->mesh_phi, qT,
+                          ne, c->e_base, e_th, e_dth, sg, dpsi, ff_over_lz, slab_coef, c->scal,
+                          elec_field ? (const double*)c->e_field : nullptr, f_elec, grp));
+      STEP_LAUNCH();
+    }
+    if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     if (f_elyt && brick) {
       CPM_TRY(cpm_internal_gather_f_brick(c, nrep, off, l_loc, dpsi, ff_over_lz, slab_coef, f_elyt, st));
     } else if (f_elyt) {
+      // cell-sorted order (the sort has joined the main stream in the b pass, or just above)
       CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for((cap + sb - 1) / sb), nrep), 256, 0, st, sb,
-                          (const T*)c->mesh_phi, off, cap, sg, l_tmp, c->l_cell, c->spl_I, splF, dpsi, ff_over_lz,
-                          slab_coef, c->scal, c->f_pair, f_elyt));
-      STEP_LAUNCH();
-    }
-    if (f_elec) {
-      CPM_CUDA(launch_pdl(k_gather_f_elec<T>, dim3(grid_for(ne), nrep), 256, 0, st, (const T*)c->mesh_phi, qT, ne, c->e_base, e_th,
-                                                                   e_dth, sg, dpsi, ff_over_lz, slab_coef, c->scal,
-                                                                   f_elec));
+                          (const T*)c->mesh_phi, off, cap, sg, (const V4*)l_loc, c->l_cell, c->spl_I, splF, dpsi,
+                          ff_over_lz, slab_coef, c->scal, c->f_pair, f_elyt, (const int*)c->l_sorted));
       STEP_LAUNCH();
     }
     ptg.stop();
-    // real space, electrode targets: Gaussian-point (forces only) + Gaussian-Gaussian (forces, and
-    // the energy of the full sum).  With forces only and the precomputed electrode pair list (mixed
-    // precision, frozen electrode), the Gaussian-Gaussian forces come from the list instead.
+    // real space, electrode targets: Gaussian-point (forces only, unless the b pass gave the field)
+    // + Gaussian-Gaussian (forces, and the energy of the full sum) unless the pair list gives them
     if (f_elec || (energy && !closed_form)) {
-      PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
-      const bool ee_list = c->ee_g != nullptr && f_elec && !(energy && !closed_form) && sizeof(T) == sizeof(float);
-      CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, qT, f_elec, nullptr};
-      PairSrc a = f_elec ? src_elyt : none;
+      CellPairTgt tg{e_loc, 0, c->e_start, 0, c->e_sorted, ne, qT, f_elec, nullptr, nullptr};
+      PairSrc a = (f_elec && !elec_field) ? src_elyt : none;
       a.beta = c->p.eta;
       PairSrc e = src_elec;
       e.qT = qT;
       e.beta = c->p.eta / std::sqrt(2.0);
       e.slot = (energy && !closed_form) ? S_E_EE : -1;
       if (ee_list) e = none;
-      if (f_elec)
-        CPM_TRY((launch_pair<T, true, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
-      else
-        CPM_TRY((launch_pair<T, false, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
-      if (ee_list) {
-        const int blocks = std::max(1, std::min((ne + 7) / 8, c->n_sm * 8));
-        CPM_CUDA(launch_pdl(k_ee_forces, dim3(blocks, nrep), 256, 0, st, (const int*)c->ee_ptr, (const float4*)c->ee_g,
-                            ne, (const float*)qT, f_elec));
-        STEP_LAUNCH();
+      const bool ee_late = ee_list && !ee_field;
+      if (a.loc != nullptr || e.loc != nullptr || ee_late) {
+        PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELEC);
+        if (a.loc == nullptr && e.loc == nullptr) {
+          // the pair list alone
+        } else if (f_elec) {
+          CPM_TRY((launch_pair<T, true, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
+        } else {
+          CPM_TRY((launch_pair<T, false, false>(c, true, tg, a, e, g, nrep, ne, PairLj{}, st)));
+        }
+        if (ee_late) CPM_TRY(launch_ee(st, f_elec, 1));
       }
     }
     if (energy) {
@@ -2442,6 +2710,10 @@ static int pair_cell_attributes() {
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<float, false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, w32));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<float, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, w32));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_warp<float, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, w32));
+  // compressed electrode pair list: the table of distinct G vectors
+  const int et = (int)(sizeof(float4) * cpm::kEeTabMax);
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_ee_forces_tab<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, et));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_ee_forces_tab<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, et));
   return CPM_OK;
 }
 
@@ -2479,7 +2751,6 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   c->pair_gz = 1;
   CPM_TRY(cpm_internal_fft_setup(c));
   CPM_TRY(cpm_internal_brick_setup(c));
-  CPM_TRY(cpm_internal_sym_setup(c));
   if (stream_available(c)) {
     CPM_CUDA(cudaFuncSetAttribute(cpm::k_sapply_stream<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   cpm::SS_SMEM_MAX));
@@ -2491,6 +2762,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
     // default before any tuning: stream matrices well above the L2 capacity
     c->sapply_variant = (rows * c->ld32 * 4LL >= (64LL << 20)) ? CPM_SAPPLY_STREAM : CPM_SAPPLY_ROWS;
   }
+  CPM_TRY(cpm_internal_sym_setup(c));          // after qpart: the packed S-apply adds into it
   const size_t R = c->p.max_replicas, cap = c->p.max_elyt, ne = c->ne;
   const size_t tsz = c->mixed ? sizeof(float) : sizeof(double);
   const size_t v4 = c->mixed ? sizeof(float4) : sizeof(double4_32a);
@@ -2508,6 +2780,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaMalloc(&c->l_tmp, v4 * R * cap));
   CPM_CUDA(cudaMalloc(&c->qT, tsz * R * ne));
   CPM_CUDA(cudaMalloc(&c->phi_real, sizeof(double) * R * ne));
+  CPM_CUDA(cudaMalloc(&c->e_field, sizeof(double) * 3 * R * ne));
   CPM_CUDA(cudaMalloc(&c->b_tmp, sizeof(double) * R * c->ldb));
   CPM_CUDA(cudaMemset(c->b_tmp, 0, sizeof(double) * R * c->ldb));
   CPM_CUDA(cudaMalloc(&c->b32, sizeof(float) * R * 2 * c->ldx));
@@ -2522,6 +2795,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_sorted, cudaEventDisableTiming));
+  CPM_CUDA(cudaEventCreateWithFlags(&c->ev_ee, cudaEventDisableTiming));
   CPM_CUDA(cudaMalloc(&c->scal, sizeof(double) * R * cpm::NSCAL));
   if (c->mixed && (int)R >= cpm::TC_MIN_REPLICAS) CPM_CUDA(cudaMalloc(&c->qraw32, sizeof(float) * R * ne));
   CPM_CUDA(cudaMalloc(&c->status, sizeof(int)));
@@ -2564,7 +2838,7 @@ extern "C" int cpm_set_sapply_variant(cpm_ctx* c, int32_t variant) {
     return CPM_OK;
   }
   if (((variant == CPM_SAPPLY_STREAM || variant == CPM_SAPPLY_STREAM16) && stream_available(c) && c->qpart) ||
-      (variant == CPM_SAPPLY_SYM && c->sym_ok)) {
+      ((variant == CPM_SAPPLY_SYM || variant == CPM_SAPPLY_SYM_TMA) && c->sym_ok)) {
     c->sapply_variant = variant;
     return CPM_OK;
   }
@@ -2703,7 +2977,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   // choices made so far
   int best_s = keep_s, best_f = CPM_FFT_LIBRARY, best_m = CPM_MESH_SITES;
   float best_ms = 0.f, t = 0.f;
-  for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16, CPM_SAPPLY_SYM}) {
+  for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16, CPM_SAPPLY_SYM, CPM_SAPPLY_SYM_TMA}) {
     if (time_config(sv, CPM_FFT_LIBRARY, CPM_MESH_SITES, &t) && (best_ms == 0.f || t < best_ms)) {
       best_ms = t;
       best_s = sv;

@@ -249,15 +249,23 @@ def _rms_rel(a, b):
     return float(np.sqrt(((a - b) ** 2).sum() / (b ** 2).sum()))
 
 
-@pytest.mark.parametrize("case", ["plain", "dc", "batched"])
+@pytest.mark.parametrize("case", ["plain", "jittered", "dc", "batched"])
 def test_electrode_forces_from_the_precomputed_pair_list(plain_ff, case):
     """cpm_step with electrode forces (closed-form energy) in mixed precision takes the
-    Gaussian-Gaussian forces of the frozen electrode from the pair list precomputed at build;
-    cpm_forces with the full energy computes them in the pair kernels.  Both must agree, and
-    with the oracle's electrode forces."""
+    Gaussian-Gaussian forces of the frozen electrode from the pair list precomputed at build, and
+    the electrolyte's real-space force on the electrode sites from the field of the b pass;
+    cpm_forces with the full energy computes both in the pair kernels.  Both must agree, and
+    with the oracle's electrode forces.  The lattice electrodes take the compressed list (a table
+    of distinct G vectors); `jittered` moves every electrode site by up to 0.02 A, so that the G
+    vectors no longer repeat and the full list is used."""
     g, System = _lib()
     if case == "plain":
         w, _, out = plain_ff
+    elif case == "jittered":
+        w = dataclasses.replace(plain_ff[0])
+        rng = np.random.Generator(np.random.PCG64(91))
+        w.elec_xyz = np.asarray(w.elec_xyz, float) + rng.uniform(-0.02, 0.02, size=np.shape(w.elec_xyz))
+        out = ocpm.Reference(w).step()
     elif case == "dc":
         w = synth.mirror_to_doubled(synth.tiny_cell(seed=4, n_pairs=4), "independent", seed=40)
         w.grid = (18, 16, 144)
@@ -266,6 +274,9 @@ def test_electrode_forces_from_the_precomputed_pair_list(plain_ff, case):
         w = synth.config_batched(n_rep=3)
         out = None
     a = System(w, "mixed", order=8)
+    pairs, table = g.cpm_pair_list_layout(a.ctx)
+    assert pairs > 0
+    assert (table == 0) if case == "jittered" else (0 < table < 4096)
     a.step(elec=True, energy=True)
     ra = a.results()
     assert g.cpm_status(a.ctx) == 0

@@ -1,10 +1,11 @@
 """S-apply kernel variants and the autotuner (GPU).
 
-The single-replica mixed-precision S-apply has two kernels: one warp per row of S, and a streaming
-kernel (persistent CTAs with the right-hand side in shared memory, equal contiguous spans of S per
-warp, float64 row partial sums).  Both must give the same charges to float32 rounding and match the
-oracle at the charge bar, in the full and the mirror-block layouts; cpm_autotune must keep one of
-them and leave the context's results unchanged.
+The single-replica mixed-precision S-apply has several kernels: one warp per row of S, streaming
+kernels (persistent CTAs with the right-hand side in shared memory, equal contiguous spans of S per
+warp, float64 row partial sums), and the packed upper-triangle tiles read with plain loads or with
+bulk asynchronous copies into shared memory.  All must give the same charges to float32 rounding
+and match the oracle at the charge bar, in the full and the mirror-block layouts; cpm_autotune must
+keep one of them and leave the context's results unchanged.
 """
 import numpy as np
 import pytest
@@ -38,7 +39,7 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
         out = ocpm.Reference(w).step(want_forces=False, want_energy=False)
     s = System(w, "mixed", order=8)
     qs = {}
-    for v in ("rows", "stream", "stream16", "sym"):
+    for v in ("rows", "stream", "stream16", "sym", "sym-tma"):
         g.cpm_set_sapply_variant(s.ctx, v)
         for _ in range(2):                          # the second call checks the cleared partial sums
             s.charges()
@@ -49,8 +50,9 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
     assert np.max(np.abs(qs["rows"] - qs["stream"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["stream16"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["sym"])) <= 1e-6
+    assert np.max(np.abs(qs["rows"] - qs["sym-tma"])) <= 1e-6
     choice, transform, assign = g.cpm_autotune(s.ctx, s.offsets, s.xyzq, s.dpsi, s.q)
-    assert choice in ("rows", "stream", "stream16", "sym") and transform in ("library", "own")
+    assert choice in ("rows", "stream", "stream16", "sym", "sym-tma") and transform in ("library", "own")
     assert assign in ("sites", "brick")
     s.charges()
     # float32 mesh spreading adds with atomics in no fixed order: repeated mixed-precision runs

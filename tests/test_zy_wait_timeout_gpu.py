@@ -2,7 +2,7 @@
 usable.
 
 The library's only spin-waits are the mbarrier waits of the tcgen05 S-apply (batched replicas,
-mixed precision) and of the TMA brick force gather.  The test hook cpm_set_wait_test makes the
+mixed precision), of the packed S-apply's bulk copies and of the TMA brick force gather.  The test hook cpm_set_wait_test makes the
 first of those waits give up without polling; the kernel then latches the timeout, waits once more
 (bounded) for its own tensor-core work or copy still in flight, and leaves without using it.  So
 the forced timeout causes no fault: the call's results are invalid, cpm_status reports
@@ -62,3 +62,20 @@ def test_brick_gather_timeout_is_latched_and_recoverable(plain_ff):
     F = s.results()["F_elyt"][0]
     # float32 atomics in the spread: repeated runs differ at rounding; held to the force bar
     assert np.sqrt(((F - F0) ** 2).sum() / (F0 ** 2).sum()) <= 1e-5
+
+
+def test_packed_bulk_copy_s_apply_timeout_is_latched_and_recoverable(plain_ff):
+    g, System = _lib()
+    s = System(plain_ff[0], "mixed", order=8)
+    g.cpm_set_sapply_variant(s.ctx, "sym-tma")               # packed tiles by cp.async.bulk
+    s.charges()
+    assert g.cpm_status(s.ctx) == 0
+    q0 = s.q.cpu().numpy().copy()
+    g.cpm_set_wait_test(s.ctx, True)
+    s.charges()
+    assert g.cpm_status(s.ctx) == TIMEOUT
+    g.cpm_set_wait_test(s.ctx, False)
+    s.charges()
+    assert g.cpm_status(s.ctx) == 0
+    # the row vector the tiles add into is cleared by the finishing kernel of the timed-out call
+    assert np.max(np.abs(s.q.cpu().numpy() - q0)) <= 1e-5
