@@ -416,14 +416,15 @@ int cpm_set_pair_variant(cpm_ctx* ctx, int32_t variant);
 int cpm_get_pair_variant(const cpm_ctx* ctx, int32_t* variant);
 
 /*
- * cpm_autotune - time every available S-apply variant on the given single-replica input (nine
- * replays each of the whole step captured as a CUDA graph on a private stream, after a warm-up,
- * each started with a cold L2 cache, CUDA events; direct calls when the profiler is on), keep the
- * fastest (median) in the context; then, with that S-apply, the two mesh
- * convolutions (cpm_fft_variant), then the two charge assignments (cpm_mesh_variant), then the pair
- * kernels' z groups of 1, 2 and 4 cells (cpm_set_pair_group), then the four pair-kernel variant
- * masks (cpm_pair_variant), keeping the faster each time.  Each timed call is a whole cpm_step
- * with forces on all sites, electrolyte and electrode (scratch force and energy outputs).  choice_host[3] (may be NULL) receives the kept
+ * cpm_autotune - choose the kernel variants on the given single-replica input, in stages: every
+ * available S-apply variant, then with that S-apply the two mesh convolutions (cpm_fft_variant),
+ * then the two charge assignments (cpm_mesh_variant), then the pair kernels' z groups of 1, 2 and
+ * 4 cells (cpm_set_pair_group), then the four pair-kernel variant masks (cpm_pair_variant).  A
+ * stage captures the whole step of each candidate (the current choice among them) as a CUDA graph
+ * on a private stream and replays them interleaved for 15 rounds after a warm-up round, each
+ * replay started with a cold L2 cache and timed with CUDA events (direct calls when the profiler
+ * is on); the smallest median wins.  Each timed call is a whole cpm_step with forces on all
+ * sites, electrolyte and electrode (scratch force and energy outputs).  choice_host[3] (may be NULL) receives the kept
  * (cpm_sapply_variant, cpm_fft_variant, cpm_mesh_variant); cpm_get_pair_group and
  * cpm_get_pair_variant report the rest.
  * Allocates and frees a scratch buffer of twice the L2 size, scratch outputs, a stream and the

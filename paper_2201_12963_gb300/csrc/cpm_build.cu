@@ -1004,14 +1004,21 @@ static int build_ee_list(cpm_ctx* c, const std::vector<double4_32a>& pos, const 
     };
     std::unordered_map<Key, int, KeyHash> seen;
     std::vector<float4> tab;
-    // rows padded to a multiple of 4 entries (the zero table entry, j = 0), so that the kernel
-    // reads them as aligned 16-byte chunks
+    // Rows padded to a multiple of 4 entries (the zero table entry, j = 0), so that the kernel
+    // reads them as aligned 16-byte chunks: with `lpr` lanes per row, lane l takes chunks
+    // l, l + lpr, l + 2 lpr, ...  Within a row the entries are sorted by j and placed so that the
+    // lanes of one load instruction (the same chunk slot and the same entry of the chunk) hold
+    // consecutive j: their charge gathers then fall on few cache sectors.
+    int nsm = 0;
+    CPM_CUDA(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->dev));
+    const int lpr = ((long long)ne * c->p.max_replicas * 8 < (long long)std::max(1, nsm) * 24 * 32) ? 32 : 8;
     std::vector<int> ptr4(ne + 1, 0);
-    std::vector<unsigned> idx;
+    std::vector<unsigned> idx, rowv, slot;
     idx.reserve(ent.size() + 3 * (size_t)ne);
     const unsigned kPad = 0xFFFFFFFFu;         // placeholder until the zero entry's index is known
     bool fits = true;
     for (int i = 0; i < ne && fits; ++i) {
+      rowv.clear();
       for (int k = ptr[i]; k < ptr[i + 1]; ++k) {
         Key key;
         std::memcpy(&key.x, &ent[k].x, 4);
@@ -1032,9 +1039,22 @@ static int build_ee_list(cpm_ctx* c, const std::vector<double4_32a>& pos, const 
         }
         int j;
         std::memcpy(&j, &ent[k].w, sizeof(int));
-        idx.push_back((unsigned)j | ((unsigned)t << 16));
+        rowv.push_back((unsigned)j | ((unsigned)t << 16));
       }
-      while (idx.size() % 4) idx.push_back(kPad);
+      std::stable_sort(rowv.begin(), rowv.end(),
+                       [](unsigned a, unsigned b) { return (a & 0xffffu) < (b & 0xffffu); });
+      while (rowv.size() % 4) rowv.push_back(kPad);
+      const int nch = (int)rowv.size() / 4;
+      slot.clear();                            // positions in the order the kernel's loads visit them
+      for (int mm = 0; mm * lpr < nch; ++mm)
+        for (int h = 0; h < 4; ++h)
+          for (int l = 0; l < lpr; ++l) {
+            const int ch = l + lpr * mm;
+            if (ch < nch) slot.push_back((unsigned)(4 * ch + h));
+          }
+      const size_t base = idx.size();
+      idx.resize(base + rowv.size());
+      for (size_t r = 0; r < rowv.size(); ++r) idx[base + slot[r]] = rowv[r];
       ptr4[i + 1] = (int)idx.size();
     }
     if (fits && idx.size() <= (size_t)INT32_MAX - 4096) {
@@ -1047,6 +1067,7 @@ static int build_ee_list(cpm_ctx* c, const std::vector<double4_32a>& pos, const 
       CPM_TRY(upload(&c->ee_idx, idx, st));
       CPM_TRY(upload(&c->ee_tab, tab, st));
       c->ee_ntab = (int)tab.size();
+      c->ee_lpr = lpr;
       return CPM_OK;
     }
   }

@@ -137,6 +137,7 @@ struct cpm_ctx {
   unsigned* ee_idx = nullptr;
   float4* ee_tab = nullptr;
   int ee_ntab = 0;
+  int ee_lpr = 8;               // lanes per row of k_ee_forces_tab, fixed by the entry order of the build
   long long ee_nnz = 0;
   int n_sm = 0;                 // streaming multiprocessors of the device (persistent grids)
   // mesh convolution variant (enum cpm_fft_variant) and the tables of this library's own

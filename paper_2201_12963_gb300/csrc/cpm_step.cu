@@ -39,7 +39,15 @@ struct CellGeom {
   double box[3];
   double inv_box[3];
   double rc2;
+  // float32 copies for the float32 pair kernels (no float64 conversion in the kernels: each costs
+  // a float64-pipe instruction per warp on GB300)
+  float alpha_f, rc2_f, edge_f[3];
 };
+
+// the field of the working precision: the float32 copy for float, the float64 value for double
+template <typename T> __host__ __device__ __forceinline__ T prec_pick(double d, float f);
+template <> __host__ __device__ __forceinline__ double prec_pick<double>(double d, float) { return d; }
+template <> __host__ __device__ __forceinline__ float prec_pick<float>(double, float f) { return f; }
 
 
 
@@ -284,6 +292,7 @@ struct PairSrc {
   int q_stride;
   double beta;              // second screening width: 0 = point source, else Gaussian kernel
   int slot;                 // energy slot receiving sum_t c_t phi_t, or -1
+  float beta_f;             // float32 copy of beta (set by launch_pair)
 };
 
 struct CellPairTgt {
@@ -304,6 +313,7 @@ constexpr int PC_MAXT = 64;        // targets per pass of a block
 constexpr int kPairSrcCap = 1024;  // sources staged per pass (dynamic shared memory)
 constexpr int PC_MAXSTEN = kMaxStencil;
 constexpr int PC_THREADS = 256;
+constexpr int PC_WARPS = PC_THREADS / 32;
 
 // Lennard-Jones of an MD run, fused into the electrolyte-target force pass (LJ = true): the same
 // staged sources and pair list within r_c serve both interactions.  Lorentz-Berthelot mixing,
@@ -343,7 +353,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   __shared__ int st_first[PC_MAXSTEN];
   __shared__ int st_pre[PC_MAXSTEN + 1];
   __shared__ T st_sh[3][PC_MAXSTEN];                // image / neighbour-cell shift of each stencil cell
-  __shared__ int wq[PC_THREADS / 32][64];       // per-warp ring of staged sources within r_c
+  __shared__ int wq[PC_WARPS][64];              // per-warp ring of staged sources within r_c
+  // per warp: the later part of a target whose first sweeps another warp owns (target or -1;
+  // potential sum and error, force, Lennard-Jones force and energy)
+  __shared__ int xs_tag[PC_WARPS];
+  __shared__ T xs_v[PC_WARPS][9];
 
   const int rep = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -356,11 +370,13 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   const int* tst = t.start + rep * t.start_stride;
   const int t0 = tst[cell], t1 = tst[cell + gzb];
   if (t1 <= t0) return;                                    // whole block: empty cells
+  if (tid < PC_WARPS) xs_tag[tid] = -1;                    // read only after the staging barriers
   const int wz = gzb + 2 * g.sten[2];                      // stencil extent in z for this group
   const int nsten = g.w[0] * g.w[1] * wz;
-  const T alpha = (T)alpha_d;
-  const T rc2 = (T)g.rc2;
-  const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
+  const T alpha = prec_pick<T>(alpha_d, g.alpha_f);
+  const T rc2 = prec_pick<T>(g.rc2, g.rc2_f);
+  const T e0 = prec_pick<T>(g.edge[0], g.edge_f[0]), e1 = prec_pick<T>(g.edge[1], g.edge_f[1]),
+          e2 = prec_pick<T>(g.edge[2], g.edge_f[2]);
   const V4* tl = (const V4*)t.loc + rep * t.loc_stride;
   const int* tso = t.sorted + rep * t.loc_stride;
   const T* tq = t.qT ? (const T*)t.qT + (size_t)rep * t.n_fixed : nullptr;
@@ -380,7 +396,6 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
 
   for (int tb = t0; tb < t1; tb += PC_MAXT) {
     const int nt = min(PC_MAXT, t1 - tb);
-    const int P = max(1, (PC_THREADS / 32) / nt);          // parts per target: items nt * P <= PC_MAXT
     for (int k = tid; k < nt; k += PC_THREADS) {
       V4 p = tl[tb + k];
       if (tq) p.w = tq[tso[tb + k]];
@@ -396,7 +411,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         tlj[k] = par;
       }
     }
-    for (int k = tid; k < nt * P; k += PC_THREADS) {
+    for (int k = tid; k < nt; k += PC_THREADS) {
       ipot[0][k][0] = ipot[0][k][1] = ipot[1][k][0] = ipot[1][k][1] = T(0);
       ifrc[0][k] = ifrc[1][k] = ifrc[2][k] = T(0);
       if (LJ) ilj[0][k] = ilj[1][k] = ilj[2][k] = ilj[3][k] = T(0);
@@ -411,10 +426,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       const T* sq = s_q ? (const T*)s_q + (size_t)rep * (set ? s1.q_stride : s0.q_stride) : nullptr;
       const int* s_sorted = set ? s1.sorted : s0.sorted;
       const int* s_sorted_r = s_sorted + rep * (set ? s1.loc_stride : s0.loc_stride);
-      const double s_beta = set ? s1.beta : s0.beta;
+      const T beta = set ? prec_pick<T>(s1.beta, s1.beta_f) : prec_pick<T>(s0.beta, s0.beta_f);
       const T ljw = set ? T(1) : T(0.5);      // electrolyte-electrolyte LJ pairs are seen from both ends
-      const bool gauss = s_beta > 0.0;
-      const T beta = (T)s_beta;
+      const bool gauss = beta > T(0);
+      // the potential sum of this set is wanted for an energy slot or (set 0) the potential output
+      const bool need_pot = (set ? s1.slot : s0.slot) >= 0 || (set == 0 && t.phi_out != nullptr);
       __syncthreads();
       // ---- stencil cells whose box can hold a source within r_c of some point of this cell
       const float inv_w0 = 1.0f / (float)g.w[0], inv_w1 = 1.0f / (float)g.w[1];
@@ -486,14 +502,24 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           }
         }
         __syncthreads();
-        // ---- compute: work item = (target, part); a warp sweeps 1/P of the staged sources for
-        // one target.  A cheap distance filter compacts the sources within r_c into a per-warp ring
-        // (ballot + prefix), and the screened kernels run on 32 queued pairs at a time, so every lane
-        // of the expensive part does useful work.  Per-lane running sums (compensated for the
-        // potential) are reduced once per item.
+        // ---- compute: the work of the batch, nt targets x nch sweeps of 32 staged sources, is
+        // split into equal contiguous ranges of (target, sweep) units, one per warp, so that every
+        // warp reaches the barrier after the same work.  A warp takes the targets of its range in
+        // turn; only its first target can start mid-way (the warp holding a target's first sweep
+        // owns the target's slot, a later part goes to the warp's extra slot, added after the
+        // barrier).  A cheap distance filter compacts the sources within r_c into a per-warp ring
+        // (ballot + prefix), and the screened kernels run on 32 queued pairs at a time, so every
+        // lane of the expensive part does useful work.  Per-lane running sums (compensated for the
+        // potential) are reduced once per target and warp.
         int* ring = wq[warp];
-        for (int item = warp; item < nt * P; item += PC_THREADS / 32) {
-          const int ti = item / P, part = item - ti * P;
+        const int nch = (ns + 31) >> 5;
+        const int units = nt * nch;
+        const int u_end = ((warp + 1) * units) / PC_WARPS;
+        for (int u = (warp * units) / PC_WARPS; u < u_end;) {
+          const int ti = u / nch;
+          const int kc0 = u - ti * nch, kc1 = min(nch, kc0 + (u_end - u));
+          u += kc1 - kc0;
+          const bool owner = kc0 == 0;
           const V4 tp = tpos[ti];
           Acc<T> pot;
           T fx = 0, fy = 0, fz = 0;
@@ -509,7 +535,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
               const T r2 = dx * dx + dy * dy + dz * dz;
               T pr, fr = T(0);
               PairMath<T>::template eval<FORCE>(r2, alpha, beta, gauss, pr, fr);
-              pot.add(sp.w * pr);
+              if (need_pot) pot.add(sp.w * pr);
               if (FORCE) {
                 fr *= sp.w;
                 fx += fr * dx;
@@ -539,7 +565,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
             cnt -= n;
             __syncwarp();
           };
-          for (int kb = part * 32; kb < ns; kb += 32 * P) {
+          for (int kb = kc0 * 32; kb < kc1 * 32; kb += 32) {
             const int k = kb + lane;
             bool hit = false;
             if (k < ns) {
@@ -566,27 +592,62 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
             ly = warp_sum_t(ly);
             lz = warp_sum_t(lz);
             lu = warp_sum_t(lu);
-            if (lane == 0) {
-              ilj[0][item] += lx;
-              ilj[1][item] += ly;
-              ilj[2][item] += lz;
-              ilj[3][item] += lu;
-            }
           }
-          if (lane == 0) {                       // the item's slot belongs to this warp alone
-            T* a = ipot[set][item];
+          if (lane == 0 && owner) {              // the target's slot belongs to its owner warp alone
+            T* a = ipot[set][ti];
             const T t = a[0] + pot.s;
             const T bp = t - a[0];
             a[1] += ((a[0] - (t - bp)) + (pot.s - bp)) + pot.c;
             a[0] = t;
             if (FORCE) {
-              ifrc[0][item] += fx;
-              ifrc[1][item] += fy;
-              ifrc[2][item] += fz;
+              ifrc[0][ti] += fx;
+              ifrc[1][ti] += fy;
+              ifrc[2][ti] += fz;
             }
+            if (LJ) {
+              ilj[0][ti] += lx;
+              ilj[1][ti] += ly;
+              ilj[2][ti] += lz;
+              ilj[3][ti] += lu;
+            }
+          } else if (lane == 0) {                // a later part: the warp's extra slot
+            xs_tag[warp] = ti;
+            T* x = xs_v[warp];
+            x[0] = pot.s;
+            x[1] = pot.c;
+            x[2] = fx;
+            x[3] = fy;
+            x[4] = fz;
+            x[5] = lx;
+            x[6] = ly;
+            x[7] = lz;
+            x[8] = lu;
           }
         }
         __syncthreads();
+        // the warps' extra slots into the owners' slots (one thread: a target may have several)
+        if (tid == 0) {
+          for (int w = 0; w < PC_WARPS; ++w) {
+            const int ti = xs_tag[w];
+            if (ti < 0) continue;
+            xs_tag[w] = -1;
+            const T* x = xs_v[w];
+            T* a = ipot[set][ti];
+            const T t = a[0] + x[0];
+            const T bp = t - a[0];
+            a[1] += ((a[0] - (t - bp)) + (x[0] - bp)) + x[1];
+            a[0] = t;
+            ifrc[0][ti] += x[2];
+            ifrc[1][ti] += x[3];
+            ifrc[2][ti] += x[4];
+            if (LJ) {
+              ilj[0][ti] += x[5];
+              ilj[1][ti] += x[6];
+              ilj[2][ti] += x[7];
+              ilj[3][ti] += x[8];
+            }
+          }
+        }
       }
     }
     __syncthreads();
@@ -596,19 +657,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       const int orig = tso[tb + k];
       const double qt = (double)tpos[k].w;
       Acc<T> p0, p1;
-      T fx = 0, fy = 0, fz = 0;
-      for (int part = 0; part < P; ++part) {
-        const int item = k * P + part;
-        p0.add(ipot[0][item][0]);
-        p0.c += ipot[0][item][1];
-        p1.add(ipot[1][item][0]);
-        p1.c += ipot[1][item][1];
-        if (FORCE) {
-          fx += ifrc[0][item];
-          fy += ifrc[1][item];
-          fz += ifrc[2][item];
-        }
-      }
+      p0.s = ipot[0][k][0];
+      p0.c = ipot[0][k][1];
+      p1.s = ipot[1][k][0];
+      p1.c = ipot[1][k][1];
+      const T fx = FORCE ? ifrc[0][k] : T(0), fy = FORCE ? ifrc[1][k] : T(0), fz = FORCE ? ifrc[2][k] : T(0);
       if (t.phi_out) t.phi_out[(size_t)rep * t.n_fixed + orig] = p0.value();
       if (FORCE && t.field) {
         double* fo = t.field + 3 * ((size_t)rep * t.n_fixed + orig);
@@ -625,14 +678,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       }
       double ljf[3] = {0.0, 0.0, 0.0};
       if (LJ) {
-        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
-        for (int part = 0; part < P; ++part) {
-          const int item = k * P + part;
-          a0 += ilj[0][item];
-          a1 += ilj[1][item];
-          a2 += ilj[2][item];
-          a3 += ilj[3][item];
-        }
+        const T a0 = ilj[0][k], a1 = ilj[1][k], a2 = ilj[2][k], a3 = ilj[3][k];
         ljf[0] = (double)a0;
         ljf[1] = (double)a1;
         ljf[2] = (double)a2;
@@ -902,9 +948,10 @@ __global__ void __launch_bounds__(PW_THREADS) k_pair_warp(const CellPairTgt t, c
   const int* tso = t.sorted + rep * t.loc_stride;
   const T* tq = t.qT ? (const T*)t.qT + (size_t)rep * t.n_fixed : nullptr;
   const bool want_energy = s0.slot >= 0 || s1.slot >= 0;
-  const T alpha = (T)alpha_d;
-  const T rc2 = (T)g.rc2;
-  const T e0 = (T)g.edge[0], e1 = (T)g.edge[1], e2 = (T)g.edge[2];
+  const T alpha = prec_pick<T>(alpha_d, g.alpha_f);
+  const T rc2 = prec_pick<T>(g.rc2, g.rc2_f);
+  const T e0 = prec_pick<T>(g.edge[0], g.edge_f[0]), e1 = prec_pick<T>(g.edge[1], g.edge_f[1]),
+          e2 = prec_pick<T>(g.edge[2], g.edge_f[2]);
   const int lj_o = LJ ? lj.off[rep] : 0;
   const T ljc = (T)lj.cut, ljc2 = ljc * ljc, ljic = LJ ? T(1) / ljc : T(0);
   Acc<T> ea0, ea1;                                                      // lane 0 of each warp
@@ -940,9 +987,8 @@ __global__ void __launch_bounds__(PW_THREADS) k_pair_warp(const CellPairTgt t, c
       const T* sq = s_q ? (const T*)s_q + (size_t)rep * (set ? s1.q_stride : s0.q_stride) : nullptr;
       const int* s_sorted = set ? s1.sorted : s0.sorted;
       const int* s_sorted_r = s_sorted + rep * s_ls;
-      const double s_beta = set ? s1.beta : s0.beta;
-      const bool gauss = s_beta > 0.0;
-      const T beta = (T)s_beta;
+      const T beta = set ? prec_pick<T>(s1.beta, s1.beta_f) : prec_pick<T>(s0.beta, s0.beta_f);
+      const bool gauss = beta > T(0);
       const T ljw = set ? T(1) : T(0.5);
       // ---- stencil cells within r_c of the target point, and their source counts
       int run = 0;
@@ -2104,6 +2150,9 @@ static CellGeom cell_geom(const cpm_ctx* c) {
     g.inv_box[d] = 1.0 / c->ebox[d];
   }
   g.rc2 = c->p.rcut * c->p.rcut;
+  g.alpha_f = (float)c->p.alpha;
+  g.rc2_f = (float)g.rc2;
+  for (int d = 0; d < 3; ++d) g.edge_f[d] = (float)g.edge[d];
   g.gz = c->pair_gz;
   g.ngz = (g.nc[2] + g.gz - 1) / g.gz;
   return g;
@@ -2270,8 +2319,11 @@ static int sapply_stream(cpm_ctx* c, const float* S, int rows, int ld, const flo
 // elec_targets: the electrode-target kernels (real-space b, electrode forces) rather than the
 // electrolyte-target ones; each kind follows its bit of the variant mask.
 template <typename T, bool FORCE, bool LJ>
-static int launch_pair(cpm_ctx* c, bool elec_targets, const CellPairTgt& tg, const PairSrc& a, const PairSrc& e,
+static int launch_pair(cpm_ctx* c, bool elec_targets, const CellPairTgt& tg, const PairSrc& a_in, const PairSrc& e_in,
                        const CellGeom& g, int nrep, int max_targets, const PairLj& lj, cudaStream_t s) {
+  PairSrc a = a_in, e = e_in;
+  a.beta_f = (float)a.beta;
+  e.beta_f = (float)e.beta;
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   const int bit = elec_targets ? CPM_PAIR_WARP_ELEC : CPM_PAIR_WARP_ELYT;
@@ -2516,9 +2568,9 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     const bool ee_field = ee_list && elec_field;
     auto launch_ee = [&](cudaStream_t s_ee, double* dst, int mulq) -> int {
       if (c->ee_idx) {
-        // 8 lanes per row when the rows fill the resident warps, else 32; row groups of 4 or 1 rows
-        // per warp pass (a multiple of the rows one pass takes)
-        const bool wide = (long long)ne * nrep * 8 < (long long)c->n_sm * 24 * 32;
+        // 8 lanes per row when the rows fill the resident warps, else 32 (chosen at build, which
+        // orders the entries for it); row groups of 4 or 1 rows per warp pass
+        const bool wide = c->ee_lpr == 32;
         const int rpp = wide ? 1 : 4;
         const int grp = std::max(rpp, (elec_group(c, ne, nrep) + rpp - 1) / rpp * rpp);
         const int blocks = std::max(1, std::min((ne + 8 * grp - 1) / (8 * grp), c->n_sm * 8));
@@ -2561,7 +2613,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       PairSrc e = src_elec;
       e.qT = qT;
       e.beta = c->p.eta;
-      e.slot = S_E_LE;
+      e.slot = closed_form ? -1 : S_E_LE;         // the closed-form energy does not use it
       if (f_elyt && c->lj) {
         // Lennard-Jones of a running MD loop, fused: the same staged sources and pair list
         PairLj lj;
@@ -2927,93 +2979,119 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   CPM_CUDA(cudaMalloc(&f_scr, sizeof(double) * 3 * (size_t)c->p.max_elyt + 64));
   CPM_CUDA(cudaMalloc(&fe_scr, sizeof(double) * 3 * (size_t)c->ne + 64));
   CPM_CUDA(cudaMalloc(&e_scr, sizeof(double) * cpm::NENERGY));
-  // Median of nine timed steps (charges, forces, energy) after a warm-up; false if unavailable.
-  // The step is timed as the replay of a CUDA graph captured on a private stream, as it runs in an
-  // MD loop (direct calls would add the host's launch work); without graphs (profiler on), direct.
+  // Each stage times its candidates, the current choice among them, as replays of CUDA graphs of
+  // the whole step (charges, forces, energy) captured on a private stream, as the step runs in an
+  // MD loop; without graphs (profiler on), direct calls.  The candidates' replays are interleaved
+  // round by round, so that a drift of the clocks during the tuning biases none of them; each
+  // candidate's median decides.
   cudaStream_t cs = nullptr;
   CPM_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   const bool use_graph = c->prof_cap == 0;
-  auto time_config = [&](int sv, int fv, int mv, float* med) -> bool {
-    if (cpm_set_sapply_variant(c, sv) != CPM_OK || cpm_set_fft_variant(c, fv) != CPM_OK ||
-        cpm_set_mesh_variant(c, mv) != CPM_OK)
+  struct Cfg {
+    int sv, fv, mv, gz, pv;
+  };
+  auto apply = [&](const Cfg& k) -> bool {
+    if (cpm_set_sapply_variant(c, k.sv) != CPM_OK || cpm_set_fft_variant(c, k.fv) != CPM_OK ||
+        cpm_set_mesh_variant(c, k.mv) != CPM_OK || !pair_group_ok(c, k.gz))
       return false;
-    rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, st);
-    if (rc == CPM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CPM_ERR_CUDA;
-    cudaGraph_t gr = nullptr;
-    cudaGraphExec_t ge = nullptr;
-    if (rc == CPM_OK && use_graph) {
-      if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        rc = CPM_ERR_CUDA;
-      } else {
-        const int r2 = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, cs);
-        const cudaError_t ec = cudaStreamEndCapture(cs, &gr);
-        if (r2 != CPM_OK) rc = r2;
-        else if (ec != cudaSuccess || cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) rc = CPM_ERR_CUDA;
-      }
-    }
-    constexpr int NT = 9;
-    float ms[NT];
-    cudaStream_t ts = use_graph ? cs : st;
-    for (int k = 0; k < NT + 1 && rc == CPM_OK; ++k) {
-      cudaMemsetAsync(flush, k, flush_bytes, ts);
-      cudaEventRecord(e0, ts);
-      if (use_graph) {
-        if (cudaGraphLaunch(ge, ts) != cudaSuccess) rc = CPM_ERR_CUDA;
-      } else {
-        rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, ts);
-      }
-      cudaEventRecord(e1, ts);
-      if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
-      else if (k > 0) cudaEventElapsedTime(&ms[k - 1], e0, e1);     // the first replay warms up
-    }
-    if (ge) cudaGraphExecDestroy(ge);
-    if (gr) cudaGraphDestroy(gr);
-    if (rc != CPM_OK) return false;
-    std::sort(ms, ms + NT);
-    *med = ms[NT / 2];
+    c->pair_gz = k.gz;
+    c->pair_variant = k.pv;
     return true;
   };
-  // the S-apply kernel first, then the transform, then the charge assignment, each with the
-  // choices made so far
-  int best_s = keep_s, best_f = CPM_FFT_LIBRARY, best_m = CPM_MESH_SITES;
-  float best_ms = 0.f, t = 0.f;
-  for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16, CPM_SAPPLY_SYM, CPM_SAPPLY_SYM_TMA}) {
-    if (time_config(sv, CPM_FFT_LIBRARY, CPM_MESH_SITES, &t) && (best_ms == 0.f || t < best_ms)) {
-      best_ms = t;
-      best_s = sv;
+  constexpr int ROUNDS = 15;
+  auto choose = [&](const std::vector<Cfg>& cand, Cfg* best) {
+    std::vector<Cfg> ok;
+    std::vector<cudaGraph_t> gr;
+    std::vector<cudaGraphExec_t> ge;
+    for (const Cfg& k : cand) {
+      if (rc != CPM_OK) break;
+      if (!apply(k)) continue;
+      rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, st);
+      if (rc == CPM_OK && cudaStreamSynchronize(st) != cudaSuccess) rc = CPM_ERR_CUDA;
+      if (rc != CPM_OK) break;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t x = nullptr;
+      if (use_graph) {
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+          rc = CPM_ERR_CUDA;
+          break;
+        }
+        const int r2 = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, cs);
+        const cudaError_t ec = cudaStreamEndCapture(cs, &g);
+        if (r2 != CPM_OK) rc = r2;
+        else if (ec != cudaSuccess || cudaGraphInstantiate(&x, g, 0) != cudaSuccess) rc = CPM_ERR_CUDA;
+        if (rc != CPM_OK) {
+          if (g) cudaGraphDestroy(g);
+          break;
+        }
+      }
+      ok.push_back(k);
+      gr.push_back(g);
+      ge.push_back(x);
     }
-    if (rc != CPM_OK) break;
-  }
-  if (rc == CPM_OK && time_config(best_s, CPM_FFT_OWN, CPM_MESH_SITES, &t) && t < best_ms) {
-    best_ms = t;
-    best_f = CPM_FFT_OWN;
-  }
-  if (rc == CPM_OK && time_config(best_s, best_f, CPM_MESH_BRICK, &t) && t < best_ms) {
-    best_ms = t;
-    best_m = CPM_MESH_BRICK;
-  }
-  // then the z group of the real-space pair kernels
-  int best_g = keep_g;
-  for (int gz : {1, 2, 4}) {
-    if (rc != CPM_OK || gz == keep_g || !pair_group_ok(c, gz)) continue;
-    c->pair_gz = gz;
-    if (time_config(best_s, best_f, best_m, &t) && t < best_ms) {
-      best_ms = t;
-      best_g = gz;
+    std::vector<std::vector<float>> ms(ok.size());
+    cudaStream_t ts = use_graph ? cs : st;
+    for (int r = 0; r < ROUNDS + 1 && rc == CPM_OK; ++r) {      // round 0 warms up
+      for (size_t i = 0; i < ok.size() && rc == CPM_OK; ++i) {
+        if (!use_graph) apply(ok[i]);
+        cudaMemsetAsync(flush, r, flush_bytes, ts);
+        cudaEventRecord(e0, ts);
+        if (use_graph) {
+          if (cudaGraphLaunch(ge[i], ts) != cudaSuccess) rc = CPM_ERR_CUDA;
+        } else {
+          rc = cpm_step(c, 1, off, xyzq, dpsi, q, nullptr, f_scr, fe_scr, e_scr, ts);
+        }
+        cudaEventRecord(e1, ts);
+        float t = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = CPM_ERR_CUDA;
+        else if (r > 0 && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms[i].push_back(t);
+      }
     }
-  }
-  c->pair_gz = (rc == CPM_OK) ? best_g : keep_g;
-  // and the warp-per-target pair kernels against the cell blocks, per target kind
-  int best_p = keep_p;
-  for (int pv : {CPM_PAIR_CELL, CPM_PAIR_WARP_ELEC, CPM_PAIR_WARP_ELYT, CPM_PAIR_WARP}) {
-    if (rc != CPM_OK || pv == keep_p) continue;
-    c->pair_variant = pv;
-    if (time_config(best_s, best_f, best_m, &t) && t < best_ms) {
-      best_ms = t;
-      best_p = pv;
+    for (size_t i = 0; i < ok.size(); ++i) {
+      if (ge[i]) cudaGraphExecDestroy(ge[i]);
+      if (gr[i]) cudaGraphDestroy(gr[i]);
     }
+    float best_t = 0.f;
+    for (size_t i = 0; i < ok.size() && rc == CPM_OK; ++i) {
+      if (ms[i].empty()) continue;
+      std::sort(ms[i].begin(), ms[i].end());
+      const float med = ms[i][ms[i].size() / 2];
+      if (best_t == 0.f || med < best_t) {
+        best_t = med;
+        *best = ok[i];
+      }
+    }
+  };
+  // the S-apply kernel first, then the transform, then the charge assignment, then the z group
+  // of the real-space pair kernels and the pair-kernel form, each stage with the choices so far
+  Cfg best{keep_s, CPM_FFT_LIBRARY, CPM_MESH_SITES, keep_g, keep_p};
+  {
+    std::vector<Cfg> cand;
+    for (int sv : {CPM_SAPPLY_ROWS, CPM_SAPPLY_STREAM, CPM_SAPPLY_STREAM16, CPM_SAPPLY_SYM, CPM_SAPPLY_SYM_TMA})
+      cand.push_back({sv, best.fv, best.mv, best.gz, best.pv});
+    choose(cand, &best);
   }
-  c->pair_variant = (rc == CPM_OK) ? best_p : keep_p;
+  if (rc == CPM_OK) choose({best, {best.sv, CPM_FFT_OWN, best.mv, best.gz, best.pv}}, &best);
+  if (rc == CPM_OK) choose({best, {best.sv, best.fv, CPM_MESH_BRICK, best.gz, best.pv}}, &best);
+  if (rc == CPM_OK) {
+    std::vector<Cfg> cand{best};
+    for (int gz : {1, 2, 4})
+      if (gz != best.gz) cand.push_back({best.sv, best.fv, best.mv, gz, best.pv});
+    choose(cand, &best);
+  }
+  if (rc == CPM_OK) {
+    std::vector<Cfg> cand{best};
+    for (int pv : {CPM_PAIR_CELL, CPM_PAIR_WARP_ELEC, CPM_PAIR_WARP_ELYT, CPM_PAIR_WARP})
+      if (pv != best.pv) cand.push_back({best.sv, best.fv, best.mv, best.gz, pv});
+    choose(cand, &best);
+  }
+  if (rc != CPM_OK || !apply(best)) {
+    c->pair_gz = keep_g;
+    c->pair_variant = keep_p;
+    c->sapply_variant = keep_s;
+    c->fft_variant = keep_f;
+    c->mesh_variant = keep_m;
+  }
   cudaFree(f_scr);
   cudaFree(fe_scr);
   cudaFree(e_scr);
@@ -3021,9 +3099,6 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   cudaEventDestroy(e1);
   cudaStreamDestroy(cs);
   cudaFree(flush);
-  c->sapply_variant = (rc == CPM_OK) ? best_s : keep_s;
-  c->fft_variant = (rc == CPM_OK) ? best_f : keep_f;
-  c->mesh_variant = (rc == CPM_OK) ? best_m : keep_m;
   if (choice_host) {
     choice_host[0] = c->sapply_variant;
     choice_host[1] = c->fft_variant;
