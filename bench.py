@@ -245,8 +245,15 @@ TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tf32 / bf16 tensor rate of GB300
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels, keyed by workload
 # and "phase:kernel variant" (the autotuner may pick another S-apply kernel, whose traffic was not
 # captured: then traffic is null).  Set an entry to None whenever its kernel changes.
-NCU_TRAFFIC_MIXED = {"paper": {}, "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {},
-                     "paper-dc-md": {}, "large": {}, "dc-large": {}, "batched": {}}
+# dc-large s_apply: the two packed applies (823.83 + 823.89 MB) and the two finishes (0.99 MB each);
+# the fold before them reads b from L2.  profiles/dram_dc-large-and-paper-cell-mixed.md.
+NCU_TRAFFIC_MIXED = {"paper": {"s_apply:sym": 19_894_000, "s_apply:sym-tma": 19_894_000, "f_pair_elyt": 214_000,
+                               "f_pair_elec": 6_720_000},
+                     "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {},
+                     "paper-dc-md": {}, "large": {},
+                     "dc-large": {"s_apply:sym-tma": 1_649_700_000, "f_pair_elyt": 5_580_000,
+                                  "f_pair_elec": 51_420_000},
+                     "batched": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
                         "f_pair_elec", "energy")
 
@@ -377,7 +384,11 @@ def roofline(workload_kind, s, w, phase_ms, clk):
         roof["dominant_phase_overall"] = max(phase_ms, key=phase_ms.get)
     roof_s = roof_for("s_apply") if "s_apply" in phase_ms else None
     roof_pair = roof_for("f_pair_elyt") if "f_pair_elyt" in phase_ms else None
-    return roof, roof_s, roof_pair
+    # the electrode pair list (HBM model), where the step uses it
+    roof_ee = None
+    if "f_pair_elec" in phase_ms and (phase_model("f_pair_elec", s, w, pairs) or ("",))[0] == "hbm":
+        roof_ee = roof_for("f_pair_elec")
+    return roof, roof_s, roof_pair, roof_ee
 
 
 # ----------------------------------------------------------------------------------------------
@@ -546,7 +557,7 @@ def run_gb300(args):
 
     e2e_value, h2d, d2h = end_to_end(s, w, graph, dev, min(K, 50), world, True)
     phase_ms = profile_phases(s, flush, min(K, 50), True)
-    roof, roof_s, roof_pair = roofline(args.workload, s, w, phase_ms, clk)
+    roof, roof_s, roof_pair, roof_ee = roofline(args.workload, s, w, phase_ms, clk)
     geo = GEOMETRY_NAME[args.workload]
     out = {"metric": METRIC, "value": round(value, 2), "unit": "ns/day", "n_gpus": world, "steps": K,
            "warmup": max(3, args.warmup), "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
@@ -577,7 +588,8 @@ def run_gb300(args):
                                 "unit": "ns/day", "steps": Kf,
                                 "note": "the same step without electrode forces (forces on electrolyte sites only)"},
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
-           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair}
+           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair,
+           "roofline_pair_list": roof_ee}
     del graph
     if rank == 0 and world == 1 and not args.no_extras:
         extras(args, w, s, mixed_res, dev, flush, out)
@@ -747,7 +759,7 @@ def paper_cell(args, dev, flush, tmp):
     tot_fe, _, _ = time_replays(graph_fe, flush, K, dev, 3)
     del graph_fe
     phase_ms = profile_phases(s, flush, min(K, 50), True)
-    roof, roof_s, roof_pair = roofline("paper", s, w, phase_ms, clk)
+    roof, roof_s, roof_pair, roof_ee = roofline("paper", s, w, phase_ms, clk)
     ms = tot / K
     obj = {"workload": WORKLOADS["paper"][0], "precision": a2.precision, "ms_per_step": round(ms, 5),
            "value": round(1e3 / ms * NS_PER_DAY_PER_STEP_PER_S, 2), "unit": "ns/day", "steps": K, "status": st,
@@ -755,7 +767,8 @@ def paper_cell(args, dev, flush, tmp):
            "kernels": {"s_apply": sv, "transform": fv, "assignment": mv, "pair": g.cpm_get_pair_variant(s.ctx),
                        "pair_group_z": g.cpm_get_pair_group(s.ctx)},
            "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()},
-           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair, "clocks": clk}
+           "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair,
+           "roofline_pair_list": roof_ee, "clocks": clk}
     del graph
     try:
         obj["plain_fp64"], fp64_res = plain_fp64(a2, w, s, dev, flush)
@@ -1161,7 +1174,7 @@ def run_md(args):
     g.cpm_profile_enable(s.ctx, 0)
     g.cpm_status(s.ctx)
     phase_ms = {kk: v[0] / max(1, v[1]) for kk, v in prof.items() if v[1] > 0}
-    roof, roof_s, roof_pair = roofline(args.workload, s, w, phase_ms, clk)
+    roof, roof_s, roof_pair, roof_ee = roofline(args.workload, s, w, phase_ms, clk)
 
     out = {"metric": METRIC, "value": round(value, 2), "unit": "ns/day", "n_gpus": world, "steps": K,
            "warmup": warm, "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,

@@ -353,7 +353,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   __shared__ int st_first[PC_MAXSTEN];
   __shared__ int st_pre[PC_MAXSTEN + 1];
   __shared__ T st_sh[3][PC_MAXSTEN];                // image / neighbour-cell shift of each stencil cell
-  __shared__ int wq[PC_WARPS][64];              // per-warp ring of staged sources within r_c
+  __shared__ int wq[PC_WARPS][128];             // per-warp ring of staged sources within r_c
   // per warp: the later part of a target whose first sweeps another warp owns (target or -1;
   // potential sum and error, force, Lennard-Jones force and energy)
   __shared__ int xs_tag[PC_WARPS];
@@ -526,10 +526,10 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           T lx = 0, ly = 0, lz = 0, lu = 0;      // Lennard-Jones force and energy (LJ only)
           V2 tpar;
           if (LJ) tpar = tlj[ti];
-          int head = 0, cnt = 0;                 // queued entries: ring[(head .. head + cnt) mod 64]
+          int head = 0, cnt = 0;                 // queued entries: ring[(head .. head + cnt) mod 128]
           auto consume = [&](int n) {
             if (lane < n) {
-              const int idx = ring[(head + lane) & 63];
+              const int idx = ring[(head + lane) & 127];
               const V4 sp = src[idx];
               const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
               const T r2 = dx * dx + dy * dy + dz * dz;
@@ -561,23 +561,36 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
                 }
               }
             }
-            head = (head + n) & 63;
+            head = (head + n) & 127;
             cnt -= n;
             __syncwarp();
           };
-          for (int kb = kc0 * 32; kb < kc1 * 32; kb += 32) {
-            const int k = kb + lane;
-            bool hit = false;
-            if (k < ns) {
-              const V4 sp = src[k];
+          // two candidates per lane per step (64 staged sources), one ballot each: the ring's
+          // bookkeeping is shared by both; at most 31 + 64 entries are queued before consuming
+          const int kend = min(ns, kc1 * 32);
+          const unsigned lt = (1u << lane) - 1u;
+          for (int kb = kc0 * 32; kb < kend; kb += 64) {
+            const int k1 = kb + lane, k2 = kb + 32 + lane;
+            bool h1 = false, h2 = false;
+            if (k1 < kend) {
+              const V4 sp = src[k1];
               const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
               const T r2 = dx * dx + dy * dy + dz * dz;
-              hit = r2 < rc2 && r2 > T(0);
+              h1 = r2 < rc2 && r2 > T(0);
             }
-            const unsigned bal = __ballot_sync(FULL, hit);
-            if (hit) ring[(head + cnt + __popc(bal & ((1u << lane) - 1u))) & 63] = k;
-            cnt += __popc(bal);
+            if (k2 < kend) {
+              const V4 sp = src[k2];
+              const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
+              const T r2 = dx * dx + dy * dy + dz * dz;
+              h2 = r2 < rc2 && r2 > T(0);
+            }
+            const unsigned b1 = __ballot_sync(FULL, h1), b2 = __ballot_sync(FULL, h2);
+            const int n1 = __popc(b1);
+            if (h1) ring[(head + cnt + __popc(b1 & lt)) & 127] = k1;
+            if (h2) ring[(head + cnt + n1 + __popc(b2 & lt)) & 127] = k2;
+            cnt += n1 + __popc(b2);
             __syncwarp();
+            if (cnt >= 32) consume(32);
             if (cnt >= 32) consume(32);
           }
           if (cnt > 0) consume(cnt);
