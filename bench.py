@@ -63,7 +63,8 @@ def parse(argv=None):
     ap.add_argument("--kernels", default="auto",
                     help="auto (cpm_autotune picks) or 'S-apply,transform,assignment' names, e.g. "
                          "sym,library,sites, to run a fixed kernel choice (profiling captures)")
-    ap.add_argument("--pair-variant", default="auto", choices=["auto", "cell", "warp-elec", "warp-elyt", "warp"],
+    ap.add_argument("--pair-variant", default="auto",
+                    choices=["auto", "cell", "warp-elec", "warp-elyt", "warp", "n3", "n3-warp-elec"],
                     help="real-space pair kernels: one block per cell, or one warp per target for electrode "
                          "targets, electrolyte targets or both (default: autotuned)")
     ap.add_argument("--pair-group", type=int, default=0,
@@ -247,11 +248,11 @@ TF32_OVER_BF16 = 1.1 / 2.25   # nominal dense tf32 / bf16 tensor rate of GB300
 # captured: then traffic is null).  Set an entry to None whenever its kernel changes.
 # dc-large s_apply: the two packed applies (823.83 + 823.89 MB) and the two finishes (0.99 MB each);
 # the fold before them reads b from L2.  profiles/dram_dc-large-and-paper-cell-mixed.md.
-NCU_TRAFFIC_MIXED = {"paper": {"s_apply:sym": 19_894_000, "s_apply:sym-tma": 19_894_000, "f_pair_elyt": 214_000,
+NCU_TRAFFIC_MIXED = {"paper": {"s_apply:sym": 19_894_000, "s_apply:sym-tma": 19_894_000, "f_pair_elyt:cell": 214_000,
                                "f_pair_elec": 6_720_000},
                      "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {},
                      "paper-dc-md": {}, "large": {},
-                     "dc-large": {"s_apply:sym-tma": 1_649_700_000, "f_pair_elyt": 5_580_000,
+                     "dc-large": {"s_apply:sym-tma": 1_649_700_000, "f_pair_elyt:cell": 5_580_000,
                                   "f_pair_elec": 51_420_000},
                      "batched": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
@@ -360,6 +361,8 @@ def roofline(workload_kind, s, w, phase_ms, clk):
     pairs = pair_counts(w)
     mixed_prec = s.params.precision == 1
     sapply_variant = s.sapply_variant
+    import paper_2201_12963_gb300 as g
+    pair_variant = g.cpm_get_pair_variant(s.ctx)
 
     def roof_for(p):
         bound, amount, unit, desc = phase_model(p, s, w, pairs)
@@ -371,7 +374,8 @@ def roofline(workload_kind, s, w, phase_ms, clk):
         else:
             achieved, peak = amount / sec / 1e12, alu_peak_tflops(clk.get("sm_mhz"))
             src = "derived: 152 SMs x 128 FP32 lanes x 2 x median SM clock under load"
-        key = f"{p}:{sapply_variant}" if p == "s_apply" else p
+        key = (f"{p}:{sapply_variant}" if p == "s_apply" else
+               f"{p}:{pair_variant}" if p in ("f_pair_elyt", "b_real") else p)
         traffic = NCU_TRAFFIC_MIXED.get(workload_kind, {}).get(key) if mixed_prec else None
         return {"bound": bound, "kernel": p, "achieved": round(achieved, 3), "peak": round(peak, 1), "unit": unit,
                 "frac": round(achieved / peak, 4), "traffic": traffic, "algorithmic_per_launch": amount,

@@ -410,8 +410,15 @@ int cpm_set_wait_test(cpm_ctx* ctx, int32_t on);
  * Both compact the sources within r_c into a per-warp queue before the screened kernels, and give the
  * same results up to the order of the sums.  The variant is a mask of the target kinds that use the
  * warp form: electrode targets (real-space b, electrode forces) and electrolyte targets (electrolyte
- * forces, with the MD loop's Lennard-Jones).  Default CPM_PAIR_CELL; cpm_autotune times all four. */
-enum cpm_pair_variant { CPM_PAIR_CELL = 0, CPM_PAIR_WARP_ELEC = 1, CPM_PAIR_WARP_ELYT = 2, CPM_PAIR_WARP = 3 };
+ * forces, with the MD loop's Lennard-Jones).  CPM_PAIR_N3_ELYT (combinable with CPM_PAIR_WARP_ELEC, not
+ * with CPM_PAIR_WARP_ELYT): the electrolyte forces of the mixed path by a cell kernel that applies
+ * Newton's third law to the electrolyte-electrolyte pairs (one block per cell, the half stencil,
+ * each pair evaluated once, the reaction added to the source with float32 atomics into a
+ * cell-sorted force buffer); used where the cell kernel would be, outside an MD loop with
+ * Lennard-Jones and with the site charge assignment; the same forces to float32 rounding.
+ * Default CPM_PAIR_CELL; cpm_autotune times all six. */
+enum cpm_pair_variant { CPM_PAIR_CELL = 0, CPM_PAIR_WARP_ELEC = 1, CPM_PAIR_WARP_ELYT = 2, CPM_PAIR_WARP = 3,
+                        CPM_PAIR_N3_ELYT = 4 };
 int cpm_set_pair_variant(cpm_ctx* ctx, int32_t variant);
 int cpm_get_pair_variant(const cpm_ctx* ctx, int32_t* variant);
 

@@ -387,7 +387,7 @@ def cpm_get_pair_group(ctx: Context) -> int:
     return int(v.value)
 
 
-PAIR_VARIANTS = {"cell": 0, "warp-elec": 1, "warp-elyt": 2, "warp": 3}   # enum cpm_pair_variant
+PAIR_VARIANTS = {"cell": 0, "warp-elec": 1, "warp-elyt": 2, "warp": 3, "n3": 4, "n3-warp-elec": 5}   # enum cpm_pair_variant
 
 
 def cpm_set_pair_variant(ctx: Context, variant):

@@ -205,6 +205,7 @@ struct cpm_ctx {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double* f_pair = nullptr;     // [max_rep][max_elyt][3] real-space electrolyte forces (original order)
+  float* f_sorted32 = nullptr;  // [max_rep][max_elyt][3] the same from the third-law kernel (sorted order)
   const cpm::LjSetup* lj = nullptr;  // Lennard-Jones of a running MD loop (added into f_pair), or none
   // libraries
   cublasHandle_t cublas = nullptr;

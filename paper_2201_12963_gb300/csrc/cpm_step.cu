@@ -307,6 +307,7 @@ struct CellPairTgt {
   double* phi_out;          // sum over set 0 of c_s kernel(r), [rep][n_fixed] original order, or nullptr
   double* field;            // FORCE: = KE sum_s c_s g(r) d over both sets, the force per unit target charge,
                             // at [rep * n_fixed + original index][3] (written, not added), or nullptr
+  float* force_sorted;      // N3 kernels: forces added with float32 atomics at [rep * n_fixed + sorted index][3]
 };
 
 constexpr int PC_MAXT = 64;        // targets per pass of a block
@@ -331,14 +332,26 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
-template <typename T, bool FORCE, bool LJ = false>
-__global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
+// N3 (electrolyte targets, float32, forces): Newton's third law for the point-point pairs of set 0,
+// whose targets and sources are the same sites.  Set 0 is staged from the half stencil: the
+// neighbour cells at a lexicographically positive offset (x, then y, then z) from the group's
+// origin cell, which include the group's own cells; there a pair is taken once (source after
+// target in the sorted order), so each unordered pair and each periodic image pair is evaluated
+// once.  The source's
+// reaction is added into a shared-memory accumulator of the staged source; after each batch the
+// accumulators, and at the end the targets' own sums, are added with float32 atomics into
+// t.force_sorted, indexed by sorted position (neighbouring sites, so the atomics of a block fall in
+// few cache lines; float32 also keeps the conversions off GB300's narrow float64 pipe).  Set 1 (electrode sources) is as in the plain kernel.  The set-0 energy counts
+// each pair twice, as the ordered sum of the plain kernel does.
+template <typename T, bool FORCE, bool LJ = false, bool N3 = false>
+__global__ void __launch_bounds__(PC_THREADS, N3 ? 4 : 0) k_pair_cell(const CellPairTgt t, const PairSrc s0, const PairSrc s1,
                                                           const CellGeom g, const double alpha_d, int src_cap,
                                                           double* __restrict__ scal, const PairLj lj) {
   pdl_enter();
   using V4 = typename Vec4<T>::type;
   using V2 = typename Vec2<T>::type;
   static_assert(!LJ || FORCE, "the Lennard-Jones pass computes forces");
+  static_assert(!N3 || (FORCE && !LJ), "the third-law pass computes Coulomb forces");
   extern __shared__ __align__(32) unsigned char pc_dyn[];
   V4* src = reinterpret_cast<V4*>(pc_dyn);
   V2* src_lj = reinterpret_cast<V2*>(src + src_cap);          // LJ: (sigma / 2, sqrt eps) per staged source
@@ -358,6 +371,13 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
   // potential sum and error, force, Lennard-Jones force and energy)
   __shared__ int xs_tag[PC_WARPS];
   __shared__ T xs_v[PC_WARPS][9];
+  // N3: reaction accumulator and sorted index of each staged source of set 0; its ordering key
+  // (the sorted index for sources in the group's own cells, -1 for every other staged source), and
+  // per stencil cell whether it is one of the group's own cells
+  __shared__ float n3_f[N3 ? 3 * kPairSrcCap : 1];
+  __shared__ int n3_gi[N3 ? kPairSrcCap : 1];
+  __shared__ int n3_key[N3 ? kPairSrcCap : 1];
+  __shared__ unsigned char n3_own[N3 ? PC_MAXSTEN : 1];
 
   const int rep = blockIdx.y;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -445,7 +465,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         const int gapz = dz < 0 ? -dz - 1 : max(0, dz - gzb);
         const T gx = (T)max(0, abs(dx) - 1) * e0, gy = (T)max(0, abs(dy) - 1) * e1, gz = (T)gapz * e2;
         int c = 0, f = 0;
-        if (gx * gx + gy * gy + gz * gz < rc2) {
+        // N3, set 0: the target cell and the neighbours at a lexicographically positive offset
+        const bool half_ok = !N3 || set != 0 || dx > 0 || (dx == 0 && (dy > 0 || (dy == 0 && dz >= 0)));
+        if (half_ok && gx * gx + gy * gy + gz * gz < rc2) {
           const int flat = (wrap_index(cx + dx, g.nc[0]) * g.nc[1] + wrap_index(cy + dy, g.nc[1])) * g.nc[2] +
                            wrap_index(cz + dz, g.nc[2]);
           f = sst[flat];
@@ -453,6 +475,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         }
         st_first[si] = f;
         st_pre[si + 1] = c;                 // counts, scanned below
+        if (N3) n3_own[si] = (dx == 0 && dy == 0 && dz >= 0 && dz < gzb) ? 1 : 0;
         st_sh[0][si] = (T)dx * e0;
         st_sh[1][si] = (T)dy * e1;
         st_sh[2][si] = (T)dz * e2;
@@ -476,6 +499,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       }
       __syncthreads();
       const int total = st_pre[nsten];
+      const bool n3s = N3 && set == 0;
       for (int c0 = 0; c0 < total; c0 += src_cap) {
         const int ns = min(src_cap, total - c0);
         // ---- stage: k -> stencil entry by binary search over the prefix sums
@@ -493,6 +517,11 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           p.z += st_sh[2][lo];
           if (sq) p.w = sq[s_sorted[gi]];
           src[k] = p;
+          if (N3 && n3s) {
+            n3_gi[k] = gi;
+            n3_key[k] = n3_own[lo] ? gi : -1;
+            n3_f[3 * k + 0] = n3_f[3 * k + 1] = n3_f[3 * k + 2] = 0.f;
+          }
           if (LJ) {
             const int ty = set ? lj.elec_type : min(kLjMaxTypes - 1, max(0, lj.type[lj_o + s_sorted_r[gi]]));
             V2 par;
@@ -541,6 +570,12 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
                 fx += fr * dx;
                 fy += fr * dy;
                 fz += fr * dz;
+                if (N3 && n3s) {                 // the source's reaction, c_t c_s g(r) (-d)
+                  const float rq = -(float)(tp.w * fr);
+                  atomicAdd(&n3_f[3 * idx + 0], rq * (float)dx);
+                  atomicAdd(&n3_f[3 * idx + 1], rq * (float)dy);
+                  atomicAdd(&n3_f[3 * idx + 2], rq * (float)dz);
+                }
               }
               if (LJ) {
                 const V2 spar = src_lj[idx];
@@ -569,6 +604,9 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
           // bookkeeping is shared by both; at most 31 + 64 entries are queued before consuming
           const int kend = min(ns, kc1 * 32);
           const unsigned lt = (1u << lane) - 1u;
+          // N3, set 0: in the group's own cells only sources after the target in the sorted order
+          // (the group's cells are the half stencil's lowest cells of its own column)
+          const int tgi = tb + ti;
           for (int kb = kc0 * 32; kb < kend; kb += 64) {
             const int k1 = kb + lane, k2 = kb + 32 + lane;
             bool h1 = false, h2 = false;
@@ -577,12 +615,20 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
               const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
               const T r2 = dx * dx + dy * dy + dz * dz;
               h1 = r2 < rc2 && r2 > T(0);
+              if (N3 && n3s) {
+                const int key = n3_key[k1];
+                h1 = h1 && (key < 0 || key > tgi);
+              }
             }
             if (k2 < kend) {
               const V4 sp = src[k2];
               const T dx = tp.x - sp.x, dy = tp.y - sp.y, dz = tp.z - sp.z;
               const T r2 = dx * dx + dy * dy + dz * dz;
               h2 = r2 < rc2 && r2 > T(0);
+              if (N3 && n3s) {
+                const int key = n3_key[k2];
+                h2 = h2 && (key < 0 || key > tgi);
+              }
             }
             const unsigned b1 = __ballot_sync(FULL, h1), b2 = __ballot_sync(FULL, h2);
             const int n1 = __popc(b1);
@@ -661,6 +707,21 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
             }
           }
         }
+        // N3: the staged sources' reactions of this batch (the same thread per staged slot as in
+        // the staging loop, so the next batch's staging needs no extra barrier)
+        if (N3 && n3s) {
+          float* fs = t.force_sorted + 3 * (size_t)rep * t.n_fixed;
+          const float ke = (float)KE;
+          for (int k = tid; k < ns; k += PC_THREADS) {
+            const float ax = n3_f[3 * k + 0], ay = n3_f[3 * k + 1], az = n3_f[3 * k + 2];
+            if (ax != 0.f || ay != 0.f || az != 0.f) {
+              float* o = fs + 3 * (size_t)n3_gi[k];
+              atomicAdd(o + 0, ke * ax);
+              atomicAdd(o + 1, ke * ay);
+              atomicAdd(o + 2, ke * az);
+            }
+          }
+        }
       }
     }
     __syncthreads();
@@ -684,10 +745,18 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
       }
       if (want_energy) {
         const T ct = tpos[k].w;
-        ea0.add(ct * p0.s);
-        ea0.c += ct * p0.c;
+        const T c0 = N3 ? T(2) * ct : ct;     // N3: set 0 saw each pair once; the slot wants both ends
+        ea0.add(c0 * p0.s);
+        ea0.c += c0 * p0.c;
         ea1.add(ct * p1.s);
         ea1.c += ct * p1.c;
+      }
+      if (N3) {                              // the target's own sums, beside the reactions it receives
+        float* o = t.force_sorted + 3 * ((size_t)rep * t.n_fixed + tb + k);
+        const float f = (float)KE * (float)tpos[k].w;
+        atomicAdd(o + 0, f * (float)fx);
+        atomicAdd(o + 1, f * (float)fy);
+        atomicAdd(o + 2, f * (float)fz);
       }
       double ljf[3] = {0.0, 0.0, 0.0};
       if (LJ) {
@@ -697,7 +766,7 @@ __global__ void __launch_bounds__(PC_THREADS) k_pair_cell(const CellPairTgt t, c
         ljf[2] = (double)a2;
         elj += (double)a3;
       }
-      if (FORCE && t.force) {
+      if (FORCE && !N3 && t.force) {
         const size_t gi = (size_t)rep * t.n_fixed + orig;
         const double f = KE * qt;
         t.force[3 * gi + 0] += f * (double)fx + ljf[0];
@@ -1400,7 +1469,8 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
                                                        const T* __restrict__ splF, const double* __restrict__ dpsi,
                                                        double ff_over_lz, double slab_coef,
                                                        const double* __restrict__ scal,
-                                                       const double* __restrict__ f_pair, double* __restrict__ F,
+                                                       const double* __restrict__ f_pair,
+                                                       const float* __restrict__ f_sorted, double* __restrict__ F,
                                                        const int* __restrict__ srt) {
   pdl_enter();
   __shared__ T sw[8][kSiteBatch][3][PMAX], sdw[8][kSiteBatch][3][PMAX];
@@ -1467,7 +1537,19 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
       const int i = srt ? srt[(size_t)rep * cap + i0 + lane] : i0 + lane;      // input index
       const double q = (double)sq[wib][lane];
       const size_t gi = 3 * (size_t)(o + i);
-      const double* fp = f_pair + 3 * ((size_t)rep * cap + i);
+      // the real-space force, by input index, or by sorted index (f_sorted, srt given)
+      double fp[3];
+      if (f_sorted) {
+        const float* fs = f_sorted + 3 * ((size_t)rep * cap + i0 + lane);
+        fp[0] = (double)fs[0];
+        fp[1] = (double)fs[1];
+        fp[2] = (double)fs[2];
+      } else {
+        const double* fd = f_pair + 3 * ((size_t)rep * cap + i);
+        fp[0] = fd[0];
+        fp[1] = fd[1];
+        fp[2] = fd[2];
+      }
       F[gi + 0] = -q * (double)kx * sg.kl[0] + fp[0];
       F[gi + 1] = -q * (double)ky * sg.kl[1] + fp[1];
       F[gi + 2] = -q * (double)kz * sg.kl[2] + q * ezf + fp[2];
@@ -2355,6 +2437,21 @@ static int launch_pair(cpm_ctx* c, bool elec_targets, const CellPairTgt& tg, con
   return CPM_OK;
 }
 
+// The third-law cell kernel for electrolyte targets (float32): one block per target-cell group.
+static int launch_pair_n3(cpm_ctx* c, const CellPairTgt& tg, const PairSrc& a_in, const PairSrc& e_in,
+                          const CellGeom& g_in, int nrep, cudaStream_t s) {
+  PairSrc a = a_in, e = e_in;
+  a.beta_f = (float)a.beta;
+  e.beta_f = (float)e.beta;
+  const CellGeom& g = g_in;
+  const size_t smem = sizeof(float4) * kPairSrcCap;
+  CPM_CUDA(launch_pdl(k_pair_cell<float, true, false, true>, dim3(pair_blocks(g), nrep), PC_THREADS, smem, s, tg,
+                      a, e, g, c->p.alpha, kPairSrcCap, c->scal, PairLj{}));
+  ++c->launches;
+  CPM_LAUNCH();
+  return CPM_OK;
+}
+
 template <typename T>
 static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const double* dpsi, bool charges,
                double* q, double* b_out, double* psibar, double* f_elyt, double* f_elec, double* energy,
@@ -2566,6 +2663,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
 
   if (f_elyt || f_elec || energy) {
     cudaStream_t sp = sside;
+    // electrolyte forces by the third-law cell kernel (CPM_PAIR_N3_ELYT; mixed precision, not in an
+    // MD loop with Lennard-Jones, site charge assignment): into the float32 sorted-order buffer
+    const bool n3 = f_elyt != nullptr && c->lj == nullptr && c->mixed && (c->pair_variant & CPM_PAIR_N3_ELYT) &&
+                    !(c->pair_variant & CPM_PAIR_WARP_ELYT) && !brick && c->f_sorted32 != nullptr;
     if (!charges) {                      // charges given by the caller (cpm_forces, cpm_energy)
       PhaseTimer pt(c, st, CPM_PH_F_SPREAD);
       CPM_CUDA(launch_pdl(k_charge_prep<T>, dim3((ne + 255) / 256, nrep), 256, 0, st, q, ne, c->e_z, c->e_v, c->e_plus, qT, c->scal));
@@ -2618,9 +2719,10 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     }
     {
       PhaseTimer pt(c, st, CPM_PH_F_PAIR_ELYT);
-      if (f_elyt) CPM_CUDA(cudaMemsetAsync(c->f_pair, 0, sizeof(double) * 3 * (size_t)cap * nrep, sp));
+      if (f_elyt && !n3) CPM_CUDA(cudaMemsetAsync(c->f_pair, 0, sizeof(double) * 3 * (size_t)cap * nrep, sp));
+      if (n3) CPM_CUDA(cudaMemsetAsync(c->f_sorted32, 0, sizeof(float) * 3 * (size_t)cap * nrep, sp));
       CellPairTgt tg{l_loc, (long long)cap, c->l_start, (long long)c->ncell + 1, c->l_sorted, cap, nullptr,
-                     f_elyt ? c->f_pair : nullptr, nullptr};
+                     (f_elyt && !n3) ? c->f_pair : nullptr, nullptr, nullptr, n3 ? c->f_sorted32 : nullptr};
       PairSrc a = src_elyt;
       a.slot = S_E_LL;
       PairSrc e = src_elec;
@@ -2639,6 +2741,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
           lj.sqrt_eps[k] = c->lj->sqrt_eps[k];
         }
         CPM_TRY((launch_pair<T, true, true>(c, false, tg, a, e, g, nrep, cap, lj, sp)));
+      } else if (n3) {
+        CPM_TRY(launch_pair_n3(c, tg, a, e, g, nrep, sp));
       } else if (f_elyt) {
         CPM_TRY((launch_pair<T, true, false>(c, false, tg, a, e, g, nrep, cap, PairLj{}, sp)));
       } else {
@@ -2687,7 +2791,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
       // cell-sorted order (the sort has joined the main stream in the b pass, or just above)
       CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for((cap + sb - 1) / sb), nrep), 256, 0, st, sb,
                           (const T*)c->mesh_phi, off, cap, sg, (const V4*)l_loc, c->l_cell, c->spl_I, splF, dpsi,
-                          ff_over_lz, slab_coef, c->scal, c->f_pair, f_elyt, (const int*)c->l_sorted));
+                          ff_over_lz, slab_coef, c->scal, c->f_pair, n3 ? (const float*)c->f_sorted32 : nullptr,
+                          f_elyt, (const int*)c->l_sorted));
       STEP_LAUNCH();
     }
     ptg.stop();
@@ -2760,6 +2865,8 @@ static int pair_cell_attributes() {
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d64));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
+  CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<float, true, false, true>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, d32));
   const int l64 = (int)((sizeof(double4_32a) + sizeof(double2)) * cpm::kPairSrcCap);
   const int l32 = (int)((sizeof(float4) + sizeof(float2)) * cpm::kPairSrcCap);
   CPM_CUDA(cudaFuncSetAttribute(cpm::k_pair_cell<double, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2856,6 +2963,7 @@ int cpm_internal_alloc_step_buffers(cpm_ctx* c) {
     CPM_CUDA(cudaMalloc(&c->qpm, sizeof(double) * R * 2 * c->nh));
   }
   CPM_CUDA(cudaMalloc(&c->f_pair, sizeof(double) * R * cap * 3));
+  CPM_CUDA(cudaMalloc(&c->f_sorted32, sizeof(float) * R * cap * 3));
   CPM_CUDA(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
   CPM_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
@@ -2936,7 +3044,8 @@ extern "C" int cpm_get_pair_group(const cpm_ctx* c, int32_t* gz) {
 }
 
 extern "C" int cpm_set_pair_variant(cpm_ctx* c, int32_t variant) {
-  if (!c || variant < CPM_PAIR_CELL || variant > CPM_PAIR_WARP) {
+  if (!c || variant < CPM_PAIR_CELL || variant > (CPM_PAIR_N3_ELYT | CPM_PAIR_WARP_ELEC) ||
+      ((variant & CPM_PAIR_N3_ELYT) && (variant & CPM_PAIR_WARP_ELYT))) {
     cpm::set_error("cpm_set_pair_variant: unknown variant %d", variant);
     return CPM_ERR_ARG;
   }
@@ -3094,7 +3203,8 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   }
   if (rc == CPM_OK) {
     std::vector<Cfg> cand{best};
-    for (int pv : {CPM_PAIR_CELL, CPM_PAIR_WARP_ELEC, CPM_PAIR_WARP_ELYT, CPM_PAIR_WARP})
+    for (int pv : {(int)CPM_PAIR_CELL, (int)CPM_PAIR_WARP_ELEC, (int)CPM_PAIR_WARP_ELYT, (int)CPM_PAIR_WARP,
+                   (int)CPM_PAIR_N3_ELYT, (int)CPM_PAIR_N3_ELYT | (int)CPM_PAIR_WARP_ELEC})
       if (pv != best.pv) cand.push_back({best.sv, best.fv, best.mv, best.gz, pv});
     choose(cand, &best);
   }

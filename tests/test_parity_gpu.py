@@ -289,3 +289,51 @@ def test_electrode_forces_from_the_precomputed_pair_list(plain_ff, case):
         assert _rms_rel(ra["F_elyt"][r], rb["F_elyt"][r]) <= 1e-6
     if out is not None:
         assert _rms_rel(ra["F_elec"][0], out["F_elec"]) <= 3e-5
+
+
+@pytest.mark.parametrize("case", ["plain", "dc", "batched", "large"])
+def test_third_law_pair_kernel_matches_the_cell_kernel(plain_ff, case):
+    """CPM_PAIR_N3_ELYT: the electrolyte-electrolyte pairs taken once (half stencil, each periodic
+    image pair once: the 17 x 17 A plain cell spans fewer cells than the stencil, so every
+    neighbour cell appears at several images), the reaction added to the source.  Forces and
+    energies must equal the cell kernel's to float32 rounding, and the forces the oracle's."""
+    g, System = _lib()
+    out = None
+    if case == "plain":
+        w, _, out = plain_ff
+    elif case == "dc":
+        w = synth.mirror_to_doubled(synth.tiny_cell(seed=4, n_pairs=4), "independent", seed=40)
+        w.grid = (18, 16, 144)
+        out = ocpm.Reference(w).step()
+    elif case == "batched":
+        w = synth.config_batched(n_rep=3)
+    else:
+        w = synth.config_large_ff()
+    s = System(w, "mixed", order=8) if case != "large" else System(w, "mixed", matrix_kspace="mesh")
+    res = {}
+    for v, gz in (("cell", 1), ("n3", 1), ("n3-warp-elec", 1), ("n3", 2)):
+        g.cpm_set_pair_variant(s.ctx, v)
+        assert g.cpm_get_pair_variant(s.ctx) == v
+        g.cpm_set_pair_group(s.ctx, gz)                  # z groups of cells: the ordering rule
+        s.step(elec=True, energy=True)
+        res[(v, gz)] = s.results()
+        assert g.cpm_status(s.ctx) == 0
+    ra = res[("cell", 1)]
+    for v in (("n3", 1), ("n3-warp-elec", 1), ("n3", 2)):
+        rb = res[v]
+        for r in range(w.n_rep):
+            assert np.max(np.abs(rb["q"][r] - ra["q"][r])) <= 1e-6
+            assert _rms_rel(rb["F_elyt"][r], ra["F_elyt"][r]) <= 2e-6
+            assert _rms_rel(rb["F_elec"][r], ra["F_elec"][r]) <= 2e-6
+            # the pair energies are float32 terms summed in another order: on the dense batched
+            # electrolyte (sites 1.5 A apart, terms of several eV) their rounding reaches 1e-6 of H
+            etol = 1e-5 if case == "batched" else 1e-6
+            if case != "batched":
+                # per site: a pair within r_c taken twice or missed would move two sites by
+                # ~2e-5 eV/A (the pair force at r_c), above float32 rounding of the sums
+                assert np.max(np.abs(rb["F_elyt"][r] - ra["F_elyt"][r])) <= 5e-6
+            assert abs(rb["energy"][r, 1] - ra["energy"][r, 1]) <= etol * abs(ra["energy"][r, 1])
+        if out is not None:
+            assert _rms_rel(rb["F_elyt"][0], out["F_elyt"]) <= 3e-5
+    with pytest.raises(g.CPMError):
+        g.cpm_set_pair_variant(s.ctx, 6)                 # third law with warp-per-target electrolyte
