@@ -425,8 +425,8 @@ int cpm_get_pair_variant(const cpm_ctx* ctx, int32_t* variant);
 /*
  * cpm_autotune - choose the kernel variants on the given single-replica input, in stages: every
  * available S-apply variant, then with that S-apply the two mesh convolutions (cpm_fft_variant),
- * then the two charge assignments (cpm_mesh_variant), then the pair kernels' z groups of 1, 2 and
- * 4 cells (cpm_set_pair_group), then the four pair-kernel variant masks (cpm_pair_variant).  A
+ * then the two charge assignments (cpm_mesh_variant), then the pair-kernel variants
+ * (cpm_pair_variant) together with their z groups of 1, 2 and 4 cells (cpm_set_pair_group).  A
  * stage captures the whole step of each candidate (the current choice among them) as a CUDA graph
  * on a private stream and replays them interleaved for 15 rounds after a warm-up round, each
  * replay started with a cold L2 cache and timed with CUDA events (direct calls when the profiler

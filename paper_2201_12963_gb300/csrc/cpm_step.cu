@@ -3195,17 +3195,15 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
   }
   if (rc == CPM_OK) choose({best, {best.sv, CPM_FFT_OWN, best.mv, best.gz, best.pv}}, &best);
   if (rc == CPM_OK) choose({best, {best.sv, best.fv, CPM_MESH_BRICK, best.gz, best.pv}}, &best);
-  if (rc == CPM_OK) {
-    std::vector<Cfg> cand{best};
-    for (int gz : {1, 2, 4})
-      if (gz != best.gz) cand.push_back({best.sv, best.fv, best.mv, gz, best.pv});
-    choose(cand, &best);
-  }
+  // the pair-kernel form and its z group together (the cell and third-law kernels prefer
+  // different groups)
   if (rc == CPM_OK) {
     std::vector<Cfg> cand{best};
     for (int pv : {(int)CPM_PAIR_CELL, (int)CPM_PAIR_WARP_ELEC, (int)CPM_PAIR_WARP_ELYT, (int)CPM_PAIR_WARP,
                    (int)CPM_PAIR_N3_ELYT, (int)CPM_PAIR_N3_ELYT | (int)CPM_PAIR_WARP_ELEC})
-      if (pv != best.pv) cand.push_back({best.sv, best.fv, best.mv, best.gz, pv});
+      for (int gz : {1, 2, 4})
+        if ((pv != best.pv || gz != best.gz) && pair_group_ok(c, gz))
+          cand.push_back({best.sv, best.fv, best.mv, gz, pv});
     choose(cand, &best);
   }
   if (rc != CPM_OK || !apply(best)) {
