@@ -666,7 +666,8 @@ def extras(args, w, s, mixed_res, dev, flush, out):
         acc["vs_oracle"] = res if ok else {"error": res}
     out["accuracy"] = acc
     if paper_pending is not None:
-        finish_paper_cell(out["paper_cell"], done["paper"], paper_pending[1], out.get("batched"), q_batched)
+        finish_paper_cell(out["paper_cell"], done["paper"], paper_pending[1], out.get("batched"), q_batched,
+                          paper_pending[4])
     if not args.no_cpu_baseline and args.workload not in DENSE_ORACLE:
         ok, res = finish_child(spawn_child(args, "oracle-sample", wfile, os.path.join(tmp, "cpu_all.json"),
                                            cores=os.cpu_count() or 1))
@@ -774,22 +775,26 @@ def paper_cell(args, dev, flush, tmp):
            "roofline": roof, "roofline_s_apply": roof_s, "roofline_pair_elyt": roof_pair,
            "roofline_pair_list": roof_ee, "clocks": clk}
     del graph
+    fp64_res = None
     try:
         obj["plain_fp64"], fp64_res = plain_fp64(a2, w, s, dev, flush)
         obj["accuracy"] = {"vs_plain_fp64_gpu": precision_errors(mixed_res, fp64_res)}
     except Exception as e:
         obj["plain_fp64"] = {"error": f"{type(e).__name__}: {e}"[:300]}
         obj["accuracy"] = {}
-    return obj, (None, mixed_res, a2, wfile)
+    return obj, (None, mixed_res, a2, wfile, fp64_res)
 
 
-def finish_paper_cell(obj, done, mixed_res, batched_obj, q_batched):
-    """The paper cell's oracle comparison and CPU time, and the batched replicas' accuracy."""
+def finish_paper_cell(obj, done, mixed_res, batched_obj, q_batched, fp64_res=None):
+    """The paper cell's oracle comparison (the timed mixed step, and the float64 GPU path on the
+    same mesh: the mesh's own error) and CPU time, and the batched replicas' accuracy."""
     ok, ref = done
     if not ok:
         obj["accuracy"]["vs_oracle"] = {"error": ref}
         return
     obj["accuracy"]["vs_oracle"] = accuracy_against(ref, mixed_res)
+    if fp64_res is not None:
+        obj["accuracy"]["plain_fp64_vs_oracle"] = accuracy_against(ref, fp64_res)
     obj["cpu_baseline"] = ref["cpu_baseline"]
     if batched_obj is not None and q_batched is not None and "q_batched" in ref:
         try:
