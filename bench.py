@@ -252,7 +252,7 @@ NCU_TRAFFIC_MIXED = {"paper": {"s_apply:sym": 19_894_000, "s_apply:sym-tma": 19_
                                "f_pair_elec": 6_720_000},
                      "paper-dc": {}, "paper-slab": {}, "paper-proximal": {}, "paper-md": {},
                      "paper-dc-md": {}, "large": {},
-                     "dc-large": {"s_apply:sym-tma": 1_649_700_000, "f_pair_elyt:cell": 5_580_000,
+                     "dc-large": {"s_apply:sym-tma": 1_649_700_000, "f_pair_elyt:cell": 5_580_000, "f_pair_elyt:n3": 4_340_000,
                                   "f_pair_elec": 51_420_000},
                      "batched": {}}
 SINGLE_KERNEL_PHASES = ("b_real", "b_spread", "b_gather", "s_apply", "project", "f_gather", "f_pair_elyt",
