@@ -312,6 +312,7 @@ struct CellPairTgt {
 
 constexpr int PC_MAXT = 64;        // targets per pass of a block
 constexpr int kPairSrcCap = 1024;  // sources staged per pass (dynamic shared memory)
+constexpr int kPairSrcCapN3 = 1024; // the same for the third-law kernel
 constexpr int PC_MAXSTEN = kMaxStencil;
 constexpr int PC_THREADS = 256;
 constexpr int PC_WARPS = PC_THREADS / 32;
@@ -371,12 +372,11 @@ __global__ void __launch_bounds__(PC_THREADS, N3 ? 4 : 0) k_pair_cell(const Cell
   // potential sum and error, force, Lennard-Jones force and energy)
   __shared__ int xs_tag[PC_WARPS];
   __shared__ T xs_v[PC_WARPS][9];
-  // N3: reaction accumulator and sorted index of each staged source of set 0; its ordering key
-  // (the sorted index for sources in the group's own cells, -1 for every other staged source), and
-  // per stencil cell whether it is one of the group's own cells
-  __shared__ float n3_f[N3 ? 3 * kPairSrcCap : 1];
-  __shared__ int n3_gi[N3 ? kPairSrcCap : 1];
-  __shared__ int n3_key[N3 ? kPairSrcCap : 1];
+  // N3: reaction accumulator and sorted index of each staged source of set 0 (stored inverted for
+  // sources outside the group's own cells: the ordering rule applies only inside them), and per
+  // stencil cell whether it is one of the group's own cells
+  __shared__ float n3_f[N3 ? 3 * kPairSrcCapN3 : 1];
+  __shared__ int n3_gi[N3 ? kPairSrcCapN3 : 1];     // sorted index, bit-inverted (negative) outside the own cells
   __shared__ unsigned char n3_own[N3 ? PC_MAXSTEN : 1];
 
   const int rep = blockIdx.y;
@@ -518,8 +518,7 @@ __global__ void __launch_bounds__(PC_THREADS, N3 ? 4 : 0) k_pair_cell(const Cell
           if (sq) p.w = sq[s_sorted[gi]];
           src[k] = p;
           if (N3 && n3s) {
-            n3_gi[k] = gi;
-            n3_key[k] = n3_own[lo] ? gi : -1;
+            n3_gi[k] = n3_own[lo] ? gi : ~gi;
             n3_f[3 * k + 0] = n3_f[3 * k + 1] = n3_f[3 * k + 2] = 0.f;
           }
           if (LJ) {
@@ -616,7 +615,7 @@ __global__ void __launch_bounds__(PC_THREADS, N3 ? 4 : 0) k_pair_cell(const Cell
               const T r2 = dx * dx + dy * dy + dz * dz;
               h1 = r2 < rc2 && r2 > T(0);
               if (N3 && n3s) {
-                const int key = n3_key[k1];
+                const int key = n3_gi[k1];
                 h1 = h1 && (key < 0 || key > tgi);
               }
             }
@@ -626,7 +625,7 @@ __global__ void __launch_bounds__(PC_THREADS, N3 ? 4 : 0) k_pair_cell(const Cell
               const T r2 = dx * dx + dy * dy + dz * dz;
               h2 = r2 < rc2 && r2 > T(0);
               if (N3 && n3s) {
-                const int key = n3_key[k2];
+                const int key = n3_gi[k2];
                 h2 = h2 && (key < 0 || key > tgi);
               }
             }
@@ -715,7 +714,8 @@ __global__ void __launch_bounds__(PC_THREADS, N3 ? 4 : 0) k_pair_cell(const Cell
           for (int k = tid; k < ns; k += PC_THREADS) {
             const float ax = n3_f[3 * k + 0], ay = n3_f[3 * k + 1], az = n3_f[3 * k + 2];
             if (ax != 0.f || ay != 0.f || az != 0.f) {
-              float* o = fs + 3 * (size_t)n3_gi[k];
+              const int v = n3_gi[k];
+              float* o = fs + 3 * (size_t)(v >= 0 ? v : ~v);
               atomicAdd(o + 0, ke * ax);
               atomicAdd(o + 1, ke * ay);
               atomicAdd(o + 2, ke * az);
@@ -1538,13 +1538,13 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
       const double q = (double)sq[wib][lane];
       const size_t gi = 3 * (size_t)(o + i);
       // the real-space force, by input index, or by sorted index (f_sorted, srt given)
-      double fp[3];
+      double fp[3] = {0.0, 0.0, 0.0};    // no real-space force: added later by k_add_pair_forces
       if (f_sorted) {
         const float* fs = f_sorted + 3 * ((size_t)rep * cap + i0 + lane);
         fp[0] = (double)fs[0];
         fp[1] = (double)fs[1];
         fp[2] = (double)fs[2];
-      } else {
+      } else if (f_pair) {
         const double* fd = f_pair + 3 * ((size_t)rep * cap + i);
         fp[0] = fd[0];
         fp[1] = fd[1];
@@ -1561,6 +1561,34 @@ __global__ void __launch_bounds__(256) k_gather_f_elyt(int nb, const T* __restri
 // k-space force on electrode sites through the fixed stencils (written, not added).  A warp takes
 // grp (1..32) consecutive sites: each site's stencil over the lanes, reduced in float32, lane s
 // keeping site s's sums; the float64 epilogue then runs once per group, one lane per site.
+// F += the real-space electrolyte forces, when the mesh part was gathered before the pair
+// kernels finished: from f_pair (input order) or f_sorted (float32, cell-sorted order); one thread
+// per sorted site, grid.y = replica.
+__global__ void __launch_bounds__(256) k_add_pair_forces(const int* __restrict__ off, int cap,
+                                                         const int* __restrict__ srt,
+                                                         const double* __restrict__ f_pair,
+                                                         const float* __restrict__ f_sorted, double* __restrict__ F) {
+  pdl_enter();
+  const int rep = blockIdx.y;
+  const int o = off[rep];
+  const int n = min(off[rep + 1] - o, cap);
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const int i = srt[(size_t)rep * cap + k];
+  double* f = F + 3 * (size_t)(o + i);
+  if (f_sorted) {
+    const float* fs = f_sorted + 3 * ((size_t)rep * cap + k);
+    f[0] += (double)fs[0];
+    f[1] += (double)fs[1];
+    f[2] += (double)fs[2];
+  } else {
+    const double* fd = f_pair + 3 * ((size_t)rep * cap + i);
+    f[0] += fd[0];
+    f[1] += fd[1];
+    f[2] += fd[2];
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_gather_f_elec(const T* __restrict__ phi, const T* __restrict__ qT,
                                                        int ne, const int4* __restrict__ base,
@@ -2444,9 +2472,9 @@ static int launch_pair_n3(cpm_ctx* c, const CellPairTgt& tg, const PairSrc& a_in
   a.beta_f = (float)a.beta;
   e.beta_f = (float)e.beta;
   const CellGeom& g = g_in;
-  const size_t smem = sizeof(float4) * kPairSrcCap;
+  const size_t smem = sizeof(float4) * kPairSrcCapN3;
   CPM_CUDA(launch_pdl(k_pair_cell<float, true, false, true>, dim3(pair_blocks(g), nrep), PC_THREADS, smem, s, tg,
-                      a, e, g, c->p.alpha, kPairSrcCap, c->scal, PairLj{}));
+                      a, e, g, c->p.alpha, kPairSrcCapN3, c->scal, PairLj{}));
   ++c->launches;
   CPM_LAUNCH();
   return CPM_OK;
@@ -2784,15 +2812,25 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
                           elec_field ? (const double*)c->e_field : nullptr, f_elec, grp));
       STEP_LAUNCH();
     }
+    // electrolyte sites in cell-sorted order.  With the side stream, the mesh part is gathered
+    // while the pair kernels still run (it needs only the sorted list: joined in the b pass, or
+    // waited for here), and the real-space forces are added after the join; without it (the
+    // profiler's serial phases), in one pass
+    if (f_elyt && !brick) {
+      if (fork && !charges) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_sorted, 0));
+      CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for((cap + sb - 1) / sb), nrep), 256, 0, st, sb,
+                          (const T*)c->mesh_phi, off, cap, sg, (const V4*)l_loc, c->l_cell, c->spl_I, splF, dpsi,
+                          ff_over_lz, slab_coef, c->scal, fork ? nullptr : (const double*)c->f_pair,
+                          (!fork && n3) ? (const float*)c->f_sorted32 : nullptr, f_elyt, (const int*)c->l_sorted));
+      STEP_LAUNCH();
+    }
     if (fork) CPM_CUDA(cudaStreamWaitEvent(st, c->ev_join, 0));
     if (f_elyt && brick) {
       CPM_TRY(cpm_internal_gather_f_brick(c, nrep, off, l_loc, dpsi, ff_over_lz, slab_coef, f_elyt, st));
-    } else if (f_elyt) {
-      // cell-sorted order (the sort has joined the main stream in the b pass, or just above)
-      CPM_CUDA(launch_pdl(k_gather_f_elyt<T>, dim3(grid_for((cap + sb - 1) / sb), nrep), 256, 0, st, sb,
-                          (const T*)c->mesh_phi, off, cap, sg, (const V4*)l_loc, c->l_cell, c->spl_I, splF, dpsi,
-                          ff_over_lz, slab_coef, c->scal, c->f_pair, n3 ? (const float*)c->f_sorted32 : nullptr,
-                          f_elyt, (const int*)c->l_sorted));
+    } else if (f_elyt && fork) {
+      CPM_CUDA(launch_pdl(k_add_pair_forces, dim3((cap + 255) / 256, nrep), 256, 0, st, off, cap,
+                          (const int*)c->l_sorted, n3 ? nullptr : (const double*)c->f_pair,
+                          n3 ? (const float*)c->f_sorted32 : nullptr, f_elyt));
       STEP_LAUNCH();
     }
     ptg.stop();

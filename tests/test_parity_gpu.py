@@ -329,9 +329,10 @@ def test_third_law_pair_kernel_matches_the_cell_kernel(plain_ff, case):
             # electrolyte (sites 1.5 A apart, terms of several eV) their rounding reaches 1e-6 of H
             etol = 1e-5 if case == "batched" else 1e-6
             if case != "batched":
-                # per site: a pair within r_c taken twice or missed would move two sites by
-                # ~2e-5 eV/A (the pair force at r_c), above float32 rounding of the sums
-                assert np.max(np.abs(rb["F_elyt"][r] - ra["F_elyt"][r])) <= 5e-6
+                # per site: a pair within r_c taken twice or missed would move two sites by at
+                # least the pair force at r_c, 2.7e-5 eV/A for these +-0.78 e ions (1.5e-5 in its
+                # largest component), above float32 rounding of the sums (up to 5e-6 measured)
+                assert np.max(np.abs(rb["F_elyt"][r] - ra["F_elyt"][r])) <= 1e-5
             assert abs(rb["energy"][r, 1] - ra["energy"][r, 1]) <= etol * abs(ra["energy"][r, 1])
         if out is not None:
             assert _rms_rel(rb["F_elyt"][0], out["F_elyt"]) <= 3e-5
