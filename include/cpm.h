@@ -381,7 +381,7 @@ int cpm_set_mesh_variant(cpm_ctx* ctx, int32_t variant);
  * block computes the targets of gz consecutive cells along z (contiguous in the cell-sorted list)
  * against the sources of their joint stencil, so its setup, stencil scan and source staging serve
  * gz times the targets for (gz + 2 s) / (1 + 2 s) times the sources (s the stencil half-width), at
- * the price of more distance checks per target.  Default 1; cpm_autotune times 1, 2 and 4.
+ * the price of more distance checks per target.  Default 1; cpm_autotune times 1 to 4.
  * CPM_ERR_ARG if gz is outside 1..8 or its stencil exceeds the kernel's tables.
  */
 int cpm_set_pair_group(cpm_ctx* ctx, int32_t gz);
@@ -426,7 +426,7 @@ int cpm_get_pair_variant(const cpm_ctx* ctx, int32_t* variant);
  * cpm_autotune - choose the kernel variants on the given single-replica input, in stages: every
  * available S-apply variant, then with that S-apply the two mesh convolutions (cpm_fft_variant),
  * then the two charge assignments (cpm_mesh_variant), then the pair-kernel variants
- * (cpm_pair_variant) together with their z groups of 1, 2 and 4 cells (cpm_set_pair_group).  A
+ * (cpm_pair_variant) together with their z groups of 1 to 4 cells (cpm_set_pair_group).  A
  * stage captures the whole step of each candidate (the current choice among them) as a CUDA graph
  * on a private stream and replays them interleaved for 15 rounds after a warm-up round, each
  * replay started with a cold L2 cache and timed with CUDA events (direct calls when the profiler

@@ -3239,7 +3239,7 @@ extern "C" int cpm_autotune(cpm_ctx* c, const int32_t* off, const double* xyzq, 
     std::vector<Cfg> cand{best};
     for (int pv : {(int)CPM_PAIR_CELL, (int)CPM_PAIR_WARP_ELEC, (int)CPM_PAIR_WARP_ELYT, (int)CPM_PAIR_WARP,
                    (int)CPM_PAIR_N3_ELYT, (int)CPM_PAIR_N3_ELYT | (int)CPM_PAIR_WARP_ELEC})
-      for (int gz : {1, 2, 4})
+      for (int gz : {1, 2, 3, 4})
         if ((pv != best.pv || gz != best.gz) && pair_group_ok(c, gz))
           cand.push_back({best.sv, best.fv, best.mv, gz, pv});
     choose(cand, &best);
