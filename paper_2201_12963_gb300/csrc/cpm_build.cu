@@ -1359,7 +1359,7 @@ extern "C" void cpm_destroy(cpm_ctx* c) {
                   c->l_start, c->l_sorted, c->l_loc64, c->l_loc32, c->l_tmp, c->qT, c->spl_I,
                   c->spl_F64, c->spl_F32, c->phi_real, c->b_tmp, c->b32, c->qraw32, c->f_pair,
                   c->scal, c->status, c->m_i0, c->m_j, c->e_c1m, c->ypm, c->qpm, c->qpart, c->fft_tw, c->br_pad, c->sym_S, c->ee_ptr, c->ee_g,
-                  c->ee_idx, c->ee_tab, c->e_field, c->f_sorted32};
+                  c->ee_idx, c->ee_tab, c->e_field, c->f_sorted32, c->sym_w32, c->sym_c1f};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (int b = 0; b < 2; ++b)

@@ -127,6 +127,12 @@ struct cpm_ctx {
   bool sym_ok = false;
   int sym_nt = 0;
   float* sym_S = nullptr;
+  // inputs of the projection sums the packed S-apply forms: W = A^-1 C as float32 pairs
+  // (W0 hi, W0 lo, W1 hi, W1 lo) and the c1 indicator per row of S (or of both mirror blocks),
+  // and (1^T S v, c1^T S v), which the projection multiplies by dpsi
+  float4* sym_w32 = nullptr;
+  float* sym_c1f = nullptr;
+  double sym_sv[2] = {0.0, 0.0};
   // electrode-electrode real-space force list of the frozen electrode (mixed precision): CSR rows
   // per target (original order), entries (G_x, G_y, G_z, source index as int bits); or, when the
   // G vectors take few distinct values (a lattice electrode), the compressed form: entries
@@ -519,9 +525,10 @@ int cpm_internal_convolve_own(cpm_ctx* c, int nrep, int energy_slot, cudaStream_
 cpm::SpmeGeom cpm_internal_spme_geom(const cpm_ctx* c);
 int cpm_internal_brick_setup(cpm_ctx* c);
 int cpm_internal_sym_setup(cpm_ctx* c);
+bool cpm_internal_sym_fuse(const cpm_ctx* c);
 int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* xl, const double* b,
                             const double* dpsi, const double* Sv, const double* W, const double* c1, double* qout,
-                            cudaStream_t st);
+                            cudaStream_t st, bool fuse_sums);
 int cpm_internal_spread_brick(cpm_ctx* c, int nrep, const void* l_loc, const float* qT, cudaStream_t st);
 int cpm_internal_gather_f_brick(cpm_ctx* c, int nrep, const int* off, const void* l_loc, const double* dpsi,
                                 double ff_over_lz, double slab_coef, double* F, cudaStream_t st);

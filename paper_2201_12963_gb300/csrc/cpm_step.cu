@@ -2135,16 +2135,34 @@ __device__ __forceinline__ void project_sums(double (&acc)[5], double* s) {
   block_atomic_add<5>(acc, dst);
 }
 
+// q_raw held as the packed S-apply's row accumulator (one replica): q_raw = part + dpsi S v, and
+// the projection clears part for the next call; the S-apply's sums S_CQ0, S_CQ1 leave out the
+// dpsi S v terms, dpsi (sv0, sv1) = dpsi (1^T S v, c1^T S v).  part == nullptr: q_raw is in the
+// charge array and the sums are complete.
+struct QRawPart {
+  double* part;
+  const double* Sv;
+  double sv0, sv1;
+};
+
+__device__ __forceinline__ double qraw_take(const QRawPart& qp, int i, double dpsi) {
+  const double r = qp.part[i] + dpsi * qp.Sv[i];
+  qp.part[i] = 0.0;
+  return r;
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FIN_THREADS) k_project(double* __restrict__ q, int ne, int nrep, int ncons,
                                                  const double* __restrict__ W, const double* __restrict__ b, int ldb,
                                                  double* __restrict__ scal, const double* __restrict__ dpsi,
                                                  double m00, double m01, double m10, double m11, double wtv0,
-                                                 double wtv1, double* __restrict__ psibar, ChargePrep<T> cp) {
+                                                 double wtv1, double* __restrict__ psibar, ChargePrep<T> cp,
+                                                 QRawPart qp) {
   pdl_enter();
   const int rep = blockIdx.y;
   double* s = scal + rep * NSCAL;
-  const double c0 = s[S_CQ0], cq1 = (ncons == 2) ? s[S_CQ1] : 0.0;
+  const double dq0 = qp.part ? dpsi[rep] * qp.sv0 : 0.0, dq1 = qp.part ? dpsi[rep] * qp.sv1 : 0.0;
+  const double c0 = s[S_CQ0] + dq0, cq1 = (ncons == 2) ? s[S_CQ1] + dq1 : 0.0;
   const double a0 = m00 * c0 + m01 * cq1, a1 = m10 * c0 + m11 * cq1;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
@@ -2152,7 +2170,7 @@ __global__ void __launch_bounds__(FIN_THREADS) k_project(double* __restrict__ q,
     double corr = W[2 * i] * a0;
     if (ncons == 2) corr += W[2 * i + 1] * a1;
     const size_t k = (size_t)rep * ne + i;
-    const double qi = q[k] - corr;
+    const double qi = (qp.part ? qraw_take(qp, i, dpsi[rep]) : q[k]) - corr;
     q[k] = qi;
     acc[0] = qi * b[(size_t)rep * ldb + i];
     prep_site(cp, rep, ne, i, qi, acc);
@@ -2202,18 +2220,21 @@ __global__ void __launch_bounds__(FIN_THREADS) k_project_mirror(const double* __
                                                         int ldb, int ne, double* __restrict__ scal,
                                                         const double* __restrict__ dpsi, double mp, double mm,
                                                         double wtvp, double wtvm, double* __restrict__ q,
-                                                        double* __restrict__ psibar, ChargePrep<T> cp) {
+                                                        double* __restrict__ psibar, ChargePrep<T> cp, QRawPart qp) {
   pdl_enter();
   const int rep = blockIdx.y;
   double* s = scal + rep * NSCAL;
-  const double cpl = s[S_CQ0] - s[S_CQ1], cm = s[S_CQ1];
+  const double dq0 = qp.part ? dpsi[rep] * qp.sv0 : 0.0, dq1 = qp.part ? dpsi[rep] * qp.sv1 : 0.0;
+  const double cpl = (s[S_CQ0] + dq0) - (s[S_CQ1] + dq1), cm = s[S_CQ1] + dq1;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
   if (k < nh) {
-    const double qp = qpm[(size_t)rep * 2 * nh + k] - W[2 * k] * mp * cpl;
-    const double qm = qpm[(size_t)rep * 2 * nh + nh + k] - W[2 * (size_t)nh + 2 * k + 1] * mm * cm;
+    const double rp = qp.part ? qraw_take(qp, k, dpsi[rep]) : qpm[(size_t)rep * 2 * nh + k];
+    const double rm = qp.part ? qraw_take(qp, nh + k, dpsi[rep]) : qpm[(size_t)rep * 2 * nh + nh + k];
+    const double qpl = rp - W[2 * k] * mp * cpl;
+    const double qm = rm - W[2 * (size_t)nh + 2 * k + 1] * mm * cm;
     const int i = i0[k], j = jm[k];
-    const double qi = 0.5 * (qp + qm), qj = 0.5 * (qp - qm);
+    const double qi = 0.5 * (qpl + qm), qj = 0.5 * (qpl - qm);
     q[(size_t)rep * ne + i] = qi;
     q[(size_t)rep * ne + j] = qj;
     acc[0] = qi * b[(size_t)rep * ldb + i] + qj * b[(size_t)rep * ldb + j];
@@ -2628,6 +2649,8 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
                            (c->sapply_variant == CPM_SAPPLY_STREAM || c->sapply_variant == CPM_SAPPLY_STREAM16);
     const bool sym_ok = c->mixed && nrep == 1 && c->sym_ok &&
                         (c->sapply_variant == CPM_SAPPLY_SYM || c->sapply_variant == CPM_SAPPLY_SYM_TMA);
+    // the packed S-apply forms the projection sums itself (no finish pass) when its CTAs have few tiles
+    const bool sym_fuse = sym_ok && cpm_internal_sym_fuse(c);
     {
       PhaseTimer pt(c, st, CPM_PH_S_APPLY);
       if (c->mirror) {
@@ -2641,7 +2664,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
             CPM_TRY(cpm_internal_sapply_sym(c, blk, c->b32 + (size_t)blk * ldh,
                                             c->b32 + 2 * (size_t)ldh + (size_t)blk * ldh, c->ypm + (size_t)blk * ldh,
                                             dpsi, c->Sv + (size_t)blk * nh, c->W + (size_t)blk * 2 * nh,
-                                            c->e_c1m + (size_t)blk * nh, c->qpm + (size_t)blk * nh, st));
+                                            c->e_c1m + (size_t)blk * nh, c->qpm + (size_t)blk * nh, st, sym_fuse));
             continue;
           }
           if (stream_ok) {
@@ -2658,7 +2681,7 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
                          c->qpm + (size_t)blk * nh, 2 * nh));
         }
       } else if (sym_ok) {
-        CPM_TRY(cpm_internal_sapply_sym(c, 0, c->b32, c->b32 + c->ldx, b, dpsi, c->Sv, c->W, c->e_c1, q, st));
+        CPM_TRY(cpm_internal_sapply_sym(c, 0, c->b32, c->b32 + c->ldx, b, dpsi, c->Sv, c->W, c->e_c1, q, st, sym_fuse));
       } else if (stream_ok) {
         CPM_TRY(sapply_stream(c, c->S32, ne, c->ld32, c->b32, c->b32 + c->ldx, c->qpart, b, dpsi, c->Sv, c->W, c->e_c1,
                               q, st));
@@ -2677,14 +2700,17 @@ static int run(cpm_ctx* c, int nrep, const int* off, const double* xyzq, const d
     // and their sums (the work of k_charge_prep)
     const bool forces_follow = f_elyt || f_elec || energy;
     const ChargePrep<T> cprep{forces_follow ? qT : nullptr, c->e_z, c->e_v, c->e_plus};
+    // after the packed S-apply with its own sums the projection reads its row accumulator
+    // (q_raw - dpsi S v)
+    const QRawPart qp{sym_fuse ? c->qpart : nullptr, c->Sv, c->sym_sv[0], c->sym_sv[1]};
     if (c->mirror) {
       CPM_CUDA(launch_pdl(k_project_mirror<T>, dim3((c->nh + FIN_THREADS - 1) / FIN_THREADS, nrep), FIN_THREADS, 0, st, c->qpm, c->nh, c->m_i0, c->m_j, c->W, b,
                                                                         ldb, ne, c->scal, dpsi, c->Mh[0], c->Mh[1],
-                                                                        c->WTv[0], c->WTv[1], q, psibar, cprep));
+                                                                        c->WTv[0], c->WTv[1], q, psibar, cprep, qp));
     } else {
       CPM_CUDA(launch_pdl(k_project<T>, dim3((ne + FIN_THREADS - 1) / FIN_THREADS, nrep), FIN_THREADS, 0, st, q, ne, nrep, c->ncons, c->W, b, ldb, c->scal, dpsi,
                                                               c->Mh[0], c->Mh[1], c->Mh[2], c->Mh[3], c->WTv[0],
-                                                              c->WTv[1], psibar, cprep));
+                                                              c->WTv[1], psibar, cprep, qp));
     }
     STEP_LAUNCH();
   }

@@ -38,15 +38,20 @@ def test_sapply_variants_agree_and_match_oracle(plain_ff, case):
     if out is None:
         out = ocpm.Reference(w).step(want_forces=False, want_energy=False)
     s = System(w, "mixed", order=8)
-    qs = {}
+    qs, pb = {}, {}
     for v in ("rows", "stream", "stream16", "sym", "sym-tma"):
         g.cpm_set_sapply_variant(s.ctx, v)
         for _ in range(2):                          # the second call checks the cleared partial sums
             s.charges()
         assert g.cpm_status(s.ctx) == 0
         qs[v] = s.q.cpu().numpy().copy()
+        pb[v] = s.psibar.cpu().numpy().copy()
         assert np.max(np.abs(qs[v] - out["q"])) <= 1e-5
         assert abs(qs[v].sum()) <= 1e-12
+        # the packed kernels form the offsets' sums (A^-1 C)^T b in their own epilogue (Eq. 9;
+        # Eqs. 13-15 per mirror block): the same offsets as the finish pass of the other kernels,
+        # up to the run-to-run float32 rounding of b (mesh atomics in no fixed order)
+        assert np.max(np.abs(pb[v] - pb["rows"])) <= 1e-5
     assert np.max(np.abs(qs["rows"] - qs["stream"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["stream16"])) <= 1e-6
     assert np.max(np.abs(qs["rows"] - qs["sym"])) <= 1e-6
@@ -206,3 +211,31 @@ def test_pair_kernel_z_groups_match_single_cells_and_oracle(plain_ff, case, prec
         assert np.max(np.abs(a["energy"] - b["energy"])) <= tol * np.max(np.abs(b["energy"]))
     with pytest.raises(g.CPMError):
         g.cpm_set_pair_group(s.ctx, 0)
+
+
+@pytest.mark.parametrize("case", ["ff", "dc", "large"])
+def test_packed_variants_at_full_size(case):
+    """The packed kernels at the paper-scale cell (3,024 sites: 24 tile rows, 300 tiles, about two
+    per CTA, a ragged last tile row; the doubled cell: two mirror blocks of the same size), where
+    they form the projection sums in their own epilogue, and at the 10,080-site cell (79 tile rows,
+    about 21 tiles per CTA), where a finish pass forms them, give the charges and offsets of the row
+    kernel, whose charges the full-size tests check against the oracle.  The charge sum stays
+    neutral to float64 rounding either way; b differs between calls at float32 rounding (mesh
+    atomics), which bounds the comparisons (about 2e-6 e in q at the paper-scale cell)."""
+    g, System = _lib()
+    w = synth.config_large_ff() if case == "large" else synth.config_paper_cell(geometry=case)
+    s = System(w, "mixed")
+    res = {}
+    for v in ("rows", "sym", "sym-tma", "sym"):
+        g.cpm_set_sapply_variant(s.ctx, v)
+        for _ in range(2):                          # the second call checks the cleared partial sums
+            s.charges()
+        assert g.cpm_status(s.ctx) == 0
+        q, pb = s.q.cpu().numpy().copy(), s.psibar.cpu().numpy().copy()
+        assert abs(q.sum()) <= 1e-12
+        if v in res:
+            assert np.max(np.abs(q - res[v][0])) <= 1e-5
+        res[v] = (q, pb)
+    for v in ("sym", "sym-tma"):
+        assert np.max(np.abs(res[v][0] - res["rows"][0])) <= 1e-5
+        assert np.max(np.abs(res[v][1] - res["rows"][1])) <= 1e-5
