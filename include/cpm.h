@@ -333,9 +333,13 @@ int cpm_step_charges_static(cpm_ctx* ctx, const int32_t* elyt_offsets_dev, const
  *   CPM_SAPPLY_SYM     S (or each mirror block) kept as the upper triangle of 128 x 128 float32
  *                      tiles: one read of an off-diagonal tile serves its rows and, transposed, its
  *                      columns, so about half the bytes of S are streamed; each tile's row and
- *                      column sums are added into a float64 row vector with atomics, and a second
- *                      kernel finishes the rows.  Same availability as the streaming variants; the
- *                      packed copy costs half an extra float32 S in memory;
+ *                      column sums are added into a float64 row vector with atomics.  With at
+ *                      most 16 tiles per CTA (S of up to about 8,800 rows, or mirror blocks of
+ *                      that size) the same kernel also forms the projection sums (exact
+ *                      fixed-point sums of its float32 products) and the projection finishes the
+ *                      rows; with more tiles a second kernel finishes them.  Same availability as
+ *                      the streaming variants; the packed copy costs half an extra float32 S in
+ *                      memory;
  *   CPM_SAPPLY_SYM_TMA the same packed tiles moved into shared memory by bulk asynchronous copies
  *                      (three 64 KB stages per CTA, all requested at the start; bounded mbarrier
  *                      waits that latch CPM_ERR_TIMEOUT), the right-hand side read per tile.
