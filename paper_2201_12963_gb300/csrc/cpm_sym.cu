@@ -503,19 +503,22 @@ int cpm_internal_sym_setup(cpm_ctx* c) {
   std::vector<float4> w32(rows);
   std::vector<float> c1f(rows);
   c->sym_sv[0] = c->sym_sv[1] = 0.0;
+  bool indicator = true;                        // the kernel's sums take c1 as an indicator
   for (size_t r = 0; r < rows; ++r) {
     const double a = Wh[2 * r], b = Wh[2 * r + 1];
     const float ah = (float)a, bh = (float)b;
     w32[r] = make_float4(ah, (float)(a - (double)ah), bh, (float)(b - (double)bh));
-    if (c1h[r] != 0.0 && c1h[r] != 1.0) return CPM_OK;          // the sums take c1 as an indicator
+    indicator = indicator && (c1h[r] == 0.0 || c1h[r] == 1.0);
     c1f[r] = (float)c1h[r];
     c->sym_sv[0] += svh[r];
     c->sym_sv[1] += c1h[r] * svh[r];
   }
-  CPM_CUDA(cudaMalloc(&c->sym_w32, sizeof(float4) * rows));
-  CPM_CUDA(cudaMalloc(&c->sym_c1f, sizeof(float) * rows));
-  CPM_CUDA(cudaMemcpy(c->sym_w32, w32.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice));
-  CPM_CUDA(cudaMemcpy(c->sym_c1f, c1f.data(), sizeof(float) * rows, cudaMemcpyHostToDevice));
+  if (indicator) {                              // else the finish pass forms the sums (sym_w32 null)
+    CPM_CUDA(cudaMalloc(&c->sym_w32, sizeof(float4) * rows));
+    CPM_CUDA(cudaMalloc(&c->sym_c1f, sizeof(float) * rows));
+    CPM_CUDA(cudaMemcpy(c->sym_w32, w32.data(), sizeof(float4) * rows, cudaMemcpyHostToDevice));
+    CPM_CUDA(cudaMemcpy(c->sym_c1f, c1f.data(), sizeof(float) * rows, cudaMemcpyHostToDevice));
+  }
   CPM_CUDA(cudaDeviceSynchronize());
   CPM_CUDA(cudaFuncSetAttribute(k_sapply_sym, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_smem(npad)));
   CPM_CUDA(cudaFuncSetAttribute(k_sapply_sym_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sym_tma_smem()));
@@ -542,7 +545,8 @@ int cpm_internal_sapply_sym(cpm_ctx* c, int blk, const float* xh, const float* x
   const int nt = c->sym_nt, npad = nt * SY_T;
   const float* Sp = c->sym_S + (size_t)blk * sy_tiles(nt) * SY_T * SY_T;
   double* qpart = c->qpart + (size_t)blk * n;
-  const SymSums fs{c->sym_w32 + (size_t)blk * n, c->sym_c1f + (size_t)blk * n, fuse_sums ? c->scal : nullptr};
+  const SymSums fs = fuse_sums ? SymSums{c->sym_w32 + (size_t)blk * n, c->sym_c1f + (size_t)blk * n, c->scal}
+                               : SymSums{nullptr, nullptr, nullptr};
   if (c->sapply_variant == CPM_SAPPLY_SYM_TMA)
     CPM_CUDA(launch_pdl(k_sapply_sym_tma, c->n_sm, SY_THREADS, sym_tma_smem(), st, Sp, nt, n, xh, xl, qpart,
                         c->wait_test ? 1 : 0, c->status, fs));
