@@ -12,6 +12,7 @@
 // same kernel sums them (each tile's contributions as they are added into qpart, W^T b in one
 // grid-strided pass at its start; the dpsi S v terms are dpsi times sums fixed at setup), so the
 // projection reads qpart itself, adds dpsi S v and clears it for the next call.
+#include "cpm_fixed.cuh"
 #include "cpm_internal.cuh"
 
 #include <algorithm>
@@ -32,63 +33,6 @@ struct SymSums {
   const float* c1;       // second constraint column of the block's rows: an indicator (0 or 1)
   double* scal;          // S_CQ0, S_CQ1, S_WB0, S_WB1 accumulate here (null: no sums)
 };
-
-// Exact fixed-point accumulator: a two's-complement 128-bit integer in units of 2^-FX_F.  A float
-// enters exactly (its 24-bit mantissa shifted into place; only parts below 2^-FX_F, under 1e-26,
-// are dropped), so a sum of any number of floats is exact up to overflow (|sum| < 2^(127 - FX_F),
-// about 5e11: far beyond any charge or potential here); the final conversion to float64 rounds
-// once.  Integer adds keep these sums off GB300's narrow float64 pipe in every tile.
-constexpr int FX_F = 88;
-struct Fx128 {
-  unsigned long long lo = 0, hi = 0;
-  __device__ __forceinline__ void add(unsigned long long al, unsigned long long ah) {
-    lo += al;
-    hi += ah + (lo < al ? 1ull : 0ull);
-  }
-  // the 128-bit image of x (zero for zero, subnormal or non-finite x)
-  __device__ static __forceinline__ void image(float x, unsigned long long& l, unsigned long long& h) {
-    const unsigned int bits = __float_as_uint(x);
-    const int e = (int)((bits >> 23) & 0xffu);
-    const unsigned long long m = (bits & 0x7fffffu) | 0x800000u;
-    const int sh = e - 150 + FX_F;                      // |x| = m 2^(e - 150) = m units << sh
-    l = 0;
-    h = 0;
-    if (e == 0 || e == 0xff || sh <= -24 || sh > 103) return;
-    if (sh >= 64) {
-      h = m << (sh - 64);
-    } else if (sh > 0) {
-      l = m << sh;
-      h = m >> (64 - sh);
-    } else {
-      l = m >> (-sh);
-    }
-    if (bits >> 31) {                                   // two's complement of the magnitude
-      l = ~l + 1ull;
-      h = ~h + (l == 0ull ? 1ull : 0ull);
-    }
-  }
-  __device__ __forceinline__ void add(float x) {
-    unsigned long long l, h;
-    image(x, l, h);
-    add(l, h);
-  }
-  __device__ __forceinline__ void add(const Fx128& o) { add(o.lo, o.hi); }
-  __device__ __forceinline__ void shfl_add(int o) {
-    const unsigned long long ol = __shfl_xor_sync(0xffffffffu, lo, o), oh = __shfl_xor_sync(0xffffffffu, hi, o);
-    add(ol, oh);
-  }
-  __device__ __forceinline__ double value() const {
-    const bool neg = (hi >> 63) != 0;
-    unsigned long long l = lo, h = hi;
-    if (neg) {
-      l = ~l + 1ull;
-      h = ~h + (l == 0ull ? 1ull : 0ull);
-    }
-    const double v = (double)h * 0x1p-24 + (double)l * 0x1p-88;   // 2^(64 - FX_F), 2^-FX_F
-    return neg ? -v : v;
-  }
-};
-static_assert(FX_F == 88, "value() scales by 2^(64 - FX_F) and 2^-FX_F");
 
 // Running sums of one thread: 1^T q_raw, c1^T q_raw, W_0^T b, W_1^T b, less the dpsi S v terms
 // (constants times dpsi, added by the projection).  The S-apply products enter per tile as the
