@@ -116,8 +116,9 @@ struct cpm_ctx {
   double* e_c1m = nullptr;      // [2 nh] zeros then ones (constraint indicator of the S-apply rows)
   double* ypm = nullptr;        // [max_rep][2 ldh] y+ = b_I0 + b_m(I0), y- = b_I0 - b_m(I0)
   double* qpm = nullptr;        // [max_rep][2 nh] q+, q- before the projection
-  // S-apply variant (enum cpm_sapply_variant) and the streaming variant's row partial sums
-  // ([rows of S], float64, zero between calls: its finish kernel clears what it consumed)
+  // S-apply variant (enum cpm_sapply_variant) and the streaming and packed variants' row partial
+  // sums ([rows of S], float64, zero between calls: the finish kernel, or the projection after a
+  // packed S-apply that formed the projection sums itself, clears what it consumed)
   int pair_gz = 1;               // real-space pair kernels: z cells per block (cpm_set_pair_group)
   bool wait_test = false;       // cpm_set_wait_test: the first bounded mbarrier waits give up at once
   int pair_variant = 0;         // enum cpm_pair_variant
