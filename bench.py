@@ -662,6 +662,9 @@ def extras(args, w, s, mixed_res, dev, flush, out):
             out["cpu_baseline"] = ref["cpu_baseline"]
             if args.workload == "paper" and q_batched is not None and "q_batched" in ref:
                 out["batched"]["accuracy"] = batched_accuracy(ref["q_batched"], q_batched)
+                if "batched_step_s" in ref:
+                    out["batched"]["cpu_baseline"] = batched_cpu_baseline(float(ref["batched_step_s"]),
+                                                                          ref["cpu_baseline"].get("cores"))
         else:
             acc["vs_oracle"] = {"error": ref}
     if "accuracy" in done:
@@ -804,6 +807,12 @@ def finish_paper_cell(obj, done, mixed_res, batched_obj, q_batched, fp64_res=Non
             batched_obj["accuracy"] = batched_accuracy(ref["q_batched"], q_batched)
         except Exception as e:
             batched_obj["accuracy"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    if batched_obj is not None and "batched_step_s" in ref:
+        try:
+            batched_obj["cpu_baseline"] = batched_cpu_baseline(float(ref["batched_step_s"]),
+                                                               ref["cpu_baseline"].get("cores"))
+        except Exception as e:
+            batched_obj["cpu_baseline"] = {"error": f"{type(e).__name__}: {e}"[:300]}
 
 
 def graph_step_ms(s, flush, steps, dev, elec=True):
@@ -855,7 +864,8 @@ def batched_replicas(args, dev, flush):
 
 def batched_oracle_charges(n_rep=64):
     """The oracle's charges [n_rep, 672] for every replica of the batched workload (one A and
-    Cholesky factor for the shared electrode, one b and KKT solve per replica)."""
+    Cholesky factor for the shared electrode, one b and KKT solve per replica), and the time of
+    one full oracle step of replica 0 (charges, full-Ewald energy and forces; seconds)."""
     import numpy as np
     import synth
     from oracle import cpm as ocpm
@@ -864,7 +874,20 @@ def batched_oracle_charges(n_rep=64):
     out = np.zeros((n_rep, wb.n_elec))
     for r in range(n_rep):
         out[r] = ref.charges(wb.elyt_xyz[r], wb.elyt_q[r], float(wb.dpsi[r]))[0]
-    return out
+    t0 = time.perf_counter()
+    ref.step(0)
+    return out, time.perf_counter() - t0
+
+
+def batched_cpu_baseline(step_s, cores):
+    """cpu_baseline of the batched line: the oracle steps independent replicas one after another,
+    so its replica-steps/s is the inverse of one replica's full step."""
+    return {"value": round(1.0 / step_s, 4), "unit": "replica-steps/s", "cores": cores, "kind": "oracle",
+            "seconds_per_step": round(step_s, 3),
+            "sample": "one full FP64 oracle step of replica 0 of the batched workload (672 sites: direct "
+                      "Ewald b, KKT solve with a prebuilt Cholesky factor, full-Ewald energy and forces); "
+                      "replicas are independent and the oracle runs them one after another; numpy, BLAS "
+                      "threads = all cores, elementwise work single-threaded"}
 
 
 def batched_accuracy(q_ref, q):
@@ -908,7 +931,7 @@ def child_oracle_step(args):
     dt = time.perf_counter() - t0
     extra = {}
     if os.environ.get("CPM_BENCH_BATCHED") == "1":        # untimed: the batched line's per-replica accuracy
-        extra["q_batched"] = batched_oracle_charges()
+        extra["q_batched"], extra["batched_step_s"] = batched_oracle_charges()
     base = {"value": round(NS_PER_DAY_PER_STEP_PER_S / dt, 6), "unit": "ns/day", "cores": os.cpu_count(),
             "kind": "oracle", "seconds_per_step": round(dt, 3),
             "sample": "one full FP64 oracle step (direct Ewald b, KKT solve with a prebuilt Cholesky factor, "

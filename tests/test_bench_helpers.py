@@ -73,7 +73,10 @@ def test_sampled_oracle_time_model():
 
 
 def test_batched_oracle_charges_are_neutral_per_replica():
-    q = bench.batched_oracle_charges(n_rep=2)
+    q, step_s = bench.batched_oracle_charges(n_rep=2)
     assert q.shape == (2, 672) and np.all(np.isfinite(q))
     assert np.max(np.abs(q.sum(axis=1))) <= 1e-12
     assert np.max(np.abs(q[0] - q[1])) > 1e-3          # different electrolytes and dpsi (0 and 4 V)
+    base = bench.batched_cpu_baseline(step_s, 8)
+    assert step_s > 0 and base["unit"] == "replica-steps/s" and base["kind"] == "oracle"
+    assert abs(base["value"] - 1.0 / step_s) <= 1e-4 and base["cores"] == 8
