@@ -641,6 +641,13 @@ def extras(args, w, s, mixed_res, dev, flush, out):
         out["batched"], q_batched = batched_replicas(args, dev, flush)
     except Exception as e:
         out["batched"] = {"error": f"{type(e).__name__}: {e}"[:300]}
+    torch.cuda.empty_cache()
+    plain_pending = None
+    if args.workload == "dc-large":
+        try:
+            out["plain_cell"], plain_pending = plain_cell(args, dev, flush, tmp)
+        except Exception as e:
+            out["plain_cell"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     # ---- CPU: the oracle ----
     acc = {"vs_plain_fp64_gpu": prec}
     first = []
@@ -674,6 +681,11 @@ def extras(args, w, s, mixed_res, dev, flush, out):
     if paper_pending is not None:
         finish_paper_cell(out["paper_cell"], done["paper"], paper_pending[1], out.get("batched"), q_batched,
                           paper_pending[4])
+    if plain_pending is not None:
+        try:
+            finish_plain_cell(out["plain_cell"], plain_pending[0], plain_pending[1], tmp)
+        except Exception as e:
+            out["plain_cell"]["accuracy"] = {"error": f"{type(e).__name__}: {e}"[:300]}
     if not args.no_cpu_baseline and args.workload not in DENSE_ORACLE:
         ok, res = finish_child(spawn_child(args, "oracle-sample", wfile, os.path.join(tmp, "cpu_all.json"),
                                            cores=os.cpu_count() or 1))
@@ -860,6 +872,49 @@ def batched_replicas(args, dev, flush):
             "plain_fp64_one_replica": {"ms_per_step": round(ms_1, 5), "steps_per_s": round(1e3 / ms_1, 1)},
             "speedup_replica_steps": round((64 / ms_b) / (1 / ms_1), 2), "status": st,
             "phase_ms": {k: round(v, 5) for k, v in phase_ms.items()}, "roofline": roof}, q_b
+
+
+def plain_cell(args, dev, flush, tmp):
+    """The 672-site plain finite-field cell (17.04 x 17.22 x 60 A, 100 + 100 point ions, dpsi 2 V,
+    mesh 18 x 18 x 60 order 5) on the float64 path: one step with forces on all sites, timed as
+    graph replays (latency-bound: its S is 3.6 MB).  Returns the object and (its results, the
+    workload file for the oracle children)."""
+    import synth
+    import paper_2201_12963_gb300 as g
+    from paper_2201_12963_gb300.driver import System
+    w = synth.config_plain_ff()
+    wfile = os.path.join(tmp, "plain.pkl")
+    with open(wfile, "wb") as f:
+        pickle.dump(w, f)
+    s = System(w, "fp64", device=dev)
+    steps = max(10, min(args.steps, 200))
+    ms = graph_step_ms(s, flush, steps, dev)
+    res = step_results(s, True)
+    obj = {"workload": "672-site plain finite-field cell (17.04x17.22x60 A), 100 + 100 point ions "
+                       "+-0.78 e, dpsi 2 V, mesh 18x18x60 order 5, forces on all sites",
+           "precision": "fp64", "ms_per_step": round(ms, 5), "steps_per_s": round(1e3 / ms, 1),
+           "value": round(NS_PER_DAY_PER_STEP_PER_S * 1e3 / ms, 2), "unit": "ns/day", "steps": steps,
+           "status": g.cpm_status(s.ctx)}
+    return obj, (res, wfile)
+
+
+def finish_plain_cell(obj, res, wfile, tmp):
+    """The plain cell's oracle comparison and the oracle's step time on all cores and on one core
+    (one child after the other)."""
+    a1 = argparse.Namespace(workload="paper", seed=WORKLOADS["paper"][1])
+    ok, ref = finish_child(spawn_child(a1, "oracle-step", wfile, os.path.join(tmp, "plain_all.npz"),
+                                       cores=os.cpu_count() or 1))
+    if not ok:
+        obj["accuracy"] = {"vs_oracle": {"error": ref}}
+        return
+    obj["accuracy"] = {"vs_oracle": accuracy_against(ref, res)}
+    base = dict(ref["cpu_baseline"])
+    ok1, ref1 = finish_child(spawn_child(a1, "oracle-step", wfile, os.path.join(tmp, "plain_1.npz"), cores=1))
+    base["one_core"] = ref1["cpu_baseline"] if ok1 else {"error": ref1}
+    if ok1:
+        base["one_core"]["cores"] = 1
+        base["one_core"]["sample"] = "the same oracle step with BLAS threads = 1"
+    obj["cpu_baseline"] = base
 
 
 def batched_oracle_charges(n_rep=64):

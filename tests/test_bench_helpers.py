@@ -80,3 +80,24 @@ def test_batched_oracle_charges_are_neutral_per_replica():
     base = bench.batched_cpu_baseline(step_s, 8)
     assert step_s > 0 and base["unit"] == "replica-steps/s" and base["kind"] == "oracle"
     assert abs(base["value"] - 1.0 / step_s) <= 1e-4 and base["cores"] == 8
+
+
+def test_plain_cell_oracle_comparison_and_baselines(tmp_path):
+    """The 672-site plain cell's oracle children: the comparison against a result, and the oracle's
+    step time on all cores and on one core."""
+    import pickle
+    import synth
+    from oracle import cpm as ocpm
+    w = synth.config_plain_ff()
+    wfile = str(tmp_path / "plain.pkl")
+    with open(wfile, "wb") as f:
+        pickle.dump(w, f)
+    out = ocpm.Reference(w).step(0)
+    res = {"q": out["q"] + 1e-7, "F_elyt": out["F_elyt"], "energy": np.array([out["U"], out["H"], 0.0, 0.0])}
+    obj = {}
+    bench.finish_plain_cell(obj, res, wfile, str(tmp_path))
+    acc = obj["accuracy"]["vs_oracle"]
+    assert abs(acc["dq_max_e"] - 1e-7) < 1e-12 and acc["force_rms_rel"] == 0.0 and acc["energy_U_rel"] == 0.0
+    base = obj["cpu_baseline"]
+    assert base["kind"] == "oracle" and base["unit"] == "ns/day" and base["seconds_per_step"] > 0
+    assert base["one_core"]["cores"] == 1 and base["one_core"]["seconds_per_step"] > 0
