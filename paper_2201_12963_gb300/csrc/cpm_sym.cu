@@ -8,10 +8,12 @@
 // and S_IJ^T x_I (rows of block J), so the HBM bytes per step are about half of the full matrix.
 // Each tile's 128 row products and 128 transposed products are added into a float64 row vector
 // (qpart, shared with the streaming variant) with atomics, nt additions per row from different
-// CTAs.  The projection (Eq. 9) needs C^T q_raw and (A^-1 C)^T b of q_raw = qpart + dpsi S v: the
-// same kernel sums them (each tile's contributions as they are added into qpart, W^T b in one
-// grid-strided pass at its start; the dpsi S v terms are dpsi times sums fixed at setup), so the
-// projection reads qpart itself, adds dpsi S v and clears it for the next call.
+// CTAs.  The projection (Eq. 9) needs C^T q_raw and (A^-1 C)^T b of q_raw = qpart + dpsi S v.  With
+// at most SY_FUSE_TILES_PER_CTA tiles per CTA the same kernel sums them (each tile's contributions
+// as they are added into qpart, exactly, in fixed point; W^T b in one grid-strided pass at its
+// start; the dpsi S v terms are dpsi times sums fixed at setup), and the projection reads qpart
+// itself, adds dpsi S v and clears it for the next call; with more tiles per CTA k_sapply_finish
+// forms q_raw and the sums in float64 and clears qpart.
 #include "cpm_fixed.cuh"
 #include "cpm_internal.cuh"
 
